@@ -1,0 +1,186 @@
+"""Pins for the oracle's random-number and math building blocks.
+
+Philox-4x32-10 is checked against an independent library implementation
+(Triton's ``tl.philox`` run by its CPU interpreter) on random counters and
+keys; the uniform map, the logarithm, the isotropic direction, the elastic
+kinematics, the rotation and the tabulated-CDF sampler are checked against
+closed forms, library routines and exact properties.
+"""
+import json
+import math
+import os
+import subprocess
+import sys
+
+import numpy as np
+import pytest
+
+import oracle
+
+_TRITON_SCRIPT = r"""
+import json, os, sys
+os.environ["TRITON_INTERPRET"] = "1"
+import numpy as np, torch, triton, triton.language as tl
+
+@triton.jit
+def _k(ctr_ptr, out_ptr, seed, N: tl.constexpr):
+    i = tl.arange(0, N)
+    c0 = tl.load(ctr_ptr + 4 * i + 0).to(tl.uint32)
+    c1 = tl.load(ctr_ptr + 4 * i + 1).to(tl.uint32)
+    c2 = tl.load(ctr_ptr + 4 * i + 2).to(tl.uint32)
+    c3 = tl.load(ctr_ptr + 4 * i + 3).to(tl.uint32)
+    a, b, c, d = tl.philox(seed, c0, c1, c2, c3, 10)
+    tl.store(out_ptr + 4 * i + 0, a.to(tl.int64) & 0xFFFFFFFF)
+    tl.store(out_ptr + 4 * i + 1, b.to(tl.int64) & 0xFFFFFFFF)
+    tl.store(out_ptr + 4 * i + 2, c.to(tl.int64) & 0xFFFFFFFF)
+    tl.store(out_ptr + 4 * i + 3, d.to(tl.int64) & 0xFFFFFFFF)
+
+req = json.loads(sys.stdin.read())
+res = []
+for seed, ctrs in req:
+    ctr = torch.tensor(ctrs, dtype=torch.int64).reshape(-1)
+    n = len(ctrs)
+    out = torch.zeros(4 * n, dtype=torch.int64)
+    _k[(1,)](ctr, out, seed, n)
+    res.append(out.reshape(n, 4).tolist())
+print(json.dumps(res))
+"""
+
+
+def test_philox_matches_independent_library_implementation():
+    pytest.importorskip("triton")
+    rng = np.random.default_rng(123)
+    req = []
+    seeds = [0, 1, 0x123456789ABCDEF0, (1 << 64) - 1, int(rng.integers(0, 1 << 62))]
+    for s in seeds:
+        ctrs = rng.integers(0, 1 << 32, size=(16, 4), dtype=np.uint64).astype(np.int64)
+        ctrs[0] = 0
+        ctrs[1] = (1 << 32) - 1
+        req.append([s if s < (1 << 63) else s - (1 << 64), ctrs.tolist()])
+    env = dict(os.environ, TRITON_INTERPRET="1")
+    p = subprocess.run([sys.executable, "-c", _TRITON_SCRIPT], input=json.dumps(req), capture_output=True,
+                       text=True, env=env, timeout=600)
+    if p.returncode != 0:
+        pytest.skip("triton interpreter unavailable: " + p.stderr.strip().splitlines()[-1])
+    ref = json.loads(p.stdout)
+    n = 0
+    for (s, ctrs), outs in zip(req, ref):
+        s &= (1 << 64) - 1
+        key = (s & 0xFFFFFFFF, s >> 32)
+        for c, o in zip(ctrs, outs):
+            assert oracle.philox(c, key) == tuple(o), (c, key)
+            n += 1
+    assert n == 80
+
+
+def test_uniform_map_is_exact_and_open():
+    # ((w >> 12) + 1/2) 2^-52 for the extreme words and a random sample
+    assert oracle.uniform(0, 0) == 2.0 ** -53
+    assert oracle.uniform(0xFFFFFFFF, 0xFFFFFFFF) == 1.0 - 2.0 ** -53
+    rng = np.random.default_rng(5)
+    for lo, hi in rng.integers(0, 1 << 32, size=(2000, 2)):
+        u = oracle.uniform(int(lo), int(hi))
+        w = (int(hi) << 32) | int(lo)
+        assert u == ((w >> 12) + 0.5) / 2.0 ** 52          # exact rational value
+        assert 0.0 < u < 1.0
+
+
+def _ulp(x):
+    return math.ulp(x)
+
+
+def test_log_against_library_log():
+    rng = np.random.default_rng(7)
+    xs = list(rng.random(20000) + 2.0 ** -53)
+    xs += [2.0 ** -k for k in range(1, 60)]
+    xs += [1.0 - k * 2.0 ** -53 for k in range(1, 200)] + [1.0 + k * 2.0 ** -52 for k in range(1, 200)]
+    xs += [math.sqrt(2.0) * (1 + d) for d in (-2e-16, 0.0, 2e-16)] + [math.sqrt(0.5), 0.75, 1.5, 3.0, 1e300, 1e-300]
+    xs += list(np.exp(rng.uniform(-700, 700, 5000)))
+    worst = 0.0
+    for x in xs:
+        got, ref = oracle.log(x), math.log(x)
+        if ref == 0.0:
+            assert got == 0.0
+            continue
+        err = abs(got - ref) / _ulp(ref)
+        worst = max(worst, err)
+    # the atanh series keeps the error within a few units in the last place
+    assert worst <= 4.0, worst
+    assert oracle.log(1.0) == 0.0
+    assert oracle.log(2.0) == math.log(2.0)
+
+
+def test_isotropic_direction_moments():
+    rng = np.random.default_rng(9)
+    n = 40000
+    d = np.array([oracle.iso_dir(1, 0, i, 3, float(rng.random() * (1 - 2 ** -52) + 2 ** -53)) for i in range(n)])
+    norm = np.linalg.norm(d, axis=1)
+    assert np.all(np.abs(norm - 1.0) < 1e-14)
+    se = 1.0 / math.sqrt(n)
+    for k in range(3):
+        assert abs(d[:, k].mean()) < 5 * se * math.sqrt(1 / 3)
+        assert abs((d[:, k] ** 2).mean() - 1 / 3) < 5 * se * math.sqrt(4 / 45)
+    # azimuth uniform: the y-z projection angle has zero mean cosine/sine of 2phi
+    phi = np.arctan2(d[:, 2], d[:, 1])
+    assert abs(np.cos(2 * phi).mean()) < 5 * se
+    assert abs(np.sin(phi).mean()) < 5 * se
+
+
+@pytest.mark.parametrize("A", [1.0, 2.0, 16.0, 238.0])
+def test_elastic_kinematics_closed_forms(A):
+    # isotropic in the CM frame: E'/E uniform on [alpha, 1] and <mu_lab> = 2/(3A)
+    alpha = ((A - 1) / (A + 1)) ** 2
+    rng = np.random.default_rng(int(A))
+    mus = 2.0 * rng.random(40000) - 1.0
+    res = np.array([oracle.elastic(A, 1e6, float(m)) for m in mus])
+    r = res[:, 0] / 1e6
+    assert np.all(r >= alpha * (1 - 1e-12)) and np.all(r <= 1 + 1e-12)
+    n = len(mus)
+    assert abs(r.mean() - (1 + alpha) / 2) < 5 * (1 - alpha) / math.sqrt(12 * n)
+    assert abs(res[:, 1].mean() - 2.0 / (3.0 * A)) < 5 / math.sqrt(n)
+    assert np.all(np.abs(res[:, 1]) <= 1.0 + 1e-15)
+    # forward and backward scattering limits
+    e, mu = oracle.elastic(A, 1.0, 1.0)
+    assert abs(e - 1.0) < 1e-15 and abs(mu - 1.0) < 1e-15
+
+
+def test_rotation_preserves_norm_and_angle():
+    rng = np.random.default_rng(3)
+    for _ in range(3000):
+        d = rng.normal(size=3)
+        d /= np.linalg.norm(d)
+        if rng.random() < 0.05:
+            d = np.array([0.0, 0.0, 1.0 if rng.random() < 0.5 else -1.0])
+        mu = 2 * rng.random() - 1
+        phi = 2 * math.pi * rng.random()
+        o = oracle.rotate(d, mu, math.cos(phi), math.sin(phi))
+        assert abs(np.linalg.norm(o) - 1.0) < 1e-12
+        assert abs(float(np.dot(o, d)) - mu) < 1e-12
+
+
+def test_cdf_sampler_against_piecewise_linear_expectation():
+    E = np.array([0.0, 1.0, 3.0, 4.0, 10.0])
+    P = np.array([0.0, 0.1, 0.5, 0.6, 1.0])
+    # within each interval the sample is uniform: mean = sum dP (E_k + E_k+1) / 2
+    exact = float(np.sum(np.diff(P) * 0.5 * (E[1:] + E[:-1])))
+    rng = np.random.default_rng(1)
+    xi = rng.random(100000) * (1 - 2 ** -52) + 2 ** -53
+    s = np.array([oracle.cdf_sample(E, P, float(x)) for x in xi])
+    var = float(np.sum(np.diff(P) * ((E[1:] ** 2 + E[1:] * E[:-1] + E[:-1] ** 2) / 3.0))) - exact ** 2
+    assert abs(s.mean() - exact) < 5 * math.sqrt(var / len(xi))
+    # exact knots map to the knot energies
+    for k in range(len(E) - 1):
+        assert oracle.cdf_sample(E, P, float(P[k])) == E[k]
+
+
+def test_nuclide_index_against_linear_search():
+    rng = np.random.default_rng(4)
+    e = np.unique(np.exp(rng.uniform(-11, 16, 5000)))
+    qs = np.concatenate([rng.uniform(e[0], e[-1], 5000), e, [e[0], e[-1], e[-1] * 2]])
+    ref = np.minimum(np.searchsorted(e, qs, side="right") - 1, len(e) - 2)
+    got = np.array([oracle.nuclide_index(e, float(q)) for q in qs])
+    assert np.array_equal(got, ref)
+    # literal linear scan on a subset
+    for q in qs[::97]:
+        lin = max(i for i in range(len(e) - 1) if e[i] <= q)
+        assert oracle.nuclide_index(e, float(q)) == lin
