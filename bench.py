@@ -1,0 +1,340 @@
+#!/usr/bin/env python
+"""Throughput of the event-based Monte Carlo transport loop on GB300.
+
+Workload: the C5G7-shaped 7-group lattice k-eigenvalue problem with synthetic
+cross sections (2x2 assemblies of 17x17 pins plus reflector), 1e6 histories
+per batch, 20 inactive + 50 active batches, 51x51x1 pin-mesh flux tally.  One
+step is one complete power iteration of that workload (all batches: source,
+lookup, distance, move, collide / cross, tally, remap, bank ordering,
+splitting roulette).  The metric is particle events per second (collision and
+surface outcomes; source events excluded) over the whole job.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+With N > 1 (torchrun) every rank runs an independent replica with its own
+seed (weak scaling, no collective on the data path); rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+N_PER_BATCH = 1_000_000
+N_INACTIVE, N_ACTIVE = 20, 50
+WORKLOAD = "c5g7-shaped 7-group lattice k-eigenvalue, 1e6 histories/batch, 20 inactive + 50 active batches"
+
+# Algorithmic bytes per event of an event-based implementation: the particle
+# record read and written once (position, direction, cached reciprocals of
+# the direction, group, cell, history index, event count, site count, pending
+# flags: 10 x 8 + 6 x 4 = 104 bytes each way).  Cross sections (3.5 KB) and
+# the 20.8 KB tally stay on chip.
+B_EVENT = 2 * 104
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), float(p.get("sm_max_mhz", 2070.0)), "measured"
+    except Exception:
+        return 6800.0, 2070.0, "fallback"
+
+
+# FP64 issue model of GB300 (measured: 2 FP64 add/mul/fma thread-operations per
+# clock per SM; 152 SMs): peak = 152 * 2 * f_max.
+FP64_OPS_PER_CLK_PER_SM = 2.0
+N_SM = 152
+
+
+class ClockSampler:
+    """Samples nvidia-smi SM clocks and throttle reasons during a region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.samples = []
+        self._stop = threading.Event()
+        self._t = None
+
+    def _run(self):
+        while not self._stop.is_set():
+            try:
+                out = subprocess.run(["nvidia-smi", f"--id={self.dev}", f"--query-gpu={self.FIELDS}",
+                                      "--format=csv,noheader,nounits"], capture_output=True, text=True, timeout=5)
+                if out.returncode == 0 and out.stdout.strip():
+                    self.samples.append([x.strip() for x in out.stdout.strip().split(",")])
+            except Exception:
+                pass
+            self._stop.wait(0.2)
+
+    def __enter__(self):
+        self._t = threading.Thread(target=self._run, daemon=True)
+        self._t.start()
+        return self
+
+    def __exit__(self, *a):
+        self._stop.set()
+        if self._t:
+            self._t.join(timeout=10)
+
+    def summary(self):
+        if not self.samples:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        mhz = [float(s[1]) for s in self.samples if s[1].replace(".", "").isdigit()]
+        mx = [float(s[2]) for s in self.samples if s[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for s in self.samples:
+            for name, v in zip(names, s[5:9]):
+                if v.strip().lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(mhz) if mhz else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(self.samples)}
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def _cpu_baseline(seconds_budget: float = 15.0):
+    """The oracle, as it stands, on a bounded sample of the same workload."""
+    import oracle
+    from paper_2506_00263_gb300 import inputs
+    p = inputs.c5g7_lattice()
+    nper, ni, na = 100_000, 2, 8
+    t0 = time.perf_counter()
+    r = oracle.power_iteration(p, nper, ni, na, seed=1)
+    dt = time.perf_counter() - t0
+    ev = int(r["events_by_type"][1:].sum())
+    return {"value": ev / dt, "unit": "events/s", "cores": 1, "kind": "oracle",
+            "sample": f"lattice power iteration, {nper} histories/batch x {ni + na} batches "
+                      f"({ev} events, {dt:.1f} s, one host core)",
+            "histories_per_s": nper * (ni + na) / dt}
+
+
+def run_reference(args):
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return 0
+    import oracle
+    from paper_2506_00263_gb300 import inputs
+    p = inputs.c5g7_lattice()
+    nper, ni, na = 50_000, 1, 2          # a bounded sample of the workload per step
+    for _ in range(args.warmup):
+        oracle.power_iteration(p, nper, ni, na, seed=1)
+    ev_tot, t_tot = 0, 0.0
+    for k in range(args.steps):
+        t0 = time.perf_counter()
+        r = oracle.power_iteration(p, nper, ni, na, seed=1 + k)
+        t_tot += time.perf_counter() - t0
+        ev_tot += int(r["events_by_type"][1:].sum())
+    value = ev_tot / t_tot
+    line = {"impl": "reference", "metric": "particle-events/s", "value": value, "unit": "events/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * t_tot / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD + f" (oracle sample: {nper}/batch x {ni + na} batches per step)",
+                       "l2": "n/a (host)"},
+            "cpu_baseline": {"value": value, "unit": "events/s", "cores": 1, "kind": "oracle",
+                             "sample": f"{nper} histories/batch x {ni + na} batches per step, one core"},
+            "e2e": {"value": value, "unit": "events/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    ws, rank, local = _dist()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    from paper_2506_00263_gb300 import binding as tb
+    from paper_2506_00263_gb300 import build as tbuild
+    from paper_2506_00263_gb300 import inputs
+
+    if rank == 0 or not os.path.exists(tbuild.LIB):
+        tbuild.build()
+    if ws > 1:
+        torch.distributed.barrier()
+    scheme = tb.SCHEME_ASYNC if args.scheme == "async" else tb.SCHEME_STACK
+    decomp = tb.DECOMP_SPLIT if args.decomp == "split" else tb.DECOMP_MONO
+    spec = inputs.c5g7_lattice()
+    opts = tb.RunOpts(seed=1 + 1000 * rank, scheme=scheme, decomposition=decomp)
+    stream = torch.cuda.current_stream()
+    prob = tb.Problem(spec)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float64, device="cuda")   # 512 MB > L2
+
+    def step(p):
+        return p.power_iteration(args.n_per_batch, args.inactive, args.active, opts)
+
+    for _ in range(args.warmup):
+        step(prob)
+    torch.cuda.synchronize()
+    if ws > 1:
+        torch.distributed.barrier()
+    launches0 = tb.kernel_launch_count()
+    ev_tot = hist_tot = 0
+    kern_s = 0.0
+    kern_launches = 0
+    times = []
+    sampler = ClockSampler(torch.cuda.current_device())
+    torch.cuda.synchronize()
+    with sampler:
+        for k in range(args.steps):
+            flush.fill_(float(k))
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            r = step(prob)
+            e1.record(stream)
+            e1.synchronize()
+            times.append(e0.elapsed_time(e1) * 1e-3)
+            ev_tot += int(r["events"])
+            hist_tot += int(r["histories"])
+            kern_s += r["transport_seconds"]
+            kern_launches += int(r["transport_launches"])
+    torch.cuda.synchronize()
+    launches = tb.kernel_launch_count() - launches0      # this library's kernels only (the L2 flush is torch's)
+    t = sum(times)
+    if ws > 1:
+        tt = torch.tensor([t, float(ev_tot), float(hist_tot)], dtype=torch.float64, device="cuda")
+        tmax = tt.clone()
+        torch.distributed.all_reduce(tmax[:1], op=torch.distributed.ReduceOp.MAX)
+        torch.distributed.all_reduce(tt[1:], op=torch.distributed.ReduceOp.SUM)
+        t, ev_all, hist_all = float(tmax[0]), float(tt[1]), float(tt[2])
+    else:
+        ev_all, hist_all = float(ev_tot), float(hist_tot)
+    value = ev_all / t
+
+    # ---- roofline of the dominant kernel (the transport loop) ----
+    hbm, fmax, peak_kind = _peaks()
+    avg_launch = kern_s / max(kern_launches, 1)
+    ev_per_launch = ev_tot / max(kern_launches, 1)
+    fp64_ops_per_event = FP64_OPS_PER_EVENT.get((args.scheme, args.decomp))
+    fp64_peak = N_SM * FP64_OPS_PER_CLK_PER_SM * fmax * 1e6 / 1e12     # TFLOP/s
+    if fp64_ops_per_event:
+        ach = fp64_ops_per_event * ev_per_launch / avg_launch / 1e12
+        roof = {"bound": "alu", "achieved": ach, "peak": fp64_peak, "unit": "TFLOP/s", "frac": ach / fp64_peak,
+                "traffic": None, "what": "FP64 pipe (add/mul/fma) of the transport kernel, "
+                                         f"{fp64_ops_per_event:.0f} FP64 ops/event",
+                "peak_source": f"derived: {N_SM} SMs x {FP64_OPS_PER_CLK_PER_SM:g} FP64/clk x {fmax:.0f} MHz"}
+    else:
+        roof = None
+    hbm_ach = B_EVENT * ev_per_launch / avg_launch / 1e9
+    hbm_roof = {"bound": "hbm", "achieved": hbm_ach, "peak": hbm, "unit": "GB/s", "frac": hbm_ach / hbm,
+                "traffic": None, "what": f"{B_EVENT} algorithmic bytes/event, {peak_kind} peak"}
+    if roof is None:
+        roof = hbm_roof
+
+    # ---- end to end through the C ABI with host buffers ----
+    e2e = None
+    if rank == 0 and args.e2e_steps > 0:
+        pinned_spec, h2d = _pinned_copy(spec, torch)
+        torch.cuda.synchronize()
+        ev_e, t_e = 0, 0.0
+        d2h = 0
+        for k in range(args.e2e_steps):
+            flush.fill_(float(k))
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            p2 = tb.Problem(pinned_spec)
+            r = step(p2)
+            mesh = p2.tally(tb.TALLY_MESH)
+            sc = p2.tally(tb.TALLY_SCALARS)
+            p2.close()
+            torch.cuda.synchronize()
+            t_e += time.perf_counter() - t0
+            ev_e += int(r["events"])
+            d2h = mesh.nbytes + sc.nbytes + 3 * 8 * (args.inactive + args.active)
+        e2e = {"value": ev_e / t_e, "unit": "events/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
+
+    if rank != 0:
+        return 0
+    cpu = None if args.no_cpu_baseline else _cpu_baseline()
+    line = {
+        "metric": "particle-events/s", "value": value, "unit": "events/s", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "scheme": args.scheme, "decomposition": args.decomp,
+                   "n_per_batch": args.n_per_batch, "batches": args.inactive + args.active,
+                   "l2": "flushed between steps (512 MB write)"},
+        "histories_per_s": hist_all / t,
+        "roofline": roof, "hbm_roofline": hbm_roof,
+        "e2e": e2e, "cpu_baseline": cpu, "gpu_launches": launches,
+        "clocks": sampler.summary(),
+        "transport": {"kernel_seconds": kern_s, "launches": kern_launches, "avg_launch_ms": 1e3 * avg_launch},
+    }
+    print(json.dumps(line), flush=True)
+    prob.close()
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+# FP64 thread-operations (dadd + dmul + dfma, divisions and square roots
+# included as executed) per transport event, from an ncu capture of the
+# transport kernel on the lattice workload.
+FP64_OPS_PER_EVENT = {}
+
+
+def _pinned_copy(spec, torch):
+    """The problem's arrays copied into page-locked host memory; returns the
+    spec and the bytes the library uploads."""
+    import numpy as np
+    nbytes = 0
+    kw = {}
+    for name in ("x_planes", "y_planes", "z_planes", "cell_material", "pin_material", "sigma_t", "sigma_s",
+                 "nu_sigma_f", "chi", "src_materials"):
+        a = getattr(spec, name)
+        if a is None:
+            continue
+        t = torch.empty(a.shape, dtype={np.dtype("float64"): torch.float64, np.dtype("int32"): torch.int32,
+                                        np.dtype("uint8"): torch.uint8}[a.dtype], pin_memory=True)
+        t.numpy()[...] = a
+        kw[name] = t.numpy()
+        nbytes += a.nbytes
+    return spec.replace(**kw), nbytes
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--scheme", choices=["async", "stack"], default="async")
+    ap.add_argument("--decomp", choices=["split", "mono"], default="split")
+    ap.add_argument("--n-per-batch", type=int, default=N_PER_BATCH)
+    ap.add_argument("--inactive", type=int, default=N_INACTIVE)
+    ap.add_argument("--active", type=int, default=N_ACTIVE)
+    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "ours":
+        print("warning: fewer than 3 warm-up steps", file=sys.stderr)
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,247 @@
+/*
+ * tr.h -- C ABI of the GB300-native event-based Monte Carlo transport library.
+ *
+ * The library advances neutron histories event by event on one GPU and
+ * regroups ("remaps") particles between events so that every warp executes a
+ * single event type: thread-data remapping, the event-based approach of
+ * Cuneo, Morgan, Variansyah, Niemeyer (M&C 2025), Sec. 2.  Two remapping
+ * schemes are provided: stack-based (Sec. 3.1) and asynchronous (Sec. 3.2),
+ * each with the monolithic ("step" = one history-loop iteration) or the
+ * decomposed (step / collision / surface crossing) task scheme of Sec. 4.
+ *
+ * Conventions shared by every entry point:
+ *  - All arguments are plain C types.  Host pointers are read during the call
+ *    only and never retained; the library copies what it needs.
+ *  - Every function returns a tr_status.  No C++ exception crosses this
+ *    boundary, the library never aborts and no device code traps.  On any
+ *    status other than TR_OK, tr_last_error() returns a one-line message for
+ *    the calling thread.
+ *  - Device memory comes from the allocator callbacks of tr_device_ctx (or
+ *    cudaMallocAsync/cudaFreeAsync on the context stream when they are NULL)
+ *    and all work is enqueued on the context stream.  Functions that return
+ *    results on the host synchronise that stream before returning.
+ *  - Floating point: IEEE binary64 everywhere, FMA contraction disabled.
+ */
+#ifndef TR_H
+#define TR_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    TR_OK = 0,
+    TR_ERR_INVALID = 1,   /* malformed description or options */
+    TR_ERR_NOMEM = 2,     /* allocation failed */
+    TR_ERR_CAPACITY = 3,  /* a particle queue, link arena or fission bank overflowed */
+    TR_ERR_TIMEOUT = 4,   /* a bounded device spin-wait gave up (max_spin) */
+    TR_ERR_CUDA = 5,      /* a CUDA runtime call failed */
+    TR_ERR_STATE = 6      /* call order violated (e.g. no prior forward run) */
+} tr_status;
+
+/* Event / final-state codes, the event vocabulary of Sec. 4. */
+enum {
+    TR_EV_SOURCE = 0, TR_EV_SCATTER = 1, TR_EV_ABSORB = 2, TR_EV_SURF_INTERNAL = 3,
+    TR_EV_SURF_REFLECT = 4, TR_EV_LEAK = 5, TR_EV_CUTOFF = 6, TR_EV_MAXEV = 7
+};
+
+enum { TR_BC_VACUUM = 0, TR_BC_REFLECT = 1 };
+enum { TR_XS_MG = 0, TR_XS_CE = 1 };
+enum { TR_SRC_POINT = 0, TR_SRC_BOX = 1, TR_SRC_PINS = 2 };
+/* Remapping scheme: stack-based (Sec. 3.1) or asynchronous (Sec. 3.2). */
+enum { TR_SCHEME_STACK = 0, TR_SCHEME_ASYNC = 1 };
+/* Task decomposition (Sec. 4): one "step" event, or step / collision / surface. */
+enum { TR_DECOMP_MONO = 0, TR_DECOMP_SPLIT = 1 };
+
+/* Rectilinear grid of cells; each cell may hold one z-aligned cylinder
+ * ("pin") of radius pin_radius centred in its x-y box.  Planes are ascending;
+ * the outermost z planes may be -inf/+inf (unbounded).  Arrays are row-major
+ * [nz][ny][nx].  pin_material < 0 (or a NULL array) means no pin. */
+typedef struct {
+    int32_t nx, ny, nz;                 /* 1 .. 1023 each */
+    const double *x_planes;             /* nx + 1 */
+    const double *y_planes;             /* ny + 1 */
+    const double *z_planes;             /* nz + 1 */
+    int32_t bc[6];                      /* faces x-, x+, y-, y+, z-, z+ */
+    const int32_t *cell_material;       /* [nz][ny][nx] */
+    const int32_t *pin_material;        /* [nz][ny][nx] or NULL */
+    double pin_radius;
+} tr_geometry_desc;
+
+/* Cross sections.  Multigroup: sigma_t[m][g], sigma_s[m][g][g'] (from g to
+ * g'), nu_sigma_f[m][g], chi[m][g].  Continuous energy: per nuclide an
+ * ascending energy grid (eV) with elastic, capture and fission cross sections
+ * (barn) per point, rows concatenated over nuclides (nuc_offset[n]..
+ * nuc_offset[n+1]); target mass ratio A per nuclide; number densities
+ * density[m][n] (atoms / barn cm).  Histories below energy_cutoff end. */
+typedef struct {
+    int32_t kind;                       /* TR_XS_MG or TR_XS_CE */
+    int32_t n_materials;                /* 1 .. 256 */
+    int32_t n_groups;                   /* MG: 1 .. 128 */
+    const double *sigma_t, *sigma_s, *nu_sigma_f, *chi;
+    int32_t n_nuclides;                 /* CE: 1 .. 16 */
+    const int64_t *nuc_offset;          /* n_nuclides + 1 */
+    const double *nuc_energy;           /* nuc_offset[n_nuclides] */
+    const double *nuc_sigma;            /* [row][3] elastic, capture, fission */
+    const double *nuc_awr;              /* n_nuclides */
+    const double *density;              /* [n_materials][n_nuclides] */
+    double energy_cutoff;
+} tr_xs_desc;
+
+/* Source (the make_work entry point of Sec. 3).  POINT: fixed position,
+ * isotropic unless `isotropic` is 0 (then `direction`).  BOX: uniform in
+ * [lo, hi].  PINS: uniform in [lo, hi] restricted by rejection to pins whose
+ * material has source_material[m] != 0.  Multigroup group: `group`, or chi of
+ * the birth material when group < 0.  CE energy: tabulated inverse CDF
+ * (cdf_energy, cdf_prob with n_cdf points) or `energy` when n_cdf == 0. */
+typedef struct {
+    int32_t kind;
+    int32_t isotropic;
+    int32_t group;
+    int32_t n_cdf;
+    double point[3], direction[3], lo[3], hi[3];
+    double energy;
+    const uint8_t *source_material;     /* [n_materials] (PINS) */
+    const double *cdf_energy, *cdf_prob;
+} tr_source_desc;
+
+/* Tallies: an optional track-length flux mesh over [lo, hi] with n cells per
+ * axis (per group when by_group != 0, multigroup only), and an optional
+ * continuous-energy flux tally per material over n_energy_bins bins with
+ * ascending edges.  The flux, absorption-rate and production-rate totals are
+ * always scored. */
+typedef struct {
+    int32_t has_mesh;
+    int32_t mesh_n[3];
+    int32_t by_group;
+    int32_t n_energy_bins;
+    double mesh_lo[3], mesh_hi[3];
+    const double *energy_edges;         /* n_energy_bins + 1 */
+} tr_tally_desc;
+
+/* Device context.  alloc/free (optional) receive the byte size or pointer,
+ * the stream and `user`; they must return 256-byte aligned device memory
+ * usable on `stream`.  When both are NULL the library uses
+ * cudaMallocAsync / cudaFreeAsync on `stream`. */
+typedef struct {
+    int32_t device;
+    void *stream;                       /* cudaStream_t; NULL = legacy default stream */
+    void *(*alloc)(size_t bytes, void *stream, void *user);
+    void (*free)(void *ptr, void *stream, void *user);
+    void *user;
+} tr_device_ctx;
+
+typedef struct tr_problem tr_problem;
+
+/* Run options.  Zero-valued tuning fields take the library's defaults. */
+typedef struct {
+    uint64_t n_histories;
+    uint64_t seed;
+    int32_t scheme;                     /* TR_SCHEME_STACK / TR_SCHEME_ASYNC */
+    int32_t decomposition;              /* TR_DECOMP_MONO / TR_DECOMP_SPLIT */
+    uint64_t queue_capacity;            /* stack: particles per event stack; async: global links */
+    int32_t blocks_per_sm;              /* resident blocks per SM */
+    int32_t remap_every;                /* events a particle advances between remaps (>= 1) */
+    int32_t stash_slots;                /* async: particle slots per block stash */
+    int64_t max_spin;                   /* async: iterations before a spin-wait gives up */
+    uint32_t max_events;                /* per-history event cap (default 1e7) */
+    int32_t want_event_log;             /* keep per-history (events, cell, type) for tr_event_log */
+    int32_t spill_threshold;            /* async: spill a full link once a queue exceeds this (0 = default) */
+    uint32_t problem_tag;               /* random stream tag (batched runs: problem index) */
+} tr_run_opts;
+
+typedef struct {
+    uint64_t histories;
+    uint64_t events;                    /* processed transport events (source events excluded) */
+    uint64_t events_by_type[8];         /* TR_EV_* counts, source included */
+    uint64_t final_by_type[8];          /* histories by final event type */
+    uint64_t launches;                  /* kernel launches of the transport loop */
+    uint64_t spills, refills;           /* async: links moved to / from global memory */
+    double seconds;                     /* device time of the whole run */
+    double transport_seconds;           /* device time of the transport-loop kernels alone */
+} tr_run_stats;
+
+/* Create a problem on the device.  Copies every array (the caller keeps
+ * ownership of its buffers).  n_tallies is 0 or 1.  Errors: TR_ERR_INVALID
+ * for malformed descriptions (sizes, non-ascending planes, material ids out
+ * of range), TR_ERR_NOMEM, TR_ERR_CUDA.  *out is NULL on failure. */
+tr_status tr_problem_create(const tr_geometry_desc *geometry, const tr_xs_desc *xs,
+                            const tr_source_desc *source, const tr_tally_desc *tallies, int32_t n_tallies,
+                            const tr_device_ctx *ctx, tr_problem **out);
+
+/* Destroy a problem (NULL-safe); frees through the context's callbacks on its stream. */
+void tr_problem_destroy(tr_problem *problem);
+
+/* Fixed-source run (Sec. 4: source, step, collision, surface-crossing events
+ * until every history ends).  Zeroes the tallies first; tallies become means
+ * per source particle.  Synchronises the context stream before filling
+ * `stats` (may be NULL).  TR_ERR_CAPACITY / TR_ERR_TIMEOUT leave the problem
+ * usable with undefined tallies. */
+tr_status tr_run_fixed_source(tr_problem *problem, const tr_run_opts *opts, tr_run_stats *stats);
+
+typedef struct {
+    uint64_t n_per_batch;
+    uint32_t n_inactive, n_active;
+    double k0;                          /* initial eigenvalue guess (default 1) */
+    double bank_capacity_factor;        /* fission bank = factor * n_per_batch (default 4) */
+    tr_run_opts run;                    /* seed, scheme, decomposition, tuning */
+} tr_eig_opts;
+
+typedef struct {
+    double k_mean, k_std;               /* over active batches; std of the mean */
+    double *k_batch;                    /* caller buffer, n_inactive + n_active (may be NULL) */
+    double *ktl_batch;                  /* caller buffer, track-length k per batch (may be NULL) */
+    uint64_t *n_source;                 /* caller buffer, source size per batch (may be NULL) */
+    uint64_t histories, events;
+    uint64_t final_by_type[8];
+    double seconds;                     /* device time of all batches */
+    double transport_seconds;           /* device time of the transport-loop kernels alone */
+    uint64_t transport_launches;        /* launches of the transport-loop kernels */
+} tr_eig_result;
+
+/* k-eigenvalue power iteration (Sec. 4: inactive then active cycles with
+ * splitting-roulette population control).  Each batch banks fission sites,
+ * orders the bank by (parent history, site sequence), and resamples it to
+ * n_per_batch by splitting roulette.  Tallies become the mean over active
+ * batches of the per-batch means per source particle; tr_tally_stddev gives
+ * the standard deviation of that mean.  Multigroup only (TR_ERR_INVALID
+ * otherwise).  The event log holds the last batch. */
+tr_status tr_run_power_iteration(tr_problem *problem, const tr_eig_opts *opts, tr_eig_result *out);
+
+/* Tally ids for tr_tallies / tr_tally_stddev. */
+enum { TR_TALLY_MESH = 0, TR_TALLY_ENERGY = 1, TR_TALLY_SCALARS = 2 };
+
+/* Copy a tally (mesh: [group][z][y][x]; energy: [material][bin]; scalars:
+ * flux, absorption rate, production rate) into `out`, host memory unless
+ * out_on_device != 0.  n_out must equal the tally size (TR_ERR_INVALID
+ * otherwise).  Synchronises the context stream. */
+tr_status tr_tallies(const tr_problem *problem, int32_t tally_id, double *out, size_t n_out, int32_t out_on_device);
+tr_status tr_tally_stddev(const tr_problem *problem, int32_t tally_id, double *out, size_t n_out,
+                          int32_t out_on_device);
+/* Number of doubles of a tally (0 if absent). */
+size_t tr_tally_size(const tr_problem *problem, int32_t tally_id);
+
+/* Per-history log of the last run (requires want_event_log): final event
+ * count, final cell id ((k ny + j) nx + i) * 2 + inside_pin, final type.
+ * n must equal the number of histories of that run.  Host buffers. */
+tr_status tr_event_log(const tr_problem *problem, uint32_t *n_events, int32_t *final_cell, uint8_t *final_type,
+                       size_t n);
+
+/* Diagnostics: number of kernels this library has launched in this process
+ * (all kernels, all problems).  Read it before and after a call to count the
+ * launches the call made. */
+uint64_t tr_kernel_launch_count(void);
+
+/* Thread-local message for the last non-OK status of this thread. */
+const char *tr_last_error(void);
+
+/* Library version string. */
+const char *tr_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -70,6 +70,7 @@ class OrcProblem(C.Structure):
 class OrcFixed(C.Structure):
     _fields_ = [
         ("n_hist", C.c_uint64), ("seed", C.c_uint64), ("tag", C.c_uint32), ("max_events", C.c_uint32),
+        ("id_offset", C.c_uint64),
         ("mesh", C.POINTER(C.c_double)), ("energy", C.POINTER(C.c_double)),
         ("log_n", C.POINTER(C.c_uint32)), ("log_cell", C.POINTER(C.c_int32)), ("log_type", C.POINTER(C.c_uint8)),
         ("hist_track", C.POINTER(C.c_double)), ("hist_coll", C.POINTER(C.c_uint32)),
@@ -201,12 +202,13 @@ class _Marshalled:
 
 
 def run_fixed_source(prob, n_hist: int, seed: int = 1, tag: int = 0, max_events: int = 0, logs: bool = True,
-                     per_history: bool = False) -> dict:
-    """History-based fixed-source run; tallies are means per source particle."""
+                     per_history: bool = False, id_offset: int = 0) -> dict:
+    """History-based fixed-source run of histories id_offset .. id_offset + n_hist - 1;
+    tallies are means per source particle."""
     L = lib()
     m = _Marshalled(prob)
     o = OrcFixed()
-    o.n_hist, o.seed, o.tag, o.max_events = n_hist, seed, tag, max_events
+    o.n_hist, o.seed, o.tag, o.max_events, o.id_offset = n_hist, seed, tag, max_events, id_offset
     out = {"mesh": np.zeros(prob.mesh_size), "energy": np.zeros(prob.energy_size)}
     o.mesh, o.energy = _dp(out["mesh"]), _dp(out["energy"])
     if logs:

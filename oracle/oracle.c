@@ -842,17 +842,18 @@ int orc_fixed_source(const orc_problem *P, orc_fixed *o)
     C.tag = o->tag;
     C.max_events = o->max_events ? o->max_events : 10000000u;
     memset(o->final_by_type, 0, sizeof(o->final_by_type));
-    for (uint64_t id = 0; id < o->n_hist; ++id) {
+    for (uint64_t i = 0; i < o->n_hist; ++i) {
+        const uint64_t id = o->id_offset + i;
         particle p;
         st = source_particle(&C, &p, id, NULL, 0, 0, 0.0);
         if (st) break;
         while (p.alive) event(&C, &p);
         o->final_by_type[p.final_type]++;
-        if (o->log_n) o->log_n[id] = p.n;
-        if (o->log_cell) o->log_cell[id] = cell_id(P, &p);
-        if (o->log_type) o->log_type[id] = (uint8_t)p.final_type;
-        if (o->hist_track) o->hist_track[id] = p.track;
-        if (o->hist_coll) o->hist_coll[id] = p.coll;
+        if (o->log_n) o->log_n[i] = p.n;
+        if (o->log_cell) o->log_cell[i] = cell_id(P, &p);
+        if (o->log_type) o->log_type[i] = (uint8_t)p.final_type;
+        if (o->hist_track) o->hist_track[i] = p.track;
+        if (o->hist_coll) o->hist_coll[i] = p.coll;
     }
     finish_tallies(&C, (double)o->n_hist, o->mesh, o->energy, o->scalars);
     memcpy(o->events_by_type, C.events_by_type, sizeof(C.events_by_type));

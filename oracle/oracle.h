@@ -60,6 +60,7 @@ typedef struct {
     /* inputs */
     uint64_t n_hist, seed;
     uint32_t tag, max_events;
+    uint64_t id_offset;                  /* histories id_offset .. id_offset + n_hist - 1 */
     /* outputs: caller-allocated arrays, any may be NULL */
     double *mesh;                        /* mesh tally, mean per source particle */
     double *energy;                      /* energy tally [m][bin], mean per source particle */

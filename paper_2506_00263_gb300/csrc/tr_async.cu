@@ -1,0 +1,527 @@
+// tr_async.cu -- asynchronous remapping (Sec. 3.2 of Cuneo et al., M&C 2025).
+//
+// One persistent launch.  Each block owns a shared-memory stash: a pool of
+// particle slots (structure of arrays) and, per event type, a queue of slot
+// indices.  The block's warps share the stash (the paper's future-work item
+// of Sec. 5.2: one stash used by several warps, for higher occupancy);
+// metadata changes happen under a short shared-memory lock, while particle
+// state is read and written only by the warp that owns the slot.
+//
+// A warp takes 32 particles of one event type from the fullest queue, runs
+// that event with one particle per lane in registers, writes the particles
+// back into the slots it owns and pushes each slot onto the queue of its next
+// event type.  When no queue holds a full warp's worth, the warp calls
+// make_work: it claims source indices with one atomic add and runs their
+// source events.  Once the source is exhausted, partial queues are run as
+// they are.
+//
+// Global memory is the last resort (Sec. 3.2): a link arena of 32-particle
+// links, organised in linked lists whose (head, tail) pair is packed in one
+// 64-bit word.  A warp claims a list by swapping it with the empty list,
+// edits it privately and deposits it back, merging with whatever another warp
+// deposited meanwhile -- no inter-block synchronisation.  Blocks with surplus
+// particles spill full links when some warp of another block is starving;
+// starving warps refill from those lists (work stealing).  Every wait is
+// bounded by max_spin and ends with TR_ERR_TIMEOUT instead of hanging.
+#include "tr_events.cuh"
+#include "tr_kernels.h"
+
+namespace tr {
+
+constexpr unsigned FULLM = 0xFFFFFFFFu;
+constexpr unsigned long long EMPTY_LIST = ~0ull;
+constexpr unsigned NIL = 0xFFFFFFFFu;
+constexpr int N_GQ = 32;
+
+struct Stash {
+    double *x, *y, *z, *u, *v, *w, *iu, *iv, *iw, *ia, *E;
+    int* g;
+    unsigned *cell, *id, *n, *nsites, *pend;
+    unsigned short* q[N_QUEUES];       // slot-index queues per event type
+    unsigned short* fr;                // free-slot stack
+    int* cnt;                          // [0..2] queue counts, [3] free count, [4] lock, [5] block error
+};
+
+__host__ __device__ __forceinline__ size_t stash_bytes(int S)
+{
+    return (size_t)S * (11 * sizeof(double) + sizeof(int) + 5 * sizeof(unsigned)) +
+           (size_t)S * (N_QUEUES + 1) * sizeof(unsigned short) + 16 * sizeof(int);
+}
+
+__device__ __forceinline__ Stash carve(unsigned char* base, int S)
+{
+    Stash s;
+    double* d = reinterpret_cast<double*>(base);
+    s.x = d; d += S; s.y = d; d += S; s.z = d; d += S;
+    s.u = d; d += S; s.v = d; d += S; s.w = d; d += S;
+    s.iu = d; d += S; s.iv = d; d += S; s.iw = d; d += S; s.ia = d; d += S;
+    s.E = d; d += S;
+    unsigned* u = reinterpret_cast<unsigned*>(d);
+    s.g = reinterpret_cast<int*>(u); u += S;
+    s.cell = u; u += S; s.id = u; u += S; s.n = u; u += S; s.nsites = u; u += S; s.pend = u; u += S;
+    unsigned short* h = reinterpret_cast<unsigned short*>(u);
+    for (int q = 0; q < N_QUEUES; ++q) {
+        s.q[q] = h;
+        h += S;
+    }
+    s.fr = h;
+    h += S;
+    size_t off = reinterpret_cast<unsigned char*>(h) - base;
+    off = (off + 15) & ~size_t(15);
+    s.cnt = reinterpret_cast<int*>(base + off);
+    return s;
+}
+
+__device__ __forceinline__ void slot_load(const Stash& s, int i, Particle& p)
+{
+    p.x = s.x[i]; p.y = s.y[i]; p.z = s.z[i];
+    p.u = s.u[i]; p.v = s.v[i]; p.w = s.w[i];
+    p.iu = s.iu[i]; p.iv = s.iv[i]; p.iw = s.iw[i]; p.ia = s.ia[i];
+    p.E = s.E[i]; p.g = s.g[i];
+    p.cell = s.cell[i]; p.id = s.id[i]; p.n = s.n[i]; p.nsites = s.nsites[i]; p.pend = s.pend[i];
+}
+
+__device__ __forceinline__ void slot_store(const Stash& s, int i, const Particle& p)
+{
+    s.x[i] = p.x; s.y[i] = p.y; s.z[i] = p.z;
+    s.u[i] = p.u; s.v[i] = p.v; s.w[i] = p.w;
+    s.iu[i] = p.iu; s.iv[i] = p.iv; s.iw[i] = p.iw; s.ia[i] = p.ia;
+    s.E[i] = p.E; s.g[i] = p.g;
+    s.cell[i] = p.cell; s.id[i] = p.id; s.n[i] = p.n; s.nsites[i] = p.nsites; s.pend[i] = p.pend;
+}
+
+// Particle state of a global link, read through L2 (ld.global.cg): the link
+// was written by another SM, and this SM's L1 may still hold lines from an
+// earlier use of the same link.
+__device__ __forceinline__ void load_particle_l2(const SoA& s, unsigned long long i, Particle& p)
+{
+    p.x = __ldcg(s.x + i); p.y = __ldcg(s.y + i); p.z = __ldcg(s.z + i);
+    p.u = __ldcg(s.u + i); p.v = __ldcg(s.v + i); p.w = __ldcg(s.w + i);
+    p.iu = __ldcg(s.iu + i); p.iv = __ldcg(s.iv + i); p.iw = __ldcg(s.iw + i); p.ia = __ldcg(s.ia + i);
+    p.E = __ldcg(s.E + i); p.g = __ldcg(s.g + i);
+    p.cell = __ldcg(s.cell + i); p.id = __ldcg(s.id + i); p.n = __ldcg(s.n + i);
+    p.nsites = __ldcg(s.nsites + i); p.pend = __ldcg(s.pend + i);
+}
+
+__device__ __forceinline__ void fail(ErrorWord* err, int code, int where)
+{
+    if (atomicCAS(&err->code, 0, code) == 0) err->where = where;
+}
+
+// Shared-memory lock, taken by lane 0 for the whole warp.  Bounded.
+__device__ __forceinline__ bool lock_stash(const Stash& s, const RunParams& R, ErrorWord* err)
+{
+    bool ok = true;
+    if ((threadIdx.x & 31) == 0) {
+        unsigned long long spins = 0;
+        while (atomicCAS(s.cnt + 4, 0, 1) != 0) {
+            if (++spins > R.max_spin) {
+                fail(err, ERR_TIMEOUT, 1);
+                ok = false;
+                break;
+            }
+            __nanosleep(32);
+        }
+        __threadfence_block();
+    }
+    return __shfl_sync(FULLM, ok, 0);
+}
+
+__device__ __forceinline__ void unlock_stash(const Stash& s)
+{
+    __threadfence_block();
+    __syncwarp();
+    if ((threadIdx.x & 31) == 0) {
+        __threadfence_block();
+        atomicExch(s.cnt + 4, 0);
+    }
+    __syncwarp();
+}
+
+// ---------------------------------------------------------------------------
+// Lock-free global lists: claim by swapping with the empty list, deposit by
+// swapping back, merging with whatever was deposited meanwhile.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ unsigned list_head(unsigned long long L) { return (unsigned)(L & 0xFFFFFFFFull); }
+__device__ __forceinline__ unsigned list_tail(unsigned long long L) { return (unsigned)(L >> 32); }
+__device__ __forceinline__ unsigned long long make_list(unsigned h, unsigned t)
+{
+    return (unsigned long long)h | ((unsigned long long)t << 32);
+}
+
+// Called by one lane.  Returns false on timeout or on a corrupt list.
+__device__ bool list_deposit(unsigned long long* slot, unsigned long long L, unsigned* next, unsigned long long n_links,
+                             const RunParams& R, ErrorWord* err)
+{
+    unsigned long long spins = 0;
+    for (;;) {
+        __threadfence();
+        const unsigned long long cur = atomicExch(slot, EMPTY_LIST);   // claim whatever is there
+        if (cur != EMPTY_LIST) {                                        // append it after L
+            if (list_tail(L) >= n_links || list_head(cur) >= n_links) {
+                fail(err, ERR_INVALID, 8);
+                return false;
+            }
+            next[list_tail(L)] = list_head(cur);
+            L = make_list(list_head(L), list_tail(cur));
+        }
+        __threadfence();
+        const unsigned long long old = atomicExch(slot, L);
+        if (old == EMPTY_LIST) return true;
+        L = old;                                                        // deposited meanwhile: merge again
+        if (++spins > R.max_spin) {
+            fail(err, ERR_TIMEOUT, 2);
+            return false;
+        }
+    }
+}
+
+// Pop one link from the lists `q[0..N_GQ)` starting at `start`.  One lane.
+// List pointers written by other SMs are read through L2.
+__device__ unsigned list_pop(unsigned long long* q, int start, unsigned* next, unsigned long long n_links,
+                             const RunParams& R, ErrorWord* err)
+{
+    for (int t = 0; t < N_GQ; ++t) {
+        unsigned long long* slot = q + ((start + t) & (N_GQ - 1));
+        if (*(volatile unsigned long long*)slot == EMPTY_LIST) continue;
+        const unsigned long long L = atomicExch(slot, EMPTY_LIST);
+        if (L == EMPTY_LIST) continue;
+        __threadfence();
+        const unsigned h = list_head(L);
+        if (h >= n_links || list_tail(L) >= n_links) {
+            fail(err, ERR_INVALID, 9);
+            return NIL;
+        }
+        if (h != list_tail(L)) {
+            const unsigned rest = __ldcg(next + h);
+            if (rest >= n_links) {
+                fail(err, ERR_INVALID, 10);
+                return NIL;
+            }
+            if (!list_deposit(slot, make_list(rest, list_tail(L)), next, n_links, R, err)) return NIL;
+        }
+        next[h] = NIL;
+        return h;
+    }
+    return NIL;
+}
+
+__device__ __forceinline__ unsigned new_link(const AsyncArgs& A, int start, const RunParams& R, ErrorWord* err)
+{
+    unsigned l = list_pop(A.ctl->free_q, start, A.link_next, A.n_links, R, err);
+    if (l != NIL) return l;
+    const unsigned long long k = atomicAdd(&A.ctl->links_made, 1ull);
+    if (k < A.n_links) return (unsigned)k;
+    return NIL;
+}
+
+// ---------------------------------------------------------------------------
+// The persistent kernel
+// ---------------------------------------------------------------------------
+template <bool CE>
+__global__ void __launch_bounds__(256) k_async(DevProblem P, RunParams R, AsyncArgs A, Tallies T, ErrorWord* err)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int S = A.stash_slots;
+    const Stash st = carve(smem, S);
+    const int lane = threadIdx.x & 31;
+    const int nq = A.split ? N_QUEUES : 1;
+    AsyncCtl* ctl = A.ctl;
+
+    if (threadIdx.x == 0) {
+        for (int q = 0; q < 6; ++q) st.cnt[q] = 0;
+        st.cnt[3] = S;
+    }
+    for (int i = threadIdx.x; i < S; i += blockDim.x) st.fr[i] = (unsigned short)(S - 1 - i);
+    __syncthreads();
+
+    Acc acc;
+    acc.zero();
+    unsigned long long idle_spins = 0;
+    bool idle = false;
+    bool spill_ok = true;   // cleared once the link arena is exhausted
+    const int qstart = (int)(blockIdx.x * 7 + (threadIdx.x >> 5)) & (N_GQ - 1);
+
+    for (;;) {
+        // warp-uniform reads of the global state (lane 0, broadcast)
+        int g_err = 0;
+        unsigned long long g_src = 0, g_live = 0;
+        unsigned g_hungry = 0;
+        if (lane == 0) {
+            g_err = *(volatile int*)&err->code;
+            g_src = *(volatile unsigned long long*)&ctl->src_cursor;
+            g_live = *(volatile unsigned long long*)&ctl->live;
+            g_hungry = *(volatile unsigned*)&ctl->hungry;
+        }
+        g_err = __shfl_sync(FULLM, g_err, 0);
+        if (g_err != 0) break;
+        g_src = __shfl_sync(FULLM, g_src, 0);
+        g_live = __shfl_sync(FULLM, g_live, 0);
+        g_hungry = __shfl_sync(FULLM, g_hungry, 0);
+        // ---------------- take work (under the stash lock) ----------------
+        if (!lock_stash(st, R, err)) break;
+        int cnts[N_QUEUES];
+#pragma unroll
+        for (int q = 0; q < N_QUEUES; ++q) cnts[q] = *(volatile int*)(st.cnt + q);
+        const int nfree = *(volatile int*)(st.cnt + 3);
+        int q = 0;
+        for (int k = 1; k < nq; ++k)
+            if (cnts[k] > cnts[q]) q = k;
+        const bool src_left = g_src < R.n_hist;
+        // mode: 0 process a link of queue q, 1 make_work, 2 spill, 3 idle
+        int mode, take;
+        const int thr = R.spill_threshold < 0 ? -R.spill_threshold : R.spill_threshold;
+        const bool want_spill = spill_ok && (R.spill_threshold < 0 ||
+                                             (!src_left && g_hungry > 0u));
+        if (want_spill && cnts[q] >= thr + 32) {
+            mode = 2;
+            take = 32;
+        } else if (cnts[q] >= 32) {
+            mode = 0;
+            take = 32;
+        } else if (src_left && nfree >= 32) {
+            mode = 1;
+            take = 32;
+        } else if (cnts[q] > 0) {
+            mode = 0;
+            take = cnts[q];
+        } else {
+            mode = 3;
+            take = 0;
+        }
+        int slot = -1;
+        if (mode == 0 || mode == 2) {
+            if (lane < take) slot = st.q[q][cnts[q] - take + lane];
+        } else if (mode == 1) {
+            slot = st.fr[nfree - 32 + lane];
+        }
+        __syncwarp();
+        if (lane == 0) {
+            if (mode == 0 || mode == 2) st.cnt[q] = cnts[q] - take;
+            else if (mode == 1) st.cnt[3] = nfree - 32;
+        }
+        unlock_stash(st);
+
+        if (mode == 3) {
+            // ---------------- starving: steal, or wait for termination ----------------
+            if (!idle) {
+                idle = true;
+                if (lane == 0) atomicAdd(&ctl->hungry, 1u);
+            }
+            unsigned link = NIL;
+            if (lane == 0) link = list_pop(ctl->full_q, qstart, A.link_next, A.n_links, R, err);
+            link = __shfl_sync(FULLM, link, 0);
+            if (link != NIL) {
+                // refill: move the link's particles into free slots of this stash
+                __threadfence();
+                __syncwarp();
+                const int fill = __ldcg(A.link_fill + link);
+                const int type = __ldcg(A.link_type + link);
+                if (link >= A.n_links || fill < 1 || fill > 32 || type < 0 || type >= nq) {
+                    if (lane == 0) fail(err, ERR_INVALID, 6);
+                    break;
+                }
+                bool ok = lock_stash(st, R, err);
+                if (!ok) break;
+                const int nf = *(volatile int*)(st.cnt + 3);
+                int sl = -1;
+                if (lane < fill && nf >= fill) sl = st.fr[nf - fill + lane];
+                __syncwarp();
+                if (lane == 0 && nf >= fill) st.cnt[3] = nf - fill;
+                unlock_stash(st);
+                if (nf < fill) {
+                    fail(err, ERR_CAPACITY, 3);
+                    break;
+                }
+                bool bad = false;
+                if (lane < fill) {
+                    Particle p;
+                    load_particle_l2(A.links, (unsigned long long)link * 32 + lane, p);
+                    bad = p.id >= R.n_hist || cell_i(p.cell) >= P.nx || cell_j(p.cell) >= P.ny ||
+                          cell_k(p.cell) >= P.nz || sl < 0 || sl >= S || (!CE && (p.g < 0 || p.g >= P.G));
+                    if (!bad && cell_in(p.cell)) bad = info_pin(cell_info(P, p.cell)) < 0;
+                    if (!bad) slot_store(st, sl, p);
+                }
+                if (__any_sync(FULLM, bad)) {
+                    if (lane == 0) fail(err, ERR_INVALID, 7);
+                    break;
+                }
+                __syncwarp();
+                if (lane == 0) {
+                    A.link_next[link] = NIL;
+                    list_deposit(ctl->free_q + qstart, make_list(link, link), A.link_next, A.n_links, R, err);
+                    atomicAdd(&ctl->refills, 1ull);
+                }
+                ok = lock_stash(st, R, err);
+                if (!ok) break;
+                const int c = *(volatile int*)(st.cnt + type);
+                if (lane < fill) st.q[type][c + lane] = (unsigned short)sl;
+                __syncwarp();
+                if (lane == 0) st.cnt[type] = c + fill;
+                unlock_stash(st);
+                continue;
+            }
+            if (!src_left && g_live == 0ull) break;
+            if (++idle_spins > R.max_spin) {
+                if (lane == 0) fail(err, ERR_TIMEOUT, 4);
+                break;
+            }
+            __nanosleep(200);
+            continue;
+        }
+        if (idle) {
+            idle = false;
+            idle_spins = 0;
+            if (lane == 0) atomicSub(&ctl->hungry, 1u);
+        }
+
+        if (mode == 2) {
+            // ---------------- spill one full link to global memory ----------------
+            unsigned link = NIL;
+            if (lane == 0) link = new_link(A, qstart, R, err);
+            link = __shfl_sync(FULLM, link, 0);
+            if (link == NIL) {
+                // arena exhausted: keep the particles local and stop spilling
+                if (!lock_stash(st, R, err)) break;
+                const int c = *(volatile int*)(st.cnt + q);
+                st.q[q][c + lane] = (unsigned short)slot;
+                __syncwarp();
+                if (lane == 0) st.cnt[q] = c + 32;
+                unlock_stash(st);
+                spill_ok = false;
+                continue;
+            }
+            Particle p;
+            slot_load(st, slot, p);
+            store_particle(A.links, (unsigned long long)link * 32 + lane, p, CE);
+            __threadfence();
+            __syncwarp();
+            if (lane == 0) {
+                A.link_fill[link] = 32;
+                A.link_type[link] = q;
+                A.link_next[link] = NIL;
+                list_deposit(ctl->full_q + qstart, make_list(link, link), A.link_next, A.n_links, R, err);
+                atomicAdd(&ctl->spills, 1ull);
+            }
+            if (!lock_stash(st, R, err)) break;
+            const int nf = *(volatile int*)(st.cnt + 3);
+            st.fr[nf + lane] = (unsigned short)slot;
+            __syncwarp();
+            if (lane == 0) st.cnt[3] = nf + 32;
+            unlock_stash(st);
+            continue;
+        }
+
+        // ---------------- run one event (or make_work) ----------------
+        Particle p;
+        bool live = false;
+        int next = Q_DEAD;
+        if (mode == 1) {
+            unsigned long long first = 0;
+            if (lane == 0) first = atomicAdd(&ctl->src_cursor, 32ull);
+            first = __shfl_sync(FULLM, first, 0);
+            const unsigned long long id = first + lane;
+            if (id < R.n_hist) {
+                live = source_particle(P, R, (unsigned)id, p, A.use_src ? &A.src : nullptr, id);
+                if (!live) fail(err, ERR_INVALID, 5);
+                acc.ev[EV_SOURCE] += 1u;
+                next = Q_STEP;
+            }
+            const unsigned made = __popc(__ballot_sync(FULLM, live));
+            if (lane == 0 && made) atomicAdd(&ctl->live, (unsigned long long)made);
+        } else {
+            // mode 0 (warp-uniform): lanes beyond a partial link hold no slot and stay idle
+            if (slot >= 0) {
+                slot_load(st, slot, p);
+                live = true;
+                if (!A.split) {
+                    for (int r = 0; r < R.remap_every && live; ++r) live = mono_event(P, R, p, T, acc, A.bank, err);
+                    next = live ? Q_STEP : Q_DEAD;
+                } else if (q == Q_STEP) {
+                    XS X;
+                    double xr;
+                    step_event(P, R, p, T, acc, X, xr);
+                    next = next_queue_after_step(p);
+                } else if (q == Q_COLLIDE) {
+                    live = split_collide(P, R, p, T, acc, A.bank, err);
+                    next = live ? Q_STEP : Q_DEAD;
+                } else {
+                    live = split_surface(P, R, p, T, acc, A.bank);
+                    next = live ? Q_STEP : Q_DEAD;
+                }
+                if (!live) next = Q_DEAD;
+            }
+            const unsigned died = __popc(__ballot_sync(FULLM, slot >= 0 && !live));
+            if (lane == 0 && died) atomicAdd(&ctl->live, 0ull - (unsigned long long)died);
+        }
+        if (live) slot_store(st, slot, p);
+        // ---------------- deposit (under the stash lock) ----------------
+        __syncwarp();
+        if (!lock_stash(st, R, err)) break;
+        const bool has = slot >= 0;
+        for (int qq = 0; qq <= N_QUEUES; ++qq) {
+            const bool mine = has && (qq == N_QUEUES ? next == Q_DEAD : next == qq);
+            const unsigned mask = __ballot_sync(FULLM, mine);
+            if (!mask) continue;
+            int* cp = st.cnt + (qq == N_QUEUES ? 3 : qq);
+            const int c = *(volatile int*)cp;
+            if (mine) {
+                const int pos = c + __popc(mask & ((1u << lane) - 1u));
+                if (qq == N_QUEUES) st.fr[pos] = (unsigned short)slot;
+                else st.q[qq][pos] = (unsigned short)slot;
+            }
+            __syncwarp();
+            if (lane == 0) *cp = c + __popc(mask);
+            __syncwarp();
+        }
+        unlock_stash(st);
+    }
+    if (idle && lane == 0) atomicSub(&ctl->hungry, 1u);
+    flush_acc(acc, T);
+}
+
+}  // namespace tr
+
+namespace tr {
+
+template <bool CE>
+static cudaError_t prepare_async(size_t smem)
+{
+    return cudaFuncSetAttribute(k_async<CE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+}
+
+int async_max_blocks_per_sm(const DevProblem& P, int split, int stash_slots)
+{
+    (void)split;
+    const size_t smem = stash_bytes(stash_slots);
+    int nb = 0;
+    if (P.kind == 1) {
+        if (prepare_async<true>(smem) != cudaSuccess) return 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_async<true>, 256, smem);
+    } else {
+        if (prepare_async<false>(smem) != cudaSuccess) return 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_async<false>, 256, smem);
+    }
+    return nb;
+}
+
+cudaError_t launch_async(const DevProblem& P, const RunParams& R, const AsyncArgs& A, const Tallies& T, ErrorWord* err,
+                         int blocks, cudaStream_t st, int* smem_bytes_out)
+{
+    const size_t smem = stash_bytes(A.stash_slots);
+    if (smem_bytes_out) *smem_bytes_out = (int)smem;
+    count_launches(1);
+    cudaError_t e;
+    if (P.kind == 1) {
+        e = prepare_async<true>(smem);
+        if (e != cudaSuccess) return e;
+        k_async<true><<<blocks, 256, smem, st>>>(P, R, A, T, err);
+    } else {
+        e = prepare_async<false>(smem);
+        if (e != cudaSuccess) return e;
+        k_async<false><<<blocks, 256, smem, st>>>(P, R, A, T, err);
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace tr

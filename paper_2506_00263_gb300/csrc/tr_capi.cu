@@ -1,0 +1,893 @@
+// tr_capi.cu -- the C ABI (include/tr.h): problem creation, run drivers for
+// the stack-based and asynchronous schemes, power iteration, tally readout.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "../../include/tr.h"
+#include "tr_kernels.h"
+
+using namespace tr;
+
+static thread_local std::string g_err;
+
+static tr_status set_err(tr_status s, const std::string& msg)
+{
+    g_err = msg;
+    return s;
+}
+
+#define TR_CUDA(call)                                                                              \
+    do {                                                                                           \
+        cudaError_t e_ = (call);                                                                   \
+        if (e_ != cudaSuccess)                                                                     \
+            return set_err(TR_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_));       \
+    } while (0)
+
+struct Buf {
+    void* p = nullptr;
+    size_t bytes = 0;
+};
+
+struct tr_problem {
+    tr_device_ctx ctx{};
+    cudaStream_t stream = nullptr;
+    int sms = 0;
+    DevProblem dp{};
+    std::vector<void*> owned;                 // problem data, freed at destroy
+    std::map<std::string, Buf> ws;            // run workspaces, grown on demand
+    // tallies: raw accumulators, results, eigenvalue statistics
+    double *raw_mesh = nullptr, *raw_energy = nullptr, *raw_scal = nullptr;
+    double *res_mesh = nullptr, *res_energy = nullptr, *res_scal = nullptr;
+    double *sd_mesh = nullptr, *sd_energy = nullptr, *sd_scal = nullptr;
+    double *sum_all = nullptr, *sq_all = nullptr;   // mesh | energy | scalars concatenated
+    unsigned long long* counts = nullptr;     // ev_type[8], fin_type[8]
+    ErrorWord* err = nullptr;
+    uint32_t* log_n = nullptr;
+    int32_t* log_cell = nullptr;
+    uint8_t* log_type = nullptr;
+    size_t log_cap = 0, log_count = 0;
+    bool have_run = false;
+    bool have_std = false;
+};
+
+// ---------------------------------------------------------------------------
+// memory
+// ---------------------------------------------------------------------------
+static void* dev_alloc(tr_problem* pr, size_t bytes)
+{
+    if (bytes == 0) bytes = 16;
+    bytes = (bytes + 255) & ~size_t(255);
+    void* p = nullptr;
+    if (pr->ctx.alloc) {
+        p = pr->ctx.alloc(bytes, pr->ctx.stream, pr->ctx.user);
+    } else if (cudaMallocAsync(&p, bytes, pr->stream) != cudaSuccess) {
+        cudaGetLastError();
+        p = nullptr;
+    }
+    return p;
+}
+
+static void dev_free(tr_problem* pr, void* p)
+{
+    if (!p) return;
+    if (pr->ctx.free) pr->ctx.free(p, pr->ctx.stream, pr->ctx.user);
+    else cudaFreeAsync(p, pr->stream);
+}
+
+static void* own(tr_problem* pr, size_t bytes)
+{
+    void* p = dev_alloc(pr, bytes);
+    if (p) pr->owned.push_back(p);
+    return p;
+}
+
+template <class T>
+static T* upload(tr_problem* pr, const T* src, size_t n, bool* ok)
+{
+    T* d = (T*)own(pr, n * sizeof(T));
+    if (!d) {
+        *ok = false;
+        return nullptr;
+    }
+    if (n && cudaMemcpyAsync(d, src, n * sizeof(T), cudaMemcpyHostToDevice, pr->stream) != cudaSuccess) *ok = false;
+    // the host vectors may die right after return: make the copy complete
+    if (cudaStreamSynchronize(pr->stream) != cudaSuccess) *ok = false;
+    return d;
+}
+
+static void* workspace(tr_problem* pr, const char* name, size_t bytes)
+{
+    Buf& b = pr->ws[name];
+    if (b.p && b.bytes >= bytes) return b.p;
+    if (b.p) dev_free(pr, b.p);
+    b.p = dev_alloc(pr, bytes);
+    b.bytes = b.p ? bytes : 0;
+    return b.p;
+}
+
+// ---------------------------------------------------------------------------
+// problem creation
+// ---------------------------------------------------------------------------
+static bool ascending(const double* p, int n)
+{
+    for (int i = 0; i < n; ++i)
+        if (!(p[i] < p[i + 1])) return false;
+    return true;
+}
+
+static long long dbl_bits(double d)
+{
+    long long b;
+    std::memcpy(&b, &d, 8);
+    return b;
+}
+
+extern "C" tr_status tr_problem_create(const tr_geometry_desc* G, const tr_xs_desc* X, const tr_source_desc* S,
+                                       const tr_tally_desc* Tl, int32_t n_tallies, const tr_device_ctx* ctx,
+                                       tr_problem** out)
+{
+    if (!out) return set_err(TR_ERR_INVALID, "out is NULL");
+    *out = nullptr;
+    if (!G || !X || !S || !ctx) return set_err(TR_ERR_INVALID, "NULL description");
+    if (n_tallies < 0 || n_tallies > 1 || (n_tallies == 1 && !Tl))
+        return set_err(TR_ERR_INVALID, "n_tallies must be 0 or 1");
+    if (G->nx < 1 || G->ny < 1 || G->nz < 1 || G->nx > 1023 || G->ny > 1023 || G->nz > 1023)
+        return set_err(TR_ERR_INVALID, "grid dimensions must be in 1..1023");
+    if (!G->x_planes || !G->y_planes || !G->z_planes || !G->cell_material)
+        return set_err(TR_ERR_INVALID, "geometry arrays missing");
+    if (!ascending(G->x_planes, G->nx) || !ascending(G->y_planes, G->ny) || !ascending(G->z_planes, G->nz))
+        return set_err(TR_ERR_INVALID, "planes must be strictly ascending");
+    if (!std::isfinite(G->x_planes[0]) || !std::isfinite(G->x_planes[G->nx]) || !std::isfinite(G->y_planes[0]) ||
+        !std::isfinite(G->y_planes[G->ny]))
+        return set_err(TR_ERR_INVALID, "x and y extents must be finite");
+    for (int f = 0; f < 6; ++f)
+        if (G->bc[f] != TR_BC_VACUUM && G->bc[f] != TR_BC_REFLECT) return set_err(TR_ERR_INVALID, "bad boundary code");
+    if (X->kind != TR_XS_MG && X->kind != TR_XS_CE) return set_err(TR_ERR_INVALID, "bad cross-section kind");
+    const int M = X->n_materials;
+    if (M < 1 || M > 256) return set_err(TR_ERR_INVALID, "n_materials must be in 1..256");
+    const size_t ncell = (size_t)G->nx * G->ny * G->nz;
+    for (size_t c = 0; c < ncell; ++c) {
+        if (G->cell_material[c] < 0 || G->cell_material[c] >= M) return set_err(TR_ERR_INVALID, "cell material out of range");
+        if (G->pin_material && (G->pin_material[c] >= M)) return set_err(TR_ERR_INVALID, "pin material out of range");
+    }
+    if (G->pin_material && !(G->pin_radius >= 0.0)) return set_err(TR_ERR_INVALID, "negative pin radius");
+
+    tr_problem* pr = new tr_problem();
+    pr->ctx = *ctx;
+    pr->stream = (cudaStream_t)ctx->stream;
+    if (cudaSetDevice(ctx->device) != cudaSuccess) {
+        delete pr;
+        cudaGetLastError();
+        return set_err(TR_ERR_CUDA, "cudaSetDevice failed");
+    }
+    cudaDeviceGetAttribute(&pr->sms, cudaDevAttrMultiProcessorCount, ctx->device);
+    DevProblem& P = pr->dp;
+    bool ok = true;
+    auto fail_out = [&](tr_status s, const std::string& m) {
+        tr_problem_destroy(pr);
+        return set_err(s, m);
+    };
+
+    // geometry
+    P.nx = G->nx; P.ny = G->ny; P.nz = G->nz;
+    P.xp = upload(pr, G->x_planes, G->nx + 1, &ok);
+    P.yp = upload(pr, G->y_planes, G->ny + 1, &ok);
+    P.zp = upload(pr, G->z_planes, G->nz + 1, &ok);
+    std::vector<double> xc(G->nx), yc(G->ny);
+    for (int i = 0; i < G->nx; ++i) xc[i] = 0.5 * (G->x_planes[i] + G->x_planes[i + 1]);
+    for (int j = 0; j < G->ny; ++j) yc[j] = 0.5 * (G->y_planes[j] + G->y_planes[j + 1]);
+    P.xc = upload(pr, xc.data(), xc.size(), &ok);
+    P.yc = upload(pr, yc.data(), yc.size(), &ok);
+    std::vector<int> info(ncell);
+    for (size_t c = 0; c < ncell; ++c) {
+        const int pm = G->pin_material ? G->pin_material[c] : -1;
+        info[c] = G->cell_material[c] | ((pm < 0 ? 0 : pm + 1) << 16);
+    }
+    P.cellinfo = upload(pr, info.data(), ncell, &ok);
+    for (int f = 0; f < 6; ++f) P.bc[f] = G->bc[f];
+    P.r2 = G->pin_radius * G->pin_radius;
+
+    // cross sections
+    P.kind = X->kind;
+    P.n_mat = M;
+    if (X->kind == TR_XS_MG) {
+        const int Gn = X->n_groups;
+        if (Gn < 1 || Gn > 128 || !X->sigma_t || !X->sigma_s || !X->nu_sigma_f || !X->chi)
+            return fail_out(TR_ERR_INVALID, "multigroup data missing or n_groups out of 1..128");
+        P.G = Gn;
+        const size_t MG = (size_t)M * Gn;
+        std::vector<double> inv(MG), sa(MG), cs(MG * Gn), cc(MG);
+        for (int m = 0; m < M; ++m) {
+            double c = 0.0;
+            for (int g = 0; g < Gn; ++g) {
+                c = c + X->chi[m * Gn + g];
+                cc[m * Gn + g] = c;
+            }
+            for (int g = 0; g < Gn; ++g) {
+                const double st = X->sigma_t[m * Gn + g];
+                if (!(st > 0.0)) return fail_out(TR_ERR_INVALID, "sigma_t must be positive");
+                inv[m * Gn + g] = 1.0 / st;
+                double s = 0.0;
+                for (int h = 0; h < Gn; ++h) {
+                    const double v = X->sigma_s[((size_t)m * Gn + g) * Gn + h];
+                    if (v < 0.0) return fail_out(TR_ERR_INVALID, "negative sigma_s");
+                    s = s + v;
+                    cs[((size_t)m * Gn + g) * Gn + h] = s;
+                }
+                sa[m * Gn + g] = st - s;
+            }
+        }
+        P.sigt = upload(pr, X->sigma_t, MG, &ok);
+        P.inv_sigt = upload(pr, inv.data(), MG, &ok);
+        P.sig_a = upload(pr, sa.data(), MG, &ok);
+        P.nusigf = upload(pr, X->nu_sigma_f, MG, &ok);
+        P.cum_s = upload(pr, cs.data(), MG * Gn, &ok);
+        P.cum_chi = upload(pr, cc.data(), MG, &ok);
+        P.chi = upload(pr, X->chi, MG, &ok);
+    } else {
+        const int Nn = X->n_nuclides;
+        if (Nn < 1 || Nn > 16 || !X->nuc_offset || !X->nuc_energy || !X->nuc_sigma || !X->nuc_awr || !X->density)
+            return fail_out(TR_ERR_INVALID, "continuous-energy data missing or n_nuclides out of 1..16");
+        P.G = 1;
+        P.n_nuc = Nn;
+        const long long rows = X->nuc_offset[Nn];
+        std::vector<double> invde(rows, 0.0);
+        for (int n = 0; n < Nn; ++n) {
+            const long long a = X->nuc_offset[n], b = X->nuc_offset[n + 1];
+            if (b - a < 2 || !ascending(X->nuc_energy + a, (int)(b - a - 1)))
+                return fail_out(TR_ERR_INVALID, "each nuclide grid needs >= 2 ascending points");
+            for (long long r = a; r + 1 < b; ++r) invde[r] = 1.0 / (X->nuc_energy[r + 1] - X->nuc_energy[r]);
+        }
+        // union grid: all nuclide energies, sorted and unique; per union point
+        // and nuclide the largest nuclide row with E_row <= E_union (clamped
+        // to the nuclide's last interval)
+        std::vector<double> ue(X->nuc_energy, X->nuc_energy + rows);
+        std::sort(ue.begin(), ue.end());
+        ue.erase(std::unique(ue.begin(), ue.end()), ue.end());
+        const long long U = (long long)ue.size();
+        std::vector<int> uptr((size_t)U * Nn);
+        for (int n = 0; n < Nn; ++n) {
+            const long long a = X->nuc_offset[n], b = X->nuc_offset[n + 1];
+            long long i = a;
+            for (long long u = 0; u < U; ++u) {
+                while (i + 1 < b && X->nuc_energy[i + 1] <= ue[u]) ++i;
+                long long r = std::min(i, b - 2);
+                uptr[(size_t)u * Nn + n] = (int)r;
+            }
+        }
+        // hash on the bit pattern of E: exponent plus 8 leading mantissa bits
+        const int shift = 44;
+        const long long base = dbl_bits(ue[0]) >> shift, top = dbl_bits(ue[U - 1]) >> shift;
+        const int nh = (int)(top - base + 1);
+        std::vector<int> hash(nh + 1);
+        long long u = 0;
+        for (int b = 0; b <= nh; ++b) {
+            while (u < U && (dbl_bits(ue[u]) >> shift) - base < b) ++u;
+            hash[b] = (int)u;
+        }
+        std::vector<double> iap(Nn);
+        for (int n = 0; n < Nn; ++n) {
+            const double A = X->nuc_awr[n];
+            iap[n] = 1.0 / ((A + 1.0) * (A + 1.0));
+        }
+        P.nuc_e = upload(pr, X->nuc_energy, rows, &ok);
+        P.nuc_sig = upload(pr, X->nuc_sigma, rows * 3, &ok);
+        P.nuc_inv_de = upload(pr, invde.data(), rows, &ok);
+        P.dens = upload(pr, X->density, (size_t)M * Nn, &ok);
+        P.awr = upload(pr, X->nuc_awr, Nn, &ok);
+        P.inv_ap1sq = upload(pr, iap.data(), Nn, &ok);
+        P.e_cut = X->energy_cutoff;
+        P.n_union = (int)U;
+        P.ue = upload(pr, ue.data(), U, &ok);
+        P.uptr = upload(pr, uptr.data(), uptr.size(), &ok);
+        P.n_hash = nh;
+        P.hash_shift = shift;
+        P.hash_base = base;
+        P.hash = upload(pr, hash.data(), hash.size(), &ok);
+    }
+
+    // source
+    if (S->kind < 0 || S->kind > 2) return fail_out(TR_ERR_INVALID, "bad source kind");
+    P.src_kind = S->kind;
+    P.src_iso = S->isotropic ? 1 : 0;
+    P.src_group = S->group;
+    if (X->kind == TR_XS_MG && S->group >= P.G) return fail_out(TR_ERR_INVALID, "source group out of range");
+    for (int a = 0; a < 3; ++a) {
+        P.src_pt[a] = S->point[a];
+        P.src_dir[a] = S->direction[a];
+        P.src_lo[a] = S->lo[a];
+        P.src_hi[a] = S->hi[a];
+    }
+    P.src_energy = S->energy;
+    std::vector<unsigned char> sm(M, 1);
+    if (S->source_material) std::memcpy(sm.data(), S->source_material, M);
+    P.src_mat = upload(pr, sm.data(), M, &ok);
+    P.n_cdf = 0;
+    if (X->kind == TR_XS_CE && S->n_cdf > 1) {
+        if (!S->cdf_energy || !S->cdf_prob) return fail_out(TR_ERR_INVALID, "source CDF arrays missing");
+        P.n_cdf = S->n_cdf;
+        P.cdf_e = upload(pr, S->cdf_energy, S->n_cdf, &ok);
+        P.cdf_p = upload(pr, S->cdf_prob, S->n_cdf, &ok);
+    }
+
+    // tallies
+    P.has_mesh = 0;
+    P.mesh_vox = 0;
+    P.mesh_size = 0;
+    P.energy_size = 0;
+    P.n_ebins = 0;
+    if (n_tallies == 1 && Tl->has_mesh) {
+        P.has_mesh = 1;
+        long long nv = 1;
+        for (int a = 0; a < 3; ++a) {
+            if (Tl->mesh_n[a] < 1 || !(Tl->mesh_hi[a] > Tl->mesh_lo[a])) return fail_out(TR_ERR_INVALID, "bad mesh");
+            P.mesh_n[a] = Tl->mesh_n[a];
+            P.mesh_lo[a] = Tl->mesh_lo[a];
+            P.mesh_hi[a] = Tl->mesh_hi[a];
+            P.mesh_w[a] = (Tl->mesh_hi[a] - Tl->mesh_lo[a]) / (double)Tl->mesh_n[a];
+            P.mesh_iw[a] = 1.0 / P.mesh_w[a];
+            nv *= Tl->mesh_n[a];
+        }
+        if (nv > (1ll << 26)) return fail_out(TR_ERR_INVALID, "mesh too large");
+        P.mesh_vox = (int)nv;
+        P.by_group = (Tl->by_group && X->kind == TR_XS_MG) ? 1 : 0;
+        P.mesh_size = (int)(nv * (P.by_group ? P.G : 1));
+    }
+    if (n_tallies == 1 && Tl->n_energy_bins > 0) {
+        if (!Tl->energy_edges || !ascending(Tl->energy_edges, Tl->n_energy_bins))
+            return fail_out(TR_ERR_INVALID, "energy edges must be ascending");
+        P.n_ebins = Tl->n_energy_bins;
+        P.e_edges = upload(pr, Tl->energy_edges, Tl->n_energy_bins + 1, &ok);
+        P.energy_size = M * Tl->n_energy_bins;
+    }
+    const size_t ms = std::max(P.mesh_size, 1), es = std::max(P.energy_size, 1);
+    pr->raw_mesh = (double*)own(pr, ms * 8);
+    pr->raw_energy = (double*)own(pr, es * 8);
+    pr->raw_scal = (double*)own(pr, 4 * 8);
+    pr->res_mesh = (double*)own(pr, ms * 8);
+    pr->res_energy = (double*)own(pr, es * 8);
+    pr->res_scal = (double*)own(pr, 4 * 8);
+    pr->sd_mesh = (double*)own(pr, ms * 8);
+    pr->sd_energy = (double*)own(pr, es * 8);
+    pr->sd_scal = (double*)own(pr, 4 * 8);
+    pr->sum_all = (double*)own(pr, (ms + es + 4) * 8);
+    pr->sq_all = (double*)own(pr, (ms + es + 4) * 8);
+    pr->counts = (unsigned long long*)own(pr, 16 * 8);
+    pr->err = (ErrorWord*)own(pr, sizeof(ErrorWord));
+    if (!ok || !pr->raw_mesh || !pr->raw_energy || !pr->raw_scal || !pr->res_mesh || !pr->res_energy ||
+        !pr->res_scal || !pr->sd_mesh || !pr->sd_energy || !pr->sd_scal || !pr->sum_all || !pr->sq_all ||
+        !pr->counts || !pr->err)
+        return fail_out(TR_ERR_NOMEM, "device allocation or upload failed");
+    if (cudaStreamSynchronize(pr->stream) != cudaSuccess) return fail_out(TR_ERR_CUDA, "stream sync failed");
+    *out = pr;
+    return TR_OK;
+}
+
+extern "C" void tr_problem_destroy(tr_problem* pr)
+{
+    if (!pr) return;
+    cudaStreamSynchronize(pr->stream);
+    for (auto& kv : pr->ws) dev_free(pr, kv.second.p);
+    for (void* p : pr->owned) dev_free(pr, p);
+    if (pr->log_n) dev_free(pr, pr->log_n);
+    if (pr->log_cell) dev_free(pr, pr->log_cell);
+    if (pr->log_type) dev_free(pr, pr->log_type);
+    cudaStreamSynchronize(pr->stream);
+    cudaGetLastError();
+    delete pr;
+}
+
+// ---------------------------------------------------------------------------
+// run helpers
+// ---------------------------------------------------------------------------
+static bool carve_soa(tr_problem* pr, const char* name, unsigned long long cap, SoA& s)
+{
+    const size_t n = (size_t)cap;
+    const size_t bytes = n * (11 * 8 + 6 * 4) + 17 * 256;
+    unsigned char* b = (unsigned char*)workspace(pr, name, bytes);
+    if (!b) return false;
+    auto take = [&](size_t sz) {
+        unsigned char* p = b;
+        b += (n * sz + 255) & ~size_t(255);
+        return p;
+    };
+    s.x = (double*)take(8); s.y = (double*)take(8); s.z = (double*)take(8);
+    s.u = (double*)take(8); s.v = (double*)take(8); s.w = (double*)take(8);
+    s.iu = (double*)take(8); s.iv = (double*)take(8); s.iw = (double*)take(8); s.ia = (double*)take(8);
+    s.E = (double*)take(8);
+    s.g = (int*)take(4);
+    s.cell = (unsigned*)take(4); s.id = (unsigned*)take(4); s.n = (unsigned*)take(4);
+    s.nsites = (unsigned*)take(4); s.pend = (unsigned*)take(4);
+    return true;
+}
+
+static bool carve_bank(tr_problem* pr, const char* name, unsigned long long cap, Bank& B, bool with_key)
+{
+    const size_t n = (size_t)cap;
+    const size_t bytes = n * (3 * 8 + 4 + 4 + 8) + 8 * 256;
+    unsigned char* b = (unsigned char*)workspace(pr, name, bytes);
+    if (!b) return false;
+    auto take = [&](size_t sz) {
+        unsigned char* p = b;
+        b += (n * sz + 255) & ~size_t(255);
+        return p;
+    };
+    B.x = (double*)take(8); B.y = (double*)take(8); B.z = (double*)take(8);
+    B.g = (int*)take(4); B.cell = (unsigned*)take(4);
+    B.key = with_key ? (unsigned long long*)take(8) : nullptr;
+    B.count = (unsigned long long*)take(8);
+    B.capacity = cap;
+    B.site_count = nullptr;
+    return true;
+}
+
+static tr_status check_err(tr_problem* pr)
+{
+    ErrorWord h{};
+    TR_CUDA(cudaMemcpyAsync(&h, pr->err, sizeof(h), cudaMemcpyDeviceToHost, pr->stream));
+    TR_CUDA(cudaStreamSynchronize(pr->stream));
+    if (h.code == ERR_CAPACITY) return set_err(TR_ERR_CAPACITY, "a queue, link arena or fission bank overflowed");
+    if (h.code == ERR_TIMEOUT)
+        return set_err(TR_ERR_TIMEOUT, "a device spin-wait exceeded max_spin (site " + std::to_string(h.where) + ")");
+    if (h.code != 0) return set_err(TR_ERR_INVALID, "device reported invalid state (code " + std::to_string(h.code) + ")");
+    return TR_OK;
+}
+
+static tr_status ensure_log(tr_problem* pr, size_t n)
+{
+    if (pr->log_cap >= n) return TR_OK;
+    if (pr->log_n) dev_free(pr, pr->log_n);
+    if (pr->log_cell) dev_free(pr, pr->log_cell);
+    if (pr->log_type) dev_free(pr, pr->log_type);
+    pr->log_n = (uint32_t*)dev_alloc(pr, n * 4);
+    pr->log_cell = (int32_t*)dev_alloc(pr, n * 4);
+    pr->log_type = (uint8_t*)dev_alloc(pr, n);
+    pr->log_cap = (pr->log_n && pr->log_cell && pr->log_type) ? n : 0;
+    if (!pr->log_cap) return set_err(TR_ERR_NOMEM, "event log allocation failed");
+    return TR_OK;
+}
+
+static tr_status validate_opts(const tr_run_opts* o)
+{
+    if (!o) return set_err(TR_ERR_INVALID, "opts is NULL");
+    if (o->scheme != TR_SCHEME_STACK && o->scheme != TR_SCHEME_ASYNC) return set_err(TR_ERR_INVALID, "bad scheme");
+    if (o->decomposition != TR_DECOMP_MONO && o->decomposition != TR_DECOMP_SPLIT)
+        return set_err(TR_ERR_INVALID, "bad decomposition");
+    if (o->n_histories >= (1ull << 32)) return set_err(TR_ERR_INVALID, "n_histories must be < 2^32 per run");
+    if (o->remap_every < 0 || o->blocks_per_sm < 0 || o->stash_slots < 0 || o->max_spin < 0)
+        return set_err(TR_ERR_INVALID, "negative tuning option");
+    if (o->decomposition == TR_DECOMP_SPLIT && o->remap_every > 1)
+        return set_err(TR_ERR_INVALID, "remap_every > 1 applies to the monolithic scheme only");
+    return TR_OK;
+}
+
+static Tallies make_tallies(tr_problem* pr, bool log)
+{
+    Tallies T;
+    T.mesh = pr->raw_mesh;
+    T.energy = pr->raw_energy;
+    T.scal = pr->raw_scal;
+    T.ev_type = pr->counts;
+    T.fin_type = pr->counts + 8;
+    T.log_n = log ? pr->log_n : nullptr;
+    T.log_cell = log ? pr->log_cell : nullptr;
+    T.log_type = log ? pr->log_type : nullptr;
+    return T;
+}
+
+static tr_status zero_raw(tr_problem* pr)
+{
+    const DevProblem& P = pr->dp;
+    TR_CUDA(cudaMemsetAsync(pr->raw_mesh, 0, std::max(P.mesh_size, 1) * 8, pr->stream));
+    TR_CUDA(cudaMemsetAsync(pr->raw_energy, 0, std::max(P.energy_size, 1) * 8, pr->stream));
+    TR_CUDA(cudaMemsetAsync(pr->raw_scal, 0, 4 * 8, pr->stream));
+    return TR_OK;
+}
+
+struct TransportOut {
+    unsigned long long launches = 0, spills = 0, refills = 0;
+    double kernel_ms = 0.0;
+};
+
+// Device time of one kernel launch: events recorded around it on the stream.
+struct LaunchTimer {
+    cudaEvent_t a = nullptr, b = nullptr;
+    LaunchTimer()
+    {
+        cudaEventCreate(&a);
+        cudaEventCreate(&b);
+    }
+    ~LaunchTimer()
+    {
+        cudaEventDestroy(a);
+        cudaEventDestroy(b);
+    }
+    float elapsed()
+    {
+        float ms = 0.f;
+        cudaEventSynchronize(b);
+        cudaEventElapsedTime(&ms, a, b);
+        return ms;
+    }
+};
+
+// One transport pass over n histories (fixed source, or one eigenvalue batch).
+static tr_status transport(tr_problem* pr, const tr_run_opts* o, RunParams R, const Bank& bank, const Bank* src,
+                           TransportOut& out)
+{
+    const DevProblem& P = pr->dp;
+    const cudaStream_t st = pr->stream;
+    const bool split = o->decomposition == TR_DECOMP_SPLIT;
+    const Tallies T = make_tallies(pr, R.want_log != 0);
+    if (R.n_hist == 0) return TR_OK;
+    if (o->scheme == TR_SCHEME_STACK) {
+        unsigned long long cap = o->queue_capacity ? o->queue_capacity : std::min<unsigned long long>(R.n_hist, 1ull << 22);
+        cap = std::max<unsigned long long>((cap + 31) & ~31ull, 64);
+        const int nst = split ? 3 : 1;
+        SoA bufs[2][N_QUEUES] = {};
+        const char* names[2][3] = {{"s0a", "s0b", "s0c"}, {"s1a", "s1b", "s1c"}};
+        for (int h = 0; h < 2; ++h)
+            for (int q = 0; q < nst; ++q)
+                if (!carve_soa(pr, names[h][q], cap, bufs[h][q])) return set_err(TR_ERR_NOMEM, "stack allocation failed");
+        StackCtl* dctl = (StackCtl*)workspace(pr, "stackctl", sizeof(StackCtl));
+        if (!dctl) return set_err(TR_ERR_NOMEM, "control block allocation failed");
+        StackCtl h{};
+        h.capacity = cap;
+        const int bps = o->blocks_per_sm > 0 ? o->blocks_per_sm : 4;
+        const int blocks = pr->sms * bps;
+        int cur = 0;
+        LaunchTimer lt;
+        for (unsigned long long it = 0;; ++it) {
+            h.pop = 0;
+            for (int q = 0; q < 3; ++q) {
+                h.out_count[q] = 0;
+                h.reserve[q] = 0;
+            }
+            h.reserve[Q_STEP] = split ? h.in_count[Q_COLLIDE] + h.in_count[Q_SURFACE] : h.in_count[Q_STEP];
+            TR_CUDA(cudaMemcpyAsync(dctl, &h, sizeof(h), cudaMemcpyHostToDevice, st));
+            TR_CUDA(cudaEventRecord(lt.a, st));
+            TR_CUDA(launch_stack(P, R, bufs[cur], bufs[cur ^ 1], dctl, T, bank, src, pr->err, split ? 1 : 0, blocks, st));
+            TR_CUDA(cudaEventRecord(lt.b, st));
+            ++out.launches;
+            TR_CUDA(cudaMemcpyAsync(&h, dctl, sizeof(h), cudaMemcpyDeviceToHost, st));
+            TR_CUDA(cudaStreamSynchronize(st));
+            out.kernel_ms += lt.elapsed();
+            tr_status es = check_err(pr);
+            if (es != TR_OK) return es;
+            unsigned long long tot = 0;
+            for (int q = 0; q < 3; ++q) {
+                if (h.out_count[q] > cap) return set_err(TR_ERR_CAPACITY, "stack overflow");
+                h.in_count[q] = h.out_count[q];
+                tot += h.out_count[q];
+            }
+            cur ^= 1;
+            if (tot == 0 && h.src_cursor >= R.n_hist) break;
+            if (it > 4ull * R.max_events + 1000000ull) return set_err(TR_ERR_TIMEOUT, "stack loop did not terminate");
+        }
+        return TR_OK;
+    }
+    // asynchronous scheme: one persistent launch
+    int S = o->stash_slots > 0 ? o->stash_slots : 512;
+    S = (S + 31) & ~31;
+    if (S < 32 * 9 || S > 16384) return set_err(TR_ERR_INVALID, "stash_slots must be in 288..16384");
+    const unsigned long long n_links = o->queue_capacity ? (o->queue_capacity + 31) / 32 : 8192;
+    AsyncArgs A{};
+    if (!carve_soa(pr, "links", n_links * 32, A.links)) return set_err(TR_ERR_NOMEM, "link arena allocation failed");
+    A.link_next = (unsigned*)workspace(pr, "link_next", n_links * 4);
+    A.link_type = (int*)workspace(pr, "link_type", n_links * 4);
+    A.link_fill = (int*)workspace(pr, "link_fill", n_links * 4);
+    A.ctl = (AsyncCtl*)workspace(pr, "asyncctl", sizeof(AsyncCtl));
+    if (!A.link_next || !A.link_type || !A.link_fill || !A.ctl) return set_err(TR_ERR_NOMEM, "link arena allocation failed");
+    A.n_links = n_links;
+    A.bank = bank;
+    A.use_src = src != nullptr;
+    A.src = src ? *src : bank;
+    A.split = split ? 1 : 0;
+    A.stash_slots = S;
+    AsyncCtl hc;
+    std::memset(&hc, 0, sizeof(hc));
+    std::memset(hc.free_q, 0xFF, sizeof(hc.free_q));
+    std::memset(hc.full_q, 0xFF, sizeof(hc.full_q));
+    TR_CUDA(cudaMemcpyAsync(A.ctl, &hc, sizeof(hc), cudaMemcpyHostToDevice, st));
+    int maxb = async_max_blocks_per_sm(P, A.split, S);
+    if (maxb < 1) return set_err(TR_ERR_INVALID, "stash does not fit in shared memory");
+    const int bps = o->blocks_per_sm > 0 ? std::min(o->blocks_per_sm, maxb) : maxb;
+    int smem = 0;
+    LaunchTimer lt;
+    TR_CUDA(cudaEventRecord(lt.a, st));
+    TR_CUDA(launch_async(P, R, A, T, pr->err, pr->sms * bps, st, &smem));
+    TR_CUDA(cudaEventRecord(lt.b, st));
+    out.launches += 1;
+    TR_CUDA(cudaMemcpyAsync(&hc, A.ctl, sizeof(hc), cudaMemcpyDeviceToHost, st));
+    TR_CUDA(cudaStreamSynchronize(st));
+    out.kernel_ms += lt.elapsed();
+    tr_status es = check_err(pr);
+    if (es != TR_OK) return es;
+    out.spills += hc.spills;
+    out.refills += hc.refills;
+    if (hc.live != 0) return set_err(TR_ERR_STATE, "asynchronous run ended with live particles");
+    return TR_OK;
+}
+
+static RunParams base_params(const tr_run_opts* o, unsigned long long n)
+{
+    RunParams R{};
+    R.n_hist = n;
+    R.key0 = (uint32_t)o->seed;
+    R.key1 = (uint32_t)(o->seed >> 32) ^ o->problem_tag;
+    R.id_hi = 0;
+    R.max_events = o->max_events ? o->max_events : 10000000u;
+    R.eig = 0;
+    R.inv_k = 1.0;
+    R.want_log = o->want_event_log ? 1 : 0;
+    R.remap_every = o->remap_every > 0 ? o->remap_every : 1;
+    R.max_spin = o->max_spin > 0 ? (uint64_t)o->max_spin : (1ull << 24);
+    R.spill_threshold = o->spill_threshold ? o->spill_threshold : 64;
+    return R;
+}
+
+extern "C" tr_status tr_run_fixed_source(tr_problem* pr, const tr_run_opts* o, tr_run_stats* stats)
+{
+    if (!pr) return set_err(TR_ERR_INVALID, "problem is NULL");
+    tr_status s = validate_opts(o);
+    if (s != TR_OK) return s;
+    const DevProblem& P = pr->dp;
+    const cudaStream_t st = pr->stream;
+    RunParams R = base_params(o, o->n_histories);
+    if (R.want_log) {
+        s = ensure_log(pr, std::max<unsigned long long>(o->n_histories, 1));
+        if (s != TR_OK) return s;
+    }
+    s = zero_raw(pr);
+    if (s != TR_OK) return s;
+    TR_CUDA(cudaMemsetAsync(pr->counts, 0, 16 * 8, st));
+    TR_CUDA(cudaMemsetAsync(pr->err, 0, sizeof(ErrorWord), st));
+    Bank bank{};
+    cudaEvent_t e0, e1;
+    TR_CUDA(cudaEventCreate(&e0));
+    TR_CUDA(cudaEventCreate(&e1));
+    TR_CUDA(cudaEventRecord(e0, st));
+    TransportOut to;
+    s = transport(pr, o, R, bank, nullptr, to);
+    cudaEventRecord(e1, st);
+    cudaEventSynchronize(e1);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (s != TR_OK) {
+        pr->have_run = false;
+        return s;
+    }
+    const double inv = o->n_histories ? 1.0 / (double)o->n_histories : 0.0;
+    TR_CUDA(launch_scale(pr->raw_mesh, P.mesh_size, inv, pr->res_mesh, st));
+    TR_CUDA(launch_scale(pr->raw_energy, P.energy_size, inv, pr->res_energy, st));
+    TR_CUDA(launch_scale(pr->raw_scal, 3, inv, pr->res_scal, st));
+    unsigned long long cnt[16];
+    TR_CUDA(cudaMemcpyAsync(cnt, pr->counts, sizeof(cnt), cudaMemcpyDeviceToHost, st));
+    TR_CUDA(cudaStreamSynchronize(st));
+    pr->have_run = true;
+    pr->have_std = false;
+    pr->log_count = R.want_log ? o->n_histories : 0;
+    if (stats) {
+        std::memset(stats, 0, sizeof(*stats));
+        stats->histories = o->n_histories;
+        unsigned long long ev = 0;
+        for (int i = 0; i < 8; ++i) {
+            stats->events_by_type[i] = cnt[i];
+            stats->final_by_type[i] = cnt[8 + i];
+            if (i != EV_SOURCE) ev += cnt[i];
+        }
+        stats->events = ev;
+        stats->launches = to.launches;
+        stats->spills = to.spills;
+        stats->refills = to.refills;
+        stats->seconds = ms * 1e-3;
+        stats->transport_seconds = to.kernel_ms * 1e-3;
+    }
+    return TR_OK;
+}
+
+// ---------------------------------------------------------------------------
+// power iteration
+// ---------------------------------------------------------------------------
+extern "C" tr_status tr_run_power_iteration(tr_problem* pr, const tr_eig_opts* eo, tr_eig_result* res)
+{
+    if (!pr || !eo || !res) return set_err(TR_ERR_INVALID, "NULL argument");
+    if (pr->dp.kind != TR_XS_MG) return set_err(TR_ERR_INVALID, "power iteration needs multigroup data");
+    tr_status s = validate_opts(&eo->run);
+    if (s != TR_OK) return s;
+    if (eo->n_per_batch < 1 || eo->n_active < 2) return set_err(TR_ERR_INVALID, "need n_per_batch >= 1 and n_active >= 2");
+    const DevProblem& P = pr->dp;
+    const cudaStream_t st = pr->stream;
+    const double factor = eo->bank_capacity_factor > 0.0 ? eo->bank_capacity_factor : 4.0;
+    const unsigned long long cap = (unsigned long long)std::ceil(factor * (double)eo->n_per_batch) + 64;
+    if (cap >= (1ull << 32)) return set_err(TR_ERR_INVALID, "bank capacity must stay below 2^32");
+    Bank bank, ordered, source;
+    if (!carve_bank(pr, "bank", cap, bank, true) || !carve_bank(pr, "ordered", cap, ordered, true) ||
+        !carve_bank(pr, "source", cap, source, false))
+        return set_err(TR_ERR_NOMEM, "bank allocation failed");
+    unsigned* site_count = (unsigned*)workspace(pr, "site_count", cap * 4);
+    unsigned* copies = (unsigned*)workspace(pr, "copies", cap * 4);
+    unsigned long long* offs = (unsigned long long*)workspace(pr, "offsets", cap * 8);
+    unsigned long long* tiles = (unsigned long long*)workspace(pr, "scan_tiles", ((cap + 2047) / 2048 + 1) * 8);
+    unsigned long long* total = (unsigned long long*)workspace(pr, "scan_total", 8);
+    if (!site_count || !copies || !offs || !tiles || !total) return set_err(TR_ERR_NOMEM, "bank allocation failed");
+    bank.site_count = site_count;
+    const tr_run_opts* o = &eo->run;
+    RunParams R = base_params(o, eo->n_per_batch);
+    R.eig = 1;
+    if (R.want_log) {
+        s = ensure_log(pr, cap);
+        if (s != TR_OK) return s;
+    }
+    const int ms = std::max(P.mesh_size, 0), es = std::max(P.energy_size, 0);
+    const int nall = ms + es + 3;
+    TR_CUDA(cudaMemsetAsync(pr->sum_all, 0, (size_t)(nall + 1) * 8, st));
+    TR_CUDA(cudaMemsetAsync(pr->sq_all, 0, (size_t)(nall + 1) * 8, st));
+    TR_CUDA(cudaMemsetAsync(pr->counts, 0, 16 * 8, st));
+    TR_CUDA(cudaMemsetAsync(pr->err, 0, sizeof(ErrorWord), st));
+    const uint32_t nb = eo->n_inactive + eo->n_active;
+    double k = eo->k0 > 0.0 ? eo->k0 : 1.0;
+    unsigned long long N = eo->n_per_batch;
+    double ksum = 0.0, ksq = 0.0;
+    cudaEvent_t e0, e1;
+    TR_CUDA(cudaEventCreate(&e0));
+    TR_CUDA(cudaEventCreate(&e1));
+    TR_CUDA(cudaEventRecord(e0, st));
+    std::vector<double> scal(3);
+    bool have_src = false;
+    double kernel_ms = 0.0;
+    unsigned long long tlaunch = 0;
+    for (uint32_t b = 0; b < nb; ++b) {
+        s = zero_raw(pr);
+        if (s != TR_OK) return s;
+        TR_CUDA(cudaMemsetAsync(bank.count, 0, 8, st));
+        R.id_hi = b;
+        R.inv_k = 1.0 / k;
+        R.n_hist = N;
+        TransportOut to;
+        s = transport(pr, o, R, bank, have_src ? &source : nullptr, to);
+        if (s != TR_OK) return s;
+        kernel_ms += to.kernel_ms;
+        tlaunch += to.launches;
+        // the raw accumulators hold separate copies for mesh, energy, scalars;
+        // gather them into one contiguous view for the statistics
+        unsigned long long M = 0;
+        TR_CUDA(cudaMemcpyAsync(&M, bank.count, 8, cudaMemcpyDeviceToHost, st));
+        TR_CUDA(cudaMemcpyAsync(scal.data(), pr->raw_scal, 3 * 8, cudaMemcpyDeviceToHost, st));
+        TR_CUDA(cudaStreamSynchronize(st));
+        if (M > cap) return set_err(TR_ERR_CAPACITY, "fission bank overflow");
+        const double kb = k * ((double)M / (double)N);
+        if (res->k_batch) res->k_batch[b] = kb;
+        if (res->ktl_batch) res->ktl_batch[b] = scal[2] / (double)N;
+        if (res->n_source) res->n_source[b] = N;
+        if (b >= eo->n_inactive) {
+            const double inv = 1.0 / (double)N;
+            TR_CUDA(launch_eig_accumulate(pr->raw_mesh, ms, inv, pr->sum_all, pr->sq_all, st));
+            TR_CUDA(launch_eig_accumulate(pr->raw_energy, es, inv, pr->sum_all + ms, pr->sq_all + ms, st));
+            TR_CUDA(launch_eig_accumulate(pr->raw_scal, 3, inv, pr->sum_all + ms + es, pr->sq_all + ms + es, st));
+            ksum += kb;
+            ksq += kb * kb;
+        }
+        k = kb;
+        if (M == 0) return set_err(TR_ERR_STATE, "the fission source died out");
+        if (b + 1 == nb) {
+            pr->log_count = R.want_log ? N : 0;
+            break;
+        }
+        // order the bank by (parent, site sequence)
+        TR_CUDA(launch_scan(site_count, N, tiles, offs, total, st));
+        unsigned long long tot = 0;
+        TR_CUDA(cudaMemcpyAsync(&tot, total, 8, cudaMemcpyDeviceToHost, st));
+        TR_CUDA(cudaStreamSynchronize(st));
+        if (tot != M) return set_err(TR_ERR_STATE, "bank site counts disagree with the bank size");
+        TR_CUDA(launch_bank_order(bank, M, offs, ordered, pr->err, st));
+        // splitting roulette back to n_per_batch
+        const double r = (double)eo->n_per_batch / (double)M;
+        const double fl = std::floor(r), fr = r - fl;
+        TR_CUDA(launch_pop_copies(M, R.key0, (uint32_t)(o->seed >> 32) ^ TAG_POP, b, (unsigned)fl, fr, copies, st));
+        TR_CUDA(launch_scan(copies, M, tiles, offs, total, st));
+        unsigned long long nn = 0;
+        TR_CUDA(cudaMemcpyAsync(&nn, total, 8, cudaMemcpyDeviceToHost, st));
+        TR_CUDA(cudaStreamSynchronize(st));
+        if (nn > cap) return set_err(TR_ERR_CAPACITY, "source bank overflow after population control");
+        if (nn >= (1ull << 32)) return set_err(TR_ERR_CAPACITY, "batch too large");
+        TR_CUDA(launch_pop_write(ordered, M, copies, offs, source, st));
+        s = check_err(pr);
+        if (s != TR_OK) return s;
+        N = nn;
+        have_src = true;
+    }
+    TR_CUDA(cudaEventRecord(e1, st));
+    TR_CUDA(cudaEventSynchronize(e1));
+    float msec = 0.f;
+    cudaEventElapsedTime(&msec, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    const double na = (double)eo->n_active;
+    TR_CUDA(launch_eig_finish(pr->sum_all, pr->sq_all, ms, na, pr->res_mesh, pr->sd_mesh, st));
+    TR_CUDA(launch_eig_finish(pr->sum_all + ms, pr->sq_all + ms, es, na, pr->res_energy, pr->sd_energy, st));
+    TR_CUDA(launch_eig_finish(pr->sum_all + ms + es, pr->sq_all + ms + es, 3, na, pr->res_scal, pr->sd_scal, st));
+    unsigned long long cnt[16];
+    TR_CUDA(cudaMemcpyAsync(cnt, pr->counts, sizeof(cnt), cudaMemcpyDeviceToHost, st));
+    TR_CUDA(cudaStreamSynchronize(st));
+    res->k_mean = ksum / na;
+    const double var = (ksq / na - res->k_mean * res->k_mean) / (na - 1.0);
+    res->k_std = var > 0.0 ? std::sqrt(var) : 0.0;
+    unsigned long long ev = 0;
+    for (int i = 0; i < 8; ++i) {
+        res->final_by_type[i] = cnt[8 + i];
+        if (i != EV_SOURCE) ev += cnt[i];
+    }
+    res->histories = cnt[EV_SOURCE];
+    res->events = ev;
+    res->seconds = msec * 1e-3;
+    res->transport_seconds = kernel_ms * 1e-3;
+    res->transport_launches = tlaunch;
+    pr->have_run = true;
+    pr->have_std = true;
+    return TR_OK;
+}
+
+// ---------------------------------------------------------------------------
+// readout
+// ---------------------------------------------------------------------------
+extern "C" size_t tr_tally_size(const tr_problem* pr, int32_t id)
+{
+    if (!pr) return 0;
+    if (id == TR_TALLY_MESH) return (size_t)pr->dp.mesh_size;
+    if (id == TR_TALLY_ENERGY) return (size_t)pr->dp.energy_size;
+    if (id == TR_TALLY_SCALARS) return 3;
+    return 0;
+}
+
+static tr_status copy_tally(const tr_problem* pr, int32_t id, double* out, size_t n, int32_t on_dev, bool sd)
+{
+    if (!pr || !out) return set_err(TR_ERR_INVALID, "NULL argument");
+    if (!pr->have_run) return set_err(TR_ERR_STATE, "no completed run");
+    if (sd && !pr->have_std) return set_err(TR_ERR_STATE, "standard deviations come from power iteration only");
+    const size_t want = tr_tally_size(pr, id);
+    if (id < 0 || id > 2 || n != want) return set_err(TR_ERR_INVALID, "tally id or size mismatch");
+    if (n == 0) return TR_OK;
+    const double* src = id == TR_TALLY_MESH ? (sd ? pr->sd_mesh : pr->res_mesh)
+                      : id == TR_TALLY_ENERGY ? (sd ? pr->sd_energy : pr->res_energy)
+                                              : (sd ? pr->sd_scal : pr->res_scal);
+    TR_CUDA(cudaMemcpyAsync(out, src, n * 8, on_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, pr->stream));
+    TR_CUDA(cudaStreamSynchronize(pr->stream));
+    return TR_OK;
+}
+
+extern "C" tr_status tr_tallies(const tr_problem* pr, int32_t id, double* out, size_t n, int32_t on_dev)
+{
+    return copy_tally(pr, id, out, n, on_dev, false);
+}
+
+extern "C" tr_status tr_tally_stddev(const tr_problem* pr, int32_t id, double* out, size_t n, int32_t on_dev)
+{
+    return copy_tally(pr, id, out, n, on_dev, true);
+}
+
+extern "C" tr_status tr_event_log(const tr_problem* pr, uint32_t* n_events, int32_t* final_cell, uint8_t* final_type,
+                                  size_t n)
+{
+    if (!pr) return set_err(TR_ERR_INVALID, "problem is NULL");
+    if (!pr->have_run || pr->log_count == 0) return set_err(TR_ERR_STATE, "no event log (set want_event_log)");
+    if (n != pr->log_count) return set_err(TR_ERR_INVALID, "n must equal the histories of the logged run");
+    if (n_events) TR_CUDA(cudaMemcpyAsync(n_events, pr->log_n, n * 4, cudaMemcpyDeviceToHost, pr->stream));
+    if (final_cell) TR_CUDA(cudaMemcpyAsync(final_cell, pr->log_cell, n * 4, cudaMemcpyDeviceToHost, pr->stream));
+    if (final_type) TR_CUDA(cudaMemcpyAsync(final_type, pr->log_type, n, cudaMemcpyDeviceToHost, pr->stream));
+    TR_CUDA(cudaStreamSynchronize(pr->stream));
+    return TR_OK;
+}
+
+extern "C" const char* tr_last_error(void) { return g_err.c_str(); }
+
+extern "C" uint64_t tr_kernel_launch_count(void) { return tr::launch_count(); }
+
+extern "C" const char* tr_version(void) { return "tr 0.1 (sm_103a)"; }

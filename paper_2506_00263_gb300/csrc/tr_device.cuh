@@ -1,0 +1,442 @@
+// tr_device.cuh -- device-side problem data, particle state and per-event physics.
+//
+// Every floating-point operation that decides a branch follows the library's
+// arithmetic contract: IEEE binary64, evaluated in the written order, with FMA
+// contraction disabled (-fmad=false).  Where a result is produced with integer
+// bit manipulation instead of a double instruction (uniforms, exponent
+// extraction, comparisons of non-negative doubles), the integer form yields
+// exactly the value the double form would; GB300 issues FP64 at a small
+// fraction of its integer rate, so every FP64 instruction saved counts.
+//
+// Paper context (Cuneo et al., M&C 2025): the transport loop is split into
+// events (Sec. 4): source (make_work, Sec. 3), step (move to the next site and
+// score the path), collision, surface crossing.  Particles are created through
+// an atomic counter and a counter-based random number generator (Sec. 3).
+#pragma once
+#include <stdint.h>
+#include <cuda_runtime.h>
+
+namespace tr {
+
+constexpr int EV_SOURCE = 0, EV_SCATTER = 1, EV_ABSORB = 2, EV_SURF_INTERNAL = 3, EV_SURF_REFLECT = 4,
+              EV_LEAK = 5, EV_CUTOFF = 6, EV_MAXEV = 7;
+constexpr int ERR_NONE = 0, ERR_CAPACITY = 3, ERR_TIMEOUT = 4, ERR_INVALID = 1;
+
+// Random-block assignment within one event (counter word 1).
+constexpr uint32_t BLK_MAIN = 0u;      // (distance | source cosine, reaction | source group/energy)
+constexpr uint32_t BLK_ANGLE = 1u;     // (scatter cosine / CM cosine, -)
+constexpr uint32_t BLK_FISSION = 2u;   // (fission-site count, -)
+constexpr uint32_t BLK_AZIMUTH = 3u;   // 3 + t, t < 64: azimuth rejection tries
+constexpr uint32_t N_AZIMUTH = 64u;
+constexpr uint32_t BLK_SITE = 100u;    // 100 + c: fission site c
+constexpr uint32_t BLK_POS = 200u;     // 200 + 2t, 201 + 2t: source position trial t
+constexpr uint32_t N_POS = 1024u;
+constexpr uint32_t TAG_POP = 0x80000000u;
+
+// next event types of the decomposed scheme (queue ids); DEAD ends the history
+constexpr int Q_STEP = 0, Q_COLLIDE = 1, Q_SURFACE = 2, N_QUEUES = 3, Q_DEAD = 3;
+
+struct DevProblem {
+    // geometry
+    int nx, ny, nz;
+    const double *xp, *yp, *zp;        // planes
+    const double *xc, *yc;             // pin centres per column / row: 0.5 (p[i] + p[i+1])
+    const int *cellinfo;               // [nz][ny][nx]: cell material | (pin material + 1) << 16
+    int bc[6];
+    double r2;                         // pin radius squared
+    // cross sections
+    int kind, n_mat, G;
+    const double *sigt, *inv_sigt, *sig_a, *nusigf, *cum_s, *cum_chi, *chi;
+    int n_nuc;
+    const double *nuc_e, *nuc_sig, *nuc_inv_de;   // CE rows
+    const double *dens;                // [m][n]
+    const double *awr, *inv_ap1sq;     // per nuclide
+    double e_cut;
+    int n_union;
+    const double *ue;                  // union grid energies
+    const int *uptr;                   // [u][n] absolute nuclide row of the largest point <= ue[u]
+    int n_hash;                        // buckets over the double bit pattern of E
+    int hash_shift;
+    long long hash_base;
+    const int *hash;                   // n_hash + 1: first union index whose bucket >= b
+    // source
+    int src_kind, src_iso, src_group, n_cdf;
+    double src_pt[3], src_dir[3], src_lo[3], src_hi[3], src_energy;
+    const unsigned char *src_mat;
+    const double *cdf_e, *cdf_p;
+    // tallies
+    int has_mesh, mesh_n[3], by_group, n_ebins, mesh_vox;
+    double mesh_lo[3], mesh_hi[3], mesh_w[3], mesh_iw[3];
+    const double *e_edges;
+    int mesh_size, energy_size;
+};
+
+// Per-run parameters.
+struct RunParams {
+    uint64_t n_hist;
+    uint32_t key0, key1;               // (seed_lo, seed_hi ^ tag)
+    uint32_t id_hi;                    // batch index (eigenvalue) or 0
+    uint32_t max_events;
+    int eig;
+    double inv_k;
+    int want_log;
+    int remap_every;
+    uint64_t max_spin;
+    int spill_threshold;
+};
+
+// Structure-of-arrays particle storage (global memory stacks and links).
+// Fields: position, direction, cached reciprocals of the direction
+// components and of u^2 + v^2 (pure functions of the direction, stored so
+// that a surface event does not repeat four divisions), energy (CE) or
+// group (MG), packed cell, history index, event count, banked-site count and
+// the pending surface flags of the decomposed scheme.
+struct SoA {
+    double *x, *y, *z, *u, *v, *w, *iu, *iv, *iw, *ia, *E;
+    int *g;
+    unsigned *cell, *id, *n, *nsites, *pend;
+};
+
+struct Particle {
+    double x, y, z, u, v, w;
+    double iu, iv, iw, ia;
+    double E;
+    int g;
+    unsigned cell;                     // i | j << 10 | k << 20 | inside << 30
+    unsigned id, n, nsites, pend;
+};
+
+// Tally accumulators written by kernels (raw sums, normalised later).
+struct Tallies {
+    double *mesh;                      // mesh_size
+    double *energy;                    // energy_size
+    double *scal;                      // 3: flux, absorption, production
+    unsigned long long *ev_type;       // 8 event counts
+    unsigned long long *fin_type;      // 8 final-type counts
+    uint32_t *log_n;
+    int32_t *log_cell;
+    uint8_t *log_type;
+};
+
+// Fission bank (unordered during a batch; ordered by (parent, site) later).
+struct Bank {
+    double *x, *y, *z;
+    int *g;
+    unsigned *cell;
+    unsigned long long *key;           // parent index << 32 | site sequence
+    unsigned long long *count;
+    unsigned long long capacity;
+    unsigned *site_count;              // per parent: sites banked (written at death)
+};
+
+struct ErrorWord {
+    int code;
+    int where;
+};
+
+// ---------------------------------------------------------------------------
+// Philox-4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint4 philox10(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3, uint32_t k0,
+                                          uint32_t k1)
+{
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        if (r) {
+            k0 += 0x9E3779B9u;
+            k1 += 0xBB67AE85u;
+        }
+        const uint32_t lo0 = 0xD2511F53u * c0, hi0 = __umulhi(0xD2511F53u, c0);
+        const uint32_t lo1 = 0xCD9E8D57u * c2, hi1 = __umulhi(0xCD9E8D57u, c2);
+        const uint32_t n0 = hi1 ^ c1 ^ k0, n2 = hi0 ^ c3 ^ k1;
+        c0 = n0;
+        c1 = lo1;
+        c2 = n2;
+        c3 = lo0;
+    }
+    return make_uint4(c0, c1, c2, c3);
+}
+
+// ((w >> 12) + 1/2) 2^-52 built directly as a binary64 bit pattern:
+// v = 2 (w >> 12) + 1 < 2^53 is normalised with a leading-zero count, so the
+// value v 2^-53 is exact and no FP64 instruction is spent.
+__device__ __forceinline__ double u01(uint32_t lo, uint32_t hi)
+{
+    const unsigned long long w = ((unsigned long long)hi << 32) | lo;
+    const unsigned long long v = ((w >> 12) << 1) | 1ull;
+    const int sh = __clzll((long long)v) - 11;
+    const unsigned long long mant = (v << sh) & 0x000FFFFFFFFFFFFFull;
+    const unsigned long long ex = (unsigned long long)(1022 - sh);
+    return __longlong_as_double((long long)((ex << 52) | mant));
+}
+
+struct Stream {
+    uint32_t k0, k1, id_lo, id_hi;
+    __device__ __forceinline__ uint4 block(uint32_t n, uint32_t j) const { return philox10(n, j, id_lo, id_hi, k0, k1); }
+    __device__ __forceinline__ double first(uint32_t n, uint32_t j) const
+    {
+        const uint4 r = block(n, j);
+        return u01(r.x, r.y);
+    }
+};
+
+// Non-negative doubles (and +inf) order like their bit patterns.
+__device__ __forceinline__ long long dbits(double d) { return __double_as_longlong(d); }
+__device__ __forceinline__ bool lt_nn(double a, double b) { return dbits(a) < dbits(b); }
+// max(d, +0) with -0 and negatives mapped to +0 (no NaN reaches here)
+__device__ __forceinline__ double clamp0(double d) { return dbits(d) <= 0 ? 0.0 : d; }
+
+// ---------------------------------------------------------------------------
+// Natural logarithm (the contract's atanh series): x = 2^e m, m in
+// [sqrt(1/2), sqrt(2)); s = (m-1)/(m+1); log m = 2 s sum_{j<10} s^2j/(2j+1);
+// log x = e LN2_HI + (log m + e LN2_LO), ln 2 split at 40 bits.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double tr_log(double x)
+{
+    const long long b = __double_as_longlong(x);
+    int e = (int)((b >> 52) & 0x7FF) - 1023;
+    long long mb = (b & 0x000FFFFFFFFFFFFFll) | 0x3FF0000000000000ll;
+    if (mb > 0x3FF6A09E667F3BCDll) {   // m > sqrt(2): halve m (exact) and bump e
+        mb -= 0x0010000000000000ll;
+        e += 1;
+    }
+    const double m = __longlong_as_double(mb);
+    const double s = (m - 1.0) / (m + 1.0);
+    const double z = s * s;
+    double p = 1.0 / 19.0;
+    p = p * z + 1.0 / 17.0;
+    p = p * z + 1.0 / 15.0;
+    p = p * z + 1.0 / 13.0;
+    p = p * z + 1.0 / 11.0;
+    p = p * z + 1.0 / 9.0;
+    p = p * z + 1.0 / 7.0;
+    p = p * z + 1.0 / 5.0;
+    p = p * z + 1.0 / 3.0;
+    p = p * z + 1.0;
+    const double r = (s + s) * p;
+    const double de = (double)e;
+    return de * __longlong_as_double(0x3FE62E42FEFA4000ll) + (r + de * __longlong_as_double((long long)0xBD48432A1B0E2634ull));
+}
+
+// ---------------------------------------------------------------------------
+// Directions: azimuth by rejection in the unit square (no trig), isotropic
+// direction, lab rotation, target-at-rest elastic kinematics.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void azimuth(const Stream& S, uint32_t n, double& cphi, double& sphi)
+{
+    double a = 1.0, b = 0.0, a2 = 1.0, b2 = 0.0, s = 1.0;
+    for (uint32_t t = 0; t < N_AZIMUTH; ++t) {
+        const uint4 r = S.block(n, BLK_AZIMUTH + t);
+        const double ta = 2.0 * u01(r.x, r.y) - 1.0;
+        const double tb = 2.0 * u01(r.z, r.w) - 1.0;
+        const double ta2 = ta * ta, tb2 = tb * tb;
+        const double ts = ta2 + tb2;
+        if (ts <= 1.0 && ts > 0.0) {
+            a = ta; b = tb; a2 = ta2; b2 = tb2; s = ts;
+            break;
+        }
+    }
+    const double inv_s = 1.0 / s;
+    cphi = (a2 - b2) * inv_s;
+    sphi = (2.0 * (a * b)) * inv_s;
+}
+
+__device__ __forceinline__ void set_reciprocals(Particle& p)
+{
+    p.iu = (p.u != 0.0) ? 1.0 / p.u : 0.0;
+    p.iv = (p.v != 0.0) ? 1.0 / p.v : 0.0;
+    p.iw = (p.w != 0.0) ? 1.0 / p.w : 0.0;
+    const double a = p.u * p.u + p.v * p.v;
+    p.ia = (a > 0.0) ? 1.0 / a : 0.0;
+}
+
+__device__ __forceinline__ void iso_dir(const Stream& S, uint32_t n, double xi_mu, Particle& p)
+{
+    const double mu = 2.0 * xi_mu - 1.0;
+    double cphi, sphi;
+    azimuth(S, n, cphi, sphi);
+    const double st = sqrt(1.0 - mu * mu);
+    p.u = mu;
+    p.v = st * cphi;
+    p.w = st * sphi;
+    set_reciprocals(p);
+}
+
+__device__ __forceinline__ void rotate(Particle& p, double mu, double cphi, double sphi)
+{
+    double t = 1.0 - mu * mu;
+    if (t < 0.0) t = 0.0;
+    const double st = sqrt(t);
+    const double u = p.u, v = p.v, w = p.w;
+    if (fabs(w) > 0.9999999999) {
+        p.u = st * cphi;
+        p.v = st * sphi;
+        p.w = (w > 0.0) ? mu : -mu;
+    } else {
+        const double sq = sqrt(1.0 - w * w);
+        const double a1 = st / sq;
+        p.u = mu * u + a1 * ((u * w) * cphi - v * sphi);
+        p.v = mu * v + a1 * ((v * w) * cphi + u * sphi);
+        p.w = mu * w - (st * sq) * cphi;
+    }
+    set_reciprocals(p);
+}
+
+// ---------------------------------------------------------------------------
+// Geometry helpers
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int cell_i(unsigned c) { return (int)(c & 1023u); }
+__device__ __forceinline__ int cell_j(unsigned c) { return (int)((c >> 10) & 1023u); }
+__device__ __forceinline__ int cell_k(unsigned c) { return (int)((c >> 20) & 1023u); }
+__device__ __forceinline__ int cell_in(unsigned c) { return (int)(c >> 30); }
+__device__ __forceinline__ unsigned pack_cell(int i, int j, int k, int in)
+{
+    return (unsigned)i | ((unsigned)j << 10) | ((unsigned)k << 20) | ((unsigned)in << 30);
+}
+__device__ __forceinline__ int cell_lin(const DevProblem& P, unsigned c)
+{
+    return (cell_k(c) * P.ny + cell_j(c)) * P.nx + cell_i(c);
+}
+__device__ __forceinline__ int cell_id(const DevProblem& P, unsigned c) { return cell_lin(P, c) * 2 + cell_in(c); }
+__device__ __forceinline__ int cell_info(const DevProblem& P, unsigned c) { return __ldg(P.cellinfo + cell_lin(P, c)); }
+__device__ __forceinline__ int info_pin(int info) { return (info >> 16) - 1; }
+__device__ __forceinline__ int info_mat(int info) { return info & 0xFFFF; }
+__device__ __forceinline__ int material(const DevProblem& P, unsigned c)
+{
+    const int info = cell_info(P, c);
+    return cell_in(c) ? info_pin(info) : info_mat(info);
+}
+
+// c = (dx^2 + dy^2) - r^2 and k = dx u + dy v about the centre of the cell's pin
+__device__ __forceinline__ void pin_terms(const DevProblem& P, const Particle& p, double& c, double& k)
+{
+    const double dx = p.x - __ldg(P.xc + cell_i(p.cell));
+    const double dy = p.y - __ldg(P.yc + cell_j(p.cell));
+    c = (dx * dx + dy * dy) - P.r2;
+    k = dx * p.u + dy * p.v;
+}
+
+// largest i in [0, n-1] with pl[i] <= x; one cell down when x sits exactly on
+// an interior plane and the direction component is negative
+__device__ __forceinline__ int locate_axis(const double* pl, int n, double x, double dir)
+{
+    int lo = 0, hi = n;                 // pl[lo] <= x (or lo = 0), answer in [lo, hi)
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (__ldg(pl + mid) <= x) lo = mid; else hi = mid;
+    }
+    if (lo > 0 && x == __ldg(pl + lo) && dir < 0.0) lo -= 1;
+    return lo;
+}
+
+__device__ __forceinline__ void locate(const DevProblem& P, Particle& p)
+{
+    const int i = locate_axis(P.xp, P.nx, p.x, p.u);
+    const int j = locate_axis(P.yp, P.ny, p.y, p.v);
+    const int k = locate_axis(P.zp, P.nz, p.z, p.w);
+    p.cell = pack_cell(i, j, k, 0);
+    if (info_pin(cell_info(P, p.cell)) >= 0) {
+        double c, kk;
+        pin_terms(P, p, c, kk);
+        if (c < 0.0) p.cell |= 1u << 30;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Cross sections
+// ---------------------------------------------------------------------------
+struct XS {
+    double st, inv_st, sa, nsf;
+};
+
+__device__ __forceinline__ void xs_mg(const DevProblem& P, int m, int g, XS& X)
+{
+    const int o = m * P.G + g;
+    X.st = __ldg(P.sigt + o);
+    X.inv_st = __ldg(P.inv_sigt + o);
+    X.sa = __ldg(P.sig_a + o);
+    X.nsf = __ldg(P.nusigf + o);
+}
+
+// Union-grid index: largest u in [0, n_union-2] with ue[u] <= E.  The hash
+// buckets the double bit pattern of E (exponent + leading mantissa bits, a
+// piecewise-linear log2), giving a short range for a binary search that
+// compares bit patterns (all energies are positive).
+__device__ __forceinline__ int union_index(const DevProblem& P, double E)
+{
+    const long long eb = dbits(E);
+    long long bkt = (eb >> P.hash_shift) - P.hash_base;
+    if (bkt < 0) bkt = 0;
+    if (bkt > P.n_hash - 1) bkt = P.n_hash - 1;
+    int lo = __ldg(P.hash + bkt) - 1, hi = __ldg(P.hash + bkt + 1);
+    if (lo < 0) lo = 0;
+    if (hi > P.n_union - 1) hi = P.n_union - 1;
+    // invariant: ue[lo] <= E < ue[hi] (or boundaries)
+    if (eb < dbits(__ldg(P.ue + lo))) lo = 0;
+    if (eb >= dbits(__ldg(P.ue + hi))) return (hi >= P.n_union - 1) ? P.n_union - 2 : hi;
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (dbits(__ldg(P.ue + mid)) <= eb) lo = mid; else hi = mid;
+    }
+    return lo;
+}
+
+// CE macroscopic totals at the particle energy: per present nuclide (density
+// > 0, index order) and reaction (elastic, capture, fission) the term
+// N * (s0 + f (s1 - s0)), f = (E - E_i) / (E_i+1 - E_i) via the stored
+// reciprocal; sigma_t is the running sum, sigma_a the capture + fission part.
+__device__ __forceinline__ void xs_ce(const DevProblem& P, int m, double E, XS& X)
+{
+    const int u = union_index(P, E);
+    double cum = 0.0, sa = 0.0;
+    for (int n = 0; n < P.n_nuc; ++n) {
+        const double N = __ldg(P.dens + m * P.n_nuc + n);
+        if (!(N > 0.0)) continue;
+        const int r0 = __ldg(P.uptr + (long long)u * P.n_nuc + n);
+        const double f = (E - __ldg(P.nuc_e + r0)) * __ldg(P.nuc_inv_de + r0);
+#pragma unroll
+        for (int r = 0; r < 3; ++r) {
+            const double s0 = __ldg(P.nuc_sig + 3 * (long long)r0 + r);
+            const double s1 = __ldg(P.nuc_sig + 3 * (long long)(r0 + 1) + r);
+            const double mac = N * (s0 + f * (s1 - s0));
+            cum = cum + mac;
+            if (r > 0) sa = sa + mac;
+        }
+    }
+    X.st = cum;
+    X.inv_st = 1.0 / cum;
+    X.sa = sa;
+    X.nsf = 0.0;
+}
+
+__device__ __forceinline__ void xs_lookup(const DevProblem& P, const Particle& p, int m, XS& X)
+{
+    if (P.kind == 0) xs_mg(P, m, p.g, X);
+    else xs_ce(P, m, p.E, X);
+}
+
+__device__ __forceinline__ int sample_chi(const DevProblem& P, int m, double xi)
+{
+    const double* cc = P.cum_chi + m * P.G;
+    const double t = xi * __ldg(cc + P.G - 1);
+    for (int g = 0; g < P.G; ++g)
+        if (t < __ldg(cc + g)) return g;
+    for (int g = P.G - 1; g >= 0; --g)
+        if (__ldg(P.chi + m * P.G + g) > 0.0) return g;
+    return P.G - 1;
+}
+
+__device__ __forceinline__ double cdf_sample(const DevProblem& P, double xi)
+{
+    // largest k <= n-2 with p[k] <= xi, then linear interpolation
+    int lo = 0, hi = P.n_cdf - 1;
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (__ldg(P.cdf_p + mid) <= xi) lo = mid; else hi = mid;
+    }
+    const double e0 = __ldg(P.cdf_e + lo), e1 = __ldg(P.cdf_e + lo + 1);
+    const double p0 = __ldg(P.cdf_p + lo), p1 = __ldg(P.cdf_p + lo + 1);
+    return e0 + (xi - p0) * (e1 - e0) / (p1 - p0);
+}
+
+}  // namespace tr

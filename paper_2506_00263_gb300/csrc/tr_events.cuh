@@ -1,0 +1,549 @@
+// tr_events.cuh -- the transport events (Sec. 4 of Cuneo et al., M&C 2025):
+// source (make_work), step (cross-section lookup, distance to collision vs.
+// distance to surface, move, track-length tally), collision and surface
+// crossing.  The monolithic task scheme runs step + collision/surface as one
+// event; the decomposed scheme runs them as separate events with a remap in
+// between.  The event counter n (which keys the random numbers) advances once
+// per collision or surface outcome, so both schemes produce identical
+// histories.
+#pragma once
+#include "tr_device.cuh"
+
+namespace tr {
+
+// pending-outcome flags left by the step event for the decomposed scheme
+constexpr unsigned PEND_X = 1u, PEND_Y = 2u, PEND_Z = 4u, PEND_CYL = 8u, PEND_ESCAPE = 16u, PEND_COLLIDE = 32u;
+
+// Per-thread accumulators for the always-on scalar tallies and event counts.
+struct Acc {
+    double flux, absn, prod;
+    unsigned ev[8];
+    unsigned fin[8];
+    __device__ __forceinline__ void zero()
+    {
+        flux = absn = prod = 0.0;
+#pragma unroll
+        for (int i = 0; i < 8; ++i) ev[i] = fin[i] = 0u;
+    }
+};
+
+__device__ __forceinline__ Stream make_stream(const RunParams& R, unsigned id)
+{
+    Stream S;
+    S.k0 = R.key0;
+    S.k1 = R.key1;
+    S.id_lo = id;
+    S.id_hi = R.id_hi;
+    return S;
+}
+
+// ---------------------------------------------------------------------------
+// Track-length mesh tally: 3D DDA (Amanatides & Woo) over the mesh cells the
+// segment p0 + t d, 0 <= t <= L crosses, after clipping it to the mesh box.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void mesh_tally(const DevProblem& P, double* __restrict__ mesh, const Particle& p,
+                                           double x0, double y0, double z0, double L, int goff)
+{
+    const double p0[3] = {x0, y0, z0};
+    const double d[3] = {p.u, p.v, p.w};
+    const double inv[3] = {p.iu, p.iv, p.iw};
+    double t0 = 0.0, t1 = L;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        if (d[a] == 0.0) {
+            if (p0[a] < P.mesh_lo[a] || p0[a] >= P.mesh_hi[a]) return;
+        } else {
+            const double ta = (P.mesh_lo[a] - p0[a]) * inv[a];
+            const double tb = (P.mesh_hi[a] - p0[a]) * inv[a];
+            const double tmin = fmin(ta, tb), tmax = fmax(ta, tb);
+            t0 = fmax(t0, tmin);
+            t1 = fmin(t1, tmax);
+        }
+    }
+    if (!(t1 > t0)) return;
+    int idx[3], step[3];
+    double tn[3], dt[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const int n = P.mesh_n[a];
+        const double q = p0[a] + t0 * d[a];
+        int i = (int)floor((q - P.mesh_lo[a]) * P.mesh_iw[a]);
+        i = i < 0 ? 0 : (i > n - 1 ? n - 1 : i);
+        idx[a] = i;
+        if (d[a] > 0.0) {
+            step[a] = 1;
+            tn[a] = (P.mesh_lo[a] + (double)(i + 1) * P.mesh_w[a] - p0[a]) * inv[a];
+            dt[a] = P.mesh_w[a] * inv[a];
+        } else if (d[a] < 0.0) {
+            step[a] = -1;
+            tn[a] = (P.mesh_lo[a] + (double)i * P.mesh_w[a] - p0[a]) * inv[a];
+            dt[a] = -P.mesh_w[a] * inv[a];
+        } else {
+            step[a] = 0;
+            tn[a] = __longlong_as_double(0x7FF0000000000000ll);
+            dt[a] = 0.0;
+        }
+    }
+    double t = t0;
+    for (int guard = 0; guard < 1 << 20; ++guard) {
+        int a = 0;
+        if (tn[1] < tn[a]) a = 1;
+        if (tn[2] < tn[a]) a = 2;
+        const double te = fmin(tn[a], t1);
+        if (te > t) {
+            const int v = (idx[2] * P.mesh_n[1] + idx[1]) * P.mesh_n[0] + idx[0];
+            atomicAdd(mesh + goff + v, te - t);
+            t = te;
+        }
+        if (!(tn[a] < t1)) break;
+        idx[a] += step[a];
+        if (idx[a] < 0 || idx[a] >= P.mesh_n[a]) break;
+        tn[a] += dt[a];
+    }
+}
+
+// Energy-bin flux tally per material: bin = largest b with e[b] <= E < e[b+1].
+__device__ __forceinline__ void energy_tally(const DevProblem& P, double* __restrict__ etal, int m, double E, double L)
+{
+    const int nb = P.n_ebins;
+    if (!(E >= __ldg(P.e_edges)) || !(E < __ldg(P.e_edges + nb))) return;
+    int lo = 0, hi = nb;
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (__ldg(P.e_edges + mid) <= E) lo = mid; else hi = mid;
+    }
+    atomicAdd(etal + m * nb + lo, L);
+}
+
+// ---------------------------------------------------------------------------
+// Source event (make_work): event count 0 draws; leaves n = 1.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ bool source_particle(const DevProblem& P, const RunParams& R, unsigned id, Particle& p,
+                                                const Bank* site, unsigned long long site_idx)
+{
+    const Stream S = make_stream(R, id);
+    const uint4 b0 = S.block(0u, BLK_MAIN);
+    const double xi_mu = u01(b0.x, b0.y), xi_ge = u01(b0.z, b0.w);
+    p.id = id;
+    p.n = 1u;
+    p.nsites = 0u;
+    p.pend = 0u;
+    p.g = 0;
+    p.E = 0.0;
+    if (site != nullptr || P.src_kind != 0 || P.src_iso) {
+        iso_dir(S, 0u, xi_mu, p);
+    } else {
+        p.u = P.src_dir[0];
+        p.v = P.src_dir[1];
+        p.w = P.src_dir[2];
+        set_reciprocals(p);
+    }
+    if (site != nullptr) {
+        p.x = site->x[site_idx];
+        p.y = site->y[site_idx];
+        p.z = site->z[site_idx];
+        p.cell = site->cell[site_idx];
+        p.g = site->g[site_idx];
+        return true;
+    }
+    if (P.src_kind == 0) {
+        p.x = P.src_pt[0];
+        p.y = P.src_pt[1];
+        p.z = P.src_pt[2];
+        locate(P, p);
+    } else {
+        uint32_t t = 0;
+        for (; t < N_POS; ++t) {
+            const uint4 a = S.block(0u, BLK_POS + 2u * t);
+            const uint4 b = S.block(0u, BLK_POS + 2u * t + 1u);
+            p.x = P.src_lo[0] + u01(a.x, a.y) * (P.src_hi[0] - P.src_lo[0]);
+            p.y = P.src_lo[1] + u01(a.z, a.w) * (P.src_hi[1] - P.src_lo[1]);
+            p.z = P.src_lo[2] + u01(b.x, b.y) * (P.src_hi[2] - P.src_lo[2]);
+            locate(P, p);
+            if (P.src_kind == 1) break;
+            if (cell_in(p.cell) && __ldg(P.src_mat + info_pin(cell_info(P, p.cell)))) break;
+        }
+        if (t == N_POS) return false;
+    }
+    const int m = material(P, p.cell);
+    if (P.kind == 0) p.g = (P.src_group >= 0) ? P.src_group : sample_chi(P, m, xi_ge);
+    else p.E = (P.n_cdf > 1) ? cdf_sample(P, xi_ge) : P.src_energy;
+    return true;
+}
+
+// ---------------------------------------------------------------------------
+// Step event: lookup, distance to collision vs. surface, move, tally.
+// Leaves the outcome in p.pend.  Returns the lookup for the collision.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void step_event(const DevProblem& P, const RunParams& R, Particle& p, const Tallies& T,
+                                           Acc& acc, XS& X, double& xi_react)
+{
+    const unsigned c = p.cell;
+    const int info = cell_info(P, c);
+    const int in = cell_in(c);
+    const int pin = info_pin(info) >= 0;
+    const int m = in ? info_pin(info) : info_mat(info);
+    xs_lookup(P, p, m, X);
+    const Stream S = make_stream(R, p.id);
+    const uint4 b0 = S.block(p.n, BLK_MAIN);
+    xi_react = u01(b0.z, b0.w);
+    const double dcol = (-tr_log(u01(b0.x, b0.y))) * X.inv_st;
+
+    const double INF = __longlong_as_double(0x7FF0000000000000ll);
+    const int i = cell_i(c), j = cell_j(c), k = cell_k(c);
+    double dx, dy, dz;
+    if (p.u > 0.0) dx = (__ldg(P.xp + i + 1) - p.x) * p.iu;
+    else if (p.u < 0.0) dx = (__ldg(P.xp + i) - p.x) * p.iu;
+    else dx = INF;
+    if (p.v > 0.0) dy = (__ldg(P.yp + j + 1) - p.y) * p.iv;
+    else if (p.v < 0.0) dy = (__ldg(P.yp + j) - p.y) * p.iv;
+    else dy = INF;
+    if (p.w > 0.0) dz = (__ldg(P.zp + k + 1) - p.z) * p.iw;
+    else if (p.w < 0.0) dz = (__ldg(P.zp + k) - p.z) * p.iw;
+    else dz = INF;
+    dx = clamp0(dx);
+    dy = clamp0(dy);
+    dz = clamp0(dz);
+
+    double dcyl = INF;
+    if (pin) {
+        double cc, kk;
+        pin_terms(P, p, cc, kk);
+        const double a = p.u * p.u + p.v * p.v;
+        if (a > 0.0) {
+            if (in) {
+                double disc = kk * kk - a * cc;
+                if (disc < 0.0) disc = 0.0;
+                dcyl = (sqrt(disc) - kk) * p.ia;
+            } else if (kk < 0.0) {
+                const double disc = kk * kk - a * cc;
+                if (disc >= 0.0) dcyl = ((-kk) - sqrt(disc)) * p.ia;
+            }
+        }
+        dcyl = clamp0(dcyl);
+    }
+    unsigned flags = 0u;
+    double ds;
+    if (in) {
+        if (lt_nn(dcyl, dz)) {
+            ds = dcyl;
+            flags = PEND_CYL;
+        } else {
+            ds = dz;
+            flags = PEND_Z;
+        }
+    } else {
+        double dmin = dx;
+        if (lt_nn(dy, dmin)) dmin = dy;
+        if (lt_nn(dz, dmin)) dmin = dz;
+        if (pin && lt_nn(dcyl, dmin)) {
+            ds = dcyl;
+            flags = PEND_CYL;
+        } else {
+            ds = dmin;
+            if (dbits(dx) == dbits(ds)) flags |= PEND_X;
+            if (dbits(dy) == dbits(ds)) flags |= PEND_Y;
+            if (dbits(dz) == dbits(ds)) flags |= PEND_Z;
+        }
+    }
+    const bool collided = lt_nn(dcol, ds);
+    if (!collided && dbits(ds) == dbits(INF)) {
+        p.pend = PEND_ESCAPE;
+        return;
+    }
+    const double dist = collided ? dcol : ds;
+    const double x0 = p.x, y0 = p.y, z0 = p.z;
+    p.x = p.x + dist * p.u;
+    p.y = p.y + dist * p.v;
+    p.z = p.z + dist * p.w;
+    acc.flux += dist;
+    acc.absn += dist * X.sa;
+    acc.prod += dist * X.nsf;
+    if (P.has_mesh && dist > 0.0) {
+        const int goff = (P.by_group && P.kind == 0) ? p.g * P.mesh_vox : 0;
+        mesh_tally(P, T.mesh, p, x0, y0, z0, dist, goff);
+    }
+    if (P.n_ebins > 0 && P.kind == 1 && dist > 0.0) energy_tally(P, T.energy, m, p.E, dist);
+    p.pend = collided ? PEND_COLLIDE : flags;
+}
+
+// ---------------------------------------------------------------------------
+// Collision event.  Returns the event type (SCATTER keeps the history alive).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void bank_sites(const DevProblem& P, const RunParams& R, const Stream& S, Particle& p,
+                                           int m, const XS& X, const Bank& B, ErrorWord* err)
+{
+    const double xf = S.first(p.n, BLK_FISSION);
+    const double t = ((X.nsf * X.inv_st) * R.inv_k) + xf;
+    const int nf = (int)floor(t);
+    for (int c = 0; c < nf; ++c) {
+        const double xs = S.first(p.n, BLK_SITE + (uint32_t)c);
+        const int gs = sample_chi(P, m, xs);
+        const unsigned long long pos = atomicAdd(B.count, 1ull);
+        if (pos < B.capacity) {
+            B.x[pos] = p.x;
+            B.y[pos] = p.y;
+            B.z[pos] = p.z;
+            B.g[pos] = gs;
+            B.cell[pos] = p.cell;
+            B.key[pos] = ((unsigned long long)p.id << 32) | p.nsites;
+        } else {
+            atomicCAS(&err->code, 0, ERR_CAPACITY);
+        }
+        p.nsites += 1u;
+    }
+}
+
+__device__ __forceinline__ int collide_event(const DevProblem& P, const RunParams& R, Particle& p, const XS& X,
+                                             double xi_react, const Bank& B, ErrorWord* err)
+{
+    const Stream S = make_stream(R, p.id);
+    const int m = material(P, p.cell);
+    if (P.kind == 0) {
+        if (R.eig && X.nsf > 0.0) bank_sites(P, R, S, p, m, X, B, err);
+        const double t = xi_react * X.st;
+        const double* cs = P.cum_s + (m * P.G + p.g) * P.G;
+        int gp = -1;
+        for (int h = 0; h < P.G; ++h)
+            if (t < __ldg(cs + h)) {
+                gp = h;
+                break;
+            }
+        if (gp < 0) return EV_ABSORB;
+        p.g = gp;
+        iso_dir(S, p.n, S.first(p.n, BLK_ANGLE), p);
+        return EV_SCATTER;
+    }
+    // continuous energy: repeat the lookup terms in order and pick the first
+    // (nuclide, reaction) with xi * sigma_t below the running sum; if none
+    // (rounding), the last term with a positive value
+    const double t = xi_react * X.st;
+    const int u = union_index(P, p.E);
+    double cum = 0.0;
+    int sel_n = -1, sel_r = -1, last_n = -1, last_r = -1;
+    for (int n = 0; n < P.n_nuc && sel_n < 0; ++n) {
+        const double N = __ldg(P.dens + m * P.n_nuc + n);
+        if (!(N > 0.0)) continue;
+        const int r0 = __ldg(P.uptr + (long long)u * P.n_nuc + n);
+        const double f = (p.E - __ldg(P.nuc_e + r0)) * __ldg(P.nuc_inv_de + r0);
+        for (int r = 0; r < 3; ++r) {
+            const double s0 = __ldg(P.nuc_sig + 3 * (long long)r0 + r);
+            const double s1 = __ldg(P.nuc_sig + 3 * (long long)(r0 + 1) + r);
+            const double mac = N * (s0 + f * (s1 - s0));
+            cum = cum + mac;
+            if (mac > 0.0) {
+                last_n = n;
+                last_r = r;
+            }
+            if (t < cum) {
+                sel_n = n;
+                sel_r = r;
+                break;
+            }
+        }
+    }
+    if (sel_n < 0) {
+        sel_n = last_n;
+        sel_r = last_r;
+    }
+    if (sel_n < 0 || sel_r != 0) return EV_ABSORB;
+    const double A = __ldg(P.awr + sel_n);
+    const double mu_cm = 2.0 * S.first(p.n, BLK_ANGLE) - 1.0;
+    const double q = (A * A + (2.0 * A) * mu_cm) + 1.0;
+    const double E1 = (p.E * q) * __ldg(P.inv_ap1sq + sel_n);
+    const double mu = (1.0 + A * mu_cm) / sqrt(q);
+    double cphi, sphi;
+    azimuth(S, p.n, cphi, sphi);
+    rotate(p, mu, cphi, sphi);
+    p.E = E1;
+    if (p.E < P.e_cut) return EV_CUTOFF;
+    return EV_SCATTER;
+}
+
+// ---------------------------------------------------------------------------
+// Surface-crossing event from the step's pending flags.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int surface_event(const DevProblem& P, Particle& p)
+{
+    const unsigned f = p.pend;
+    if (f & PEND_ESCAPE) return EV_LEAK;
+    if (f & PEND_CYL) {
+        p.cell ^= 1u << 30;
+        return EV_SURF_INTERNAL;
+    }
+    int i = cell_i(p.cell), j = cell_j(p.cell), k = cell_k(p.cell), in = cell_in(p.cell);
+    bool leak = false, refl = false, moved_xy = false, moved_z = false;
+    if (f & PEND_X) {
+        const bool hi = p.u > 0.0;
+        if (hi ? (i == P.nx - 1) : (i == 0)) {
+            if (P.bc[hi ? 1 : 0] == 1) {
+                p.u = -p.u;
+                p.iu = -p.iu;
+                refl = true;
+            } else leak = true;
+        } else {
+            i += hi ? 1 : -1;
+            moved_xy = true;
+        }
+    }
+    if (f & PEND_Y) {
+        const bool hi = p.v > 0.0;
+        if (hi ? (j == P.ny - 1) : (j == 0)) {
+            if (P.bc[hi ? 3 : 2] == 1) {
+                p.v = -p.v;
+                p.iv = -p.iv;
+                refl = true;
+            } else leak = true;
+        } else {
+            j += hi ? 1 : -1;
+            moved_xy = true;
+        }
+    }
+    if (f & PEND_Z) {
+        const bool hi = p.w > 0.0;
+        if (hi ? (k == P.nz - 1) : (k == 0)) {
+            if (P.bc[hi ? 5 : 4] == 1) {
+                p.w = -p.w;
+                p.iw = -p.iw;
+                refl = true;
+            } else leak = true;
+        } else {
+            k += hi ? 1 : -1;
+            moved_z = true;
+        }
+    }
+    if (leak) {
+        // the final cell keeps the moves of the other axes crossed in the same event
+        p.cell = pack_cell(i, j, k, in);
+        return EV_LEAK;
+    }
+    if (moved_xy || moved_z) {
+        p.cell = pack_cell(i, j, k, 0);
+        const int pin = info_pin(cell_info(P, p.cell)) >= 0;
+        if (pin && !moved_xy) {
+            if (in) {
+                p.cell |= 1u << 30;
+            } else {
+                double cc, kk;
+                pin_terms(P, p, cc, kk);
+                if (cc < 0.0 || (cc == 0.0 && kk < 0.0)) p.cell |= 1u << 30;
+            }
+        }
+    }
+    return refl ? EV_SURF_REFLECT : EV_SURF_INTERNAL;
+}
+
+// Close an event: count it, advance n, apply the event cap.  Returns whether
+// the history continues; on death records the final state.
+__device__ __forceinline__ bool finish_event(const DevProblem& P, const RunParams& R, Particle& p, int type,
+                                             const Tallies& T, Acc& acc, const Bank& B)
+{
+    acc.ev[type] += 1u;
+    p.n += 1u;
+    bool alive = (type == EV_SCATTER || type == EV_SURF_INTERNAL || type == EV_SURF_REFLECT);
+    if (alive && p.n >= R.max_events) {
+        alive = false;
+        type = EV_MAXEV;
+    }
+    if (!alive) {
+        acc.fin[type] += 1u;
+        if (R.want_log) {
+            T.log_n[p.id] = p.n;
+            T.log_cell[p.id] = cell_id(P, p.cell);
+            T.log_type[p.id] = (uint8_t)type;
+        }
+        if (R.eig) B.site_count[p.id] = p.nsites;
+    }
+    return alive;
+}
+
+// One monolithic event (step followed by collision or surface crossing).
+__device__ __forceinline__ bool mono_event(const DevProblem& P, const RunParams& R, Particle& p, const Tallies& T,
+                                           Acc& acc, const Bank& B, ErrorWord* err)
+{
+    XS X;
+    double xi_react;
+    step_event(P, R, p, T, acc, X, xi_react);
+    int type;
+    if (p.pend == PEND_COLLIDE) type = collide_event(P, R, p, X, xi_react, B, err);
+    else type = surface_event(P, p);
+    return finish_event(P, R, p, type, T, acc, B);
+}
+
+// Decomposed collision event: repeats the (cheap) lookup and the reaction draw.
+__device__ __forceinline__ bool split_collide(const DevProblem& P, const RunParams& R, Particle& p, const Tallies& T,
+                                             Acc& acc, const Bank& B, ErrorWord* err)
+{
+    XS X;
+    const int m = material(P, p.cell);
+    xs_lookup(P, p, m, X);
+    const Stream S = make_stream(R, p.id);
+    const uint4 b0 = S.block(p.n, BLK_MAIN);
+    const int type = collide_event(P, R, p, X, u01(b0.z, b0.w), B, err);
+    return finish_event(P, R, p, type, T, acc, B);
+}
+
+__device__ __forceinline__ bool split_surface(const DevProblem& P, const RunParams& R, Particle& p, const Tallies& T,
+                                             Acc& acc, const Bank& B)
+{
+    const int type = surface_event(P, p);
+    return finish_event(P, R, p, type, T, acc, B);
+}
+
+// ---------------------------------------------------------------------------
+// SoA load / store
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void load_particle(const SoA& s, unsigned long long i, Particle& p, bool ce)
+{
+    p.x = s.x[i]; p.y = s.y[i]; p.z = s.z[i];
+    p.u = s.u[i]; p.v = s.v[i]; p.w = s.w[i];
+    p.iu = s.iu[i]; p.iv = s.iv[i]; p.iw = s.iw[i]; p.ia = s.ia[i];
+    if (ce) p.E = s.E[i]; else p.g = s.g[i];
+    p.cell = s.cell[i]; p.id = s.id[i]; p.n = s.n[i]; p.nsites = s.nsites[i]; p.pend = s.pend[i];
+}
+
+__device__ __forceinline__ void store_particle(const SoA& s, unsigned long long i, const Particle& p, bool ce)
+{
+    s.x[i] = p.x; s.y[i] = p.y; s.z[i] = p.z;
+    s.u[i] = p.u; s.v[i] = p.v; s.w[i] = p.w;
+    s.iu[i] = p.iu; s.iv[i] = p.iv; s.iw[i] = p.iw; s.ia[i] = p.ia;
+    if (ce) s.E[i] = p.E; else s.g[i] = p.g;
+    s.cell[i] = p.cell; s.id[i] = p.id; s.n[i] = p.n; s.nsites[i] = p.nsites; s.pend[i] = p.pend;
+}
+
+// Next queue of a live particle after an event: a step leads to collision or
+// surface crossing; those lead back to a step.
+__device__ __forceinline__ int next_queue_after_step(const Particle& p)
+{
+    return p.pend == PEND_COLLIDE ? Q_COLLIDE : Q_SURFACE;
+}
+
+// Warp-reduce the per-lane accumulators and add them to the global tallies.
+__device__ __forceinline__ void flush_acc(const Acc& acc, const Tallies& T)
+{
+    double f = acc.flux, a = acc.absn, pr = acc.prod;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        f += __shfl_xor_sync(0xFFFFFFFFu, f, o);
+        a += __shfl_xor_sync(0xFFFFFFFFu, a, o);
+        pr += __shfl_xor_sync(0xFFFFFFFFu, pr, o);
+    }
+    unsigned ev[8], fin[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        ev[i] = __reduce_add_sync(0xFFFFFFFFu, acc.ev[i]);
+        fin[i] = __reduce_add_sync(0xFFFFFFFFu, acc.fin[i]);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        if (f != 0.0) atomicAdd(T.scal + 0, f);
+        if (a != 0.0) atomicAdd(T.scal + 1, a);
+        if (pr != 0.0) atomicAdd(T.scal + 2, pr);
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            if (ev[i]) atomicAdd(T.ev_type + i, (unsigned long long)ev[i]);
+            if (fin[i]) atomicAdd(T.fin_type + i, (unsigned long long)fin[i]);
+        }
+    }
+}
+
+}  // namespace tr

@@ -1,0 +1,66 @@
+// tr_kernels.h -- host-callable launchers of the device kernels.
+#pragma once
+#include "tr_device.cuh"
+
+namespace tr {
+
+// Number of kernels launched through the launchers below (process-wide).
+unsigned long long launch_count();
+void count_launches(unsigned long long n);
+
+// Control block of one stack-scheme launch (device memory).
+struct StackCtl {
+    unsigned long long in_count[3];    // particles in each input stack
+    unsigned long long out_count[3];   // pushes into each output stack
+    unsigned long long reserve[3];     // output-stack reservations (make_work threshold)
+    unsigned long long pop;            // virtual pop cursor over the input stacks
+    unsigned long long src_cursor;     // next source index (make_work)
+    unsigned long long capacity;       // particles per stack
+};
+
+// Control block of the asynchronous scheme (device memory).
+struct AsyncCtl {
+    unsigned long long src_cursor;     // next source index (make_work)
+    unsigned long long live;           // particles created and not yet ended
+    unsigned long long spills, refills;
+    unsigned long long free_q[32];     // lock-free queues of empty global links: head | tail << 32
+    unsigned long long full_q[32];     // lock-free queues of filled global links
+    unsigned long long links_made;     // links taken from the arena's never-used tail
+    unsigned hungry;                   // warps currently starving for work
+};
+
+cudaError_t launch_stack(const DevProblem& P, const RunParams& R, const SoA* in, const SoA* out, StackCtl* ctl,
+                         const Tallies& T, const Bank& bank, const Bank* src, ErrorWord* err, int split, int blocks,
+                         cudaStream_t st);
+
+struct AsyncArgs {
+    SoA links;                         // global link arena: n_links * 32 particle slots
+    unsigned* link_next;               // per link: next link in its list
+    int* link_type;                    // per link: event type of its particles
+    int* link_fill;                    // per link: number of particles
+    unsigned long long n_links;
+    AsyncCtl* ctl;
+    Bank bank, src;
+    int use_src;
+    int split;
+    int stash_slots;
+};
+
+cudaError_t launch_async(const DevProblem& P, const RunParams& R, const AsyncArgs& A, const Tallies& T, ErrorWord* err,
+                         int blocks, cudaStream_t st, int* smem_bytes_out);
+int async_max_blocks_per_sm(const DevProblem& P, int split, int stash_slots);
+
+cudaError_t launch_scan(const unsigned* in, unsigned long long n, unsigned long long* tile_sum, unsigned long long* out,
+                        unsigned long long* total, cudaStream_t st);
+cudaError_t launch_bank_order(const Bank& in, unsigned long long m, const unsigned long long* offset, const Bank& out,
+                              ErrorWord* err, cudaStream_t st);
+cudaError_t launch_pop_copies(unsigned long long m, uint32_t key0, uint32_t key1, uint32_t batch, unsigned fl,
+                              double fr, unsigned* copies, cudaStream_t st);
+cudaError_t launch_pop_write(const Bank& in, unsigned long long m, const unsigned* copies,
+                             const unsigned long long* offset, const Bank& out, cudaStream_t st);
+cudaError_t launch_eig_accumulate(const double* raw, int n, double inv_n, double* sum, double* sq, cudaStream_t st);
+cudaError_t launch_scale(const double* in, int n, double s, double* out, cudaStream_t st);
+cudaError_t launch_eig_finish(const double* sum, const double* sq, int n, double na, double* mean, double* sd,
+                              cudaStream_t st);
+
+}  // namespace tr

@@ -1,0 +1,433 @@
+// tr_stack.cu -- stack-based remapping (Sec. 3.1 of Cuneo et al., M&C 2025)
+// and the per-batch kernels of the power iteration.
+//
+// Stack-based remapping keeps, per event type, one global input and one
+// global output buffer used as pop-only / push-only stacks.  Warps pop 32
+// particles with one atomic add, hold each particle in registers while its
+// event runs, and push survivors with one atomic add per warp and destination
+// (ballot / match_any ranks).  A warp calls make_work only once the input
+// stacks have been claimed completely, and only while the output stacks have
+// room (the launch threshold of Sec. 3.1); the host relaunches until the
+// source is exhausted and the stacks are empty.
+#include "tr_events.cuh"
+#include "tr_kernels.h"
+
+#include <atomic>
+
+namespace tr {
+
+constexpr unsigned FULL = 0xFFFFFFFFu;
+
+// warp-aggregated push of `p` (if `live`) onto stack `dst` of the output set
+__device__ __forceinline__ void push_to(const SoA* outs, unsigned long long* out_count, int dst, bool live,
+                                        const Particle& p, bool ce)
+{
+    const int lane = threadIdx.x & 31;
+    const unsigned act = __ballot_sync(FULL, live);
+    if (!act) return;
+    const int key = live ? dst : -1;
+    const unsigned grp = __match_any_sync(FULL, key);
+    const int leader = __ffs(grp) - 1;
+    unsigned long long base = 0;
+    if (live && lane == leader) base = atomicAdd(out_count + dst, (unsigned long long)__popc(grp));
+    base = __shfl_sync(FULL, base, leader);
+    if (live) {
+        const unsigned rank = __popc(grp & ((1u << lane) - 1u));
+        store_particle(outs[dst], base + rank, p, ce);
+    }
+}
+
+struct StackArgs {
+    SoA in[N_QUEUES], out[N_QUEUES];
+    StackCtl* ctl;
+    Bank bank;        // fission bank written this batch
+    Bank src;         // source sites of this batch (eigenvalue batches after the first)
+    int use_src;
+};
+
+// Monolithic ("step") event scheme: one stack pair, R events per pop.
+template <bool CE>
+__global__ void __launch_bounds__(256) k_stack_mono(DevProblem P, RunParams R, StackArgs A, Tallies T, ErrorWord* err)
+{
+    const int lane = threadIdx.x & 31;
+    StackCtl* ctl = A.ctl;
+    const unsigned long long in_count = ctl->in_count[Q_STEP];
+    const unsigned long long cap = ctl->capacity;
+    Acc acc;
+    acc.zero();
+    for (;;) {
+        unsigned long long base = 0;
+        if (lane == 0) base = atomicAdd(&ctl->pop, 32ull);
+        base = __shfl_sync(FULL, base, 0);
+        Particle p;
+        bool live = false;
+        if (base < in_count) {
+            const unsigned long long i = base + lane;
+            if (i < in_count) {
+                load_particle(A.in[Q_STEP], i, p, CE);
+                live = true;
+            }
+            for (int r = 0; r < R.remap_every; ++r) {
+                if (!__any_sync(FULL, live)) break;
+                if (live) live = mono_event(P, R, p, T, acc, A.bank, err);
+            }
+        } else {
+            // make_work: the input stack is fully claimed; create sources
+            // while the output stack keeps room for every input survivor
+            unsigned long long first = ~0ull;
+            if (lane == 0 && *(volatile unsigned long long*)&ctl->src_cursor < R.n_hist) {
+                const unsigned long long r = atomicAdd(&ctl->reserve[Q_STEP], 32ull);
+                if (r + 32ull <= cap) first = atomicAdd(&ctl->src_cursor, 32ull);
+            }
+            first = __shfl_sync(FULL, first, 0);
+            if (first >= R.n_hist) break;
+            const unsigned long long id = first + lane;
+            if (id < R.n_hist) {
+                live = source_particle(P, R, (unsigned)id, p, A.use_src ? &A.src : nullptr, id);
+                if (!live) atomicCAS(&err->code, 0, ERR_INVALID);
+                acc.ev[EV_SOURCE] += 1u;
+            }
+        }
+        push_to(A.out, ctl->out_count, Q_STEP, live, p, CE);
+    }
+    flush_acc(acc, T);
+}
+
+// Decomposed scheme: step / collision / surface stacks processed in one
+// launch; each warp's 32 virtual indices fall in one stack (ranges padded to
+// 32), so a warp runs one event type.
+template <bool CE>
+__global__ void __launch_bounds__(256) k_stack_split(DevProblem P, RunParams R, StackArgs A, Tallies T, ErrorWord* err)
+{
+    const int lane = threadIdx.x & 31;
+    StackCtl* ctl = A.ctl;
+    unsigned long long cnt[N_QUEUES], start[N_QUEUES + 1];
+    start[0] = 0;
+#pragma unroll
+    for (int q = 0; q < N_QUEUES; ++q) {
+        cnt[q] = ctl->in_count[q];
+        start[q + 1] = start[q] + ((cnt[q] + 31ull) & ~31ull);
+    }
+    const unsigned long long cap = ctl->capacity;
+    Acc acc;
+    acc.zero();
+    for (;;) {
+        unsigned long long base = 0;
+        if (lane == 0) base = atomicAdd(&ctl->pop, 32ull);
+        base = __shfl_sync(FULL, base, 0);
+        Particle p;
+        bool live = false;
+        int dst = Q_STEP;
+        if (base < start[N_QUEUES]) {
+            int q = 0;
+            if (base >= start[1]) q = 1;
+            if (base >= start[2]) q = 2;
+            const unsigned long long i = base - start[q] + lane;
+            if (i < cnt[q]) {
+                load_particle(A.in[q], i, p, CE);
+                live = true;
+                if (q == Q_STEP) {
+                    XS X;
+                    double xr;
+                    step_event(P, R, p, T, acc, X, xr);
+                    dst = next_queue_after_step(p);
+                } else if (q == Q_COLLIDE) {
+                    live = split_collide(P, R, p, T, acc, A.bank, err);
+                } else {
+                    live = split_surface(P, R, p, T, acc, A.bank);
+                }
+            }
+        } else {
+            unsigned long long first = ~0ull;
+            if (lane == 0 && *(volatile unsigned long long*)&ctl->src_cursor < R.n_hist) {
+                const unsigned long long r = atomicAdd(&ctl->reserve[Q_STEP], 32ull);
+                if (r + 32ull <= cap) first = atomicAdd(&ctl->src_cursor, 32ull);
+            }
+            first = __shfl_sync(FULL, first, 0);
+            if (first >= R.n_hist) break;
+            const unsigned long long id = first + lane;
+            if (id < R.n_hist) {
+                live = source_particle(P, R, (unsigned)id, p, A.use_src ? &A.src : nullptr, id);
+                if (!live) atomicCAS(&err->code, 0, ERR_INVALID);
+                acc.ev[EV_SOURCE] += 1u;
+            }
+        }
+        push_to(A.out, ctl->out_count, dst, live, p, CE);
+    }
+    flush_acc(acc, T);
+}
+
+// ---------------------------------------------------------------------------
+// Scan: exclusive prefix sum of n 32-bit counts into 64-bit offsets, total in
+// out[n].  Three phases: tile sums, scan of tile sums, tile scans.
+// ---------------------------------------------------------------------------
+constexpr int SCAN_TILE = 2048;
+
+__device__ __forceinline__ unsigned long long block_excl_scan(unsigned long long v, unsigned long long* sh,
+                                                              unsigned long long& total)
+{
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    unsigned long long x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned long long y = __shfl_up_sync(FULL, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) sh[wid] = x;
+    __syncthreads();
+    if (wid == 0) {
+        unsigned long long s = lane < nw ? sh[lane] : 0ull;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned long long y = __shfl_up_sync(FULL, s, o);
+            if (lane >= o) s += y;
+        }
+        if (lane < nw) sh[lane] = s;
+    }
+    __syncthreads();
+    total = sh[nw - 1];
+    const unsigned long long res = x - v + (wid > 0 ? sh[wid - 1] : 0ull);
+    __syncthreads();
+    return res;
+}
+
+__global__ void __launch_bounds__(1024) k_scan_tiles(const unsigned* __restrict__ in, unsigned long long n,
+                                                     unsigned long long* __restrict__ tile_sum)
+{
+    __shared__ unsigned long long sh[32];
+    const unsigned long long b = (unsigned long long)blockIdx.x * SCAN_TILE;
+    unsigned long long s = 0;
+    for (unsigned long long i = b + threadIdx.x; i < b + SCAN_TILE && i < n; i += blockDim.x) s += in[i];
+    unsigned long long tot;
+    block_excl_scan(s, sh, tot);
+    if (threadIdx.x == 0) tile_sum[blockIdx.x] = tot;
+}
+
+__global__ void __launch_bounds__(1024) k_scan_sums(unsigned long long* __restrict__ tile_sum, unsigned long long nt,
+                                                    unsigned long long* __restrict__ total_out)
+{
+    __shared__ unsigned long long sh[32];
+    unsigned long long carry = 0;
+    for (unsigned long long c = 0; c < nt; c += blockDim.x) {
+        const unsigned long long i = c + threadIdx.x;
+        const unsigned long long v = i < nt ? tile_sum[i] : 0ull;
+        unsigned long long tot;
+        const unsigned long long e = block_excl_scan(v, sh, tot);
+        if (i < nt) tile_sum[i] = carry + e;
+        carry += tot;
+    }
+    if (threadIdx.x == 0) *total_out = carry;
+}
+
+__global__ void __launch_bounds__(1024) k_scan_apply(const unsigned* __restrict__ in, unsigned long long n,
+                                                     const unsigned long long* __restrict__ tile_sum,
+                                                     unsigned long long* __restrict__ out)
+{
+    __shared__ unsigned long long sh[32];
+    const unsigned long long b = (unsigned long long)blockIdx.x * SCAN_TILE;
+    constexpr int PER = SCAN_TILE / 1024;
+    unsigned long long loc[PER];
+    unsigned long long s = 0;
+#pragma unroll
+    for (int k = 0; k < PER; ++k) {
+        const unsigned long long i = b + (unsigned long long)threadIdx.x * PER + k;
+        loc[k] = i < n ? in[i] : 0u;
+        s += loc[k];
+    }
+    unsigned long long tot;
+    unsigned long long e = block_excl_scan(s, sh, tot) + tile_sum[blockIdx.x];
+#pragma unroll
+    for (int k = 0; k < PER; ++k) {
+        const unsigned long long i = b + (unsigned long long)threadIdx.x * PER + k;
+        if (i < n) out[i] = e;
+        e += loc[k];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Power-iteration kernels
+// ---------------------------------------------------------------------------
+// Order the bank by (parent history, site sequence): destination =
+// offset[parent] + sequence, offsets from the scan of per-parent counts.
+__global__ void k_bank_order(Bank in, unsigned long long m, const unsigned long long* __restrict__ offset, Bank out,
+                             ErrorWord* err)
+{
+    for (unsigned long long s = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; s < m;
+         s += (unsigned long long)gridDim.x * blockDim.x) {
+        const unsigned long long key = in.key[s];
+        const unsigned long long dst = offset[key >> 32] + (key & 0xFFFFFFFFull);
+        if (dst >= m) {
+            atomicCAS(&err->code, 0, ERR_INVALID);
+            continue;
+        }
+        out.x[dst] = in.x[s];
+        out.y[dst] = in.y[s];
+        out.z[dst] = in.z[s];
+        out.g[dst] = in.g[s];
+        out.cell[dst] = in.cell[s];
+        out.key[dst] = key;
+    }
+}
+
+// Splitting roulette: site s gets floor(r) copies plus one with probability
+// r - floor(r); the draw is Philox keyed by (seed, population tag) with counter
+// (batch, 0, s).
+__global__ void k_pop_copies(unsigned long long m, uint32_t key0, uint32_t key1, uint32_t batch, unsigned fl,
+                             double fr, unsigned* __restrict__ copies)
+{
+    for (unsigned long long s = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; s < m;
+         s += (unsigned long long)gridDim.x * blockDim.x) {
+        const uint4 r = philox10(batch, 0u, (uint32_t)s, (uint32_t)(s >> 32), key0, key1);
+        copies[s] = fl + (u01(r.x, r.y) < fr ? 1u : 0u);
+    }
+}
+
+__global__ void k_pop_write(Bank in, unsigned long long m, const unsigned* __restrict__ copies,
+                            const unsigned long long* __restrict__ offset, Bank out)
+{
+    for (unsigned long long s = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; s < m;
+         s += (unsigned long long)gridDim.x * blockDim.x) {
+        const unsigned long long o = offset[s];
+        const unsigned c = copies[s];
+        for (unsigned k = 0; k < c; ++k) {
+            out.x[o + k] = in.x[s];
+            out.y[o + k] = in.y[s];
+            out.z[o + k] = in.z[s];
+            out.g[o + k] = in.g[s];
+            out.cell[o + k] = in.cell[s];
+        }
+    }
+}
+
+// Active-batch statistics: sum and sum of squares of raw / n per bin.
+__global__ void k_eig_accumulate(const double* __restrict__ raw, int n, double inv_n, double* __restrict__ sum,
+                                 double* __restrict__ sq)
+{
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const double v = raw[i] * inv_n;
+        sum[i] += v;
+        sq[i] += v * v;
+    }
+}
+
+__global__ void k_scale(const double* __restrict__ in, int n, double s, double* __restrict__ out)
+{
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) out[i] = in[i] * s;
+}
+
+__global__ void k_eig_finish(const double* __restrict__ sum, const double* __restrict__ sq, int n, double na,
+                             double* __restrict__ mean, double* __restrict__ sd)
+{
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const double m = sum[i] / na;
+        const double var = (sq[i] / na - m * m) / (na - 1.0);
+        mean[i] = m;
+        sd[i] = var > 0.0 ? sqrt(var) : 0.0;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Host launchers
+// ---------------------------------------------------------------------------
+static std::atomic<unsigned long long> g_launches{0};
+unsigned long long launch_count() { return g_launches.load(); }
+void count_launches(unsigned long long n) { g_launches += n; }
+
+static int grid_for(unsigned long long n, int threads, int max_blocks)
+{
+    unsigned long long b = (n + threads - 1) / threads;
+    if (b < 1) b = 1;
+    if (b > (unsigned long long)max_blocks) b = max_blocks;
+    return (int)b;
+}
+
+cudaError_t launch_stack(const DevProblem& P, const RunParams& R, const SoA* in, const SoA* out, StackCtl* ctl,
+                         const Tallies& T, const Bank& bank, const Bank* src, ErrorWord* err, int split, int blocks,
+                         cudaStream_t st)
+{
+    StackArgs A;
+    for (int q = 0; q < N_QUEUES; ++q) {
+        A.in[q] = in[q];
+        A.out[q] = out[q];
+    }
+    A.ctl = ctl;
+    A.bank = bank;
+    A.use_src = src != nullptr;
+    if (src) A.src = *src;
+    else A.src = bank;
+    count_launches(1);
+    if (split) {
+        if (P.kind == 1) k_stack_split<true><<<blocks, 256, 0, st>>>(P, R, A, T, err);
+        else k_stack_split<false><<<blocks, 256, 0, st>>>(P, R, A, T, err);
+    } else {
+        if (P.kind == 1) k_stack_mono<true><<<blocks, 256, 0, st>>>(P, R, A, T, err);
+        else k_stack_mono<false><<<blocks, 256, 0, st>>>(P, R, A, T, err);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_scan(const unsigned* in, unsigned long long n, unsigned long long* tile_sum, unsigned long long* out,
+                        unsigned long long* total, cudaStream_t st)
+{
+    const unsigned long long nt = (n + SCAN_TILE - 1) / SCAN_TILE;
+    if (n == 0) return cudaMemsetAsync(total, 0, sizeof(unsigned long long), st);
+    count_launches(3);
+    k_scan_tiles<<<(unsigned)nt, 1024, 0, st>>>(in, n, tile_sum);
+    k_scan_sums<<<1, 1024, 0, st>>>(tile_sum, nt, total);
+    k_scan_apply<<<(unsigned)nt, 1024, 0, st>>>(in, n, tile_sum, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_bank_order(const Bank& in, unsigned long long m, const unsigned long long* offset, const Bank& out,
+                              ErrorWord* err, cudaStream_t st)
+{
+    if (m == 0) return cudaSuccess;
+    count_launches(1);
+    k_bank_order<<<grid_for(m, 256, 4096), 256, 0, st>>>(in, m, offset, out, err);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pop_copies(unsigned long long m, uint32_t key0, uint32_t key1, uint32_t batch, unsigned fl,
+                              double fr, unsigned* copies, cudaStream_t st)
+{
+    if (m == 0) return cudaSuccess;
+    count_launches(1);
+    k_pop_copies<<<grid_for(m, 256, 4096), 256, 0, st>>>(m, key0, key1, batch, fl, fr, copies);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pop_write(const Bank& in, unsigned long long m, const unsigned* copies,
+                             const unsigned long long* offset, const Bank& out, cudaStream_t st)
+{
+    if (m == 0) return cudaSuccess;
+    count_launches(1);
+    k_pop_write<<<grid_for(m, 256, 4096), 256, 0, st>>>(in, m, copies, offset, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_eig_accumulate(const double* raw, int n, double inv_n, double* sum, double* sq, cudaStream_t st)
+{
+    if (n <= 0) return cudaSuccess;
+    count_launches(1);
+    k_eig_accumulate<<<grid_for(n, 256, 1024), 256, 0, st>>>(raw, n, inv_n, sum, sq);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_scale(const double* in, int n, double s, double* out, cudaStream_t st)
+{
+    if (n <= 0) return cudaSuccess;
+    count_launches(1);
+    k_scale<<<grid_for(n, 256, 1024), 256, 0, st>>>(in, n, s, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_eig_finish(const double* sum, const double* sq, int n, double na, double* mean, double* sd,
+                              cudaStream_t st)
+{
+    if (n <= 0) return cudaSuccess;
+    count_launches(1);
+    k_eig_finish<<<grid_for(n, 256, 1024), 256, 0, st>>>(sum, sq, n, na, mean, sd);
+    return cudaGetLastError();
+}
+
+}  // namespace tr

@@ -1,0 +1,86 @@
+"""The C-ABI library builds for sm_103a, loads, exports every entry point the
+header declares, and rejects malformed descriptions on the host (no GPU
+needed for these checks)."""
+import ctypes as C
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_2506_00263_gb300 import binding as tb
+from paper_2506_00263_gb300 import build
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    build.build()
+    return tb.lib()
+
+
+def _declared(header):
+    text = open(os.path.join(ROOT, "include", header)).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(tr_[a-z_0-9]+)\s*\(", text)))
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = _declared("tr.h")
+    assert "tr_problem_create" in names and "tr_run_power_iteration" in names
+    raw = C.CDLL(tb.LIB_PATH)
+    missing = [n for n in names if not hasattr(raw, n)]
+    assert not missing, missing
+
+
+def test_version_and_error_strings(lib):
+    assert "sm_103a" in tb.version()
+    assert isinstance(lib.tr_last_error(), bytes)
+
+
+def _geom(nx=1, planes=(0.0, 1.0)):
+    g = tb.GeometryDesc()
+    g.nx = g.ny = g.nz = nx
+    arr = np.array(planes, dtype=np.float64)
+    g.x_planes = g.y_planes = g.z_planes = arr.ctypes.data_as(C.POINTER(C.c_double))
+    cm = np.zeros(max(nx, 1) ** 3, np.int32)
+    g.cell_material = cm.ctypes.data_as(C.POINTER(C.c_int32))
+    return g, (arr, cm)
+
+
+@pytest.mark.parametrize("case", ["zero_cells", "descending_planes", "bad_bc", "material_range", "null_out"])
+def test_invalid_descriptions_rejected_on_host(lib, case):
+    g, keep = _geom()
+    x = tb.XsDesc()
+    x.kind, x.n_materials, x.n_groups = 0, 1, 1
+    s = tb.SourceDesc()
+    ctx = tb.DeviceCtx()
+    out = C.c_void_p()
+    if case == "zero_cells":
+        g.nx = 0
+    elif case == "descending_planes":
+        bad = np.array([1.0, 0.0])
+        keep = keep + (bad,)
+        g.x_planes = bad.ctypes.data_as(C.POINTER(C.c_double))
+    elif case == "bad_bc":
+        g.bc[2] = 9
+    elif case == "material_range":
+        x.n_materials = 0
+    st = lib.tr_problem_create(C.byref(g), C.byref(x), C.byref(s), None, 0, C.byref(ctx),
+                               None if case == "null_out" else C.byref(out))
+    assert st == tb.TR_ERR_INVALID
+    assert lib.tr_last_error()
+    assert not out.value
+
+
+def test_destroy_is_null_safe(lib):
+    lib.tr_problem_destroy(None)
+
+
+def test_header_documents_every_entry_point():
+    text = open(os.path.join(ROOT, "include", "tr.h")).read()
+    for name in _declared("tr.h"):
+        i = text.index(name + "(")
+        before = text[max(0, i - 1500):i]
+        assert "/*" in before, name
