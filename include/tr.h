@@ -151,6 +151,7 @@ typedef struct {
     int32_t want_event_log;             /* keep per-history (events, cell, type) for tr_event_log */
     int32_t spill_threshold;            /* async: spill a full link once a queue exceeds this (0 = default) */
     uint32_t problem_tag;               /* random stream tag (batched runs: problem index) */
+    uint64_t first_history;             /* fixed source: run histories first .. first + n - 1 (a shard) */
 } tr_run_opts;
 
 typedef struct {

@@ -71,7 +71,7 @@ class RunOptsC(C.Structure):
                 ("decomposition", C.c_int32), ("queue_capacity", C.c_uint64), ("blocks_per_sm", C.c_int32),
                 ("remap_every", C.c_int32), ("stash_slots", C.c_int32), ("max_spin", C.c_int64),
                 ("max_events", C.c_uint32), ("want_event_log", C.c_int32), ("spill_threshold", C.c_int32),
-                ("problem_tag", C.c_uint32)]
+                ("problem_tag", C.c_uint32), ("first_history", C.c_uint64)]
 
 
 class RunStats(C.Structure):
@@ -152,6 +152,7 @@ class RunOpts:
     want_event_log: bool = False
     spill_threshold: int = 0
     problem_tag: int = 0
+    first_history: int = 0
 
     def to_c(self) -> RunOptsC:
         c = RunOptsC()

@@ -459,6 +459,8 @@ static tr_status validate_opts(const tr_run_opts* o)
     if (o->decomposition != TR_DECOMP_MONO && o->decomposition != TR_DECOMP_SPLIT)
         return set_err(TR_ERR_INVALID, "bad decomposition");
     if (o->n_histories >= (1ull << 32)) return set_err(TR_ERR_INVALID, "n_histories must be < 2^32 per run");
+    if (o->first_history + o->n_histories > (1ull << 32))
+        return set_err(TR_ERR_INVALID, "first_history + n_histories must not exceed 2^32");
     if (o->remap_every < 0 || o->blocks_per_sm < 0 || o->stash_slots < 0 || o->max_spin < 0)
         return set_err(TR_ERR_INVALID, "negative tuning option");
     if (o->decomposition == TR_DECOMP_SPLIT && o->remap_every > 1)
@@ -628,6 +630,7 @@ static RunParams base_params(const tr_run_opts* o, unsigned long long n)
     R.remap_every = o->remap_every > 0 ? o->remap_every : 1;
     R.max_spin = o->max_spin > 0 ? (uint64_t)o->max_spin : (1ull << 24);
     R.spill_threshold = o->spill_threshold ? o->spill_threshold : 64;
+    R.id_base = (uint32_t)o->first_history;
     return R;
 }
 
@@ -720,6 +723,7 @@ extern "C" tr_status tr_run_power_iteration(tr_problem* pr, const tr_eig_opts* e
     if (!site_count || !copies || !offs || !tiles || !total) return set_err(TR_ERR_NOMEM, "bank allocation failed");
     bank.site_count = site_count;
     const tr_run_opts* o = &eo->run;
+    if (o->first_history != 0) return set_err(TR_ERR_INVALID, "first_history applies to fixed-source runs only");
     RunParams R = base_params(o, eo->n_per_batch);
     R.eig = 1;
     if (R.want_log) {

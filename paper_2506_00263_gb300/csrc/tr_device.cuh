@@ -76,6 +76,7 @@ struct RunParams {
     uint64_t n_hist;
     uint32_t key0, key1;               // (seed_lo, seed_hi ^ tag)
     uint32_t id_hi;                    // batch index (eigenvalue) or 0
+    uint32_t id_base;                  // first history of a fixed-source shard (random-stream id offset)
     uint32_t max_events;
     int eig;
     double inv_k;

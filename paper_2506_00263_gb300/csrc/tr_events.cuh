@@ -32,7 +32,7 @@ __device__ __forceinline__ Stream make_stream(const RunParams& R, unsigned id)
     Stream S;
     S.k0 = R.key0;
     S.k1 = R.key1;
-    S.id_lo = id;
+    S.id_lo = R.id_base + id;
     S.id_hi = R.id_hi;
     return S;
 }

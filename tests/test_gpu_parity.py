@@ -211,3 +211,27 @@ def test_invalid_options_rejected():
         tb.lib()
         prob.tally(7)
     prob.close()
+
+
+def test_virtual_ranks_sum_equals_single_run():
+    """Three contiguous shards (first_history) run separately and combined in
+    rank order reproduce the single run: the multi-GPU replica/shard path
+    emulated on one GPU, one shard after another."""
+    from paper_2506_00263_gb300 import parallel
+    n, world = 50_021, 3
+    p = _problem("lattice")
+    whole = _gpu_fixed("lattice", n, tb.SCHEME_ASYNC, tb.DECOMP_SPLIT)
+    parts, logs = [], []
+    for r in range(world):
+        first, count = parallel.shard(n, r, world)
+        g = _gpu_fixed("lattice", count, tb.SCHEME_STACK, tb.DECOMP_MONO, first_history=first)
+        parts.append((count, g["mesh"], g["scalars"]))
+        logs.append(g["log"])
+    for k in range(3):
+        assert np.array_equal(np.concatenate([l[k] for l in logs]), whole["log"][k])
+    assert_tally_close(parallel.combine_means([(c, m) for c, m, _ in parts]), whole["mesh"], "sharded mesh")
+    assert_tally_close(parallel.combine_means([(c, s) for c, _, s in parts]), whole["scalars"], "sharded scalars")
+    # and against the oracle's shard of the middle rank
+    first, count = parallel.shard(n, 1, world)
+    o = oracle.run_fixed_source(p, count, seed=1, id_offset=first)
+    assert_logs_equal(logs[1], (o["log_n"], o["log_cell"], o["log_type"]), "middle shard")
