@@ -220,6 +220,10 @@ enum { TR_TALLY_MESH = 0, TR_TALLY_ENERGY = 1, TR_TALLY_SCALARS = 2 };
  * out_on_device != 0.  n_out must equal the tally size (TR_ERR_INVALID
  * otherwise).  Synchronises the context stream. */
 tr_status tr_tallies(const tr_problem *problem, int32_t tally_id, double *out, size_t n_out, int32_t out_on_device);
+
+/* Standard deviation of the mean of a tally over the active batches of the
+ * last power iteration (TR_ERR_STATE after a fixed-source run); same
+ * arguments, layout and errors as tr_tallies. */
 tr_status tr_tally_stddev(const tr_problem *problem, int32_t tally_id, double *out, size_t n_out,
                           int32_t out_on_device);
 /* Number of doubles of a tally (0 if absent). */

@@ -79,8 +79,13 @@ def test_destroy_is_null_safe(lib):
 
 
 def test_header_documents_every_entry_point():
-    text = open(os.path.join(ROOT, "include", "tr.h")).read()
+    """Every declaration is directly preceded by a comment block."""
+    lines = open(os.path.join(ROOT, "include", "tr.h")).read().splitlines()
     for name in _declared("tr.h"):
-        i = text.index(name + "(")
-        before = text[max(0, i - 1500):i]
-        assert "/*" in before, name
+        decl = [i for i, l in enumerate(lines)
+                if re.match(r"^[A-Za-z_].*\b" + name + r"\s*\(", l) and not l.lstrip().startswith("*")]
+        assert decl, name
+        j = decl[0] - 1
+        while j >= 0 and not lines[j].strip():
+            j -= 1
+        assert lines[j].rstrip().endswith("*/"), name
