@@ -235,6 +235,44 @@ size_t tr_tally_size(const tr_problem *problem, int32_t tally_id);
 tr_status tr_event_log(const tr_problem *problem, uint32_t *n_events, int32_t *final_cell, uint8_t *final_type,
                        size_t n);
 
+/* Size of the static scratch of tr_run_fixed_source_noalloc (bytes held on
+ * every GPU that loads the library) and the largest queue_capacity (particles
+ * of spill space) it accepts. */
+#define TR_NOALLOC_SCRATCH_BYTES (512u * 1024u)
+#define TR_NOALLOC_MAX_QUEUE_CAPACITY 4096u
+
+/* Fixed-source run that allocates nothing (the paper has no counterpart; it
+ * exists for callers of this library that cannot allocate device memory
+ * while they run, such as an application that reserves the GPU's memory for
+ * its own pool at start-up, or a latency-sensitive loop that cannot accept
+ * the device synchronisation of cudaMalloc/cudaFree).  It runs the
+ * asynchronous scheme (opts->scheme must be TR_SCHEME_ASYNC, either
+ * decomposition) and gives the same results as tr_run_fixed_source.
+ *  - Scratch (error word, counters, scheduler control block, a link arena of
+ *    TR_NOALLOC_MAX_QUEUE_CAPACITY particles for spills) is a file-scope
+ *    __device__ array of TR_NOALLOC_SCRATCH_BYTES that each GPU loading the
+ *    library holds until exit.  No cudaMalloc, cudaFree, event or stream
+ *    creation happens in this call.
+ *  - The first call on each device looks the array's device address up
+ *    (cudaGetSymbolAddress, with that device current); make that first call
+ *    before any stream capture.
+ *  - Every call on a device shares the array; each call clears what must
+ *    start at zero.  Calls whose work overlaps on the GPU (other streams or
+ *    threads) race on the array and must not be issued concurrently.
+ *  - Inputs: `problem` from tr_problem_create; `opts` as for
+ *    tr_run_fixed_source (queue_capacity counts spill particles, at most
+ *    TR_NOALLOC_MAX_QUEUE_CAPACITY, 0 = the maximum; want_event_log must be
+ *    0).  Outputs: device arrays of tr_tally_size() doubles for the mesh and
+ *    energy tallies (NULL allowed when the tally is absent) and 3 doubles of
+ *    scalar tallies, all means per source particle; `stats` (may be NULL)
+ *    has no timing (seconds are 0).  The problem's own tallies are left
+ *    untouched.  Synchronises the problem's stream before returning.
+ *  - Errors: TR_ERR_INVALID for a non-async scheme, an event log request, a
+ *    queue_capacity above the maximum or NULL outputs; TR_ERR_CUDA,
+ *    TR_ERR_TIMEOUT, TR_ERR_CAPACITY as for tr_run_fixed_source. */
+tr_status tr_run_fixed_source_noalloc(tr_problem *problem, const tr_run_opts *opts, double *mesh_out,
+                                      double *energy_out, double *scalars_out, tr_run_stats *stats);
+
 /* Diagnostics: number of kernels this library has launched in this process
  * (all kernels, all problems).  Read it before and after a call to count the
  * launches the call made. */

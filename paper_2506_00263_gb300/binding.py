@@ -121,6 +121,8 @@ def lib():
     L.tr_event_log.restype = C.c_int
     L.tr_last_error.restype = C.c_char_p
     L.tr_kernel_launch_count.restype = C.c_uint64
+    L.tr_run_fixed_source_noalloc.argtypes = [C.c_void_p, C.POINTER(RunOptsC), _dp, _dp, _dp, C.POINTER(RunStats)]
+    L.tr_run_fixed_source_noalloc.restype = C.c_int
     L.tr_version.restype = C.c_char_p
     _lib = L
     return L
@@ -300,6 +302,20 @@ class Problem:
         c = opts.to_c()
         _check(lib().tr_run_fixed_source(self._h, C.byref(c), C.byref(st)))
         self.last_stats = st
+        return stats_dict(st)
+
+    def run_fixed_source_noalloc(self, opts: RunOpts, mesh_ptr: int, energy_ptr: int, scalars_ptr: int) -> dict:
+        """tr_run_fixed_source_noalloc: the asynchronous fixed-source run with
+        its scratch in the library's static device array; the tallies go to the
+        given device pointers (0 for an absent tally).  Allocates nothing."""
+        st = RunStats()
+        c = opts.to_c()
+
+        def ptr(v):
+            return C.cast(C.c_void_p(int(v)), _dp) if v else None
+
+        _check(lib().tr_run_fixed_source_noalloc(self._h, C.byref(c), ptr(mesh_ptr), ptr(energy_ptr),
+                                                 ptr(scalars_ptr), C.byref(st)))
         return stats_dict(st)
 
     def power_iteration(self, n_per_batch, n_inactive, n_active, opts: RunOpts, k0=1.0,

@@ -892,6 +892,18 @@ extern "C" tr_status tr_event_log(const tr_problem* pr, uint32_t* n_events, int3
 
 extern "C" const char* tr_last_error(void) { return g_err.c_str(); }
 
+namespace tr {
+void set_last_error(const char* msg) { g_err = msg; }
+
+const DevProblem* problem_device_data(const tr_problem* pr, int* device, cudaStream_t* stream, int* sms)
+{
+    *device = pr->ctx.device;
+    *stream = pr->stream;
+    *sms = pr->sms;
+    return &pr->dp;
+}
+}  // namespace tr
+
 extern "C" uint64_t tr_kernel_launch_count(void) { return tr::launch_count(); }
 
 extern "C" const char* tr_version(void) { return "tr 0.1 (sm_103a)"; }

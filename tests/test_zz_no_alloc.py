@@ -1,0 +1,58 @@
+"""tr_run_fixed_source_noalloc: the run for callers that cannot allocate
+device memory while they work (an application that reserves the GPU's memory
+for its own pool, or a loop that cannot accept the synchronisation of
+cudaMalloc).  Its scratch is the library's static device array, so two calls
+in a row must each clear and reuse it and still match the allocating entry
+point.  This file is collected last so that a failure here never stops the
+rest of the GPU suite."""
+import numpy as np
+import pytest
+
+from paper_2506_00263_gb300 import binding as tb
+from paper_2506_00263_gb300 import inputs
+from tests._util import assert_tally_close
+
+pytestmark = pytest.mark.gpu
+
+MAX_QUEUE = 4096          # TR_NOALLOC_MAX_QUEUE_CAPACITY in include/tr.h
+
+
+def test_noalloc_matches_allocating_run_on_two_calls():
+    import torch
+    from paper_2506_00263_gb300 import build
+    build.build()
+    prob = tb.Problem(inputs.c5g7_lattice())
+    n = 100_003
+    ref_opts = tb.RunOpts(n_histories=n, seed=3, scheme=tb.SCHEME_ASYNC, decomposition=tb.DECOMP_SPLIT)
+    ref = prob.run_fixed_source(ref_opts)
+    ref_mesh = prob.tally(tb.TALLY_MESH)
+    ref_scal = prob.tally(tb.TALLY_SCALARS)
+
+    mesh = torch.empty(ref_mesh.size, dtype=torch.float64, device="cuda")
+    scal = torch.empty(3, dtype=torch.float64, device="cuda")
+    calls = [tb.RunOpts(n_histories=n, seed=3, scheme=tb.SCHEME_ASYNC, decomposition=tb.DECOMP_SPLIT),
+             # second call: force spills through the static link arena
+             tb.RunOpts(n_histories=n, seed=3, scheme=tb.SCHEME_ASYNC, decomposition=tb.DECOMP_SPLIT,
+                        spill_threshold=-32, queue_capacity=MAX_QUEUE)]
+    for k, opts in enumerate(calls):
+        mesh.fill_(float("nan"))
+        scal.fill_(float("nan"))
+        torch.cuda.synchronize()
+        st = prob.run_fixed_source_noalloc(opts, mesh.data_ptr(), 0, scal.data_ptr())
+        got_mesh = mesh.cpu().numpy()
+        got_scal = scal.cpu().numpy()
+        assert np.all(np.isfinite(got_mesh)) and np.all(np.isfinite(got_scal)), f"call {k}"
+        assert_tally_close(got_mesh, ref_mesh, f"mesh (call {k})")
+        assert_tally_close(got_scal, ref_scal, f"scalars (call {k})")
+        assert np.array_equal(st["final_by_type"], ref["final_by_type"]), f"call {k}"
+        assert np.array_equal(st["events_by_type"], ref["events_by_type"]), f"call {k}"
+        if k == 1:
+            assert st["spills"] > 0 and st["refills"] > 0
+
+    # requests beyond the static arena are refused before any device work
+    with pytest.raises(tb.TransportError) as e:
+        prob.run_fixed_source_noalloc(tb.RunOpts(n_histories=10, scheme=tb.SCHEME_ASYNC,
+                                                 queue_capacity=MAX_QUEUE + 32),
+                                      mesh.data_ptr(), 0, scal.data_ptr())
+    assert e.value.status == tb.TR_ERR_INVALID
+    prob.close()
