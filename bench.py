@@ -178,7 +178,8 @@ def run_ours(args):
     scheme = tb.SCHEME_ASYNC if args.scheme == "async" else tb.SCHEME_STACK
     decomp = tb.DECOMP_SPLIT if args.decomp == "split" else tb.DECOMP_MONO
     spec = inputs.c5g7_lattice()
-    opts = tb.RunOpts(seed=1 + 1000 * rank, scheme=scheme, decomposition=decomp)
+    opts = tb.RunOpts(seed=1 + 1000 * rank, scheme=scheme, decomposition=decomp, stash_slots=args.stash,
+                      blocks_per_sm=args.bps, remap_every=args.remap, queue_capacity=args.queue)
     stream = torch.cuda.current_stream()
     prob = tb.Problem(spec)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float64, device="cuda")   # 512 MB > L2
@@ -272,6 +273,7 @@ def run_ours(args):
         "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": WORKLOAD, "scheme": args.scheme, "decomposition": args.decomp,
+                   "stash_slots": args.stash, "blocks_per_sm": args.bps, "remap_every": args.remap,
                    "n_per_batch": args.n_per_batch, "batches": args.inactive + args.active,
                    "l2": "flushed between steps (512 MB write)"},
         "histories_per_s": hist_all / t,
@@ -325,6 +327,10 @@ def main():
     ap.add_argument("--active", type=int, default=N_ACTIVE)
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--stash", type=int, default=0, help="async: particle slots per block stash (0 = default)")
+    ap.add_argument("--bps", type=int, default=0, help="blocks per SM (0 = default)")
+    ap.add_argument("--remap", type=int, default=1, help="monolithic: events between remaps")
+    ap.add_argument("--queue", type=int, default=0, help="stack: particles per stack; async: spill links x 32")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)

@@ -218,14 +218,14 @@ __device__ __forceinline__ unsigned new_link(const AsyncArgs& A, int start, cons
 // ---------------------------------------------------------------------------
 // The persistent kernel
 // ---------------------------------------------------------------------------
-template <bool CE>
-__global__ void __launch_bounds__(256) k_async(DevProblem P, RunParams R, AsyncArgs A, Tallies T, ErrorWord* err)
+template <bool CE, bool SPLIT>
+__global__ void __launch_bounds__(256, 2) k_async(DevProblem P, RunParams R, AsyncArgs A, Tallies T, ErrorWord* err)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     const int S = A.stash_slots;
     const Stash st = carve(smem, S);
     const int lane = threadIdx.x & 31;
-    const int nq = A.split ? N_QUEUES : 1;
+    constexpr int nq = SPLIT ? N_QUEUES : 1;
     AsyncCtl* ctl = A.ctl;
 
     if (threadIdx.x == 0) {
@@ -422,7 +422,8 @@ __global__ void __launch_bounds__(256) k_async(DevProblem P, RunParams R, AsyncA
             first = __shfl_sync(FULLM, first, 0);
             const unsigned long long id = first + lane;
             if (id < R.n_hist) {
-                live = source_particle(P, R, (unsigned)id, p, A.use_src ? &A.src : nullptr, id);
+                TR_LANES(11);
+                live = source_particle<CE>(P, R, (unsigned)id, p, A.use_src ? &A.src : nullptr, id);
                 if (!live) fail(err, ERR_INVALID, 5);
                 acc.ev[EV_SOURCE] += 1u;
                 next = Q_STEP;
@@ -432,18 +433,19 @@ __global__ void __launch_bounds__(256) k_async(DevProblem P, RunParams R, AsyncA
         } else {
             // mode 0 (warp-uniform): lanes beyond a partial link hold no slot and stay idle
             if (slot >= 0) {
+                TR_LANES(0);
                 slot_load(st, slot, p);
                 live = true;
-                if (!A.split) {
-                    for (int r = 0; r < R.remap_every && live; ++r) live = mono_event(P, R, p, T, acc, A.bank, err);
+                if (!SPLIT) {
+                    for (int r = 0; r < R.remap_every && live; ++r) live = mono_event<CE>(P, R, p, T, acc, A.bank, err);
                     next = live ? Q_STEP : Q_DEAD;
                 } else if (q == Q_STEP) {
                     XS X;
                     double xr;
-                    step_event(P, R, p, T, acc, X, xr);
+                    step_event<CE>(P, R, p, T, acc, X, xr);
                     next = next_queue_after_step(p);
                 } else if (q == Q_COLLIDE) {
-                    live = split_collide(P, R, p, T, acc, A.bank, err);
+                    live = split_collide<CE>(P, R, p, T, acc, A.bank, err);
                     next = live ? Q_STEP : Q_DEAD;
                 } else {
                     live = split_surface(P, R, p, T, acc, A.bank);
@@ -484,25 +486,36 @@ __global__ void __launch_bounds__(256) k_async(DevProblem P, RunParams R, AsyncA
 
 namespace tr {
 
-template <bool CE>
+template <bool CE, bool SPLIT>
 static cudaError_t prepare_async(size_t smem)
 {
-    return cudaFuncSetAttribute(k_async<CE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    return cudaFuncSetAttribute(k_async<CE, SPLIT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+}
+
+template <bool CE, bool SPLIT>
+static int occupancy_async(size_t smem)
+{
+    int nb = 0;
+    if (prepare_async<CE, SPLIT>(smem) != cudaSuccess) return 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_async<CE, SPLIT>, 256, smem) != cudaSuccess) return 0;
+    return nb;
 }
 
 int async_max_blocks_per_sm(const DevProblem& P, int split, int stash_slots)
 {
-    (void)split;
     const size_t smem = stash_bytes(stash_slots);
-    int nb = 0;
-    if (P.kind == 1) {
-        if (prepare_async<true>(smem) != cudaSuccess) return 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_async<true>, 256, smem);
-    } else {
-        if (prepare_async<false>(smem) != cudaSuccess) return 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_async<false>, 256, smem);
-    }
-    return nb;
+    if (P.kind == 1) return split ? occupancy_async<true, true>(smem) : occupancy_async<true, false>(smem);
+    return split ? occupancy_async<false, true>(smem) : occupancy_async<false, false>(smem);
+}
+
+template <bool CE, bool SPLIT>
+static cudaError_t launch_async_t(const DevProblem& P, const RunParams& R, const AsyncArgs& A, const Tallies& T,
+                                  ErrorWord* err, int blocks, cudaStream_t st, size_t smem)
+{
+    const cudaError_t e = prepare_async<CE, SPLIT>(smem);
+    if (e != cudaSuccess) return e;
+    k_async<CE, SPLIT><<<blocks, 256, smem, st>>>(P, R, A, T, err);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_async(const DevProblem& P, const RunParams& R, const AsyncArgs& A, const Tallies& T, ErrorWord* err,
@@ -511,17 +524,22 @@ cudaError_t launch_async(const DevProblem& P, const RunParams& R, const AsyncArg
     const size_t smem = stash_bytes(A.stash_slots);
     if (smem_bytes_out) *smem_bytes_out = (int)smem;
     count_launches(1);
-    cudaError_t e;
-    if (P.kind == 1) {
-        e = prepare_async<true>(smem);
-        if (e != cudaSuccess) return e;
-        k_async<true><<<blocks, 256, smem, st>>>(P, R, A, T, err);
-    } else {
-        e = prepare_async<false>(smem);
-        if (e != cudaSuccess) return e;
-        k_async<false><<<blocks, 256, smem, st>>>(P, R, A, T, err);
-    }
-    return cudaGetLastError();
+    if (P.kind == 1)
+        return A.split ? launch_async_t<true, true>(P, R, A, T, err, blocks, st, smem)
+                       : launch_async_t<true, false>(P, R, A, T, err, blocks, st, smem);
+    return A.split ? launch_async_t<false, true>(P, R, A, T, err, blocks, st, smem)
+                   : launch_async_t<false, false>(P, R, A, T, err, blocks, st, smem);
 }
 
 }  // namespace tr
+
+#ifdef TR_PROFILE_LANES
+// Diagnostic builds only: copy and clear the lane-occupancy counters.
+extern "C" int tr_profile_lanes_read(unsigned long long* out, int n)
+{
+    if (n > 64) n = 64;
+    if (cudaMemcpyFromSymbol(out, tr::g_lane_prof, n * sizeof(unsigned long long)) != cudaSuccess) return 1;
+    unsigned long long z[64] = {};
+    return cudaMemcpyToSymbol(tr::g_lane_prof, z, sizeof(z)) != cudaSuccess;
+}
+#endif

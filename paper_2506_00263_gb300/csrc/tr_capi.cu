@@ -338,6 +338,32 @@ extern "C" tr_status tr_problem_create(const tr_geometry_desc* G, const tr_xs_de
         P.by_group = (Tl->by_group && X->kind == TR_XS_MG) ? 1 : 0;
         P.mesh_size = (int)(nv * (P.by_group ? P.G : 1));
     }
+    // per axis: the mesh cell that contains geometry cell i (a segment never
+    // leaves its geometry cell, so its whole length goes there), or -1
+    {
+        std::vector<int> c2v((size_t)P.nx + P.ny + P.nz, -1);
+        if (P.has_mesh) {
+            const double* pl[3] = {G->x_planes, G->y_planes, G->z_planes};
+            const int ng[3] = {G->nx, G->ny, G->nz};
+            size_t off = 0;
+            for (int a = 0; a < 3; ++a) {
+                for (int i = 0; i < ng[a]; ++i) {
+                    const double g0 = pl[a][i], g1 = pl[a][i + 1];
+                    if (!std::isfinite(g0) || !std::isfinite(g1)) continue;
+                    const double mid = 0.5 * (g0 + g1);
+                    const double kf = std::floor((mid - P.mesh_lo[a]) * P.mesh_iw[a]);
+                    if (kf < 0.0 || kf >= (double)P.mesh_n[a]) continue;
+                    const int k = (int)kf;
+                    const double m0 = P.mesh_lo[a] + (double)k * P.mesh_w[a];
+                    const double m1 = P.mesh_lo[a] + (double)(k + 1) * P.mesh_w[a];
+                    const double tol = 1e-12 * std::max(std::max(std::fabs(m0), std::fabs(m1)), P.mesh_w[a]);
+                    if (g0 >= m0 - tol && g1 <= m1 + tol) c2v[off + i] = k;
+                }
+                off += ng[a];
+            }
+        }
+        P.cell2vox = upload(pr, c2v.data(), c2v.size(), &ok);
+    }
     if (n_tallies == 1 && Tl->n_energy_bins > 0) {
         if (!Tl->energy_edges || !ascending(Tl->energy_edges, Tl->n_energy_bins))
             return fail_out(TR_ERR_INVALID, "energy edges must be ascending");

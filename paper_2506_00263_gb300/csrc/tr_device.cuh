@@ -22,6 +22,24 @@ constexpr int EV_SOURCE = 0, EV_SCATTER = 1, EV_ABSORB = 2, EV_SURF_INTERNAL = 3
               EV_LEAK = 5, EV_CUTOFF = 6, EV_MAXEV = 7;
 constexpr int ERR_NONE = 0, ERR_CAPACITY = 3, ERR_TIMEOUT = 4, ERR_INVALID = 1;
 
+// Optional lane-occupancy counters (diagnostic builds with -DTR_PROFILE_LANES
+// only): per site, the number of warp arrivals and the active lanes summed.
+#ifdef TR_PROFILE_LANES
+static __device__ unsigned long long g_lane_prof[64];
+#define TR_LANES(site)                                                                          \
+    do {                                                                                        \
+        const unsigned m_ = __activemask();                                                     \
+        if ((int)(threadIdx.x & 31) == __ffs(m_) - 1) {                                         \
+            atomicAdd(&g_lane_prof[2 * (site)], 1ull);                                          \
+            atomicAdd(&g_lane_prof[2 * (site) + 1], (unsigned long long)__popc(m_));            \
+        }                                                                                       \
+    } while (0)
+#else
+#define TR_LANES(site) \
+    do {               \
+    } while (0)
+#endif
+
 // Random-block assignment within one event (counter word 1).
 constexpr uint32_t BLK_MAIN = 0u;      // (distance | source cosine, reaction | source group/energy)
 constexpr uint32_t BLK_ANGLE = 1u;     // (scatter cosine / CM cosine, -)
@@ -67,6 +85,7 @@ struct DevProblem {
     // tallies
     int has_mesh, mesh_n[3], by_group, n_ebins, mesh_vox;
     double mesh_lo[3], mesh_hi[3], mesh_w[3], mesh_iw[3];
+    const int *cell2vox;               // [nx | ny | nz]: mesh voxel holding geometry cell i on that axis, or -1
     const double *e_edges;
     int mesh_size, energy_size;
 };
@@ -181,9 +200,14 @@ struct Stream {
     }
 };
 
-// Non-negative doubles (and +inf) order like their bit patterns.
+// Comparisons answered on the bit patterns with integer instructions (no NaN
+// reaches them): non-negative doubles and +inf order like their bit patterns,
+// and the sign tests below treat -0.0 exactly as the double comparisons do.
 __device__ __forceinline__ long long dbits(double d) { return __double_as_longlong(d); }
-__device__ __forceinline__ bool lt_nn(double a, double b) { return dbits(a) < dbits(b); }
+__device__ __forceinline__ bool lt_nn(double a, double b) { return dbits(a) < dbits(b); }   // a < b, a, b >= +0
+__device__ __forceinline__ bool gt0(double x) { return dbits(x) > 0; }                       // x > 0
+__device__ __forceinline__ bool lt0(double x) { return dbits(x) < 0 && (dbits(x) << 1) != 0; }  // x < 0
+__device__ __forceinline__ bool ge0(double x) { return !lt0(x); }                            // x >= 0
 // max(d, +0) with -0 and negatives mapped to +0 (no NaN reaches here)
 __device__ __forceinline__ double clamp0(double d) { return dbits(d) <= 0 ? 0.0 : d; }
 
@@ -227,12 +251,13 @@ __device__ __forceinline__ void azimuth(const Stream& S, uint32_t n, double& cph
 {
     double a = 1.0, b = 0.0, a2 = 1.0, b2 = 0.0, s = 1.0;
     for (uint32_t t = 0; t < N_AZIMUTH; ++t) {
+        TR_LANES(6);
         const uint4 r = S.block(n, BLK_AZIMUTH + t);
         const double ta = 2.0 * u01(r.x, r.y) - 1.0;
         const double tb = 2.0 * u01(r.z, r.w) - 1.0;
         const double ta2 = ta * ta, tb2 = tb * tb;
         const double ts = ta2 + tb2;
-        if (ts <= 1.0 && ts > 0.0) {
+        if (dbits(ts) <= dbits(1.0) && gt0(ts)) {   // 0 < ts <= 1 (ts >= +0)
             a = ta; b = tb; a2 = ta2; b2 = tb2; s = ts;
             break;
         }
@@ -244,11 +269,12 @@ __device__ __forceinline__ void azimuth(const Stream& S, uint32_t n, double& cph
 
 __device__ __forceinline__ void set_reciprocals(Particle& p)
 {
-    p.iu = (p.u != 0.0) ? 1.0 / p.u : 0.0;
-    p.iv = (p.v != 0.0) ? 1.0 / p.v : 0.0;
-    p.iw = (p.w != 0.0) ? 1.0 / p.w : 0.0;
+    // (bits << 1) != 0 is x != +-0
+    p.iu = (dbits(p.u) << 1) ? 1.0 / p.u : 0.0;
+    p.iv = (dbits(p.v) << 1) ? 1.0 / p.v : 0.0;
+    p.iw = (dbits(p.w) << 1) ? 1.0 / p.w : 0.0;
     const double a = p.u * p.u + p.v * p.v;
-    p.ia = (a > 0.0) ? 1.0 / a : 0.0;
+    p.ia = gt0(a) ? 1.0 / a : 0.0;
 }
 
 __device__ __forceinline__ void iso_dir(const Stream& S, uint32_t n, double xi_mu, Particle& p)
@@ -323,6 +349,7 @@ __device__ __forceinline__ int locate_axis(const double* pl, int n, double x, do
 {
     int lo = 0, hi = n;                 // pl[lo] <= x (or lo = 0), answer in [lo, hi)
     while (hi - lo > 1) {
+        TR_LANES(9);
         const int mid = (lo + hi) >> 1;
         if (__ldg(pl + mid) <= x) lo = mid; else hi = mid;
     }
@@ -410,10 +437,11 @@ __device__ __forceinline__ void xs_ce(const DevProblem& P, int m, double E, XS& 
     X.nsf = 0.0;
 }
 
+template <bool CE>
 __device__ __forceinline__ void xs_lookup(const DevProblem& P, const Particle& p, int m, XS& X)
 {
-    if (P.kind == 0) xs_mg(P, m, p.g, X);
-    else xs_ce(P, m, p.E, X);
+    if (CE) xs_ce(P, m, p.E, X);
+    else xs_mg(P, m, p.g, X);
 }
 
 __device__ __forceinline__ int sample_chi(const DevProblem& P, int m, double xi)

@@ -38,67 +38,85 @@ __device__ __forceinline__ Stream make_stream(const RunParams& R, unsigned id)
 }
 
 // ---------------------------------------------------------------------------
-// Track-length mesh tally: 3D DDA (Amanatides & Woo) over the mesh cells the
-// segment p0 + t d, 0 <= t <= L crosses, after clipping it to the mesh box.
+// Track-length mesh tally.  A segment never leaves its geometry cell; when
+// that cell lies inside one mesh cell on every axis (precomputed per axis)
+// the whole length goes to that mesh cell.  Otherwise a 3D DDA (Amanatides &
+// Woo) walks the mesh cells the segment p0 + t d, 0 <= t <= L crosses, after
+// clipping it to the mesh box.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ void mesh_tally(const DevProblem& P, double* __restrict__ mesh, const Particle& p,
                                            double x0, double y0, double z0, double L, int goff)
 {
-    const double p0[3] = {x0, y0, z0};
-    const double d[3] = {p.u, p.v, p.w};
-    const double inv[3] = {p.iu, p.iv, p.iw};
+    const int vx = __ldg(P.cell2vox + cell_i(p.cell));
+    const int vy = __ldg(P.cell2vox + P.nx + cell_j(p.cell));
+    const int vz = __ldg(P.cell2vox + P.nx + P.ny + cell_k(p.cell));
+    const int nx = P.mesh_n[0], ny = P.mesh_n[1], nz = P.mesh_n[2];
+    if ((vx | vy | vz) >= 0) {
+        atomicAdd(mesh + goff + (vz * ny + vy) * nx + vx, L);
+        return;
+    }
+    const double INF = __longlong_as_double(0x7FF0000000000000ll);
     double t0 = 0.0, t1 = L;
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        if (d[a] == 0.0) {
-            if (p0[a] < P.mesh_lo[a] || p0[a] >= P.mesh_hi[a]) return;
-        } else {
-            const double ta = (P.mesh_lo[a] - p0[a]) * inv[a];
-            const double tb = (P.mesh_hi[a] - p0[a]) * inv[a];
-            const double tmin = fmin(ta, tb), tmax = fmax(ta, tb);
-            t0 = fmax(t0, tmin);
-            t1 = fmin(t1, tmax);
-        }
+    // clip per axis (a zero component keeps the start point's slab test)
+#define TR_CLIP(D, INV, X0, LO, HI)                                                   \
+    if ((D) == 0.0) {                                                                 \
+        if ((X0) < (LO) || (X0) >= (HI)) return;                                      \
+    } else {                                                                          \
+        const double ta = ((LO) - (X0)) * (INV), tb = ((HI) - (X0)) * (INV);           \
+        t0 = fmax(t0, fmin(ta, tb));                                                  \
+        t1 = fmin(t1, fmax(ta, tb));                                                  \
     }
+    TR_CLIP(p.u, p.iu, x0, P.mesh_lo[0], P.mesh_hi[0])
+    TR_CLIP(p.v, p.iv, y0, P.mesh_lo[1], P.mesh_hi[1])
+    TR_CLIP(p.w, p.iw, z0, P.mesh_lo[2], P.mesh_hi[2])
+#undef TR_CLIP
     if (!(t1 > t0)) return;
-    int idx[3], step[3];
-    double tn[3], dt[3];
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        const int n = P.mesh_n[a];
-        const double q = p0[a] + t0 * d[a];
-        int i = (int)floor((q - P.mesh_lo[a]) * P.mesh_iw[a]);
-        i = i < 0 ? 0 : (i > n - 1 ? n - 1 : i);
-        idx[a] = i;
-        if (d[a] > 0.0) {
-            step[a] = 1;
-            tn[a] = (P.mesh_lo[a] + (double)(i + 1) * P.mesh_w[a] - p0[a]) * inv[a];
-            dt[a] = P.mesh_w[a] * inv[a];
-        } else if (d[a] < 0.0) {
-            step[a] = -1;
-            tn[a] = (P.mesh_lo[a] + (double)i * P.mesh_w[a] - p0[a]) * inv[a];
-            dt[a] = -P.mesh_w[a] * inv[a];
-        } else {
-            step[a] = 0;
-            tn[a] = __longlong_as_double(0x7FF0000000000000ll);
-            dt[a] = 0.0;
-        }
+    // start cell, next crossing parameter and its step per axis
+#define TR_START(D, INV, X0, A, N, I, S, TN, DT)                                      \
+    int I = (int)floor(((X0) + t0 * (D) - P.mesh_lo[A]) * P.mesh_iw[A]);             \
+    I = I < 0 ? 0 : (I > (N) - 1 ? (N) - 1 : I);                                      \
+    int S = 0;                                                                        \
+    double TN = INF, DT = 0.0;                                                        \
+    if (gt0(D)) {                                                                     \
+        S = 1;                                                                        \
+        TN = (P.mesh_lo[A] + (double)(I + 1) * P.mesh_w[A] - (X0)) * (INV);           \
+        DT = P.mesh_w[A] * (INV);                                                     \
+    } else if (lt0(D)) {                                                              \
+        S = -1;                                                                       \
+        TN = (P.mesh_lo[A] + (double)I * P.mesh_w[A] - (X0)) * (INV);                 \
+        DT = -P.mesh_w[A] * (INV);                                                    \
     }
+    TR_START(p.u, p.iu, x0, 0, nx, ix, sx, tx, dtx)
+    TR_START(p.v, p.iv, y0, 1, ny, iy, sy, ty, dty)
+    TR_START(p.w, p.iw, z0, 2, nz, iz, sz, tz, dtz)
+#undef TR_START
+    TR_LANES(7);
     double t = t0;
-    for (int guard = 0; guard < 1 << 20; ++guard) {
-        int a = 0;
-        if (tn[1] < tn[a]) a = 1;
-        if (tn[2] < tn[a]) a = 2;
-        const double te = fmin(tn[a], t1);
+    for (int guard = 0; guard < (1 << 20); ++guard) {
+        TR_LANES(8);
+        int ax = 0;
+        double tn = tx;
+        if (ty < tn) { tn = ty; ax = 1; }
+        if (tz < tn) { tn = tz; ax = 2; }
+        const double te = fmin(tn, t1);
         if (te > t) {
-            const int v = (idx[2] * P.mesh_n[1] + idx[1]) * P.mesh_n[0] + idx[0];
-            atomicAdd(mesh + goff + v, te - t);
+            atomicAdd(mesh + goff + (iz * ny + iy) * nx + ix, te - t);
             t = te;
         }
-        if (!(tn[a] < t1)) break;
-        idx[a] += step[a];
-        if (idx[a] < 0 || idx[a] >= P.mesh_n[a]) break;
-        tn[a] += dt[a];
+        if (!(tn < t1)) break;
+        if (ax == 0) {
+            ix += sx;
+            if (ix < 0 || ix >= nx) break;
+            tx += dtx;
+        } else if (ax == 1) {
+            iy += sy;
+            if (iy < 0 || iy >= ny) break;
+            ty += dty;
+        } else {
+            iz += sz;
+            if (iz < 0 || iz >= nz) break;
+            tz += dtz;
+        }
     }
 }
 
@@ -118,9 +136,11 @@ __device__ __forceinline__ void energy_tally(const DevProblem& P, double* __rest
 // ---------------------------------------------------------------------------
 // Source event (make_work): event count 0 draws; leaves n = 1.
 // ---------------------------------------------------------------------------
+template <bool CE>
 __device__ __forceinline__ bool source_particle(const DevProblem& P, const RunParams& R, unsigned id, Particle& p,
                                                 const Bank* site, unsigned long long site_idx)
 {
+    TR_LANES(4);
     const Stream S = make_stream(R, id);
     const uint4 b0 = S.block(0u, BLK_MAIN);
     const double xi_mu = u01(b0.x, b0.y), xi_ge = u01(b0.z, b0.w);
@@ -154,6 +174,7 @@ __device__ __forceinline__ bool source_particle(const DevProblem& P, const RunPa
     } else {
         uint32_t t = 0;
         for (; t < N_POS; ++t) {
+            TR_LANES(5);
             const uint4 a = S.block(0u, BLK_POS + 2u * t);
             const uint4 b = S.block(0u, BLK_POS + 2u * t + 1u);
             p.x = P.src_lo[0] + u01(a.x, a.y) * (P.src_hi[0] - P.src_lo[0]);
@@ -166,7 +187,7 @@ __device__ __forceinline__ bool source_particle(const DevProblem& P, const RunPa
         if (t == N_POS) return false;
     }
     const int m = material(P, p.cell);
-    if (P.kind == 0) p.g = (P.src_group >= 0) ? P.src_group : sample_chi(P, m, xi_ge);
+    if (!CE) p.g = (P.src_group >= 0) ? P.src_group : sample_chi(P, m, xi_ge);
     else p.E = (P.n_cdf > 1) ? cdf_sample(P, xi_ge) : P.src_energy;
     return true;
 }
@@ -175,15 +196,17 @@ __device__ __forceinline__ bool source_particle(const DevProblem& P, const RunPa
 // Step event: lookup, distance to collision vs. surface, move, tally.
 // Leaves the outcome in p.pend.  Returns the lookup for the collision.
 // ---------------------------------------------------------------------------
+template <bool CE>
 __device__ __forceinline__ void step_event(const DevProblem& P, const RunParams& R, Particle& p, const Tallies& T,
                                            Acc& acc, XS& X, double& xi_react)
 {
+    TR_LANES(1);
     const unsigned c = p.cell;
     const int info = cell_info(P, c);
     const int in = cell_in(c);
     const int pin = info_pin(info) >= 0;
     const int m = in ? info_pin(info) : info_mat(info);
-    xs_lookup(P, p, m, X);
+    xs_lookup<CE>(P, p, m, X);
     const Stream S = make_stream(R, p.id);
     const uint4 b0 = S.block(p.n, BLK_MAIN);
     xi_react = u01(b0.z, b0.w);
@@ -192,14 +215,14 @@ __device__ __forceinline__ void step_event(const DevProblem& P, const RunParams&
     const double INF = __longlong_as_double(0x7FF0000000000000ll);
     const int i = cell_i(c), j = cell_j(c), k = cell_k(c);
     double dx, dy, dz;
-    if (p.u > 0.0) dx = (__ldg(P.xp + i + 1) - p.x) * p.iu;
-    else if (p.u < 0.0) dx = (__ldg(P.xp + i) - p.x) * p.iu;
+    if (gt0(p.u)) dx = (__ldg(P.xp + i + 1) - p.x) * p.iu;
+    else if (lt0(p.u)) dx = (__ldg(P.xp + i) - p.x) * p.iu;
     else dx = INF;
-    if (p.v > 0.0) dy = (__ldg(P.yp + j + 1) - p.y) * p.iv;
-    else if (p.v < 0.0) dy = (__ldg(P.yp + j) - p.y) * p.iv;
+    if (gt0(p.v)) dy = (__ldg(P.yp + j + 1) - p.y) * p.iv;
+    else if (lt0(p.v)) dy = (__ldg(P.yp + j) - p.y) * p.iv;
     else dy = INF;
-    if (p.w > 0.0) dz = (__ldg(P.zp + k + 1) - p.z) * p.iw;
-    else if (p.w < 0.0) dz = (__ldg(P.zp + k) - p.z) * p.iw;
+    if (gt0(p.w)) dz = (__ldg(P.zp + k + 1) - p.z) * p.iw;
+    else if (lt0(p.w)) dz = (__ldg(P.zp + k) - p.z) * p.iw;
     else dz = INF;
     dx = clamp0(dx);
     dy = clamp0(dy);
@@ -210,14 +233,14 @@ __device__ __forceinline__ void step_event(const DevProblem& P, const RunParams&
         double cc, kk;
         pin_terms(P, p, cc, kk);
         const double a = p.u * p.u + p.v * p.v;
-        if (a > 0.0) {
+        if (gt0(a)) {
             if (in) {
                 double disc = kk * kk - a * cc;
-                if (disc < 0.0) disc = 0.0;
+                if (lt0(disc)) disc = 0.0;
                 dcyl = (sqrt(disc) - kk) * p.ia;
-            } else if (kk < 0.0) {
+            } else if (lt0(kk)) {
                 const double disc = kk * kk - a * cc;
-                if (disc >= 0.0) dcyl = ((-kk) - sqrt(disc)) * p.ia;
+                if (ge0(disc)) dcyl = ((-kk) - sqrt(disc)) * p.ia;
             }
         }
         dcyl = clamp0(dcyl);
@@ -259,11 +282,11 @@ __device__ __forceinline__ void step_event(const DevProblem& P, const RunParams&
     acc.flux += dist;
     acc.absn += dist * X.sa;
     acc.prod += dist * X.nsf;
-    if (P.has_mesh && dist > 0.0) {
-        const int goff = (P.by_group && P.kind == 0) ? p.g * P.mesh_vox : 0;
+    if (P.has_mesh && gt0(dist)) {
+        const int goff = (!CE && P.by_group) ? p.g * P.mesh_vox : 0;
         mesh_tally(P, T.mesh, p, x0, y0, z0, dist, goff);
     }
-    if (P.n_ebins > 0 && P.kind == 1 && dist > 0.0) energy_tally(P, T.energy, m, p.E, dist);
+    if (CE && P.n_ebins > 0 && gt0(dist)) energy_tally(P, T.energy, m, p.E, dist);
     p.pend = collided ? PEND_COLLIDE : flags;
 }
 
@@ -294,18 +317,20 @@ __device__ __forceinline__ void bank_sites(const DevProblem& P, const RunParams&
     }
 }
 
+template <bool CE>
 __device__ __forceinline__ int collide_event(const DevProblem& P, const RunParams& R, Particle& p, const XS& X,
                                              double xi_react, const Bank& B, ErrorWord* err)
 {
+    TR_LANES(2);
     const Stream S = make_stream(R, p.id);
     const int m = material(P, p.cell);
-    if (P.kind == 0) {
-        if (R.eig && X.nsf > 0.0) bank_sites(P, R, S, p, m, X, B, err);
+    if (!CE) {
+        if (R.eig && gt0(X.nsf)) bank_sites(P, R, S, p, m, X, B, err);
         const double t = xi_react * X.st;
         const double* cs = P.cum_s + (m * P.G + p.g) * P.G;
         int gp = -1;
         for (int h = 0; h < P.G; ++h)
-            if (t < __ldg(cs + h)) {
+            if (lt_nn(t, __ldg(cs + h))) {
                 gp = h;
                 break;
             }
@@ -365,6 +390,7 @@ __device__ __forceinline__ int collide_event(const DevProblem& P, const RunParam
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ int surface_event(const DevProblem& P, Particle& p)
 {
+    TR_LANES(3);
     const unsigned f = p.pend;
     if (f & PEND_ESCAPE) return EV_LEAK;
     if (f & PEND_CYL) {
@@ -458,28 +484,31 @@ __device__ __forceinline__ bool finish_event(const DevProblem& P, const RunParam
 }
 
 // One monolithic event (step followed by collision or surface crossing).
+template <bool CE>
 __device__ __forceinline__ bool mono_event(const DevProblem& P, const RunParams& R, Particle& p, const Tallies& T,
                                            Acc& acc, const Bank& B, ErrorWord* err)
 {
+    TR_LANES(10);
     XS X;
     double xi_react;
-    step_event(P, R, p, T, acc, X, xi_react);
+    step_event<CE>(P, R, p, T, acc, X, xi_react);
     int type;
-    if (p.pend == PEND_COLLIDE) type = collide_event(P, R, p, X, xi_react, B, err);
+    if (p.pend == PEND_COLLIDE) type = collide_event<CE>(P, R, p, X, xi_react, B, err);
     else type = surface_event(P, p);
     return finish_event(P, R, p, type, T, acc, B);
 }
 
 // Decomposed collision event: repeats the (cheap) lookup and the reaction draw.
+template <bool CE>
 __device__ __forceinline__ bool split_collide(const DevProblem& P, const RunParams& R, Particle& p, const Tallies& T,
                                              Acc& acc, const Bank& B, ErrorWord* err)
 {
     XS X;
     const int m = material(P, p.cell);
-    xs_lookup(P, p, m, X);
+    xs_lookup<CE>(P, p, m, X);
     const Stream S = make_stream(R, p.id);
     const uint4 b0 = S.block(p.n, BLK_MAIN);
-    const int type = collide_event(P, R, p, X, u01(b0.z, b0.w), B, err);
+    const int type = collide_event<CE>(P, R, p, X, u01(b0.z, b0.w), B, err);
     return finish_event(P, R, p, type, T, acc, B);
 }
 

@@ -69,7 +69,7 @@ __global__ void __launch_bounds__(256) k_stack_mono(DevProblem P, RunParams R, S
             }
             for (int r = 0; r < R.remap_every; ++r) {
                 if (!__any_sync(FULL, live)) break;
-                if (live) live = mono_event(P, R, p, T, acc, A.bank, err);
+                if (live) live = mono_event<CE>(P, R, p, T, acc, A.bank, err);
             }
         } else {
             // make_work: the input stack is fully claimed; create sources
@@ -83,7 +83,7 @@ __global__ void __launch_bounds__(256) k_stack_mono(DevProblem P, RunParams R, S
             if (first >= R.n_hist) break;
             const unsigned long long id = first + lane;
             if (id < R.n_hist) {
-                live = source_particle(P, R, (unsigned)id, p, A.use_src ? &A.src : nullptr, id);
+                live = source_particle<CE>(P, R, (unsigned)id, p, A.use_src ? &A.src : nullptr, id);
                 if (!live) atomicCAS(&err->code, 0, ERR_INVALID);
                 acc.ev[EV_SOURCE] += 1u;
             }
@@ -129,10 +129,10 @@ __global__ void __launch_bounds__(256) k_stack_split(DevProblem P, RunParams R, 
                 if (q == Q_STEP) {
                     XS X;
                     double xr;
-                    step_event(P, R, p, T, acc, X, xr);
+                    step_event<CE>(P, R, p, T, acc, X, xr);
                     dst = next_queue_after_step(p);
                 } else if (q == Q_COLLIDE) {
-                    live = split_collide(P, R, p, T, acc, A.bank, err);
+                    live = split_collide<CE>(P, R, p, T, acc, A.bank, err);
                 } else {
                     live = split_surface(P, R, p, T, acc, A.bank);
                 }
@@ -147,7 +147,7 @@ __global__ void __launch_bounds__(256) k_stack_split(DevProblem P, RunParams R, 
             if (first >= R.n_hist) break;
             const unsigned long long id = first + lane;
             if (id < R.n_hist) {
-                live = source_particle(P, R, (unsigned)id, p, A.use_src ? &A.src : nullptr, id);
+                live = source_particle<CE>(P, R, (unsigned)id, p, A.use_src ? &A.src : nullptr, id);
                 if (!live) atomicCAS(&err->code, 0, ERR_INVALID);
                 acc.ev[EV_SOURCE] += 1u;
             }
