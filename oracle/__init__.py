@@ -97,6 +97,15 @@ class OrcEig(C.Structure):
     ]
 
 
+class OrcSens(C.Structure):
+    _fields_ = [
+        ("n_hist", C.c_uint64), ("seed", C.c_uint64), ("tag", C.c_uint32), ("max_events", C.c_uint32),
+        ("g_mesh", C.POINTER(C.c_double)), ("g_scal", C.POINTER(C.c_double)),
+        ("d_sigt", C.POINTER(C.c_double)), ("d_sigs", C.POINTER(C.c_double)), ("d_nusigf", C.POINTER(C.c_double)),
+        ("value", C.c_double),
+    ]
+
+
 def lib():
     global _lib
     if _lib is None:
@@ -104,6 +113,8 @@ def lib():
         L = C.CDLL(_LIB_PATH)
         L.orc_fixed_source.argtypes = [C.POINTER(OrcProblem), C.POINTER(OrcFixed)]
         L.orc_fixed_source.restype = C.c_int
+        L.orc_sensitivities.argtypes = [C.POINTER(OrcProblem), C.POINTER(OrcSens)]
+        L.orc_sensitivities.restype = C.c_int
         L.orc_power_iteration.argtypes = [C.POINTER(OrcProblem), C.POINTER(OrcEig)]
         L.orc_power_iteration.restype = C.c_int
         L.orc_philox4x32_10.argtypes = [C.POINTER(C.c_uint32)] * 3
@@ -228,6 +239,31 @@ def run_fixed_source(prob, n_hist: int, seed: int = 1, tag: int = 0, max_events:
     out["scalars"] = np.array(o.scalars[:])
     out["events_by_type"] = np.array(o.events_by_type[:], np.uint64)
     out["final_by_type"] = np.array(o.final_by_type[:], np.uint64)
+    return out
+
+
+def sensitivities(prob, n_hist: int, g_mesh=None, g_scal=None, seed: int = 1, tag: int = 0,
+                  max_events: int = 0) -> dict:
+    """Score-function + pathwise derivatives of L = g . tallies with respect to
+    sigma_t [m][g], sigma_s [m][g][g'] and nu_sigma_f [m][g]."""
+    L = lib()
+    m = _Marshalled(prob)
+    o = OrcSens()
+    o.n_hist, o.seed, o.tag, o.max_events = n_hist, seed, tag, max_events
+    keep = []
+    if g_mesh is not None:
+        gm = np.ascontiguousarray(g_mesh, np.float64)
+        keep.append(gm)
+        o.g_mesh = _dp(gm)
+    if g_scal is not None:
+        gs = np.ascontiguousarray(g_scal, np.float64)
+        keep.append(gs)
+        o.g_scal = _dp(gs)
+    M, G = prob.n_materials, prob.n_groups
+    out = {"d_sigt": np.zeros((M, G)), "d_sigs": np.zeros((M, G, G)), "d_nusigf": np.zeros((M, G))}
+    o.d_sigt, o.d_sigs, o.d_nusigf = _dp(out["d_sigt"]), _dp(out["d_sigs"]), _dp(out["d_nusigf"])
+    out["status"] = L.orc_sensitivities(C.byref(m.s), C.byref(o))
+    out["value"] = o.value
     return out
 
 

@@ -262,6 +262,10 @@ typedef struct {
     uint64_t bank_n, bank_cap;
     int bank_overflow;
     uint64_t events_by_type[8];
+    /* adjoint: per-event record of the current history */
+    struct orc_rec { int m, g, collided, react, h; double len, f; } *rec;
+    int rec_n, rec_cap, recording;
+    const double *gw_mesh, *gw_scal;
 } ctx;
 
 static int setup(ctx *C, const orc_problem *P)
@@ -312,6 +316,7 @@ static int setup(ctx *C, const orc_problem *P)
 
 static void teardown(ctx *C)
 {
+    free(C->rec);
     free(C->inv_sigt); free(C->cum_s); free(C->sig_a); free(C->cum_chi); free(C->inv_de);
     free(C->mesh); free(C->energy);
     free(C->bank_pos); free(C->bank_g); free(C->bank_cell); free(C->bank_E);
@@ -545,6 +550,55 @@ static void score_segment(ctx *C, const particle *p, const double p0[3], double 
     }
 }
 
+/* Upstream-gradient-weighted contribution of one segment to L:
+ * sum over mesh cells of g_mesh * length in the cell (same slab clipping as
+ * the mesh tally) + g_flux*len + g_abs*len*sigma_a + g_prod*len*nu_sigma_f. */
+static double weighted_segment(const ctx *C, const particle *p, const double p0[3], double len, const xsval *X)
+{
+    const orc_problem *P = C->P;
+    nsum f;
+    memset(&f, 0, sizeof(f));
+    if (C->gw_mesh && P->has_mesh && len > 0.0) {
+        int r0[3], r1[3], ok = 1;
+        for (int a = 0; a < 3 && ok; ++a) {
+            double x1 = p0[a] + len * p->d[a];
+            if ((p0[a] < P->mesh_lo[a] && x1 < P->mesh_lo[a]) || (p0[a] > P->mesh_hi[a] && x1 > P->mesh_hi[a])) ok = 0;
+            else {
+                mesh_range(P, a, p0[a], x1, &r0[a], &r1[a]);
+                if (r0[a] > r1[a]) ok = 0;
+            }
+        }
+        int64_t goff = (P->mesh_by_group && P->xs_kind == 0) ? (int64_t)p->g * C->mesh_vox : 0;
+        int idx[3];
+        if (ok)
+            for (idx[2] = r0[2]; idx[2] <= r1[2]; ++idx[2])
+                for (idx[1] = r0[1]; idx[1] <= r1[1]; ++idx[1])
+                    for (idx[0] = r0[0]; idx[0] <= r1[0]; ++idx[0]) {
+                        double l = clip_voxel(P, p0, p->d, len, idx);
+                        if (l > 0.0) {
+                            int64_t v = ((int64_t)idx[2] * P->mesh_n[1] + idx[1]) * P->mesh_n[0] + idx[0];
+                            nadd(&f, C->gw_mesh[goff + v] * l);
+                        }
+                    }
+    }
+    if (C->gw_scal) {
+        nadd(&f, C->gw_scal[0] * len);
+        nadd(&f, C->gw_scal[1] * (len * X->sa));
+        nadd(&f, C->gw_scal[2] * (len * X->nsf));
+    }
+    return nval(&f);
+}
+
+static void record_event(ctx *C, const particle *p, int m, int collided, double len, double f)
+{
+    if (C->rec_n == C->rec_cap) {
+        C->rec_cap = C->rec_cap ? 2 * C->rec_cap : 256;
+        C->rec = realloc(C->rec, sizeof(*C->rec) * (size_t)C->rec_cap);
+    }
+    struct orc_rec *r = &C->rec[C->rec_n++];
+    r->m = m; r->g = p->g; r->collided = collided; r->react = 0; r->h = -1; r->len = len; r->f = f;
+}
+
 /* ------------------------------------------------------------------------ */
 /* Source event (make_work, Sec. 3): n = 0 draws.                            */
 /* ------------------------------------------------------------------------ */
@@ -665,9 +719,14 @@ static void collide(ctx *C, particle *p, int m, const xsval *X, double xi_react)
         for (int h = 0; h < G; ++h)
             if (t < cs[h]) { gp = h; break; }
         if (gp < 0) {
+            if (C->recording) C->rec[C->rec_n - 1].react = 2;
             kill(p, ORC_ABSORB);
             C->events_by_type[ORC_ABSORB]++;
             return;
+        }
+        if (C->recording) {
+            C->rec[C->rec_n - 1].react = 1;
+            C->rec[C->rec_n - 1].h = gp;
         }
         p->g = gp;
         double xa[2];
@@ -775,6 +834,7 @@ static void event(ctx *C, particle *p)
     p->x[2] = p->x[2] + dist * p->d[2];
     score_segment(C, p, p0, dist, m, &X);
     p->track += dist;
+    if (C->recording) record_event(C, p, m, collided, dist, weighted_segment(C, p, p0, dist, &X));
 
     if (collided) {
         collide(C, p, m, &X, xi[1]);
@@ -857,6 +917,90 @@ int orc_fixed_source(const orc_problem *P, orc_fixed *o)
     }
     finish_tallies(&C, (double)o->n_hist, o->mesh, o->energy, o->scalars);
     memcpy(o->events_by_type, C.events_by_type, sizeof(C.events_by_type));
+    teardown(&C);
+    return st;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Sensitivities.  Per history the events are recorded, F = sum_k f_k is the  */
+/* history's weighted score, and every random decision d contributes          */
+/* s_d * (F - F_before_d), where F_before_d sums the segments completed before */
+/* d (a flight decision owns the segment it creates; a reaction decision comes */
+/* after it).  Scores:                                                         */
+/*   flight ending in a collision   d/dSt = 1/St - len                         */
+/*   flight ending at a surface     d/dSt = -len                               */
+/*   scatter g -> h                 d/dSs[g->h] = 1/Ss[g->h], d/dSt = -1/St     */
+/*   absorption (prob. Sa/St)       d/dSt = 1/Sa - 1/St, d/dSs[g->*] = -1/Sa    */
+/* Pathwise terms of f_k: g_abs*len on St and -g_abs*len on every Ss[g->*]   */
+/* (Sa = St - sum Ss), g_prod*len on nuSf.  Directions and the source do not   */
+/* depend on the cross sections.                                               */
+/* ------------------------------------------------------------------------ */
+int orc_sensitivities(const orc_problem *P, orc_sens *o)
+{
+    if (P->xs_kind != 0) return ORC_ERR_INVALID;
+    ctx C;
+    int st = setup(&C, P);
+    if (st) { teardown(&C); return st; }
+    C.seed = o->seed;
+    C.tag = o->tag;
+    C.max_events = o->max_events ? o->max_events : 10000000u;
+    C.recording = 1;
+    C.gw_mesh = o->g_mesh;
+    C.gw_scal = o->g_scal;
+    const int M = P->n_mat, G = C.G;
+    nsum *dst = calloc((size_t)M * G, sizeof(nsum)), *dss = calloc((size_t)M * G * G, sizeof(nsum));
+    nsum *dnf = calloc((size_t)M * G, sizeof(nsum)), val;
+    memset(&val, 0, sizeof(val));
+    for (uint64_t id = 0; id < o->n_hist && st == ORC_OK; ++id) {
+        particle p;
+        C.rec_n = 0;
+        st = source_particle(&C, &p, id, NULL, 0, 0, 0.0);
+        if (st) break;
+        while (p.alive) event(&C, &p);
+        nsum Fs;
+        memset(&Fs, 0, sizeof(Fs));
+        for (int k = 0; k < C.rec_n; ++k) nadd(&Fs, C.rec[k].f);
+        const double F = nval(&Fs);
+        nadd(&val, F);
+        double before = 0.0;
+        for (int k = 0; k < C.rec_n; ++k) {
+            const struct orc_rec *r = &C.rec[k];
+            const int mg = r->m * G + r->g;
+            const double inv_st = C.inv_sigt[mg];
+            const double after_flight = F - before;
+            /* flight decision */
+            const double sf = r->collided ? inv_st - r->len : -r->len;
+            nadd(&dst[mg], sf * after_flight);
+            /* pathwise terms of this segment */
+            if (o->g_scal) {
+                const double ga = o->g_scal[1] * r->len;
+                nadd(&dst[mg], ga);
+                for (int h = 0; h < G; ++h) nadd(&dss[(size_t)mg * G + h], -ga);
+                nadd(&dnf[mg], o->g_scal[2] * r->len);
+            }
+            before = before + r->f;
+            if (!r->collided) continue;
+            const double after = F - before;
+            if (r->react == 1) {
+                const double ss = P->sigs[(size_t)mg * G + r->h];
+                nadd(&dss[(size_t)mg * G + r->h], (1.0 / ss) * after);
+                nadd(&dst[mg], (-inv_st) * after);
+            } else if (r->react == 2) {
+                const double inv_sa = 1.0 / C.sig_a[mg];
+                nadd(&dst[mg], (inv_sa - inv_st) * after);
+                for (int h = 0; h < G; ++h) nadd(&dss[(size_t)mg * G + h], (-inv_sa) * after);
+            }
+        }
+    }
+    const double n = (double)o->n_hist;
+    for (int i = 0; i < M * G; ++i) {
+        if (o->d_sigt) o->d_sigt[i] = nval(&dst[i]) / n;
+        if (o->d_nusigf) o->d_nusigf[i] = nval(&dnf[i]) / n;
+    }
+    for (int i = 0; i < M * G * G; ++i)
+        if (o->d_sigs) o->d_sigs[i] = nval(&dss[i]) / n;
+    o->value = nval(&val) / n;
+    free(dst); free(dss); free(dnf);
     teardown(&C);
     return st;
 }

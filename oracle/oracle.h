@@ -97,7 +97,23 @@ typedef struct {
 /* status codes (same meaning as the library's, numbered independently) */
 enum { ORC_OK = 0, ORC_ERR_INVALID = 1, ORC_ERR_NOMEM = 2, ORC_ERR_CAPACITY = 3, ORC_ERR_STATE = 6 };
 
+/* Derivatives of L = sum_b g_b T_b (T = fixed-source tallies per source
+ * particle, g = upstream gradients) with respect to the multigroup data, by
+ * the score-function (likelihood-ratio) estimator in causal form plus the
+ * pathwise terms of the reaction-rate tallies.  Multigroup, fixed source. */
+typedef struct {
+    uint64_t n_hist, seed;
+    uint32_t tag, max_events;
+    const double *g_mesh;                /* mesh_size upstream gradients (NULL = 0) */
+    const double *g_scal;                /* 3: flux, absorption, production (NULL = 0) */
+    double *d_sigt;                      /* out [m][g] */
+    double *d_sigs;                      /* out [m][g][g'] */
+    double *d_nusigf;                    /* out [m][g] */
+    double value;                        /* out: L itself (mean per source particle) */
+} orc_sens;
+
 int orc_fixed_source(const orc_problem *P, orc_fixed *o);
+int orc_sensitivities(const orc_problem *P, orc_sens *o);
 int orc_power_iteration(const orc_problem *P, orc_eig *o);
 
 /* unit-level entry points used by the pin tests */
