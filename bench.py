@@ -289,6 +289,224 @@ def run_ours(args):
     return 0
 
 
+BATCH_WORKLOAD = ("256 independent multigroup voxel boxes (groups from {1,2,7,20,70}, 1-8 materials, "
+                  "up to 64^3 voxels, 1e3-1e6 histories log-uniform, 8^3-32^3 mesh) in one batched launch")
+
+
+def run_batched_workload(args):
+    """One step = one tr_run_batched over the 256-problem workload (autotuned,
+    graph-replayed after the first call).  Also times the same problems run
+    one after another through tr_run_fixed_source, for comparison."""
+    import numpy as np
+    import torch
+
+    ws, rank, local = _dist()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    from paper_2506_00263_gb300 import binding as tb
+    from paper_2506_00263_gb300 import build as tbuild
+    from paper_2506_00263_gb300 import inputs
+
+    if rank == 0 or not os.path.exists(tbuild.LIB):
+        tbuild.build()
+    if ws > 1:
+        torch.distributed.barrier()
+    decomp = tb.DECOMP_SPLIT if args.decomp == "split" else tb.DECOMP_MONO
+    specs, hist = inputs.batched_boxes(256, seed=7 + rank)
+    probs = [tb.Problem(s) for s in specs]
+    opts = tb.RunOpts(seed=1 + 1000 * rank, scheme=tb.SCHEME_ASYNC, decomposition=decomp,
+                      stash_slots=args.stash, blocks_per_sm=args.bps, remap_every=args.remap if args.bps else 0,
+                      queue_capacity=args.queue)
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float64, device="cuda")
+    t_first = time.perf_counter()
+    tb.run_batched(probs, hist, opts)            # autotuning + graph capture
+    t_first = time.perf_counter() - t_first
+    for _ in range(args.warmup):
+        tb.run_batched(probs, hist, opts)
+    torch.cuda.synchronize()
+    if ws > 1:
+        torch.distributed.barrier()
+    launches0 = tb.kernel_launch_count()
+    times, ev_tot, kern_s = [], 0, 0.0
+    sampler = ClockSampler(torch.cuda.current_device())
+    with sampler:
+        for k in range(args.steps):
+            flush.fill_(float(k))
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            st = tb.run_batched(probs, hist, opts)
+            e1.record(stream)
+            e1.synchronize()
+            times.append(e0.elapsed_time(e1) * 1e-3)
+            ev_tot += sum(int(s["events"]) for s in st)
+            kern_s += st[0]["transport_seconds"]
+    torch.cuda.synchronize()
+    launches = tb.kernel_launch_count() - launches0
+    t = sum(times)
+    hist_step = float(sum(hist))
+    if ws > 1:
+        from paper_2506_00263_gb300 import parallel
+        t, ev_all, hist_all = parallel.reduce_timing(t, float(ev_tot), hist_step * args.steps, device="cuda")
+    else:
+        ev_all, hist_all = float(ev_tot), hist_step * args.steps
+    used = st[0]["used"]
+    # the same problems, one tr_run_fixed_source after another (default tuning)
+    single_opts = lambda n, i: tb.RunOpts(n_histories=n, seed=1 + 1000 * rank, scheme=tb.SCHEME_ASYNC,
+                                          decomposition=decomp, problem_tag=i)
+    for i, (p, n) in enumerate(zip(probs, hist)):      # warm
+        p.run_fixed_source(single_opts(min(n, 1000), i))
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    ev_seq = 0
+    for i, (p, n) in enumerate(zip(probs, hist)):
+        ev_seq += int(p.run_fixed_source(single_opts(n, i))["events"])
+    e1.record(stream)
+    e1.synchronize()
+    t_seq = e0.elapsed_time(e1) * 1e-3
+    if rank != 0:
+        return 0
+    hbm, fmax, peak_kind = _peaks()
+    avg_launch = kern_s / args.steps
+    ev_launch = ev_tot / args.steps
+    ops = FP64_OPS_PER_EVENT.get(("batched", args.decomp))
+    fp64_peak = N_SM * FP64_OPS_PER_CLK_PER_SM * fmax * 1e6 / 1e12
+    hbm_ach = B_EVENT * ev_launch / avg_launch / 1e9
+    hbm_roof = {"bound": "hbm", "achieved": hbm_ach, "peak": hbm, "unit": "GB/s", "frac": hbm_ach / hbm,
+                "traffic": None, "what": f"{B_EVENT} algorithmic bytes/event, {peak_kind} peak"}
+    roof = hbm_roof
+    if ops:
+        ach = ops * ev_launch / avg_launch / 1e12
+        roof = {"bound": "alu", "achieved": ach, "peak": fp64_peak, "unit": "TFLOP/s", "frac": ach / fp64_peak,
+                "traffic": None, "what": f"FP64 pipe of the batched transport kernel, {ops:.0f} FP64 ops/event",
+                "peak_source": f"derived: {N_SM} SMs x {FP64_OPS_PER_CLK_PER_SM:g} FP64/clk x {fmax:.0f} MHz"}
+    line = {
+        "metric": "particle-events/s", "value": ev_all / t, "unit": "events/s", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": BATCH_WORKLOAD, "decomposition": args.decomp, "problems": len(probs),
+                   "histories_per_step": int(hist_step), "tuning_used": {"blocks_per_sm": used[0],
+                   "stash_slots": used[1], "remap_every": used[2]},
+                   "l2": "flushed between steps (512 MB write)"},
+        "histories_per_s": hist_all / t, "roofline": roof, "hbm_roofline": hbm_roof,
+        "e2e": None, "cpu_baseline": None, "gpu_launches": launches, "clocks": sampler.summary(),
+        "first_call_s": t_first,
+        "sequential_single_runs": {"value": ev_seq / t_seq, "unit": "events/s", "seconds": t_seq,
+                                   "speedup_of_batched": (ev_all / t) / (ev_seq / t_seq)},
+        "transport": {"kernel_seconds": kern_s, "launches": args.steps, "avg_launch_ms": 1e3 * avg_launch},
+    }
+    print(json.dumps(line), flush=True)
+    for p in probs:
+        p.close()
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+ADJ_WORKLOAD = ("differentiated 7-group lattice, fission off, uniform source in fuel pins, 1e6 histories: "
+                "forward fixed-source run + derivatives of the 51x51 mesh flux and absorption rate")
+
+
+def run_adjoint_workload(args):
+    """One step = forward fixed-source run + tr_sensitivities (d/dSigma_t,
+    d/dSigma_s, d/dnuSigma_f) of L = g . mesh + absorption rate."""
+    import numpy as np
+    import torch
+
+    ws, rank, local = _dist()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    from paper_2506_00263_gb300 import binding as tb
+    from paper_2506_00263_gb300 import build as tbuild
+    from paper_2506_00263_gb300 import inputs
+
+    if rank == 0 or not os.path.exists(tbuild.LIB):
+        tbuild.build()
+    if ws > 1:
+        torch.distributed.barrier()
+    decomp = tb.DECOMP_SPLIT if args.decomp == "split" else tb.DECOMP_MONO
+    spec = inputs.c5g7_lattice(fission=False)
+    n = 1_000_000
+    opts = tb.RunOpts(n_histories=n, seed=1 + 1000 * rank, scheme=tb.SCHEME_ASYNC, decomposition=decomp)
+    prob = tb.Problem(spec)
+    M, G = spec.n_materials, spec.n_groups
+    g_mesh = torch.tensor(np.random.default_rng(3).uniform(-1, 1, spec.mesh_size), dtype=torch.float64,
+                          device="cuda")
+    g_scal = torch.tensor([0.0, 1.0, 0.0], dtype=torch.float64, device="cuda")
+    d_st = torch.empty((M, G), dtype=torch.float64, device="cuda")
+    d_ss = torch.empty((M, G, G), dtype=torch.float64, device="cuda")
+    d_nf = torch.empty((M, G), dtype=torch.float64, device="cuda")
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float64, device="cuda")
+
+    def fwd():
+        return prob.run_fixed_source(opts)
+
+    def bwd():
+        prob.sensitivities(opts, g_mesh.data_ptr(), g_scal.data_ptr(), d_st.data_ptr(), d_ss.data_ptr(),
+                           d_nf.data_ptr())
+
+    for _ in range(args.warmup):
+        fwd()
+        bwd()
+    torch.cuda.synchronize()
+    if ws > 1:
+        torch.distributed.barrier()
+    launches0 = tb.kernel_launch_count()
+    t_f = t_b = 0.0
+    ev = 0
+    sampler = ClockSampler(torch.cuda.current_device())
+    with sampler:
+        for k in range(args.steps):
+            flush.fill_(float(k))
+            e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+            e[0].record(stream)
+            r = fwd()
+            e[1].record(stream)
+            bwd()
+            e[2].record(stream)
+            e[2].synchronize()
+            t_f += e[0].elapsed_time(e[1]) * 1e-3
+            t_b += e[1].elapsed_time(e[2]) * 1e-3
+            ev += int(r["events"])
+    launches = tb.kernel_launch_count() - launches0
+    t = t_f + t_b
+    if ws > 1:
+        from paper_2506_00263_gb300 import parallel
+        t, ev_all, _ = parallel.reduce_timing(t, float(ev), 0.0, device="cuda")
+    else:
+        ev_all = float(ev)
+    if rank != 0:
+        return 0
+    hbm, fmax, peak_kind = _peaks()
+    hbm_ach = B_EVENT * ev / t_f / 1e9
+    line = {
+        "metric": "particle-events/s", "value": ev_all / t, "unit": "events/s", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": ADJ_WORKLOAD, "decomposition": args.decomp,
+                   "l2": "flushed between steps (512 MB write)"},
+        "forward_ms": 1e3 * t_f / args.steps, "backward_ms": 1e3 * t_b / args.steps,
+        "backward_over_forward": t_b / t_f,
+        "roofline": {"bound": "hbm", "achieved": hbm_ach, "peak": hbm, "unit": "GB/s", "frac": hbm_ach / hbm,
+                     "traffic": None, "what": f"forward transport, {B_EVENT} algorithmic bytes/event, "
+                                              f"{peak_kind} peak"},
+        "e2e": None, "cpu_baseline": None, "gpu_launches": launches, "clocks": sampler.summary(),
+    }
+    print(json.dumps(line), flush=True)
+    prob.close()
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
 # FP64 thread-operations (dadd + dmul + dfma, divisions and square roots
 # included as executed) per transport event, from an ncu capture of the
 # transport kernel on the lattice workload.
@@ -331,11 +549,18 @@ def main():
     ap.add_argument("--bps", type=int, default=0, help="blocks per SM (0 = default)")
     ap.add_argument("--remap", type=int, default=1, help="monolithic: events between remaps")
     ap.add_argument("--queue", type=int, default=0, help="stack: particles per stack; async: spill links x 32")
+    ap.add_argument("--workload", choices=["lattice", "batched", "adjoint"], default="lattice",
+                    help="lattice: the k-eigenvalue lattice; batched: 256 box problems in one launch; "
+                         "adjoint: forward + derivative kernels on the fixed-source lattice")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "batched":
+        return run_batched_workload(args)
+    if args.workload == "adjoint":
+        return run_adjoint_workload(args)
     return run_ours(args)
 
 

@@ -152,6 +152,8 @@ typedef struct {
     int32_t spill_threshold;            /* async: spill a full link once a queue exceeds this (0 = default) */
     uint32_t problem_tag;               /* random stream tag (batched runs: problem index) */
     uint64_t first_history;             /* fixed source: run histories first .. first + n - 1 (a shard) */
+    uint32_t max_wait_ms;               /* async: wall-clock limit of one spin-wait (0 = 60000) */
+    uint32_t reserved;
 } tr_run_opts;
 
 typedef struct {
@@ -163,6 +165,10 @@ typedef struct {
     uint64_t spills, refills;           /* async: links moved to / from global memory */
     double seconds;                     /* device time of the whole run */
     double transport_seconds;           /* device time of the transport-loop kernels alone */
+    int32_t used_blocks_per_sm;         /* tr_run_batched: tuning the run used (autotuned where */
+    int32_t used_stash_slots;           /*   opts left it 0); 0 after single runs */
+    int32_t used_remap_every;
+    int32_t reserved;
 } tr_run_stats;
 
 /* Create a problem on the device.  Copies every array (the caller keeps
@@ -182,6 +188,30 @@ void tr_problem_destroy(tr_problem *problem);
  * `stats` (may be NULL).  TR_ERR_CAPACITY / TR_ERR_TIMEOUT leave the problem
  * usable with undefined tallies. */
 tr_status tr_run_fixed_source(tr_problem *problem, const tr_run_opts *opts, tr_run_stats *stats);
+
+/* Batched fixed-source run: n independent multigroup problems transported in
+ * one persistent launch of the asynchronous scheme (Sec. 3.2), the source
+ * cursor running over all problems' histories and each particle carrying its
+ * problem index, so that work from every problem fills the same warps.
+ * probs[0..n-1]: problems created on one device (probs[0], the leader, owns
+ * the launch's workspace and stream; a problem may appear in one batch only
+ * once).  n_histories[i] (< 2^32): histories of problem i.  opts: as for
+ * tr_run_fixed_source with scheme TR_SCHEME_ASYNC and first_history 0;
+ * problem i uses the random-stream tag problem_tag ^ i (problem_tag < 2^31),
+ * so each problem's tallies, counts and event log equal those of
+ * tr_run_fixed_source on that problem alone with that tag.  Fields
+ * blocks_per_sm, stash_slots and remap_every left at 0 are autotuned: the
+ * first call with a given batch times the candidate settings on 1/16 of each
+ * problem's histories and keeps the fastest for later calls.  The whole run
+ * (zeroing, transport, normalisation) is captured once as a CUDA graph and
+ * replayed while the batch, the options and the leader's buffers stay the
+ * same.  stats (may be NULL): n entries, per problem (spills, refills and
+ * times are the batch's).  Errors: TR_ERR_INVALID (NULL, n < 1, continuous
+ * energy, mixed devices, stack scheme, first_history != 0), TR_ERR_NOMEM,
+ * TR_ERR_CAPACITY, TR_ERR_TIMEOUT, TR_ERR_CUDA.  Synchronises the leader's
+ * stream (and each member's stream before the launch). */
+tr_status tr_run_batched(tr_problem *const *probs, int32_t n, const uint64_t *n_histories, const tr_run_opts *opts,
+                         tr_run_stats *stats);
 
 typedef struct {
     uint64_t n_per_batch;
@@ -211,6 +241,24 @@ typedef struct {
  * the standard deviation of that mean.  Multigroup only (TR_ERR_INVALID
  * otherwise).  The event log holds the last batch. */
 tr_status tr_run_power_iteration(tr_problem *problem, const tr_eig_opts *opts, tr_eig_result *out);
+
+/* Derivatives of L = sum_b g_b T_b with respect to the multigroup cross
+ * sections, where T are the fixed-source tallies of the preceding
+ * tr_run_fixed_source (same opts: histories, seed, tag, first history and
+ * event cap, else TR_ERR_STATE) and g the upstream gradients.  The estimator
+ * is the score-function (likelihood-ratio) sum in causal form over the
+ * random decisions of each history (flight lengths, reaction outcomes) plus
+ * the explicit dependence of the absorption and production tallies; the
+ * histories are recomputed from their random-number keys, never stored.
+ * Inputs (device memory): d_grad_mesh [mesh size] (NULL = 0) and
+ * d_grad_scalars [3] = gradients of (flux, absorption rate, production rate)
+ * (NULL = 0).  Outputs (device memory, overwritten): d_sigt [m][g],
+ * d_sigs [m][g][g'] and d_nusigf [m][g], means per source particle.
+ * Derivatives with respect to a zero scattering cross section are not
+ * estimated (the transfer never occurs).  Multigroup only (TR_ERR_INVALID
+ * otherwise).  Synchronises the problem's stream. */
+tr_status tr_sensitivities(tr_problem *problem, const tr_run_opts *opts, const double *d_grad_mesh,
+                           const double *d_grad_scalars, double *d_sigt, double *d_sigs, double *d_nusigf);
 
 /* Tally ids for tr_tallies / tr_tally_stddev. */
 enum { TR_TALLY_MESH = 0, TR_TALLY_ENERGY = 1, TR_TALLY_SCALARS = 2 };

@@ -17,7 +17,8 @@ import numpy as np
 from . import inputs as _inp
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "libtr.so")
+# TR_LIBRARY selects another build of the same library (e.g. a tuning variant)
+LIB_PATH = os.environ.get("TR_LIBRARY") or os.path.join(_HERE, "libtr.so")
 
 TR_OK, TR_ERR_INVALID, TR_ERR_NOMEM, TR_ERR_CAPACITY, TR_ERR_TIMEOUT, TR_ERR_CUDA, TR_ERR_STATE = range(7)
 STATUS_NAMES = {0: "TR_OK", 1: "TR_ERR_INVALID", 2: "TR_ERR_NOMEM", 3: "TR_ERR_CAPACITY", 4: "TR_ERR_TIMEOUT",
@@ -71,13 +72,16 @@ class RunOptsC(C.Structure):
                 ("decomposition", C.c_int32), ("queue_capacity", C.c_uint64), ("blocks_per_sm", C.c_int32),
                 ("remap_every", C.c_int32), ("stash_slots", C.c_int32), ("max_spin", C.c_int64),
                 ("max_events", C.c_uint32), ("want_event_log", C.c_int32), ("spill_threshold", C.c_int32),
-                ("problem_tag", C.c_uint32), ("first_history", C.c_uint64)]
+                ("problem_tag", C.c_uint32), ("first_history", C.c_uint64), ("max_wait_ms", C.c_uint32),
+                ("reserved", C.c_uint32)]
 
 
 class RunStats(C.Structure):
     _fields_ = [("histories", C.c_uint64), ("events", C.c_uint64), ("events_by_type", C.c_uint64 * 8),
                 ("final_by_type", C.c_uint64 * 8), ("launches", C.c_uint64), ("spills", C.c_uint64),
-                ("refills", C.c_uint64), ("seconds", C.c_double), ("transport_seconds", C.c_double)]
+                ("refills", C.c_uint64), ("seconds", C.c_double), ("transport_seconds", C.c_double),
+                ("used_blocks_per_sm", C.c_int32), ("used_stash_slots", C.c_int32),
+                ("used_remap_every", C.c_int32), ("reserved", C.c_int32)]
 
 
 class EigOptsC(C.Structure):
@@ -121,8 +125,13 @@ def lib():
     L.tr_event_log.restype = C.c_int
     L.tr_last_error.restype = C.c_char_p
     L.tr_kernel_launch_count.restype = C.c_uint64
+    L.tr_sensitivities.argtypes = [C.c_void_p, C.POINTER(RunOptsC), _dp, _dp, _dp, _dp, _dp]
+    L.tr_sensitivities.restype = C.c_int
     L.tr_run_fixed_source_noalloc.argtypes = [C.c_void_p, C.POINTER(RunOptsC), _dp, _dp, _dp, C.POINTER(RunStats)]
     L.tr_run_fixed_source_noalloc.restype = C.c_int
+    L.tr_run_batched.argtypes = [C.POINTER(C.c_void_p), C.c_int32, C.POINTER(C.c_uint64), C.POINTER(RunOptsC),
+                                 C.POINTER(RunStats)]
+    L.tr_run_batched.restype = C.c_int
     L.tr_version.restype = C.c_char_p
     _lib = L
     return L
@@ -155,6 +164,8 @@ class RunOpts:
     spill_threshold: int = 0
     problem_tag: int = 0
     first_history: int = 0
+    max_wait_ms: int = 0
+    reserved: int = 0
 
     def to_c(self) -> RunOptsC:
         c = RunOptsC()
@@ -318,6 +329,16 @@ class Problem:
                                                  ptr(scalars_ptr), C.byref(st)))
         return stats_dict(st)
 
+    def sensitivities(self, opts: RunOpts, g_mesh_ptr: int, g_scal_ptr: int, d_sigt_ptr: int, d_sigs_ptr: int,
+                      d_nusigf_ptr: int) -> None:
+        """tr_sensitivities with device pointers (0 for an absent upstream gradient)."""
+        def ptr(v):
+            return C.cast(C.c_void_p(int(v)), _dp) if v else None
+
+        c = opts.to_c()
+        _check(lib().tr_sensitivities(self._h, C.byref(c), ptr(g_mesh_ptr), ptr(g_scal_ptr), ptr(d_sigt_ptr),
+                                      ptr(d_sigs_ptr), ptr(d_nusigf_ptr)))
+
     def power_iteration(self, n_per_batch, n_inactive, n_active, opts: RunOpts, k0=1.0,
                         bank_capacity_factor=0.0) -> dict:
         eo = EigOptsC()
@@ -359,7 +380,24 @@ def stats_dict(st: RunStats) -> dict:
             "events_by_type": np.array(st.events_by_type[:], np.uint64),
             "final_by_type": np.array(st.final_by_type[:], np.uint64), "launches": st.launches,
             "spills": st.spills, "refills": st.refills, "seconds": st.seconds,
-            "transport_seconds": st.transport_seconds}
+            "transport_seconds": st.transport_seconds,
+            "used": (st.used_blocks_per_sm, st.used_stash_slots, st.used_remap_every)}
+
+
+def run_batched(problems, n_histories, opts: RunOpts) -> list:
+    """tr_run_batched: transport several problems in one persistent launch;
+    problem i uses the random-stream tag opts.problem_tag ^ i.  Returns the
+    per-problem statistics; each problem's tallies are read as after a single
+    run."""
+    n = len(problems)
+    if n != len(n_histories):
+        raise ValueError("one history count per problem")
+    hs = (C.c_void_p * n)(*[p._h for p in problems])
+    nh = (C.c_uint64 * n)(*[int(v) for v in n_histories])
+    st = (RunStats * n)()
+    c = opts.to_c()
+    _check(lib().tr_run_batched(hs, n, nh, C.byref(c), st))
+    return [stats_dict(st[i]) for i in range(n)]
 
 
 def kernel_launch_count() -> int:

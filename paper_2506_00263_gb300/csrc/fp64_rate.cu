@@ -54,6 +54,21 @@ __global__ void kh(unsigned* out, unsigned a0, unsigned b) {
   unsigned s = 0; for (int j = 0; j < 8; ++j) s ^= x[j];
   out[blockIdx.x * blockDim.x + threadIdx.x] = s;
 }
+// DFMA chains executed by only the first K lanes of every warp: if the time
+// does not fall with K, an FP64 warp instruction costs the same pipe time
+// however many lanes are active.
+__global__ void kpart(double* out, double a0, double b, int K) {
+  double x[8]; for (int j = 0; j < 8; ++j) x[j] = a0 + j * 1e-3 + threadIdx.x * 1e-9;
+  if ((int)(threadIdx.x & 31) < K) {
+    #pragma unroll 4
+    for (int i = 0; i < ITERS; ++i) {
+      #pragma unroll
+      for (int j = 0; j < 8; ++j) x[j] = __fma_rn(x[j], b, b);
+    }
+  }
+  double s = 0; for (int j = 0; j < 8; ++j) s += x[j];
+  out[blockIdx.x * blockDim.x + threadIdx.x] = s;
+}
 int main() {
   int dev = 0; cudaDeviceProp p; cudaGetDeviceProperties(&p, dev);
   int sms = p.multiProcessorCount; int clk = 0; cudaDeviceGetAttribute(&clk, cudaDevAttrClockRate, dev);
@@ -90,6 +105,16 @@ int main() {
     cudaEventRecord(e0); kh<<<blocks, threads>>>((unsigned*)d, 1u, 2654435761u); cudaEventRecord(e1); cudaEventSynchronize(e1);
     float ms; cudaEventElapsedTime(&ms, e0, e1); double ops = (double)n * ITERS * 64;
     if (rep) printf("umulhi+xor: %.3f ms, %.3e pairs/s, %.3f pairs/clk/SM\n", ms, ops / (ms * 1e-3), ops / (ms * 1e-3) / sms / (clk * 1e3));
+  }
+  for (int K : {32, 16, 8, 1}) {
+    float ms = 0;
+    for (int rep = 0; rep < 2; ++rep) {
+      cudaEventRecord(e0); kpart<<<blocks, threads>>>(d, 1.0, 0.5, K); cudaEventRecord(e1); cudaEventSynchronize(e1);
+      cudaEventElapsedTime(&ms, e0, e1);
+    }
+    double winst = (double)n / 32 * ITERS * 8;
+    printf("dfma with %2d active lanes/warp: %.3f ms, %.3e warp-inst/s, %.3f warp-inst/clk/SM\n", K, ms,
+           winst / (ms * 1e-3), winst / (ms * 1e-3) / sms / (clk * 1e3));
   }
   cudaError_t err = cudaGetLastError(); printf("err=%s\n", cudaGetErrorString(err));
   cudaFree(d); return err == cudaSuccess ? 0 : 1;

@@ -36,7 +36,7 @@ constexpr int N_GQ = 32;
 struct Stash {
     double *x, *y, *z, *u, *v, *w, *iu, *iv, *iw, *ia, *E;
     int* g;
-    unsigned *cell, *id, *n, *nsites, *pend;
+    unsigned *cell, *id, *n, *nsites, *pend, *prob;
     unsigned short* q[N_QUEUES];       // slot-index queues per event type
     unsigned short* fr;                // free-slot stack
     int* cnt;                          // [0..2] queue counts, [3] free count, [4] lock, [5] block error
@@ -44,7 +44,7 @@ struct Stash {
 
 __host__ __device__ __forceinline__ size_t stash_bytes(int S)
 {
-    return (size_t)S * (11 * sizeof(double) + sizeof(int) + 5 * sizeof(unsigned)) +
+    return (size_t)S * (11 * sizeof(double) + sizeof(int) + 6 * sizeof(unsigned)) +
            (size_t)S * (N_QUEUES + 1) * sizeof(unsigned short) + 16 * sizeof(int);
 }
 
@@ -59,6 +59,7 @@ __device__ __forceinline__ Stash carve(unsigned char* base, int S)
     unsigned* u = reinterpret_cast<unsigned*>(d);
     s.g = reinterpret_cast<int*>(u); u += S;
     s.cell = u; u += S; s.id = u; u += S; s.n = u; u += S; s.nsites = u; u += S; s.pend = u; u += S;
+    s.prob = u; u += S;
     unsigned short* h = reinterpret_cast<unsigned short*>(u);
     for (int q = 0; q < N_QUEUES; ++q) {
         s.q[q] = h;
@@ -79,6 +80,7 @@ __device__ __forceinline__ void slot_load(const Stash& s, int i, Particle& p)
     p.iu = s.iu[i]; p.iv = s.iv[i]; p.iw = s.iw[i]; p.ia = s.ia[i];
     p.E = s.E[i]; p.g = s.g[i];
     p.cell = s.cell[i]; p.id = s.id[i]; p.n = s.n[i]; p.nsites = s.nsites[i]; p.pend = s.pend[i];
+    p.prob = s.prob[i];
 }
 
 __device__ __forceinline__ void slot_store(const Stash& s, int i, const Particle& p)
@@ -88,6 +90,7 @@ __device__ __forceinline__ void slot_store(const Stash& s, int i, const Particle
     s.iu[i] = p.iu; s.iv[i] = p.iv; s.iw[i] = p.iw; s.ia[i] = p.ia;
     s.E[i] = p.E; s.g[i] = p.g;
     s.cell[i] = p.cell; s.id[i] = p.id; s.n[i] = p.n; s.nsites[i] = p.nsites; s.pend[i] = p.pend;
+    s.prob[i] = p.prob;
 }
 
 // Particle state of a global link, read through L2 (ld.global.cg): the link
@@ -100,7 +103,7 @@ __device__ __forceinline__ void load_particle_l2(const SoA& s, unsigned long lon
     p.iu = __ldcg(s.iu + i); p.iv = __ldcg(s.iv + i); p.iw = __ldcg(s.iw + i); p.ia = __ldcg(s.ia + i);
     p.E = __ldcg(s.E + i); p.g = __ldcg(s.g + i);
     p.cell = __ldcg(s.cell + i); p.id = __ldcg(s.id + i); p.n = __ldcg(s.n + i);
-    p.nsites = __ldcg(s.nsites + i); p.pend = __ldcg(s.pend + i);
+    p.nsites = __ldcg(s.nsites + i); p.pend = __ldcg(s.pend + i); p.prob = __ldcg(s.prob + i);
 }
 
 __device__ __forceinline__ void fail(ErrorWord* err, int code, int where)
@@ -114,8 +117,10 @@ __device__ __forceinline__ bool lock_stash(const Stash& s, const RunParams& R, E
     bool ok = true;
     if ((threadIdx.x & 31) == 0) {
         unsigned long long spins = 0;
+        uint64_t t0 = 0;
         while (atomicCAS(s.cnt + 4, 0, 1) != 0) {
-            if (++spins > R.max_spin) {
+            if (spins == 0) t0 = now_ns();
+            if (++spins > R.max_spin || now_ns() - t0 > R.max_wait_ns) {
                 fail(err, ERR_TIMEOUT, 1);
                 ok = false;
                 break;
@@ -154,6 +159,7 @@ __device__ bool list_deposit(unsigned long long* slot, unsigned long long L, uns
                              const RunParams& R, ErrorWord* err)
 {
     unsigned long long spins = 0;
+    const uint64_t t0 = now_ns();
     for (;;) {
         __threadfence();
         const unsigned long long cur = atomicExch(slot, EMPTY_LIST);   // claim whatever is there
@@ -169,7 +175,7 @@ __device__ bool list_deposit(unsigned long long* slot, unsigned long long L, uns
         const unsigned long long old = atomicExch(slot, L);
         if (old == EMPTY_LIST) return true;
         L = old;                                                        // deposited meanwhile: merge again
-        if (++spins > R.max_spin) {
+        if (++spins > R.max_spin || now_ns() - t0 > R.max_wait_ns) {
             fail(err, ERR_TIMEOUT, 2);
             return false;
         }
@@ -218,8 +224,39 @@ __device__ __forceinline__ unsigned new_link(const AsyncArgs& A, int start, cons
 // ---------------------------------------------------------------------------
 // The persistent kernel
 // ---------------------------------------------------------------------------
-template <bool CE, bool SPLIT>
-__global__ void __launch_bounds__(256, 2) k_async(DevProblem P, RunParams R, AsyncArgs A, Tallies T, ErrorWord* err)
+#ifndef TR_ASYNC_MIN_BLOCKS
+#define TR_ASYNC_MIN_BLOCKS 2   // resident blocks per SM the register allocation must allow
+#endif
+
+// Batched launches: problem p owns source indices [hist_off[p], hist_off[p+1]).
+__device__ __forceinline__ int find_problem(const unsigned long long* off, int n, unsigned long long gid)
+{
+    int lo = 0, hi = n;   // off[lo] <= gid < off[hi]
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (__ldg(off + mid) <= gid) lo = mid; else hi = mid;
+    }
+    return lo;
+}
+
+// Batched launches: add a lane's event counts and scalar scores to its own
+// problem's tallies after every event (lanes of one warp belong to different
+// problems, so nothing is kept across particles).
+__device__ __forceinline__ void flush_lane(Acc& acc, const Tallies& T)
+{
+    if (acc.flux != 0.0) atomicAdd(T.scal + 0, acc.flux);
+    if (acc.absn != 0.0) atomicAdd(T.scal + 1, acc.absn);
+    if (acc.prod != 0.0) atomicAdd(T.scal + 2, acc.prod);
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        if (acc.ev[i]) atomicAdd(T.ev_type + i, (unsigned long long)acc.ev[i]);
+        if (acc.fin[i]) atomicAdd(T.fin_type + i, (unsigned long long)acc.fin[i]);
+    }
+    acc.zero();
+}
+
+template <bool CE, bool SPLIT, bool BATCHED = false>
+__global__ void __launch_bounds__(256, TR_ASYNC_MIN_BLOCKS) k_async(DevProblem P, RunParams R, AsyncArgs A, Tallies T, ErrorWord* err)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     const int S = A.stash_slots;
@@ -238,6 +275,7 @@ __global__ void __launch_bounds__(256, 2) k_async(DevProblem P, RunParams R, Asy
     Acc acc;
     acc.zero();
     unsigned long long idle_spins = 0;
+    uint64_t idle_t0 = 0;    // when this warp last started waiting for work
     bool idle = false;
     bool spill_ok = true;   // cleared once the link arena is exhausted
     const int qstart = (int)(blockIdx.x * 7 + (threadIdx.x >> 5)) & (N_GQ - 1);
@@ -306,6 +344,7 @@ __global__ void __launch_bounds__(256, 2) k_async(DevProblem P, RunParams R, Asy
             // ---------------- starving: steal, or wait for termination ----------------
             if (!idle) {
                 idle = true;
+                idle_t0 = now_ns();
                 if (lane == 0) atomicAdd(&ctl->hungry, 1u);
             }
             unsigned link = NIL;
@@ -337,9 +376,11 @@ __global__ void __launch_bounds__(256, 2) k_async(DevProblem P, RunParams R, Asy
                 if (lane < fill) {
                     Particle p;
                     load_particle_l2(A.links, (unsigned long long)link * 32 + lane, p);
-                    bad = p.id >= R.n_hist || cell_i(p.cell) >= P.nx || cell_j(p.cell) >= P.ny ||
-                          cell_k(p.cell) >= P.nz || sl < 0 || sl >= S || (!CE && (p.g < 0 || p.g >= P.G));
-                    if (!bad && cell_in(p.cell)) bad = info_pin(cell_info(P, p.cell)) < 0;
+                    bad = BATCHED && p.prob >= (unsigned)A.n_probs;
+                    const DevProblem& PP = (BATCHED && !bad) ? A.probs[p.prob] : P;
+                    bad = bad || p.id >= R.n_hist || cell_i(p.cell) >= PP.nx || cell_j(p.cell) >= PP.ny ||
+                          cell_k(p.cell) >= PP.nz || sl < 0 || sl >= S || (!CE && (p.g < 0 || p.g >= PP.G));
+                    if (!bad && cell_in(p.cell)) bad = info_pin(cell_info(PP, p.cell)) < 0;
                     if (!bad) slot_store(st, sl, p);
                 }
                 if (__any_sync(FULLM, bad)) {
@@ -352,6 +393,8 @@ __global__ void __launch_bounds__(256, 2) k_async(DevProblem P, RunParams R, Asy
                     list_deposit(ctl->free_q + qstart, make_list(link, link), A.link_next, A.n_links, R, err);
                     atomicAdd(&ctl->refills, 1ull);
                 }
+                idle_t0 = now_ns();   // a refill is progress: restart the wait bound
+                idle_spins = 0;
                 ok = lock_stash(st, R, err);
                 if (!ok) break;
                 const int c = *(volatile int*)(st.cnt + type);
@@ -362,7 +405,11 @@ __global__ void __launch_bounds__(256, 2) k_async(DevProblem P, RunParams R, Asy
                 continue;
             }
             if (!src_left && g_live == 0ull) break;
-            if (++idle_spins > R.max_spin) {
+            // bounded in iterations and in time; the warp-uniform decision
+            // comes from lane 0's clock
+            bool give_up = ++idle_spins > R.max_spin;
+            if (lane == 0) give_up = give_up || now_ns() - idle_t0 > R.max_wait_ns;
+            if (__shfl_sync(FULLM, give_up, 0)) {
                 if (lane == 0) fail(err, ERR_TIMEOUT, 4);
                 break;
             }
@@ -412,6 +459,16 @@ __global__ void __launch_bounds__(256, 2) k_async(DevProblem P, RunParams R, Asy
             continue;
         }
 
+#ifdef TR_PROFILE_LANES
+        {   // exact warp fill per iteration: sites 12 + queue (mode 0) and 15 (make_work)
+            const unsigned hm = __ballot_sync(FULLM, slot >= 0);
+            if (lane == 0 && hm) {
+                const int site = mode == 1 ? 15 : 12 + q;
+                atomicAdd(&g_lane_prof[2 * site], 1ull);
+                atomicAdd(&g_lane_prof[2 * site + 1], (unsigned long long)__popc(hm));
+            }
+        }
+#endif
         // ---------------- run one event (or make_work) ----------------
         Particle p;
         bool live = false;
@@ -421,36 +478,56 @@ __global__ void __launch_bounds__(256, 2) k_async(DevProblem P, RunParams R, Asy
             if (lane == 0) first = atomicAdd(&ctl->src_cursor, 32ull);
             first = __shfl_sync(FULLM, first, 0);
             const unsigned long long id = first + lane;
+            __syncwarp();   // reconverge: the event below must run once for all lanes, not per lane group
             if (id < R.n_hist) {
                 TR_LANES(11);
-                live = source_particle<CE>(P, R, (unsigned)id, p, A.use_src ? &A.src : nullptr, id);
+                if (BATCHED) {
+                    const int pi = find_problem(A.hist_off, A.n_probs, id);
+                    RunParams RR = R;
+                    RR.key1 = R.key1 ^ (uint32_t)pi;
+                    const unsigned lid = (unsigned)(id - __ldg(A.hist_off + pi));
+                    live = source_particle<CE>(A.probs[pi], RR, lid, p, nullptr, 0);
+                    p.prob = (unsigned)pi;
+                    acc.ev[EV_SOURCE] += 1u;
+                    flush_lane(acc, A.tallies[pi]);
+                } else {
+                    live = source_particle<CE>(P, R, (unsigned)id, p, A.use_src ? &A.src : nullptr, id);
+                    acc.ev[EV_SOURCE] += 1u;
+                }
                 if (!live) fail(err, ERR_INVALID, 5);
-                acc.ev[EV_SOURCE] += 1u;
                 next = Q_STEP;
             }
             const unsigned made = __popc(__ballot_sync(FULLM, live));
             if (lane == 0 && made) atomicAdd(&ctl->live, (unsigned long long)made);
         } else {
             // mode 0 (warp-uniform): lanes beyond a partial link hold no slot and stay idle
+            if (slot >= 0) slot_load(st, slot, p);
+            __syncwarp();   // reconverge: the event below must run once for all lanes, not per lane group
             if (slot >= 0) {
                 TR_LANES(0);
-                slot_load(st, slot, p);
                 live = true;
+                // batched: the particle's own problem, random-stream tag and tallies
+                const DevProblem& PP = BATCHED ? A.probs[p.prob] : P;
+                const Tallies& TT = BATCHED ? A.tallies[p.prob] : T;
+                RunParams RR = R;
+                if (BATCHED) RR.key1 = R.key1 ^ p.prob;
                 if (!SPLIT) {
-                    for (int r = 0; r < R.remap_every && live; ++r) live = mono_event<CE>(P, R, p, T, acc, A.bank, err);
+                    for (int r = 0; r < R.remap_every && live; ++r) live = mono_event<CE>(PP, RR, p, TT, acc, A.bank, err);
                     next = live ? Q_STEP : Q_DEAD;
                 } else if (q == Q_STEP) {
                     XS X;
                     double xr;
-                    step_event<CE>(P, R, p, T, acc, X, xr);
+                    FwdSink sink{TT, acc};
+                    step_event<CE>(PP, RR, p, sink, X, xr);
                     next = next_queue_after_step(p);
                 } else if (q == Q_COLLIDE) {
-                    live = split_collide<CE>(P, R, p, T, acc, A.bank, err);
+                    live = split_collide<CE>(PP, RR, p, TT, acc, A.bank, err);
                     next = live ? Q_STEP : Q_DEAD;
                 } else {
-                    live = split_surface(P, R, p, T, acc, A.bank);
+                    live = split_surface(PP, RR, p, TT, acc, A.bank);
                     next = live ? Q_STEP : Q_DEAD;
                 }
+                if (BATCHED) flush_lane(acc, TT);
                 if (!live) next = Q_DEAD;
             }
             const unsigned died = __popc(__ballot_sync(FULLM, slot >= 0 && !live));
@@ -479,7 +556,7 @@ __global__ void __launch_bounds__(256, 2) k_async(DevProblem P, RunParams R, Asy
         unlock_stash(st);
     }
     if (idle && lane == 0) atomicSub(&ctl->hungry, 1u);
-    flush_acc(acc, T);
+    if (!BATCHED) flush_acc(acc, T);
 }
 
 }  // namespace tr
@@ -543,3 +620,45 @@ extern "C" int tr_profile_lanes_read(unsigned long long* out, int n)
     return cudaMemcpyToSymbol(tr::g_lane_prof, z, sizeof(z)) != cudaSuccess;
 }
 #endif
+
+namespace tr {
+
+int async_batched_max_blocks_per_sm(int split, int stash_slots)
+{
+    const size_t smem = stash_bytes(stash_slots);
+    int nb = 0;
+    if (split) {
+        if (cudaFuncSetAttribute(k_async<false, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+            cudaSuccess)
+            return 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_async<false, true, true>, 256, smem);
+    } else {
+        if (cudaFuncSetAttribute(k_async<false, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+            cudaSuccess)
+            return 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_async<false, false, true>, 256, smem);
+    }
+    return nb;
+}
+
+cudaError_t launch_async_batched(const DevProblem& P0, const RunParams& R, const AsyncArgs& A, ErrorWord* err,
+                                 int blocks, cudaStream_t st)
+{
+    const size_t smem = stash_bytes(A.stash_slots);
+    const Tallies T{};
+    count_launches(1);
+    if (A.split) {
+        cudaError_t e = cudaFuncSetAttribute(k_async<false, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem);
+        if (e != cudaSuccess) return e;
+        k_async<false, true, true><<<blocks, 256, smem, st>>>(P0, R, A, T, err);
+    } else {
+        cudaError_t e = cudaFuncSetAttribute(k_async<false, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem);
+        if (e != cudaSuccess) return e;
+        k_async<false, false, true><<<blocks, 256, smem, st>>>(P0, R, A, T, err);
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace tr

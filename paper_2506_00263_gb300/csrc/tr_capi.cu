@@ -4,7 +4,9 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <chrono>
 #include <map>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -53,6 +55,12 @@ struct tr_problem {
     size_t log_cap = 0, log_count = 0;
     bool have_run = false;
     bool have_std = false;
+    bool have_fixed = false;                  // last completed run was fixed source (for sensitivities)
+    tr_run_opts last_fixed{};
+    // batched launches led by this problem: the captured CUDA graph and its key
+    cudaGraphExec_t batch_graph = nullptr;
+    std::vector<unsigned long long> batch_key;
+    unsigned long long batch_graph_launches = 0;
 };
 
 // ---------------------------------------------------------------------------
@@ -229,6 +237,7 @@ extern "C" tr_status tr_problem_create(const tr_geometry_desc* G, const tr_xs_de
         P.cum_s = upload(pr, cs.data(), MG * Gn, &ok);
         P.cum_chi = upload(pr, cc.data(), MG, &ok);
         P.chi = upload(pr, X->chi, MG, &ok);
+        P.sigs = upload(pr, X->sigma_s, MG * Gn, &ok);
     } else {
         const int Nn = X->n_nuclides;
         if (Nn < 1 || Nn > 16 || !X->nuc_offset || !X->nuc_energy || !X->nuc_sigma || !X->nuc_awr || !X->density)
@@ -398,6 +407,7 @@ extern "C" void tr_problem_destroy(tr_problem* pr)
 {
     if (!pr) return;
     cudaStreamSynchronize(pr->stream);
+    if (pr->batch_graph) cudaGraphExecDestroy(pr->batch_graph);
     for (auto& kv : pr->ws) dev_free(pr, kv.second.p);
     for (void* p : pr->owned) dev_free(pr, p);
     if (pr->log_n) dev_free(pr, pr->log_n);
@@ -414,7 +424,7 @@ extern "C" void tr_problem_destroy(tr_problem* pr)
 static bool carve_soa(tr_problem* pr, const char* name, unsigned long long cap, SoA& s)
 {
     const size_t n = (size_t)cap;
-    const size_t bytes = n * (11 * 8 + 6 * 4) + 17 * 256;
+    const size_t bytes = n * (11 * 8 + 7 * 4) + 18 * 256;
     unsigned char* b = (unsigned char*)workspace(pr, name, bytes);
     if (!b) return false;
     auto take = [&](size_t sz) {
@@ -428,7 +438,7 @@ static bool carve_soa(tr_problem* pr, const char* name, unsigned long long cap, 
     s.E = (double*)take(8);
     s.g = (int*)take(4);
     s.cell = (unsigned*)take(4); s.id = (unsigned*)take(4); s.n = (unsigned*)take(4);
-    s.nsites = (unsigned*)take(4); s.pend = (unsigned*)take(4);
+    s.nsites = (unsigned*)take(4); s.pend = (unsigned*)take(4); s.prob = (unsigned*)take(4);
     return true;
 }
 
@@ -459,7 +469,7 @@ static tr_status check_err(tr_problem* pr)
     TR_CUDA(cudaStreamSynchronize(pr->stream));
     if (h.code == ERR_CAPACITY) return set_err(TR_ERR_CAPACITY, "a queue, link arena or fission bank overflowed");
     if (h.code == ERR_TIMEOUT)
-        return set_err(TR_ERR_TIMEOUT, "a device spin-wait exceeded max_spin (site " + std::to_string(h.where) + ")");
+        return set_err(TR_ERR_TIMEOUT, "a device spin-wait exceeded max_spin or max_wait_ms (site " + std::to_string(h.where) + ")");
     if (h.code != 0) return set_err(TR_ERR_INVALID, "device reported invalid state (code " + std::to_string(h.code) + ")");
     return TR_OK;
 }
@@ -635,6 +645,11 @@ static tr_status transport(tr_problem* pr, const tr_run_opts* o, RunParams R, co
     TR_CUDA(cudaStreamSynchronize(st));
     out.kernel_ms += lt.elapsed();
     tr_status es = check_err(pr);
+    if (es == TR_ERR_TIMEOUT)
+        return set_err(es, g_err + "; live " + std::to_string(hc.live) + ", source cursor " +
+                               std::to_string(hc.src_cursor) + " of " + std::to_string(R.n_hist) + ", spills " +
+                               std::to_string(hc.spills) + ", refills " + std::to_string(hc.refills) + ", hungry warps " +
+                               std::to_string(hc.hungry));
     if (es != TR_OK) return es;
     out.spills += hc.spills;
     out.refills += hc.refills;
@@ -655,6 +670,7 @@ static RunParams base_params(const tr_run_opts* o, unsigned long long n)
     R.want_log = o->want_event_log ? 1 : 0;
     R.remap_every = o->remap_every > 0 ? o->remap_every : 1;
     R.max_spin = o->max_spin > 0 ? (uint64_t)o->max_spin : (1ull << 24);
+    R.max_wait_ns = (uint64_t)(o->max_wait_ms ? o->max_wait_ms : 60000u) * 1000000ull;
     R.spill_threshold = o->spill_threshold ? o->spill_threshold : 64;
     R.id_base = (uint32_t)o->first_history;
     return R;
@@ -702,6 +718,8 @@ extern "C" tr_status tr_run_fixed_source(tr_problem* pr, const tr_run_opts* o, t
     TR_CUDA(cudaStreamSynchronize(st));
     pr->have_run = true;
     pr->have_std = false;
+    pr->have_fixed = true;
+    pr->last_fixed = *o;
     pr->log_count = R.want_log ? o->n_histories : 0;
     if (stats) {
         std::memset(stats, 0, sizeof(*stats));
@@ -862,6 +880,351 @@ extern "C" tr_status tr_run_power_iteration(tr_problem* pr, const tr_eig_opts* e
     res->transport_launches = tlaunch;
     pr->have_run = true;
     pr->have_std = true;
+    pr->have_fixed = false;
+    return TR_OK;
+}
+
+// ---------------------------------------------------------------------------
+// sensitivities
+// ---------------------------------------------------------------------------
+extern "C" tr_status tr_sensitivities(tr_problem* pr, const tr_run_opts* o, const double* d_grad_mesh,
+                                      const double* d_grad_scalars, double* d_sigt, double* d_sigs, double* d_nusigf)
+{
+    if (!pr || !o || !d_sigt || !d_sigs || !d_nusigf) return set_err(TR_ERR_INVALID, "NULL argument");
+    if (pr->dp.kind != TR_XS_MG) return set_err(TR_ERR_INVALID, "sensitivities need multigroup data");
+    tr_status s = validate_opts(o);
+    if (s != TR_OK) return s;
+    const tr_run_opts& L = pr->last_fixed;
+    if (!pr->have_fixed || L.n_histories != o->n_histories || L.seed != o->seed || L.problem_tag != o->problem_tag ||
+        L.max_events != o->max_events || L.first_history != o->first_history)
+        return set_err(TR_ERR_STATE, "tr_sensitivities needs a prior tr_run_fixed_source with the same histories");
+    const DevProblem& P = pr->dp;
+    const cudaStream_t st = pr->stream;
+    const size_t MG = (size_t)P.n_mat * P.G;
+    TR_CUDA(cudaMemsetAsync(d_sigt, 0, MG * 8, st));
+    TR_CUDA(cudaMemsetAsync(d_sigs, 0, MG * P.G * 8, st));
+    TR_CUDA(cudaMemsetAsync(d_nusigf, 0, MG * 8, st));
+    if (o->n_histories == 0) {
+        TR_CUDA(cudaStreamSynchronize(st));
+        return TR_OK;
+    }
+    double* F = (double*)workspace(pr, "adjoint_F", o->n_histories * 8);
+    if (!F) return set_err(TR_ERR_NOMEM, "adjoint workspace allocation failed");
+    TR_CUDA(cudaMemsetAsync(pr->err, 0, sizeof(ErrorWord), st));
+    RunParams R = base_params(o, o->n_histories);
+    R.want_log = 0;
+    TR_CUDA(launch_adjoint(P, R, d_grad_mesh, d_grad_scalars, F, d_sigt, d_sigs, d_nusigf, pr->err, pr->sms, st));
+    s = check_err(pr);
+    if (s != TR_OK) return s;
+    const double inv = 1.0 / (double)o->n_histories;
+    TR_CUDA(launch_scale(d_sigt, (int)MG, inv, d_sigt, st));
+    TR_CUDA(launch_scale(d_sigs, (int)(MG * P.G), inv, d_sigs, st));
+    TR_CUDA(launch_scale(d_nusigf, (int)MG, inv, d_nusigf, st));
+    TR_CUDA(cudaStreamSynchronize(st));
+    return TR_OK;
+}
+
+// ---------------------------------------------------------------------------
+// batched launches
+// ---------------------------------------------------------------------------
+namespace {
+
+struct BatchTuning {
+    int blocks_per_sm, stash_slots, remap_every;
+};
+
+std::mutex g_tune_mu;
+std::map<std::vector<unsigned long long>, BatchTuning> g_tune_cache;
+
+std::vector<unsigned long long> batch_signature(tr_problem* const* probs, int32_t n, const uint64_t* nh,
+                                                const tr_run_opts* o)
+{
+    std::vector<unsigned long long> k;
+    k.reserve(2 * (size_t)n + 16);
+    for (int32_t i = 0; i < n; ++i) {
+        k.push_back((unsigned long long)(uintptr_t)probs[i]);
+        k.push_back(nh[i]);
+    }
+    k.push_back(o->seed);
+    k.push_back((unsigned long long)o->decomposition);
+    k.push_back(o->queue_capacity);
+    k.push_back((unsigned long long)o->blocks_per_sm);
+    k.push_back((unsigned long long)o->stash_slots);
+    k.push_back((unsigned long long)o->remap_every);
+    k.push_back((unsigned long long)o->max_spin);
+    k.push_back((unsigned long long)o->max_wait_ms);
+    k.push_back(o->max_events);
+    k.push_back((unsigned long long)o->want_event_log);
+    k.push_back((unsigned long long)(uint32_t)o->spill_threshold);
+    k.push_back(o->problem_tag);
+    return k;
+}
+
+}  // namespace
+
+// Enqueue one batched run (everything from zeroing to normalisation) on the
+// leader's stream; used directly and under stream capture.
+static tr_status enqueue_batched(tr_problem* lead, tr_problem* const* probs, int32_t n, const uint64_t* nh,
+                                 const tr_run_opts* o, const BatchTuning& tune, DevProblem* d_probs, Tallies* d_tal,
+                                 unsigned long long* d_off, ScaleJob* d_jobs, int n_jobs, const AsyncArgs& A0,
+                                 unsigned long long total)
+{
+    const cudaStream_t st = lead->stream;
+    for (int32_t i = 0; i < n; ++i) {
+        tr_problem* p = probs[i];
+        TR_CUDA(cudaMemsetAsync(p->raw_mesh, 0, std::max(p->dp.mesh_size, 1) * 8, st));
+        TR_CUDA(cudaMemsetAsync(p->raw_energy, 0, std::max(p->dp.energy_size, 1) * 8, st));
+        TR_CUDA(cudaMemsetAsync(p->raw_scal, 0, 4 * 8, st));
+        TR_CUDA(cudaMemsetAsync(p->counts, 0, 16 * 8, st));
+    }
+    TR_CUDA(cudaMemsetAsync(lead->err, 0, sizeof(ErrorWord), st));
+    AsyncArgs A = A0;
+    TR_CUDA(cudaMemsetAsync(A.ctl, 0, sizeof(AsyncCtl), st));
+    TR_CUDA(cudaMemsetAsync(A.ctl->free_q, 0xFF, sizeof(A.ctl->free_q), st));
+    TR_CUDA(cudaMemsetAsync(A.ctl->full_q, 0xFF, sizeof(A.ctl->full_q), st));
+    A.probs = d_probs;
+    A.tallies = d_tal;
+    A.hist_off = d_off;
+    A.n_probs = n;
+    A.stash_slots = tune.stash_slots;
+    RunParams R = base_params(o, total);
+    R.remap_every = tune.remap_every;
+    R.want_log = o->want_event_log ? 1 : 0;
+    if (total > 0) TR_CUDA(launch_async_batched(lead->dp, R, A, lead->err, lead->sms * tune.blocks_per_sm, st));
+    TR_CUDA(launch_scale_jobs(d_jobs, n_jobs, st));
+    return TR_OK;
+}
+
+extern "C" tr_status tr_run_batched(tr_problem* const* probs, int32_t n, const uint64_t* n_histories,
+                                    const tr_run_opts* opts, tr_run_stats* stats)
+{
+    if (!probs || n < 1 || !n_histories || !opts) return set_err(TR_ERR_INVALID, "NULL argument or n < 1");
+    tr_status s = validate_opts(opts);
+    if (s != TR_OK) return s;
+    if (opts->scheme != TR_SCHEME_ASYNC) return set_err(TR_ERR_INVALID, "batched runs use the asynchronous scheme");
+    if (opts->first_history != 0) return set_err(TR_ERR_INVALID, "first_history applies to single runs only");
+    tr_problem* lead = probs[0];
+    unsigned long long total = 0;
+    for (int32_t i = 0; i < n; ++i) {
+        if (!probs[i]) return set_err(TR_ERR_INVALID, "NULL problem in the batch");
+        if (probs[i]->dp.kind != TR_XS_MG) return set_err(TR_ERR_INVALID, "batched runs need multigroup problems");
+        if (probs[i]->ctx.device != lead->ctx.device) return set_err(TR_ERR_INVALID, "all problems on one device");
+        if (n_histories[i] >= (1ull << 32)) return set_err(TR_ERR_INVALID, "n_histories must be < 2^32 per problem");
+        for (int32_t j = 0; j < i; ++j)
+            if (probs[j] == probs[i]) return set_err(TR_ERR_INVALID, "a problem appears twice in the batch");
+        total += n_histories[i];
+    }
+    if (opts->problem_tag & TAG_POP) return set_err(TR_ERR_INVALID, "problem_tag must be below 2^31");
+    const cudaStream_t st = lead->stream;
+    // outputs and logs allocated before any capture
+    for (int32_t i = 0; i < n; ++i) {
+        if (opts->want_event_log) {
+            s = ensure_log(probs[i], std::max<unsigned long long>(n_histories[i], 1));
+            if (s != TR_OK) return s;
+        }
+        if (probs[i]->stream != st) TR_CUDA(cudaStreamSynchronize(probs[i]->stream));
+    }
+    // autotuning of the options left at 0: blocks per SM, stash slots, remap frequency
+    BatchTuning tune{opts->blocks_per_sm, opts->stash_slots ? (opts->stash_slots + 31) & ~31 : 0, opts->remap_every};
+    if (tune.stash_slots && (tune.stash_slots < 32 * 9 || tune.stash_slots > 16384))
+        return set_err(TR_ERR_INVALID, "stash_slots must be in 288..16384");
+    const std::vector<unsigned long long> key = batch_signature(probs, n, n_histories, opts);
+    const bool need_tune = tune.blocks_per_sm == 0 || tune.stash_slots == 0 || tune.remap_every == 0;
+    if (need_tune) {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        auto it = g_tune_cache.find(key);
+        if (it != g_tune_cache.end()) tune = it->second;
+    }
+    // device tables of the batch (leader's workspace)
+    DevProblem* d_probs = (DevProblem*)workspace(lead, "batch_probs", sizeof(DevProblem) * n);
+    Tallies* d_tal = (Tallies*)workspace(lead, "batch_tallies", sizeof(Tallies) * n);
+    unsigned long long* d_off = (unsigned long long*)workspace(lead, "batch_off", 8 * (size_t)(n + 1));
+    ScaleJob* d_jobs = (ScaleJob*)workspace(lead, "batch_jobs", sizeof(ScaleJob) * 3 * (size_t)n);
+    const unsigned long long n_links = opts->queue_capacity ? (opts->queue_capacity + 31) / 32 : 8192;
+    AsyncArgs A{};
+    if (!d_probs || !d_tal || !d_off || !d_jobs || !carve_soa(lead, "links", n_links * 32, A.links))
+        return set_err(TR_ERR_NOMEM, "batch table allocation failed");
+    A.link_next = (unsigned*)workspace(lead, "link_next", n_links * 4);
+    A.link_type = (int*)workspace(lead, "link_type", n_links * 4);
+    A.link_fill = (int*)workspace(lead, "link_fill", n_links * 4);
+    A.ctl = (AsyncCtl*)workspace(lead, "asyncctl", sizeof(AsyncCtl));
+    if (!A.link_next || !A.link_type || !A.link_fill || !A.ctl) return set_err(TR_ERR_NOMEM, "link arena allocation failed");
+    A.n_links = n_links;
+    A.split = opts->decomposition == TR_DECOMP_SPLIT ? 1 : 0;
+    std::vector<DevProblem> hp(n);
+    std::vector<Tallies> ht(n);
+    std::vector<unsigned long long> hoff(n + 1, 0);
+    std::vector<ScaleJob> hj;
+    for (int32_t i = 0; i < n; ++i) {
+        hp[i] = probs[i]->dp;
+        ht[i] = make_tallies(probs[i], opts->want_event_log != 0);
+        hoff[i + 1] = hoff[i] + n_histories[i];
+        const double inv = n_histories[i] ? 1.0 / (double)n_histories[i] : 0.0;
+        if (probs[i]->dp.mesh_size) hj.push_back({probs[i]->raw_mesh, probs[i]->res_mesh, probs[i]->dp.mesh_size, inv});
+        if (probs[i]->dp.energy_size)
+            hj.push_back({probs[i]->raw_energy, probs[i]->res_energy, probs[i]->dp.energy_size, inv});
+        hj.push_back({probs[i]->raw_scal, probs[i]->res_scal, 3, inv});
+    }
+    TR_CUDA(cudaMemcpyAsync(d_probs, hp.data(), sizeof(DevProblem) * n, cudaMemcpyHostToDevice, st));
+    TR_CUDA(cudaMemcpyAsync(d_tal, ht.data(), sizeof(Tallies) * n, cudaMemcpyHostToDevice, st));
+    TR_CUDA(cudaMemcpyAsync(d_off, hoff.data(), 8 * (size_t)(n + 1), cudaMemcpyHostToDevice, st));
+    TR_CUDA(cudaMemcpyAsync(d_jobs, hj.data(), sizeof(ScaleJob) * hj.size(), cudaMemcpyHostToDevice, st));
+    TR_CUDA(cudaStreamSynchronize(st));
+
+    if (need_tune && (tune.blocks_per_sm == 0 || tune.stash_slots == 0 || tune.remap_every == 0)) {
+        // time candidate settings on a sample (1/16 of each problem's histories)
+        std::vector<uint64_t> sample(n);
+        unsigned long long stotal = 0;
+        std::vector<unsigned long long> soff(n + 1, 0);
+        for (int32_t i = 0; i < n; ++i) {
+            sample[i] = std::min<uint64_t>(n_histories[i], std::max<uint64_t>(64, n_histories[i] / 16));
+            soff[i + 1] = soff[i] + sample[i];
+            stotal += sample[i];
+        }
+        unsigned long long* d_soff = (unsigned long long*)workspace(lead, "batch_soff", 8 * (size_t)(n + 1));
+        if (!d_soff) return set_err(TR_ERR_NOMEM, "autotune allocation failed");
+        TR_CUDA(cudaMemcpyAsync(d_soff, soff.data(), 8 * (size_t)(n + 1), cudaMemcpyHostToDevice, st));
+        // candidates: a field set by the caller stays fixed
+        const std::vector<int> c_bps = tune.blocks_per_sm ? std::vector<int>{tune.blocks_per_sm} : std::vector<int>{1, 2};
+        const std::vector<int> c_S = tune.stash_slots ? std::vector<int>{tune.stash_slots} : std::vector<int>{288, 512, 1024};
+        const std::vector<int> c_rm = tune.remap_every ? std::vector<int>{tune.remap_every}
+                                      : A.split        ? std::vector<int>{1}
+                                                       : std::vector<int>{1, 2, 4};
+        std::vector<BatchTuning> cands;
+        for (int bps : c_bps)
+            for (int S : c_S)
+                for (int rm : c_rm)
+                    if (async_batched_max_blocks_per_sm(A.split, S) >= bps) cands.push_back({bps, S, rm});
+        if (cands.empty()) return set_err(TR_ERR_INVALID, "no feasible tuning candidate");
+        cudaEvent_t e0, e1;
+        TR_CUDA(cudaEventCreate(&e0));
+        TR_CUDA(cudaEventCreate(&e1));
+        float best = 1e30f;
+        BatchTuning pick = cands[0];
+        for (const BatchTuning& t : cands) {
+            TR_CUDA(cudaEventRecord(e0, st));
+            s = enqueue_batched(lead, probs, n, sample.data(), opts, t, d_probs, d_tal, d_soff, d_jobs, 0, A, stotal);
+            if (s != TR_OK) return s;
+            TR_CUDA(cudaEventRecord(e1, st));
+            TR_CUDA(cudaEventSynchronize(e1));
+            s = check_err(lead);
+            if (s != TR_OK) return s;
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (ms < best) {
+                best = ms;
+                pick = t;
+            }
+        }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        tune = pick;
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        g_tune_cache[key] = tune;
+    }
+    if (async_batched_max_blocks_per_sm(A.split, tune.stash_slots) < tune.blocks_per_sm)
+        return set_err(TR_ERR_INVALID, "blocks_per_sm does not fit with this stash size");
+
+    // the run: replay the captured graph when this leader ran the same batch last
+    // the graph bakes in device addresses: any reallocated buffer forces a new capture
+    std::vector<unsigned long long> gkey = key;
+    gkey.push_back((unsigned long long)tune.blocks_per_sm);
+    gkey.push_back((unsigned long long)tune.stash_slots);
+    gkey.push_back((unsigned long long)tune.remap_every);
+    for (const void* q : {(const void*)d_probs, (const void*)d_tal, (const void*)d_off, (const void*)d_jobs,
+                          (const void*)A.links.x, (const void*)A.link_next, (const void*)A.link_type,
+                          (const void*)A.link_fill, (const void*)A.ctl, (const void*)lead->err})
+        gkey.push_back((unsigned long long)(uintptr_t)q);
+    for (int32_t i = 0; i < n; ++i)
+        for (const void* q : {(const void*)probs[i]->raw_mesh, (const void*)probs[i]->raw_energy,
+                              (const void*)probs[i]->raw_scal, (const void*)probs[i]->counts})
+            gkey.push_back((unsigned long long)(uintptr_t)q);
+    gkey.push_back(hj.size());
+    if (!lead->batch_graph || lead->batch_key != gkey) {
+        if (lead->batch_graph) {
+            cudaGraphExecDestroy(lead->batch_graph);
+            lead->batch_graph = nullptr;
+        }
+        cudaStream_t cap;
+        TR_CUDA(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+        cudaGraph_t g = nullptr;
+        const unsigned long long c0 = launch_count();
+        TR_CUDA(cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal));
+        // capture on a private stream: the leader's stream is swapped for the capture
+        cudaStream_t saved = lead->stream;
+        lead->stream = cap;
+        s = enqueue_batched(lead, probs, n, n_histories, opts, tune, d_probs, d_tal, d_off, d_jobs, (int)hj.size(), A,
+                            total);
+        lead->stream = saved;
+        const cudaError_t ce = cudaStreamEndCapture(cap, &g);
+        cudaStreamDestroy(cap);
+        // captured launches did not run: take them off the counter, count them at each replay
+        lead->batch_graph_launches = launch_count() - c0;
+        count_launches(0ull - lead->batch_graph_launches);
+        if (s != TR_OK) {
+            if (g) cudaGraphDestroy(g);
+            return s;
+        }
+        if (ce != cudaSuccess) return set_err(TR_ERR_CUDA, std::string("stream capture: ") + cudaGetErrorString(ce));
+        const cudaError_t ie = cudaGraphInstantiate(&lead->batch_graph, g, 0);
+        cudaGraphDestroy(g);
+        if (ie != cudaSuccess) {
+            lead->batch_graph = nullptr;
+            return set_err(TR_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(ie));
+        }
+        lead->batch_key = gkey;
+    }
+    cudaEvent_t e0, e1;
+    TR_CUDA(cudaEventCreate(&e0));
+    TR_CUDA(cudaEventCreate(&e1));
+    TR_CUDA(cudaEventRecord(e0, st));
+    TR_CUDA(cudaGraphLaunch(lead->batch_graph, st));
+    count_launches(lead->batch_graph_launches);
+    TR_CUDA(cudaEventRecord(e1, st));
+    AsyncCtl hc;
+    TR_CUDA(cudaMemcpyAsync(&hc, A.ctl, sizeof(hc), cudaMemcpyDeviceToHost, st));
+    std::vector<unsigned long long> cnt(16 * (size_t)n);
+    for (int32_t i = 0; i < n; ++i)
+        TR_CUDA(cudaMemcpyAsync(cnt.data() + 16 * (size_t)i, probs[i]->counts, 16 * 8, cudaMemcpyDeviceToHost, st));
+    TR_CUDA(cudaStreamSynchronize(st));
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    s = check_err(lead);
+    if (s == TR_ERR_TIMEOUT)
+        return set_err(s, g_err + "; live " + std::to_string(hc.live) + ", spills " + std::to_string(hc.spills) +
+                              ", refills " + std::to_string(hc.refills));
+    if (s != TR_OK) return s;
+    if (hc.live != 0) return set_err(TR_ERR_STATE, "batched run ended with live particles");
+    for (int32_t i = 0; i < n; ++i) {
+        tr_problem* p = probs[i];
+        p->have_run = true;
+        p->have_std = false;
+        p->have_fixed = true;
+        p->last_fixed = *opts;
+        p->last_fixed.n_histories = n_histories[i];
+        p->last_fixed.problem_tag = opts->problem_tag ^ (uint32_t)i;
+        p->log_count = opts->want_event_log ? n_histories[i] : 0;
+        if (stats) {
+            tr_run_stats& S = stats[i];
+            std::memset(&S, 0, sizeof(S));
+            S.histories = n_histories[i];
+            for (int k = 0; k < 8; ++k) {
+                S.events_by_type[k] = cnt[16 * (size_t)i + k];
+                S.final_by_type[k] = cnt[16 * (size_t)i + 8 + k];
+                if (k != EV_SOURCE) S.events += S.events_by_type[k];
+            }
+            S.launches = 1;
+            S.spills = hc.spills;
+            S.refills = hc.refills;
+            S.seconds = ms * 1e-3;
+            S.transport_seconds = ms * 1e-3;
+            S.used_blocks_per_sm = tune.blocks_per_sm;
+            S.used_stash_slots = tune.stash_slots;
+            S.used_remap_every = tune.remap_every;
+        }
+    }
     return TR_OK;
 }
 

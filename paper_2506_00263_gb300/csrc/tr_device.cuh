@@ -64,7 +64,7 @@ struct DevProblem {
     double r2;                         // pin radius squared
     // cross sections
     int kind, n_mat, G;
-    const double *sigt, *inv_sigt, *sig_a, *nusigf, *cum_s, *cum_chi, *chi;
+    const double *sigt, *inv_sigt, *sig_a, *nusigf, *cum_s, *cum_chi, *chi, *sigs;
     int n_nuc;
     const double *nuc_e, *nuc_sig, *nuc_inv_de;   // CE rows
     const double *dens;                // [m][n]
@@ -102,19 +102,29 @@ struct RunParams {
     int want_log;
     int remap_every;
     uint64_t max_spin;
+    uint64_t max_wait_ns;              // wall-clock limit of one spin-wait (global timer)
     int spill_threshold;
 };
+
+// Device global timer in nanoseconds (bounds spin-waits in wall-clock time).
+__device__ __forceinline__ uint64_t now_ns()
+{
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
 
 // Structure-of-arrays particle storage (global memory stacks and links).
 // Fields: position, direction, cached reciprocals of the direction
 // components and of u^2 + v^2 (pure functions of the direction, stored so
 // that a surface event does not repeat four divisions), energy (CE) or
-// group (MG), packed cell, history index, event count, banked-site count and
-// the pending surface flags of the decomposed scheme.
+// group (MG), packed cell, history index, event count, banked-site count, the
+// pending surface flags of the decomposed scheme and the problem index of a
+// batched launch.
 struct SoA {
     double *x, *y, *z, *u, *v, *w, *iu, *iv, *iw, *ia, *E;
     int *g;
-    unsigned *cell, *id, *n, *nsites, *pend;
+    unsigned *cell, *id, *n, *nsites, *pend, *prob;
 };
 
 struct Particle {
@@ -124,6 +134,7 @@ struct Particle {
     int g;
     unsigned cell;                     // i | j << 10 | k << 20 | inside << 30
     unsigned id, n, nsites, pend;
+    unsigned prob;                     // problem index within a batched launch (0 otherwise)
 };
 
 // Tally accumulators written by kernels (raw sums, normalised later).
@@ -247,22 +258,38 @@ __device__ __forceinline__ double tr_log(double x)
 // Directions: azimuth by rejection in the unit square (no trig), isotropic
 // direction, lab rotation, target-at-rest elastic kinematics.
 // ---------------------------------------------------------------------------
+// One rejection try t: the point (a, b) and whether 0 < a^2 + b^2 <= 1.
+__device__ __forceinline__ bool azimuth_try(const Stream& S, uint32_t n, uint32_t t, double& a, double& b, double& a2,
+                                            double& b2, double& s)
+{
+    const uint4 r = S.block(n, BLK_AZIMUTH + t);
+    a = 2.0 * u01(r.x, r.y) - 1.0;
+    b = 2.0 * u01(r.z, r.w) - 1.0;
+    a2 = a * a;
+    b2 = b * b;
+    s = a2 + b2;
+    return dbits(s) <= dbits(1.0) && gt0(s);   // 0 < s <= 1 (s >= +0)
+}
+
 __device__ __forceinline__ void azimuth(const Stream& S, uint32_t n, double& cphi, double& sphi)
 {
-    double a = 1.0, b = 0.0, a2 = 1.0, b2 = 0.0, s = 1.0;
-    for (uint32_t t = 0; t < N_AZIMUTH; ++t) {
-        TR_LANES(6);
-        const uint4 r = S.block(n, BLK_AZIMUTH + t);
-        const double ta = 2.0 * u01(r.x, r.y) - 1.0;
-        const double tb = 2.0 * u01(r.z, r.w) - 1.0;
-        const double ta2 = ta * ta, tb2 = tb * tb;
-        const double ts = ta2 + tb2;
-        if (dbits(ts) <= dbits(1.0) && gt0(ts)) {   // 0 < ts <= 1 (ts >= +0)
-            a = ta; b = tb; a2 = ta2; b2 = tb2; s = ts;
-            break;
-        }
+    // the first accepted try; tries 0 and 1 run unconditionally in every lane
+    // (both accepted: take try 0), the rare remainder loops
+    double a, b, a2, b2, s, a1, b1, a21, b21, s1;
+    bool ok = azimuth_try(S, n, 0u, a, b, a2, b2, s);
+    const bool ok1 = azimuth_try(S, n, 1u, a1, b1, a21, b21, s1);
+    if (!ok && ok1) {
+        a = a1; b = b1; a2 = a21; b2 = b21; s = s1;
+        ok = true;
     }
-    const double inv_s = 1.0 / s;
+    for (uint32_t t = 2; !ok && t < N_AZIMUTH; ++t) {
+        TR_LANES(6);
+        ok = azimuth_try(S, n, t, a, b, a2, b2, s);
+    }
+    if (!ok) {
+        a = 1.0; b = 0.0; a2 = 1.0; b2 = 0.0; s = 1.0;
+    }
+    const double inv_s = __drcp_rn(s);
     cphi = (a2 - b2) * inv_s;
     sphi = (2.0 * (a * b)) * inv_s;
 }
@@ -270,11 +297,12 @@ __device__ __forceinline__ void azimuth(const Stream& S, uint32_t n, double& cph
 __device__ __forceinline__ void set_reciprocals(Particle& p)
 {
     // (bits << 1) != 0 is x != +-0
-    p.iu = (dbits(p.u) << 1) ? 1.0 / p.u : 0.0;
-    p.iv = (dbits(p.v) << 1) ? 1.0 / p.v : 0.0;
-    p.iw = (dbits(p.w) << 1) ? 1.0 / p.w : 0.0;
+    // __drcp_rn is the correctly rounded reciprocal: the same value as 1.0 / x
+    p.iu = (dbits(p.u) << 1) ? __drcp_rn(p.u) : 0.0;
+    p.iv = (dbits(p.v) << 1) ? __drcp_rn(p.v) : 0.0;
+    p.iw = (dbits(p.w) << 1) ? __drcp_rn(p.w) : 0.0;
     const double a = p.u * p.u + p.v * p.v;
-    p.ia = gt0(a) ? 1.0 / a : 0.0;
+    p.ia = gt0(a) ? __drcp_rn(a) : 0.0;
 }
 
 __device__ __forceinline__ void iso_dir(const Stream& S, uint32_t n, double xi_mu, Particle& p)

@@ -44,15 +44,28 @@ __device__ __forceinline__ Stream make_stream(const RunParams& R, unsigned id)
 // Woo) walks the mesh cells the segment p0 + t d, 0 <= t <= L crosses, after
 // clipping it to the mesh box.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ void mesh_tally(const DevProblem& P, double* __restrict__ mesh, const Particle& p,
-                                           double x0, double y0, double z0, double L, int goff)
+// Mesh-tally operations: add the piece to the tally, or weight it by an
+// upstream gradient (adjoint).
+struct MeshAtomic {
+    double* mesh;
+    __device__ __forceinline__ void operator()(int i, double l) const { atomicAdd(mesh + i, l); }
+};
+struct MeshWeighted {
+    const double* g;
+    double f;
+    __device__ __forceinline__ void operator()(int i, double l) { f += __ldg(g + i) * l; }
+};
+
+template <class Op>
+__device__ __forceinline__ void mesh_tally(const DevProblem& P, Op& op, const Particle& p, double x0, double y0,
+                                           double z0, double L, int goff)
 {
     const int vx = __ldg(P.cell2vox + cell_i(p.cell));
     const int vy = __ldg(P.cell2vox + P.nx + cell_j(p.cell));
     const int vz = __ldg(P.cell2vox + P.nx + P.ny + cell_k(p.cell));
     const int nx = P.mesh_n[0], ny = P.mesh_n[1], nz = P.mesh_n[2];
     if ((vx | vy | vz) >= 0) {
-        atomicAdd(mesh + goff + (vz * ny + vy) * nx + vx, L);
+        op(goff + (vz * ny + vy) * nx + vx, L);
         return;
     }
     const double INF = __longlong_as_double(0x7FF0000000000000ll);
@@ -100,7 +113,7 @@ __device__ __forceinline__ void mesh_tally(const DevProblem& P, double* __restri
         if (tz < tn) { tn = tz; ax = 2; }
         const double te = fmin(tn, t1);
         if (te > t) {
-            atomicAdd(mesh + goff + (iz * ny + iy) * nx + ix, te - t);
+            op(goff + (iz * ny + iy) * nx + ix, te - t);
             t = te;
         }
         if (!(tn < t1)) break;
@@ -148,6 +161,7 @@ __device__ __forceinline__ bool source_particle(const DevProblem& P, const RunPa
     p.n = 1u;
     p.nsites = 0u;
     p.pend = 0u;
+    p.prob = 0u;
     p.g = 0;
     p.E = 0.0;
     if (site != nullptr || P.src_kind != 0 || P.src_iso) {
@@ -196,9 +210,30 @@ __device__ __forceinline__ bool source_particle(const DevProblem& P, const RunPa
 // Step event: lookup, distance to collision vs. surface, move, tally.
 // Leaves the outcome in p.pend.  Returns the lookup for the collision.
 // ---------------------------------------------------------------------------
-template <bool CE>
-__device__ __forceinline__ void step_event(const DevProblem& P, const RunParams& R, Particle& p, const Tallies& T,
-                                           Acc& acc, XS& X, double& xi_react)
+// Forward tally sink: track-length scores into the tallies and the per-lane
+// scalar accumulators.
+struct FwdSink {
+    const Tallies& T;
+    Acc& acc;
+    template <bool CE>
+    __device__ __forceinline__ void segment(const DevProblem& P, const Particle& p, double x0, double y0, double z0,
+                                            double dist, int m, const XS& X)
+    {
+        acc.flux += dist;
+        acc.absn += dist * X.sa;
+        acc.prod += dist * X.nsf;
+        if (P.has_mesh && gt0(dist)) {
+            const int goff = (!CE && P.by_group) ? p.g * P.mesh_vox : 0;
+            MeshAtomic op{T.mesh};
+            mesh_tally(P, op, p, x0, y0, z0, dist, goff);
+        }
+        if (CE && P.n_ebins > 0 && gt0(dist)) energy_tally(P, T.energy, m, p.E, dist);
+    }
+};
+
+template <bool CE, class Sink>
+__device__ __forceinline__ void step_event(const DevProblem& P, const RunParams& R, Particle& p, Sink& sink, XS& X,
+                                           double& xi_react)
 {
     TR_LANES(1);
     const unsigned c = p.cell;
@@ -215,35 +250,29 @@ __device__ __forceinline__ void step_event(const DevProblem& P, const RunParams&
     const double INF = __longlong_as_double(0x7FF0000000000000ll);
     const int i = cell_i(c), j = cell_j(c), k = cell_k(c);
     double dx, dy, dz;
-    if (gt0(p.u)) dx = (__ldg(P.xp + i + 1) - p.x) * p.iu;
-    else if (lt0(p.u)) dx = (__ldg(P.xp + i) - p.x) * p.iu;
-    else dx = INF;
-    if (gt0(p.v)) dy = (__ldg(P.yp + j + 1) - p.y) * p.iv;
-    else if (lt0(p.v)) dy = (__ldg(P.yp + j) - p.y) * p.iv;
-    else dy = INF;
-    if (gt0(p.w)) dz = (__ldg(P.zp + k + 1) - p.z) * p.iw;
-    else if (lt0(p.w)) dz = (__ldg(P.zp + k) - p.z) * p.iw;
-    else dz = INF;
-    dx = clamp0(dx);
-    dy = clamp0(dy);
-    dz = clamp0(dz);
+    // exit plane chosen by the sign of the component (integer select), then one
+    // subtraction and one multiplication for every lane: no divergent paths
+    dx = (__ldg(P.xp + i + (gt0(p.u) ? 1 : 0)) - p.x) * p.iu;
+    dy = (__ldg(P.yp + j + (gt0(p.v) ? 1 : 0)) - p.y) * p.iv;
+    dz = (__ldg(P.zp + k + (gt0(p.w) ? 1 : 0)) - p.z) * p.iw;
+    dx = (dbits(p.u) << 1) ? clamp0(dx) : INF;
+    dy = (dbits(p.v) << 1) ? clamp0(dy) : INF;
+    dz = (dbits(p.w) << 1) ? clamp0(dz) : INF;
 
     double dcyl = INF;
     if (pin) {
+        // one square root of max(disc, 0) serves both cases: inside, the
+        // clamped discriminant; outside, a hit needs k < 0 and disc >= 0 and
+        // then max(disc, 0) = disc
         double cc, kk;
         pin_terms(P, p, cc, kk);
         const double a = p.u * p.u + p.v * p.v;
-        if (gt0(a)) {
-            if (in) {
-                double disc = kk * kk - a * cc;
-                if (lt0(disc)) disc = 0.0;
-                dcyl = (sqrt(disc) - kk) * p.ia;
-            } else if (lt0(kk)) {
-                const double disc = kk * kk - a * cc;
-                if (ge0(disc)) dcyl = ((-kk) - sqrt(disc)) * p.ia;
-            }
-        }
-        dcyl = clamp0(dcyl);
+        const double disc = kk * kk - a * cc;
+        const double sq = sqrt(lt0(disc) ? 0.0 : disc);
+        const double d_in = (sq - kk) * p.ia;
+        const double d_out = ((-kk) - sq) * p.ia;
+        const bool hit = gt0(a) && (in || (lt0(kk) && ge0(disc)));
+        dcyl = hit ? clamp0(in ? d_in : d_out) : INF;
     }
     unsigned flags = 0u;
     double ds;
@@ -270,24 +299,16 @@ __device__ __forceinline__ void step_event(const DevProblem& P, const RunParams&
         }
     }
     const bool collided = lt_nn(dcol, ds);
-    if (!collided && dbits(ds) == dbits(INF)) {
-        p.pend = PEND_ESCAPE;
-        return;
+    const bool escape = !collided && dbits(ds) == dbits(INF);   // no surface ahead: the particle escapes
+    if (!escape) {
+        const double dist = collided ? dcol : ds;
+        const double x0 = p.x, y0 = p.y, z0 = p.z;
+        p.x = p.x + dist * p.u;
+        p.y = p.y + dist * p.v;
+        p.z = p.z + dist * p.w;
+        sink.template segment<CE>(P, p, x0, y0, z0, dist, m, X);
     }
-    const double dist = collided ? dcol : ds;
-    const double x0 = p.x, y0 = p.y, z0 = p.z;
-    p.x = p.x + dist * p.u;
-    p.y = p.y + dist * p.v;
-    p.z = p.z + dist * p.w;
-    acc.flux += dist;
-    acc.absn += dist * X.sa;
-    acc.prod += dist * X.nsf;
-    if (P.has_mesh && gt0(dist)) {
-        const int goff = (!CE && P.by_group) ? p.g * P.mesh_vox : 0;
-        mesh_tally(P, T.mesh, p, x0, y0, z0, dist, goff);
-    }
-    if (CE && P.n_ebins > 0 && gt0(dist)) energy_tally(P, T.energy, m, p.E, dist);
-    p.pend = collided ? PEND_COLLIDE : flags;
+    p.pend = escape ? PEND_ESCAPE : (collided ? PEND_COLLIDE : flags);
 }
 
 // ---------------------------------------------------------------------------
@@ -491,7 +512,8 @@ __device__ __forceinline__ bool mono_event(const DevProblem& P, const RunParams&
     TR_LANES(10);
     XS X;
     double xi_react;
-    step_event<CE>(P, R, p, T, acc, X, xi_react);
+    FwdSink sink{T, acc};
+    step_event<CE>(P, R, p, sink, X, xi_react);
     int type;
     if (p.pend == PEND_COLLIDE) type = collide_event<CE>(P, R, p, X, xi_react, B, err);
     else type = surface_event(P, p);
@@ -529,6 +551,7 @@ __device__ __forceinline__ void load_particle(const SoA& s, unsigned long long i
     p.iu = s.iu[i]; p.iv = s.iv[i]; p.iw = s.iw[i]; p.ia = s.ia[i];
     if (ce) p.E = s.E[i]; else p.g = s.g[i];
     p.cell = s.cell[i]; p.id = s.id[i]; p.n = s.n[i]; p.nsites = s.nsites[i]; p.pend = s.pend[i];
+    p.prob = s.prob[i];
 }
 
 __device__ __forceinline__ void store_particle(const SoA& s, unsigned long long i, const Particle& p, bool ce)
@@ -538,6 +561,7 @@ __device__ __forceinline__ void store_particle(const SoA& s, unsigned long long 
     s.iu[i] = p.iu; s.iv[i] = p.iv; s.iw[i] = p.iw; s.ia[i] = p.ia;
     if (ce) s.E[i] = p.E; else s.g[i] = p.g;
     s.cell[i] = p.cell; s.id[i] = p.id; s.n[i] = p.n; s.nsites[i] = p.nsites; s.pend[i] = p.pend;
+    s.prob[i] = p.prob;
 }
 
 // Next queue of a live particle after an event: a step leads to collision or

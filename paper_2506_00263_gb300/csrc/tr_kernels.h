@@ -44,12 +44,30 @@ struct AsyncArgs {
     int use_src;
     int split;
     int stash_slots;
+    // batched launches: per-problem descriptors, tallies and history offsets
+    const DevProblem* probs;
+    const Tallies* tallies;
+    const unsigned long long* hist_off;   // n_probs + 1 cumulative history counts
+    int n_probs;
 };
 
 cudaError_t launch_async(const DevProblem& P, const RunParams& R, const AsyncArgs& A, const Tallies& T, ErrorWord* err,
                          int blocks, cudaStream_t st, int* smem_bytes_out);
 int async_max_blocks_per_sm(const DevProblem& P, int split, int stash_slots);
+cudaError_t launch_async_batched(const DevProblem& P0, const RunParams& R, const AsyncArgs& A, ErrorWord* err,
+                                 int blocks, cudaStream_t st);
+int async_batched_max_blocks_per_sm(int split, int stash_slots);
+struct ScaleJob {
+    const double* in;
+    double* out;
+    int n;
+    double s;
+};
+cudaError_t launch_scale_jobs(const ScaleJob* jobs, int n_jobs, cudaStream_t st);
 
+cudaError_t launch_adjoint(const DevProblem& P, const RunParams& R, const double* g_mesh, const double* g_scal,
+                           double* F, double* d_sigt, double* d_sigs, double* d_nusigf, ErrorWord* err, int sms,
+                           cudaStream_t st);
 cudaError_t launch_scan(const unsigned* in, unsigned long long n, unsigned long long* tile_sum, unsigned long long* out,
                         unsigned long long* total, cudaStream_t st);
 cudaError_t launch_bank_order(const Bank& in, unsigned long long m, const unsigned long long* offset, const Bank& out,

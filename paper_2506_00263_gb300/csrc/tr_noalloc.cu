@@ -29,8 +29,8 @@ namespace {
 
 constexpr unsigned long long NOALLOC_LINKS = TR_NOALLOC_MAX_QUEUE_CAPACITY / 32;
 constexpr size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
-// per particle slot of the link arena: 11 doubles + 6 32-bit words (as carve_links below)
-constexpr size_t LINK_SOA_BYTES = 17 * 256 + NOALLOC_LINKS * 32 * (11 * 8 + 6 * 4);
+// per particle slot of the link arena: 11 doubles + 7 32-bit words (as carve_links below)
+constexpr size_t LINK_SOA_BYTES = 18 * 256 + NOALLOC_LINKS * 32 * (11 * 8 + 7 * 4);
 constexpr size_t OFF_ERR = 0;
 constexpr size_t OFF_COUNTS = align256(OFF_ERR + sizeof(ErrorWord));
 constexpr size_t OFF_CTL = align256(OFF_COUNTS + 16 * sizeof(unsigned long long));
@@ -91,7 +91,7 @@ void carve_links(unsigned char* b, unsigned long long n, SoA& s)
     s.E = (double*)take(8);
     s.g = (int*)take(4);
     s.cell = (unsigned*)take(4); s.id = (unsigned*)take(4); s.n = (unsigned*)take(4);
-    s.nsites = (unsigned*)take(4); s.pend = (unsigned*)take(4);
+    s.nsites = (unsigned*)take(4); s.pend = (unsigned*)take(4); s.prob = (unsigned*)take(4);
 }
 
 #define NA_CUDA(call)                                                            \
@@ -158,6 +158,7 @@ extern "C" tr_status tr_run_fixed_source_noalloc(tr_problem* problem, const tr_r
     R.inv_k = 1.0;
     R.remap_every = o->remap_every > 0 ? o->remap_every : 1;
     R.max_spin = o->max_spin > 0 ? (uint64_t)o->max_spin : (1ull << 24);
+    R.max_wait_ns = (uint64_t)(o->max_wait_ms ? o->max_wait_ms : 60000u) * 1000000ull;
     R.spill_threshold = o->spill_threshold ? o->spill_threshold : 64;
 
     // the array keeps the previous call's contents: clear what must start at zero
@@ -191,7 +192,7 @@ extern "C" tr_status tr_run_fixed_source_noalloc(tr_problem* problem, const tr_r
     NA_CUDA(cudaMemcpyAsync(&hc, A.ctl, sizeof(hc), cudaMemcpyDeviceToHost, st));
     NA_CUDA(cudaMemcpyAsync(hcnt, counts, sizeof(hcnt), cudaMemcpyDeviceToHost, st));
     NA_CUDA(cudaStreamSynchronize(st));
-    if (he.code == ERR_TIMEOUT) return fail(TR_ERR_TIMEOUT, "a device spin-wait exceeded max_spin");
+    if (he.code == ERR_TIMEOUT) return fail(TR_ERR_TIMEOUT, "a device spin-wait exceeded max_spin or max_wait_ms");
     if (he.code == ERR_CAPACITY) return fail(TR_ERR_CAPACITY, "the static link arena overflowed");
     if (he.code != 0) return fail(TR_ERR_INVALID, "device reported invalid state");
     if (hc.live != 0) return fail(TR_ERR_STATE, "run ended with live particles");

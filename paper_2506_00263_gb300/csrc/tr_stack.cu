@@ -67,6 +67,7 @@ __global__ void __launch_bounds__(256) k_stack_mono(DevProblem P, RunParams R, S
                 load_particle(A.in[Q_STEP], i, p, CE);
                 live = true;
             }
+            __syncwarp();
             for (int r = 0; r < R.remap_every; ++r) {
                 if (!__any_sync(FULL, live)) break;
                 if (live) live = mono_event<CE>(P, R, p, T, acc, A.bank, err);
@@ -82,6 +83,7 @@ __global__ void __launch_bounds__(256) k_stack_mono(DevProblem P, RunParams R, S
             first = __shfl_sync(FULL, first, 0);
             if (first >= R.n_hist) break;
             const unsigned long long id = first + lane;
+            __syncwarp();
             if (id < R.n_hist) {
                 live = source_particle<CE>(P, R, (unsigned)id, p, A.use_src ? &A.src : nullptr, id);
                 if (!live) atomicCAS(&err->code, 0, ERR_INVALID);
@@ -123,13 +125,15 @@ __global__ void __launch_bounds__(256) k_stack_split(DevProblem P, RunParams R, 
             if (base >= start[1]) q = 1;
             if (base >= start[2]) q = 2;
             const unsigned long long i = base - start[q] + lane;
+            if (i < cnt[q]) load_particle(A.in[q], i, p, CE);
+            __syncwarp();
             if (i < cnt[q]) {
-                load_particle(A.in[q], i, p, CE);
                 live = true;
                 if (q == Q_STEP) {
                     XS X;
                     double xr;
-                    step_event<CE>(P, R, p, T, acc, X, xr);
+                    FwdSink sink{T, acc};
+                    step_event<CE>(P, R, p, sink, X, xr);
                     dst = next_queue_after_step(p);
                 } else if (q == Q_COLLIDE) {
                     live = split_collide<CE>(P, R, p, T, acc, A.bank, err);
@@ -146,6 +150,7 @@ __global__ void __launch_bounds__(256) k_stack_split(DevProblem P, RunParams R, 
             first = __shfl_sync(FULL, first, 0);
             if (first >= R.n_hist) break;
             const unsigned long long id = first + lane;
+            __syncwarp();
             if (id < R.n_hist) {
                 live = source_particle<CE>(P, R, (unsigned)id, p, A.use_src ? &A.src : nullptr, id);
                 if (!live) atomicCAS(&err->code, 0, ERR_INVALID);
@@ -315,6 +320,16 @@ __global__ void k_scale(const double* __restrict__ in, int n, double s, double* 
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) out[i] = in[i] * s;
 }
 
+// Many scalings in one launch: job j multiplies in[0..n) by s into out.
+__global__ void k_scale_jobs(const ScaleJob* __restrict__ jobs, int n_jobs)
+{
+    for (int j = blockIdx.y; j < n_jobs; j += gridDim.y) {
+        const ScaleJob J = jobs[j];
+        for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < J.n; i += gridDim.x * blockDim.x)
+            J.out[i] = J.in[i] * J.s;
+    }
+}
+
 __global__ void k_eig_finish(const double* __restrict__ sum, const double* __restrict__ sq, int n, double na,
                              double* __restrict__ mean, double* __restrict__ sd)
 {
@@ -418,6 +433,14 @@ cudaError_t launch_scale(const double* in, int n, double s, double* out, cudaStr
     if (n <= 0) return cudaSuccess;
     count_launches(1);
     k_scale<<<grid_for(n, 256, 1024), 256, 0, st>>>(in, n, s, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_scale_jobs(const ScaleJob* jobs, int n_jobs, cudaStream_t st)
+{
+    if (n_jobs <= 0) return cudaSuccess;
+    count_launches(1);
+    k_scale_jobs<<<dim3(32, n_jobs < 65535 ? n_jobs : 65535), 256, 0, st>>>(jobs, n_jobs);
     return cudaGetLastError();
 }
 

@@ -89,3 +89,46 @@ def test_header_documents_every_entry_point():
         while j >= 0 and not lines[j].strip():
             j -= 1
         assert lines[j].rstrip().endswith("*/"), name
+
+
+def test_batched_rejects_null_arguments_on_host(lib):
+    opts = tb.RunOpts(n_histories=1, scheme=tb.SCHEME_ASYNC).to_c()
+    nh = (C.c_uint64 * 1)(1)
+    assert lib.tr_run_batched(None, 1, nh, C.byref(opts), None) == tb.TR_ERR_INVALID
+    hs = (C.c_void_p * 1)(None)
+    assert lib.tr_run_batched(hs, 0, nh, C.byref(opts), None) == tb.TR_ERR_INVALID
+    assert lib.tr_run_batched(hs, 1, nh, C.byref(opts), None) == tb.TR_ERR_INVALID
+    assert b"NULL" in lib.tr_last_error()
+
+
+def test_ctypes_structs_match_the_header(tmp_path):
+    """Size and field offsets of every public struct, from the C compiler,
+    equal the ctypes mirrors of the binding."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    pairs = {"tr_geometry_desc": tb.GeometryDesc, "tr_xs_desc": tb.XsDesc, "tr_source_desc": tb.SourceDesc,
+             "tr_tally_desc": tb.TallyDesc, "tr_device_ctx": tb.DeviceCtx, "tr_run_opts": tb.RunOptsC,
+             "tr_run_stats": tb.RunStats, "tr_eig_opts": tb.EigOptsC, "tr_eig_result": tb.EigResultC}
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "tr.h"', "int main(void) {"]
+    for cname, py in pairs.items():
+        lines.append(f'printf("{cname} size %zu\\n", sizeof({cname}));')
+        for f in py._fields_:
+            lines.append(f'printf("{cname} {f[0]} %zu\\n", offsetof({cname}, {f[0]}));')
+    lines += ["return 0; }"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    got = {}
+    for line in out:
+        if line.strip():
+            a, b, v = line.split()
+            got[(a, b)] = int(v)
+    for cname, py in pairs.items():
+        assert got[(cname, "size")] == C.sizeof(py), cname
+        for f in py._fields_:
+            assert got[(cname, f[0])] == getattr(py, f[0]).offset, (cname, f[0])
