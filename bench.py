@@ -179,7 +179,8 @@ def run_ours(args):
     decomp = tb.DECOMP_SPLIT if args.decomp == "split" else tb.DECOMP_MONO
     spec = inputs.c5g7_lattice()
     opts = tb.RunOpts(seed=1 + 1000 * rank, scheme=scheme, decomposition=decomp, stash_slots=args.stash,
-                      blocks_per_sm=args.bps, remap_every=args.remap, queue_capacity=args.queue)
+                      blocks_per_sm=args.bps, remap_every=args.remap if args.decomp == "mono" else 1,
+                      queue_capacity=args.queue)
     stream = torch.cuda.current_stream()
     prob = tb.Problem(spec)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float64, device="cuda")   # 512 MB > L2
@@ -265,6 +266,19 @@ def run_ours(args):
             d2h = mesh.nbytes + sc.nbytes + 3 * 8 * (args.inactive + args.active)
         e2e = {"value": ev_e / t_e, "unit": "events/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
 
+    # ---- the other reported quantities (not part of the timed value) ----
+    extras = None
+    if rank == 0 and not args.no_extras:
+        adj = measure_adjoint(torch, tb, inputs, 3, 2, decomp)
+        bat = measure_batched(torch, tb, inputs, 2, 2, decomp)
+        extras = {
+            "gradient": {"workload": ADJ_WORKLOAD, "forward_ms": adj["forward_ms"], "backward_ms": adj["backward_ms"],
+                         "gradient_over_forward": adj["gradient_over_forward"]},
+            "batched": {"workload": BATCH_WORKLOAD, "events_per_s": bat["events_per_s"],
+                        "ms_per_call": 1e3 * bat["seconds"] / 2, "first_call_s": bat["first_call_s"],
+                        "tuning_used": bat["tuning_used"],
+                        "sequential_single_runs_events_per_s": bat["sequential_single_runs"]["events_per_s"],
+                        "speedup_of_batched": bat["sequential_single_runs"]["speedup_of_batched"]}}
     if rank != 0:
         return 0
     cpu = None if args.no_cpu_baseline else _cpu_baseline()
@@ -273,7 +287,8 @@ def run_ours(args):
         "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": WORKLOAD, "scheme": args.scheme, "decomposition": args.decomp,
-                   "stash_slots": args.stash, "blocks_per_sm": args.bps, "remap_every": args.remap,
+                   "stash_slots": args.stash, "blocks_per_sm": args.bps,
+                   "remap_every": args.remap if args.decomp == "mono" else 1,
                    "n_per_batch": args.n_per_batch, "batches": args.inactive + args.active,
                    "l2": "flushed between steps (512 MB write)"},
         "histories_per_s": hist_all / t,
@@ -281,6 +296,7 @@ def run_ours(args):
         "e2e": e2e, "cpu_baseline": cpu, "gpu_launches": launches,
         "clocks": sampler.summary(),
         "transport": {"kernel_seconds": kern_s, "launches": kern_launches, "avg_launch_ms": 1e3 * avg_launch},
+        "extras": extras,
     }
     print(json.dumps(line), flush=True)
     prob.close()
@@ -291,15 +307,12 @@ def run_ours(args):
 
 BATCH_WORKLOAD = ("256 independent multigroup voxel boxes (groups from {1,2,7,20,70}, 1-8 materials, "
                   "up to 64^3 voxels, 1e3-1e6 histories log-uniform, 8^3-32^3 mesh) in one batched launch")
+ADJ_WORKLOAD = ("differentiated 7-group lattice, fission off, uniform source in fuel pins, 1e6 histories: "
+                "forward fixed-source run + derivatives of the 51x51 mesh flux and absorption rate")
 
 
-def run_batched_workload(args):
-    """One step = one tr_run_batched over the 256-problem workload (autotuned,
-    graph-replayed after the first call).  Also times the same problems run
-    one after another through tr_run_fixed_source, for comparison."""
-    import numpy as np
-    import torch
-
+def _setup(torch):
+    """Process group (N > 1), device, library build; returns (ws, rank, tb, inputs)."""
     ws, rank, local = _dist()
     if ws > 1:
         import torch.distributed as dist
@@ -308,32 +321,38 @@ def run_batched_workload(args):
     from paper_2506_00263_gb300 import binding as tb
     from paper_2506_00263_gb300 import build as tbuild
     from paper_2506_00263_gb300 import inputs
-
     if rank == 0 or not os.path.exists(tbuild.LIB):
         tbuild.build()
     if ws > 1:
         torch.distributed.barrier()
-    decomp = tb.DECOMP_SPLIT if args.decomp == "split" else tb.DECOMP_MONO
-    specs, hist = inputs.batched_boxes(256, seed=7 + rank)
+    return ws, rank, tb, inputs
+
+
+def measure_batched(torch, tb, inputs, steps, warmup, decomp, seed=1, tuning=(0, 0, 0), sampler=None,
+                    barrier=None):
+    """One step = one tr_run_batched over the 256-problem workload (autotuned
+    and graph-replayed after the first call), timed with CUDA events; then
+    the same problems once more, one tr_run_fixed_source after another."""
+    specs, hist = inputs.batched_boxes(256, seed=7 + seed)
     probs = [tb.Problem(s) for s in specs]
-    opts = tb.RunOpts(seed=1 + 1000 * rank, scheme=tb.SCHEME_ASYNC, decomposition=decomp,
-                      stash_slots=args.stash, blocks_per_sm=args.bps, remap_every=args.remap if args.bps else 0,
-                      queue_capacity=args.queue)
+    bps, stash, remap = tuning
+    opts = tb.RunOpts(seed=seed, scheme=tb.SCHEME_ASYNC, decomposition=decomp, stash_slots=stash,
+                      blocks_per_sm=bps, remap_every=remap)
     stream = torch.cuda.current_stream()
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float64, device="cuda")
     t_first = time.perf_counter()
     tb.run_batched(probs, hist, opts)            # autotuning + graph capture
     t_first = time.perf_counter() - t_first
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         tb.run_batched(probs, hist, opts)
     torch.cuda.synchronize()
-    if ws > 1:
-        torch.distributed.barrier()
+    if barrier:
+        barrier()
     launches0 = tb.kernel_launch_count()
     times, ev_tot, kern_s = [], 0, 0.0
-    sampler = ClockSampler(torch.cuda.current_device())
-    with sampler:
-        for k in range(args.steps):
+    import contextlib
+    with (sampler or contextlib.nullcontext()):
+        for k in range(steps):
             flush.fill_(float(k))
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
@@ -346,95 +365,39 @@ def run_batched_workload(args):
             kern_s += st[0]["transport_seconds"]
     torch.cuda.synchronize()
     launches = tb.kernel_launch_count() - launches0
-    t = sum(times)
-    hist_step = float(sum(hist))
-    if ws > 1:
-        from paper_2506_00263_gb300 import parallel
-        t, ev_all, hist_all = parallel.reduce_timing(t, float(ev_tot), hist_step * args.steps, device="cuda")
-    else:
-        ev_all, hist_all = float(ev_tot), hist_step * args.steps
     used = st[0]["used"]
-    # the same problems, one tr_run_fixed_source after another (default tuning)
-    single_opts = lambda n, i: tb.RunOpts(n_histories=n, seed=1 + 1000 * rank, scheme=tb.SCHEME_ASYNC,
-                                          decomposition=decomp, problem_tag=i)
+    single = lambda n, i: tb.RunOpts(n_histories=n, seed=seed, scheme=tb.SCHEME_ASYNC, decomposition=decomp,
+                                     problem_tag=i)
     for i, (p, n) in enumerate(zip(probs, hist)):      # warm
-        p.run_fixed_source(single_opts(min(n, 1000), i))
+        p.run_fixed_source(single(min(n, 1000), i))
     torch.cuda.synchronize()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     ev_seq = 0
     for i, (p, n) in enumerate(zip(probs, hist)):
-        ev_seq += int(p.run_fixed_source(single_opts(n, i))["events"])
+        ev_seq += int(p.run_fixed_source(single(n, i))["events"])
     e1.record(stream)
     e1.synchronize()
     t_seq = e0.elapsed_time(e1) * 1e-3
-    if rank != 0:
-        return 0
-    hbm, fmax, peak_kind = _peaks()
-    avg_launch = kern_s / args.steps
-    ev_launch = ev_tot / args.steps
-    ops = FP64_OPS_PER_EVENT.get(("batched", args.decomp))
-    fp64_peak = N_SM * FP64_OPS_PER_CLK_PER_SM * fmax * 1e6 / 1e12
-    hbm_ach = B_EVENT * ev_launch / avg_launch / 1e9
-    hbm_roof = {"bound": "hbm", "achieved": hbm_ach, "peak": hbm, "unit": "GB/s", "frac": hbm_ach / hbm,
-                "traffic": None, "what": f"{B_EVENT} algorithmic bytes/event, {peak_kind} peak"}
-    roof = hbm_roof
-    if ops:
-        ach = ops * ev_launch / avg_launch / 1e12
-        roof = {"bound": "alu", "achieved": ach, "peak": fp64_peak, "unit": "TFLOP/s", "frac": ach / fp64_peak,
-                "traffic": None, "what": f"FP64 pipe of the batched transport kernel, {ops:.0f} FP64 ops/event",
-                "peak_source": f"derived: {N_SM} SMs x {FP64_OPS_PER_CLK_PER_SM:g} FP64/clk x {fmax:.0f} MHz"}
-    line = {
-        "metric": "particle-events/s", "value": ev_all / t, "unit": "events/s", "n_gpus": ws, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": BATCH_WORKLOAD, "decomposition": args.decomp, "problems": len(probs),
-                   "histories_per_step": int(hist_step), "tuning_used": {"blocks_per_sm": used[0],
-                   "stash_slots": used[1], "remap_every": used[2]},
-                   "l2": "flushed between steps (512 MB write)"},
-        "histories_per_s": hist_all / t, "roofline": roof, "hbm_roofline": hbm_roof,
-        "e2e": None, "cpu_baseline": None, "gpu_launches": launches, "clocks": sampler.summary(),
-        "first_call_s": t_first,
-        "sequential_single_runs": {"value": ev_seq / t_seq, "unit": "events/s", "seconds": t_seq,
-                                   "speedup_of_batched": (ev_all / t) / (ev_seq / t_seq)},
-        "transport": {"kernel_seconds": kern_s, "launches": args.steps, "avg_launch_ms": 1e3 * avg_launch},
-    }
-    print(json.dumps(line), flush=True)
     for p in probs:
         p.close()
-    if ws > 1:
-        torch.distributed.destroy_process_group()
-    return 0
+    t = sum(times)
+    return {"seconds": t, "events": ev_tot, "histories": float(sum(hist)) * steps, "kernel_seconds": kern_s,
+            "launches": launches, "first_call_s": t_first, "problems": len(specs),
+            "tuning_used": {"blocks_per_sm": used[0], "stash_slots": used[1], "remap_every": used[2]},
+            "events_per_s": ev_tot / t,
+            "sequential_single_runs": {"events_per_s": ev_seq / t_seq, "seconds": t_seq,
+                                       "speedup_of_batched": (ev_tot / t) / (ev_seq / t_seq)}}
 
 
-ADJ_WORKLOAD = ("differentiated 7-group lattice, fission off, uniform source in fuel pins, 1e6 histories: "
-                "forward fixed-source run + derivatives of the 51x51 mesh flux and absorption rate")
-
-
-def run_adjoint_workload(args):
-    """One step = forward fixed-source run + tr_sensitivities (d/dSigma_t,
-    d/dSigma_s, d/dnuSigma_f) of L = g . mesh + absorption rate."""
+def measure_adjoint(torch, tb, inputs, steps, warmup, decomp, seed=1, sampler=None, barrier=None):
+    """One step = forward fixed-source run + tr_sensitivities (derivatives of
+    g . mesh + absorption rate) on the fission-off lattice, 1e6 histories."""
+    import contextlib
     import numpy as np
-    import torch
-
-    ws, rank, local = _dist()
-    if ws > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
-    torch.cuda.set_device(local)
-    from paper_2506_00263_gb300 import binding as tb
-    from paper_2506_00263_gb300 import build as tbuild
-    from paper_2506_00263_gb300 import inputs
-
-    if rank == 0 or not os.path.exists(tbuild.LIB):
-        tbuild.build()
-    if ws > 1:
-        torch.distributed.barrier()
-    decomp = tb.DECOMP_SPLIT if args.decomp == "split" else tb.DECOMP_MONO
     spec = inputs.c5g7_lattice(fission=False)
-    n = 1_000_000
-    opts = tb.RunOpts(n_histories=n, seed=1 + 1000 * rank, scheme=tb.SCHEME_ASYNC, decomposition=decomp)
+    opts = tb.RunOpts(n_histories=1_000_000, seed=seed, scheme=tb.SCHEME_ASYNC, decomposition=decomp)
     prob = tb.Problem(spec)
     M, G = spec.n_materials, spec.n_groups
     g_mesh = torch.tensor(np.random.default_rng(3).uniform(-1, 1, spec.mesh_size), dtype=torch.float64,
@@ -453,18 +416,17 @@ def run_adjoint_workload(args):
         prob.sensitivities(opts, g_mesh.data_ptr(), g_scal.data_ptr(), d_st.data_ptr(), d_ss.data_ptr(),
                            d_nf.data_ptr())
 
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         fwd()
         bwd()
     torch.cuda.synchronize()
-    if ws > 1:
-        torch.distributed.barrier()
+    if barrier:
+        barrier()
     launches0 = tb.kernel_launch_count()
     t_f = t_b = 0.0
     ev = 0
-    sampler = ClockSampler(torch.cuda.current_device())
-    with sampler:
-        for k in range(args.steps):
+    with (sampler or contextlib.nullcontext()):
+        for k in range(steps):
             flush.fill_(float(k))
             e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
             e[0].record(stream)
@@ -477,40 +439,82 @@ def run_adjoint_workload(args):
             t_b += e[1].elapsed_time(e[2]) * 1e-3
             ev += int(r["events"])
     launches = tb.kernel_launch_count() - launches0
-    t = t_f + t_b
+    prob.close()
+    return {"seconds": t_f + t_b, "events": ev, "launches": launches, "forward_ms": 1e3 * t_f / steps,
+            "backward_ms": 1e3 * t_b / steps, "gradient_over_forward": t_b / t_f,
+            "forward_events_per_s": ev / t_f}
+
+
+def _side_line(args, ws, workload, m, t, ev_all, hist_all, sampler, roof, extra):
+    return {"metric": "particle-events/s", "value": ev_all / t, "unit": "events/s", "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": dict({"workload": workload, "decomposition": args.decomp,
+                            "l2": "flushed between steps (512 MB write)"}, **extra),
+            "histories_per_s": hist_all / t if hist_all else None, "roofline": roof, "e2e": None,
+            "cpu_baseline": None, "gpu_launches": m["launches"], "clocks": sampler.summary()}
+
+
+def _hbm_roof(ev, seconds):
+    hbm, _, peak_kind = _peaks()
+    ach = B_EVENT * ev / seconds / 1e9
+    return {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm, "traffic": None,
+            "what": f"{B_EVENT} algorithmic bytes/event, {peak_kind} peak"}
+
+
+def run_batched_workload(args):
+    import torch
+    ws, rank, tb, inputs = _setup(torch)
+    decomp = tb.DECOMP_SPLIT if args.decomp == "split" else tb.DECOMP_MONO
+    sampler = ClockSampler(torch.cuda.current_device())
+    m = measure_batched(torch, tb, inputs, args.steps, args.warmup, decomp, seed=1 + 1000 * rank,
+                        tuning=(args.bps, args.stash, args.remap if args.bps else 0), sampler=sampler,
+                        barrier=torch.distributed.barrier if ws > 1 else None)
+    t, ev_all, hist_all = m["seconds"], float(m["events"]), m["histories"]
     if ws > 1:
         from paper_2506_00263_gb300 import parallel
-        t, ev_all, _ = parallel.reduce_timing(t, float(ev), 0.0, device="cuda")
-    else:
-        ev_all = float(ev)
-    if rank != 0:
-        return 0
-    hbm, fmax, peak_kind = _peaks()
-    hbm_ach = B_EVENT * ev / t_f / 1e9
-    line = {
-        "metric": "particle-events/s", "value": ev_all / t, "unit": "events/s", "n_gpus": ws, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": ADJ_WORKLOAD, "decomposition": args.decomp,
-                   "l2": "flushed between steps (512 MB write)"},
-        "forward_ms": 1e3 * t_f / args.steps, "backward_ms": 1e3 * t_b / args.steps,
-        "backward_over_forward": t_b / t_f,
-        "roofline": {"bound": "hbm", "achieved": hbm_ach, "peak": hbm, "unit": "GB/s", "frac": hbm_ach / hbm,
-                     "traffic": None, "what": f"forward transport, {B_EVENT} algorithmic bytes/event, "
-                                              f"{peak_kind} peak"},
-        "e2e": None, "cpu_baseline": None, "gpu_launches": launches, "clocks": sampler.summary(),
-    }
-    print(json.dumps(line), flush=True)
-    prob.close()
+        t, ev_all, hist_all = parallel.reduce_timing(t, ev_all, hist_all, device="cuda")
+    if rank == 0:
+        line = _side_line(args, ws, BATCH_WORKLOAD, m, t, ev_all, hist_all, sampler,
+                          _hbm_roof(m["events"], m["kernel_seconds"]),
+                          {"problems": m["problems"], "tuning_used": m["tuning_used"]})
+        line.update({"first_call_s": m["first_call_s"], "sequential_single_runs": m["sequential_single_runs"],
+                     "transport": {"kernel_seconds": m["kernel_seconds"], "launches": args.steps}})
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def run_adjoint_workload(args):
+    import torch
+    ws, rank, tb, inputs = _setup(torch)
+    decomp = tb.DECOMP_SPLIT if args.decomp == "split" else tb.DECOMP_MONO
+    sampler = ClockSampler(torch.cuda.current_device())
+    m = measure_adjoint(torch, tb, inputs, args.steps, args.warmup, decomp, seed=1 + 1000 * rank, sampler=sampler,
+                        barrier=torch.distributed.barrier if ws > 1 else None)
+    t, ev_all = m["seconds"], float(m["events"])
+    if ws > 1:
+        from paper_2506_00263_gb300 import parallel
+        t, ev_all, _ = parallel.reduce_timing(t, ev_all, 0.0, device="cuda")
+    if rank == 0:
+        line = _side_line(args, ws, ADJ_WORKLOAD, m, t, ev_all, None, sampler,
+                          _hbm_roof(m["events"], m["forward_ms"] * 1e-3 * args.steps), {})
+        line.update({k: m[k] for k in ("forward_ms", "backward_ms", "gradient_over_forward")})
+        print(json.dumps(line), flush=True)
     if ws > 1:
         torch.distributed.destroy_process_group()
     return 0
 
 
 # FP64 thread-operations (dadd + dmul + dfma, divisions and square roots
-# included as executed) per transport event, from an ncu capture of the
-# transport kernel on the lattice workload.
-FP64_OPS_PER_EVENT = {("async", "split"): 141.0}
+# included as executed) per transport event on the lattice workload, from an
+# ncu capture of the transport kernel
+# (sm__sass_thread_inst_executed_ops_dadd_dmul_dfma_pred_on.sum / events).
+# The arithmetic per event is the same in every scheme (the decomposed one
+# only repeats table loads).
+FP64_OPS_LATTICE = 104.4
+FP64_OPS_PER_EVENT = {(s, d): FP64_OPS_LATTICE for s in ("async", "stack") for d in ("mono", "split")}
 
 
 def _pinned_copy(spec, torch):
@@ -539,15 +543,16 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--scheme", choices=["async", "stack"], default="async")
-    ap.add_argument("--decomp", choices=["split", "mono"], default="split")
+    ap.add_argument("--decomp", choices=["split", "mono"], default="mono")
     ap.add_argument("--n-per-batch", type=int, default=N_PER_BATCH)
     ap.add_argument("--inactive", type=int, default=N_INACTIVE)
     ap.add_argument("--active", type=int, default=N_ACTIVE)
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true", help="skip the gradient and batched side measurements")
     ap.add_argument("--stash", type=int, default=0, help="async: particle slots per block stash (0 = default)")
     ap.add_argument("--bps", type=int, default=0, help="blocks per SM (0 = default)")
-    ap.add_argument("--remap", type=int, default=1, help="monolithic: events between remaps")
+    ap.add_argument("--remap", type=int, default=3, help="monolithic: events between remaps")
     ap.add_argument("--queue", type=int, default=0, help="stack: particles per stack; async: spill links x 32")
     ap.add_argument("--workload", choices=["lattice", "batched", "adjoint"], default="lattice",
                     help="lattice: the k-eigenvalue lattice; batched: 256 box problems in one launch; "

@@ -239,9 +239,9 @@ __device__ __forceinline__ int find_problem(const unsigned long long* off, int n
     return lo;
 }
 
-// Batched launches: add a lane's event counts and scalar scores to its own
-// problem's tallies after every event (lanes of one warp belong to different
-// problems, so nothing is kept across particles).
+// Batched launches: add a lane's event counts and scalar scores to the
+// tallies of the problem they belong to.  A lane accumulates while its
+// particles come from one problem and flushes when the problem changes.
 __device__ __forceinline__ void flush_lane(Acc& acc, const Tallies& T)
 {
     if (acc.flux != 0.0) atomicAdd(T.scal + 0, acc.flux);
@@ -277,6 +277,7 @@ __global__ void __launch_bounds__(256, TR_ASYNC_MIN_BLOCKS) k_async(DevProblem P
     unsigned long long idle_spins = 0;
     uint64_t idle_t0 = 0;    // when this warp last started waiting for work
     bool idle = false;
+    unsigned acc_prob = 0;   // batched: the problem whose scores acc holds
     bool spill_ok = true;   // cleared once the link arena is exhausted
     const int qstart = (int)(blockIdx.x * 7 + (threadIdx.x >> 5)) & (N_GQ - 1);
 
@@ -488,8 +489,11 @@ __global__ void __launch_bounds__(256, TR_ASYNC_MIN_BLOCKS) k_async(DevProblem P
                     const unsigned lid = (unsigned)(id - __ldg(A.hist_off + pi));
                     live = source_particle<CE>(A.probs[pi], RR, lid, p, nullptr, 0);
                     p.prob = (unsigned)pi;
+                    if ((unsigned)pi != acc_prob) {
+                        flush_lane(acc, A.tallies[acc_prob]);
+                        acc_prob = (unsigned)pi;
+                    }
                     acc.ev[EV_SOURCE] += 1u;
-                    flush_lane(acc, A.tallies[pi]);
                 } else {
                     live = source_particle<CE>(P, R, (unsigned)id, p, A.use_src ? &A.src : nullptr, id);
                     acc.ev[EV_SOURCE] += 1u;
@@ -503,16 +507,30 @@ __global__ void __launch_bounds__(256, TR_ASYNC_MIN_BLOCKS) k_async(DevProblem P
             // mode 0 (warp-uniform): lanes beyond a partial link hold no slot and stay idle
             if (slot >= 0) slot_load(st, slot, p);
             __syncwarp();   // reconverge: the event below must run once for all lanes, not per lane group
+            const unsigned em = __ballot_sync(FULLM, slot >= 0);   // the lanes that hold a particle
             if (slot >= 0) {
+                __syncwarp(em);
                 TR_LANES(0);
                 live = true;
                 // batched: the particle's own problem, random-stream tag and tallies
                 const DevProblem& PP = BATCHED ? A.probs[p.prob] : P;
                 const Tallies& TT = BATCHED ? A.tallies[p.prob] : T;
                 RunParams RR = R;
-                if (BATCHED) RR.key1 = R.key1 ^ p.prob;
+                if (BATCHED) {
+                    RR.key1 = R.key1 ^ p.prob;
+                    if (p.prob != acc_prob) {
+                        flush_lane(acc, A.tallies[acc_prob]);
+                        acc_prob = p.prob;
+                    }
+                }
                 if (!SPLIT) {
-                    for (int r = 0; r < R.remap_every && live; ++r) live = mono_event<CE>(PP, RR, p, TT, acc, A.bank, err);
+                    // up to remap_every events; each pass's lane mask is a ballot of the previous one
+                    unsigned lm = em;
+                    for (int r = 0; r < R.remap_every; ++r) {
+                        lm = __ballot_sync(lm, live);
+                        if (!live) break;
+                        live = mono_event<CE>(PP, RR, p, TT, acc, A.bank, err, lm);
+                    }
                     next = live ? Q_STEP : Q_DEAD;
                 } else if (q == Q_STEP) {
                     XS X;
@@ -521,13 +539,12 @@ __global__ void __launch_bounds__(256, TR_ASYNC_MIN_BLOCKS) k_async(DevProblem P
                     step_event<CE>(PP, RR, p, sink, X, xr);
                     next = next_queue_after_step(p);
                 } else if (q == Q_COLLIDE) {
-                    live = split_collide<CE>(PP, RR, p, TT, acc, A.bank, err);
+                    live = split_collide<CE>(PP, RR, p, TT, acc, A.bank, err, em);
                     next = live ? Q_STEP : Q_DEAD;
                 } else {
                     live = split_surface(PP, RR, p, TT, acc, A.bank);
                     next = live ? Q_STEP : Q_DEAD;
                 }
-                if (BATCHED) flush_lane(acc, TT);
                 if (!live) next = Q_DEAD;
             }
             const unsigned died = __popc(__ballot_sync(FULLM, slot >= 0 && !live));
@@ -556,7 +573,8 @@ __global__ void __launch_bounds__(256, TR_ASYNC_MIN_BLOCKS) k_async(DevProblem P
         unlock_stash(st);
     }
     if (idle && lane == 0) atomicSub(&ctl->hungry, 1u);
-    if (!BATCHED) flush_acc(acc, T);
+    if (BATCHED) flush_lane(acc, A.tallies[acc_prob]);
+    else flush_acc(acc, T);
 }
 
 }  // namespace tr

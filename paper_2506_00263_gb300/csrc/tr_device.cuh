@@ -26,13 +26,14 @@ constexpr int ERR_NONE = 0, ERR_CAPACITY = 3, ERR_TIMEOUT = 4, ERR_INVALID = 1;
 // only): per site, the number of warp arrivals and the active lanes summed.
 #ifdef TR_PROFILE_LANES
 static __device__ unsigned long long g_lane_prof[64];
+// Branch-free: every active lane adds (1 for the group's first lane, else 0)
+// and 1, so the counters themselves split no warp.
 #define TR_LANES(site)                                                                          \
     do {                                                                                        \
         const unsigned m_ = __activemask();                                                     \
-        if ((int)(threadIdx.x & 31) == __ffs(m_) - 1) {                                         \
-            atomicAdd(&g_lane_prof[2 * (site)], 1ull);                                          \
-            atomicAdd(&g_lane_prof[2 * (site) + 1], (unsigned long long)__popc(m_));            \
-        }                                                                                       \
+        const unsigned long long lead_ = (int)(threadIdx.x & 31) == __ffs(m_) - 1 ? 1ull : 0ull; \
+        atomicAdd(&g_lane_prof[2 * (site)], lead_);                                             \
+        atomicAdd(&g_lane_prof[2 * (site) + 1], 1ull);                                          \
     } while (0)
 #else
 #define TR_LANES(site) \
@@ -271,10 +272,14 @@ __device__ __forceinline__ bool azimuth_try(const Stream& S, uint32_t n, uint32_
     return dbits(s) <= dbits(1.0) && gt0(s);   // 0 < s <= 1 (s >= +0)
 }
 
-__device__ __forceinline__ void azimuth(const Stream& S, uint32_t n, double& cphi, double& sphi)
+// sm: the lanes of this warp that call azimuth together (a mask every one of
+// them passes, computed by a ballot), regrouped after the rejection loop; 0 =
+// no regrouping.
+__device__ __forceinline__ void azimuth(const Stream& S, uint32_t n, double& cphi, double& sphi, unsigned sm = 0u)
 {
     // the first accepted try; tries 0 and 1 run unconditionally in every lane
     // (both accepted: take try 0), the rare remainder loops
+    TR_LANES(18);
     double a, b, a2, b2, s, a1, b1, a21, b21, s1;
     bool ok = azimuth_try(S, n, 0u, a, b, a2, b2, s);
     const bool ok1 = azimuth_try(S, n, 1u, a1, b1, a21, b21, s1);
@@ -289,6 +294,8 @@ __device__ __forceinline__ void azimuth(const Stream& S, uint32_t n, double& cph
     if (!ok) {
         a = 1.0; b = 0.0; a2 = 1.0; b2 = 0.0; s = 1.0;
     }
+    if (sm) __syncwarp(sm);
+    TR_LANES(19);
     const double inv_s = __drcp_rn(s);
     cphi = (a2 - b2) * inv_s;
     sphi = (2.0 * (a * b)) * inv_s;
@@ -296,6 +303,7 @@ __device__ __forceinline__ void azimuth(const Stream& S, uint32_t n, double& cph
 
 __device__ __forceinline__ void set_reciprocals(Particle& p)
 {
+    TR_LANES(20);
     // (bits << 1) != 0 is x != +-0
     // __drcp_rn is the correctly rounded reciprocal: the same value as 1.0 / x
     p.iu = (dbits(p.u) << 1) ? __drcp_rn(p.u) : 0.0;
@@ -305,11 +313,11 @@ __device__ __forceinline__ void set_reciprocals(Particle& p)
     p.ia = gt0(a) ? __drcp_rn(a) : 0.0;
 }
 
-__device__ __forceinline__ void iso_dir(const Stream& S, uint32_t n, double xi_mu, Particle& p)
+__device__ __forceinline__ void iso_dir(const Stream& S, uint32_t n, double xi_mu, Particle& p, unsigned sm = 0u)
 {
     const double mu = 2.0 * xi_mu - 1.0;
     double cphi, sphi;
-    azimuth(S, n, cphi, sphi);
+    azimuth(S, n, cphi, sphi, sm);
     const double st = sqrt(1.0 - mu * mu);
     p.u = mu;
     p.v = st * cphi;
@@ -474,13 +482,17 @@ __device__ __forceinline__ void xs_lookup(const DevProblem& P, const Particle& p
 
 __device__ __forceinline__ int sample_chi(const DevProblem& P, int m, double xi)
 {
+    // the first g with t < cc[g]; if none (rounding), the last group with
+    // chi > 0, else G - 1.  Every lane runs all G steps (no early exit that
+    // would split the warp).
     const double* cc = P.cum_chi + m * P.G;
     const double t = xi * __ldg(cc + P.G - 1);
-    for (int g = 0; g < P.G; ++g)
-        if (t < __ldg(cc + g)) return g;
-    for (int g = P.G - 1; g >= 0; --g)
-        if (__ldg(P.chi + m * P.G + g) > 0.0) return g;
-    return P.G - 1;
+    int sel = -1, last = P.G - 1;
+    for (int g = 0; g < P.G; ++g) {
+        sel = (sel < 0 && t < __ldg(cc + g)) ? g : sel;
+        last = __ldg(P.chi + m * P.G + g) > 0.0 ? g : last;
+    }
+    return sel >= 0 ? sel : last;
 }
 
 __device__ __forceinline__ double cdf_sample(const DevProblem& P, double xi)

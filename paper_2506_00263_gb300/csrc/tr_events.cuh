@@ -56,18 +56,12 @@ struct MeshWeighted {
     __device__ __forceinline__ void operator()(int i, double l) { f += __ldg(g + i) * l; }
 };
 
+// The generic walk (segments that leave their one-cell fast path).
 template <class Op>
-__device__ __forceinline__ void mesh_tally(const DevProblem& P, Op& op, const Particle& p, double x0, double y0,
-                                           double z0, double L, int goff)
+__device__ __forceinline__ void mesh_tally_dda(const DevProblem& P, Op& op, const Particle& p, double x0, double y0,
+                                               double z0, double L, int goff)
 {
-    const int vx = __ldg(P.cell2vox + cell_i(p.cell));
-    const int vy = __ldg(P.cell2vox + P.nx + cell_j(p.cell));
-    const int vz = __ldg(P.cell2vox + P.nx + P.ny + cell_k(p.cell));
     const int nx = P.mesh_n[0], ny = P.mesh_n[1], nz = P.mesh_n[2];
-    if ((vx | vy | vz) >= 0) {
-        op(goff + (vz * ny + vy) * nx + vx, L);
-        return;
-    }
     const double INF = __longlong_as_double(0x7FF0000000000000ll);
     double t0 = 0.0, t1 = L;
     // clip per axis (a zero component keeps the start point's slab test)
@@ -133,6 +127,20 @@ __device__ __forceinline__ void mesh_tally(const DevProblem& P, Op& op, const Pa
     }
 }
 
+template <class Op>
+__device__ __forceinline__ void mesh_tally(const DevProblem& P, Op& op, const Particle& p, double x0, double y0,
+                                           double z0, double L, int goff)
+{
+    const int vx = __ldg(P.cell2vox + cell_i(p.cell));
+    const int vy = __ldg(P.cell2vox + P.nx + cell_j(p.cell));
+    const int vz = __ldg(P.cell2vox + P.nx + P.ny + cell_k(p.cell));
+    if ((vx | vy | vz) >= 0) {
+        op(goff + (vz * P.mesh_n[1] + vy) * P.mesh_n[0] + vx, L);
+        return;
+    }
+    mesh_tally_dda(P, op, p, x0, y0, z0, L, goff);
+}
+
 // Energy-bin flux tally per material: bin = largest b with e[b] <= E < e[b+1].
 __device__ __forceinline__ void energy_tally(const DevProblem& P, double* __restrict__ etal, int m, double E, double L)
 {
@@ -153,7 +161,7 @@ template <bool CE>
 __device__ __forceinline__ bool source_particle(const DevProblem& P, const RunParams& R, unsigned id, Particle& p,
                                                 const Bank* site, unsigned long long site_idx)
 {
-    TR_LANES(4);
+    TR_LANES(23);
     const Stream S = make_stream(R, id);
     const uint4 b0 = S.block(0u, BLK_MAIN);
     const double xi_mu = u01(b0.x, b0.y), xi_ge = u01(b0.z, b0.w);
@@ -188,7 +196,7 @@ __device__ __forceinline__ bool source_particle(const DevProblem& P, const RunPa
     } else {
         uint32_t t = 0;
         for (; t < N_POS; ++t) {
-            TR_LANES(5);
+            TR_LANES(24);
             const uint4 a = S.block(0u, BLK_POS + 2u * t);
             const uint4 b = S.block(0u, BLK_POS + 2u * t + 1u);
             p.x = P.src_lo[0] + u01(a.x, a.y) * (P.src_hi[0] - P.src_lo[0]);
@@ -246,6 +254,7 @@ __device__ __forceinline__ void step_event(const DevProblem& P, const RunParams&
     const uint4 b0 = S.block(p.n, BLK_MAIN);
     xi_react = u01(b0.z, b0.w);
     const double dcol = (-tr_log(u01(b0.x, b0.y))) * X.inv_st;
+    TR_LANES(2);
 
     const double INF = __longlong_as_double(0x7FF0000000000000ll);
     const int i = cell_i(c), j = cell_j(c), k = cell_k(c);
@@ -274,6 +283,7 @@ __device__ __forceinline__ void step_event(const DevProblem& P, const RunParams&
         const bool hit = gt0(a) && (in || (lt0(kk) && ge0(disc)));
         dcyl = hit ? clamp0(in ? d_in : d_out) : INF;
     }
+    TR_LANES(3);
     unsigned flags = 0u;
     double ds;
     if (in) {
@@ -300,6 +310,7 @@ __device__ __forceinline__ void step_event(const DevProblem& P, const RunParams&
     }
     const bool collided = lt_nn(dcol, ds);
     const bool escape = !collided && dbits(ds) == dbits(INF);   // no surface ahead: the particle escapes
+    TR_LANES(4);
     if (!escape) {
         const double dist = collided ? dcol : ds;
         const double x0 = p.x, y0 = p.y, z0 = p.z;
@@ -308,6 +319,7 @@ __device__ __forceinline__ void step_event(const DevProblem& P, const RunParams&
         p.z = p.z + dist * p.w;
         sink.template segment<CE>(P, p, x0, y0, z0, dist, m, X);
     }
+    TR_LANES(5);
     p.pend = escape ? PEND_ESCAPE : (collided ? PEND_COLLIDE : flags);
 }
 
@@ -338,68 +350,77 @@ __device__ __forceinline__ void bank_sites(const DevProblem& P, const RunParams&
     }
 }
 
+// cm: the lanes of this warp that run the collision together (a mask every
+// one of them passes, from a ballot), or 0.  With a mask the colliding lanes
+// are regrouped after the fission banking and the reaction selection (which
+// runs every candidate in every lane instead of stopping at the first hit),
+// and the scattering lanes after the azimuth loop, so that the FP64 work of
+// the direction sampling is issued once for all of them: the FP64 pipe
+// charges a warp instruction the same however few lanes are active.
 template <bool CE>
 __device__ __forceinline__ int collide_event(const DevProblem& P, const RunParams& R, Particle& p, const XS& X,
-                                             double xi_react, const Bank& B, ErrorWord* err)
+                                             double xi_react, const Bank& B, ErrorWord* err, unsigned cm = 0u)
 {
-    TR_LANES(2);
+    TR_LANES(16);
     const Stream S = make_stream(R, p.id);
     const int m = material(P, p.cell);
     if (!CE) {
         if (R.eig && gt0(X.nsf)) bank_sites(P, R, S, p, m, X, B, err);
+        if (cm) __syncwarp(cm);
+        // the first g' with xi * Sigma_t below the cumulative Sigma_s; none: absorption
         const double t = xi_react * X.st;
         const double* cs = P.cum_s + (m * P.G + p.g) * P.G;
         int gp = -1;
-        for (int h = 0; h < P.G; ++h)
-            if (lt_nn(t, __ldg(cs + h))) {
-                gp = h;
-                break;
-            }
+        for (int h = 0; h < P.G; ++h) gp = (gp < 0 && lt_nn(t, __ldg(cs + h))) ? h : gp;
+        const unsigned sm = cm ? __ballot_sync(cm, gp >= 0) : 0u;
         if (gp < 0) return EV_ABSORB;
+        TR_LANES(17);
         p.g = gp;
-        iso_dir(S, p.n, S.first(p.n, BLK_ANGLE), p);
+        iso_dir(S, p.n, S.first(p.n, BLK_ANGLE), p, sm);
         return EV_SCATTER;
     }
     // continuous energy: repeat the lookup terms in order and pick the first
     // (nuclide, reaction) with xi * sigma_t below the running sum; if none
-    // (rounding), the last term with a positive value
+    // (rounding), the last term with a positive value.  Nuclides absent from
+    // the material (density <= 0) add nothing.
     const double t = xi_react * X.st;
     const int u = union_index(P, p.E);
+    if (cm) __syncwarp(cm);
     double cum = 0.0;
     int sel_n = -1, sel_r = -1, last_n = -1, last_r = -1;
-    for (int n = 0; n < P.n_nuc && sel_n < 0; ++n) {
+    for (int n = 0; n < P.n_nuc; ++n) {
         const double N = __ldg(P.dens + m * P.n_nuc + n);
-        if (!(N > 0.0)) continue;
+        const bool use = N > 0.0;
         const int r0 = __ldg(P.uptr + (long long)u * P.n_nuc + n);
         const double f = (p.E - __ldg(P.nuc_e + r0)) * __ldg(P.nuc_inv_de + r0);
         for (int r = 0; r < 3; ++r) {
             const double s0 = __ldg(P.nuc_sig + 3 * (long long)r0 + r);
             const double s1 = __ldg(P.nuc_sig + 3 * (long long)(r0 + 1) + r);
             const double mac = N * (s0 + f * (s1 - s0));
-            cum = cum + mac;
-            if (mac > 0.0) {
-                last_n = n;
-                last_r = r;
-            }
-            if (t < cum) {
-                sel_n = n;
-                sel_r = r;
-                break;
-            }
+            const double c2 = use ? cum + mac : cum;
+            const bool pos = use && mac > 0.0;
+            last_n = pos ? n : last_n;
+            last_r = pos ? r : last_r;
+            const bool take = use && sel_n < 0 && t < c2;
+            sel_n = take ? n : sel_n;
+            sel_r = take ? r : sel_r;
+            cum = c2;
         }
     }
     if (sel_n < 0) {
         sel_n = last_n;
         sel_r = last_r;
     }
-    if (sel_n < 0 || sel_r != 0) return EV_ABSORB;
+    const bool scatter = !(sel_n < 0 || sel_r != 0);
+    const unsigned sm = cm ? __ballot_sync(cm, scatter) : 0u;
+    if (!scatter) return EV_ABSORB;
     const double A = __ldg(P.awr + sel_n);
     const double mu_cm = 2.0 * S.first(p.n, BLK_ANGLE) - 1.0;
     const double q = (A * A + (2.0 * A) * mu_cm) + 1.0;
     const double E1 = (p.E * q) * __ldg(P.inv_ap1sq + sel_n);
     const double mu = (1.0 + A * mu_cm) / sqrt(q);
     double cphi, sphi;
-    azimuth(S, p.n, cphi, sphi);
+    azimuth(S, p.n, cphi, sphi, sm);
     rotate(p, mu, cphi, sphi);
     p.E = E1;
     if (p.E < P.e_cut) return EV_CUTOFF;
@@ -411,7 +432,7 @@ __device__ __forceinline__ int collide_event(const DevProblem& P, const RunParam
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ int surface_event(const DevProblem& P, Particle& p)
 {
-    TR_LANES(3);
+    TR_LANES(21);
     const unsigned f = p.pend;
     if (f & PEND_ESCAPE) return EV_LEAK;
     if (f & PEND_CYL) {
@@ -485,6 +506,7 @@ __device__ __forceinline__ int surface_event(const DevProblem& P, Particle& p)
 __device__ __forceinline__ bool finish_event(const DevProblem& P, const RunParams& R, Particle& p, int type,
                                              const Tallies& T, Acc& acc, const Bank& B)
 {
+    TR_LANES(22);
     acc.ev[type] += 1u;
     p.n += 1u;
     bool alive = (type == EV_SCATTER || type == EV_SURF_INTERNAL || type == EV_SURF_REFLECT);
@@ -505,17 +527,20 @@ __device__ __forceinline__ bool finish_event(const DevProblem& P, const RunParam
 }
 
 // One monolithic event (step followed by collision or surface crossing).
+// em: the lanes of this warp that run this event together (from a ballot), or 0.
 template <bool CE>
 __device__ __forceinline__ bool mono_event(const DevProblem& P, const RunParams& R, Particle& p, const Tallies& T,
-                                           Acc& acc, const Bank& B, ErrorWord* err)
+                                           Acc& acc, const Bank& B, ErrorWord* err, unsigned em = 0u)
 {
     TR_LANES(10);
     XS X;
     double xi_react;
     FwdSink sink{T, acc};
     step_event<CE>(P, R, p, sink, X, xi_react);
+    const bool coll = p.pend == PEND_COLLIDE;
+    const unsigned cm = em ? __ballot_sync(em, coll) : 0u;
     int type;
-    if (p.pend == PEND_COLLIDE) type = collide_event<CE>(P, R, p, X, xi_react, B, err);
+    if (coll) type = collide_event<CE>(P, R, p, X, xi_react, B, err, cm);
     else type = surface_event(P, p);
     return finish_event(P, R, p, type, T, acc, B);
 }
@@ -523,14 +548,14 @@ __device__ __forceinline__ bool mono_event(const DevProblem& P, const RunParams&
 // Decomposed collision event: repeats the (cheap) lookup and the reaction draw.
 template <bool CE>
 __device__ __forceinline__ bool split_collide(const DevProblem& P, const RunParams& R, Particle& p, const Tallies& T,
-                                             Acc& acc, const Bank& B, ErrorWord* err)
+                                             Acc& acc, const Bank& B, ErrorWord* err, unsigned em = 0u)
 {
     XS X;
     const int m = material(P, p.cell);
     xs_lookup<CE>(P, p, m, X);
     const Stream S = make_stream(R, p.id);
     const uint4 b0 = S.block(p.n, BLK_MAIN);
-    const int type = collide_event<CE>(P, R, p, X, u01(b0.z, b0.w), B, err);
+    const int type = collide_event<CE>(P, R, p, X, u01(b0.z, b0.w), B, err, em);
     return finish_event(P, R, p, type, T, acc, B);
 }
 

@@ -69,8 +69,9 @@ __global__ void __launch_bounds__(256) k_stack_mono(DevProblem P, RunParams R, S
             }
             __syncwarp();
             for (int r = 0; r < R.remap_every; ++r) {
-                if (!__any_sync(FULL, live)) break;
-                if (live) live = mono_event<CE>(P, R, p, T, acc, A.bank, err);
+                const unsigned em = __ballot_sync(FULL, live);   // every lane of the warp is here
+                if (!em) break;
+                if (live) live = mono_event<CE>(P, R, p, T, acc, A.bank, err, em);
             }
         } else {
             // make_work: the input stack is fully claimed; create sources
@@ -127,6 +128,7 @@ __global__ void __launch_bounds__(256) k_stack_split(DevProblem P, RunParams R, 
             const unsigned long long i = base - start[q] + lane;
             if (i < cnt[q]) load_particle(A.in[q], i, p, CE);
             __syncwarp();
+            const unsigned em = __ballot_sync(FULL, i < cnt[q]);   // the lanes that hold a particle
             if (i < cnt[q]) {
                 live = true;
                 if (q == Q_STEP) {
@@ -136,7 +138,7 @@ __global__ void __launch_bounds__(256) k_stack_split(DevProblem P, RunParams R, 
                     step_event<CE>(P, R, p, sink, X, xr);
                     dst = next_queue_after_step(p);
                 } else if (q == Q_COLLIDE) {
-                    live = split_collide<CE>(P, R, p, T, acc, A.bank, err);
+                    live = split_collide<CE>(P, R, p, T, acc, A.bank, err, em);
                 } else {
                     live = split_surface(P, R, p, T, acc, A.bank);
                 }
