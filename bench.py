@@ -117,7 +117,7 @@ def _cpu_baseline(seconds_budget: float = 15.0):
     import oracle
     from paper_2506_00263_gb300 import inputs
     p = inputs.c5g7_lattice()
-    nper, ni, na = 100_000, 2, 8
+    nper, ni, na = 100_000, 4, 36       # about 10-20 s on one host core
     t0 = time.perf_counter()
     r = oracle.power_iteration(p, nper, ni, na, seed=1)
     dt = time.perf_counter() - t0
@@ -232,15 +232,17 @@ def run_ours(args):
     fp64_peak = N_SM * FP64_OPS_PER_CLK_PER_SM * fmax * 1e6 / 1e12     # TFLOP/s
     if fp64_ops_per_event:
         ach = fp64_ops_per_event * ev_per_launch / avg_launch / 1e12
+        traffic = TRAFFIC_PER_LAUNCH.get((args.scheme, args.decomp, opts.remap_every, args.n_per_batch))
         roof = {"bound": "alu", "achieved": ach, "peak": fp64_peak, "unit": "TFLOP/s", "frac": ach / fp64_peak,
-                "traffic": None, "what": "FP64 pipe (add/mul/fma) of the transport kernel, "
+                "traffic": traffic, "what": "FP64 pipe (add/mul/fma) of the transport kernel, "
                                          f"{fp64_ops_per_event:.0f} FP64 ops/event",
                 "peak_source": f"derived: {N_SM} SMs x {FP64_OPS_PER_CLK_PER_SM:g} FP64/clk x {fmax:.0f} MHz"}
     else:
         roof = None
     hbm_ach = B_EVENT * ev_per_launch / avg_launch / 1e9
     hbm_roof = {"bound": "hbm", "achieved": hbm_ach, "peak": hbm, "unit": "GB/s", "frac": hbm_ach / hbm,
-                "traffic": None, "what": f"{B_EVENT} algorithmic bytes/event, {peak_kind} peak"}
+                "traffic": TRAFFIC_PER_LAUNCH.get((args.scheme, args.decomp, opts.remap_every, args.n_per_batch)),
+                "what": f"{B_EVENT} algorithmic bytes/event, {peak_kind} peak"}
     if roof is None:
         roof = hbm_roof
 
@@ -513,7 +515,11 @@ def run_adjoint_workload(args):
 # (sm__sass_thread_inst_executed_ops_dadd_dmul_dfma_pred_on.sum / events).
 # The arithmetic per event is the same in every scheme (the decomposed one
 # only repeats table loads).
-FP64_OPS_LATTICE = 104.4
+FP64_OPS_LATTICE = 81.9
+# DRAM bytes (read + write) of one transport launch (one 1e6-history lattice
+# batch, asynchronous monolithic scheme, 3 events between remaps), from one ncu
+# capture of the current kernel: dram__bytes_read.sum + dram__bytes_write.sum.
+TRAFFIC_PER_LAUNCH = {("async", "mono", 3, 1_000_000): 51.44e6}
 FP64_OPS_PER_EVENT = {(s, d): FP64_OPS_LATTICE for s in ("async", "stack") for d in ("mono", "split")}
 
 

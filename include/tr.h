@@ -20,7 +20,8 @@
  *    cudaMallocAsync/cudaFreeAsync on the context stream when they are NULL)
  *    and all work is enqueued on the context stream.  Functions that return
  *    results on the host synchronise that stream before returning.
- *  - Floating point: IEEE binary64 everywhere, FMA contraction disabled.
+ *  - Floating point: IEEE binary64 everywhere; no implicit FMA contraction,
+ *    fused multiply-adds only where the arithmetic contract writes them.
  */
 #ifndef TR_H
 #define TR_H

@@ -9,7 +9,12 @@
  * Build with contraction off (gcc -O2 -ffp-contract=off): every floating-
  * point operation below is one IEEE-754 binary64 operation, evaluated in the
  * order written, so that the GPU library (which implements the same contract
- * independently, also without FMA contraction) takes every branch the same way.
+ * independently, also without implicit contraction) takes every branch the
+ * same way.  Where the contract fuses a product with a sum, the code says so
+ * with an explicit fma() (one correctly rounded operation, the same on every
+ * machine): the log polynomial and its exponent term, the move, the pin
+ * terms, the squared transverse direction, the cylinder discriminant, and
+ * 1 - mu^2 in the direction formulas.
  *
  * What the paper fixes, and what is a reading:
  *  - The transport loop is split into events: a source event (make_work),
@@ -96,8 +101,9 @@ static void rng_block(uint64_t seed, uint32_t tag, uint64_t id, uint32_t n, uint
 /* ------------------------------------------------------------------------ */
 /* Natural logarithm of a positive normal double (the contract's own):       */
 /* x = 2^e m with m in [sqrt(1/2), sqrt(2)); s = (m-1)/(m+1);                 */
-/* log m = 2 atanh(s) = 2 s sum_{j=0..9} s^(2j)/(2j+1) (Horner in s^2);      */
-/* log x = e*LN2_HI + (log m + e*LN2_LO) with ln 2 split at 40 bits.          */
+/* log m = 2 atanh(s) = 2 s sum_{j=0..9} s^(2j)/(2j+1) (Horner in s^2, each  */
+/* step one fma); log x = fma(e, LN2_HI, fma(e, LN2_LO, log m)) with ln 2     */
+/* split at 40 bits (e*LN2_HI is exact).                                       */
 /* ------------------------------------------------------------------------ */
 static double bits_to_double(uint64_t b) { double d; memcpy(&d, &b, 8); return d; }
 static uint64_t double_to_bits(double d) { uint64_t b; memcpy(&b, &d, 8); return b; }
@@ -117,18 +123,18 @@ double orc_log(double x)
     double s = (m - 1.0) / (m + 1.0);
     double z = s * s;
     double p = 1.0 / 19.0;
-    p = p * z + 1.0 / 17.0;
-    p = p * z + 1.0 / 15.0;
-    p = p * z + 1.0 / 13.0;
-    p = p * z + 1.0 / 11.0;
-    p = p * z + 1.0 / 9.0;
-    p = p * z + 1.0 / 7.0;
-    p = p * z + 1.0 / 5.0;
-    p = p * z + 1.0 / 3.0;
-    p = p * z + 1.0;
+    p = fma(p, z, 1.0 / 17.0);
+    p = fma(p, z, 1.0 / 15.0);
+    p = fma(p, z, 1.0 / 13.0);
+    p = fma(p, z, 1.0 / 11.0);
+    p = fma(p, z, 1.0 / 9.0);
+    p = fma(p, z, 1.0 / 7.0);
+    p = fma(p, z, 1.0 / 5.0);
+    p = fma(p, z, 1.0 / 3.0);
+    p = fma(p, z, 1.0);
     double r = (s + s) * p;
     double de = (double)e;
-    return de * LN2_HI + (r + de * LN2_LO);
+    return fma(de, LN2_HI, fma(de, LN2_LO, r));
 }
 
 /* ------------------------------------------------------------------------ */
@@ -161,7 +167,7 @@ void orc_iso_dir(uint64_t seed, uint32_t tag, uint64_t id, uint32_t n, double xi
     double mu = 2.0 * xi_mu - 1.0;
     double cphi, sphi;
     azimuth(seed, tag, id, n, &cphi, &sphi);
-    double st = sqrt(1.0 - mu * mu);
+    double st = sqrt(fma(-mu, mu, 1.0));
     dir[0] = mu;
     dir[1] = st * cphi;
     dir[2] = st * sphi;
@@ -172,7 +178,7 @@ void orc_iso_dir(uint64_t seed, uint32_t tag, uint64_t id, uint32_t n, double xi
  * direction is taken about the z axis. */
 void orc_rotate(const double d[3], double mu, double cphi, double sphi, double out[3])
 {
-    double t = 1.0 - mu * mu;
+    double t = fma(-mu, mu, 1.0);
     if (t < 0.0) t = 0.0;
     double st = sqrt(t);
     double u = d[0], v = d[1], w = d[2];
@@ -182,7 +188,7 @@ void orc_rotate(const double d[3], double mu, double cphi, double sphi, double o
         out[2] = (w > 0.0) ? mu : -mu;
         return;
     }
-    double sq = sqrt(1.0 - w * w);
+    double sq = sqrt(fma(-w, w, 1.0));
     double a1 = st / sq;
     out[0] = mu * u + a1 * ((u * w) * cphi - v * sphi);
     out[1] = mu * v + a1 * ((v * w) * cphi + u * sphi);
@@ -371,8 +377,8 @@ static void pin_terms(const orc_problem *P, const particle *p, double *c, double
     double yc = 0.5 * (P->yp[p->ci[1]] + P->yp[p->ci[1] + 1]);
     *dx = p->x[0] - xc;
     *dy = p->x[1] - yc;
-    *c = ((*dx) * (*dx) + (*dy) * (*dy)) - P->pin_r * P->pin_r;
-    *k = (*dx) * p->d[0] + (*dy) * p->d[1];
+    *c = fma(*dx, *dx, (*dy) * (*dy)) - P->pin_r * P->pin_r;
+    *k = fma(*dx, p->d[0], (*dy) * p->d[1]);
 }
 
 static int has_pin(const orc_problem *P, const particle *p) { return P->pin_mat[cell_lin(P, p)] >= 0; }
@@ -790,15 +796,15 @@ static void event(ctx *C, particle *p)
     if (pin) {
         double c, k, dx, dy;
         pin_terms(P, p, &c, &k, &dx, &dy);
-        double a = p->d[0] * p->d[0] + p->d[1] * p->d[1];
+        double a = fma(p->d[0], p->d[0], p->d[1] * p->d[1]);
         if (a > 0.0) {
             double inv_a = 1.0 / a;
             if (p->in) {
-                double disc = k * k - a * c;
+                double disc = fma(k, k, -(a * c));
                 if (disc < 0.0) disc = 0.0;
                 dcyl = (sqrt(disc) - k) * inv_a;
             } else if (k < 0.0) {
-                double disc = k * k - a * c;
+                double disc = fma(k, k, -(a * c));
                 if (disc >= 0.0) dcyl = ((-k) - sqrt(disc)) * inv_a;
             }
         }
@@ -829,9 +835,9 @@ static void event(ctx *C, particle *p)
         p->n++;
         return;
     }
-    p->x[0] = p->x[0] + dist * p->d[0];
-    p->x[1] = p->x[1] + dist * p->d[1];
-    p->x[2] = p->x[2] + dist * p->d[2];
+    p->x[0] = fma(dist, p->d[0], p->x[0]);
+    p->x[1] = fma(dist, p->d[1], p->x[1]);
+    p->x[2] = fma(dist, p->d[2], p->x[2]);
     score_segment(C, p, p0, dist, m, &X);
     p->track += dist;
     if (C->recording) record_event(C, p, m, collided, dist, weighted_segment(C, p, p0, dist, &X));

@@ -1,8 +1,10 @@
 """Build the CUDA library libtr.so in-tree for sm_103a.
 
-Each translation unit compiles in parallel with nvcc; FMA contraction is off
-in device code (-fmad=false) and host code (-ffp-contract=off) so every
-double operation is one IEEE-754 operation in the written order.
+Each translation unit compiles in parallel with nvcc; implicit FMA
+contraction is off in device code (-fmad=false) and host code
+(-ffp-contract=off) so every double operation is one IEEE-754 operation in the
+written order, and fused multiply-adds appear only where the code writes
+__fma_rn.
 """
 from __future__ import annotations
 

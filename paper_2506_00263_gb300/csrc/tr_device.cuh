@@ -1,8 +1,13 @@
 // tr_device.cuh -- device-side problem data, particle state and per-event physics.
 //
 // Every floating-point operation that decides a branch follows the library's
-// arithmetic contract: IEEE binary64, evaluated in the written order, with FMA
-// contraction disabled (-fmad=false).  Where a result is produced with integer
+// arithmetic contract: IEEE binary64, evaluated in the written order, with no
+// implicit contraction (-fmad=false); where the contract fuses a product with
+// a sum the code calls __fma_rn (one correctly rounded operation): the log
+// polynomial and its exponent term, the move, the pin terms, the squared
+// transverse direction, the cylinder discriminant and 1 - mu^2 in the
+// direction formulas.  Each fused operation also saves an FP64 instruction.
+// Where a result is produced with integer
 // bit manipulation instead of a double instruction (uniforms, exponent
 // extraction, comparisons of non-negative doubles), the integer form yields
 // exactly the value the double form would; GB300 issues FP64 at a small
@@ -241,18 +246,19 @@ __device__ __forceinline__ double tr_log(double x)
     const double s = (m - 1.0) / (m + 1.0);
     const double z = s * s;
     double p = 1.0 / 19.0;
-    p = p * z + 1.0 / 17.0;
-    p = p * z + 1.0 / 15.0;
-    p = p * z + 1.0 / 13.0;
-    p = p * z + 1.0 / 11.0;
-    p = p * z + 1.0 / 9.0;
-    p = p * z + 1.0 / 7.0;
-    p = p * z + 1.0 / 5.0;
-    p = p * z + 1.0 / 3.0;
-    p = p * z + 1.0;
+    p = __fma_rn(p, z, 1.0 / 17.0);
+    p = __fma_rn(p, z, 1.0 / 15.0);
+    p = __fma_rn(p, z, 1.0 / 13.0);
+    p = __fma_rn(p, z, 1.0 / 11.0);
+    p = __fma_rn(p, z, 1.0 / 9.0);
+    p = __fma_rn(p, z, 1.0 / 7.0);
+    p = __fma_rn(p, z, 1.0 / 5.0);
+    p = __fma_rn(p, z, 1.0 / 3.0);
+    p = __fma_rn(p, z, 1.0);
     const double r = (s + s) * p;
     const double de = (double)e;
-    return de * __longlong_as_double(0x3FE62E42FEFA4000ll) + (r + de * __longlong_as_double((long long)0xBD48432A1B0E2634ull));
+    return __fma_rn(de, __longlong_as_double(0x3FE62E42FEFA4000ll),
+                    __fma_rn(de, __longlong_as_double((long long)0xBD48432A1B0E2634ull), r));
 }
 
 // ---------------------------------------------------------------------------
@@ -264,8 +270,8 @@ __device__ __forceinline__ bool azimuth_try(const Stream& S, uint32_t n, uint32_
                                             double& b2, double& s)
 {
     const uint4 r = S.block(n, BLK_AZIMUTH + t);
-    a = 2.0 * u01(r.x, r.y) - 1.0;
-    b = 2.0 * u01(r.z, r.w) - 1.0;
+    a = __fma_rn(2.0, u01(r.x, r.y), -1.0);   // 2 xi is exact: the same value as 2.0 * xi - 1.0
+    b = __fma_rn(2.0, u01(r.z, r.w), -1.0);
     a2 = a * a;
     b2 = b * b;
     s = a2 + b2;
@@ -309,16 +315,16 @@ __device__ __forceinline__ void set_reciprocals(Particle& p)
     p.iu = (dbits(p.u) << 1) ? __drcp_rn(p.u) : 0.0;
     p.iv = (dbits(p.v) << 1) ? __drcp_rn(p.v) : 0.0;
     p.iw = (dbits(p.w) << 1) ? __drcp_rn(p.w) : 0.0;
-    const double a = p.u * p.u + p.v * p.v;
+    const double a = __fma_rn(p.u, p.u, p.v * p.v);
     p.ia = gt0(a) ? __drcp_rn(a) : 0.0;
 }
 
 __device__ __forceinline__ void iso_dir(const Stream& S, uint32_t n, double xi_mu, Particle& p, unsigned sm = 0u)
 {
-    const double mu = 2.0 * xi_mu - 1.0;
+    const double mu = __fma_rn(2.0, xi_mu, -1.0);   // 2 xi is exact: the same value as 2.0 * xi - 1.0
     double cphi, sphi;
     azimuth(S, n, cphi, sphi, sm);
-    const double st = sqrt(1.0 - mu * mu);
+    const double st = sqrt(__fma_rn(-mu, mu, 1.0));
     p.u = mu;
     p.v = st * cphi;
     p.w = st * sphi;
@@ -327,7 +333,7 @@ __device__ __forceinline__ void iso_dir(const Stream& S, uint32_t n, double xi_m
 
 __device__ __forceinline__ void rotate(Particle& p, double mu, double cphi, double sphi)
 {
-    double t = 1.0 - mu * mu;
+    double t = __fma_rn(-mu, mu, 1.0);
     if (t < 0.0) t = 0.0;
     const double st = sqrt(t);
     const double u = p.u, v = p.v, w = p.w;
@@ -336,7 +342,7 @@ __device__ __forceinline__ void rotate(Particle& p, double mu, double cphi, doub
         p.v = st * sphi;
         p.w = (w > 0.0) ? mu : -mu;
     } else {
-        const double sq = sqrt(1.0 - w * w);
+        const double sq = sqrt(__fma_rn(-w, w, 1.0));
         const double a1 = st / sq;
         p.u = mu * u + a1 * ((u * w) * cphi - v * sphi);
         p.v = mu * v + a1 * ((v * w) * cphi + u * sphi);
@@ -375,8 +381,8 @@ __device__ __forceinline__ void pin_terms(const DevProblem& P, const Particle& p
 {
     const double dx = p.x - __ldg(P.xc + cell_i(p.cell));
     const double dy = p.y - __ldg(P.yc + cell_j(p.cell));
-    c = (dx * dx + dy * dy) - P.r2;
-    k = dx * p.u + dy * p.v;
+    c = __fma_rn(dx, dx, dy * dy) - P.r2;
+    k = __fma_rn(dx, p.u, dy * p.v);
 }
 
 // largest i in [0, n-1] with pl[i] <= x; one cell down when x sits exactly on

@@ -228,8 +228,8 @@ struct FwdSink {
                                             double dist, int m, const XS& X)
     {
         acc.flux += dist;
-        acc.absn += dist * X.sa;
-        acc.prod += dist * X.nsf;
+        acc.absn = __fma_rn(dist, X.sa, acc.absn);   // tallies: compared within tolerance, fused freely
+        acc.prod = __fma_rn(dist, X.nsf, acc.prod);
         if (P.has_mesh && gt0(dist)) {
             const int goff = (!CE && P.by_group) ? p.g * P.mesh_vox : 0;
             MeshAtomic op{T.mesh};
@@ -275,8 +275,8 @@ __device__ __forceinline__ void step_event(const DevProblem& P, const RunParams&
         // then max(disc, 0) = disc
         double cc, kk;
         pin_terms(P, p, cc, kk);
-        const double a = p.u * p.u + p.v * p.v;
-        const double disc = kk * kk - a * cc;
+        const double a = __fma_rn(p.u, p.u, p.v * p.v);
+        const double disc = __fma_rn(kk, kk, -(a * cc));
         const double sq = sqrt(lt0(disc) ? 0.0 : disc);
         const double d_in = (sq - kk) * p.ia;
         const double d_out = ((-kk) - sq) * p.ia;
@@ -314,9 +314,9 @@ __device__ __forceinline__ void step_event(const DevProblem& P, const RunParams&
     if (!escape) {
         const double dist = collided ? dcol : ds;
         const double x0 = p.x, y0 = p.y, z0 = p.z;
-        p.x = p.x + dist * p.u;
-        p.y = p.y + dist * p.v;
-        p.z = p.z + dist * p.w;
+        p.x = __fma_rn(dist, p.u, p.x);
+        p.y = __fma_rn(dist, p.v, p.y);
+        p.z = __fma_rn(dist, p.w, p.z);
         sink.template segment<CE>(P, p, x0, y0, z0, dist, m, X);
     }
     TR_LANES(5);
@@ -415,7 +415,7 @@ __device__ __forceinline__ int collide_event(const DevProblem& P, const RunParam
     const unsigned sm = cm ? __ballot_sync(cm, scatter) : 0u;
     if (!scatter) return EV_ABSORB;
     const double A = __ldg(P.awr + sel_n);
-    const double mu_cm = 2.0 * S.first(p.n, BLK_ANGLE) - 1.0;
+    const double mu_cm = __fma_rn(2.0, S.first(p.n, BLK_ANGLE), -1.0);   // 2 xi exact: same as 2 xi - 1
     const double q = (A * A + (2.0 * A) * mu_cm) + 1.0;
     const double E1 = (p.E * q) * __ldg(P.inv_ap1sq + sel_n);
     const double mu = (1.0 + A * mu_cm) / sqrt(q);
