@@ -176,7 +176,7 @@ def run_ours(args):
     if ws > 1:
         torch.distributed.barrier()
     scheme = tb.SCHEME_ASYNC if args.scheme == "async" else tb.SCHEME_STACK
-    decomp = tb.DECOMP_SPLIT if args.decomp == "split" else tb.DECOMP_MONO
+    decomp = _DECOMPS[args.decomp]
     spec = inputs.c5g7_lattice()
     opts = tb.RunOpts(seed=1 + 1000 * rank, scheme=scheme, decomposition=decomp, stash_slots=args.stash,
                       blocks_per_sm=args.bps, remap_every=args.remap if args.decomp == "mono" else 1,
@@ -491,7 +491,7 @@ def run_batched_workload(args):
 def run_adjoint_workload(args):
     import torch
     ws, rank, tb, inputs = _setup(torch)
-    decomp = tb.DECOMP_SPLIT if args.decomp == "split" else tb.DECOMP_MONO
+    decomp = _DECOMPS[args.decomp]
     sampler = ClockSampler(torch.cuda.current_device())
     m = measure_adjoint(torch, tb, inputs, args.steps, args.warmup, decomp, seed=1 + 1000 * rank, sampler=sampler,
                         barrier=torch.distributed.barrier if ws > 1 else None)
@@ -506,6 +506,125 @@ def run_adjoint_workload(args):
         print(json.dumps(line), flush=True)
     if ws > 1:
         torch.distributed.destroy_process_group()
+    return 0
+
+
+CE_WORKLOAD = ("continuous-energy infinite pin cell (4 synthetic nuclides, 1e5 points and 300 resonances each, "
+               "union grid ~4e5), Watt-like source in the fuel, energy tally per material")
+_DECOMPS = {"mono": 0, "split": 1, "lookup": 2}
+
+
+def _time_fixed(torch, tb, prob, opts, steps, warmup):
+    """Device time (CUDA events) of `steps` fixed-source runs after `warmup`."""
+    stream = torch.cuda.current_stream()
+    for _ in range(warmup):
+        prob.run_fixed_source(opts)
+    torch.cuda.synchronize()
+    t, ev = 0.0, 0
+    for _ in range(steps):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        r = prob.run_fixed_source(opts)
+        e1.record(stream)
+        e1.synchronize()
+        t += e0.elapsed_time(e1) * 1e-3
+        ev += int(r["events"])
+    return t, ev
+
+
+def run_ce_workload(args):
+    """One step = one fixed-source run of the CE pin cell (args.n_hist histories,
+    args.ebins energy bins) with the chosen scheme and decomposition."""
+    import torch
+    ws, rank, tb, inputs = _setup(torch)
+    spec = inputs.ce_pin_cell(n_ebins=args.ebins)
+    prob = tb.Problem(spec)
+    opts = tb.RunOpts(n_histories=args.n_hist, seed=1 + 1000 * rank,
+                      scheme=tb.SCHEME_ASYNC if args.scheme == "async" else tb.SCHEME_STACK,
+                      decomposition=_DECOMPS[args.decomp], remap_every=args.remap if args.decomp == "mono" else 1)
+    sampler = ClockSampler(torch.cuda.current_device())
+    launches0 = tb.kernel_launch_count()
+    with sampler:
+        t, ev = _time_fixed(torch, tb, prob, opts, args.steps, args.warmup)
+    m = {"launches": tb.kernel_launch_count() - launches0}
+    ev_all = float(ev)
+    if ws > 1:
+        from paper_2506_00263_gb300 import parallel
+        t, ev_all, _ = parallel.reduce_timing(t, ev_all, 0.0, device="cuda")
+    if rank == 0:
+        line = _side_line(args, ws, CE_WORKLOAD, m, t, ev_all, float(args.n_hist) * args.steps * ws, sampler,
+                          _hbm_roof(ev, t), {"scheme": args.scheme, "energy_bins": args.ebins,
+                                             "histories": args.n_hist, "remap_every": opts.remap_every})
+        print(json.dumps(line), flush=True)
+    prob.close()
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def run_ce_sweep(args):
+    """The paper's continuous-energy comparison (Sec. 5.2) on the synthetic pin
+    cell: events/s for stack and asynchronous remapping under the monolithic,
+    decomposed and lookup-event decompositions, over histories x energy-bin
+    resolution, with each point's speedup over stack remapping with the
+    monolithic scheme.  One JSON line per point."""
+    import torch
+    ws, rank, tb, inputs = _setup(torch)
+    if rank != 0:
+        return 0
+    for nb in (1, 100, 10000):
+        prob = tb.Problem(inputs.ce_pin_cell(n_ebins=nb))
+        for n in (100_000, 1_000_000, 10_000_000):
+            base = None
+            for scheme in ("stack", "async"):
+                for dname in ("mono", "split", "lookup"):
+                    opts = tb.RunOpts(n_histories=n, seed=1, decomposition=_DECOMPS[dname], remap_every=1,
+                                      scheme=tb.SCHEME_ASYNC if scheme == "async" else tb.SCHEME_STACK)
+                    t, ev = _time_fixed(torch, tb, prob, opts, 1 if n >= 10_000_000 else 2, 1)
+                    rate = ev / t
+                    if base is None:
+                        base = rate
+                    print(json.dumps({"workload": "ce-sweep", "energy_bins": nb, "histories": n, "scheme": scheme,
+                                      "decomposition": dname, "events_per_s": rate,
+                                      "speedup_vs_stack_mono": rate / base}), flush=True)
+        prob.close()
+    return 0
+
+
+def run_lattice_sweep(args):
+    """The paper's multigroup comparison (Sec. 5.1): power iterations of the
+    lattice with 25 % inactive cycles, over particles per cycle and cycle
+    counts, asynchronous vs stack remapping (monolithic scheme, one event per
+    remap as in the paper); one JSON line per point."""
+    import torch
+    ws, rank, tb, inputs = _setup(torch)
+    if rank != 0:
+        return 0
+    prob = tb.Problem(inputs.c5g7_lattice())
+    stream = torch.cuda.current_stream()
+    for cycles in (24, 48, 100, 200, 400):
+        ni = cycles // 4
+        for nper in (10_000, 100_000, 1_000_000):
+            if nper * cycles > 100_000_000:
+                continue
+            rates = {}
+            for scheme in ("stack", "async"):
+                opts = tb.RunOpts(seed=1, scheme=tb.SCHEME_ASYNC if scheme == "async" else tb.SCHEME_STACK,
+                                  decomposition=tb.DECOMP_MONO, remap_every=1)
+                prob.power_iteration(nper, 1, 2, opts)
+                torch.cuda.synchronize()
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                r = prob.power_iteration(nper, ni, cycles - ni, opts)
+                e1.record(stream)
+                e1.synchronize()
+                rates[scheme] = int(r["events"]) / (e0.elapsed_time(e1) * 1e-3)
+            print(json.dumps({"workload": "lattice-sweep", "cycles": cycles, "particles_per_cycle": nper,
+                              "stack_events_per_s": rates["stack"], "async_events_per_s": rates["async"],
+                              "async_speedup": rates["async"] / rates["stack"]}), flush=True)
+    prob.close()
     return 0
 
 
@@ -549,7 +668,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--scheme", choices=["async", "stack"], default="async")
-    ap.add_argument("--decomp", choices=["split", "mono"], default="mono")
+    ap.add_argument("--decomp", choices=["split", "mono", "lookup"], default="mono")
     ap.add_argument("--n-per-batch", type=int, default=N_PER_BATCH)
     ap.add_argument("--inactive", type=int, default=N_INACTIVE)
     ap.add_argument("--active", type=int, default=N_ACTIVE)
@@ -560,9 +679,13 @@ def main():
     ap.add_argument("--bps", type=int, default=0, help="blocks per SM (0 = default)")
     ap.add_argument("--remap", type=int, default=3, help="monolithic: events between remaps")
     ap.add_argument("--queue", type=int, default=0, help="stack: particles per stack; async: spill links x 32")
-    ap.add_argument("--workload", choices=["lattice", "batched", "adjoint"], default="lattice",
+    ap.add_argument("--workload", choices=["lattice", "batched", "adjoint", "ce", "ce-sweep", "lattice-sweep"],
+                    default="lattice",
                     help="lattice: the k-eigenvalue lattice; batched: 256 box problems in one launch; "
-                         "adjoint: forward + derivative kernels on the fixed-source lattice")
+                         "adjoint: forward + derivative kernels on the fixed-source lattice; ce: the continuous-"
+                         "energy pin cell; ce-sweep / lattice-sweep: the paper's scheme comparisons")
+    ap.add_argument("--ebins", type=int, default=100, help="ce: energy-tally bins per material")
+    ap.add_argument("--n-hist", type=int, default=1_000_000, help="ce: histories per run")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
@@ -572,6 +695,12 @@ def main():
         return run_batched_workload(args)
     if args.workload == "adjoint":
         return run_adjoint_workload(args)
+    if args.workload == "ce":
+        return run_ce_workload(args)
+    if args.workload == "ce-sweep":
+        return run_ce_sweep(args)
+    if args.workload == "lattice-sweep":
+        return run_lattice_sweep(args)
     return run_ours(args)
 
 

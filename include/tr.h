@@ -54,8 +54,12 @@ enum { TR_XS_MG = 0, TR_XS_CE = 1 };
 enum { TR_SRC_POINT = 0, TR_SRC_BOX = 1, TR_SRC_PINS = 2 };
 /* Remapping scheme: stack-based (Sec. 3.1) or asynchronous (Sec. 3.2). */
 enum { TR_SCHEME_STACK = 0, TR_SCHEME_ASYNC = 1 };
-/* Task decomposition (Sec. 4): one "step" event, or step / collision / surface. */
-enum { TR_DECOMP_MONO = 0, TR_DECOMP_SPLIT = 1 };
+/* Task decomposition (Sec. 4): one "step" event; step / collision / surface;
+ * or those three plus a cross-section lookup event of its own (one of the
+ * alternate decompositions Sec. 5.2 points to), whose values travel with the
+ * particle to the step and collision that follow.  The lookup event does not
+ * count as an event: all three give the same histories. */
+enum { TR_DECOMP_MONO = 0, TR_DECOMP_SPLIT = 1, TR_DECOMP_SPLIT_LOOKUP = 2 };
 
 /* Rectilinear grid of cells; each cell may hold one z-aligned cylinder
  * ("pin") of radius pin_radius centred in its x-y box.  Planes are ascending;

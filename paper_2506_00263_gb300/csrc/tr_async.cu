@@ -35,20 +35,22 @@ constexpr int N_GQ = 32;
 
 struct Stash {
     double *x, *y, *z, *u, *v, *w, *iu, *iv, *iw, *ia, *E;
+    double *xst, *xist, *xsa, *xnsf;   // lookup-event decomposition only (else NULL)
     int* g;
     unsigned *cell, *id, *n, *nsites, *pend, *prob;
     unsigned short* q[N_QUEUES];       // slot-index queues per event type
     unsigned short* fr;                // free-slot stack
-    int* cnt;                          // [0..2] queue counts, [3] free count, [4] lock, [5] block error
+    int* cnt;                          // [0, N_QUEUES) queue counts, [CNT_FREE] free count, [CNT_LOCK] lock
 };
+constexpr int CNT_FREE = N_QUEUES, CNT_LOCK = N_QUEUES + 1;   // control words after the queue counts
 
-__host__ __device__ __forceinline__ size_t stash_bytes(int S)
+__host__ __device__ __forceinline__ size_t stash_bytes(int S, bool xs = false)
 {
-    return (size_t)S * (11 * sizeof(double) + sizeof(int) + 6 * sizeof(unsigned)) +
+    return (size_t)S * ((xs ? 15 : 11) * sizeof(double) + sizeof(int) + 6 * sizeof(unsigned)) +
            (size_t)S * (N_QUEUES + 1) * sizeof(unsigned short) + 16 * sizeof(int);
 }
 
-__device__ __forceinline__ Stash carve(unsigned char* base, int S)
+__device__ __forceinline__ Stash carve(unsigned char* base, int S, bool xs)
 {
     Stash s;
     double* d = reinterpret_cast<double*>(base);
@@ -56,6 +58,10 @@ __device__ __forceinline__ Stash carve(unsigned char* base, int S)
     s.u = d; d += S; s.v = d; d += S; s.w = d; d += S;
     s.iu = d; d += S; s.iv = d; d += S; s.iw = d; d += S; s.ia = d; d += S;
     s.E = d; d += S;
+    s.xst = s.xist = s.xsa = s.xnsf = nullptr;
+    if (xs) {
+        s.xst = d; d += S; s.xist = d; d += S; s.xsa = d; d += S; s.xnsf = d; d += S;
+    }
     unsigned* u = reinterpret_cast<unsigned*>(d);
     s.g = reinterpret_cast<int*>(u); u += S;
     s.cell = u; u += S; s.id = u; u += S; s.n = u; u += S; s.nsites = u; u += S; s.pend = u; u += S;
@@ -73,8 +79,12 @@ __device__ __forceinline__ Stash carve(unsigned char* base, int S)
     return s;
 }
 
+template <bool XS>
 __device__ __forceinline__ void slot_load(const Stash& s, int i, Particle& p)
 {
+    if (XS) {
+        p.xst = s.xst[i]; p.xist = s.xist[i]; p.xsa = s.xsa[i]; p.xnsf = s.xnsf[i];
+    }
     p.x = s.x[i]; p.y = s.y[i]; p.z = s.z[i];
     p.u = s.u[i]; p.v = s.v[i]; p.w = s.w[i];
     p.iu = s.iu[i]; p.iv = s.iv[i]; p.iw = s.iw[i]; p.ia = s.ia[i];
@@ -83,8 +93,12 @@ __device__ __forceinline__ void slot_load(const Stash& s, int i, Particle& p)
     p.prob = s.prob[i];
 }
 
+template <bool XS>
 __device__ __forceinline__ void slot_store(const Stash& s, int i, const Particle& p)
 {
+    if (XS) {
+        s.xst[i] = p.xst; s.xist[i] = p.xist; s.xsa[i] = p.xsa; s.xnsf[i] = p.xnsf;
+    }
     s.x[i] = p.x; s.y[i] = p.y; s.z[i] = p.z;
     s.u[i] = p.u; s.v[i] = p.v; s.w[i] = p.w;
     s.iu[i] = p.iu; s.iv[i] = p.iv; s.iw[i] = p.iw; s.ia[i] = p.ia;
@@ -96,8 +110,12 @@ __device__ __forceinline__ void slot_store(const Stash& s, int i, const Particle
 // Particle state of a global link, read through L2 (ld.global.cg): the link
 // was written by another SM, and this SM's L1 may still hold lines from an
 // earlier use of the same link.
+template <bool XS>
 __device__ __forceinline__ void load_particle_l2(const SoA& s, unsigned long long i, Particle& p)
 {
+    if (XS) {
+        p.xst = __ldcg(s.xst + i); p.xist = __ldcg(s.xist + i); p.xsa = __ldcg(s.xsa + i); p.xnsf = __ldcg(s.xnsf + i);
+    }
     p.x = __ldcg(s.x + i); p.y = __ldcg(s.y + i); p.z = __ldcg(s.z + i);
     p.u = __ldcg(s.u + i); p.v = __ldcg(s.v + i); p.w = __ldcg(s.w + i);
     p.iu = __ldcg(s.iu + i); p.iv = __ldcg(s.iv + i); p.iw = __ldcg(s.iw + i); p.ia = __ldcg(s.ia + i);
@@ -118,7 +136,7 @@ __device__ __forceinline__ bool lock_stash(const Stash& s, const RunParams& R, E
     if ((threadIdx.x & 31) == 0) {
         unsigned long long spins = 0;
         uint64_t t0 = 0;
-        while (atomicCAS(s.cnt + 4, 0, 1) != 0) {
+        while (atomicCAS(s.cnt + CNT_LOCK, 0, 1) != 0) {
             if (spins == 0) t0 = now_ns();
             if (++spins > R.max_spin || now_ns() - t0 > R.max_wait_ns) {
                 fail(err, ERR_TIMEOUT, 1);
@@ -138,7 +156,7 @@ __device__ __forceinline__ void unlock_stash(const Stash& s)
     __syncwarp();
     if ((threadIdx.x & 31) == 0) {
         __threadfence_block();
-        atomicExch(s.cnt + 4, 0);
+        atomicExch(s.cnt + CNT_LOCK, 0);
     }
     __syncwarp();
 }
@@ -255,19 +273,22 @@ __device__ __forceinline__ void flush_lane(Acc& acc, const Tallies& T)
     acc.zero();
 }
 
-template <bool CE, bool SPLIT, bool BATCHED = false>
+// DEC: the task decomposition (DEC_MONO, DEC_SPLIT or DEC_LOOKUP).
+template <bool CE, int DEC, bool BATCHED = false>
 __global__ void __launch_bounds__(256, TR_ASYNC_MIN_BLOCKS) k_async(DevProblem P, RunParams R, AsyncArgs A, Tallies T, ErrorWord* err)
 {
     extern __shared__ __align__(16) unsigned char smem[];
+    constexpr bool SPLIT = DEC != DEC_MONO;
+    constexpr bool XS = DEC == DEC_LOOKUP;   // cross sections travel with the particle
     const int S = A.stash_slots;
-    const Stash st = carve(smem, S);
+    const Stash st = carve(smem, S, XS);
     const int lane = threadIdx.x & 31;
-    constexpr int nq = SPLIT ? N_QUEUES : 1;
+    constexpr int nq = dec_queues(DEC);
     AsyncCtl* ctl = A.ctl;
 
     if (threadIdx.x == 0) {
-        for (int q = 0; q < 6; ++q) st.cnt[q] = 0;
-        st.cnt[3] = S;
+        for (int q = 0; q <= CNT_LOCK; ++q) st.cnt[q] = 0;
+        st.cnt[CNT_FREE] = S;
     }
     for (int i = threadIdx.x; i < S; i += blockDim.x) st.fr[i] = (unsigned short)(S - 1 - i);
     __syncthreads();
@@ -302,7 +323,7 @@ __global__ void __launch_bounds__(256, TR_ASYNC_MIN_BLOCKS) k_async(DevProblem P
         int cnts[N_QUEUES];
 #pragma unroll
         for (int q = 0; q < N_QUEUES; ++q) cnts[q] = *(volatile int*)(st.cnt + q);
-        const int nfree = *(volatile int*)(st.cnt + 3);
+        const int nfree = *(volatile int*)(st.cnt + CNT_FREE);
         int q = 0;
         for (int k = 1; k < nq; ++k)
             if (cnts[k] > cnts[q]) q = k;
@@ -337,7 +358,7 @@ __global__ void __launch_bounds__(256, TR_ASYNC_MIN_BLOCKS) k_async(DevProblem P
         __syncwarp();
         if (lane == 0) {
             if (mode == 0 || mode == 2) st.cnt[q] = cnts[q] - take;
-            else if (mode == 1) st.cnt[3] = nfree - 32;
+            else if (mode == 1) st.cnt[CNT_FREE] = nfree - 32;
         }
         unlock_stash(st);
 
@@ -363,11 +384,11 @@ __global__ void __launch_bounds__(256, TR_ASYNC_MIN_BLOCKS) k_async(DevProblem P
                 }
                 bool ok = lock_stash(st, R, err);
                 if (!ok) break;
-                const int nf = *(volatile int*)(st.cnt + 3);
+                const int nf = *(volatile int*)(st.cnt + CNT_FREE);
                 int sl = -1;
                 if (lane < fill && nf >= fill) sl = st.fr[nf - fill + lane];
                 __syncwarp();
-                if (lane == 0 && nf >= fill) st.cnt[3] = nf - fill;
+                if (lane == 0 && nf >= fill) st.cnt[CNT_FREE] = nf - fill;
                 unlock_stash(st);
                 if (nf < fill) {
                     fail(err, ERR_CAPACITY, 3);
@@ -376,13 +397,13 @@ __global__ void __launch_bounds__(256, TR_ASYNC_MIN_BLOCKS) k_async(DevProblem P
                 bool bad = false;
                 if (lane < fill) {
                     Particle p;
-                    load_particle_l2(A.links, (unsigned long long)link * 32 + lane, p);
+                    load_particle_l2<XS>(A.links, (unsigned long long)link * 32 + lane, p);
                     bad = BATCHED && p.prob >= (unsigned)A.n_probs;
                     const DevProblem& PP = (BATCHED && !bad) ? A.probs[p.prob] : P;
                     bad = bad || p.id >= R.n_hist || cell_i(p.cell) >= PP.nx || cell_j(p.cell) >= PP.ny ||
                           cell_k(p.cell) >= PP.nz || sl < 0 || sl >= S || (!CE && (p.g < 0 || p.g >= PP.G));
                     if (!bad && cell_in(p.cell)) bad = info_pin(cell_info(PP, p.cell)) < 0;
-                    if (!bad) slot_store(st, sl, p);
+                    if (!bad) slot_store<XS>(st, sl, p);
                 }
                 if (__any_sync(FULLM, bad)) {
                     if (lane == 0) fail(err, ERR_INVALID, 7);
@@ -440,8 +461,8 @@ __global__ void __launch_bounds__(256, TR_ASYNC_MIN_BLOCKS) k_async(DevProblem P
                 continue;
             }
             Particle p;
-            slot_load(st, slot, p);
-            store_particle(A.links, (unsigned long long)link * 32 + lane, p, CE);
+            slot_load<XS>(st, slot, p);
+            store_particle(A.links, (unsigned long long)link * 32 + lane, p, CE, XS);
             __threadfence();
             __syncwarp();
             if (lane == 0) {
@@ -452,10 +473,10 @@ __global__ void __launch_bounds__(256, TR_ASYNC_MIN_BLOCKS) k_async(DevProblem P
                 atomicAdd(&ctl->spills, 1ull);
             }
             if (!lock_stash(st, R, err)) break;
-            const int nf = *(volatile int*)(st.cnt + 3);
+            const int nf = *(volatile int*)(st.cnt + CNT_FREE);
             st.fr[nf + lane] = (unsigned short)slot;
             __syncwarp();
-            if (lane == 0) st.cnt[3] = nf + 32;
+            if (lane == 0) st.cnt[CNT_FREE] = nf + 32;
             unlock_stash(st);
             continue;
         }
@@ -464,7 +485,7 @@ __global__ void __launch_bounds__(256, TR_ASYNC_MIN_BLOCKS) k_async(DevProblem P
         {   // exact warp fill per iteration: sites 12 + queue (mode 0) and 15 (make_work)
             const unsigned hm = __ballot_sync(FULLM, slot >= 0);
             if (lane == 0 && hm) {
-                const int site = mode == 1 ? 15 : 12 + q;
+                const int site = mode == 1 ? 25 : 12 + q;
                 atomicAdd(&g_lane_prof[2 * site], 1ull);
                 atomicAdd(&g_lane_prof[2 * site + 1], (unsigned long long)__popc(hm));
             }
@@ -499,13 +520,13 @@ __global__ void __launch_bounds__(256, TR_ASYNC_MIN_BLOCKS) k_async(DevProblem P
                     acc.ev[EV_SOURCE] += 1u;
                 }
                 if (!live) fail(err, ERR_INVALID, 5);
-                next = Q_STEP;
+                next = XS ? Q_LOOKUP : Q_STEP;
             }
             const unsigned made = __popc(__ballot_sync(FULLM, live));
             if (lane == 0 && made) atomicAdd(&ctl->live, (unsigned long long)made);
         } else {
             // mode 0 (warp-uniform): lanes beyond a partial link hold no slot and stay idle
-            if (slot >= 0) slot_load(st, slot, p);
+            if (slot >= 0) slot_load<XS>(st, slot, p);
             __syncwarp();   // reconverge: the event below must run once for all lanes, not per lane group
             const unsigned em = __ballot_sync(FULLM, slot >= 0);   // the lanes that hold a particle
             if (slot >= 0) {
@@ -533,14 +554,20 @@ __global__ void __launch_bounds__(256, TR_ASYNC_MIN_BLOCKS) k_async(DevProblem P
                     }
                     next = live ? Q_STEP : Q_DEAD;
                 } else if (q == Q_STEP) {
-                    XS X;
+                    tr::XS X;
                     double xr;
                     FwdSink sink{TT, acc};
-                    step_event<CE>(PP, RR, p, sink, X, xr);
+                    step_event<CE, XS>(PP, RR, p, sink, X, xr);
                     next = next_queue_after_step(p);
                 } else if (q == Q_COLLIDE) {
-                    live = split_collide<CE>(PP, RR, p, TT, acc, A.bank, err, em);
-                    next = live ? Q_STEP : Q_DEAD;
+                    live = split_collide<CE, XS>(PP, RR, p, TT, acc, A.bank, err, em);
+                    next = live ? (XS ? Q_LOOKUP : Q_STEP) : Q_DEAD;
+                } else if (XS && q == Q_LOOKUP) {
+                    lookup_event<CE>(PP, p);
+                    next = Q_STEP;
+                } else if (XS) {
+                    next = split_surface_next(PP, RR, p, TT, acc, A.bank);
+                    live = next != Q_DEAD;
                 } else {
                     live = split_surface(PP, RR, p, TT, acc, A.bank);
                     next = live ? Q_STEP : Q_DEAD;
@@ -550,7 +577,7 @@ __global__ void __launch_bounds__(256, TR_ASYNC_MIN_BLOCKS) k_async(DevProblem P
             const unsigned died = __popc(__ballot_sync(FULLM, slot >= 0 && !live));
             if (lane == 0 && died) atomicAdd(&ctl->live, 0ull - (unsigned long long)died);
         }
-        if (live) slot_store(st, slot, p);
+        if (live) slot_store<XS>(st, slot, p);
         // ---------------- deposit (under the stash lock) ----------------
         __syncwarp();
         if (!lock_stash(st, R, err)) break;
@@ -559,7 +586,7 @@ __global__ void __launch_bounds__(256, TR_ASYNC_MIN_BLOCKS) k_async(DevProblem P
             const bool mine = has && (qq == N_QUEUES ? next == Q_DEAD : next == qq);
             const unsigned mask = __ballot_sync(FULLM, mine);
             if (!mask) continue;
-            int* cp = st.cnt + (qq == N_QUEUES ? 3 : qq);
+            int* cp = st.cnt + (qq == N_QUEUES ? CNT_FREE : qq);
             const int c = *(volatile int*)cp;
             if (mine) {
                 const int pos = c + __popc(mask & ((1u << lane) - 1u));
@@ -581,49 +608,73 @@ __global__ void __launch_bounds__(256, TR_ASYNC_MIN_BLOCKS) k_async(DevProblem P
 
 namespace tr {
 
-template <bool CE, bool SPLIT>
+template <bool CE, int DEC, bool BATCHED = false>
 static cudaError_t prepare_async(size_t smem)
 {
-    return cudaFuncSetAttribute(k_async<CE, SPLIT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    return cudaFuncSetAttribute(k_async<CE, DEC, BATCHED>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
 }
 
-template <bool CE, bool SPLIT>
+template <bool CE, int DEC, bool BATCHED = false>
 static int occupancy_async(size_t smem)
 {
     int nb = 0;
-    if (prepare_async<CE, SPLIT>(smem) != cudaSuccess) return 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_async<CE, SPLIT>, 256, smem) != cudaSuccess) return 0;
+    if (prepare_async<CE, DEC, BATCHED>(smem) != cudaSuccess) return 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_async<CE, DEC, BATCHED>, 256, smem) != cudaSuccess) return 0;
     return nb;
 }
 
-int async_max_blocks_per_sm(const DevProblem& P, int split, int stash_slots)
+int async_max_blocks_per_sm(const DevProblem& P, int dec, int stash_slots)
 {
-    const size_t smem = stash_bytes(stash_slots);
-    if (P.kind == 1) return split ? occupancy_async<true, true>(smem) : occupancy_async<true, false>(smem);
-    return split ? occupancy_async<false, true>(smem) : occupancy_async<false, false>(smem);
+    const size_t smem = stash_bytes(stash_slots, dec == DEC_LOOKUP);
+    if (P.kind == 1) {
+        if (dec == DEC_LOOKUP) return occupancy_async<true, DEC_LOOKUP>(smem);
+        return dec == DEC_SPLIT ? occupancy_async<true, DEC_SPLIT>(smem) : occupancy_async<true, DEC_MONO>(smem);
+    }
+    if (dec == DEC_LOOKUP) return occupancy_async<false, DEC_LOOKUP>(smem);
+    return dec == DEC_SPLIT ? occupancy_async<false, DEC_SPLIT>(smem) : occupancy_async<false, DEC_MONO>(smem);
 }
 
-template <bool CE, bool SPLIT>
+template <bool CE, int DEC, bool BATCHED = false>
 static cudaError_t launch_async_t(const DevProblem& P, const RunParams& R, const AsyncArgs& A, const Tallies& T,
                                   ErrorWord* err, int blocks, cudaStream_t st, size_t smem)
 {
-    const cudaError_t e = prepare_async<CE, SPLIT>(smem);
+    const cudaError_t e = prepare_async<CE, DEC, BATCHED>(smem);
     if (e != cudaSuccess) return e;
-    k_async<CE, SPLIT><<<blocks, 256, smem, st>>>(P, R, A, T, err);
+    k_async<CE, DEC, BATCHED><<<blocks, 256, smem, st>>>(P, R, A, T, err);
     return cudaGetLastError();
 }
 
 cudaError_t launch_async(const DevProblem& P, const RunParams& R, const AsyncArgs& A, const Tallies& T, ErrorWord* err,
                          int blocks, cudaStream_t st, int* smem_bytes_out)
 {
-    const size_t smem = stash_bytes(A.stash_slots);
+    const size_t smem = stash_bytes(A.stash_slots, A.dec == DEC_LOOKUP);
     if (smem_bytes_out) *smem_bytes_out = (int)smem;
     count_launches(1);
-    if (P.kind == 1)
-        return A.split ? launch_async_t<true, true>(P, R, A, T, err, blocks, st, smem)
-                       : launch_async_t<true, false>(P, R, A, T, err, blocks, st, smem);
-    return A.split ? launch_async_t<false, true>(P, R, A, T, err, blocks, st, smem)
-                   : launch_async_t<false, false>(P, R, A, T, err, blocks, st, smem);
+    if (P.kind == 1) {
+        if (A.dec == DEC_LOOKUP) return launch_async_t<true, DEC_LOOKUP>(P, R, A, T, err, blocks, st, smem);
+        return A.dec == DEC_SPLIT ? launch_async_t<true, DEC_SPLIT>(P, R, A, T, err, blocks, st, smem)
+                                  : launch_async_t<true, DEC_MONO>(P, R, A, T, err, blocks, st, smem);
+    }
+    if (A.dec == DEC_LOOKUP) return launch_async_t<false, DEC_LOOKUP>(P, R, A, T, err, blocks, st, smem);
+    return A.dec == DEC_SPLIT ? launch_async_t<false, DEC_SPLIT>(P, R, A, T, err, blocks, st, smem)
+                              : launch_async_t<false, DEC_MONO>(P, R, A, T, err, blocks, st, smem);
+}
+
+// Batched launches (multigroup; monolithic or decomposed).
+int async_batched_max_blocks_per_sm(int dec, int stash_slots)
+{
+    const size_t smem = stash_bytes(stash_slots);
+    return dec == DEC_SPLIT ? occupancy_async<false, DEC_SPLIT, true>(smem) : occupancy_async<false, DEC_MONO, true>(smem);
+}
+
+cudaError_t launch_async_batched(const DevProblem& P0, const RunParams& R, const AsyncArgs& A, ErrorWord* err,
+                                 int blocks, cudaStream_t st)
+{
+    const size_t smem = stash_bytes(A.stash_slots);
+    const Tallies T{};
+    count_launches(1);
+    return A.dec == DEC_SPLIT ? launch_async_t<false, DEC_SPLIT, true>(P0, R, A, T, err, blocks, st, smem)
+                              : launch_async_t<false, DEC_MONO, true>(P0, R, A, T, err, blocks, st, smem);
 }
 
 }  // namespace tr
@@ -638,45 +689,3 @@ extern "C" int tr_profile_lanes_read(unsigned long long* out, int n)
     return cudaMemcpyToSymbol(tr::g_lane_prof, z, sizeof(z)) != cudaSuccess;
 }
 #endif
-
-namespace tr {
-
-int async_batched_max_blocks_per_sm(int split, int stash_slots)
-{
-    const size_t smem = stash_bytes(stash_slots);
-    int nb = 0;
-    if (split) {
-        if (cudaFuncSetAttribute(k_async<false, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
-            cudaSuccess)
-            return 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_async<false, true, true>, 256, smem);
-    } else {
-        if (cudaFuncSetAttribute(k_async<false, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
-            cudaSuccess)
-            return 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_async<false, false, true>, 256, smem);
-    }
-    return nb;
-}
-
-cudaError_t launch_async_batched(const DevProblem& P0, const RunParams& R, const AsyncArgs& A, ErrorWord* err,
-                                 int blocks, cudaStream_t st)
-{
-    const size_t smem = stash_bytes(A.stash_slots);
-    const Tallies T{};
-    count_launches(1);
-    if (A.split) {
-        cudaError_t e = cudaFuncSetAttribute(k_async<false, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)smem);
-        if (e != cudaSuccess) return e;
-        k_async<false, true, true><<<blocks, 256, smem, st>>>(P0, R, A, T, err);
-    } else {
-        cudaError_t e = cudaFuncSetAttribute(k_async<false, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)smem);
-        if (e != cudaSuccess) return e;
-        k_async<false, false, true><<<blocks, 256, smem, st>>>(P0, R, A, T, err);
-    }
-    return cudaGetLastError();
-}
-
-}  // namespace tr

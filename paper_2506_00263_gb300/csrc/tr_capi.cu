@@ -424,7 +424,7 @@ extern "C" void tr_problem_destroy(tr_problem* pr)
 static bool carve_soa(tr_problem* pr, const char* name, unsigned long long cap, SoA& s)
 {
     const size_t n = (size_t)cap;
-    const size_t bytes = n * (11 * 8 + 7 * 4) + 18 * 256;
+    const size_t bytes = n * (15 * 8 + 7 * 4) + 22 * 256;
     unsigned char* b = (unsigned char*)workspace(pr, name, bytes);
     if (!b) return false;
     auto take = [&](size_t sz) {
@@ -436,6 +436,7 @@ static bool carve_soa(tr_problem* pr, const char* name, unsigned long long cap, 
     s.u = (double*)take(8); s.v = (double*)take(8); s.w = (double*)take(8);
     s.iu = (double*)take(8); s.iv = (double*)take(8); s.iw = (double*)take(8); s.ia = (double*)take(8);
     s.E = (double*)take(8);
+    s.xst = (double*)take(8); s.xist = (double*)take(8); s.xsa = (double*)take(8); s.xnsf = (double*)take(8);
     s.g = (int*)take(4);
     s.cell = (unsigned*)take(4); s.id = (unsigned*)take(4); s.n = (unsigned*)take(4);
     s.nsites = (unsigned*)take(4); s.pend = (unsigned*)take(4); s.prob = (unsigned*)take(4);
@@ -492,14 +493,15 @@ static tr_status validate_opts(const tr_run_opts* o)
 {
     if (!o) return set_err(TR_ERR_INVALID, "opts is NULL");
     if (o->scheme != TR_SCHEME_STACK && o->scheme != TR_SCHEME_ASYNC) return set_err(TR_ERR_INVALID, "bad scheme");
-    if (o->decomposition != TR_DECOMP_MONO && o->decomposition != TR_DECOMP_SPLIT)
+    if (o->decomposition != TR_DECOMP_MONO && o->decomposition != TR_DECOMP_SPLIT &&
+        o->decomposition != TR_DECOMP_SPLIT_LOOKUP)
         return set_err(TR_ERR_INVALID, "bad decomposition");
     if (o->n_histories >= (1ull << 32)) return set_err(TR_ERR_INVALID, "n_histories must be < 2^32 per run");
     if (o->first_history + o->n_histories > (1ull << 32))
         return set_err(TR_ERR_INVALID, "first_history + n_histories must not exceed 2^32");
     if (o->remap_every < 0 || o->blocks_per_sm < 0 || o->stash_slots < 0 || o->max_spin < 0)
         return set_err(TR_ERR_INVALID, "negative tuning option");
-    if (o->decomposition == TR_DECOMP_SPLIT && o->remap_every > 1)
+    if (o->decomposition != TR_DECOMP_MONO && o->remap_every > 1)
         return set_err(TR_ERR_INVALID, "remap_every > 1 applies to the monolithic scheme only");
     return TR_OK;
 }
@@ -560,15 +562,15 @@ static tr_status transport(tr_problem* pr, const tr_run_opts* o, RunParams R, co
 {
     const DevProblem& P = pr->dp;
     const cudaStream_t st = pr->stream;
-    const bool split = o->decomposition == TR_DECOMP_SPLIT;
+    const int dec = o->decomposition;   // DEC_MONO, DEC_SPLIT, DEC_LOOKUP (same values as TR_DECOMP_*)
     const Tallies T = make_tallies(pr, R.want_log != 0);
     if (R.n_hist == 0) return TR_OK;
     if (o->scheme == TR_SCHEME_STACK) {
         unsigned long long cap = o->queue_capacity ? o->queue_capacity : std::min<unsigned long long>(R.n_hist, 1ull << 22);
         cap = std::max<unsigned long long>((cap + 31) & ~31ull, 64);
-        const int nst = split ? 3 : 1;
+        const int nst = dec_queues(dec);
         SoA bufs[2][N_QUEUES] = {};
-        const char* names[2][3] = {{"s0a", "s0b", "s0c"}, {"s1a", "s1b", "s1c"}};
+        const char* names[2][N_QUEUES] = {{"s0a", "s0b", "s0c", "s0d"}, {"s1a", "s1b", "s1c", "s1d"}};
         for (int h = 0; h < 2; ++h)
             for (int q = 0; q < nst; ++q)
                 if (!carve_soa(pr, names[h][q], cap, bufs[h][q])) return set_err(TR_ERR_NOMEM, "stack allocation failed");
@@ -582,14 +584,16 @@ static tr_status transport(tr_problem* pr, const tr_run_opts* o, RunParams R, co
         LaunchTimer lt;
         for (unsigned long long it = 0;; ++it) {
             h.pop = 0;
-            for (int q = 0; q < 3; ++q) {
+            for (int q = 0; q < N_QUEUES; ++q) {
                 h.out_count[q] = 0;
                 h.reserve[q] = 0;
             }
-            h.reserve[Q_STEP] = split ? h.in_count[Q_COLLIDE] + h.in_count[Q_SURFACE] : h.in_count[Q_STEP];
+            // sources go where the survivors of the collision and surface stacks go
+            if (dec == DEC_MONO) h.reserve[Q_STEP] = h.in_count[Q_STEP];
+            else h.reserve[dec == DEC_LOOKUP ? Q_LOOKUP : Q_STEP] = h.in_count[Q_COLLIDE] + h.in_count[Q_SURFACE];
             TR_CUDA(cudaMemcpyAsync(dctl, &h, sizeof(h), cudaMemcpyHostToDevice, st));
             TR_CUDA(cudaEventRecord(lt.a, st));
-            TR_CUDA(launch_stack(P, R, bufs[cur], bufs[cur ^ 1], dctl, T, bank, src, pr->err, split ? 1 : 0, blocks, st));
+            TR_CUDA(launch_stack(P, R, bufs[cur], bufs[cur ^ 1], dctl, T, bank, src, pr->err, dec, blocks, st));
             TR_CUDA(cudaEventRecord(lt.b, st));
             ++out.launches;
             TR_CUDA(cudaMemcpyAsync(&h, dctl, sizeof(h), cudaMemcpyDeviceToHost, st));
@@ -598,7 +602,7 @@ static tr_status transport(tr_problem* pr, const tr_run_opts* o, RunParams R, co
             tr_status es = check_err(pr);
             if (es != TR_OK) return es;
             unsigned long long tot = 0;
-            for (int q = 0; q < 3; ++q) {
+            for (int q = 0; q < N_QUEUES; ++q) {
                 if (h.out_count[q] > cap) return set_err(TR_ERR_CAPACITY, "stack overflow");
                 h.in_count[q] = h.out_count[q];
                 tot += h.out_count[q];
@@ -625,14 +629,14 @@ static tr_status transport(tr_problem* pr, const tr_run_opts* o, RunParams R, co
     A.bank = bank;
     A.use_src = src != nullptr;
     A.src = src ? *src : bank;
-    A.split = split ? 1 : 0;
+    A.dec = dec;
     A.stash_slots = S;
     AsyncCtl hc;
     std::memset(&hc, 0, sizeof(hc));
     std::memset(hc.free_q, 0xFF, sizeof(hc.free_q));
     std::memset(hc.full_q, 0xFF, sizeof(hc.full_q));
     TR_CUDA(cudaMemcpyAsync(A.ctl, &hc, sizeof(hc), cudaMemcpyHostToDevice, st));
-    int maxb = async_max_blocks_per_sm(P, A.split, S);
+    int maxb = async_max_blocks_per_sm(P, A.dec, S);
     if (maxb < 1) return set_err(TR_ERR_INVALID, "stash does not fit in shared memory");
     const int bps = o->blocks_per_sm > 0 ? std::min(o->blocks_per_sm, maxb) : maxb;
     int smem = 0;
@@ -1002,6 +1006,8 @@ extern "C" tr_status tr_run_batched(tr_problem* const* probs, int32_t n, const u
     tr_status s = validate_opts(opts);
     if (s != TR_OK) return s;
     if (opts->scheme != TR_SCHEME_ASYNC) return set_err(TR_ERR_INVALID, "batched runs use the asynchronous scheme");
+    if (opts->decomposition == TR_DECOMP_SPLIT_LOOKUP)
+        return set_err(TR_ERR_INVALID, "batched runs use the monolithic or decomposed scheme");
     if (opts->first_history != 0) return set_err(TR_ERR_INVALID, "first_history applies to single runs only");
     tr_problem* lead = probs[0];
     unsigned long long total = 0;
@@ -1050,7 +1056,7 @@ extern "C" tr_status tr_run_batched(tr_problem* const* probs, int32_t n, const u
     A.ctl = (AsyncCtl*)workspace(lead, "asyncctl", sizeof(AsyncCtl));
     if (!A.link_next || !A.link_type || !A.link_fill || !A.ctl) return set_err(TR_ERR_NOMEM, "link arena allocation failed");
     A.n_links = n_links;
-    A.split = opts->decomposition == TR_DECOMP_SPLIT ? 1 : 0;
+    A.dec = opts->decomposition;
     std::vector<DevProblem> hp(n);
     std::vector<Tallies> ht(n);
     std::vector<unsigned long long> hoff(n + 1, 0);
@@ -1088,13 +1094,13 @@ extern "C" tr_status tr_run_batched(tr_problem* const* probs, int32_t n, const u
         const std::vector<int> c_bps = tune.blocks_per_sm ? std::vector<int>{tune.blocks_per_sm} : std::vector<int>{1, 2};
         const std::vector<int> c_S = tune.stash_slots ? std::vector<int>{tune.stash_slots} : std::vector<int>{288, 512, 1024};
         const std::vector<int> c_rm = tune.remap_every ? std::vector<int>{tune.remap_every}
-                                      : A.split        ? std::vector<int>{1}
+                                      : A.dec          ? std::vector<int>{1}
                                                        : std::vector<int>{1, 2, 4};
         std::vector<BatchTuning> cands;
         for (int bps : c_bps)
             for (int S : c_S)
                 for (int rm : c_rm)
-                    if (async_batched_max_blocks_per_sm(A.split, S) >= bps) cands.push_back({bps, S, rm});
+                    if (async_batched_max_blocks_per_sm(A.dec, S) >= bps) cands.push_back({bps, S, rm});
         if (cands.empty()) return set_err(TR_ERR_INVALID, "no feasible tuning candidate");
         cudaEvent_t e0, e1;
         TR_CUDA(cudaEventCreate(&e0));
@@ -1122,7 +1128,7 @@ extern "C" tr_status tr_run_batched(tr_problem* const* probs, int32_t n, const u
         std::lock_guard<std::mutex> lk(g_tune_mu);
         g_tune_cache[key] = tune;
     }
-    if (async_batched_max_blocks_per_sm(A.split, tune.stash_slots) < tune.blocks_per_sm)
+    if (async_batched_max_blocks_per_sm(A.dec, tune.stash_slots) < tune.blocks_per_sm)
         return set_err(TR_ERR_INVALID, "blocks_per_sm does not fit with this stash size");
 
     // the run: replay the captured graph when this leader ran the same batch last

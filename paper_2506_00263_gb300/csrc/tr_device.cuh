@@ -57,8 +57,13 @@ constexpr uint32_t BLK_POS = 200u;     // 200 + 2t, 201 + 2t: source position tr
 constexpr uint32_t N_POS = 1024u;
 constexpr uint32_t TAG_POP = 0x80000000u;
 
-// next event types of the decomposed scheme (queue ids); DEAD ends the history
-constexpr int Q_STEP = 0, Q_COLLIDE = 1, Q_SURFACE = 2, N_QUEUES = 3, Q_DEAD = 3;
+// next event types of the decomposed schemes (queue ids); DEAD ends the history
+constexpr int Q_STEP = 0, Q_COLLIDE = 1, Q_SURFACE = 2, Q_LOOKUP = 3, N_QUEUES = 4, Q_DEAD = 4;
+// task decompositions: monolithic (one event per step), decomposed (step,
+// collision, surface crossing), decomposed with the cross-section lookup as
+// an event of its own (the lookup's values travel with the particle)
+constexpr int DEC_MONO = 0, DEC_SPLIT = 1, DEC_LOOKUP = 2;
+__host__ __device__ constexpr int dec_queues(int dec) { return dec == DEC_MONO ? 1 : (dec == DEC_SPLIT ? 3 : 4); }
 
 struct DevProblem {
     // geometry
@@ -126,9 +131,11 @@ __device__ __forceinline__ uint64_t now_ns()
 // that a surface event does not repeat four divisions), energy (CE) or
 // group (MG), packed cell, history index, event count, banked-site count, the
 // pending surface flags of the decomposed scheme and the problem index of a
-// batched launch.
+// batched launch; with the lookup event, the cached cross sections (Sigma_t,
+// 1/Sigma_t, Sigma_a, nu Sigma_f).
 struct SoA {
     double *x, *y, *z, *u, *v, *w, *iu, *iv, *iw, *ia, *E;
+    double *xst, *xist, *xsa, *xnsf;
     int *g;
     unsigned *cell, *id, *n, *nsites, *pend, *prob;
 };
@@ -137,6 +144,7 @@ struct Particle {
     double x, y, z, u, v, w;
     double iu, iv, iw, ia;
     double E;
+    double xst, xist, xsa, xnsf;       // lookup-event decomposition: cross sections of (material, E or g)
     int g;
     unsigned cell;                     // i | j << 10 | k << 20 | inside << 30
     unsigned id, n, nsites, pend;

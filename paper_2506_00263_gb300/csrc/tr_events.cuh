@@ -239,7 +239,9 @@ struct FwdSink {
     }
 };
 
-template <bool CE, class Sink>
+// CACHED: the cross sections come from the particle (left there by the
+// lookup event) instead of a lookup here; the values are the same.
+template <bool CE, bool CACHED = false, class Sink>
 __device__ __forceinline__ void step_event(const DevProblem& P, const RunParams& R, Particle& p, Sink& sink, XS& X,
                                            double& xi_react)
 {
@@ -249,7 +251,14 @@ __device__ __forceinline__ void step_event(const DevProblem& P, const RunParams&
     const int in = cell_in(c);
     const int pin = info_pin(info) >= 0;
     const int m = in ? info_pin(info) : info_mat(info);
-    xs_lookup<CE>(P, p, m, X);
+    if (CACHED) {
+        X.st = p.xst;
+        X.inv_st = p.xist;
+        X.sa = p.xsa;
+        X.nsf = p.xnsf;
+    } else {
+        xs_lookup<CE>(P, p, m, X);
+    }
     const Stream S = make_stream(R, p.id);
     const uint4 b0 = S.block(p.n, BLK_MAIN);
     xi_react = u01(b0.z, b0.w);
@@ -545,14 +554,36 @@ __device__ __forceinline__ bool mono_event(const DevProblem& P, const RunParams&
     return finish_event(P, R, p, type, T, acc, B);
 }
 
-// Decomposed collision event: repeats the (cheap) lookup and the reaction draw.
+// Lookup event (decomposition with the lookup as an event of its own): the
+// cross sections of the particle's material at its energy or group, kept in
+// the particle for the step and collision that follow.  Does not count as an
+// event (n unchanged).
 template <bool CE>
+__device__ __forceinline__ void lookup_event(const DevProblem& P, Particle& p)
+{
+    XS X;
+    xs_lookup<CE>(P, p, material(P, p.cell), X);
+    p.xst = X.st;
+    p.xist = X.inv_st;
+    p.xsa = X.sa;
+    p.xnsf = X.nsf;
+}
+
+// Decomposed collision event: repeats the lookup (or, CACHED, takes the
+// particle's) and the reaction draw.
+template <bool CE, bool CACHED = false>
 __device__ __forceinline__ bool split_collide(const DevProblem& P, const RunParams& R, Particle& p, const Tallies& T,
                                              Acc& acc, const Bank& B, ErrorWord* err, unsigned em = 0u)
 {
     XS X;
-    const int m = material(P, p.cell);
-    xs_lookup<CE>(P, p, m, X);
+    if (CACHED) {
+        X.st = p.xst;
+        X.inv_st = p.xist;
+        X.sa = p.xsa;
+        X.nsf = p.xnsf;
+    } else {
+        xs_lookup<CE>(P, p, material(P, p.cell), X);
+    }
     const Stream S = make_stream(R, p.id);
     const uint4 b0 = S.block(p.n, BLK_MAIN);
     const int type = collide_event<CE>(P, R, p, X, u01(b0.z, b0.w), B, err, em);
@@ -566,11 +597,26 @@ __device__ __forceinline__ bool split_surface(const DevProblem& P, const RunPara
     return finish_event(P, R, p, type, T, acc, B);
 }
 
+// Surface event of the lookup-event decomposition: the next event is a lookup
+// when the particle entered another material, else the step (the cached cross
+// sections depend only on material and energy).
+__device__ __forceinline__ int split_surface_next(const DevProblem& P, const RunParams& R, Particle& p,
+                                                  const Tallies& T, Acc& acc, const Bank& B)
+{
+    const int m0 = material(P, p.cell);
+    const int type = surface_event(P, p);
+    if (!finish_event(P, R, p, type, T, acc, B)) return Q_DEAD;
+    return material(P, p.cell) != m0 ? Q_LOOKUP : Q_STEP;
+}
+
 // ---------------------------------------------------------------------------
 // SoA load / store
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ void load_particle(const SoA& s, unsigned long long i, Particle& p, bool ce)
+__device__ __forceinline__ void load_particle(const SoA& s, unsigned long long i, Particle& p, bool ce, bool xs = false)
 {
+    if (xs) {
+        p.xst = s.xst[i]; p.xist = s.xist[i]; p.xsa = s.xsa[i]; p.xnsf = s.xnsf[i];
+    }
     p.x = s.x[i]; p.y = s.y[i]; p.z = s.z[i];
     p.u = s.u[i]; p.v = s.v[i]; p.w = s.w[i];
     p.iu = s.iu[i]; p.iv = s.iv[i]; p.iw = s.iw[i]; p.ia = s.ia[i];
@@ -579,8 +625,12 @@ __device__ __forceinline__ void load_particle(const SoA& s, unsigned long long i
     p.prob = s.prob[i];
 }
 
-__device__ __forceinline__ void store_particle(const SoA& s, unsigned long long i, const Particle& p, bool ce)
+__device__ __forceinline__ void store_particle(const SoA& s, unsigned long long i, const Particle& p, bool ce,
+                                               bool xs = false)
 {
+    if (xs) {
+        s.xst[i] = p.xst; s.xist[i] = p.xist; s.xsa[i] = p.xsa; s.xnsf[i] = p.xnsf;
+    }
     s.x[i] = p.x; s.y[i] = p.y; s.z[i] = p.z;
     s.u[i] = p.u; s.v[i] = p.v; s.w[i] = p.w;
     s.iu[i] = p.iu; s.iv[i] = p.iv; s.iw[i] = p.iw; s.ia[i] = p.ia;

@@ -10,9 +10,9 @@ void count_launches(unsigned long long n);
 
 // Control block of one stack-scheme launch (device memory).
 struct StackCtl {
-    unsigned long long in_count[3];    // particles in each input stack
-    unsigned long long out_count[3];   // pushes into each output stack
-    unsigned long long reserve[3];     // output-stack reservations (make_work threshold)
+    unsigned long long in_count[N_QUEUES];    // particles in each input stack
+    unsigned long long out_count[N_QUEUES];   // pushes into each output stack
+    unsigned long long reserve[N_QUEUES];     // output-stack reservations (make_work threshold)
     unsigned long long pop;            // virtual pop cursor over the input stacks
     unsigned long long src_cursor;     // next source index (make_work)
     unsigned long long capacity;       // particles per stack
@@ -30,7 +30,7 @@ struct AsyncCtl {
 };
 
 cudaError_t launch_stack(const DevProblem& P, const RunParams& R, const SoA* in, const SoA* out, StackCtl* ctl,
-                         const Tallies& T, const Bank& bank, const Bank* src, ErrorWord* err, int split, int blocks,
+                         const Tallies& T, const Bank& bank, const Bank* src, ErrorWord* err, int dec, int blocks,
                          cudaStream_t st);
 
 struct AsyncArgs {
@@ -42,7 +42,7 @@ struct AsyncArgs {
     AsyncCtl* ctl;
     Bank bank, src;
     int use_src;
-    int split;
+    int dec;                           // task decomposition: DEC_MONO, DEC_SPLIT, DEC_LOOKUP
     int stash_slots;
     // batched launches: per-problem descriptors, tallies and history offsets
     const DevProblem* probs;
@@ -53,10 +53,10 @@ struct AsyncArgs {
 
 cudaError_t launch_async(const DevProblem& P, const RunParams& R, const AsyncArgs& A, const Tallies& T, ErrorWord* err,
                          int blocks, cudaStream_t st, int* smem_bytes_out);
-int async_max_blocks_per_sm(const DevProblem& P, int split, int stash_slots);
+int async_max_blocks_per_sm(const DevProblem& P, int dec, int stash_slots);
 cudaError_t launch_async_batched(const DevProblem& P0, const RunParams& R, const AsyncArgs& A, ErrorWord* err,
                                  int blocks, cudaStream_t st);
-int async_batched_max_blocks_per_sm(int split, int stash_slots);
+int async_batched_max_blocks_per_sm(int dec, int stash_slots);
 struct ScaleJob {
     const double* in;
     double* out;

@@ -89,6 +89,7 @@ void carve_links(unsigned char* b, unsigned long long n, SoA& s)
     s.u = (double*)take(8); s.v = (double*)take(8); s.w = (double*)take(8);
     s.iu = (double*)take(8); s.iv = (double*)take(8); s.iw = (double*)take(8); s.ia = (double*)take(8);
     s.E = (double*)take(8);
+    s.xst = s.xist = s.xsa = s.xnsf = nullptr;   // the lookup-event decomposition is not offered here
     s.g = (int*)take(4);
     s.cell = (unsigned*)take(4); s.id = (unsigned*)take(4); s.n = (unsigned*)take(4);
     s.nsites = (unsigned*)take(4); s.pend = (unsigned*)take(4); s.prob = (unsigned*)take(4);
@@ -112,7 +113,7 @@ extern "C" tr_status tr_run_fixed_source_noalloc(tr_problem* problem, const tr_r
     if (!problem || !o) return fail(TR_ERR_INVALID, "NULL problem or options");
     if (o->scheme != TR_SCHEME_ASYNC) return fail(TR_ERR_INVALID, "the no-allocation run uses the asynchronous scheme");
     if (o->decomposition != TR_DECOMP_MONO && o->decomposition != TR_DECOMP_SPLIT)
-        return fail(TR_ERR_INVALID, "bad decomposition");
+        return fail(TR_ERR_INVALID, "decomposition must be TR_DECOMP_MONO or TR_DECOMP_SPLIT");
     if (o->want_event_log) return fail(TR_ERR_INVALID, "the no-allocation run keeps no event log");
     if (o->n_histories >= (1ull << 32) || o->first_history + o->n_histories > (1ull << 32))
         return fail(TR_ERR_INVALID, "histories must stay below 2^32");
@@ -146,7 +147,7 @@ extern "C" tr_status tr_run_fixed_source_noalloc(tr_problem* problem, const tr_r
     carve_links(base + OFF_LINKS, NOALLOC_LINKS * 32, A.links);
     A.n_links = o->queue_capacity ? (o->queue_capacity + 31) / 32 : NOALLOC_LINKS;
     A.use_src = 0;
-    A.split = o->decomposition == TR_DECOMP_SPLIT ? 1 : 0;
+    A.dec = o->decomposition;
     A.stash_slots = S;
 
     RunParams R{};
@@ -179,7 +180,7 @@ extern "C" tr_status tr_run_fixed_source_noalloc(tr_problem* problem, const tr_r
     T.ev_type = counts;
     T.fin_type = counts + 8;
     if (o->n_histories > 0) {
-        const int maxb = async_max_blocks_per_sm(P, A.split, S);
+        const int maxb = async_max_blocks_per_sm(P, A.dec, S);
         if (maxb < 1) return fail(TR_ERR_INVALID, "stash does not fit in shared memory");
         const int bps = o->blocks_per_sm > 0 ? (o->blocks_per_sm < maxb ? o->blocks_per_sm : maxb) : maxb;
         int smem = 0;

@@ -18,9 +18,12 @@ namespace tr {
 
 constexpr unsigned FULL = 0xFFFFFFFFu;
 
-// warp-aggregated push of `p` (if `live`) onto stack `dst` of the output set
+// warp-aggregated push of `p` (if `live`) onto stack `dst` of the output set;
+// a push beyond the capacity (which the launch-threshold rule prevents) is not
+// written and raises a capacity error
 __device__ __forceinline__ void push_to(const SoA* outs, unsigned long long* out_count, int dst, bool live,
-                                        const Particle& p, bool ce)
+                                        const Particle& p, bool ce, unsigned long long cap, ErrorWord* err,
+                                        bool xs = false)
 {
     const int lane = threadIdx.x & 31;
     const unsigned act = __ballot_sync(FULL, live);
@@ -32,8 +35,9 @@ __device__ __forceinline__ void push_to(const SoA* outs, unsigned long long* out
     if (live && lane == leader) base = atomicAdd(out_count + dst, (unsigned long long)__popc(grp));
     base = __shfl_sync(FULL, base, leader);
     if (live) {
-        const unsigned rank = __popc(grp & ((1u << lane) - 1u));
-        store_particle(outs[dst], base + rank, p, ce);
+        const unsigned long long pos = base + __popc(grp & ((1u << lane) - 1u));
+        if (pos < cap) store_particle(outs[dst], pos, p, ce, xs);
+        else atomicCAS(&err->code, 0, ERR_CAPACITY);
     }
 }
 
@@ -91,23 +95,29 @@ __global__ void __launch_bounds__(256) k_stack_mono(DevProblem P, RunParams R, S
                 acc.ev[EV_SOURCE] += 1u;
             }
         }
-        push_to(A.out, ctl->out_count, Q_STEP, live, p, CE);
+        push_to(A.out, ctl->out_count, Q_STEP, live, p, CE, cap, err);
     }
     flush_acc(acc, T);
 }
 
-// Decomposed scheme: step / collision / surface stacks processed in one
-// launch; each warp's 32 virtual indices fall in one stack (ranges padded to
-// 32), so a warp runs one event type.
-template <bool CE>
+// Decomposed schemes: the event stacks (step / collision / surface, and with
+// DEC_LOOKUP the lookup) processed in one launch; each warp's 32 virtual
+// indices fall in one stack (ranges padded to 32), so a warp runs one event
+// type.  With DEC_LOOKUP every collision and surface crossing is followed by a
+// lookup, so each output stack receives at most one input stack's particles
+// (plus reserved sources) and cannot overflow.
+template <bool CE, int DEC>
 __global__ void __launch_bounds__(256) k_stack_split(DevProblem P, RunParams R, StackArgs A, Tallies T, ErrorWord* err)
 {
+    constexpr int nq = dec_queues(DEC);
+    constexpr bool XS = DEC == DEC_LOOKUP;
+    constexpr int FIRST = XS ? Q_LOOKUP : Q_STEP;   // where sources start
     const int lane = threadIdx.x & 31;
     StackCtl* ctl = A.ctl;
-    unsigned long long cnt[N_QUEUES], start[N_QUEUES + 1];
+    unsigned long long cnt[nq], start[nq + 1];
     start[0] = 0;
 #pragma unroll
-    for (int q = 0; q < N_QUEUES; ++q) {
+    for (int q = 0; q < nq; ++q) {
         cnt[q] = ctl->in_count[q];
         start[q + 1] = start[q] + ((cnt[q] + 31ull) & ~31ull);
     }
@@ -120,25 +130,29 @@ __global__ void __launch_bounds__(256) k_stack_split(DevProblem P, RunParams R, 
         base = __shfl_sync(FULL, base, 0);
         Particle p;
         bool live = false;
-        int dst = Q_STEP;
-        if (base < start[N_QUEUES]) {
+        int dst = XS ? Q_LOOKUP : Q_STEP;
+        if (base < start[nq]) {
             int q = 0;
-            if (base >= start[1]) q = 1;
-            if (base >= start[2]) q = 2;
+#pragma unroll
+            for (int k = 1; k < nq; ++k)
+                if (base >= start[k]) q = k;
             const unsigned long long i = base - start[q] + lane;
-            if (i < cnt[q]) load_particle(A.in[q], i, p, CE);
+            if (i < cnt[q]) load_particle(A.in[q], i, p, CE, XS);
             __syncwarp();
             const unsigned em = __ballot_sync(FULL, i < cnt[q]);   // the lanes that hold a particle
             if (i < cnt[q]) {
                 live = true;
                 if (q == Q_STEP) {
-                    XS X;
+                    tr::XS X;
                     double xr;
                     FwdSink sink{T, acc};
-                    step_event<CE>(P, R, p, sink, X, xr);
+                    step_event<CE, XS>(P, R, p, sink, X, xr);
                     dst = next_queue_after_step(p);
                 } else if (q == Q_COLLIDE) {
-                    live = split_collide<CE>(P, R, p, T, acc, A.bank, err, em);
+                    live = split_collide<CE, XS>(P, R, p, T, acc, A.bank, err, em);
+                } else if (XS && q == Q_LOOKUP) {
+                    lookup_event<CE>(P, p);
+                    dst = Q_STEP;
                 } else {
                     live = split_surface(P, R, p, T, acc, A.bank);
                 }
@@ -146,7 +160,7 @@ __global__ void __launch_bounds__(256) k_stack_split(DevProblem P, RunParams R, 
         } else {
             unsigned long long first = ~0ull;
             if (lane == 0 && *(volatile unsigned long long*)&ctl->src_cursor < R.n_hist) {
-                const unsigned long long r = atomicAdd(&ctl->reserve[Q_STEP], 32ull);
+                const unsigned long long r = atomicAdd(&ctl->reserve[FIRST], 32ull);
                 if (r + 32ull <= cap) first = atomicAdd(&ctl->src_cursor, 32ull);
             }
             first = __shfl_sync(FULL, first, 0);
@@ -159,7 +173,7 @@ __global__ void __launch_bounds__(256) k_stack_split(DevProblem P, RunParams R, 
                 acc.ev[EV_SOURCE] += 1u;
             }
         }
-        push_to(A.out, ctl->out_count, dst, live, p, CE);
+        push_to(A.out, ctl->out_count, dst, live, p, CE, cap, err, XS);
     }
     flush_acc(acc, T);
 }
@@ -359,7 +373,7 @@ static int grid_for(unsigned long long n, int threads, int max_blocks)
 }
 
 cudaError_t launch_stack(const DevProblem& P, const RunParams& R, const SoA* in, const SoA* out, StackCtl* ctl,
-                         const Tallies& T, const Bank& bank, const Bank* src, ErrorWord* err, int split, int blocks,
+                         const Tallies& T, const Bank& bank, const Bank* src, ErrorWord* err, int dec, int blocks,
                          cudaStream_t st)
 {
     StackArgs A;
@@ -373,9 +387,12 @@ cudaError_t launch_stack(const DevProblem& P, const RunParams& R, const SoA* in,
     if (src) A.src = *src;
     else A.src = bank;
     count_launches(1);
-    if (split) {
-        if (P.kind == 1) k_stack_split<true><<<blocks, 256, 0, st>>>(P, R, A, T, err);
-        else k_stack_split<false><<<blocks, 256, 0, st>>>(P, R, A, T, err);
+    if (dec == DEC_LOOKUP) {
+        if (P.kind == 1) k_stack_split<true, DEC_LOOKUP><<<blocks, 256, 0, st>>>(P, R, A, T, err);
+        else k_stack_split<false, DEC_LOOKUP><<<blocks, 256, 0, st>>>(P, R, A, T, err);
+    } else if (dec == DEC_SPLIT) {
+        if (P.kind == 1) k_stack_split<true, DEC_SPLIT><<<blocks, 256, 0, st>>>(P, R, A, T, err);
+        else k_stack_split<false, DEC_SPLIT><<<blocks, 256, 0, st>>>(P, R, A, T, err);
     } else {
         if (P.kind == 1) k_stack_mono<true><<<blocks, 256, 0, st>>>(P, R, A, T, err);
         else k_stack_mono<false><<<blocks, 256, 0, st>>>(P, R, A, T, err);

@@ -14,8 +14,10 @@ from tests._util import assert_logs_equal, assert_tally_close
 pytestmark = pytest.mark.gpu
 
 SCHEMES = [(tb.SCHEME_STACK, tb.DECOMP_MONO), (tb.SCHEME_STACK, tb.DECOMP_SPLIT),
-           (tb.SCHEME_ASYNC, tb.DECOMP_MONO), (tb.SCHEME_ASYNC, tb.DECOMP_SPLIT)]
-IDS = ["stack-mono", "stack-split", "async-mono", "async-split"]
+           (tb.SCHEME_STACK, tb.DECOMP_SPLIT_LOOKUP),
+           (tb.SCHEME_ASYNC, tb.DECOMP_MONO), (tb.SCHEME_ASYNC, tb.DECOMP_SPLIT),
+           (tb.SCHEME_ASYNC, tb.DECOMP_SPLIT_LOOKUP)]
+IDS = ["stack-mono", "stack-split", "stack-lookup", "async-mono", "async-split", "async-lookup"]
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -139,6 +141,8 @@ def test_scheduler_invariance_tuning():
         (tb.SCHEME_ASYNC, tb.DECOMP_MONO, dict(remap_every=3, stash_slots=288, blocks_per_sm=1)),
         (tb.SCHEME_ASYNC, tb.DECOMP_SPLIT, dict(stash_slots=288, spill_threshold=-32, queue_capacity=4096)),
         (tb.SCHEME_ASYNC, tb.DECOMP_MONO, dict(spill_threshold=-32, queue_capacity=64 * 32)),
+        (tb.SCHEME_STACK, tb.DECOMP_SPLIT_LOOKUP, dict(queue_capacity=96)),
+        (tb.SCHEME_ASYNC, tb.DECOMP_SPLIT_LOOKUP, dict(stash_slots=288, spill_threshold=-32, queue_capacity=4096)),
     ]
     for scheme, decomp, kw in variants:
         g = _gpu_fixed("lattice", n, scheme, decomp, **kw)
@@ -172,9 +176,10 @@ def test_ce_full_size_sampled_histories():
     ids = np.unique(rng.integers(0, n, 400))
     ref = [oracle.run_fixed_source(p, 1, seed=1, id_offset=int(i)) for i in ids]
     ref_log = tuple(np.array([r[k][0] for r in ref]) for k in ("log_n", "log_cell", "log_type"))
-    g = _gpu_fixed("ce_full", n, tb.SCHEME_ASYNC, tb.DECOMP_SPLIT)
-    assert_logs_equal(tuple(a[ids] for a in g["log"]), ref_log, "sampled CE")
-    assert abs(g["energy"].sum() - g["scalars"][0]) <= 1e-10 * g["scalars"][0]
+    for decomp in (tb.DECOMP_SPLIT, tb.DECOMP_SPLIT_LOOKUP):
+        g = _gpu_fixed("ce_full", n, tb.SCHEME_ASYNC, decomp)
+        assert_logs_equal(tuple(a[ids] for a in g["log"]), ref_log, "sampled CE")
+        assert abs(g["energy"].sum() - g["scalars"][0]) <= 1e-10 * g["scalars"][0]
 
 
 # --------------------------------------------------------------- error paths
@@ -201,7 +206,7 @@ def test_bank_overflow_is_capacity_error():
 def test_invalid_options_rejected():
     prob = tb.Problem(_problem("cube"))
     for bad in (dict(scheme=7), dict(decomposition=5), dict(decomposition=tb.DECOMP_SPLIT, remap_every=2),
-                dict(n_histories=1 << 33)):
+                dict(decomposition=tb.DECOMP_SPLIT_LOOKUP, remap_every=2), dict(n_histories=1 << 33)):
         kw = dict(n_histories=10)
         kw.update(bad)
         with pytest.raises(tb.TransportError) as e:
