@@ -592,6 +592,36 @@ def run_ce_sweep(args):
     return 0
 
 
+def run_ce_time_sweep(args):
+    """The paper's temporal tally resolution (Sec. 4): the CE pin cell with a
+    14 MeV source and a census at 1 microsecond, over time-tally widths 1..128
+    (powers of two) and histories, for stack and asynchronous remapping under
+    the three decompositions, with each point's speedup over stack remapping
+    with the monolithic scheme.  One JSON line per point."""
+    import torch
+    ws, rank, tb, inputs = _setup(torch)
+    if rank != 0:
+        return 0
+    base_spec = inputs.ce_pin_cell(n_ebins=1, source_energy=14e6)
+    for nb in (1, 2, 4, 8, 16, 32, 64, 128):
+        prob = tb.Problem(base_spec.replace(t_census=1e-6, n_time_bins=nb))
+        for n in (100_000, 1_000_000):
+            base = None
+            for scheme in ("stack", "async"):
+                for dname in ("mono", "split", "lookup"):
+                    opts = tb.RunOpts(n_histories=n, seed=1, decomposition=_DECOMPS[dname], remap_every=1,
+                                      scheme=tb.SCHEME_ASYNC if scheme == "async" else tb.SCHEME_STACK)
+                    t, ev = _time_fixed(torch, tb, prob, opts, 2, 1)
+                    rate = ev / t
+                    if base is None:
+                        base = rate
+                    print(json.dumps({"workload": "ce-time-sweep", "time_bins": nb, "histories": n,
+                                      "scheme": scheme, "decomposition": dname, "events_per_s": rate,
+                                      "speedup_vs_stack_mono": rate / base}), flush=True)
+        prob.close()
+    return 0
+
+
 def run_lattice_sweep(args):
     """The paper's multigroup comparison (Sec. 5.1): power iterations of the
     lattice with 25 % inactive cycles, over particles per cycle and cycle
@@ -679,7 +709,8 @@ def main():
     ap.add_argument("--bps", type=int, default=0, help="blocks per SM (0 = default)")
     ap.add_argument("--remap", type=int, default=3, help="monolithic: events between remaps")
     ap.add_argument("--queue", type=int, default=0, help="stack: particles per stack; async: spill links x 32")
-    ap.add_argument("--workload", choices=["lattice", "batched", "adjoint", "ce", "ce-sweep", "lattice-sweep"],
+    ap.add_argument("--workload", choices=["lattice", "batched", "adjoint", "ce", "ce-sweep", "ce-time-sweep",
+                                           "lattice-sweep"],
                     default="lattice",
                     help="lattice: the k-eigenvalue lattice; batched: 256 box problems in one launch; "
                          "adjoint: forward + derivative kernels on the fixed-source lattice; ce: the continuous-"
@@ -699,6 +730,8 @@ def main():
         return run_ce_workload(args)
     if args.workload == "ce-sweep":
         return run_ce_sweep(args)
+    if args.workload == "ce-time-sweep":
+        return run_ce_time_sweep(args)
     if args.workload == "lattice-sweep":
         return run_lattice_sweep(args)
     return run_ours(args)

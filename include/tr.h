@@ -94,6 +94,7 @@ typedef struct {
     const double *nuc_awr;              /* n_nuclides */
     const double *density;              /* [n_materials][n_nuclides] */
     double energy_cutoff;
+    const double *inv_velocity;         /* MG: [n_groups] inverse speeds (s/cm), needed by timed problems */
 } tr_xs_desc;
 
 /* Source (the make_work entry point of Sec. 3).  POINT: fixed position,
@@ -117,7 +118,14 @@ typedef struct {
  * axis (per group when by_group != 0, multigroup only), and an optional
  * continuous-energy flux tally per material over n_energy_bins bins with
  * ascending edges.  The flux, absorption-rate and production-rate totals are
- * always scored. */
+ * always scored.
+ * Time (the paper's temporal tally resolution, Sec. 4; the formulas are our
+ * reading): t_census > 0 makes the problem timed.  Histories start at t = 0
+ * and move at speed 1/inv_velocity[g] (multigroup) or c sqrt(2E / m_n c^2)
+ * (continuous energy); a history whose time would pass t_census first ends
+ * there with the event TR_EV_CUTOFF.  n_time_bins > 0 (at most 4096) adds a
+ * flux tally over that many uniform bins of [0, t_census).  Timed problems
+ * run fixed source only. */
 typedef struct {
     int32_t has_mesh;
     int32_t mesh_n[3];
@@ -125,6 +133,8 @@ typedef struct {
     int32_t n_energy_bins;
     double mesh_lo[3], mesh_hi[3];
     const double *energy_edges;         /* n_energy_bins + 1 */
+    int32_t n_time_bins;                /* 0 .. 4096 (needs t_census > 0) */
+    double t_census;                    /* s; 0 = untimed */
 } tr_tally_desc;
 
 /* Device context.  alloc/free (optional) receive the byte size or pointer,
@@ -266,10 +276,10 @@ tr_status tr_sensitivities(tr_problem *problem, const tr_run_opts *opts, const d
                            const double *d_grad_scalars, double *d_sigt, double *d_sigs, double *d_nusigf);
 
 /* Tally ids for tr_tallies / tr_tally_stddev. */
-enum { TR_TALLY_MESH = 0, TR_TALLY_ENERGY = 1, TR_TALLY_SCALARS = 2 };
+enum { TR_TALLY_MESH = 0, TR_TALLY_ENERGY = 1, TR_TALLY_SCALARS = 2, TR_TALLY_TIME = 3 };
 
 /* Copy a tally (mesh: [group][z][y][x]; energy: [material][bin]; scalars:
- * flux, absorption rate, production rate) into `out`, host memory unless
+ * flux, absorption rate, production rate; time: [bin]) into `out`, host memory unless
  * out_on_device != 0.  n_out must equal the tally size (TR_ERR_INVALID
  * otherwise).  Synchronises the context stream. */
 tr_status tr_tallies(const tr_problem *problem, int32_t tally_id, double *out, size_t n_out, int32_t out_on_device);

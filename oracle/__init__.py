@@ -64,6 +64,7 @@ class OrcProblem(C.Structure):
         ("n_ebins", C.c_int32),
         ("mesh_lo", C.c_double * 3), ("mesh_hi", C.c_double * 3),
         ("e_edges", C.POINTER(C.c_double)),
+        ("inv_vel", C.POINTER(C.c_double)), ("n_tbins", C.c_int32), ("t_cen", C.c_double),
     ]
 
 
@@ -76,6 +77,7 @@ class OrcFixed(C.Structure):
         ("hist_track", C.POINTER(C.c_double)), ("hist_coll", C.POINTER(C.c_uint32)),
         ("scalars", C.c_double * 3),
         ("events_by_type", C.c_uint64 * 8), ("final_by_type", C.c_uint64 * 8),
+        ("time_tally", C.POINTER(C.c_double)),
     ]
 
 
@@ -209,6 +211,10 @@ class _Marshalled:
         if prob.energy_edges is not None:
             s.n_ebins = len(prob.energy_edges) - 1
             s.e_edges = f64(prob.energy_edges)
+        s.t_cen = float(getattr(prob, "t_census", 0.0) or 0.0)
+        s.n_tbins = int(getattr(prob, "n_time_bins", 0) or 0)
+        if getattr(prob, "inv_velocity", None) is not None:
+            s.inv_vel = f64(prob.inv_velocity)
         self.s = s
 
 
@@ -220,8 +226,10 @@ def run_fixed_source(prob, n_hist: int, seed: int = 1, tag: int = 0, max_events:
     m = _Marshalled(prob)
     o = OrcFixed()
     o.n_hist, o.seed, o.tag, o.max_events, o.id_offset = n_hist, seed, tag, max_events, id_offset
-    out = {"mesh": np.zeros(prob.mesh_size), "energy": np.zeros(prob.energy_size)}
+    out = {"mesh": np.zeros(prob.mesh_size), "energy": np.zeros(prob.energy_size),
+           "time": np.zeros(int(getattr(prob, "n_time_bins", 0) or 0))}
     o.mesh, o.energy = _dp(out["mesh"]), _dp(out["energy"])
+    o.time_tally = _dp(out["time"]) if out["time"].size else None
     if logs:
         out["log_n"] = np.zeros(n_hist, np.uint32)
         out["log_cell"] = np.zeros(n_hist, np.int32)

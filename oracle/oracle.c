@@ -257,7 +257,8 @@ typedef struct {
     int64_t n_rows;
     int64_t mesh_vox;
     /* tallies */
-    nsum *mesh, *energy, scal[3];
+    nsum *mesh, *energy, scal[3], *time;
+    double v_c;          /* CE speed per sqrt(eV): v = v_c sqrt(E) cm/s */
     /* run */
     uint64_t seed;
     uint32_t tag, max_events;
@@ -317,6 +318,15 @@ static int setup(ctx *C, const orc_problem *P)
     C->mesh = calloc((size_t)(msize > 0 ? msize : 1), sizeof(nsum));
     int64_t esize = (int64_t)P->n_ebins * P->n_mat;
     C->energy = calloc((size_t)(esize > 0 ? esize : 1), sizeof(nsum));
+    if (P->t_cen < 0.0 || P->n_tbins < 0 || (P->n_tbins > 0 && !(P->t_cen > 0.0))) return ORC_ERR_INVALID;
+    if (P->t_cen > 0.0 && P->xs_kind == 0) {
+        if (!P->inv_vel) return ORC_ERR_INVALID;
+        for (int g = 0; g < C->G; ++g)
+            if (!(P->inv_vel[g] > 0.0)) return ORC_ERR_INVALID;
+    }
+    C->time = calloc((size_t)(P->n_tbins > 0 ? P->n_tbins : 1), sizeof(nsum));
+    /* neutron speed from kinetic energy: v = c sqrt(2 E / (m_n c^2)) */
+    C->v_c = 2.99792458e10 * sqrt(2.0 / 939.56542052e6);
     return ORC_OK;
 }
 
@@ -324,7 +334,7 @@ static void teardown(ctx *C)
 {
     free(C->rec);
     free(C->inv_sigt); free(C->cum_s); free(C->sig_a); free(C->cum_chi); free(C->inv_de);
-    free(C->mesh); free(C->energy);
+    free(C->mesh); free(C->energy); free(C->time);
     free(C->bank_pos); free(C->bank_g); free(C->bank_cell); free(C->bank_E);
 }
 
@@ -335,6 +345,7 @@ static void clear_tallies(ctx *C)
     if (msize > 0) memset(C->mesh, 0, sizeof(nsum) * (size_t)msize);
     int64_t esize = (int64_t)P->n_ebins * P->n_mat;
     if (esize > 0) memset(C->energy, 0, sizeof(nsum) * (size_t)esize);
+    if (P->n_tbins > 0) memset(C->time, 0, sizeof(nsum) * (size_t)P->n_tbins);
     memset(C->scal, 0, sizeof(C->scal));
 }
 
@@ -343,6 +354,7 @@ static void clear_tallies(ctx *C)
 /* ------------------------------------------------------------------------ */
 typedef struct {
     double x[3], d[3], E;
+    double t;                            /* time since the source (timed problems) */
     int32_t g, ci[3], in;
     uint32_t n;
     uint64_t id;
@@ -770,6 +782,27 @@ static void collide(ctx *C, particle *p, int m, const xsval *X, double xi_react)
     if (p->E < P->e_cut) kill(p, ORC_CUTOFF);
 }
 
+/* Time tally (our reading of the paper's temporal tally resolution, Sec. 4):
+ * the segment occupies [t0, t1] in time; each uniform bin b of width
+ * w = t_cen / n_tbins gets the track length spent in it, (hi - lo) / inv_v
+ * with [lo, hi] = [t0, t1] clipped to [b w, (b + 1) w]. */
+static void score_time(ctx *C, double t0, double t1, double inv_v)
+{
+    const orc_problem *P = C->P;
+    if (P->n_tbins <= 0 || !(t1 > t0)) return;
+    const int nb = P->n_tbins;
+    const double w = P->t_cen / (double)nb;
+    int b = (int)floor(t0 / w);
+    if (b < 0) b = 0;
+    for (; b < nb; ++b) {
+        double lo = (double)b * w, hi = (double)(b + 1) * w;
+        if (lo >= t1) break;
+        if (t0 > lo) lo = t0;
+        if (t1 < hi) hi = t1;
+        if (hi > lo) nadd(&C->time[b], (hi - lo) / inv_v);
+    }
+}
+
 static void event(ctx *C, particle *p)
 {
     const orc_problem *P = C->P;
@@ -825,10 +858,23 @@ static void event(ctx *C, particle *p)
     }
     int collided = dcol < ds;
     double dist = collided ? dcol : ds;
+    /* timed problems: the census ends the history when it comes strictly
+     * before the collision or surface (speed from the group or the energy) */
+    int census = 0;
+    double inv_v = 0.0;
+    if (P->t_cen > 0.0) {
+        inv_v = (P->xs_kind == 1) ? 1.0 / (C->v_c * sqrt(p->E)) : P->inv_vel[p->g];
+        double left = P->t_cen - p->t;
+        double dcen = left > 0.0 ? left / inv_v : 0.0;
+        if (dcen < dist) {
+            census = 1;
+            dist = dcen;
+        }
+    }
 
     /* move and score the path */
     double p0[3] = {p->x[0], p->x[1], p->x[2]};
-    if (!collided && ds == INFINITY) {
+    if (!census && !collided && ds == INFINITY) {
         /* no surface ahead and no collision: the particle escapes */
         kill(p, ORC_LEAK);
         C->events_by_type[ORC_LEAK]++;
@@ -839,10 +885,18 @@ static void event(ctx *C, particle *p)
     p->x[1] = fma(dist, p->d[1], p->x[1]);
     p->x[2] = fma(dist, p->d[2], p->x[2]);
     score_segment(C, p, p0, dist, m, &X);
+    if (P->t_cen > 0.0) {
+        double t0 = p->t;
+        p->t = census ? P->t_cen : fma(dist, inv_v, p->t);
+        score_time(C, t0, p->t, inv_v);
+    }
     p->track += dist;
     if (C->recording) record_event(C, p, m, collided, dist, weighted_segment(C, p, p0, dist, &X));
 
-    if (collided) {
+    if (census) {
+        kill(p, ORC_CUTOFF);
+        C->events_by_type[ORC_CUTOFF]++;
+    } else if (collided) {
         collide(C, p, m, &X, xi[1]);
     } else if (cyl_hit) {
         p->in = !p->in;
@@ -899,6 +953,12 @@ static void finish_tallies(ctx *C, double norm, double *mesh, double *energy, do
     for (int i = 0; i < 3; ++i) scal[i] = nval(&C->scal[i]) / norm;
 }
 
+static void finish_time(ctx *C, double norm, double *out)
+{
+    if (out)
+        for (int b = 0; b < C->P->n_tbins; ++b) out[b] = nval(&C->time[b]) / norm;
+}
+
 int orc_fixed_source(const orc_problem *P, orc_fixed *o)
 {
     ctx C;
@@ -922,6 +982,7 @@ int orc_fixed_source(const orc_problem *P, orc_fixed *o)
         if (o->hist_coll) o->hist_coll[i] = p.coll;
     }
     finish_tallies(&C, (double)o->n_hist, o->mesh, o->energy, o->scalars);
+    finish_time(&C, (double)o->n_hist, o->time_tally);
     memcpy(o->events_by_type, C.events_by_type, sizeof(C.events_by_type));
     teardown(&C);
     return st;
@@ -943,7 +1004,7 @@ int orc_fixed_source(const orc_problem *P, orc_fixed *o)
 /* ------------------------------------------------------------------------ */
 int orc_sensitivities(const orc_problem *P, orc_sens *o)
 {
-    if (P->xs_kind != 0) return ORC_ERR_INVALID;
+    if (P->xs_kind != 0 || P->t_cen > 0.0) return ORC_ERR_INVALID;   /* untimed multigroup only */
     ctx C;
     int st = setup(&C, P);
     if (st) { teardown(&C); return st; }
@@ -1020,7 +1081,7 @@ int orc_sensitivities(const orc_problem *P, orc_sens *o)
 /* ------------------------------------------------------------------------ */
 int orc_power_iteration(const orc_problem *P, orc_eig *o)
 {
-    if (P->xs_kind != 0) return ORC_ERR_INVALID;
+    if (P->xs_kind != 0 || P->t_cen > 0.0) return ORC_ERR_INVALID;   /* untimed multigroup only */
     ctx C;
     int st = setup(&C, P);
     if (st) { teardown(&C); return st; }

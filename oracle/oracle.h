@@ -54,6 +54,12 @@ typedef struct {
     int32_t has_mesh, mesh_n[3], mesh_by_group, n_ebins;
     double mesh_lo[3], mesh_hi[3];
     const double *e_edges;               /* n_ebins + 1 */
+    /* time (0 = untimed): particles start at t = 0 and end at the census time
+     * t_cen; speeds from inv_vel[g] (multigroup, s/cm) or from the energy
+     * (continuous energy); n_tbins uniform time bins over [0, t_cen) */
+    const double *inv_vel;
+    int32_t n_tbins;
+    double t_cen;
 } orc_problem;
 
 typedef struct {
@@ -73,6 +79,7 @@ typedef struct {
     double scalars[3];                   /* flux, absorption rate, production rate per source particle */
     uint64_t events_by_type[8];          /* processed events by type (SOURCE counted) */
     uint64_t final_by_type[8];           /* histories by final type */
+    double *time_tally;                  /* [n_tbins] flux per time bin, mean per source particle (may be NULL) */
 } orc_fixed;
 
 typedef struct {

@@ -26,7 +26,7 @@ STATUS_NAMES = {0: "TR_OK", 1: "TR_ERR_INVALID", 2: "TR_ERR_NOMEM", 3: "TR_ERR_C
 EV_SOURCE, EV_SCATTER, EV_ABSORB, EV_SURF_INTERNAL, EV_SURF_REFLECT, EV_LEAK, EV_CUTOFF, EV_MAXEV = range(8)
 SCHEME_STACK, SCHEME_ASYNC = 0, 1
 DECOMP_MONO, DECOMP_SPLIT, DECOMP_SPLIT_LOOKUP = 0, 1, 2
-TALLY_MESH, TALLY_ENERGY, TALLY_SCALARS = 0, 1, 2
+TALLY_MESH, TALLY_ENERGY, TALLY_SCALARS, TALLY_TIME = 0, 1, 2, 3
 
 _dp = C.POINTER(C.c_double)
 _ip = C.POINTER(C.c_int32)
@@ -42,7 +42,8 @@ class XsDesc(C.Structure):
     _fields_ = [("kind", C.c_int32), ("n_materials", C.c_int32), ("n_groups", C.c_int32),
                 ("sigma_t", _dp), ("sigma_s", _dp), ("nu_sigma_f", _dp), ("chi", _dp),
                 ("n_nuclides", C.c_int32), ("nuc_offset", C.POINTER(C.c_int64)), ("nuc_energy", _dp),
-                ("nuc_sigma", _dp), ("nuc_awr", _dp), ("density", _dp), ("energy_cutoff", C.c_double)]
+                ("nuc_sigma", _dp), ("nuc_awr", _dp), ("density", _dp), ("energy_cutoff", C.c_double),
+                ("inv_velocity", _dp)]
 
 
 class SourceDesc(C.Structure):
@@ -55,7 +56,7 @@ class SourceDesc(C.Structure):
 class TallyDesc(C.Structure):
     _fields_ = [("has_mesh", C.c_int32), ("mesh_n", C.c_int32 * 3), ("by_group", C.c_int32),
                 ("n_energy_bins", C.c_int32), ("mesh_lo", C.c_double * 3), ("mesh_hi", C.c_double * 3),
-                ("energy_edges", _dp)]
+                ("energy_edges", _dp), ("n_time_bins", C.c_int32), ("t_census", C.c_double)]
 
 
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
@@ -236,6 +237,8 @@ class Problem:
             x.n_groups = int(prob.n_groups)
             x.sigma_t, x.sigma_s = f64(prob.sigma_t), f64(prob.sigma_s)
             x.nu_sigma_f, x.chi = f64(prob.nu_sigma_f), f64(prob.chi)
+            if getattr(prob, "inv_velocity", None) is not None:
+                x.inv_velocity = f64(prob.inv_velocity)
         else:
             x.n_groups = 1
             x.n_nuclides = len(prob.nuc_energy)
@@ -278,6 +281,10 @@ class Problem:
             n_t = 1
             t.n_energy_bins = len(prob.energy_edges) - 1
             t.energy_edges = f64(prob.energy_edges)
+        if getattr(prob, "t_census", 0.0):
+            n_t = 1
+            t.t_census = float(prob.t_census)
+            t.n_time_bins = int(prob.n_time_bins)
 
         if use_torch_allocator:
             self._ctx, self._keep_ctx = _torch_ctx(device)

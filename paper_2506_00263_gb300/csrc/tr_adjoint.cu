@@ -47,6 +47,8 @@ struct AdjSink {
         len = dist;
         m = mat;
     }
+    // derivatives are offered for untimed problems only
+    __device__ __forceinline__ void time_segment(const DevProblem&, double, double, double) {}
 };
 
 struct AdjArgs {

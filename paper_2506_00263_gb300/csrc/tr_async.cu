@@ -34,7 +34,7 @@ constexpr unsigned NIL = 0xFFFFFFFFu;
 constexpr int N_GQ = 32;
 
 struct Stash {
-    double *x, *y, *z, *u, *v, *w, *iu, *iv, *iw, *ia, *E;
+    double *x, *y, *z, *u, *v, *w, *iu, *iv, *iw, *ia, *E, *t;
     double *xst, *xist, *xsa, *xnsf;   // lookup-event decomposition only (else NULL)
     int* g;
     unsigned *cell, *id, *n, *nsites, *pend, *prob;
@@ -46,7 +46,7 @@ constexpr int CNT_FREE = N_QUEUES, CNT_LOCK = N_QUEUES + 1;   // control words a
 
 __host__ __device__ __forceinline__ size_t stash_bytes(int S, bool xs = false)
 {
-    return (size_t)S * ((xs ? 15 : 11) * sizeof(double) + sizeof(int) + 6 * sizeof(unsigned)) +
+    return (size_t)S * ((xs ? 16 : 12) * sizeof(double) + sizeof(int) + 6 * sizeof(unsigned)) +
            (size_t)S * (N_QUEUES + 1) * sizeof(unsigned short) + 16 * sizeof(int);
 }
 
@@ -58,6 +58,7 @@ __device__ __forceinline__ Stash carve(unsigned char* base, int S, bool xs)
     s.u = d; d += S; s.v = d; d += S; s.w = d; d += S;
     s.iu = d; d += S; s.iv = d; d += S; s.iw = d; d += S; s.ia = d; d += S;
     s.E = d; d += S;
+    s.t = d; d += S;
     s.xst = s.xist = s.xsa = s.xnsf = nullptr;
     if (xs) {
         s.xst = d; d += S; s.xist = d; d += S; s.xsa = d; d += S; s.xnsf = d; d += S;
@@ -79,9 +80,11 @@ __device__ __forceinline__ Stash carve(unsigned char* base, int S, bool xs)
     return s;
 }
 
+// tm: the problem is timed (or the launch is batched): the particle's time travels too
 template <bool XS>
-__device__ __forceinline__ void slot_load(const Stash& s, int i, Particle& p)
+__device__ __forceinline__ void slot_load(const Stash& s, int i, Particle& p, bool tm)
 {
+    if (tm) p.t = s.t[i];
     if (XS) {
         p.xst = s.xst[i]; p.xist = s.xist[i]; p.xsa = s.xsa[i]; p.xnsf = s.xnsf[i];
     }
@@ -94,8 +97,9 @@ __device__ __forceinline__ void slot_load(const Stash& s, int i, Particle& p)
 }
 
 template <bool XS>
-__device__ __forceinline__ void slot_store(const Stash& s, int i, const Particle& p)
+__device__ __forceinline__ void slot_store(const Stash& s, int i, const Particle& p, bool tm)
 {
+    if (tm) s.t[i] = p.t;
     if (XS) {
         s.xst[i] = p.xst; s.xist[i] = p.xist; s.xsa[i] = p.xsa; s.xnsf[i] = p.xnsf;
     }
@@ -119,7 +123,7 @@ __device__ __forceinline__ void load_particle_l2(const SoA& s, unsigned long lon
     p.x = __ldcg(s.x + i); p.y = __ldcg(s.y + i); p.z = __ldcg(s.z + i);
     p.u = __ldcg(s.u + i); p.v = __ldcg(s.v + i); p.w = __ldcg(s.w + i);
     p.iu = __ldcg(s.iu + i); p.iv = __ldcg(s.iv + i); p.iw = __ldcg(s.iw + i); p.ia = __ldcg(s.ia + i);
-    p.E = __ldcg(s.E + i); p.g = __ldcg(s.g + i);
+    p.E = __ldcg(s.E + i); p.g = __ldcg(s.g + i); p.t = __ldcg(s.t + i);
     p.cell = __ldcg(s.cell + i); p.id = __ldcg(s.id + i); p.n = __ldcg(s.n + i);
     p.nsites = __ldcg(s.nsites + i); p.pend = __ldcg(s.pend + i); p.prob = __ldcg(s.prob + i);
 }
@@ -284,6 +288,7 @@ __global__ void __launch_bounds__(256, TR_ASYNC_MIN_BLOCKS) k_async(DevProblem P
     const Stash st = carve(smem, S, XS);
     const int lane = threadIdx.x & 31;
     constexpr int nq = dec_queues(DEC);
+    const bool tm = BATCHED || P.timed != 0;   // particle times travel through the stash
     AsyncCtl* ctl = A.ctl;
 
     if (threadIdx.x == 0) {
@@ -403,7 +408,7 @@ __global__ void __launch_bounds__(256, TR_ASYNC_MIN_BLOCKS) k_async(DevProblem P
                     bad = bad || p.id >= R.n_hist || cell_i(p.cell) >= PP.nx || cell_j(p.cell) >= PP.ny ||
                           cell_k(p.cell) >= PP.nz || sl < 0 || sl >= S || (!CE && (p.g < 0 || p.g >= PP.G));
                     if (!bad && cell_in(p.cell)) bad = info_pin(cell_info(PP, p.cell)) < 0;
-                    if (!bad) slot_store<XS>(st, sl, p);
+                    if (!bad) slot_store<XS>(st, sl, p, tm);
                 }
                 if (__any_sync(FULLM, bad)) {
                     if (lane == 0) fail(err, ERR_INVALID, 7);
@@ -461,7 +466,7 @@ __global__ void __launch_bounds__(256, TR_ASYNC_MIN_BLOCKS) k_async(DevProblem P
                 continue;
             }
             Particle p;
-            slot_load<XS>(st, slot, p);
+            slot_load<XS>(st, slot, p, tm);
             store_particle(A.links, (unsigned long long)link * 32 + lane, p, CE, XS);
             __threadfence();
             __syncwarp();
@@ -526,7 +531,7 @@ __global__ void __launch_bounds__(256, TR_ASYNC_MIN_BLOCKS) k_async(DevProblem P
             if (lane == 0 && made) atomicAdd(&ctl->live, (unsigned long long)made);
         } else {
             // mode 0 (warp-uniform): lanes beyond a partial link hold no slot and stay idle
-            if (slot >= 0) slot_load<XS>(st, slot, p);
+            if (slot >= 0) slot_load<XS>(st, slot, p, tm);
             __syncwarp();   // reconverge: the event below must run once for all lanes, not per lane group
             const unsigned em = __ballot_sync(FULLM, slot >= 0);   // the lanes that hold a particle
             if (slot >= 0) {
@@ -577,7 +582,7 @@ __global__ void __launch_bounds__(256, TR_ASYNC_MIN_BLOCKS) k_async(DevProblem P
             const unsigned died = __popc(__ballot_sync(FULLM, slot >= 0 && !live));
             if (lane == 0 && died) atomicAdd(&ctl->live, 0ull - (unsigned long long)died);
         }
-        if (live) slot_store<XS>(st, slot, p);
+        if (live) slot_store<XS>(st, slot, p, tm);
         // ---------------- deposit (under the stash lock) ----------------
         __syncwarp();
         if (!lock_stash(st, R, err)) break;

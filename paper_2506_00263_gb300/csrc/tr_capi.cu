@@ -43,8 +43,8 @@ struct tr_problem {
     std::vector<void*> owned;                 // problem data, freed at destroy
     std::map<std::string, Buf> ws;            // run workspaces, grown on demand
     // tallies: raw accumulators, results, eigenvalue statistics
-    double *raw_mesh = nullptr, *raw_energy = nullptr, *raw_scal = nullptr;
-    double *res_mesh = nullptr, *res_energy = nullptr, *res_scal = nullptr;
+    double *raw_mesh = nullptr, *raw_energy = nullptr, *raw_scal = nullptr, *raw_time = nullptr;
+    double *res_mesh = nullptr, *res_energy = nullptr, *res_scal = nullptr, *res_time = nullptr;
     double *sd_mesh = nullptr, *sd_energy = nullptr, *sd_scal = nullptr;
     double *sum_all = nullptr, *sq_all = nullptr;   // mesh | energy | scalars concatenated
     unsigned long long* counts = nullptr;     // ev_type[8], fin_type[8]
@@ -380,6 +380,28 @@ extern "C" tr_status tr_problem_create(const tr_geometry_desc* G, const tr_xs_de
         P.e_edges = upload(pr, Tl->energy_edges, Tl->n_energy_bins + 1, &ok);
         P.energy_size = M * Tl->n_energy_bins;
     }
+    // time: census and time bins
+    P.timed = 0;
+    P.n_tbins = 0;
+    P.t_cen = 0.0;
+    P.tb_w = 0.0;
+    P.inv_vel = nullptr;
+    P.v_c = 2.99792458e10 * std::sqrt(2.0 / 939.56542052e6);   // v = c sqrt(2 E / m_n c^2), E in eV
+    if (n_tallies == 1 && (Tl->t_census != 0.0 || Tl->n_time_bins != 0)) {
+        if (!(Tl->t_census > 0.0) || !std::isfinite(Tl->t_census) || Tl->n_time_bins < 0 || Tl->n_time_bins > 4096)
+            return fail_out(TR_ERR_INVALID, "t_census must be finite and > 0, n_time_bins in 0..4096");
+        if (X->kind == TR_XS_MG) {
+            if (!X->inv_velocity) return fail_out(TR_ERR_INVALID, "a timed multigroup problem needs inv_velocity");
+            for (int g = 0; g < X->n_groups; ++g)
+                if (!(X->inv_velocity[g] > 0.0) || !std::isfinite(X->inv_velocity[g]))
+                    return fail_out(TR_ERR_INVALID, "inv_velocity must be finite and > 0");
+            P.inv_vel = upload(pr, X->inv_velocity, X->n_groups, &ok);
+        }
+        P.timed = 1;
+        P.t_cen = Tl->t_census;
+        P.n_tbins = Tl->n_time_bins;
+        P.tb_w = P.n_tbins > 0 ? P.t_cen / (double)P.n_tbins : 0.0;
+    }
     const size_t ms = std::max(P.mesh_size, 1), es = std::max(P.energy_size, 1);
     pr->raw_mesh = (double*)own(pr, ms * 8);
     pr->raw_energy = (double*)own(pr, es * 8);
@@ -390,13 +412,15 @@ extern "C" tr_status tr_problem_create(const tr_geometry_desc* G, const tr_xs_de
     pr->sd_mesh = (double*)own(pr, ms * 8);
     pr->sd_energy = (double*)own(pr, es * 8);
     pr->sd_scal = (double*)own(pr, 4 * 8);
+    pr->raw_time = (double*)own(pr, std::max(P.n_tbins, 1) * 8);
+    pr->res_time = (double*)own(pr, std::max(P.n_tbins, 1) * 8);
     pr->sum_all = (double*)own(pr, (ms + es + 4) * 8);
     pr->sq_all = (double*)own(pr, (ms + es + 4) * 8);
     pr->counts = (unsigned long long*)own(pr, 16 * 8);
     pr->err = (ErrorWord*)own(pr, sizeof(ErrorWord));
     if (!ok || !pr->raw_mesh || !pr->raw_energy || !pr->raw_scal || !pr->res_mesh || !pr->res_energy ||
         !pr->res_scal || !pr->sd_mesh || !pr->sd_energy || !pr->sd_scal || !pr->sum_all || !pr->sq_all ||
-        !pr->counts || !pr->err)
+        !pr->counts || !pr->err || !pr->raw_time || !pr->res_time)
         return fail_out(TR_ERR_NOMEM, "device allocation or upload failed");
     if (cudaStreamSynchronize(pr->stream) != cudaSuccess) return fail_out(TR_ERR_CUDA, "stream sync failed");
     *out = pr;
@@ -424,7 +448,7 @@ extern "C" void tr_problem_destroy(tr_problem* pr)
 static bool carve_soa(tr_problem* pr, const char* name, unsigned long long cap, SoA& s)
 {
     const size_t n = (size_t)cap;
-    const size_t bytes = n * (15 * 8 + 7 * 4) + 22 * 256;
+    const size_t bytes = n * (16 * 8 + 7 * 4) + 23 * 256;
     unsigned char* b = (unsigned char*)workspace(pr, name, bytes);
     if (!b) return false;
     auto take = [&](size_t sz) {
@@ -436,6 +460,7 @@ static bool carve_soa(tr_problem* pr, const char* name, unsigned long long cap, 
     s.u = (double*)take(8); s.v = (double*)take(8); s.w = (double*)take(8);
     s.iu = (double*)take(8); s.iv = (double*)take(8); s.iw = (double*)take(8); s.ia = (double*)take(8);
     s.E = (double*)take(8);
+    s.t = (double*)take(8);
     s.xst = (double*)take(8); s.xist = (double*)take(8); s.xsa = (double*)take(8); s.xnsf = (double*)take(8);
     s.g = (int*)take(4);
     s.cell = (unsigned*)take(4); s.id = (unsigned*)take(4); s.n = (unsigned*)take(4);
@@ -512,6 +537,7 @@ static Tallies make_tallies(tr_problem* pr, bool log)
     T.mesh = pr->raw_mesh;
     T.energy = pr->raw_energy;
     T.scal = pr->raw_scal;
+    T.time = pr->raw_time;
     T.ev_type = pr->counts;
     T.fin_type = pr->counts + 8;
     T.log_n = log ? pr->log_n : nullptr;
@@ -526,6 +552,7 @@ static tr_status zero_raw(tr_problem* pr)
     TR_CUDA(cudaMemsetAsync(pr->raw_mesh, 0, std::max(P.mesh_size, 1) * 8, pr->stream));
     TR_CUDA(cudaMemsetAsync(pr->raw_energy, 0, std::max(P.energy_size, 1) * 8, pr->stream));
     TR_CUDA(cudaMemsetAsync(pr->raw_scal, 0, 4 * 8, pr->stream));
+    TR_CUDA(cudaMemsetAsync(pr->raw_time, 0, std::max(P.n_tbins, 1) * 8, pr->stream));
     return TR_OK;
 }
 
@@ -717,6 +744,7 @@ extern "C" tr_status tr_run_fixed_source(tr_problem* pr, const tr_run_opts* o, t
     TR_CUDA(launch_scale(pr->raw_mesh, P.mesh_size, inv, pr->res_mesh, st));
     TR_CUDA(launch_scale(pr->raw_energy, P.energy_size, inv, pr->res_energy, st));
     TR_CUDA(launch_scale(pr->raw_scal, 3, inv, pr->res_scal, st));
+    TR_CUDA(launch_scale(pr->raw_time, P.n_tbins, inv, pr->res_time, st));
     unsigned long long cnt[16];
     TR_CUDA(cudaMemcpyAsync(cnt, pr->counts, sizeof(cnt), cudaMemcpyDeviceToHost, st));
     TR_CUDA(cudaStreamSynchronize(st));
@@ -751,6 +779,7 @@ extern "C" tr_status tr_run_power_iteration(tr_problem* pr, const tr_eig_opts* e
 {
     if (!pr || !eo || !res) return set_err(TR_ERR_INVALID, "NULL argument");
     if (pr->dp.kind != TR_XS_MG) return set_err(TR_ERR_INVALID, "power iteration needs multigroup data");
+    if (pr->dp.timed) return set_err(TR_ERR_INVALID, "timed problems run fixed source only");
     tr_status s = validate_opts(&eo->run);
     if (s != TR_OK) return s;
     if (eo->n_per_batch < 1 || eo->n_active < 2) return set_err(TR_ERR_INVALID, "need n_per_batch >= 1 and n_active >= 2");
@@ -896,6 +925,7 @@ extern "C" tr_status tr_sensitivities(tr_problem* pr, const tr_run_opts* o, cons
 {
     if (!pr || !o || !d_sigt || !d_sigs || !d_nusigf) return set_err(TR_ERR_INVALID, "NULL argument");
     if (pr->dp.kind != TR_XS_MG) return set_err(TR_ERR_INVALID, "sensitivities need multigroup data");
+    if (pr->dp.timed) return set_err(TR_ERR_INVALID, "sensitivities are offered for untimed problems");
     tr_status s = validate_opts(o);
     if (s != TR_OK) return s;
     const tr_run_opts& L = pr->last_fixed;
@@ -979,6 +1009,7 @@ static tr_status enqueue_batched(tr_problem* lead, tr_problem* const* probs, int
         TR_CUDA(cudaMemsetAsync(p->raw_mesh, 0, std::max(p->dp.mesh_size, 1) * 8, st));
         TR_CUDA(cudaMemsetAsync(p->raw_energy, 0, std::max(p->dp.energy_size, 1) * 8, st));
         TR_CUDA(cudaMemsetAsync(p->raw_scal, 0, 4 * 8, st));
+        TR_CUDA(cudaMemsetAsync(p->raw_time, 0, std::max(p->dp.n_tbins, 1) * 8, st));
         TR_CUDA(cudaMemsetAsync(p->counts, 0, 16 * 8, st));
     }
     TR_CUDA(cudaMemsetAsync(lead->err, 0, sizeof(ErrorWord), st));
@@ -1070,6 +1101,7 @@ extern "C" tr_status tr_run_batched(tr_problem* const* probs, int32_t n, const u
         if (probs[i]->dp.energy_size)
             hj.push_back({probs[i]->raw_energy, probs[i]->res_energy, probs[i]->dp.energy_size, inv});
         hj.push_back({probs[i]->raw_scal, probs[i]->res_scal, 3, inv});
+        if (probs[i]->dp.n_tbins) hj.push_back({probs[i]->raw_time, probs[i]->res_time, probs[i]->dp.n_tbins, inv});
     }
     TR_CUDA(cudaMemcpyAsync(d_probs, hp.data(), sizeof(DevProblem) * n, cudaMemcpyHostToDevice, st));
     TR_CUDA(cudaMemcpyAsync(d_tal, ht.data(), sizeof(Tallies) * n, cudaMemcpyHostToDevice, st));
@@ -1143,7 +1175,8 @@ extern "C" tr_status tr_run_batched(tr_problem* const* probs, int32_t n, const u
         gkey.push_back((unsigned long long)(uintptr_t)q);
     for (int32_t i = 0; i < n; ++i)
         for (const void* q : {(const void*)probs[i]->raw_mesh, (const void*)probs[i]->raw_energy,
-                              (const void*)probs[i]->raw_scal, (const void*)probs[i]->counts})
+                              (const void*)probs[i]->raw_scal, (const void*)probs[i]->raw_time,
+                              (const void*)probs[i]->counts})
             gkey.push_back((unsigned long long)(uintptr_t)q);
     gkey.push_back(hj.size());
     if (!lead->batch_graph || lead->batch_key != gkey) {
@@ -1243,6 +1276,7 @@ extern "C" size_t tr_tally_size(const tr_problem* pr, int32_t id)
     if (id == TR_TALLY_MESH) return (size_t)pr->dp.mesh_size;
     if (id == TR_TALLY_ENERGY) return (size_t)pr->dp.energy_size;
     if (id == TR_TALLY_SCALARS) return 3;
+    if (id == TR_TALLY_TIME) return (size_t)pr->dp.n_tbins;
     return 0;
 }
 
@@ -1252,10 +1286,11 @@ static tr_status copy_tally(const tr_problem* pr, int32_t id, double* out, size_
     if (!pr->have_run) return set_err(TR_ERR_STATE, "no completed run");
     if (sd && !pr->have_std) return set_err(TR_ERR_STATE, "standard deviations come from power iteration only");
     const size_t want = tr_tally_size(pr, id);
-    if (id < 0 || id > 2 || n != want) return set_err(TR_ERR_INVALID, "tally id or size mismatch");
+    if (id < 0 || id > 3 || n != want) return set_err(TR_ERR_INVALID, "tally id or size mismatch");
     if (n == 0) return TR_OK;
     const double* src = id == TR_TALLY_MESH ? (sd ? pr->sd_mesh : pr->res_mesh)
                       : id == TR_TALLY_ENERGY ? (sd ? pr->sd_energy : pr->res_energy)
+                      : id == TR_TALLY_TIME ? pr->res_time
                                               : (sd ? pr->sd_scal : pr->res_scal);
     TR_CUDA(cudaMemcpyAsync(out, src, n * 8, on_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, pr->stream));
     TR_CUDA(cudaStreamSynchronize(pr->stream));

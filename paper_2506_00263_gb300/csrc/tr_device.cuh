@@ -99,6 +99,12 @@ struct DevProblem {
     const int *cell2vox;               // [nx | ny | nz]: mesh voxel holding geometry cell i on that axis, or -1
     const double *e_edges;
     int mesh_size, energy_size;
+    // time: histories start at t = 0 and end at the census time t_cen (timed
+    // problems only); speeds from inv_vel[g] (MG, s/cm) or v_c sqrt(E) (CE);
+    // n_tbins uniform flux bins of width tb_w over [0, t_cen)
+    int timed, n_tbins;
+    double t_cen, tb_w, v_c;
+    const double *inv_vel;
 };
 
 // Per-run parameters.
@@ -134,7 +140,7 @@ __device__ __forceinline__ uint64_t now_ns()
 // batched launch; with the lookup event, the cached cross sections (Sigma_t,
 // 1/Sigma_t, Sigma_a, nu Sigma_f).
 struct SoA {
-    double *x, *y, *z, *u, *v, *w, *iu, *iv, *iw, *ia, *E;
+    double *x, *y, *z, *u, *v, *w, *iu, *iv, *iw, *ia, *E, *t;
     double *xst, *xist, *xsa, *xnsf;
     int *g;
     unsigned *cell, *id, *n, *nsites, *pend, *prob;
@@ -144,6 +150,7 @@ struct Particle {
     double x, y, z, u, v, w;
     double iu, iv, iw, ia;
     double E;
+    double t;                          // time since the source (timed problems)
     double xst, xist, xsa, xnsf;       // lookup-event decomposition: cross sections of (material, E or g)
     int g;
     unsigned cell;                     // i | j << 10 | k << 20 | inside << 30
@@ -156,6 +163,7 @@ struct Tallies {
     double *mesh;                      // mesh_size
     double *energy;                    // energy_size
     double *scal;                      // 3: flux, absorption, production
+    double *time;                      // n_tbins (timed problems)
     unsigned long long *ev_type;       // 8 event counts
     unsigned long long *fin_type;      // 8 final-type counts
     uint32_t *log_n;

@@ -12,7 +12,8 @@
 namespace tr {
 
 // pending-outcome flags left by the step event for the decomposed scheme
-constexpr unsigned PEND_X = 1u, PEND_Y = 2u, PEND_Z = 4u, PEND_CYL = 8u, PEND_ESCAPE = 16u, PEND_COLLIDE = 32u;
+constexpr unsigned PEND_X = 1u, PEND_Y = 2u, PEND_Z = 4u, PEND_CYL = 8u, PEND_ESCAPE = 16u, PEND_COLLIDE = 32u,
+                   PEND_CENSUS = 64u;
 
 // Per-thread accumulators for the always-on scalar tallies and event counts.
 struct Acc {
@@ -172,6 +173,7 @@ __device__ __forceinline__ bool source_particle(const DevProblem& P, const RunPa
     p.prob = 0u;
     p.g = 0;
     p.E = 0.0;
+    p.t = 0.0;
     if (site != nullptr || P.src_kind != 0 || P.src_iso) {
         iso_dir(S, 0u, xi_mu, p);
     } else {
@@ -236,6 +238,20 @@ struct FwdSink {
             mesh_tally(P, op, p, x0, y0, z0, dist, goff);
         }
         if (CE && P.n_ebins > 0 && gt0(dist)) energy_tally(P, T.energy, m, p.E, dist);
+    }
+    // time bins: the track length spent in each bin of [t0, t1]
+    __device__ __forceinline__ void time_segment(const DevProblem& P, double t0, double t1, double inv_v)
+    {
+        if (P.n_tbins <= 0 || !(t1 > t0)) return;
+        int b = (int)floor(t0 / P.tb_w);
+        if (b < 0) b = 0;
+        for (; b < P.n_tbins; ++b) {
+            double lo = (double)b * P.tb_w, hi = (double)(b + 1) * P.tb_w;
+            if (lo >= t1) break;
+            lo = fmax(lo, t0);
+            hi = fmin(hi, t1);
+            if (hi > lo) atomicAdd(T.time + b, (hi - lo) / inv_v);
+        }
     }
 };
 
@@ -318,18 +334,36 @@ __device__ __forceinline__ void step_event(const DevProblem& P, const RunParams&
         }
     }
     const bool collided = lt_nn(dcol, ds);
-    const bool escape = !collided && dbits(ds) == dbits(INF);   // no surface ahead: the particle escapes
+    double dist = collided ? dcol : ds;
+    // timed problems: the census ends the history when it comes strictly
+    // before the collision or surface
+    bool census = false;
+    double inv_v = 0.0;
+    if (P.timed) {
+        inv_v = CE ? 1.0 / (P.v_c * sqrt(p.E)) : __ldg(P.inv_vel + p.g);
+        const double left = P.t_cen - p.t;
+        const double dcen = left > 0.0 ? left / inv_v : 0.0;
+        if (dcen < dist) {
+            census = true;
+            dist = dcen;
+        }
+    }
+    const bool escape = !census && !collided && dbits(ds) == dbits(INF);   // no surface ahead: escape
     TR_LANES(4);
     if (!escape) {
-        const double dist = collided ? dcol : ds;
         const double x0 = p.x, y0 = p.y, z0 = p.z;
         p.x = __fma_rn(dist, p.u, p.x);
         p.y = __fma_rn(dist, p.v, p.y);
         p.z = __fma_rn(dist, p.w, p.z);
         sink.template segment<CE>(P, p, x0, y0, z0, dist, m, X);
+        if (P.timed) {
+            const double t0 = p.t;
+            p.t = census ? P.t_cen : __fma_rn(dist, inv_v, p.t);
+            sink.time_segment(P, t0, p.t, inv_v);
+        }
     }
     TR_LANES(5);
-    p.pend = escape ? PEND_ESCAPE : (collided ? PEND_COLLIDE : flags);
+    p.pend = escape ? PEND_ESCAPE : (census ? PEND_CENSUS : (collided ? PEND_COLLIDE : flags));
 }
 
 // ---------------------------------------------------------------------------
@@ -443,6 +477,7 @@ __device__ __forceinline__ int surface_event(const DevProblem& P, Particle& p)
 {
     TR_LANES(21);
     const unsigned f = p.pend;
+    if (f & PEND_CENSUS) return EV_CUTOFF;
     if (f & PEND_ESCAPE) return EV_LEAK;
     if (f & PEND_CYL) {
         p.cell ^= 1u << 30;
@@ -614,6 +649,7 @@ __device__ __forceinline__ int split_surface_next(const DevProblem& P, const Run
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ void load_particle(const SoA& s, unsigned long long i, Particle& p, bool ce, bool xs = false)
 {
+    p.t = s.t[i];
     if (xs) {
         p.xst = s.xst[i]; p.xist = s.xist[i]; p.xsa = s.xsa[i]; p.xnsf = s.xnsf[i];
     }
@@ -628,6 +664,7 @@ __device__ __forceinline__ void load_particle(const SoA& s, unsigned long long i
 __device__ __forceinline__ void store_particle(const SoA& s, unsigned long long i, const Particle& p, bool ce,
                                                bool xs = false)
 {
+    s.t[i] = p.t;
     if (xs) {
         s.xst[i] = p.xst; s.xist[i] = p.xist; s.xsa[i] = p.xsa; s.xnsf[i] = p.xnsf;
     }

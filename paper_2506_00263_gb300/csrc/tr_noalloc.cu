@@ -29,8 +29,8 @@ namespace {
 
 constexpr unsigned long long NOALLOC_LINKS = TR_NOALLOC_MAX_QUEUE_CAPACITY / 32;
 constexpr size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
-// per particle slot of the link arena: 11 doubles + 7 32-bit words (as carve_links below)
-constexpr size_t LINK_SOA_BYTES = 18 * 256 + NOALLOC_LINKS * 32 * (11 * 8 + 7 * 4);
+// per particle slot of the link arena: 12 doubles + 7 32-bit words (as carve_links below)
+constexpr size_t LINK_SOA_BYTES = 19 * 256 + NOALLOC_LINKS * 32 * (12 * 8 + 7 * 4);
 constexpr size_t OFF_ERR = 0;
 constexpr size_t OFF_COUNTS = align256(OFF_ERR + sizeof(ErrorWord));
 constexpr size_t OFF_CTL = align256(OFF_COUNTS + 16 * sizeof(unsigned long long));
@@ -89,6 +89,7 @@ void carve_links(unsigned char* b, unsigned long long n, SoA& s)
     s.u = (double*)take(8); s.v = (double*)take(8); s.w = (double*)take(8);
     s.iu = (double*)take(8); s.iv = (double*)take(8); s.iw = (double*)take(8); s.ia = (double*)take(8);
     s.E = (double*)take(8);
+    s.t = (double*)take(8);
     s.xst = s.xist = s.xsa = s.xnsf = nullptr;   // the lookup-event decomposition is not offered here
     s.g = (int*)take(4);
     s.cell = (unsigned*)take(4); s.id = (unsigned*)take(4); s.n = (unsigned*)take(4);
@@ -129,6 +130,7 @@ extern "C" tr_status tr_run_fixed_source_noalloc(tr_problem* problem, const tr_r
     const DevProblem& P = *Pp;
     if ((P.mesh_size > 0 && !mesh_out) || (P.energy_size > 0 && !energy_out) || !scalars_out)
         return fail(TR_ERR_INVALID, "an output array for a present tally is NULL");
+    if (P.timed) return fail(TR_ERR_INVALID, "timed problems have no output here: use tr_run_fixed_source");
     int S = o->stash_slots > 0 ? o->stash_slots : 512;
     S = (S + 31) & ~31;
     if (S < 32 * 9 || S > 16384) return fail(TR_ERR_INVALID, "stash_slots must be in 288..16384");

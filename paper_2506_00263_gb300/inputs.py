@@ -90,6 +90,12 @@ class Problem:
     mesh_n: Optional[tuple] = None
     mesh_by_group: bool = False
     energy_edges: Optional[np.ndarray] = None        # CE energy-bin tally, per material
+    # time: histories start at t = 0 and end at the census time t_census (0 =
+    # untimed); multigroup speeds from inv_velocity (G,) s/cm; n_time_bins
+    # uniform flux bins over [0, t_census)
+    inv_velocity: Optional[np.ndarray] = None
+    n_time_bins: int = 0
+    t_census: float = 0.0
 
     @property
     def shape(self):
