@@ -234,6 +234,10 @@ typedef struct {
     double k0;                          /* initial eigenvalue guess (default 1) */
     double bank_capacity_factor;        /* fission bank = factor * n_per_batch (default 4) */
     tr_run_opts run;                    /* seed, scheme, decomposition, tuning */
+    uint32_t stop_after;                /* end after this many batches in all, keeping the state for
+                                           tr_eig_checkpoint (0 or >= n_inactive + n_active: run to the end) */
+    const void *resume_from;            /* host buffer from tr_eig_checkpoint (NULL: start afresh) */
+    size_t resume_bytes;
 } tr_eig_opts;
 
 typedef struct {
@@ -246,6 +250,7 @@ typedef struct {
     double seconds;                     /* device time of all batches */
     double transport_seconds;           /* device time of the transport-loop kernels alone */
     uint64_t transport_launches;        /* launches of the transport-loop kernels */
+    uint32_t batches_done;              /* batches completed, counting those before a resume */
 } tr_eig_result;
 
 /* k-eigenvalue power iteration (Sec. 4: inactive then active cycles with
@@ -256,6 +261,21 @@ typedef struct {
  * the standard deviation of that mean.  Multigroup only (TR_ERR_INVALID
  * otherwise).  The event log holds the last batch. */
 tr_status tr_run_power_iteration(tr_problem *problem, const tr_eig_opts *opts, tr_eig_result *out);
+
+/* Checkpoint of a power iteration that ended early (opts.stop_after): the
+ * state before the next batch, namely the opts it ran with, the batch index,
+ * the eigenvalue, the resampled source bank, the running eigenvalue sums, the
+ * active-batch tally sums, the event counters and the per-batch eigenvalue,
+ * track-length eigenvalue and source size so far.  Passing it back as
+ * opts.resume_from (same problem description and opts apart from stop_after
+ * and the resume fields, else TR_ERR_STATE) continues with the same histories
+ * and eigenvalues as an uninterrupted run; the tallies agree to rounding
+ * (summation order).  buf == NULL: *bytes receives the size.  Otherwise the
+ * state is written to buf (cap bytes, TR_ERR_INVALID if too small).  The
+ * buffer is plain host memory and may be stored in a file; it is not portable
+ * across library versions.  TR_ERR_STATE when the last power iteration ran to
+ * the end (or none ran). */
+tr_status tr_eig_checkpoint(const tr_problem *problem, void *buf, size_t cap, size_t *bytes);
 
 /* Derivatives of L = sum_b g_b T_b with respect to the multigroup cross
  * sections, where T are the fixed-source tallies of the preceding

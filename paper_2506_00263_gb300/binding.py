@@ -87,14 +87,15 @@ class RunStats(C.Structure):
 
 class EigOptsC(C.Structure):
     _fields_ = [("n_per_batch", C.c_uint64), ("n_inactive", C.c_uint32), ("n_active", C.c_uint32),
-                ("k0", C.c_double), ("bank_capacity_factor", C.c_double), ("run", RunOptsC)]
+                ("k0", C.c_double), ("bank_capacity_factor", C.c_double), ("run", RunOptsC),
+                ("stop_after", C.c_uint32), ("resume_from", C.c_void_p), ("resume_bytes", C.c_size_t)]
 
 
 class EigResultC(C.Structure):
     _fields_ = [("k_mean", C.c_double), ("k_std", C.c_double), ("k_batch", _dp), ("ktl_batch", _dp),
                 ("n_source", C.POINTER(C.c_uint64)), ("histories", C.c_uint64), ("events", C.c_uint64),
                 ("final_by_type", C.c_uint64 * 8), ("seconds", C.c_double), ("transport_seconds", C.c_double),
-                ("transport_launches", C.c_uint64)]
+                ("transport_launches", C.c_uint64), ("batches_done", C.c_uint32)]
 
 
 _lib = None
@@ -133,6 +134,8 @@ def lib():
     L.tr_run_batched.argtypes = [C.POINTER(C.c_void_p), C.c_int32, C.POINTER(C.c_uint64), C.POINTER(RunOptsC),
                                  C.POINTER(RunStats)]
     L.tr_run_batched.restype = C.c_int
+    L.tr_eig_checkpoint.argtypes = [C.c_void_p, C.c_void_p, C.c_size_t, C.POINTER(C.c_size_t)]
+    L.tr_eig_checkpoint.restype = C.c_int
     L.tr_version.restype = C.c_char_p
     _lib = L
     return L
@@ -347,11 +350,18 @@ class Problem:
                                       ptr(d_sigs_ptr), ptr(d_nusigf_ptr)))
 
     def power_iteration(self, n_per_batch, n_inactive, n_active, opts: RunOpts, k0=1.0,
-                        bank_capacity_factor=0.0) -> dict:
+                        bank_capacity_factor=0.0, stop_after: int = 0, resume: bytes = None) -> dict:
+        """tr_run_power_iteration; stop_after > 0 ends early keeping the state
+        (read it with eig_checkpoint), resume continues from such a state."""
         eo = EigOptsC()
         eo.n_per_batch, eo.n_inactive, eo.n_active = n_per_batch, n_inactive, n_active
         eo.k0, eo.bank_capacity_factor = k0, bank_capacity_factor
         eo.run = opts.to_c()
+        eo.stop_after = stop_after
+        if resume is not None:
+            rbuf = C.create_string_buffer(bytes(resume), len(resume))
+            eo.resume_from = C.cast(rbuf, C.c_void_p)
+            eo.resume_bytes = len(resume)
         nb = n_inactive + n_active
         kb, ktl, ns = np.zeros(nb), np.zeros(nb), np.zeros(nb, np.uint64)
         r = EigResultC()
@@ -361,7 +371,16 @@ class Problem:
         return {"k_mean": r.k_mean, "k_std": r.k_std, "k_batch": kb, "ktl_batch": ktl, "n_source": ns,
                 "histories": r.histories, "events": r.events,
                 "final_by_type": np.array(r.final_by_type[:], np.uint64), "seconds": r.seconds,
-                "transport_seconds": r.transport_seconds, "transport_launches": r.transport_launches}
+                "transport_seconds": r.transport_seconds, "transport_launches": r.transport_launches,
+                "batches_done": r.batches_done}
+
+    def eig_checkpoint(self) -> bytes:
+        """tr_eig_checkpoint: the state of the last power iteration stopped early."""
+        n = C.c_size_t(0)
+        _check(lib().tr_eig_checkpoint(self._h, None, 0, C.byref(n)))
+        buf = C.create_string_buffer(n.value)
+        _check(lib().tr_eig_checkpoint(self._h, buf, n.value, C.byref(n)))
+        return buf.raw[:n.value]
 
     def tally(self, tally_id: int, stddev: bool = False) -> np.ndarray:
         n = lib().tr_tally_size(self._h, tally_id)

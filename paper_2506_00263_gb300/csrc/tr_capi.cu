@@ -58,6 +58,7 @@ struct tr_problem {
     bool have_fixed = false;                  // last completed run was fixed source (for sensitivities)
     tr_run_opts last_fixed{};
     // batched launches led by this problem: the captured CUDA graph and its key
+    std::vector<unsigned char> ckpt;          // state of a power iteration stopped early (tr_eig_checkpoint)
     cudaGraphExec_t batch_graph = nullptr;
     std::vector<unsigned long long> batch_key;
     unsigned long long batch_graph_launches = 0;
@@ -775,6 +776,37 @@ extern "C" tr_status tr_run_fixed_source(tr_problem* pr, const tr_run_opts* o, t
 // ---------------------------------------------------------------------------
 // power iteration
 // ---------------------------------------------------------------------------
+// Serialised power-iteration state (tr_eig_checkpoint): this header, then
+// k_batch, ktl_batch (doubles) and n_source (u64) for the batches done, the
+// active-batch tally sums and sums of squares (nall + 1 doubles each), and the
+// source bank of the next batch (x, y, z doubles, g int32, cell uint32).
+struct EigCkpt {
+    char magic[8];
+    uint64_t n_per_batch, seed, N;
+    uint32_t n_inactive, n_active, problem_tag, b_next;
+    int32_t scheme, decomposition, mesh_size, energy_size, n_mat, G, nall, pad;
+    double k0, bank_factor, k, ksum, ksq, kernel_ms;
+    uint64_t tlaunch;
+    unsigned long long counts[16];
+};
+static const char EIG_MAGIC[8] = {'T', 'R', 'E', 'I', 'G', 'C', 'K', '1'};
+
+static size_t eig_ckpt_bytes(uint32_t b_next, int nall, unsigned long long N)
+{
+    return sizeof(EigCkpt) + (size_t)b_next * 24 + (size_t)(nall + 1) * 16 + (size_t)N * 32;
+}
+
+extern "C" tr_status tr_eig_checkpoint(const tr_problem* pr, void* buf, size_t cap, size_t* bytes)
+{
+    if (!pr || !bytes) return set_err(TR_ERR_INVALID, "NULL argument");
+    if (pr->ckpt.empty()) return set_err(TR_ERR_STATE, "no power iteration stopped early");
+    *bytes = pr->ckpt.size();
+    if (!buf) return TR_OK;
+    if (cap < pr->ckpt.size()) return set_err(TR_ERR_INVALID, "checkpoint buffer too small");
+    std::memcpy(buf, pr->ckpt.data(), pr->ckpt.size());
+    return TR_OK;
+}
+
 extern "C" tr_status tr_run_power_iteration(tr_problem* pr, const tr_eig_opts* eo, tr_eig_result* res)
 {
     if (!pr || !eo || !res) return set_err(TR_ERR_INVALID, "NULL argument");
@@ -817,15 +849,71 @@ extern "C" tr_status tr_run_power_iteration(tr_problem* pr, const tr_eig_opts* e
     double k = eo->k0 > 0.0 ? eo->k0 : 1.0;
     unsigned long long N = eo->n_per_batch;
     double ksum = 0.0, ksq = 0.0;
-    cudaEvent_t e0, e1;
-    TR_CUDA(cudaEventCreate(&e0));
-    TR_CUDA(cudaEventCreate(&e1));
-    TR_CUDA(cudaEventRecord(e0, st));
     std::vector<double> scal(3);
     bool have_src = false;
     double kernel_ms = 0.0;
     unsigned long long tlaunch = 0;
-    for (uint32_t b = 0; b < nb; ++b) {
+    std::vector<double> kh, ktlh;         // per-batch eigenvalue history (kept for checkpoints)
+    std::vector<uint64_t> nsh;
+    uint32_t b0 = 0;
+    pr->ckpt.clear();
+    if (eo->resume_from) {
+        // continue a run stopped early: check the signature, restore the state
+        const unsigned char* q = (const unsigned char*)eo->resume_from;
+        EigCkpt h;
+        if (eo->resume_bytes < sizeof(h)) return set_err(TR_ERR_INVALID, "checkpoint too short");
+        std::memcpy(&h, q, sizeof(h));
+        if (std::memcmp(h.magic, EIG_MAGIC, 8) != 0) return set_err(TR_ERR_INVALID, "not a checkpoint");
+        const double k0 = eo->k0 > 0.0 ? eo->k0 : 1.0;
+        if (h.n_per_batch != eo->n_per_batch || h.n_inactive != eo->n_inactive || h.n_active != eo->n_active ||
+            h.seed != o->seed || h.problem_tag != o->problem_tag || h.scheme != o->scheme ||
+            h.decomposition != o->decomposition || h.k0 != k0 || h.bank_factor != factor ||
+            h.mesh_size != P.mesh_size || h.energy_size != P.energy_size || h.n_mat != P.n_mat || h.G != P.G ||
+            h.nall != nall || h.b_next < 1 || h.b_next >= nb)
+            return set_err(TR_ERR_STATE, "checkpoint does not match this problem and these options");
+        if (h.N > cap || eo->resume_bytes != eig_ckpt_bytes(h.b_next, nall, h.N))
+            return set_err(TR_ERR_INVALID, "checkpoint size mismatch");
+        q += sizeof(h);
+        kh.assign((const double*)q, (const double*)q + h.b_next);
+        q += 8 * (size_t)h.b_next;
+        ktlh.assign((const double*)q, (const double*)q + h.b_next);
+        q += 8 * (size_t)h.b_next;
+        nsh.resize(h.b_next);
+        std::memcpy(nsh.data(), q, 8 * (size_t)h.b_next);
+        q += 8 * (size_t)h.b_next;
+        TR_CUDA(cudaMemcpyAsync(pr->sum_all, q, (size_t)(nall + 1) * 8, cudaMemcpyHostToDevice, st));
+        q += (size_t)(nall + 1) * 8;
+        TR_CUDA(cudaMemcpyAsync(pr->sq_all, q, (size_t)(nall + 1) * 8, cudaMemcpyHostToDevice, st));
+        q += (size_t)(nall + 1) * 8;
+        const size_t n8 = (size_t)h.N * 8, n4 = (size_t)h.N * 4;
+        TR_CUDA(cudaMemcpyAsync(source.x, q, n8, cudaMemcpyHostToDevice, st));
+        TR_CUDA(cudaMemcpyAsync(source.y, q + n8, n8, cudaMemcpyHostToDevice, st));
+        TR_CUDA(cudaMemcpyAsync(source.z, q + 2 * n8, n8, cudaMemcpyHostToDevice, st));
+        TR_CUDA(cudaMemcpyAsync(source.g, q + 3 * n8, n4, cudaMemcpyHostToDevice, st));
+        TR_CUDA(cudaMemcpyAsync(source.cell, q + 3 * n8 + n4, n4, cudaMemcpyHostToDevice, st));
+        TR_CUDA(cudaMemcpyAsync(pr->counts, h.counts, sizeof(h.counts), cudaMemcpyHostToDevice, st));
+        TR_CUDA(cudaStreamSynchronize(st));   // the host buffer may go away on return
+        b0 = h.b_next;
+        k = h.k;
+        N = h.N;
+        ksum = h.ksum;
+        ksq = h.ksq;
+        kernel_ms = h.kernel_ms;
+        tlaunch = h.tlaunch;
+        have_src = true;
+    }
+    const uint32_t stop = (eo->stop_after > 0 && eo->stop_after < nb) ? eo->stop_after : nb;
+    if (stop <= b0) return set_err(TR_ERR_INVALID, "stop_after must lie beyond the resumed batch");
+    for (uint32_t b = 0; b < b0; ++b) {
+        if (res->k_batch) res->k_batch[b] = kh[b];
+        if (res->ktl_batch) res->ktl_batch[b] = ktlh[b];
+        if (res->n_source) res->n_source[b] = nsh[b];
+    }
+    cudaEvent_t e0, e1;
+    TR_CUDA(cudaEventCreate(&e0));
+    TR_CUDA(cudaEventCreate(&e1));
+    TR_CUDA(cudaEventRecord(e0, st));
+    for (uint32_t b = b0; b < nb; ++b) {
         s = zero_raw(pr);
         if (s != TR_OK) return s;
         TR_CUDA(cudaMemsetAsync(bank.count, 0, 8, st));
@@ -848,6 +936,9 @@ extern "C" tr_status tr_run_power_iteration(tr_problem* pr, const tr_eig_opts* e
         if (res->k_batch) res->k_batch[b] = kb;
         if (res->ktl_batch) res->ktl_batch[b] = scal[2] / (double)N;
         if (res->n_source) res->n_source[b] = N;
+        kh.push_back(kb);
+        ktlh.push_back(scal[2] / (double)N);
+        nsh.push_back(N);
         if (b >= eo->n_inactive) {
             const double inv = 1.0 / (double)N;
             TR_CUDA(launch_eig_accumulate(pr->raw_mesh, ms, inv, pr->sum_all, pr->sq_all, st));
@@ -884,6 +975,74 @@ extern "C" tr_status tr_run_power_iteration(tr_problem* pr, const tr_eig_opts* e
         if (s != TR_OK) return s;
         N = nn;
         have_src = true;
+        if (b + 1 == stop) {
+            // stop early: keep the state before batch b + 1 for tr_eig_checkpoint
+            EigCkpt h{};
+            std::memcpy(h.magic, EIG_MAGIC, 8);
+            h.n_per_batch = eo->n_per_batch;
+            h.seed = o->seed;
+            h.N = N;
+            h.n_inactive = eo->n_inactive;
+            h.n_active = eo->n_active;
+            h.problem_tag = o->problem_tag;
+            h.b_next = b + 1;
+            h.scheme = o->scheme;
+            h.decomposition = o->decomposition;
+            h.mesh_size = P.mesh_size;
+            h.energy_size = P.energy_size;
+            h.n_mat = P.n_mat;
+            h.G = P.G;
+            h.nall = nall;
+            h.k0 = eo->k0 > 0.0 ? eo->k0 : 1.0;
+            h.bank_factor = factor;
+            h.k = k;
+            h.ksum = ksum;
+            h.ksq = ksq;
+            h.kernel_ms = kernel_ms;
+            h.tlaunch = tlaunch;
+            TR_CUDA(cudaMemcpyAsync(h.counts, pr->counts, sizeof(h.counts), cudaMemcpyDeviceToHost, st));
+            std::vector<unsigned char> buf(eig_ckpt_bytes(h.b_next, nall, N));
+            unsigned char* q = buf.data() + sizeof(h);
+            std::memcpy(q, kh.data(), 8 * kh.size());
+            q += 8 * kh.size();
+            std::memcpy(q, ktlh.data(), 8 * ktlh.size());
+            q += 8 * ktlh.size();
+            std::memcpy(q, nsh.data(), 8 * nsh.size());
+            q += 8 * nsh.size();
+            TR_CUDA(cudaMemcpyAsync(q, pr->sum_all, (size_t)(nall + 1) * 8, cudaMemcpyDeviceToHost, st));
+            q += (size_t)(nall + 1) * 8;
+            TR_CUDA(cudaMemcpyAsync(q, pr->sq_all, (size_t)(nall + 1) * 8, cudaMemcpyDeviceToHost, st));
+            q += (size_t)(nall + 1) * 8;
+            const size_t n8 = (size_t)N * 8, n4 = (size_t)N * 4;
+            TR_CUDA(cudaMemcpyAsync(q, source.x, n8, cudaMemcpyDeviceToHost, st));
+            TR_CUDA(cudaMemcpyAsync(q + n8, source.y, n8, cudaMemcpyDeviceToHost, st));
+            TR_CUDA(cudaMemcpyAsync(q + 2 * n8, source.z, n8, cudaMemcpyDeviceToHost, st));
+            TR_CUDA(cudaMemcpyAsync(q + 3 * n8, source.g, n4, cudaMemcpyDeviceToHost, st));
+            TR_CUDA(cudaMemcpyAsync(q + 3 * n8 + n4, source.cell, n4, cudaMemcpyDeviceToHost, st));
+            TR_CUDA(cudaStreamSynchronize(st));
+            std::memcpy(buf.data(), &h, sizeof(h));
+            TR_CUDA(cudaEventRecord(e1, st));
+            TR_CUDA(cudaEventSynchronize(e1));
+            float msec = 0.f;
+            cudaEventElapsedTime(&msec, e0, e1);
+            cudaEventDestroy(e0);
+            cudaEventDestroy(e1);
+            pr->ckpt.swap(buf);
+            std::memset(res->final_by_type, 0, sizeof(res->final_by_type));
+            res->k_mean = res->k_std = 0.0;
+            res->histories = h.counts[EV_SOURCE];
+            res->events = 0;
+            for (int i = 1; i < 8; ++i) res->events += h.counts[i];
+            for (int i = 0; i < 8; ++i) res->final_by_type[i] = h.counts[8 + i];
+            res->seconds = msec * 1e-3;
+            res->transport_seconds = kernel_ms * 1e-3;
+            res->transport_launches = tlaunch;
+            res->batches_done = b + 1;
+            pr->have_run = false;   // tallies are final only at the end of the run
+            pr->have_std = false;
+            pr->have_fixed = false;
+            return TR_OK;
+        }
     }
     TR_CUDA(cudaEventRecord(e1, st));
     TR_CUDA(cudaEventSynchronize(e1));
@@ -911,6 +1070,7 @@ extern "C" tr_status tr_run_power_iteration(tr_problem* pr, const tr_eig_opts* e
     res->seconds = msec * 1e-3;
     res->transport_seconds = kernel_ms * 1e-3;
     res->transport_launches = tlaunch;
+    res->batches_done = nb;
     pr->have_run = true;
     pr->have_std = true;
     pr->have_fixed = false;

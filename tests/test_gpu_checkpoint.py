@@ -1,0 +1,92 @@
+"""Power-iteration checkpoint and resume: a run stopped after some batches,
+saved to a file and resumed in a fresh problem, continues with the same
+histories and eigenvalues as an uninterrupted run (k per batch bit-equal,
+last batch's event log equal, tallies equal to rounding); mismatched or
+damaged states are refused."""
+import numpy as np
+import pytest
+
+from paper_2506_00263_gb300 import binding as tb
+from paper_2506_00263_gb300 import inputs
+from tests._util import assert_logs_equal, assert_tally_close
+
+pytestmark = pytest.mark.gpu
+
+NPB, NI, NA = 20_000, 2, 5
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_2506_00263_gb300 import build
+    build.build()
+
+
+def _opts(scheme=tb.SCHEME_ASYNC, seed=4):
+    return tb.RunOpts(seed=seed, scheme=scheme, decomposition=tb.DECOMP_MONO, want_event_log=True)
+
+
+def _finish(prob, r):
+    return {"k": r["k_batch"], "kmean": r["k_mean"], "log": prob.event_log(int(r["n_source"][-1])),
+            "mesh": prob.tally(tb.TALLY_MESH), "scal": prob.tally(tb.TALLY_SCALARS),
+            "mesh_sd": prob.tally(tb.TALLY_MESH, stddev=True), "final": r["final_by_type"], "done": r["batches_done"]}
+
+
+def _check_same(a, b):
+    assert np.array_equal(a["k"], b["k"]), (a["k"], b["k"])
+    assert a["kmean"] == b["kmean"] and a["done"] == b["done"] == NI + NA
+    assert_logs_equal(a["log"], b["log"], "last batch")
+    assert np.array_equal(a["final"], b["final"])
+    assert_tally_close(a["mesh"], b["mesh"], "mesh")
+    assert_tally_close(a["scal"], b["scal"], "scalars")
+    assert_tally_close(a["mesh_sd"], b["mesh_sd"], "mesh sd")
+
+
+@pytest.mark.parametrize("scheme", [tb.SCHEME_ASYNC, tb.SCHEME_STACK], ids=["async", "stack"])
+def test_resume_from_file_equals_uninterrupted_run(scheme, tmp_path):
+    spec = inputs.c5g7_lattice()
+    full = tb.Problem(spec)
+    ref = _finish(full, full.power_iteration(NPB, NI, NA, _opts(scheme)))
+    full.close()
+
+    p1 = tb.Problem(spec)
+    part = p1.power_iteration(NPB, NI, NA, _opts(scheme), stop_after=3)
+    assert part["batches_done"] == 3
+    with pytest.raises(tb.TransportError):
+        p1.tally(tb.TALLY_MESH)          # tallies are final only at the end
+    path = tmp_path / "eig.ckpt"
+    path.write_bytes(p1.eig_checkpoint())
+    p1.close()
+
+    p2 = tb.Problem(spec)
+    r = p2.power_iteration(NPB, NI, NA, _opts(scheme), resume=path.read_bytes())
+    got = _finish(p2, r)
+    assert np.array_equal(got["k"][:3], part["k_batch"][:3])
+    _check_same(ref, got)
+    p2.close()
+
+
+def test_chained_stops_and_refusals():
+    spec = inputs.c5g7_lattice()
+    full = tb.Problem(spec)
+    ref = _finish(full, full.power_iteration(NPB, NI, NA, _opts()))
+    with pytest.raises(tb.TransportError) as e:
+        full.eig_checkpoint()                    # ran to the end: nothing kept
+    assert e.value.status == tb.TR_ERR_STATE
+    full.close()
+
+    p = tb.Problem(spec)
+    p.power_iteration(NPB, NI, NA, _opts(), stop_after=2)
+    s2 = p.eig_checkpoint()
+    r = p.power_iteration(NPB, NI, NA, _opts(), stop_after=5, resume=s2)
+    assert r["batches_done"] == 5
+    s5 = p.eig_checkpoint()
+    got = _finish(p, p.power_iteration(NPB, NI, NA, _opts(), resume=s5))
+    _check_same(ref, got)
+
+    for bad_opts, bad_state, status in ((_opts(seed=5), s2, tb.TR_ERR_STATE),
+                                        (_opts(), b"XXXXXXXX" + s2[8:], tb.TR_ERR_INVALID),
+                                        (_opts(), s2[:-8], tb.TR_ERR_INVALID)):
+        with pytest.raises(tb.TransportError) as e:
+            p.power_iteration(NPB, NI, NA, bad_opts, resume=bad_state)
+        assert e.value.status == status
+    p.close()
