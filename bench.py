@@ -179,7 +179,7 @@ def run_ours(args):
     decomp = _DECOMPS[args.decomp]
     spec = inputs.c5g7_lattice()
     opts = tb.RunOpts(seed=1 + 1000 * rank, scheme=scheme, decomposition=decomp, stash_slots=args.stash,
-                      blocks_per_sm=args.bps, remap_every=args.remap if args.decomp == "mono" else 1,
+                      blocks_per_sm=args.bps, remap_every=args.remap if args.decomp in ("mono", "stream") else 1,
                       queue_capacity=args.queue)
     stream = torch.cuda.current_stream()
     prob = tb.Problem(spec)
@@ -228,7 +228,7 @@ def run_ours(args):
     hbm, fmax, peak_kind = _peaks()
     avg_launch = kern_s / max(kern_launches, 1)
     ev_per_launch = ev_tot / max(kern_launches, 1)
-    fp64_ops_per_event = FP64_OPS_PER_EVENT.get((args.scheme, args.decomp))
+    fp64_ops_per_event = FP64_OPS_PER_EVENT.get((args.scheme, args.decomp), FP64_OPS_LATTICE)
     fp64_peak = N_SM * FP64_OPS_PER_CLK_PER_SM * fmax * 1e6 / 1e12     # TFLOP/s
     if fp64_ops_per_event:
         ach = fp64_ops_per_event * ev_per_launch / avg_launch / 1e12
@@ -290,7 +290,7 @@ def run_ours(args):
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": WORKLOAD, "scheme": args.scheme, "decomposition": args.decomp,
                    "stash_slots": args.stash, "blocks_per_sm": args.bps,
-                   "remap_every": args.remap if args.decomp == "mono" else 1,
+                   "remap_every": args.remap if args.decomp in ("mono", "stream") else 1,
                    "n_per_batch": args.n_per_batch, "batches": args.inactive + args.active,
                    "l2": "flushed between steps (512 MB write)"},
         "histories_per_s": hist_all / t,
@@ -511,7 +511,7 @@ def run_adjoint_workload(args):
 
 CE_WORKLOAD = ("continuous-energy infinite pin cell (4 synthetic nuclides, 1e5 points and 300 resonances each, "
                "union grid ~4e5), Watt-like source in the fuel, energy tally per material")
-_DECOMPS = {"mono": 0, "split": 1, "lookup": 2}
+_DECOMPS = {"mono": 0, "split": 1, "lookup": 2, "stream": 3}
 
 
 def _time_fixed(torch, tb, prob, opts, steps, warmup):
@@ -542,7 +542,7 @@ def run_ce_workload(args):
     prob = tb.Problem(spec)
     opts = tb.RunOpts(n_histories=args.n_hist, seed=1 + 1000 * rank,
                       scheme=tb.SCHEME_ASYNC if args.scheme == "async" else tb.SCHEME_STACK,
-                      decomposition=_DECOMPS[args.decomp], remap_every=args.remap if args.decomp == "mono" else 1)
+                      decomposition=_DECOMPS[args.decomp], remap_every=args.remap if args.decomp in ("mono", "stream") else 1)
     sampler = ClockSampler(torch.cuda.current_device())
     launches0 = tb.kernel_launch_count()
     with sampler:
@@ -698,7 +698,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--scheme", choices=["async", "stack"], default="async")
-    ap.add_argument("--decomp", choices=["split", "mono", "lookup"], default="mono")
+    ap.add_argument("--decomp", choices=["split", "mono", "lookup", "stream"], default="mono")
     ap.add_argument("--n-per-batch", type=int, default=N_PER_BATCH)
     ap.add_argument("--inactive", type=int, default=N_INACTIVE)
     ap.add_argument("--active", type=int, default=N_ACTIVE)

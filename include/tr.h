@@ -57,9 +57,12 @@ enum { TR_SCHEME_STACK = 0, TR_SCHEME_ASYNC = 1 };
 /* Task decomposition (Sec. 4): one "step" event; step / collision / surface;
  * or those three plus a cross-section lookup event of its own (one of the
  * alternate decompositions Sec. 5.2 points to), whose values travel with the
- * particle to the step and collision that follow.  The lookup event does not
- * count as an event: all three give the same histories. */
-enum { TR_DECOMP_MONO = 0, TR_DECOMP_SPLIT = 1, TR_DECOMP_SPLIT_LOOKUP = 2 };
+ * particle to the step and collision that follow.  STREAM (asynchronous
+ * scheme only) is another alternate decomposition: steps and surface
+ * crossings run inline, up to remap_every steps, and only collisions are
+ * deferred to a queue of their own.  The lookup event does not count as an
+ * event: all four give the same histories. */
+enum { TR_DECOMP_MONO = 0, TR_DECOMP_SPLIT = 1, TR_DECOMP_SPLIT_LOOKUP = 2, TR_DECOMP_STREAM = 3 };
 
 /* Rectilinear grid of cells; each cell may hold one z-aligned cylinder
  * ("pin") of radius pin_radius centred in its x-y box.  Planes are ascending;

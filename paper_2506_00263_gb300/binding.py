@@ -25,7 +25,7 @@ STATUS_NAMES = {0: "TR_OK", 1: "TR_ERR_INVALID", 2: "TR_ERR_NOMEM", 3: "TR_ERR_C
                 5: "TR_ERR_CUDA", 6: "TR_ERR_STATE"}
 EV_SOURCE, EV_SCATTER, EV_ABSORB, EV_SURF_INTERNAL, EV_SURF_REFLECT, EV_LEAK, EV_CUTOFF, EV_MAXEV = range(8)
 SCHEME_STACK, SCHEME_ASYNC = 0, 1
-DECOMP_MONO, DECOMP_SPLIT, DECOMP_SPLIT_LOOKUP = 0, 1, 2
+DECOMP_MONO, DECOMP_SPLIT, DECOMP_SPLIT_LOOKUP, DECOMP_STREAM = 0, 1, 2, 3
 TALLY_MESH, TALLY_ENERGY, TALLY_SCALARS, TALLY_TIME = 0, 1, 2, 3
 
 _dp = C.POINTER(C.c_double)

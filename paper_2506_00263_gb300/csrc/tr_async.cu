@@ -558,6 +558,31 @@ __global__ void __launch_bounds__(256, TR_ASYNC_MIN_BLOCKS) k_async(DevProblem P
                         live = mono_event<CE>(PP, RR, p, TT, acc, A.bank, err, lm);
                     }
                     next = live ? Q_STEP : Q_DEAD;
+                } else if (DEC == DEC_STREAM) {
+                    // streaming: a deferred collision (collision queue) first,
+                    // then steps and surface crossings inline; the next
+                    // collision sends the particle back to the collision queue
+                    next = Q_STEP;
+                    if (q == Q_COLLIDE) {
+                        live = split_collide<CE, false>(PP, RR, p, TT, acc, A.bank, err, em);
+                        next = live ? Q_STEP : Q_DEAD;
+                    }
+                    unsigned lm = em;
+                    for (int r = 0; r < R.remap_every; ++r) {
+                        const bool go = live && next == Q_STEP;
+                        lm = __ballot_sync(lm, go);
+                        if (!go) break;
+                        tr::XS X;
+                        double xr;
+                        FwdSink sink{TT, acc};
+                        step_event<CE>(PP, RR, p, sink, X, xr);
+                        if (p.pend == PEND_COLLIDE) {
+                            next = Q_COLLIDE;
+                        } else {
+                            live = split_surface(PP, RR, p, TT, acc, A.bank);
+                            next = live ? Q_STEP : Q_DEAD;
+                        }
+                    }
                 } else if (q == Q_STEP) {
                     tr::XS X;
                     double xr;
@@ -632,9 +657,11 @@ int async_max_blocks_per_sm(const DevProblem& P, int dec, int stash_slots)
 {
     const size_t smem = stash_bytes(stash_slots, dec == DEC_LOOKUP);
     if (P.kind == 1) {
+        if (dec == DEC_STREAM) return occupancy_async<true, DEC_STREAM>(smem);
         if (dec == DEC_LOOKUP) return occupancy_async<true, DEC_LOOKUP>(smem);
         return dec == DEC_SPLIT ? occupancy_async<true, DEC_SPLIT>(smem) : occupancy_async<true, DEC_MONO>(smem);
     }
+    if (dec == DEC_STREAM) return occupancy_async<false, DEC_STREAM>(smem);
     if (dec == DEC_LOOKUP) return occupancy_async<false, DEC_LOOKUP>(smem);
     return dec == DEC_SPLIT ? occupancy_async<false, DEC_SPLIT>(smem) : occupancy_async<false, DEC_MONO>(smem);
 }
@@ -656,10 +683,12 @@ cudaError_t launch_async(const DevProblem& P, const RunParams& R, const AsyncArg
     if (smem_bytes_out) *smem_bytes_out = (int)smem;
     count_launches(1);
     if (P.kind == 1) {
+        if (A.dec == DEC_STREAM) return launch_async_t<true, DEC_STREAM>(P, R, A, T, err, blocks, st, smem);
         if (A.dec == DEC_LOOKUP) return launch_async_t<true, DEC_LOOKUP>(P, R, A, T, err, blocks, st, smem);
         return A.dec == DEC_SPLIT ? launch_async_t<true, DEC_SPLIT>(P, R, A, T, err, blocks, st, smem)
                                   : launch_async_t<true, DEC_MONO>(P, R, A, T, err, blocks, st, smem);
     }
+    if (A.dec == DEC_STREAM) return launch_async_t<false, DEC_STREAM>(P, R, A, T, err, blocks, st, smem);
     if (A.dec == DEC_LOOKUP) return launch_async_t<false, DEC_LOOKUP>(P, R, A, T, err, blocks, st, smem);
     return A.dec == DEC_SPLIT ? launch_async_t<false, DEC_SPLIT>(P, R, A, T, err, blocks, st, smem)
                               : launch_async_t<false, DEC_MONO>(P, R, A, T, err, blocks, st, smem);

@@ -519,16 +519,17 @@ static tr_status validate_opts(const tr_run_opts* o)
 {
     if (!o) return set_err(TR_ERR_INVALID, "opts is NULL");
     if (o->scheme != TR_SCHEME_STACK && o->scheme != TR_SCHEME_ASYNC) return set_err(TR_ERR_INVALID, "bad scheme");
-    if (o->decomposition != TR_DECOMP_MONO && o->decomposition != TR_DECOMP_SPLIT &&
-        o->decomposition != TR_DECOMP_SPLIT_LOOKUP)
+    if (o->decomposition < TR_DECOMP_MONO || o->decomposition > TR_DECOMP_STREAM)
         return set_err(TR_ERR_INVALID, "bad decomposition");
+    if (o->decomposition == TR_DECOMP_STREAM && o->scheme != TR_SCHEME_ASYNC)
+        return set_err(TR_ERR_INVALID, "the streaming decomposition is offered by the asynchronous scheme");
     if (o->n_histories >= (1ull << 32)) return set_err(TR_ERR_INVALID, "n_histories must be < 2^32 per run");
     if (o->first_history + o->n_histories > (1ull << 32))
         return set_err(TR_ERR_INVALID, "first_history + n_histories must not exceed 2^32");
     if (o->remap_every < 0 || o->blocks_per_sm < 0 || o->stash_slots < 0 || o->max_spin < 0)
         return set_err(TR_ERR_INVALID, "negative tuning option");
-    if (o->decomposition != TR_DECOMP_MONO && o->remap_every > 1)
-        return set_err(TR_ERR_INVALID, "remap_every > 1 applies to the monolithic scheme only");
+    if (o->decomposition != TR_DECOMP_MONO && o->decomposition != TR_DECOMP_STREAM && o->remap_every > 1)
+        return set_err(TR_ERR_INVALID, "remap_every > 1 applies to the monolithic and streaming schemes only");
     return TR_OK;
 }
 
@@ -1197,7 +1198,7 @@ extern "C" tr_status tr_run_batched(tr_problem* const* probs, int32_t n, const u
     tr_status s = validate_opts(opts);
     if (s != TR_OK) return s;
     if (opts->scheme != TR_SCHEME_ASYNC) return set_err(TR_ERR_INVALID, "batched runs use the asynchronous scheme");
-    if (opts->decomposition == TR_DECOMP_SPLIT_LOOKUP)
+    if (opts->decomposition != TR_DECOMP_MONO && opts->decomposition != TR_DECOMP_SPLIT)
         return set_err(TR_ERR_INVALID, "batched runs use the monolithic or decomposed scheme");
     if (opts->first_history != 0) return set_err(TR_ERR_INVALID, "first_history applies to single runs only");
     tr_problem* lead = probs[0];

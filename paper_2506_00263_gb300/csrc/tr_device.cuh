@@ -61,9 +61,14 @@ constexpr uint32_t TAG_POP = 0x80000000u;
 constexpr int Q_STEP = 0, Q_COLLIDE = 1, Q_SURFACE = 2, Q_LOOKUP = 3, N_QUEUES = 4, Q_DEAD = 4;
 // task decompositions: monolithic (one event per step), decomposed (step,
 // collision, surface crossing), decomposed with the cross-section lookup as
-// an event of its own (the lookup's values travel with the particle)
-constexpr int DEC_MONO = 0, DEC_SPLIT = 1, DEC_LOOKUP = 2;
-__host__ __device__ constexpr int dec_queues(int dec) { return dec == DEC_MONO ? 1 : (dec == DEC_SPLIT ? 3 : 4); }
+// an event of its own (the lookup's values travel with the particle), or
+// streaming: steps and surface crossings run inline, up to remap_every steps,
+// and only collisions are deferred to a queue of their own
+constexpr int DEC_MONO = 0, DEC_SPLIT = 1, DEC_LOOKUP = 2, DEC_STREAM = 3;
+__host__ __device__ constexpr int dec_queues(int dec)
+{
+    return dec == DEC_MONO ? 1 : (dec == DEC_SPLIT ? 3 : (dec == DEC_LOOKUP ? 4 : 2));
+}
 
 struct DevProblem {
     // geometry

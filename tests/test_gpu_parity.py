@@ -16,8 +16,8 @@ pytestmark = pytest.mark.gpu
 SCHEMES = [(tb.SCHEME_STACK, tb.DECOMP_MONO), (tb.SCHEME_STACK, tb.DECOMP_SPLIT),
            (tb.SCHEME_STACK, tb.DECOMP_SPLIT_LOOKUP),
            (tb.SCHEME_ASYNC, tb.DECOMP_MONO), (tb.SCHEME_ASYNC, tb.DECOMP_SPLIT),
-           (tb.SCHEME_ASYNC, tb.DECOMP_SPLIT_LOOKUP)]
-IDS = ["stack-mono", "stack-split", "stack-lookup", "async-mono", "async-split", "async-lookup"]
+           (tb.SCHEME_ASYNC, tb.DECOMP_SPLIT_LOOKUP), (tb.SCHEME_ASYNC, tb.DECOMP_STREAM)]
+IDS = ["stack-mono", "stack-split", "stack-lookup", "async-mono", "async-split", "async-lookup", "async-stream"]
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -143,6 +143,9 @@ def test_scheduler_invariance_tuning():
         (tb.SCHEME_ASYNC, tb.DECOMP_MONO, dict(spill_threshold=-32, queue_capacity=64 * 32)),
         (tb.SCHEME_STACK, tb.DECOMP_SPLIT_LOOKUP, dict(queue_capacity=96)),
         (tb.SCHEME_ASYNC, tb.DECOMP_SPLIT_LOOKUP, dict(stash_slots=288, spill_threshold=-32, queue_capacity=4096)),
+        (tb.SCHEME_ASYNC, tb.DECOMP_STREAM, dict(remap_every=5)),
+        (tb.SCHEME_ASYNC, tb.DECOMP_STREAM, dict(remap_every=2, stash_slots=288, spill_threshold=-32,
+                                                 queue_capacity=4096)),
     ]
     for scheme, decomp, kw in variants:
         g = _gpu_fixed("lattice", n, scheme, decomp, **kw)
@@ -206,7 +209,8 @@ def test_bank_overflow_is_capacity_error():
 def test_invalid_options_rejected():
     prob = tb.Problem(_problem("cube"))
     for bad in (dict(scheme=7), dict(decomposition=5), dict(decomposition=tb.DECOMP_SPLIT, remap_every=2),
-                dict(decomposition=tb.DECOMP_SPLIT_LOOKUP, remap_every=2), dict(n_histories=1 << 33)):
+                dict(decomposition=tb.DECOMP_SPLIT_LOOKUP, remap_every=2),
+                dict(decomposition=tb.DECOMP_STREAM, scheme=tb.SCHEME_STACK), dict(n_histories=1 << 33)):
         kw = dict(n_histories=10)
         kw.update(bad)
         with pytest.raises(tb.TransportError) as e:
