@@ -14,7 +14,8 @@
 //   pathwise, per segment         d/dSt += g_abs len, d/dSs[m][g][*] -= g_abs len, d/dnuSf += g_prod len
 // Histories are not stored: pass 1 recomputes each history from its Philox
 // keys to get F, pass 2 recomputes it again and accumulates the terms.  Both
-// passes are history-based (one history per thread at a time); the derivative
+// passes keep one history per lane (its running F in registers) and refill a
+// lane from a global cursor the moment its history ends; the derivative
 // arrays are accumulated per block in shared memory when they fit.
 #include <algorithm>
 
@@ -58,6 +59,7 @@ struct AdjArgs {
     double* d_sigt;         // [m][g]
     double* d_sigs;         // [m][g][h]
     double* d_nusigf;       // [m][g]
+    unsigned long long* cursor;   // next history to start (zeroed before each pass)
     int use_smem;
 };
 
@@ -80,26 +82,50 @@ __global__ void __launch_bounds__(256) k_adjoint(DevProblem P, RunParams R, AdjA
     acc.zero();
     const Tallies T{};
     const Bank B{};
-    for (unsigned long long id = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; id < R.n_hist;
-         id += (unsigned long long)gridDim.x * blockDim.x) {
-        Particle p;
-        if (!source_particle<false>(P, R, (unsigned)id, p, nullptr, 0)) {
-            atomicCAS(&err->code, 0, ERR_INVALID);
+    constexpr unsigned FULL = 0xFFFFFFFFu;
+    const int lane = threadIdx.x & 31;
+    // each lane carries one history at a time and takes the next one from the
+    // global cursor as soon as its history ends, so lanes stay busy until the
+    // histories run out; one event per lane per pass of the loop
+    Particle p;
+    bool alive = false, exhausted = false;
+    double F = 0.0, before = 0.0;
+    unsigned long long id = 0;
+    for (;;) {
+        const unsigned need = __ballot_sync(FULL, !alive);
+        if (need && !exhausted) {
+            unsigned long long base = 0;
+            if (lane == 0) base = atomicAdd(A.cursor, (unsigned long long)__popc(need));
+            base = __shfl_sync(FULL, base, 0);
+            if (base + __popc(need) >= R.n_hist) exhausted = true;   // the same in every lane
+            if (!alive) {
+                const unsigned long long mine = base + __popc(need & ((1u << lane) - 1u));
+                if (mine < R.n_hist) {
+                    id = mine;
+                    alive = source_particle<false>(P, R, (unsigned)id, p, nullptr, 0);
+                    if (!alive) atomicCAS(&err->code, 0, ERR_INVALID);
+                    F = PASS2 ? A.F[id] : 0.0;
+                    before = 0.0;
+                }
+            }
+        }
+        const unsigned am = __ballot_sync(FULL, alive);
+        if (!am) {
+            if (exhausted) break;
             continue;
         }
-        double F = PASS2 ? A.F[id] : 0.0, before = 0.0;
-        bool alive = true;
-        while (alive) {
+        if (alive) {
             AdjSink sink{A.g_mesh, A.g_scal, 0.0, 0.0, 0};
             XS X;
             double xr;
             const int g0 = p.g;
             step_event<false>(P, R, p, sink, X, xr);
+            const bool coll = p.pend == PEND_COLLIDE;
+            const unsigned cm = __ballot_sync(am, coll);   // every lane of am is here
             int type;
             if (p.pend == PEND_ESCAPE) {
                 type = surface_event(P, p);
             } else {
-                const bool coll = p.pend == PEND_COLLIDE;
                 const int mg = sink.m * G + g0;
                 if (!PASS2) {
                     F += sink.f;
@@ -115,7 +141,7 @@ __global__ void __launch_bounds__(256) k_adjoint(DevProblem P, RunParams R, AdjA
                     before = before + sink.f;
                 }
                 if (coll) {
-                    type = collide_event<false>(P, R, p, X, xr, B, err);
+                    type = collide_event<false>(P, R, p, X, xr, B, err, cm);
                     if (PASS2) {
                         const double after = F - before;
                         if (type == EV_SCATTER) {
@@ -133,8 +159,8 @@ __global__ void __launch_bounds__(256) k_adjoint(DevProblem P, RunParams R, AdjA
                 }
             }
             alive = finish_event(P, R, p, type, T, acc, B);
+            if (!alive && !PASS2) A.F[id] = F;
         }
-        if (!PASS2) A.F[id] = F;
     }
     if (PASS2 && A.use_smem) {
         __syncthreads();
@@ -149,8 +175,10 @@ __global__ void __launch_bounds__(256) k_adjoint(DevProblem P, RunParams R, AdjA
 
 cudaError_t launch_adjoint(const DevProblem& P, const RunParams& R, const double* g_mesh, const double* g_scal,
                            double* F, double* d_sigt, double* d_sigs, double* d_nusigf, ErrorWord* err, int sms,
-                           cudaStream_t st)
+                           unsigned long long* cursors, cudaStream_t st)
 {
+    cudaError_t e0 = cudaMemsetAsync(cursors, 0, 2 * sizeof(unsigned long long), st);
+    if (e0 != cudaSuccess) return e0;
     AdjArgs A;
     A.g_mesh = g_mesh;
     A.g_scal = g_scal;
@@ -168,7 +196,9 @@ cudaError_t launch_adjoint(const DevProblem& P, const RunParams& R, const double
     }
     const int blocks = sms * 4;
     count_launches(2);
+    A.cursor = cursors;
     k_adjoint<false><<<blocks, 256, 0, st>>>(P, R, A, err);
+    A.cursor = cursors + 1;
     k_adjoint<true><<<blocks, 256, A.use_smem ? smem : 0, st>>>(P, R, A, err);
     return cudaGetLastError();
 }

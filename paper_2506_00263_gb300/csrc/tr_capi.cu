@@ -1108,7 +1108,10 @@ extern "C" tr_status tr_sensitivities(tr_problem* pr, const tr_run_opts* o, cons
     TR_CUDA(cudaMemsetAsync(pr->err, 0, sizeof(ErrorWord), st));
     RunParams R = base_params(o, o->n_histories);
     R.want_log = 0;
-    TR_CUDA(launch_adjoint(P, R, d_grad_mesh, d_grad_scalars, F, d_sigt, d_sigs, d_nusigf, pr->err, pr->sms, st));
+    unsigned long long* cursors = (unsigned long long*)workspace(pr, "adj_cursors", 16);
+    if (!cursors) return set_err(TR_ERR_NOMEM, "workspace allocation failed");
+    TR_CUDA(launch_adjoint(P, R, d_grad_mesh, d_grad_scalars, F, d_sigt, d_sigs, d_nusigf, pr->err, pr->sms, cursors,
+                           st));
     s = check_err(pr);
     if (s != TR_OK) return s;
     const double inv = 1.0 / (double)o->n_histories;
