@@ -666,9 +666,9 @@ def run_lattice_sweep(args):
 # only repeats table loads).
 FP64_OPS_LATTICE = 81.9
 # DRAM bytes (read + write) of one transport launch (one 1e6-history lattice
-# batch, asynchronous monolithic scheme, 3 events between remaps), from one ncu
+# batch, asynchronous monolithic scheme, 512 events between remaps), from one ncu
 # capture of the current kernel: dram__bytes_read.sum + dram__bytes_write.sum.
-TRAFFIC_PER_LAUNCH = {("async", "mono", 3, 1_000_000): 51.44e6}
+TRAFFIC_PER_LAUNCH = {("async", "mono", 512, 1_000_000): 58.98e6}
 FP64_OPS_PER_EVENT = {(s, d): FP64_OPS_LATTICE for s in ("async", "stack") for d in ("mono", "split")}
 
 
@@ -707,7 +707,8 @@ def main():
     ap.add_argument("--no-extras", action="store_true", help="skip the gradient and batched side measurements")
     ap.add_argument("--stash", type=int, default=0, help="async: particle slots per block stash (0 = default)")
     ap.add_argument("--bps", type=int, default=0, help="blocks per SM (0 = default)")
-    ap.add_argument("--remap", type=int, default=3, help="monolithic: events between remaps")
+    ap.add_argument("--remap", type=int, default=0,
+                    help="monolithic / streaming: events between remaps (0: 512 for the lattice, 4 for the CE pin cell)")
     ap.add_argument("--queue", type=int, default=0, help="stack: particles per stack; async: spill links x 32")
     ap.add_argument("--workload", choices=["lattice", "batched", "adjoint", "ce", "ce-sweep", "ce-time-sweep",
                                            "lattice-sweep"],
@@ -718,6 +719,8 @@ def main():
     ap.add_argument("--ebins", type=int, default=100, help="ce: energy-tally bins per material")
     ap.add_argument("--n-hist", type=int, default=1_000_000, help="ce: histories per run")
     args = ap.parse_args()
+    if args.remap <= 0:
+        args.remap = 4 if args.workload.startswith("ce") else 512
     if args.warmup < 3 and args.impl == "ours":
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
     if args.impl == "reference":

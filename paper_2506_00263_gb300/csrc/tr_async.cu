@@ -550,12 +550,38 @@ __global__ void __launch_bounds__(256, TR_ASYNC_MIN_BLOCKS) k_async(DevProblem P
                     }
                 }
                 if (!SPLIT) {
-                    // up to remap_every events; each pass's lane mask is a ballot of the previous one
-                    unsigned lm = em;
+                    // up to remap_every events per lane.  While the source
+                    // lasts, a lane whose history ended starts the next source
+                    // history in place (make_work inside the loop), so the warp
+                    // stays full; the live count needs no update for that (the
+                    // lane's death and its new history cancel).  Every lane
+                    // holding a slot stays in the loop, so the ballots name em.
+                    bool src_more = !BATCHED && src_left;
+                    const int leader = __ffs(em) - 1;
                     for (int r = 0; r < R.remap_every; ++r) {
-                        lm = __ballot_sync(lm, live);
-                        if (!live) break;
-                        live = mono_event<CE>(PP, RR, p, TT, acc, A.bank, err, lm);
+                        if (!BATCHED && r > 0 && src_more) {
+                            // refill once a quarter of the warp is idle (the source
+                            // sampling then runs for several lanes at once)
+                            const unsigned dead = __ballot_sync(em, !live);
+                            if (4 * __popc(dead) >= __popc(em) || dead == em) {
+                                unsigned long long first = 0;
+                                if (lane == leader) first = atomicAdd(&ctl->src_cursor, (unsigned long long)__popc(dead));
+                                first = __shfl_sync(em, first, leader);
+                                if (first + __popc(dead) >= R.n_hist) src_more = false;
+                                if (!live) {
+                                    const unsigned long long gid = first + __popc(dead & ((1u << lane) - 1u));
+                                    if (gid < R.n_hist) {
+                                        live = source_particle<CE>(P, R, (unsigned)gid, p,
+                                                                   A.use_src ? &A.src : nullptr, gid);
+                                        if (!live) fail(err, ERR_INVALID, 5);
+                                        acc.ev[EV_SOURCE] += 1u;
+                                    }
+                                }
+                            }
+                        }
+                        const unsigned lm = __ballot_sync(em, live);
+                        if (!lm) break;
+                        if (live) live = mono_event<CE>(PP, RR, p, TT, acc, A.bank, err, lm);
                     }
                     next = live ? Q_STEP : Q_DEAD;
                 } else if (DEC == DEC_STREAM) {
