@@ -246,6 +246,10 @@ __device__ __forceinline__ unsigned new_link(const AsyncArgs& A, int start, cons
 // ---------------------------------------------------------------------------
 // The persistent kernel
 // ---------------------------------------------------------------------------
+#ifndef TR_COLL_MIN
+#define TR_COLL_MIN 16   // pending collisions that make a warp run its collision pass
+#endif
+
 #ifndef TR_ASYNC_MIN_BLOCKS
 #define TR_ASYNC_MIN_BLOCKS 2   // resident blocks per SM the register allocation must allow
 #endif
@@ -550,14 +554,25 @@ __global__ void __launch_bounds__(256, TR_ASYNC_MIN_BLOCKS) k_async(DevProblem P
                     }
                 }
                 if (!SPLIT) {
-                    // up to remap_every events per lane.  While the source
-                    // lasts, a lane whose history ended starts the next source
-                    // history in place (make_work inside the loop), so the warp
-                    // stays full; the live count needs no update for that (the
-                    // lane's death and its new history cancel).  Every lane
-                    // holding a slot stays in the loop, so the ballots name em.
+                    // Up to remap_every passes.  While the source lasts, a lane
+                    // whose history ended starts the next source history in
+                    // place (make_work inside the loop), so the warp stays full;
+                    // the live count needs no update for that (the lane's death
+                    // and its new history cancel).  A step that ends in a
+                    // collision leaves the collision pending (multigroup; continuous
+                    // energy keeps the two as one event); a pass runs either
+                    // the steps (with their surface crossings) of the lanes with
+                    // nothing pending, or, once TR_COLL_MIN lanes are pending
+                    // (or nothing else can step), their collisions together, so
+                    // the FP64 work of the collision is issued for many lanes
+                    // at once.  The collision recomputes its lookup and reaction
+                    // draw from the counter-based keys: histories are the same.
+                    // Every lane holding a slot stays in the loop, so the
+                    // ballots name em; a pending collision survives a remap in
+                    // p.pend.
                     bool src_more = !BATCHED && src_left;
                     const int leader = __ffs(em) - 1;
+                    bool pend_coll = live && p.pend == PEND_COLLIDE;
                     for (int r = 0; r < R.remap_every; ++r) {
                         if (!BATCHED && r > 0 && src_more) {
                             // refill once a quarter of the warp is idle (the source
@@ -575,13 +590,38 @@ __global__ void __launch_bounds__(256, TR_ASYNC_MIN_BLOCKS) k_async(DevProblem P
                                                                    A.use_src ? &A.src : nullptr, gid);
                                         if (!live) fail(err, ERR_INVALID, 5);
                                         acc.ev[EV_SOURCE] += 1u;
+                                        pend_coll = false;
                                     }
                                 }
                             }
                         }
                         const unsigned lm = __ballot_sync(em, live);
                         if (!lm) break;
-                        if (live) live = mono_event<CE>(PP, RR, p, TT, acc, A.bank, err, lm);
+                        if (CE) {
+                            // continuous energy: a deferred collision would repeat
+                            // the costly lookup, so step and collision stay one event
+                            if (live) live = mono_event<CE>(PP, RR, p, TT, acc, A.bank, err, lm);
+                            continue;
+                        }
+                        const unsigned pm = __ballot_sync(em, live && pend_coll);
+                        if (pm == lm || __popc(pm) >= TR_COLL_MIN) {
+                            if (live && pend_coll) {
+                                live = split_collide<CE>(PP, RR, p, TT, acc, A.bank, err, pm);
+                                pend_coll = false;
+                                p.pend = 0u;
+                            }
+                        } else if (live && !pend_coll) {
+                            tr::XS X;
+                            double xr;
+                            FwdSink sink{TT, acc};
+                            step_event<CE>(PP, RR, p, sink, X, xr);
+                            if (p.pend == PEND_COLLIDE) {
+                                pend_coll = true;
+                            } else {
+                                live = finish_event(PP, RR, p, surface_event(PP, p), TT, acc, A.bank);
+                                p.pend = 0u;
+                            }
+                        }
                     }
                     next = live ? Q_STEP : Q_DEAD;
                 } else if (DEC == DEC_STREAM) {

@@ -1291,7 +1291,7 @@ extern "C" tr_status tr_run_batched(tr_problem* const* probs, int32_t n, const u
         const std::vector<int> c_S = tune.stash_slots ? std::vector<int>{tune.stash_slots} : std::vector<int>{288, 512, 1024};
         const std::vector<int> c_rm = tune.remap_every ? std::vector<int>{tune.remap_every}
                                       : A.dec          ? std::vector<int>{1}
-                                                       : std::vector<int>{1, 2, 4};
+                                                       : std::vector<int>{1, 4, 16, 64};
         std::vector<BatchTuning> cands;
         for (int bps : c_bps)
             for (int S : c_S)
