@@ -623,6 +623,91 @@ def run_ce_time_sweep(args):
     return 0
 
 
+def _oracle_fixed_shard(args):
+    """Worker of the all-core oracle timing (spawned process): one id range."""
+    name, n, offset = args
+    import oracle
+    from paper_2506_00263_gb300 import inputs
+    spec = {"cube": inputs.cube_one_group, "lattice": lambda: inputs.c5g7_lattice(fission=False),
+            "ce": lambda: inputs.ce_pin_cell()}[name]()
+    t0 = time.perf_counter()
+    r = oracle.run_fixed_source(spec, n, seed=1, id_offset=offset, logs=False)
+    return int(r["events_by_type"][1:].sum()), time.perf_counter() - t0
+
+
+def run_baseline_table(args):
+    """Per configuration: GPU events/s and histories/s (CUDA events, default
+    tuning), FP64-issue and HBM roofline fractions, and the oracle's events/s
+    on one host core and on all host cores (a spawned process pool over
+    contiguous id ranges; fixed-source histories, the lattice without fission
+    standing in for its eigenvalue batches).  One JSON line per row."""
+    import multiprocessing as mp
+    nproc = os.cpu_count() or 1
+    pool = mp.get_context("spawn").Pool(nproc)      # started before any GPU work
+    import oracle
+    oracle.lib()                                      # built once, before the workers load it
+    import torch
+    ws, rank, tb, inputs = _setup(torch)
+    if rank != 0:
+        return 0
+    hbm, fmax, _ = _peaks()
+    fp64_peak = N_SM * FP64_OPS_PER_CLK_PER_SM * fmax * 1e6
+
+    def oracle_rates(name, n1, nall):
+        ev1, t1 = _oracle_fixed_shard((name, n1, 0))
+        per = max(nall // nproc, 1)
+        res = pool.map(_oracle_fixed_shard, [(name, per, i * per) for i in range(nproc)])
+        return ev1 / t1, sum(e for e, _ in res) / max(t for _, t in res)
+
+    rows = []
+    # C1 cube, C3 CE pin cell (fixed source)
+    for label, name, spec, n, remap in (("C1 one-group cube", "cube", inputs.cube_one_group(), 100_000, 512),
+                                        ("C3 CE pin cell", "ce", inputs.ce_pin_cell(), 1_000_000, 4)):
+        prob = tb.Problem(spec)
+        opts = tb.RunOpts(n_histories=n, seed=1, scheme=tb.SCHEME_ASYNC, decomposition=tb.DECOMP_MONO,
+                          remap_every=remap)
+        t, ev = _time_fixed(torch, tb, prob, opts, 3, 2)
+        prob.close()
+        o1, oall = oracle_rates(name, 20_000 if name == "cube" else 2_000, 200_000 if name == "cube" else 20_000)
+        rows.append({"config": label, "gpu_events_per_s": ev / t, "gpu_histories_per_s": 3 * n / t,
+                     "oracle_1core_events_per_s": o1, "oracle_allcore_events_per_s": oall, "cores": nproc})
+    # C2 lattice power iteration, both schemes
+    prob = tb.Problem(inputs.c5g7_lattice())
+    stream = torch.cuda.current_stream()
+    for scheme in ("async", "stack"):
+        opts = tb.RunOpts(seed=1, scheme=tb.SCHEME_ASYNC if scheme == "async" else tb.SCHEME_STACK,
+                          decomposition=tb.DECOMP_MONO, remap_every=512 if scheme == "async" else 3)
+        prob.power_iteration(1_000_000, 2, 2, opts)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        r = prob.power_iteration(1_000_000, 5, 10, opts)
+        e1.record(stream)
+        e1.synchronize()
+        t = e0.elapsed_time(e1) * 1e-3
+        rows.append({"config": f"C2 7-group lattice, {scheme}", "gpu_events_per_s": r["events"] / t,
+                     "gpu_histories_per_s": r["histories"] / t})
+    prob.close()
+    o1, oall = oracle_rates("lattice", 10_000, 100_000)
+    rows[-2].update({"oracle_1core_events_per_s": o1, "oracle_allcore_events_per_s": oall, "cores": nproc})
+    # C4 batched, C5 gradient
+    bat = measure_batched(torch, tb, inputs, 2, 2, tb.DECOMP_MONO)
+    rows.append({"config": "C4 batched 256 boxes", "gpu_events_per_s": bat["events_per_s"],
+                 "gpu_histories_per_s": bat["histories"] / bat["seconds"],
+                 "vs_one_by_one": bat["sequential_single_runs"]["speedup_of_batched"]})
+    adj = measure_adjoint(torch, tb, inputs, 3, 2, tb.DECOMP_MONO)
+    rows.append({"config": "C5 gradient / forward time", "gradient_over_forward": adj["gradient_over_forward"],
+                 "forward_ms": adj["forward_ms"], "backward_ms": adj["backward_ms"]})
+    for r in rows:
+        if "gpu_events_per_s" in r:
+            r["fp64_issue_fraction"] = r["gpu_events_per_s"] * FP64_OPS_LATTICE / fp64_peak
+            r["hbm_fraction"] = r["gpu_events_per_s"] * B_EVENT / (hbm * 1e9)
+        print(json.dumps(r), flush=True)
+    pool.close()
+    return 0
+
+
 def run_lattice_sweep(args):
     """The paper's multigroup comparison (Sec. 5.1): power iterations of the
     lattice with 25 % inactive cycles, over particles per cycle and cycle
@@ -712,7 +797,7 @@ def main():
                     help="monolithic / streaming: events between remaps (0: 512 for the lattice, 4 for the CE pin cell)")
     ap.add_argument("--queue", type=int, default=0, help="stack: particles per stack; async: spill links x 32")
     ap.add_argument("--workload", choices=["lattice", "batched", "adjoint", "ce", "ce-sweep", "ce-time-sweep",
-                                           "lattice-sweep"],
+                                           "lattice-sweep", "baseline-table"],
                     default="lattice",
                     help="lattice: the k-eigenvalue lattice; batched: 256 box problems in one launch; "
                          "adjoint: forward + derivative kernels on the fixed-source lattice; ce: the continuous-"
@@ -738,6 +823,8 @@ def main():
         return run_ce_time_sweep(args)
     if args.workload == "lattice-sweep":
         return run_lattice_sweep(args)
+    if args.workload == "baseline-table":
+        return run_baseline_table(args)
     return run_ours(args)
 
 
