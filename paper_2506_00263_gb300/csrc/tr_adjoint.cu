@@ -15,8 +15,9 @@
 // Histories are not stored: pass 1 recomputes each history from its Philox
 // keys to get F, pass 2 recomputes it again and accumulates the terms.  Both
 // passes keep one history per lane (its running F in registers) and refill a
-// lane from a global cursor the moment its history ends; the derivative
-// arrays are accumulated per block in shared memory when they fit.
+// lane from a global cursor the moment its history ends; collisions wait
+// until many lanes have one and then run together; the derivative arrays are
+// accumulated per block in shared memory when they fit.
 #include <algorithm>
 
 #include "tr_events.cuh"
@@ -88,7 +89,7 @@ __global__ void __launch_bounds__(256) k_adjoint(DevProblem P, RunParams R, AdjA
     // global cursor as soon as its history ends, so lanes stay busy until the
     // histories run out; one event per lane per pass of the loop
     Particle p;
-    bool alive = false, exhausted = false;
+    bool alive = false, exhausted = false, pend = false;
     double F = 0.0, before = 0.0;
     unsigned long long id = 0;
     for (;;) {
@@ -106,6 +107,7 @@ __global__ void __launch_bounds__(256) k_adjoint(DevProblem P, RunParams R, AdjA
                     if (!alive) atomicCAS(&err->code, 0, ERR_INVALID);
                     F = PASS2 ? A.F[id] : 0.0;
                     before = 0.0;
+                    pend = false;
                 }
             }
         }
@@ -114,17 +116,45 @@ __global__ void __launch_bounds__(256) k_adjoint(DevProblem P, RunParams R, AdjA
             if (exhausted) break;
             continue;
         }
-        if (alive) {
+        // a step that ends in a collision leaves it pending; collisions run
+        // together once 16 lanes hold one (or nothing else can step)
+        const unsigned pm = __ballot_sync(FULL, alive && pend);
+        const bool coll_pass = (am & ~pm) == 0u || __popc(pm) >= 16;
+        if (coll_pass) {
+            if (alive && pend) {
+                // the step's lookup and reaction draw again, from the same keys
+                XS X;
+                const int m = material(P, p.cell);
+                xs_lookup<false>(P, p, m, X);
+                const Stream S = make_stream(R, p.id);
+                const uint4 b0 = S.block(p.n, BLK_MAIN);
+                const int mg = m * G + p.g;
+                const int type = collide_event<false>(P, R, p, X, u01(b0.z, b0.w), B, err, pm);
+                if (PASS2) {
+                    const double after = F - before;
+                    if (type == EV_SCATTER) {
+                        const double ss = __ldg(P.sigs + mg * G + p.g);
+                        atomicAdd(gss + mg * G + p.g, __drcp_rn(ss) * after);
+                        atomicAdd(gst + mg, (-X.inv_st) * after);
+                    } else {
+                        const double inv_sa = __drcp_rn(__ldg(P.sig_a + mg));
+                        atomicAdd(gst + mg, (inv_sa - X.inv_st) * after);
+                        for (int h = 0; h < G; ++h) atomicAdd(gss + mg * G + h, (-inv_sa) * after);
+                    }
+                }
+                pend = false;
+                alive = finish_event(P, R, p, type, T, acc, B);
+                if (!alive && !PASS2) A.F[id] = F;
+            }
+        } else if (alive && !pend) {
             AdjSink sink{A.g_mesh, A.g_scal, 0.0, 0.0, 0};
             XS X;
             double xr;
             const int g0 = p.g;
             step_event<false>(P, R, p, sink, X, xr);
             const bool coll = p.pend == PEND_COLLIDE;
-            const unsigned cm = __ballot_sync(am, coll);   // every lane of am is here
-            int type;
             if (p.pend == PEND_ESCAPE) {
-                type = surface_event(P, p);
+                alive = finish_event(P, R, p, surface_event(P, p), T, acc, B);
             } else {
                 const int mg = sink.m * G + g0;
                 if (!PASS2) {
@@ -140,25 +170,9 @@ __global__ void __launch_bounds__(256) k_adjoint(DevProblem P, RunParams R, AdjA
                     }
                     before = before + sink.f;
                 }
-                if (coll) {
-                    type = collide_event<false>(P, R, p, X, xr, B, err, cm);
-                    if (PASS2) {
-                        const double after = F - before;
-                        if (type == EV_SCATTER) {
-                            const double ss = __ldg(P.sigs + mg * G + p.g);
-                            atomicAdd(gss + mg * G + p.g, __drcp_rn(ss) * after);
-                            atomicAdd(gst + mg, (-X.inv_st) * after);
-                        } else {
-                            const double inv_sa = __drcp_rn(__ldg(P.sig_a + mg));
-                            atomicAdd(gst + mg, (inv_sa - X.inv_st) * after);
-                            for (int h = 0; h < G; ++h) atomicAdd(gss + mg * G + h, (-inv_sa) * after);
-                        }
-                    }
-                } else {
-                    type = surface_event(P, p);
-                }
+                if (coll) pend = true;
+                else alive = finish_event(P, R, p, surface_event(P, p), T, acc, B);
             }
-            alive = finish_event(P, R, p, type, T, acc, B);
             if (!alive && !PASS2) A.F[id] = F;
         }
     }
