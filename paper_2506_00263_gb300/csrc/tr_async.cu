@@ -40,9 +40,11 @@ struct Stash {
     unsigned *cell, *id, *n, *nsites, *pend, *prob;
     unsigned short* q[N_QUEUES];       // slot-index queues per event type
     unsigned short* fr;                // free-slot stack
-    int* cnt;                          // [0, N_QUEUES) queue counts, [CNT_FREE] free count, [CNT_LOCK] lock
+    int* cnt;                          // [0, N_QUEUES) queue counts, [CNT_FREE] free count, [CNT_LOCK] lock,
+                                       // [CNT_RUN] warps between a take and its deposit
 };
-constexpr int CNT_FREE = N_QUEUES, CNT_LOCK = N_QUEUES + 1;   // control words after the queue counts
+// control words after the queue counts
+constexpr int CNT_FREE = N_QUEUES, CNT_LOCK = N_QUEUES + 1, CNT_RUN = N_QUEUES + 2;
 
 __host__ __device__ __forceinline__ size_t stash_bytes(int S, bool xs = false)
 {
@@ -250,6 +252,21 @@ __device__ __forceinline__ unsigned new_link(const AsyncArgs& A, int start, cons
 #define TR_COLL_MIN 16   // pending collisions that make a warp run its collision pass
 #endif
 
+// Batch tail of the monolithic loop (source exhausted): a warp left with at
+// most TR_TAIL_EXIT live lanes, after TR_TAIL_MINRUN passes, hands its
+// particles to the block's other running warps through the stash; a warp with
+// a quarter of its lanes idle tops them up from the stash; an idle warp waits
+// up to TR_TAIL_WAIT polls for a full warp's worth while other warps run.
+#ifndef TR_TAIL_EXIT
+#define TR_TAIL_EXIT 16
+#endif
+#ifndef TR_TAIL_MINRUN
+#define TR_TAIL_MINRUN 4
+#endif
+#ifndef TR_TAIL_WAIT
+#define TR_TAIL_WAIT 256
+#endif
+
 #ifndef TR_ASYNC_MIN_BLOCKS
 #define TR_ASYNC_MIN_BLOCKS 2   // resident blocks per SM the register allocation must allow
 #endif
@@ -293,10 +310,11 @@ __global__ void __launch_bounds__(256, TR_ASYNC_MIN_BLOCKS) k_async(DevProblem P
     const int lane = threadIdx.x & 31;
     constexpr int nq = dec_queues(DEC);
     const bool tm = BATCHED || P.timed != 0;   // particle times travel through the stash
+    constexpr bool MERGE = !SPLIT && !BATCHED;   // batch-tail consolidation of the monolithic loop
     AsyncCtl* ctl = A.ctl;
 
     if (threadIdx.x == 0) {
-        for (int q = 0; q <= CNT_LOCK; ++q) st.cnt[q] = 0;
+        for (int q = 0; q <= CNT_RUN; ++q) st.cnt[q] = 0;
         st.cnt[CNT_FREE] = S;
     }
     for (int i = threadIdx.x; i < S; i += blockDim.x) st.fr[i] = (unsigned short)(S - 1 - i);
@@ -309,6 +327,7 @@ __global__ void __launch_bounds__(256, TR_ASYNC_MIN_BLOCKS) k_async(DevProblem P
     bool idle = false;
     unsigned acc_prob = 0;   // batched: the problem whose scores acc holds
     bool spill_ok = true;   // cleared once the link arena is exhausted
+    int tail_wait = 0;      // polls passed over a partial queue while other warps run
     const int qstart = (int)(blockIdx.x * 7 + (threadIdx.x >> 5)) & (N_GQ - 1);
 
     for (;;) {
@@ -333,6 +352,7 @@ __global__ void __launch_bounds__(256, TR_ASYNC_MIN_BLOCKS) k_async(DevProblem P
 #pragma unroll
         for (int q = 0; q < N_QUEUES; ++q) cnts[q] = *(volatile int*)(st.cnt + q);
         const int nfree = *(volatile int*)(st.cnt + CNT_FREE);
+        const int n_run = *(volatile int*)(st.cnt + CNT_RUN);
         int q = 0;
         for (int k = 1; k < nq; ++k)
             if (cnts[k] > cnts[q]) q = k;
@@ -351,13 +371,17 @@ __global__ void __launch_bounds__(256, TR_ASYNC_MIN_BLOCKS) k_async(DevProblem P
         } else if (src_left && nfree >= 32) {
             mode = 1;
             take = 32;
-        } else if (cnts[q] > 0) {
+        } else if (cnts[q] > 0 && (!MERGE || src_left || n_run == 0 || tail_wait >= TR_TAIL_WAIT)) {
+            // a partial queue; in the batch tail only once no other warp of the
+            // block runs (it would take these particles into its idle lanes)
+            // or after TR_TAIL_WAIT polls
             mode = 0;
             take = cnts[q];
         } else {
             mode = 3;
             take = 0;
         }
+        tail_wait = (mode == 3 && cnts[q] > 0) ? tail_wait + 1 : 0;
         int slot = -1;
         if (mode == 0 || mode == 2) {
             if (lane < take) slot = st.q[q][cnts[q] - take + lane];
@@ -368,6 +392,7 @@ __global__ void __launch_bounds__(256, TR_ASYNC_MIN_BLOCKS) k_async(DevProblem P
         if (lane == 0) {
             if (mode == 0 || mode == 2) st.cnt[q] = cnts[q] - take;
             else if (mode == 1) st.cnt[CNT_FREE] = nfree - 32;
+            if (MERGE && (mode == 0 || mode == 1)) st.cnt[CNT_RUN] = n_run + 1;
         }
         unlock_stash(st);
 
@@ -491,10 +516,10 @@ __global__ void __launch_bounds__(256, TR_ASYNC_MIN_BLOCKS) k_async(DevProblem P
         }
 
 #ifdef TR_PROFILE_LANES
-        {   // exact warp fill per iteration: sites 12 + queue (mode 0) and 15 (make_work)
+        {   // exact warp fill per iteration: sites 26 + queue (mode 0) and 30 (make_work)
             const unsigned hm = __ballot_sync(FULLM, slot >= 0);
             if (lane == 0 && hm) {
-                const int site = mode == 1 ? 25 : 12 + q;
+                const int site = mode == 1 ? 30 : 26 + q;
                 atomicAdd(&g_lane_prof[2 * site], 1ull);
                 atomicAdd(&g_lane_prof[2 * site + 1], (unsigned long long)__popc(hm));
             }
@@ -569,11 +594,61 @@ __global__ void __launch_bounds__(256, TR_ASYNC_MIN_BLOCKS) k_async(DevProblem P
                     // draw from the counter-based keys: histories are the same.
                     // Every lane holding a slot stays in the loop, so the
                     // ballots name em; a pending collision survives a remap in
-                    // p.pend.
+                    // p.pend.  Once the source is exhausted (the batch tail),
+                    // histories end and lanes empty; the block's warps then
+                    // consolidate through the stash: a warp with a quarter of
+                    // its lanes idle takes waiting particles into them, and a
+                    // warp left with few live lanes deposits its particles for
+                    // the others, so fewer, fuller warps issue the FP64 work.
                     bool src_more = !BATCHED && src_left;
                     const int leader = __ffs(em) - 1;
                     bool pend_coll = live && p.pend == PEND_COLLIDE;
                     for (int r = 0; r < R.remap_every; ++r) {
+                        if (MERGE && r > 0 && !src_more && em == FULLM) {
+                            const unsigned dead = __ballot_sync(FULLM, !live);
+                            const int nd = __popc(dead);
+                            if (4 * nd >= 32) {
+                                int avail = 0, others = 0;
+                                if (lane == 0) {
+                                    avail = *(volatile int*)(st.cnt + Q_STEP);
+                                    others = *(volatile int*)(st.cnt + CNT_RUN) - 1;
+                                }
+                                avail = __shfl_sync(FULLM, avail, 0);
+                                others = __shfl_sync(FULLM, others, 0);
+                                if (avail > 0) {
+                                    // top up: the first k idle lanes adopt waiting
+                                    // particles and free their own slots
+                                    if (!lock_stash(st, R, err)) break;
+                                    const int c = *(volatile int*)(st.cnt + Q_STEP);
+                                    const int nf = *(volatile int*)(st.cnt + CNT_FREE);
+                                    const int k = c < nd ? c : nd;
+                                    const int rank = __popc(dead & ((1u << lane) - 1u));
+                                    const bool adopt = !live && rank < k;
+                                    int ns = -1;
+                                    if (adopt) {
+                                        ns = st.q[Q_STEP][c - k + rank];
+                                        st.fr[nf + rank] = (unsigned short)slot;
+                                    }
+                                    __syncwarp();
+                                    if (lane == 0) {
+                                        st.cnt[Q_STEP] = c - k;
+                                        st.cnt[CNT_FREE] = nf + k;
+                                    }
+                                    unlock_stash(st);
+                                    // the adopted particles were already counted live;
+                                    // the k histories they replace ended here
+                                    if (lane == 0 && k > 0) atomicAdd(&ctl->live, 0ull - (unsigned long long)k);
+                                    if (adopt) {
+                                        slot = ns;
+                                        slot_load<XS>(st, slot, p, tm);
+                                        live = true;
+                                        pend_coll = p.pend == PEND_COLLIDE;
+                                    }
+                                } else if (32 - nd <= TR_TAIL_EXIT && r >= TR_TAIL_MINRUN && others > 0) {
+                                    break;   // deposit: the block's running warps take these
+                                }
+                            }
+                        }
                         if (!BATCHED && r > 0 && src_more) {
                             // refill once a quarter of the warp is idle (the source
                             // sampling then runs for several lanes at once)
@@ -597,6 +672,10 @@ __global__ void __launch_bounds__(256, TR_ASYNC_MIN_BLOCKS) k_async(DevProblem P
                         }
                         const unsigned lm = __ballot_sync(em, live);
                         if (!lm) break;
+                        TR_LANES(12);
+                        if (!src_more) TR_LANES(25);
+                        if (live) TR_LANES(13);
+                        if (live && !src_more) TR_LANES(31);
                         if (CE) {
                             // continuous energy: a deferred collision would repeat
                             // the costly lookup, so step and collision stay one event
@@ -606,11 +685,13 @@ __global__ void __launch_bounds__(256, TR_ASYNC_MIN_BLOCKS) k_async(DevProblem P
                         const unsigned pm = __ballot_sync(em, live && pend_coll);
                         if (pm == lm || __popc(pm) >= TR_COLL_MIN) {
                             if (live && pend_coll) {
+                                TR_LANES(15);
                                 live = split_collide<CE>(PP, RR, p, TT, acc, A.bank, err, pm);
                                 pend_coll = false;
                                 p.pend = 0u;
                             }
                         } else if (live && !pend_coll) {
+                            TR_LANES(14);
                             tr::XS X;
                             double xr;
                             FwdSink sink{TT, acc};
@@ -678,6 +759,7 @@ __global__ void __launch_bounds__(256, TR_ASYNC_MIN_BLOCKS) k_async(DevProblem P
         __syncwarp();
         if (!lock_stash(st, R, err)) break;
         const bool has = slot >= 0;
+        if (MERGE && lane == 0) st.cnt[CNT_RUN] -= 1;
         for (int qq = 0; qq <= N_QUEUES; ++qq) {
             const bool mine = has && (qq == N_QUEUES ? next == Q_DEAD : next == qq);
             const unsigned mask = __ballot_sync(FULLM, mine);
