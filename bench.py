@@ -754,7 +754,7 @@ FP64_OPS_LATTICE = 82.8
 # DRAM bytes (read + write) of one transport launch (one 1e6-history lattice
 # batch, asynchronous monolithic scheme, 512 events between remaps), from one ncu
 # capture of the current kernel: dram__bytes_read.sum + dram__bytes_write.sum.
-TRAFFIC_PER_LAUNCH = {("async", "mono", 512, 1_000_000): 59.77e6}
+TRAFFIC_PER_LAUNCH = {("async", "mono", 512, 1_000_000): 64.90e6}
 FP64_OPS_PER_EVENT = {(s, d): FP64_OPS_LATTICE for s in ("async", "stack") for d in ("mono", "split")}
 
 
