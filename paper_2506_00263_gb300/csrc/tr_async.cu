@@ -271,6 +271,51 @@ __device__ __forceinline__ unsigned new_link(const AsyncArgs& A, int start, cons
 #define TR_ASYNC_MIN_BLOCKS 2   // resident blocks per SM the register allocation must allow
 #endif
 
+// Source particles sampled ahead of the transport launch: make_work then
+// only loads them.  The source event of history i depends on i alone (and its
+// fission-bank site), so a pre-sampled particle equals the one make_work
+// would sample; the sampling's FP64 work runs in full warps instead of in the
+// few lanes a refill serves.
+#ifndef TR_PRE_REFILL
+#define TR_PRE_REFILL 1   // idle lanes that make a warp refill from pre-sampled sources
+#endif
+
+template <bool CE>
+__global__ void __launch_bounds__(256) k_presample(DevProblem P, RunParams R, Bank src, int use_src, SoA out)
+{
+    const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
+    for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < R.n_hist; i += stride) {
+        Particle p;
+        const bool ok = source_particle<CE>(P, R, (unsigned)i, p, use_src ? &src : nullptr, i);
+        out.x[i] = p.x; out.y[i] = p.y; out.z[i] = p.z;
+        out.u[i] = p.u; out.v[i] = p.v; out.w[i] = p.w;
+        out.iu[i] = p.iu; out.iv[i] = p.iv; out.iw[i] = p.iw; out.ia[i] = p.ia;
+        if (CE) out.E[i] = p.E; else out.g[i] = p.g;
+        out.cell[i] = p.cell;
+        out.id[i] = ok ? (unsigned)i : ~(unsigned)i;   // a failed source keeps another id
+    }
+}
+
+// The particle k_presample left for history i, in the state source_particle
+// leaves (n = 1, nothing banked or pending, t = 0); false if sampling failed.
+template <bool CE>
+__device__ __forceinline__ bool load_presampled(const SoA& s, unsigned long long i, Particle& p)
+{
+    p.x = s.x[i]; p.y = s.y[i]; p.z = s.z[i];
+    p.u = s.u[i]; p.v = s.v[i]; p.w = s.w[i];
+    p.iu = s.iu[i]; p.iv = s.iv[i]; p.iw = s.iw[i]; p.ia = s.ia[i];
+    p.E = CE ? s.E[i] : 0.0;
+    p.g = CE ? 0 : s.g[i];
+    p.cell = s.cell[i];
+    p.id = (unsigned)i;
+    p.n = 1u;
+    p.nsites = 0u;
+    p.pend = 0u;
+    p.prob = 0u;
+    p.t = 0.0;
+    return s.id[i] == (unsigned)i;
+}
+
 // Batched launches: problem p owns source indices [hist_off[p], hist_off[p+1]).
 __device__ __forceinline__ int find_problem(const unsigned long long* off, int n, unsigned long long gid)
 {
@@ -550,7 +595,8 @@ __global__ void __launch_bounds__(256, TR_ASYNC_MIN_BLOCKS) k_async(DevProblem P
                     }
                     acc.ev[EV_SOURCE] += 1u;
                 } else {
-                    live = source_particle<CE>(P, R, (unsigned)id, p, A.use_src ? &A.src : nullptr, id);
+                    live = A.use_pre ? load_presampled<CE>(A.pre, id, p)
+                                     : source_particle<CE>(P, R, (unsigned)id, p, A.use_src ? &A.src : nullptr, id);
                     acc.ev[EV_SOURCE] += 1u;
                 }
                 if (!live) fail(err, ERR_INVALID, 5);
@@ -651,9 +697,12 @@ __global__ void __launch_bounds__(256, TR_ASYNC_MIN_BLOCKS) k_async(DevProblem P
                         }
                         if (!BATCHED && r > 0 && src_more) {
                             // refill once a quarter of the warp is idle (the source
-                            // sampling then runs for several lanes at once)
+                            // sampling then runs for several lanes at once), or,
+                            // with pre-sampled sources (a load), once
+                            // TR_PRE_REFILL lanes are idle
                             const unsigned dead = __ballot_sync(em, !live);
-                            if (4 * __popc(dead) >= __popc(em) || dead == em) {
+                            const int nd = __popc(dead);
+                            if ((A.use_pre ? nd >= TR_PRE_REFILL : 4 * nd >= __popc(em)) || dead == em) {
                                 unsigned long long first = 0;
                                 if (lane == leader) first = atomicAdd(&ctl->src_cursor, (unsigned long long)__popc(dead));
                                 first = __shfl_sync(em, first, leader);
@@ -661,8 +710,9 @@ __global__ void __launch_bounds__(256, TR_ASYNC_MIN_BLOCKS) k_async(DevProblem P
                                 if (!live) {
                                     const unsigned long long gid = first + __popc(dead & ((1u << lane) - 1u));
                                     if (gid < R.n_hist) {
-                                        live = source_particle<CE>(P, R, (unsigned)gid, p,
-                                                                   A.use_src ? &A.src : nullptr, gid);
+                                        live = A.use_pre ? load_presampled<CE>(A.pre, gid, p)
+                                                         : source_particle<CE>(P, R, (unsigned)gid, p,
+                                                                               A.use_src ? &A.src : nullptr, gid);
                                         if (!live) fail(err, ERR_INVALID, 5);
                                         acc.ev[EV_SOURCE] += 1u;
                                         pend_coll = false;
@@ -843,6 +893,14 @@ cudaError_t launch_async(const DevProblem& P, const RunParams& R, const AsyncArg
 }
 
 // Batched launches (multigroup; monolithic or decomposed).
+cudaError_t launch_presample(const DevProblem& P, const RunParams& R, const AsyncArgs& A, int blocks, cudaStream_t st)
+{
+    count_launches(1);
+    if (P.kind == 1) k_presample<true><<<blocks, 256, 0, st>>>(P, R, A.src, A.use_src, A.pre);
+    else k_presample<false><<<blocks, 256, 0, st>>>(P, R, A.src, A.use_src, A.pre);
+    return cudaGetLastError();
+}
+
 int async_batched_max_blocks_per_sm(int dec, int stash_slots)
 {
     const size_t smem = stash_bytes(stash_slots);

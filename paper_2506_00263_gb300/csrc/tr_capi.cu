@@ -446,6 +446,11 @@ extern "C" void tr_problem_destroy(tr_problem* pr)
 // ---------------------------------------------------------------------------
 // run helpers
 // ---------------------------------------------------------------------------
+// Largest history count whose sources are sampled ahead of the asynchronous
+// monolithic launch (16.8M: 2.6 GB of particle records); larger runs sample
+// inside the launch, with the same results.
+constexpr unsigned long long PRESAMPLE_MAX_HIST = 1ull << 24;
+
 static bool carve_soa(tr_problem* pr, const char* name, unsigned long long cap, SoA& s)
 {
     const size_t n = (size_t)cap;
@@ -660,6 +665,11 @@ static tr_status transport(tr_problem* pr, const tr_run_opts* o, RunParams R, co
     A.src = src ? *src : bank;
     A.dec = dec;
     A.stash_slots = S;
+    // monolithic scheme: sample the sources ahead of the launch (make_work loads them)
+    if (dec == DEC_MONO && R.n_hist <= PRESAMPLE_MAX_HIST) {
+        if (!carve_soa(pr, "presample", R.n_hist, A.pre)) return set_err(TR_ERR_NOMEM, "source buffer allocation failed");
+        A.use_pre = 1;
+    }
     AsyncCtl hc;
     std::memset(&hc, 0, sizeof(hc));
     std::memset(hc.free_q, 0xFF, sizeof(hc.free_q));
@@ -671,6 +681,7 @@ static tr_status transport(tr_problem* pr, const tr_run_opts* o, RunParams R, co
     int smem = 0;
     LaunchTimer lt;
     TR_CUDA(cudaEventRecord(lt.a, st));
+    if (A.use_pre) TR_CUDA(launch_presample(P, R, A, pr->sms * 8, st));
     TR_CUDA(launch_async(P, R, A, T, pr->err, pr->sms * bps, st, &smem));
     TR_CUDA(cudaEventRecord(lt.b, st));
     out.launches += 1;

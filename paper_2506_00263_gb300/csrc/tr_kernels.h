@@ -42,6 +42,8 @@ struct AsyncArgs {
     AsyncCtl* ctl;
     Bank bank, src;
     int use_src;
+    SoA pre;                           // source particles sampled before the launch (x..ia, E or g, cell, id)
+    int use_pre;                       // 1: make_work loads its particles from pre instead of sampling them
     int dec;                           // task decomposition: DEC_MONO, DEC_SPLIT, DEC_LOOKUP
     int stash_slots;
     // batched launches: per-problem descriptors, tallies and history offsets
@@ -54,6 +56,8 @@ struct AsyncArgs {
 cudaError_t launch_async(const DevProblem& P, const RunParams& R, const AsyncArgs& A, const Tallies& T, ErrorWord* err,
                          int blocks, cudaStream_t st, int* smem_bytes_out);
 int async_max_blocks_per_sm(const DevProblem& P, int dec, int stash_slots);
+// Samples the source particles of histories [0, R.n_hist) into A.pre.
+cudaError_t launch_presample(const DevProblem& P, const RunParams& R, const AsyncArgs& A, int blocks, cudaStream_t st);
 cudaError_t launch_async_batched(const DevProblem& P0, const RunParams& R, const AsyncArgs& A, ErrorWord* err,
                                  int blocks, cudaStream_t st);
 int async_batched_max_blocks_per_sm(int dec, int stash_slots);
