@@ -99,16 +99,22 @@ static void rng_block(uint64_t seed, uint32_t tag, uint64_t id, uint32_t n, uint
 #define TAG_POPULATION 0x80000000u
 
 /* ------------------------------------------------------------------------ */
-/* Natural logarithm of a positive normal double (the contract's own):       */
-/* x = 2^e m with m in [sqrt(1/2), sqrt(2)); s = (m-1)/(m+1);                 */
-/* log m = 2 atanh(s) = 2 s sum_{j=0..9} s^(2j)/(2j+1) (Horner in s^2, each  */
-/* step one fma); log x = fma(e, LN2_HI, fma(e, LN2_LO, log m)) with ln 2     */
-/* split at 40 bits (e*LN2_HI is exact).                                       */
+/* Natural logarithm of a positive normal double (the contract's own), by    */
+/* Tang's table-driven method (ACM TOMS 16 (1990) 378):                      */
+/*   x = 2^e m, m in [sqrt(1/2), sqrt(2)]; k = the integer nearest            */
+/*   128 (m - 1), c_k = 1 + k/128, i_k = 1/c_k (rounded);                     */
+/*   r = fma(m, i_k, -1); log1p(r) = r + r^2 (-1/2 + r (1/3 + ... + r/7))     */
+/*   (Horner from 1/7, one fma a step; |r| < 2^-7.4);                          */
+/*   log x = fma(e, LN2_HI, fma(e, LN2_LO, T_k + log1p(r))), T_k = -log(i_k).  */
+/* The table values T_k come from the atanh series:                          */
+/*   s = (m-1)/(m+1); log m = 2 s sum_{j=0..9} s^(2j)/(2j+1) (Horner in s^2,  */
+/*   each step one fma); log x = fma(e, LN2_HI, fma(e, LN2_LO, log m)).        */
+/* ln 2 is split at 40 bits (e*LN2_HI is exact).                               */
 /* ------------------------------------------------------------------------ */
 static double bits_to_double(uint64_t b) { double d; memcpy(&d, &b, 8); return d; }
 static uint64_t double_to_bits(double d) { uint64_t b; memcpy(&b, &d, 8); return b; }
 
-double orc_log(double x)
+static double log_atanh(double x)
 {
     const double SQRT2 = bits_to_double(0x3FF6A09E667F3BCDull);
     const double LN2_HI = bits_to_double(0x3FE62E42FEFA4000ull);
@@ -135,6 +141,51 @@ double orc_log(double x)
     double r = (s + s) * p;
     double de = (double)e;
     return fma(de, LN2_HI, fma(de, LN2_LO, r));
+}
+
+#define LOG_K_LO (-38)
+#define LOG_K_HI 54
+static double log_inv_c[LOG_K_HI - LOG_K_LO + 1];
+static double log_t[LOG_K_HI - LOG_K_LO + 1];
+static int log_ready = 0;
+
+static void log_make_table(void)
+{
+    for (int k = LOG_K_LO; k <= LOG_K_HI; ++k) {
+        double c = (double)(128 + k) / 128.0;
+        double ic = 1.0 / c;
+        log_inv_c[k - LOG_K_LO] = ic;
+        log_t[k - LOG_K_LO] = -log_atanh(ic);
+    }
+    log_ready = 1;
+}
+
+double orc_log(double x)
+{
+    const double SQRT2 = bits_to_double(0x3FF6A09E667F3BCDull);
+    const double LN2_HI = bits_to_double(0x3FE62E42FEFA4000ull);
+    const double LN2_LO = bits_to_double(0xBD48432A1B0E2634ull);
+    if (!log_ready) log_make_table();
+    uint64_t b = double_to_bits(x);
+    int e = (int)((b >> 52) & 0x7FF) - 1023;
+    double m = bits_to_double((b & 0x000FFFFFFFFFFFFFull) | 0x3FF0000000000000ull);
+    if (m > SQRT2) {
+        m = m * 0.5;
+        e = e + 1;
+    }
+    /* nearest table point: m - 1 is exact here, and so is its scaling by 128 */
+    int k = (int)floor((m - 1.0) * 128.0 + 0.5);
+    double ic = log_inv_c[k - LOG_K_LO];
+    double r = fma(m, ic, -1.0);
+    double q = 1.0 / 7.0;
+    q = fma(q, r, -1.0 / 6.0);
+    q = fma(q, r, 1.0 / 5.0);
+    q = fma(q, r, -1.0 / 4.0);
+    q = fma(q, r, 1.0 / 3.0);
+    q = fma(q, r, -1.0 / 2.0);
+    double p = fma(q, r * r, r);
+    double de = (double)e;
+    return fma(de, LN2_HI, fma(de, LN2_LO, log_t[k - LOG_K_LO] + p));
 }
 
 /* ------------------------------------------------------------------------ */

@@ -120,6 +120,52 @@ static void* workspace(tr_problem* pr, const char* name, size_t bytes)
 }
 
 // ---------------------------------------------------------------------------
+// Logarithm table for tr_log (Tang's table-driven method): for each table
+// point c_k = 1 + k/128, the pair {1/c_k, -log(1/c_k)}, the logarithm taken
+// from the atanh series: x = 2^e m, m in [sqrt(1/2), sqrt(2)], s = (m-1)/(m+1),
+// log m = 2 s sum_{j<10} s^(2j)/(2j+1) (Horner in s^2, one fma a step),
+// log x = fma(e, LN2_HI, fma(e, LN2_LO, log m)).
+// ---------------------------------------------------------------------------
+static double bits_double(uint64_t b)
+{
+    double d;
+    std::memcpy(&d, &b, 8);
+    return d;
+}
+
+static double log_series(double x)
+{
+    uint64_t b;
+    std::memcpy(&b, &x, 8);
+    int e = (int)((b >> 52) & 0x7FF) - 1023;
+    double m = bits_double((b & 0x000FFFFFFFFFFFFFull) | 0x3FF0000000000000ull);
+    if (m > bits_double(0x3FF6A09E667F3BCDull)) {
+        m = m * 0.5;
+        e += 1;
+    }
+    const double s = (m - 1.0) / (m + 1.0);
+    const double z = s * s;
+    double p = 1.0 / 19.0;
+    const double c[9] = {1.0 / 17.0, 1.0 / 15.0, 1.0 / 13.0, 1.0 / 11.0, 1.0 / 9.0, 1.0 / 7.0, 1.0 / 5.0, 1.0 / 3.0, 1.0};
+    for (double ci : c) p = std::fma(p, z, ci);
+    const double r = (s + s) * p;
+    const double de = (double)e;
+    return std::fma(de, bits_double(0x3FE62E42FEFA4000ull), std::fma(de, bits_double(0xBD48432A1B0E2634ull), r));
+}
+
+static std::vector<double> log_table()
+{
+    std::vector<double> t(2 * LOG_TAB_N);
+    for (int k = LOG_KMIN; k <= LOG_KMAX; ++k) {
+        const double c = (double)(128 + k) / 128.0;
+        const double ic = 1.0 / c;
+        t[2 * (k - LOG_KMIN)] = ic;
+        t[2 * (k - LOG_KMIN) + 1] = -log_series(ic);
+    }
+    return t;
+}
+
+// ---------------------------------------------------------------------------
 // problem creation
 // ---------------------------------------------------------------------------
 static bool ascending(const double* p, int n)
@@ -181,6 +227,9 @@ extern "C" tr_status tr_problem_create(const tr_geometry_desc* G, const tr_xs_de
         tr_problem_destroy(pr);
         return set_err(s, m);
     };
+
+    const std::vector<double> lt = log_table();
+    P.log_tab = upload(pr, lt.data(), lt.size(), &ok);
 
     // geometry
     P.nx = G->nx; P.ny = G->ny; P.nz = G->nz;

@@ -110,6 +110,8 @@ struct DevProblem {
     int timed, n_tbins;
     double t_cen, tb_w, v_c;
     const double *inv_vel;
+    // logarithm table: {1/c_k, -log(1/c_k)} pairs (see tr_log)
+    const double* log_tab;
 };
 
 // Per-run parameters.
@@ -250,36 +252,42 @@ __device__ __forceinline__ bool ge0(double x) { return !lt0(x); }               
 __device__ __forceinline__ double clamp0(double d) { return dbits(d) <= 0 ? 0.0 : d; }
 
 // ---------------------------------------------------------------------------
-// Natural logarithm (the contract's atanh series): x = 2^e m, m in
-// [sqrt(1/2), sqrt(2)); s = (m-1)/(m+1); log m = 2 s sum_{j<10} s^2j/(2j+1);
-// log x = e LN2_HI + (log m + e LN2_LO), ln 2 split at 40 bits.
+// Natural logarithm, table-driven (P. T. P. Tang, ACM TOMS 16 (1990) 378):
+// x = 2^e m with m in [sqrt(1/2), sqrt(2)]; c_k = 1 + k/128 is the table point
+// nearest m (k from the mantissa bits, integer only); r = m (1/c_k) - 1 in one
+// rounding; log x = e ln2 + T_k + log1p(r), with T_k = -log(1/c_k) and
+// log1p(r) = r + r^2 q(r), q the Taylor terms through r^7/7 (|r| < 2^-7.4).
+// For k = 0, 1/c_k = 1 and r = m - 1 exactly.  ln 2 is split at 40 bits, so
+// e LN2_HI is exact.  The table, {1/c_k, T_k} for k = LOG_KMIN..LOG_KMAX,
+// is built on the host from the atanh series and travels with the problem.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ double tr_log(double x)
+constexpr int LOG_KMIN = -38, LOG_KMAX = 54, LOG_TAB_N = LOG_KMAX - LOG_KMIN + 1;
+
+__device__ __forceinline__ double tr_log(const double* __restrict__ tab, double x)
 {
     const long long b = __double_as_longlong(x);
+    const long long f = b & 0x000FFFFFFFFFFFFFll;
     int e = (int)((b >> 52) & 0x7FF) - 1023;
-    long long mb = (b & 0x000FFFFFFFFFFFFFll) | 0x3FF0000000000000ll;
-    if (mb > 0x3FF6A09E667F3BCDll) {   // m > sqrt(2): halve m (exact) and bump e
+    long long mb = f | 0x3FF0000000000000ll;
+    int k = (int)((f + (1ll << 44)) >> 45);              // m in [1, sqrt 2]: round((m - 1) 128)
+    if (mb > 0x3FF6A09E667F3BCDll) {                     // m > sqrt(2): halve m (exact), bump e
         mb -= 0x0010000000000000ll;
         e += 1;
+        k = (int)((f + (1ll << 45)) >> 46) - 64;         // m/2 in (sqrt(1/2), 1): round((m/2 - 1) 128)
     }
     const double m = __longlong_as_double(mb);
-    const double s = (m - 1.0) / (m + 1.0);
-    const double z = s * s;
-    double p = 1.0 / 19.0;
-    p = __fma_rn(p, z, 1.0 / 17.0);
-    p = __fma_rn(p, z, 1.0 / 15.0);
-    p = __fma_rn(p, z, 1.0 / 13.0);
-    p = __fma_rn(p, z, 1.0 / 11.0);
-    p = __fma_rn(p, z, 1.0 / 9.0);
-    p = __fma_rn(p, z, 1.0 / 7.0);
-    p = __fma_rn(p, z, 1.0 / 5.0);
-    p = __fma_rn(p, z, 1.0 / 3.0);
-    p = __fma_rn(p, z, 1.0);
-    const double r = (s + s) * p;
+    const double2 t = __ldg(reinterpret_cast<const double2*>(tab) + (k - LOG_KMIN));
+    const double r = __fma_rn(m, t.x, -1.0);
+    double q = 1.0 / 7.0;
+    q = __fma_rn(q, r, -1.0 / 6.0);
+    q = __fma_rn(q, r, 1.0 / 5.0);
+    q = __fma_rn(q, r, -0.25);
+    q = __fma_rn(q, r, 1.0 / 3.0);
+    q = __fma_rn(q, r, -0.5);
+    const double p = __fma_rn(q, r * r, r);
     const double de = (double)e;
     return __fma_rn(de, __longlong_as_double(0x3FE62E42FEFA4000ll),
-                    __fma_rn(de, __longlong_as_double((long long)0xBD48432A1B0E2634ull), r));
+                    __fma_rn(de, __longlong_as_double((long long)0xBD48432A1B0E2634ull), t.y + p));
 }
 
 // ---------------------------------------------------------------------------

@@ -104,7 +104,7 @@ def test_log_against_library_log():
             continue
         err = abs(got - ref) / _ulp(ref)
         worst = max(worst, err)
-    # the atanh series keeps the error within a few units in the last place
+    # the table-driven method (table from the atanh series) keeps the error within a few units in the last place
     assert worst <= 4.0, worst
     assert oracle.log(1.0) == 0.0
     assert oracle.log(2.0) == math.log(2.0)
