@@ -124,7 +124,7 @@ def lib():
         L.orc_uniform.restype = C.c_double
         L.orc_log.argtypes = [C.c_double]
         L.orc_log.restype = C.c_double
-        L.orc_iso_dir.argtypes = [C.c_uint64, C.c_uint32, C.c_uint64, C.c_uint32, C.c_double, C.POINTER(C.c_double)]
+        L.orc_iso_dir.argtypes = [C.c_uint64, C.c_uint32, C.c_uint64, C.c_uint32, C.POINTER(C.c_double)]
         L.orc_elastic.argtypes = [C.c_double, C.c_double, C.c_double, C.POINTER(C.c_double), C.POINTER(C.c_double)]
         L.orc_rotate.argtypes = [C.POINTER(C.c_double), C.c_double, C.c_double, C.c_double, C.POINTER(C.c_double)]
         L.orc_cdf_sample.argtypes = [C.POINTER(C.c_double), C.POINTER(C.c_double), C.c_int32, C.c_double]
@@ -325,9 +325,9 @@ def log(x: float) -> float:
     return lib().orc_log(float(x))
 
 
-def iso_dir(seed, tag, hid, n, xi_mu):
+def iso_dir(seed, tag, hid, n):
     d = (C.c_double * 3)()
-    lib().orc_iso_dir(seed, tag, hid, n, xi_mu, d)
+    lib().orc_iso_dir(seed, tag, hid, n, d)
     return np.array(d[:])
 
 

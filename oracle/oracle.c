@@ -89,7 +89,7 @@ static void rng_block(uint64_t seed, uint32_t tag, uint64_t id, uint32_t n, uint
 
 /* Block indices within one event (the contract's fixed assignment). */
 #define BLK_MAIN 0u      /* (distance / source mu, reaction / source energy) */
-#define BLK_ANGLE 1u     /* (scatter mu or CM cosine, unused) */
+#define BLK_ANGLE 1u     /* (CM cosine of an elastic scatter, unused) */
 #define BLK_FISSION 2u   /* (number of fission sites, unused) */
 #define BLK_AZIMUTH 3u   /* 3 + t: azimuth rejection try t, t < 64 */
 #define N_AZIMUTH_TRIES 64u
@@ -189,11 +189,14 @@ double orc_log(double x)
 }
 
 /* ------------------------------------------------------------------------ */
-/* Directions.  Isotropic: mu = 2 xi - 1; azimuth by rejection in the unit   */
-/* square (von Neumann): a = 2 xi - 1, b = 2 xi' - 1, accept 0 < s <= 1 with  */
-/* s = a^2 + b^2; cos phi = (a^2 - b^2)/s, sin phi = 2ab/s (no trig).         */
+/* Directions.  A point of the unit disk by rejection in the unit square     */
+/* (von Neumann): a = 2 xi - 1, b = 2 xi' - 1, accept 0 < s <= 1 with         */
+/* s = a^2 + b^2.  Azimuth: cos phi = (a^2 - b^2)/s, sin phi = 2ab/s (no      */
+/* trig).  Isotropic direction (Marsaglia 1972): (1 - 2s, 2a sqrt(1 - s),     */
+/* 2b sqrt(1 - s)).                                                           */
 /* ------------------------------------------------------------------------ */
-static void azimuth(uint64_t seed, uint32_t tag, uint64_t id, uint32_t n, double *cphi, double *sphi)
+static void disk_point(uint64_t seed, uint32_t tag, uint64_t id, uint32_t n, double *pa, double *pb, double *pa2,
+                       double *pb2, double *ps)
 {
     double a = 1.0, b = 0.0, a2 = 1.0, b2 = 0.0, s = 1.0;
     for (uint32_t t = 0; t < N_AZIMUTH_TRIES; ++t) {
@@ -208,20 +211,26 @@ static void azimuth(uint64_t seed, uint32_t tag, uint64_t id, uint32_t n, double
             break;
         }
     }
+    *pa = a; *pb = b; *pa2 = a2; *pb2 = b2; *ps = s;
+}
+
+static void azimuth(uint64_t seed, uint32_t tag, uint64_t id, uint32_t n, double *cphi, double *sphi)
+{
+    double a, b, a2, b2, s;
+    disk_point(seed, tag, id, n, &a, &b, &a2, &b2, &s);
     double inv_s = 1.0 / s;
     *cphi = (a2 - b2) * inv_s;
     *sphi = (2.0 * (a * b)) * inv_s;
 }
 
-void orc_iso_dir(uint64_t seed, uint32_t tag, uint64_t id, uint32_t n, double xi_mu, double dir[3])
+void orc_iso_dir(uint64_t seed, uint32_t tag, uint64_t id, uint32_t n, double dir[3])
 {
-    double mu = 2.0 * xi_mu - 1.0;
-    double cphi, sphi;
-    azimuth(seed, tag, id, n, &cphi, &sphi);
-    double st = sqrt(fma(-mu, mu, 1.0));
-    dir[0] = mu;
-    dir[1] = st * cphi;
-    dir[2] = st * sphi;
+    double a, b, a2, b2, s;
+    disk_point(seed, tag, id, n, &a, &b, &a2, &b2, &s);
+    double t = 2.0 * sqrt(1.0 - s);
+    dir[0] = 1.0 - 2.0 * s;
+    dir[1] = a * t;
+    dir[2] = b * t;
 }
 
 /* Rotate direction `d` by polar cosine mu and azimuth (cphi, sphi): the
@@ -694,7 +703,7 @@ static int source_particle(ctx *C, particle *p, uint64_t id, const double *site_
     rng_block(C->seed, C->tag, id, 0, BLK_MAIN, xi0);
     /* direction first (location ties on faces use its sign) */
     if (site_pos || P->src_kind != 0 || P->src_iso) {
-        orc_iso_dir(C->seed, C->tag, id, 0, xi0[0], p->d);
+        orc_iso_dir(C->seed, C->tag, id, 0, p->d);
     } else {
         p->d[0] = P->src_dir[0]; p->d[1] = P->src_dir[1]; p->d[2] = P->src_dir[2];
     }
@@ -798,9 +807,7 @@ static void collide(ctx *C, particle *p, int m, const xsval *X, double xi_react)
             C->rec[C->rec_n - 1].h = gp;
         }
         p->g = gp;
-        double xa[2];
-        rng_block(C->seed, C->tag, p->id, p->n, BLK_ANGLE, xa);
-        orc_iso_dir(C->seed, C->tag, p->id, p->n, xa[0], p->d);
+        orc_iso_dir(C->seed, C->tag, p->id, p->n, p->d);
         C->events_by_type[ORC_SCATTER]++;
         return;
     }

@@ -127,7 +127,7 @@ int orc_power_iteration(const orc_problem *P, orc_eig *o);
 void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);
 double orc_uniform(uint32_t lo, uint32_t hi);
 double orc_log(double x);
-void orc_iso_dir(uint64_t seed, uint32_t tag, uint64_t id, uint32_t n, double xi_mu, double dir[3]);
+void orc_iso_dir(uint64_t seed, uint32_t tag, uint64_t id, uint32_t n, double dir[3]);
 void orc_elastic(double A, double E, double mu_cm, double *E_out, double *mu_lab);
 void orc_rotate(const double dir[3], double mu, double cphi, double sphi, double out[3]);
 double orc_cdf_sample(const double *e, const double *p, int32_t n, double xi);

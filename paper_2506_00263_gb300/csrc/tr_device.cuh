@@ -48,7 +48,7 @@ static __device__ unsigned long long g_lane_prof[64];
 
 // Random-block assignment within one event (counter word 1).
 constexpr uint32_t BLK_MAIN = 0u;      // (distance | source cosine, reaction | source group/energy)
-constexpr uint32_t BLK_ANGLE = 1u;     // (scatter cosine / CM cosine, -)
+constexpr uint32_t BLK_ANGLE = 1u;     // (CM cosine of an elastic scatter, -)
 constexpr uint32_t BLK_FISSION = 2u;   // (fission-site count, -)
 constexpr uint32_t BLK_AZIMUTH = 3u;   // 3 + t, t < 64: azimuth rejection tries
 constexpr uint32_t N_AZIMUTH = 64u;
@@ -291,8 +291,9 @@ __device__ __forceinline__ double tr_log(const double* __restrict__ tab, double 
 }
 
 // ---------------------------------------------------------------------------
-// Directions: azimuth by rejection in the unit square (no trig), isotropic
-// direction, lab rotation, target-at-rest elastic kinematics.
+// Directions: a point of the unit disk by rejection in the unit square (no
+// trig), giving the azimuth and the isotropic direction; lab rotation,
+// target-at-rest elastic kinematics.
 // ---------------------------------------------------------------------------
 // One rejection try t: the point (a, b) and whether 0 < a^2 + b^2 <= 1.
 __device__ __forceinline__ bool azimuth_try(const Stream& S, uint32_t n, uint32_t t, double& a, double& b, double& a2,
@@ -307,15 +308,17 @@ __device__ __forceinline__ bool azimuth_try(const Stream& S, uint32_t n, uint32_
     return dbits(s) <= dbits(1.0) && gt0(s);   // 0 < s <= 1 (s >= +0)
 }
 
-// sm: the lanes of this warp that call azimuth together (a mask every one of
-// them passes, computed by a ballot), regrouped after the rejection loop; 0 =
-// no regrouping.
-__device__ __forceinline__ void azimuth(const Stream& S, uint32_t n, double& cphi, double& sphi, unsigned sm = 0u)
+// The first accepted rejection try: (a, b) uniform in the unit disk, s =
+// a^2 + b^2.  sm: the lanes of this warp that call it together (a mask every
+// one of them passes, computed by a ballot), regrouped after the rejection
+// loop; 0 = no regrouping.
+__device__ __forceinline__ void disk_point(const Stream& S, uint32_t n, double& a, double& b, double& a2, double& b2,
+                                           double& s, unsigned sm)
 {
-    // the first accepted try; tries 0 and 1 run unconditionally in every lane
-    // (both accepted: take try 0), the rare remainder loops
+    // tries 0 and 1 run unconditionally in every lane (both accepted: take
+    // try 0), the rare remainder loops
     TR_LANES(18);
-    double a, b, a2, b2, s, a1, b1, a21, b21, s1;
+    double a1, b1, a21, b21, s1;
     bool ok = azimuth_try(S, n, 0u, a, b, a2, b2, s);
     const bool ok1 = azimuth_try(S, n, 1u, a1, b1, a21, b21, s1);
     if (!ok && ok1) {
@@ -331,6 +334,13 @@ __device__ __forceinline__ void azimuth(const Stream& S, uint32_t n, double& cph
     }
     if (sm) __syncwarp(sm);
     TR_LANES(19);
+}
+
+// Azimuth (cos phi, sin phi) = ((a^2 - b^2)/s, 2ab/s) from the disk point.
+__device__ __forceinline__ void azimuth(const Stream& S, uint32_t n, double& cphi, double& sphi, unsigned sm = 0u)
+{
+    double a, b, a2, b2, s;
+    disk_point(S, n, a, b, a2, b2, s, sm);
     const double inv_s = __drcp_rn(s);
     cphi = (a2 - b2) * inv_s;
     sphi = (2.0 * (a * b)) * inv_s;
@@ -348,15 +358,17 @@ __device__ __forceinline__ void set_reciprocals(Particle& p)
     p.ia = gt0(a) ? __drcp_rn(a) : 0.0;
 }
 
-__device__ __forceinline__ void iso_dir(const Stream& S, uint32_t n, double xi_mu, Particle& p, unsigned sm = 0u)
+// Isotropic direction (Marsaglia, Ann. Math. Stat. 43 (1972) 645): with the
+// disk point (a, b), s = a^2 + b^2, (1 - 2s, 2a sqrt(1 - s), 2b sqrt(1 - s))
+// is uniform on the unit sphere; no division and one square root.
+__device__ __forceinline__ void iso_dir(const Stream& S, uint32_t n, Particle& p, unsigned sm = 0u)
 {
-    const double mu = __fma_rn(2.0, xi_mu, -1.0);   // 2 xi is exact: the same value as 2.0 * xi - 1.0
-    double cphi, sphi;
-    azimuth(S, n, cphi, sphi, sm);
-    const double st = sqrt(__fma_rn(-mu, mu, 1.0));
-    p.u = mu;
-    p.v = st * cphi;
-    p.w = st * sphi;
+    double a, b, a2, b2, s;
+    disk_point(S, n, a, b, a2, b2, s, sm);
+    const double t = 2.0 * sqrt(1.0 - s);
+    p.u = __fma_rn(-2.0, s, 1.0);   // 2 s is exact: the same value as 1.0 - 2.0 * s
+    p.v = a * t;
+    p.w = b * t;
     set_reciprocals(p);
 }
 

@@ -165,7 +165,7 @@ __device__ __forceinline__ bool source_particle(const DevProblem& P, const RunPa
     TR_LANES(23);
     const Stream S = make_stream(R, id);
     const uint4 b0 = S.block(0u, BLK_MAIN);
-    const double xi_mu = u01(b0.x, b0.y), xi_ge = u01(b0.z, b0.w);
+    const double xi_ge = u01(b0.z, b0.w);
     p.id = id;
     p.n = 1u;
     p.nsites = 0u;
@@ -175,7 +175,7 @@ __device__ __forceinline__ bool source_particle(const DevProblem& P, const RunPa
     p.E = 0.0;
     p.t = 0.0;
     if (site != nullptr || P.src_kind != 0 || P.src_iso) {
-        iso_dir(S, 0u, xi_mu, p);
+        iso_dir(S, 0u, p);
     } else {
         p.u = P.src_dir[0];
         p.v = P.src_dir[1];
@@ -419,7 +419,7 @@ __device__ __forceinline__ int collide_event(const DevProblem& P, const RunParam
         if (gp < 0) return EV_ABSORB;
         TR_LANES(17);
         p.g = gp;
-        iso_dir(S, p.n, S.first(p.n, BLK_ANGLE), p, sm);
+        iso_dir(S, p.n, p, sm);
         return EV_SCATTER;
     }
     // continuous energy: repeat the lookup terms in order and pick the first
