@@ -344,7 +344,9 @@ __device__ __forceinline__ void flush_lane(Acc& acc, const Tallies& T)
 }
 
 // DEC: the task decomposition (DEC_MONO, DEC_SPLIT or DEC_LOOKUP).
-template <bool CE, int DEC, bool BATCHED = false>
+// PRE: make_work loads pre-sampled sources (A.pre) instead of sampling them,
+// so the sampling code is not part of this kernel.
+template <bool CE, int DEC, bool BATCHED = false, bool PRE = false>
 __global__ void __launch_bounds__(256, TR_ASYNC_MIN_BLOCKS) k_async(DevProblem P, RunParams R, AsyncArgs A, Tallies T, ErrorWord* err)
 {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -595,8 +597,8 @@ __global__ void __launch_bounds__(256, TR_ASYNC_MIN_BLOCKS) k_async(DevProblem P
                     }
                     acc.ev[EV_SOURCE] += 1u;
                 } else {
-                    live = A.use_pre ? load_presampled<CE>(A.pre, id, p)
-                                     : source_particle<CE>(P, R, (unsigned)id, p, A.use_src ? &A.src : nullptr, id);
+                    if constexpr (PRE) live = load_presampled<CE>(A.pre, id, p);
+                    else live = source_particle<CE>(P, R, (unsigned)id, p, A.use_src ? &A.src : nullptr, id);
                     acc.ev[EV_SOURCE] += 1u;
                 }
                 if (!live) fail(err, ERR_INVALID, 5);
@@ -702,7 +704,7 @@ __global__ void __launch_bounds__(256, TR_ASYNC_MIN_BLOCKS) k_async(DevProblem P
                             // TR_PRE_REFILL lanes are idle
                             const unsigned dead = __ballot_sync(em, !live);
                             const int nd = __popc(dead);
-                            if ((A.use_pre ? nd >= TR_PRE_REFILL : 4 * nd >= __popc(em)) || dead == em) {
+                            if ((PRE ? nd >= TR_PRE_REFILL : 4 * nd >= __popc(em)) || dead == em) {
                                 unsigned long long first = 0;
                                 if (lane == leader) first = atomicAdd(&ctl->src_cursor, (unsigned long long)__popc(dead));
                                 first = __shfl_sync(em, first, leader);
@@ -710,9 +712,9 @@ __global__ void __launch_bounds__(256, TR_ASYNC_MIN_BLOCKS) k_async(DevProblem P
                                 if (!live) {
                                     const unsigned long long gid = first + __popc(dead & ((1u << lane) - 1u));
                                     if (gid < R.n_hist) {
-                                        live = A.use_pre ? load_presampled<CE>(A.pre, gid, p)
-                                                         : source_particle<CE>(P, R, (unsigned)gid, p,
-                                                                               A.use_src ? &A.src : nullptr, gid);
+                                        if constexpr (PRE) live = load_presampled<CE>(A.pre, gid, p);
+                                        else live = source_particle<CE>(P, R, (unsigned)gid, p,
+                                                                        A.use_src ? &A.src : nullptr, gid);
                                         if (!live) fail(err, ERR_INVALID, 5);
                                         acc.ev[EV_SOURCE] += 1u;
                                         pend_coll = false;
@@ -836,24 +838,28 @@ __global__ void __launch_bounds__(256, TR_ASYNC_MIN_BLOCKS) k_async(DevProblem P
 
 namespace tr {
 
-template <bool CE, int DEC, bool BATCHED = false>
+template <bool CE, int DEC, bool BATCHED = false, bool PRE = false>
 static cudaError_t prepare_async(size_t smem)
 {
-    return cudaFuncSetAttribute(k_async<CE, DEC, BATCHED>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    return cudaFuncSetAttribute(k_async<CE, DEC, BATCHED, PRE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
 }
 
-template <bool CE, int DEC, bool BATCHED = false>
+template <bool CE, int DEC, bool BATCHED = false, bool PRE = false>
 static int occupancy_async(size_t smem)
 {
     int nb = 0;
-    if (prepare_async<CE, DEC, BATCHED>(smem) != cudaSuccess) return 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_async<CE, DEC, BATCHED>, 256, smem) != cudaSuccess) return 0;
+    if (prepare_async<CE, DEC, BATCHED, PRE>(smem) != cudaSuccess) return 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_async<CE, DEC, BATCHED, PRE>, 256, smem) != cudaSuccess)
+        return 0;
     return nb;
 }
 
-int async_max_blocks_per_sm(const DevProblem& P, int dec, int stash_slots)
+int async_max_blocks_per_sm(const DevProblem& P, int dec, int stash_slots, bool pre)
 {
     const size_t smem = stash_bytes(stash_slots, dec == DEC_LOOKUP);
+    if (pre && dec == DEC_MONO)
+        return P.kind == 1 ? occupancy_async<true, DEC_MONO, false, true>(smem)
+                           : occupancy_async<false, DEC_MONO, false, true>(smem);
     if (P.kind == 1) {
         if (dec == DEC_STREAM) return occupancy_async<true, DEC_STREAM>(smem);
         if (dec == DEC_LOOKUP) return occupancy_async<true, DEC_LOOKUP>(smem);
@@ -864,13 +870,13 @@ int async_max_blocks_per_sm(const DevProblem& P, int dec, int stash_slots)
     return dec == DEC_SPLIT ? occupancy_async<false, DEC_SPLIT>(smem) : occupancy_async<false, DEC_MONO>(smem);
 }
 
-template <bool CE, int DEC, bool BATCHED = false>
+template <bool CE, int DEC, bool BATCHED = false, bool PRE = false>
 static cudaError_t launch_async_t(const DevProblem& P, const RunParams& R, const AsyncArgs& A, const Tallies& T,
                                   ErrorWord* err, int blocks, cudaStream_t st, size_t smem)
 {
-    const cudaError_t e = prepare_async<CE, DEC, BATCHED>(smem);
+    const cudaError_t e = prepare_async<CE, DEC, BATCHED, PRE>(smem);
     if (e != cudaSuccess) return e;
-    k_async<CE, DEC, BATCHED><<<blocks, 256, smem, st>>>(P, R, A, T, err);
+    k_async<CE, DEC, BATCHED, PRE><<<blocks, 256, smem, st>>>(P, R, A, T, err);
     return cudaGetLastError();
 }
 
@@ -880,6 +886,9 @@ cudaError_t launch_async(const DevProblem& P, const RunParams& R, const AsyncArg
     const size_t smem = stash_bytes(A.stash_slots, A.dec == DEC_LOOKUP);
     if (smem_bytes_out) *smem_bytes_out = (int)smem;
     count_launches(1);
+    if (A.use_pre && A.dec == DEC_MONO)
+        return P.kind == 1 ? launch_async_t<true, DEC_MONO, false, true>(P, R, A, T, err, blocks, st, smem)
+                           : launch_async_t<false, DEC_MONO, false, true>(P, R, A, T, err, blocks, st, smem);
     if (P.kind == 1) {
         if (A.dec == DEC_STREAM) return launch_async_t<true, DEC_STREAM>(P, R, A, T, err, blocks, st, smem);
         if (A.dec == DEC_LOOKUP) return launch_async_t<true, DEC_LOOKUP>(P, R, A, T, err, blocks, st, smem);
@@ -892,7 +901,6 @@ cudaError_t launch_async(const DevProblem& P, const RunParams& R, const AsyncArg
                               : launch_async_t<false, DEC_MONO>(P, R, A, T, err, blocks, st, smem);
 }
 
-// Batched launches (multigroup; monolithic or decomposed).
 cudaError_t launch_presample(const DevProblem& P, const RunParams& R, const AsyncArgs& A, int blocks, cudaStream_t st)
 {
     count_launches(1);
@@ -901,6 +909,7 @@ cudaError_t launch_presample(const DevProblem& P, const RunParams& R, const Asyn
     return cudaGetLastError();
 }
 
+// Batched launches (multigroup; monolithic or decomposed).
 int async_batched_max_blocks_per_sm(int dec, int stash_slots)
 {
     const size_t smem = stash_bytes(stash_slots);

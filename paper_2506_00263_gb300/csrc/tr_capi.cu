@@ -724,7 +724,7 @@ static tr_status transport(tr_problem* pr, const tr_run_opts* o, RunParams R, co
     std::memset(hc.free_q, 0xFF, sizeof(hc.free_q));
     std::memset(hc.full_q, 0xFF, sizeof(hc.full_q));
     TR_CUDA(cudaMemcpyAsync(A.ctl, &hc, sizeof(hc), cudaMemcpyHostToDevice, st));
-    int maxb = async_max_blocks_per_sm(P, A.dec, S);
+    int maxb = async_max_blocks_per_sm(P, A.dec, S, A.use_pre != 0);
     if (maxb < 1) return set_err(TR_ERR_INVALID, "stash does not fit in shared memory");
     const int bps = o->blocks_per_sm > 0 ? std::min(o->blocks_per_sm, maxb) : maxb;
     int smem = 0;

@@ -55,7 +55,7 @@ struct AsyncArgs {
 
 cudaError_t launch_async(const DevProblem& P, const RunParams& R, const AsyncArgs& A, const Tallies& T, ErrorWord* err,
                          int blocks, cudaStream_t st, int* smem_bytes_out);
-int async_max_blocks_per_sm(const DevProblem& P, int dec, int stash_slots);
+int async_max_blocks_per_sm(const DevProblem& P, int dec, int stash_slots, bool pre = false);
 // Samples the source particles of histories [0, R.n_hist) into A.pre.
 cudaError_t launch_presample(const DevProblem& P, const RunParams& R, const AsyncArgs& A, int blocks, cudaStream_t st);
 cudaError_t launch_async_batched(const DevProblem& P0, const RunParams& R, const AsyncArgs& A, ErrorWord* err,
