@@ -224,7 +224,8 @@ def run_ours(args):
         ev_all, hist_all = float(ev_tot), float(hist_tot)
     value = ev_all / t
 
-    # ---- roofline of the dominant kernel (the transport loop) ----
+    # ---- roofline of the dominant kernel (the transport loop, with the source
+    # pre-sampling that feeds it: both run inside the timed launch bracket) ----
     hbm, fmax, peak_kind = _peaks()
     avg_launch = kern_s / max(kern_launches, 1)
     ev_per_launch = ev_tot / max(kern_launches, 1)
@@ -234,7 +235,7 @@ def run_ours(args):
         ach = fp64_ops_per_event * ev_per_launch / avg_launch / 1e12
         traffic = TRAFFIC_PER_LAUNCH.get((args.scheme, args.decomp, opts.remap_every, args.n_per_batch))
         roof = {"bound": "alu", "achieved": ach, "peak": fp64_peak, "unit": "TFLOP/s", "frac": ach / fp64_peak,
-                "traffic": traffic, "what": "FP64 pipe (add/mul/fma) of the transport kernel, "
+                "traffic": traffic, "what": "FP64 pipe (add/mul/fma) of one batch's transport (source pre-sampling + transport loop), "
                                          f"{fp64_ops_per_event:.0f} FP64 ops/event",
                 "peak_source": f"derived: {N_SM} SMs x {FP64_OPS_PER_CLK_PER_SM:g} FP64/clk x {fmax:.0f} MHz"}
     else:
@@ -746,15 +747,17 @@ def run_lattice_sweep(args):
 
 # FP64 thread-operations (dadd + dmul + dfma, divisions and square roots
 # included as executed) per transport event on the lattice workload, from an
-# ncu capture of the transport kernel
+# ncu capture of one power-iteration step of three batches: the source
+# pre-sampling and transport kernels together
 # (sm__sass_thread_inst_executed_ops_dadd_dmul_dfma_pred_on.sum / events).
 # The arithmetic per event is the same in every scheme (the decomposed one
 # only repeats table loads).
-FP64_OPS_LATTICE = 82.8
-# DRAM bytes (read + write) of one transport launch (one 1e6-history lattice
-# batch, asynchronous monolithic scheme, 512 events between remaps), from one ncu
-# capture of the current kernel: dram__bytes_read.sum + dram__bytes_write.sum.
-TRAFFIC_PER_LAUNCH = {("async", "mono", 512, 1_000_000): 64.90e6}
+FP64_OPS_LATTICE = 64.7
+# DRAM bytes (read + write) of one batch's transport (source pre-sampling and
+# transport kernels; one 1e6-history lattice batch sourced from the fission
+# bank, asynchronous monolithic scheme, 512 events between remaps), from one
+# ncu capture of the current kernels: dram__bytes_read.sum + dram__bytes_write.sum.
+TRAFFIC_PER_LAUNCH = {("async", "mono", 512, 1_000_000): 220.1e6}
 FP64_OPS_PER_EVENT = {(s, d): FP64_OPS_LATTICE for s in ("async", "stack") for d in ("mono", "split")}
 
 
