@@ -17,7 +17,10 @@
 // passes keep one history per lane (its running F in registers) and refill a
 // lane from a global cursor the moment its history ends; collisions wait
 // until many lanes have one and then run together; the derivative arrays are
-// accumulated per block in shared memory when they fit.
+// accumulated per block in shared memory when they fit, with the terms that
+// add one value to a whole scattering row d/dSs[m][g][*] summed once per row
+// and spread over the row when the block flushes.  The source particles come
+// pre-sampled (one buffer serves both passes) when a buffer is given.
 #include <algorithm>
 
 #include "tr_events.cuh"
@@ -62,22 +65,30 @@ struct AdjArgs {
     double* d_nusigf;       // [m][g]
     unsigned long long* cursor;   // next history to start (zeroed before each pass)
     int use_smem;
+    SoA pre;                // pre-sampled source particles (use_pre)
+    int use_pre;
 };
 
+#ifndef TR_ADJ_BLOCKS
+#define TR_ADJ_BLOCKS 2   // resident blocks per SM the register allocation targets (and the grid uses)
+#endif
+
 template <bool PASS2>
-__global__ void __launch_bounds__(256) k_adjoint(DevProblem P, RunParams R, AdjArgs A, ErrorWord* err)
+__global__ void __launch_bounds__(256, TR_ADJ_BLOCKS) k_adjoint(DevProblem P, RunParams R, AdjArgs A, ErrorWord* err)
 {
     extern __shared__ double sgrad[];
     const int G = P.G, MG = P.n_mat * P.G, MGG = MG * P.G;
     double* gst = A.d_sigt;
     double* gss = A.d_sigs;
     double* gnf = A.d_nusigf;
+    double* grow = nullptr;   // shared memory only: one value added to every h of row [m][g]
     if (PASS2 && A.use_smem) {
-        for (int i = threadIdx.x; i < 2 * MG + MGG; i += blockDim.x) sgrad[i] = 0.0;
+        for (int i = threadIdx.x; i < 3 * MG + MGG; i += blockDim.x) sgrad[i] = 0.0;
         __syncthreads();
         gst = sgrad;
         gss = sgrad + MG;
         gnf = sgrad + MG + MGG;
+        grow = sgrad + 2 * MG + MGG;
     }
     Acc acc;
     acc.zero();
@@ -103,7 +114,8 @@ __global__ void __launch_bounds__(256) k_adjoint(DevProblem P, RunParams R, AdjA
                 const unsigned long long mine = base + __popc(need & ((1u << lane) - 1u));
                 if (mine < R.n_hist) {
                     id = mine;
-                    alive = source_particle<false>(P, R, (unsigned)id, p, nullptr, 0);
+                    alive = A.use_pre ? load_presampled<false>(A.pre, id, p)
+                                      : source_particle<false>(P, R, (unsigned)id, p, nullptr, 0);
                     if (!alive) atomicCAS(&err->code, 0, ERR_INVALID);
                     F = PASS2 ? A.F[id] : 0.0;
                     before = 0.0;
@@ -139,7 +151,8 @@ __global__ void __launch_bounds__(256) k_adjoint(DevProblem P, RunParams R, AdjA
                     } else {
                         const double inv_sa = __drcp_rn(__ldg(P.sig_a + mg));
                         atomicAdd(gst + mg, (inv_sa - X.inv_st) * after);
-                        for (int h = 0; h < G; ++h) atomicAdd(gss + mg * G + h, (-inv_sa) * after);
+                        if (grow) atomicAdd(grow + mg, (-inv_sa) * after);
+                        else for (int h = 0; h < G; ++h) atomicAdd(gss + mg * G + h, (-inv_sa) * after);
                     }
                 }
                 pend = false;
@@ -165,7 +178,8 @@ __global__ void __launch_bounds__(256) k_adjoint(DevProblem P, RunParams R, AdjA
                     if (A.g_scal) {
                         const double ga = __ldg(A.g_scal + 1) * sink.len;
                         atomicAdd(gst + mg, ga);
-                        for (int h = 0; h < G; ++h) atomicAdd(gss + mg * G + h, -ga);
+                        if (grow) atomicAdd(grow + mg, -ga);
+                        else for (int h = 0; h < G; ++h) atomicAdd(gss + mg * G + h, -ga);
                         atomicAdd(gnf + mg, __ldg(A.g_scal + 2) * sink.len);
                     }
                     before = before + sink.f;
@@ -182,14 +196,16 @@ __global__ void __launch_bounds__(256) k_adjoint(DevProblem P, RunParams R, AdjA
             if (sgrad[i] != 0.0) atomicAdd(A.d_sigt + i, sgrad[i]);
             if (sgrad[MG + MGG + i] != 0.0) atomicAdd(A.d_nusigf + i, sgrad[MG + MGG + i]);
         }
-        for (int i = threadIdx.x; i < MGG; i += blockDim.x)
-            if (sgrad[MG + i] != 0.0) atomicAdd(A.d_sigs + i, sgrad[MG + i]);
+        for (int i = threadIdx.x; i < MGG; i += blockDim.x) {
+            const double v = sgrad[MG + i] + grow[i / G];
+            if (v != 0.0) atomicAdd(A.d_sigs + i, v);
+        }
     }
 }
 
 cudaError_t launch_adjoint(const DevProblem& P, const RunParams& R, const double* g_mesh, const double* g_scal,
                            double* F, double* d_sigt, double* d_sigs, double* d_nusigf, ErrorWord* err, int sms,
-                           unsigned long long* cursors, cudaStream_t st)
+                           unsigned long long* cursors, const SoA* pre, cudaStream_t st)
 {
     cudaError_t e0 = cudaMemsetAsync(cursors, 0, 2 * sizeof(unsigned long long), st);
     if (e0 != cudaSuccess) return e0;
@@ -200,7 +216,9 @@ cudaError_t launch_adjoint(const DevProblem& P, const RunParams& R, const double
     A.d_sigt = d_sigt;
     A.d_sigs = d_sigs;
     A.d_nusigf = d_nusigf;
-    const size_t n = (size_t)P.n_mat * P.G * (P.G + 2);
+    A.use_pre = pre != nullptr;
+    if (pre) A.pre = *pre;
+    const size_t n = (size_t)P.n_mat * P.G * (P.G + 3);
     const size_t smem = n * sizeof(double);
     A.use_smem = smem <= 96 * 1024 ? 1 : 0;
     if (A.use_smem) {
@@ -208,7 +226,7 @@ cudaError_t launch_adjoint(const DevProblem& P, const RunParams& R, const double
                                                    (int)smem);
         if (e != cudaSuccess) return e;
     }
-    const int blocks = sms * 4;
+    const int blocks = sms * TR_ADJ_BLOCKS;
     count_launches(2);
     A.cursor = cursors;
     k_adjoint<false><<<blocks, 256, 0, st>>>(P, R, A, err);

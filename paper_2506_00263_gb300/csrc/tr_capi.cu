@@ -1170,8 +1170,15 @@ extern "C" tr_status tr_sensitivities(tr_problem* pr, const tr_run_opts* o, cons
     R.want_log = 0;
     unsigned long long* cursors = (unsigned long long*)workspace(pr, "adj_cursors", 16);
     if (!cursors) return set_err(TR_ERR_NOMEM, "workspace allocation failed");
+    // both passes start the same histories: sample their sources once
+    AsyncArgs S{};
+    const bool pre = o->n_histories <= PRESAMPLE_MAX_HIST;
+    if (pre) {
+        if (!carve_soa(pr, "presample", o->n_histories, S.pre)) return set_err(TR_ERR_NOMEM, "source buffer allocation failed");
+        TR_CUDA(launch_presample(P, R, S, pr->sms * 8, st));
+    }
     TR_CUDA(launch_adjoint(P, R, d_grad_mesh, d_grad_scalars, F, d_sigt, d_sigs, d_nusigf, pr->err, pr->sms, cursors,
-                           st));
+                           pre ? &S.pre : nullptr, st));
     s = check_err(pr);
     if (s != TR_OK) return s;
     const double inv = 1.0 / (double)o->n_histories;

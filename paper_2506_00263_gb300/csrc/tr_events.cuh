@@ -676,6 +676,26 @@ __device__ __forceinline__ void store_particle(const SoA& s, unsigned long long 
     s.prob[i] = p.prob;
 }
 
+// The particle k_presample left for history i, in the state source_particle
+// leaves (n = 1, nothing banked or pending, t = 0); false if sampling failed.
+template <bool CE>
+__device__ __forceinline__ bool load_presampled(const SoA& s, unsigned long long i, Particle& p)
+{
+    p.x = s.x[i]; p.y = s.y[i]; p.z = s.z[i];
+    p.u = s.u[i]; p.v = s.v[i]; p.w = s.w[i];
+    p.iu = s.iu[i]; p.iv = s.iv[i]; p.iw = s.iw[i]; p.ia = s.ia[i];
+    p.E = CE ? s.E[i] : 0.0;
+    p.g = CE ? 0 : s.g[i];
+    p.cell = s.cell[i];
+    p.id = (unsigned)i;
+    p.n = 1u;
+    p.nsites = 0u;
+    p.pend = 0u;
+    p.prob = 0u;
+    p.t = 0.0;
+    return s.id[i] == (unsigned)i;
+}
+
 // Next queue of a live particle after an event: a step leads to collision or
 // surface crossing; those lead back to a step.
 __device__ __forceinline__ int next_queue_after_step(const Particle& p)

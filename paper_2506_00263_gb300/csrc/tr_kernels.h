@@ -71,7 +71,7 @@ cudaError_t launch_scale_jobs(const ScaleJob* jobs, int n_jobs, cudaStream_t st)
 
 cudaError_t launch_adjoint(const DevProblem& P, const RunParams& R, const double* g_mesh, const double* g_scal,
                            double* F, double* d_sigt, double* d_sigs, double* d_nusigf, ErrorWord* err, int sms,
-                           unsigned long long* cursors, cudaStream_t st);
+                           unsigned long long* cursors, const SoA* pre, cudaStream_t st);
 cudaError_t launch_scan(const unsigned* in, unsigned long long n, unsigned long long* tile_sum, unsigned long long* out,
                         unsigned long long* total, cudaStream_t st);
 cudaError_t launch_bank_order(const Bank& in, unsigned long long m, const unsigned long long* offset, const Bank& out,
