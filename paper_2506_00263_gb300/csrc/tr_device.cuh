@@ -456,8 +456,19 @@ __device__ __forceinline__ void locate(const DevProblem& P, Particle& p)
 // ---------------------------------------------------------------------------
 // Cross sections
 // ---------------------------------------------------------------------------
+// Macroscopic terms of a continuous-energy lookup, kept for the collision
+// that follows in the same event, so that it selects its (nuclide, reaction)
+// without repeating the union-grid search and the interpolations.
+constexpr int CE_KEEP_NUC = 4;
+struct CEKeep {
+    int n;                             // present nuclides kept, or -1 (more than CE_KEEP_NUC: recompute)
+    int nuc[CE_KEEP_NUC];              // their indices, in order
+    double mac[3 * CE_KEEP_NUC];       // N (s0 + f (s1 - s0)) per kept nuclide and reaction
+};
+
 struct XS {
     double st, inv_st, sa, nsf;
+    CEKeep* keep = nullptr;            // continuous energy: where the lookup leaves its terms, if anywhere
 };
 
 __device__ __forceinline__ void xs_mg(const DevProblem& P, int m, int g, XS& X)
@@ -500,6 +511,7 @@ __device__ __forceinline__ void xs_ce(const DevProblem& P, int m, double E, XS& 
 {
     const int u = union_index(P, E);
     double cum = 0.0, sa = 0.0;
+    int kept = 0;
     for (int n = 0; n < P.n_nuc; ++n) {
         const double N = __ldg(P.dens + m * P.n_nuc + n);
         if (!(N > 0.0)) continue;
@@ -510,10 +522,14 @@ __device__ __forceinline__ void xs_ce(const DevProblem& P, int m, double E, XS& 
             const double s0 = __ldg(P.nuc_sig + 3 * (long long)r0 + r);
             const double s1 = __ldg(P.nuc_sig + 3 * (long long)(r0 + 1) + r);
             const double mac = N * (s0 + f * (s1 - s0));
+            if (X.keep && kept < CE_KEEP_NUC) X.keep->mac[3 * kept + r] = mac;
             cum = cum + mac;
             if (r > 0) sa = sa + mac;
         }
+        if (X.keep && kept < CE_KEEP_NUC) X.keep->nuc[kept] = n;
+        ++kept;
     }
+    if (X.keep) X.keep->n = kept <= CE_KEEP_NUC ? kept : -1;
     X.st = cum;
     X.inv_st = 1.0 / cum;
     X.sa = sa;

@@ -422,32 +422,53 @@ __device__ __forceinline__ int collide_event(const DevProblem& P, const RunParam
         iso_dir(S, p.n, p, sm);
         return EV_SCATTER;
     }
-    // continuous energy: repeat the lookup terms in order and pick the first
-    // (nuclide, reaction) with xi * sigma_t below the running sum; if none
-    // (rounding), the last term with a positive value.  Nuclides absent from
-    // the material (density <= 0) add nothing.
+    // continuous energy: the lookup terms in order, and the first (nuclide,
+    // reaction) with xi * sigma_t below the running sum; if none (rounding),
+    // the last term with a positive value.  Nuclides absent from the material
+    // (density <= 0) add nothing.  Terms the step's lookup kept are the same
+    // values; otherwise they are computed again.
     const double t = xi_react * X.st;
-    const int u = union_index(P, p.E);
-    if (cm) __syncwarp(cm);
     double cum = 0.0;
     int sel_n = -1, sel_r = -1, last_n = -1, last_r = -1;
-    for (int n = 0; n < P.n_nuc; ++n) {
-        const double N = __ldg(P.dens + m * P.n_nuc + n);
-        const bool use = N > 0.0;
-        const int r0 = __ldg(P.uptr + (long long)u * P.n_nuc + n);
-        const double f = (p.E - __ldg(P.nuc_e + r0)) * __ldg(P.nuc_inv_de + r0);
-        for (int r = 0; r < 3; ++r) {
-            const double s0 = __ldg(P.nuc_sig + 3 * (long long)r0 + r);
-            const double s1 = __ldg(P.nuc_sig + 3 * (long long)(r0 + 1) + r);
-            const double mac = N * (s0 + f * (s1 - s0));
-            const double c2 = use ? cum + mac : cum;
-            const bool pos = use && mac > 0.0;
-            last_n = pos ? n : last_n;
-            last_r = pos ? r : last_r;
-            const bool take = use && sel_n < 0 && t < c2;
-            sel_n = take ? n : sel_n;
-            sel_r = take ? r : sel_r;
+    if (X.keep && X.keep->n >= 0) {
+        if (cm) __syncwarp(cm);
+        int sel = -1, last = -1;
+        for (int k = 0; k < 3 * X.keep->n; ++k) {
+            const double mac = X.keep->mac[k];
+            const double c2 = cum + mac;
+            last = mac > 0.0 ? k : last;
+            sel = (sel < 0 && t < c2) ? k : sel;
             cum = c2;
+        }
+        if (sel >= 0) {
+            sel_n = X.keep->nuc[sel / 3];
+            sel_r = sel % 3;
+        }
+        if (last >= 0) {
+            last_n = X.keep->nuc[last / 3];
+            last_r = last % 3;
+        }
+    } else {
+        const int u = union_index(P, p.E);
+        if (cm) __syncwarp(cm);
+        for (int n = 0; n < P.n_nuc; ++n) {
+            const double N = __ldg(P.dens + m * P.n_nuc + n);
+            const bool use = N > 0.0;
+            const int r0 = __ldg(P.uptr + (long long)u * P.n_nuc + n);
+            const double f = (p.E - __ldg(P.nuc_e + r0)) * __ldg(P.nuc_inv_de + r0);
+            for (int r = 0; r < 3; ++r) {
+                const double s0 = __ldg(P.nuc_sig + 3 * (long long)r0 + r);
+                const double s1 = __ldg(P.nuc_sig + 3 * (long long)(r0 + 1) + r);
+                const double mac = N * (s0 + f * (s1 - s0));
+                const double c2 = use ? cum + mac : cum;
+                const bool pos = use && mac > 0.0;
+                last_n = pos ? n : last_n;
+                last_r = pos ? r : last_r;
+                const bool take = use && sel_n < 0 && t < c2;
+                sel_n = take ? n : sel_n;
+                sel_r = take ? r : sel_r;
+                cum = c2;
+            }
         }
     }
     if (sel_n < 0) {
@@ -578,6 +599,8 @@ __device__ __forceinline__ bool mono_event(const DevProblem& P, const RunParams&
 {
     TR_LANES(10);
     XS X;
+    CEKeep keep;
+    if (CE) X.keep = &keep;   // the collision below reuses the lookup's terms
     double xi_react;
     FwdSink sink{T, acc};
     step_event<CE>(P, R, p, sink, X, xi_react);
