@@ -663,7 +663,7 @@ def run_baseline_table(args):
     rows = []
     # C1 cube, C3 CE pin cell (fixed source)
     for label, name, spec, n, remap in (("C1 one-group cube", "cube", inputs.cube_one_group(), 100_000, 512),
-                                        ("C3 CE pin cell", "ce", inputs.ce_pin_cell(), 1_000_000, 4)):
+                                        ("C3 CE pin cell", "ce", inputs.ce_pin_cell(), 1_000_000, 64)):
         prob = tb.Problem(spec)
         opts = tb.RunOpts(n_histories=n, seed=1, scheme=tb.SCHEME_ASYNC, decomposition=tb.DECOMP_MONO,
                           remap_every=remap)
@@ -797,7 +797,7 @@ def main():
     ap.add_argument("--stash", type=int, default=0, help="async: particle slots per block stash (0 = default)")
     ap.add_argument("--bps", type=int, default=0, help="blocks per SM (0 = default)")
     ap.add_argument("--remap", type=int, default=0,
-                    help="monolithic / streaming: events between remaps (0: 512 for the lattice, 4 for the CE pin cell)")
+                    help="monolithic / streaming: events between remaps (0: 512 for the lattice, 64 for the CE pin cell)")
     ap.add_argument("--queue", type=int, default=0, help="stack: particles per stack; async: spill links x 32")
     ap.add_argument("--workload", choices=["lattice", "batched", "adjoint", "ce", "ce-sweep", "ce-time-sweep",
                                            "lattice-sweep", "baseline-table"],
@@ -809,7 +809,7 @@ def main():
     ap.add_argument("--n-hist", type=int, default=1_000_000, help="ce: histories per run")
     args = ap.parse_args()
     if args.remap <= 0:
-        args.remap = 4 if args.workload.startswith("ce") else 512
+        args.remap = 64 if args.workload.startswith("ce") else 512
     if args.warmup < 3 and args.impl == "ours":
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
     if args.impl == "reference":
