@@ -125,6 +125,9 @@ def lib():
         L.orc_log.argtypes = [C.c_double]
         L.orc_log.restype = C.c_double
         L.orc_iso_dir.argtypes = [C.c_uint64, C.c_uint32, C.c_uint64, C.c_uint32, C.POINTER(C.c_double)]
+        L.orc_exp_event.argtypes = [C.c_uint64, C.c_uint32, C.c_uint64, C.c_uint32]
+        L.orc_exp_event.restype = C.c_double
+        L.orc_zig_table.argtypes = [C.POINTER(C.c_double)]
         L.orc_elastic.argtypes = [C.c_double, C.c_double, C.c_double, C.POINTER(C.c_double), C.POINTER(C.c_double)]
         L.orc_rotate.argtypes = [C.POINTER(C.c_double), C.c_double, C.c_double, C.c_double, C.POINTER(C.c_double)]
         L.orc_cdf_sample.argtypes = [C.POINTER(C.c_double), C.POINTER(C.c_double), C.c_int32, C.c_double]
@@ -323,6 +326,20 @@ def uniform(lo, hi):
 
 def log(x: float) -> float:
     return lib().orc_log(float(x))
+
+
+def exp_event(seed, tag, hid, n):
+    """The exponential variate (ziggurat) of event n of history hid."""
+    return lib().orc_exp_event(seed, tag, hid, n)
+
+
+def zig_table():
+    """The ziggurat's per-layer table: widths W, inner widths C, lower
+    heights f and height steps df (256 each)."""
+    out = (C.c_double * 1024)()
+    lib().orc_zig_table(out)
+    a = np.array(out[:])
+    return a[:256], a[256:512], a[512:768], a[768:]
 
 
 def iso_dir(seed, tag, hid, n):

@@ -76,13 +76,19 @@ double orc_uniform(uint32_t lo, uint32_t hi)
     return ((double)(w >> 12) + 0.5) * 0x1p-52;
 }
 
-/* One Philox block for stream (seed, tag), counter (n, j, id_lo, id_hi). */
-static void rng_block(uint64_t seed, uint32_t tag, uint64_t id, uint32_t n, uint32_t j, double xi[2])
+/* One Philox block for stream (seed, tag), counter (n, j, id_lo, id_hi):   */
+/* its four words, and its two uniforms (words 0-1 and 2-3).                 */
+static void rng_words(uint64_t seed, uint32_t tag, uint64_t id, uint32_t n, uint32_t j, uint32_t r[4])
 {
     uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32) ^ tag};
     uint32_t ctr[4] = {n, j, (uint32_t)id, (uint32_t)(id >> 32)};
-    uint32_t r[4];
     orc_philox4x32_10(ctr, key, r);
+}
+
+static void rng_block(uint64_t seed, uint32_t tag, uint64_t id, uint32_t n, uint32_t j, double xi[2])
+{
+    uint32_t r[4];
+    rng_words(seed, tag, id, n, j, r);
     xi[0] = orc_uniform(r[0], r[1]);
     xi[1] = orc_uniform(r[2], r[3]);
 }
@@ -96,6 +102,8 @@ static void rng_block(uint64_t seed, uint32_t tag, uint64_t id, uint32_t n, uint
 #define BLK_SITE 100u    /* 100 + c: fission site c (chi sample, unused) */
 #define BLK_POS 200u     /* 200 + 2t, 201 + 2t: source position trial t */
 #define N_POS_TRIES 1024u
+#define BLK_ZIG 3000u    /* 3000 + t: exponential ziggurat, try t's wedge/tail uniform (words 2-3) */
+#define N_ZIG_TRIES 64u  /*   and try t+1's layer and uniform (words 0-1)                        */
 #define TAG_POPULATION 0x80000000u
 
 /* ------------------------------------------------------------------------ */
@@ -186,6 +194,94 @@ double orc_log(double x)
     double p = fma(q, r * r, r);
     double de = (double)e;
     return fma(de, LN2_HI, fma(de, LN2_LO, log_t[k - LOG_K_LO] + p));
+}
+
+/* ------------------------------------------------------------------------ */
+/* Exponential variate (the distance to collision in mean free paths) by the */
+/* ziggurat method of Marsaglia and Tsang (J. Stat. Softw. 5, 2000), with    */
+/* 256 layers of equal area v under f(x) = e^-x and their r and v:           */
+/*   layer 0: the base [0, v/f(r)] x [0, f(r)] with the tail beyond r;        */
+/*   layer i >= 1: [0, X_i] x [f(X_i), f(X_i+1)], X_1 = r, X_256 = 0.         */
+/* Table: f(X_1) = v/(r+1) (the base area v = (r+1) e^-r), then               */
+/* f(X_i+1) = f(X_i) + v/X_i and X_i+1 = -log f(X_i+1) with the contract's    */
+/* log; f(X_256) = 1.                                                        */
+/* A try takes layer i (the low 8 bits of its word pair) and the uniform U   */
+/* of that pair: x = U W_i (W_0 = v/f(r), W_i = X_i) is accepted when below   */
+/* the inner width C_i (C_0 = r, C_i = X_i+1).  Otherwise, with the uniform   */
+/* U2 of words 2-3 of block BLK_ZIG + t: layer 0 returns r - log U2 (the      */
+/* tail, memoryless); layer i accepts x if x < -log(fma(U2, f_i+1 - f_i,     */
+/* f_i)), else try t+1 takes words 0-1 of the same block.                     */
+/* ------------------------------------------------------------------------ */
+#define ZIG_N 256
+static double zig_w[ZIG_N], zig_c[ZIG_N], zig_f[ZIG_N], zig_df[ZIG_N];
+static int zig_ready = 0;
+
+static void zig_make_table(void)
+{
+    const double r = 7.69711747013104972;
+    const double v = 0.0039496598225815571993;
+    double X[ZIG_N + 1], F[ZIG_N + 1];
+    X[1] = r;
+    F[1] = v / (r + 1.0);
+    for (int i = 1; i < ZIG_N - 1; ++i) {
+        F[i + 1] = F[i] + v / X[i];
+        X[i + 1] = -orc_log(F[i + 1]);
+    }
+    X[ZIG_N] = 0.0;
+    F[ZIG_N] = 1.0;
+    zig_w[0] = v / F[1];
+    zig_c[0] = r;
+    zig_f[0] = 0.0;
+    zig_df[0] = 0.0;
+    for (int i = 1; i < ZIG_N; ++i) {
+        zig_w[i] = X[i];
+        zig_c[i] = X[i + 1];
+        zig_f[i] = F[i];
+        zig_df[i] = F[i + 1] - F[i];
+    }
+    zig_ready = 1;
+}
+
+void orc_zig_table(double out[4 * ZIG_N])
+{
+    if (!zig_ready) zig_make_table();
+    for (int i = 0; i < ZIG_N; ++i) {
+        out[i] = zig_w[i];
+        out[ZIG_N + i] = zig_c[i];
+        out[2 * ZIG_N + i] = zig_f[i];
+        out[3 * ZIG_N + i] = zig_df[i];
+    }
+}
+
+/* words lo, hi: the pair for try 0 (words 0-1 of the event's main block) */
+static double exp_sample(uint64_t seed, uint32_t tag, uint64_t id, uint32_t n, uint32_t lo, uint32_t hi)
+{
+    if (!zig_ready) zig_make_table();
+    int i = (int)(lo & 0xFFu);
+    double U = orc_uniform(lo, hi);
+    double x = U * zig_w[i];
+    if (x < zig_c[i]) return x;
+    for (uint32_t t = 0; t < N_ZIG_TRIES; ++t) {
+        uint32_t w[4];
+        rng_words(seed, tag, id, n, BLK_ZIG + t, w);
+        double U2 = orc_uniform(w[2], w[3]);
+        if (i == 0) return zig_c[0] - orc_log(U2);
+        double y = fma(U2, zig_df[i], zig_f[i]);
+        if (x < -orc_log(y)) return x;
+        i = (int)(w[0] & 0xFFu);
+        U = orc_uniform(w[0], w[1]);
+        x = U * zig_w[i];
+        if (x < zig_c[i]) return x;
+    }
+    return -orc_log(U);   /* after N_ZIG_TRIES rejected tries (probability below 1e-100) */
+}
+
+/* the exponential variate of event n of history id (pin tests) */
+double orc_exp_event(uint64_t seed, uint32_t tag, uint64_t id, uint32_t n)
+{
+    uint32_t w[4];
+    rng_words(seed, tag, id, n, BLK_MAIN, w);
+    return exp_sample(seed, tag, id, n, w[0], w[1]);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -867,9 +963,10 @@ static void event(ctx *C, particle *p)
     int m = material(P, p);
     xsval X;
     xs_lookup(C, m, p, &X);
-    double xi[2];
-    rng_block(C->seed, C->tag, p->id, p->n, BLK_MAIN, xi);
-    double dcol = (-orc_log(xi[0])) * X.inv_st;
+    uint32_t w0[4];
+    rng_words(C->seed, C->tag, p->id, p->n, BLK_MAIN, w0);
+    double xi[2] = {orc_uniform(w0[0], w0[1]), orc_uniform(w0[2], w0[3])};
+    double dcol = exp_sample(C->seed, C->tag, p->id, p->n, w0[0], w0[1]) * X.inv_st;
 
     /* plane distances along each axis to the exit face in the direction of travel */
     double dp[3];

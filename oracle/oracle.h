@@ -128,6 +128,8 @@ void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t ou
 double orc_uniform(uint32_t lo, uint32_t hi);
 double orc_log(double x);
 void orc_iso_dir(uint64_t seed, uint32_t tag, uint64_t id, uint32_t n, double dir[3]);
+double orc_exp_event(uint64_t seed, uint32_t tag, uint64_t id, uint32_t n);
+void orc_zig_table(double out[1024]);
 void orc_elastic(double A, double E, double mu_cm, double *E_out, double *mu_lab);
 void orc_rotate(const double dir[3], double mu, double cphi, double sphi, double out[3]);
 double orc_cdf_sample(const double *e, const double *p, int32_t n, double xi);

@@ -165,6 +165,36 @@ static std::vector<double> log_table()
     return t;
 }
 
+// Exponential ziggurat table for exp_sample (Marsaglia and Tsang's r and v for
+// 256 layers): X_1 = r, f_1 = v/(r+1) (the base area v = (r+1) e^-r), then
+// f_i+1 = f_i + v/X_i and X_i+1 = -log f_i+1 with the library's own log, so
+// one thread builds it on the device; X_256 = 0, f_256 = 1.  Out: {W_i, C_i}
+// pairs (W_0 = v/f_1, C_0 = r; W_i = X_i, C_i = X_i+1), then {f_i, df_i}.
+__global__ void k_zig_table(DevProblem P, double* out)
+{
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    const double r = 7.69711747013104972;
+    const double v = 0.0039496598225815571993;
+    double X = r, F = v / (r + 1.0);
+    out[0] = v / F;
+    out[1] = r;
+    out[2 * ZIG_N] = 0.0;
+    out[2 * ZIG_N + 1] = 0.0;
+    for (int i = 1; i < ZIG_N; ++i) {
+        double Xn = 0.0, Fn = 1.0;
+        if (i < ZIG_N - 1) {
+            Fn = F + v / X;
+            Xn = -tr_log(P.log_tab, Fn);
+        }
+        out[2 * i] = X;
+        out[2 * i + 1] = Xn;
+        out[2 * ZIG_N + 2 * i] = F;
+        out[2 * ZIG_N + 2 * i + 1] = Fn - F;
+        X = Xn;
+        F = Fn;
+    }
+}
+
 // ---------------------------------------------------------------------------
 // problem creation
 // ---------------------------------------------------------------------------
@@ -230,6 +260,17 @@ extern "C" tr_status tr_problem_create(const tr_geometry_desc* G, const tr_xs_de
 
     const std::vector<double> lt = log_table();
     P.log_tab = upload(pr, lt.data(), lt.size(), &ok);
+    {
+        double* zt = (double*)own(pr, 4 * ZIG_N * sizeof(double));
+        if (!zt || !P.log_tab) {
+            ok = false;
+        } else {
+            P.zig_tab = zt;
+            count_launches(1);
+            k_zig_table<<<1, 32, 0, pr->stream>>>(P, zt);
+            if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(pr->stream) != cudaSuccess) ok = false;
+        }
+    }
 
     // geometry
     P.nx = G->nx; P.ny = G->ny; P.nz = G->nz;

@@ -55,6 +55,10 @@ constexpr uint32_t N_AZIMUTH = 64u;
 constexpr uint32_t BLK_SITE = 100u;    // 100 + c: fission site c
 constexpr uint32_t BLK_POS = 200u;     // 200 + 2t, 201 + 2t: source position trial t
 constexpr uint32_t N_POS = 1024u;
+constexpr uint32_t BLK_ZIG = 3000u;    // 3000 + t: exponential ziggurat, try t's wedge or tail
+                                       // uniform (words 2-3) and try t+1's layer and uniform (words 0-1)
+constexpr uint32_t N_ZIG = 64u;
+constexpr int ZIG_N = 256;             // ziggurat layers
 constexpr uint32_t TAG_POP = 0x80000000u;
 
 // next event types of the decomposed schemes (queue ids); DEAD ends the history
@@ -112,6 +116,8 @@ struct DevProblem {
     const double *inv_vel;
     // logarithm table: {1/c_k, -log(1/c_k)} pairs (see tr_log)
     const double* log_tab;
+    // exponential ziggurat: {W_i, C_i} pairs, then {f_i, df_i} pairs (see exp_sample)
+    const double* zig_tab;
 };
 
 // Per-run parameters.
@@ -288,6 +294,45 @@ __device__ __forceinline__ double tr_log(const double* __restrict__ tab, double 
     const double de = (double)e;
     return __fma_rn(de, __longlong_as_double(0x3FE62E42FEFA4000ll),
                     __fma_rn(de, __longlong_as_double((long long)0xBD48432A1B0E2634ull), t.y + p));
+}
+
+// ---------------------------------------------------------------------------
+// Exponential variate (the distance to collision in mean free paths) by the
+// ziggurat method of Marsaglia and Tsang (J. Stat. Softw. 5, 2000): 256
+// layers of equal area v under f(x) = e^-x.  Layer 0 is the base rectangle
+// [0, W_0 = v/f(r)] x [0, f(r)] with the tail beyond r; layer i >= 1 is
+// [0, X_i] x [f(X_i), f(X_i+1)], X_1 = r, X_256 = 0.  A try takes layer i
+// (low 8 bits of its word pair) and the pair's uniform U: x = U W_i is
+// accepted below the inner width C_i (C_0 = r, C_i = X_i+1), about 99 % of
+// tries, with one multiplication.  Otherwise, with the uniform U2 of words
+// 2-3 of block BLK_ZIG + t: layer 0 returns r - log U2 (the tail is
+// memoryless); layer i accepts x if x < -log(fma(U2, df_i, f_i)) (under the
+// curve), else try t+1 takes words 0-1 of that block.  The table
+// ({W_i, C_i}, {f_i, df_i = f_i+1 - f_i}) is built at problem creation.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double exp_sample(const DevProblem& P, const Stream& S, uint32_t n, uint32_t lo, uint32_t hi)
+{
+    const double2* wc = reinterpret_cast<const double2*>(P.zig_tab);
+    const double2* fd = wc + ZIG_N;
+    int i = (int)(lo & 0xFFu);
+    double U = u01(lo, hi);
+    double2 t = __ldg(wc + i);
+    double x = U * t.x;
+    if (lt_nn(x, t.y)) return x;
+    for (uint32_t k = 0; k < N_ZIG; ++k) {
+        const uint4 w = S.block(n, BLK_ZIG + k);
+        const double U2 = u01(w.z, w.w);
+        if (i == 0) return t.y - tr_log(P.log_tab, U2);
+        const double2 f = __ldg(fd + i);
+        const double y = __fma_rn(U2, f.y, f.x);
+        if (lt_nn(x, -tr_log(P.log_tab, y))) return x;
+        i = (int)(w.x & 0xFFu);
+        U = u01(w.x, w.y);
+        t = __ldg(wc + i);
+        x = U * t.x;
+        if (lt_nn(x, t.y)) return x;
+    }
+    return -tr_log(P.log_tab, U);   // after N_ZIG rejected tries (probability below 1e-100)
 }
 
 // ---------------------------------------------------------------------------

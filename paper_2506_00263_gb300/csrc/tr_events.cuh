@@ -278,7 +278,7 @@ __device__ __forceinline__ void step_event(const DevProblem& P, const RunParams&
     const Stream S = make_stream(R, p.id);
     const uint4 b0 = S.block(p.n, BLK_MAIN);
     xi_react = u01(b0.z, b0.w);
-    const double dcol = (-tr_log(P.log_tab, u01(b0.x, b0.y))) * X.inv_st;
+    const double dcol = exp_sample(P, S, p.n, b0.x, b0.y) * X.inv_st;
     TR_LANES(2);
 
     const double INF = __longlong_as_double(0x7FF0000000000000ll);

@@ -184,3 +184,36 @@ def test_nuclide_index_against_linear_search():
     for q in qs[::97]:
         lin = max(i for i in range(len(e) - 1) if e[i] <= q)
         assert oracle.nuclide_index(e, float(q)) == lin
+
+
+ZIG_R, ZIG_V = 7.69711747013104972, 0.0039496598225815571993
+
+
+def test_ziggurat_table_layers_have_equal_area():
+    """Every layer of the exponential ziggurat has area v: the base rectangle
+    plus the tail (r + 1) e^-r, each layer i >= 1 X_i (f(X_i+1) - f(X_i));
+    the heights are e^-X (checked against the library exp) and close at 1."""
+    W, Cc, f, df = oracle.zig_table()
+    assert Cc[0] == ZIG_R and abs(W[0] * f[1] - ZIG_V) <= 1e-15
+    assert abs((ZIG_R + 1.0) * math.exp(-ZIG_R) - ZIG_V) <= 1e-12 * ZIG_V
+    areas = W[1:] * df[1:]
+    assert np.all(np.abs(areas - ZIG_V) <= 1e-12 * ZIG_V), np.abs(areas / ZIG_V - 1).max()
+    assert np.all(np.diff(W[1:]) < 0) and Cc[255] == 0.0 and np.all(Cc[1:255] == W[2:])
+    assert np.allclose(f[1:], np.exp(-W[1:]), rtol=1e-13, atol=0)
+    assert abs(f[255] + df[255] - 1.0) <= 1e-12
+
+
+def test_ziggurat_samples_are_exponential():
+    """The event's distance variate is Exp(1): mean, variance, the tail beyond
+    r and beyond 10, and a Kolmogorov-Smirnov test on 200k samples."""
+    n = 200_000
+    x = np.array([oracle.exp_event(3, 0, i, 1 + (i % 7)) for i in range(n)])
+    assert np.all(x >= 0.0)
+    se = 1.0 / math.sqrt(n)
+    assert abs(x.mean() - 1.0) < 5 * se
+    assert abs(x.var() - 1.0) < 5 * math.sqrt(8.0) * se
+    for t in (0.05, 0.5, 1.0, 3.0, ZIG_R, 10.0):
+        p = math.exp(-t)
+        assert abs((x > t).mean() - p) < 5 * math.sqrt(p * (1 - p) / n) + 1e-6, t
+    scipy_stats = pytest.importorskip("scipy.stats")
+    assert scipy_stats.kstest(x, "expon").pvalue > 1e-4
