@@ -251,6 +251,9 @@ __device__ __forceinline__ unsigned new_link(const AsyncArgs& A, int start, cons
 #ifndef TR_COLL_MIN
 #define TR_COLL_MIN 16   // pending collisions that make a warp run its collision pass
 #endif
+#ifndef TR_COLL_MIN_CE
+#define TR_COLL_MIN_CE 16   // the same, continuous energy
+#endif
 
 // Batch tail of the monolithic loop (source exhausted): a warp left with at
 // most TR_TAIL_EXIT live lanes, after TR_TAIL_MINRUN passes, hands its
@@ -631,6 +634,11 @@ __global__ void __launch_bounds__(256, TR_ASYNC_MIN_BLOCKS) k_async(DevProblem P
                     bool src_more = !BATCHED && src_left;
                     const int leader = __ffs(em) - 1;
                     bool pend_coll = live && p.pend == PEND_COLLIDE;
+                    // continuous energy: a collision deferred in the lane that made
+                    // its step reuses the step's lookup terms (ck); one that
+                    // arrived pending from the stash computes them again
+                    CEKeep ck;
+                    bool ck_ok = false;
                     for (int r = 0; r < R.remap_every; ++r) {
                         if (MERGE && r > 0 && !src_more && em == FULLM) {
                             const unsigned dead = __ballot_sync(FULLM, !live);
@@ -671,6 +679,7 @@ __global__ void __launch_bounds__(256, TR_ASYNC_MIN_BLOCKS) k_async(DevProblem P
                                         slot_load<XS>(st, slot, p, tm);
                                         live = true;
                                         pend_coll = p.pend == PEND_COLLIDE;
+                                        ck_ok = false;
                                     }
                                 } else if (32 - nd <= TR_TAIL_EXIT && r >= TR_TAIL_MINRUN && others > 0) {
                                     break;   // deposit: the block's running warps take these
@@ -708,10 +717,34 @@ __global__ void __launch_bounds__(256, TR_ASYNC_MIN_BLOCKS) k_async(DevProblem P
                         if (!src_more) TR_LANES(25);
                         if (live) TR_LANES(13);
                         if (live && !src_more) TR_LANES(31);
-                        if (CE) {
-                            // continuous energy: a deferred collision would repeat
-                            // the costly lookup, so step and collision stay one event
-                            if (live) live = mono_event<CE>(PP, RR, p, TT, acc, A.bank, err, lm);
+                        if constexpr (CE) {
+                            const unsigned pm = __ballot_sync(em, live && pend_coll);
+                            if (pm == lm || __popc(pm) >= TR_COLL_MIN_CE) {
+                                const bool kc = live && pend_coll && ck_ok;
+                                const unsigned pk = __ballot_sync(em, kc);
+                                if (kc) live = kept_collide<CE>(PP, RR, p, TT, acc, A.bank, err, pk, ck);
+                                const unsigned pr = pm & ~pk;
+                                if ((pr >> lane) & 1u) live = split_collide<CE>(PP, RR, p, TT, acc, A.bank, err, pr);
+                                if ((pm >> lane) & 1u) {
+                                    pend_coll = false;
+                                    p.pend = 0u;
+                                }
+                            } else if (live && !pend_coll) {
+                                tr::XS X;
+                                X.keep = &ck;
+                                double xr;
+                                FwdSink sink{TT, acc};
+                                step_event<CE>(PP, RR, p, sink, X, xr);
+                                if (p.pend == PEND_COLLIDE) {
+                                    pend_coll = true;
+                                    ck_ok = true;
+                                    ck.st = X.st;
+                                    ck.xi = xr;
+                                } else {
+                                    live = finish_event(PP, RR, p, surface_event(PP, p), TT, acc, A.bank);
+                                    p.pend = 0u;
+                                }
+                            }
                             continue;
                         }
                         const unsigned pm = __ballot_sync(em, live && pend_coll);

@@ -509,6 +509,7 @@ struct CEKeep {
     int n;                             // present nuclides kept, or -1 (more than CE_KEEP_NUC: recompute)
     int nuc[CE_KEEP_NUC];              // their indices, in order
     double mac[3 * CE_KEEP_NUC];       // N (s0 + f (s1 - s0)) per kept nuclide and reaction
+    double st, xi;                     // a deferred collision: sigma_t and the reaction draw of its step
 };
 
 struct XS {

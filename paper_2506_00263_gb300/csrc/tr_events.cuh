@@ -648,6 +648,22 @@ __device__ __forceinline__ bool split_collide(const DevProblem& P, const RunPara
     return finish_event(P, R, p, type, T, acc, B);
 }
 
+// A continuous-energy collision deferred within the lane that made its step:
+// the step's lookup terms, sigma_t and reaction draw come from k.
+template <bool CE>
+__device__ __forceinline__ bool kept_collide(const DevProblem& P, const RunParams& R, Particle& p, const Tallies& T,
+                                            Acc& acc, const Bank& B, ErrorWord* err, unsigned em, CEKeep& k)
+{
+    XS X;
+    X.st = k.st;
+    X.inv_st = 0.0;
+    X.sa = 0.0;
+    X.nsf = 0.0;
+    X.keep = &k;
+    const int type = collide_event<CE>(P, R, p, X, k.xi, B, err, em);
+    return finish_event(P, R, p, type, T, acc, B);
+}
+
 __device__ __forceinline__ bool split_surface(const DevProblem& P, const RunParams& R, Particle& p, const Tallies& T,
                                              Acc& acc, const Bank& B)
 {
