@@ -752,12 +752,12 @@ def run_lattice_sweep(args):
 # (sm__sass_thread_inst_executed_ops_dadd_dmul_dfma_pred_on.sum / events).
 # The arithmetic per event is the same in every scheme (the decomposed one
 # only repeats table loads).
-FP64_OPS_LATTICE = 64.7
+FP64_OPS_LATTICE = 55.0
 # DRAM bytes (read + write) of one batch's transport (source pre-sampling and
 # transport kernels; one 1e6-history lattice batch sourced from the fission
 # bank, asynchronous monolithic scheme, 512 events between remaps), from one
 # ncu capture of the current kernels: dram__bytes_read.sum + dram__bytes_write.sum.
-TRAFFIC_PER_LAUNCH = {("async", "mono", 512, 1_000_000): 220.1e6}
+TRAFFIC_PER_LAUNCH = {("async", "mono", 512, 1_000_000): 219.9e6}
 FP64_OPS_PER_EVENT = {(s, d): FP64_OPS_LATTICE for s in ("async", "stack") for d in ("mono", "split")}
 
 

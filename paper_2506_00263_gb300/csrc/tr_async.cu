@@ -254,6 +254,9 @@ __device__ __forceinline__ unsigned new_link(const AsyncArgs& A, int start, cons
 #ifndef TR_COLL_MIN_CE
 #define TR_COLL_MIN_CE 16   // the same, continuous energy
 #endif
+#ifndef TR_DEFER_MIN
+#define TR_DEFER_MIN 4      // fewer events between remaps: each pass runs whole events (no deferred collisions)
+#endif
 
 // Batch tail of the monolithic loop (source exhausted): a warp left with at
 // most TR_TAIL_EXIT live lanes, after TR_TAIL_MINRUN passes, hands its
@@ -328,8 +331,11 @@ __device__ __forceinline__ void flush_lane(Acc& acc, const Tallies& T)
 
 // DEC: the task decomposition (DEC_MONO, DEC_SPLIT or DEC_LOOKUP).
 // PRE: make_work loads pre-sampled sources (A.pre) instead of sampling them,
-// so the sampling code is not part of this kernel.
-template <bool CE, int DEC, bool BATCHED = false, bool PRE = false>
+// so the sampling code is not part of this kernel.  FUSE (monolithic, fewer
+// than TR_DEFER_MIN events between remaps): each pass runs whole events, as
+// the paper's monolithic scheme does; a deferred collision would wait for the
+// next take.
+template <bool CE, int DEC, bool BATCHED = false, bool PRE = false, bool FUSE = false>
 __global__ void __launch_bounds__(256, TR_ASYNC_MIN_BLOCKS) k_async(DevProblem P, RunParams R, AsyncArgs A, Tallies T, ErrorWord* err)
 {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -401,10 +407,12 @@ __global__ void __launch_bounds__(256, TR_ASYNC_MIN_BLOCKS) k_async(DevProblem P
         } else if (src_left && nfree >= 32) {
             mode = 1;
             take = 32;
-        } else if (cnts[q] > 0 && (!MERGE || src_left || n_run == 0 || tail_wait >= TR_TAIL_WAIT)) {
+        } else if (cnts[q] > 0 && (!MERGE || src_left || n_run == 0 || tail_wait >= TR_TAIL_WAIT ||
+                                   R.remap_every < TR_TAIL_MINRUN)) {
             // a partial queue; in the batch tail only once no other warp of the
             // block runs (it would take these particles into its idle lanes)
-            // or after TR_TAIL_WAIT polls
+            // or after TR_TAIL_WAIT polls, unless warps run too few passes to
+            // take particles in
             mode = 0;
             take = cnts[q];
         } else {
@@ -717,6 +725,10 @@ __global__ void __launch_bounds__(256, TR_ASYNC_MIN_BLOCKS) k_async(DevProblem P
                         if (!src_more) TR_LANES(25);
                         if (live) TR_LANES(13);
                         if (live && !src_more) TR_LANES(31);
+                        if constexpr (FUSE) {
+                            if (live) live = mono_event<CE>(PP, RR, p, TT, acc, A.bank, err, lm);
+                            continue;
+                        }
                         if constexpr (CE) {
                             const unsigned pm = __ballot_sync(em, live && pend_coll);
                             if (pm == lm || __popc(pm) >= TR_COLL_MIN_CE) {
@@ -851,18 +863,20 @@ __global__ void __launch_bounds__(256, TR_ASYNC_MIN_BLOCKS) k_async(DevProblem P
 
 namespace tr {
 
-template <bool CE, int DEC, bool BATCHED = false, bool PRE = false>
+template <bool CE, int DEC, bool BATCHED = false, bool PRE = false, bool FUSE = false>
 static cudaError_t prepare_async(size_t smem)
 {
-    return cudaFuncSetAttribute(k_async<CE, DEC, BATCHED, PRE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    return cudaFuncSetAttribute(k_async<CE, DEC, BATCHED, PRE, FUSE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)smem);
 }
 
-template <bool CE, int DEC, bool BATCHED = false, bool PRE = false>
+template <bool CE, int DEC, bool BATCHED = false, bool PRE = false, bool FUSE = false>
 static int occupancy_async(size_t smem)
 {
     int nb = 0;
-    if (prepare_async<CE, DEC, BATCHED, PRE>(smem) != cudaSuccess) return 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_async<CE, DEC, BATCHED, PRE>, 256, smem) != cudaSuccess)
+    if (prepare_async<CE, DEC, BATCHED, PRE, FUSE>(smem) != cudaSuccess) return 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_async<CE, DEC, BATCHED, PRE, FUSE>, 256, smem) !=
+        cudaSuccess)
         return 0;
     return nb;
 }
@@ -883,14 +897,28 @@ int async_max_blocks_per_sm(const DevProblem& P, int dec, int stash_slots, bool 
     return dec == DEC_SPLIT ? occupancy_async<false, DEC_SPLIT>(smem) : occupancy_async<false, DEC_MONO>(smem);
 }
 
-template <bool CE, int DEC, bool BATCHED = false, bool PRE = false>
+template <bool CE, int DEC, bool BATCHED = false, bool PRE = false, bool FUSE = false>
 static cudaError_t launch_async_t(const DevProblem& P, const RunParams& R, const AsyncArgs& A, const Tallies& T,
                                   ErrorWord* err, int blocks, cudaStream_t st, size_t smem)
 {
-    const cudaError_t e = prepare_async<CE, DEC, BATCHED, PRE>(smem);
+    const cudaError_t e = prepare_async<CE, DEC, BATCHED, PRE, FUSE>(smem);
     if (e != cudaSuccess) return e;
-    k_async<CE, DEC, BATCHED, PRE><<<blocks, 256, smem, st>>>(P, R, A, T, err);
+    k_async<CE, DEC, BATCHED, PRE, FUSE><<<blocks, 256, smem, st>>>(P, R, A, T, err);
     return cudaGetLastError();
+}
+
+// The monolithic kernel for a run: pre-sampled sources or not, whole events
+// per pass (fewer than TR_DEFER_MIN events between remaps) or deferred collisions.
+template <bool CE>
+static cudaError_t launch_async_mono(const DevProblem& P, const RunParams& R, const AsyncArgs& A, const Tallies& T,
+                                     ErrorWord* err, int blocks, cudaStream_t st, size_t smem)
+{
+    const bool fuse = R.remap_every < TR_DEFER_MIN;
+    if (A.use_pre)
+        return fuse ? launch_async_t<CE, DEC_MONO, false, true, true>(P, R, A, T, err, blocks, st, smem)
+                    : launch_async_t<CE, DEC_MONO, false, true>(P, R, A, T, err, blocks, st, smem);
+    return fuse ? launch_async_t<CE, DEC_MONO, false, false, true>(P, R, A, T, err, blocks, st, smem)
+                : launch_async_t<CE, DEC_MONO>(P, R, A, T, err, blocks, st, smem);
 }
 
 cudaError_t launch_async(const DevProblem& P, const RunParams& R, const AsyncArgs& A, const Tallies& T, ErrorWord* err,
@@ -899,19 +927,17 @@ cudaError_t launch_async(const DevProblem& P, const RunParams& R, const AsyncArg
     const size_t smem = stash_bytes(A.stash_slots, A.dec == DEC_LOOKUP);
     if (smem_bytes_out) *smem_bytes_out = (int)smem;
     count_launches(1);
-    if (A.use_pre && A.dec == DEC_MONO)
-        return P.kind == 1 ? launch_async_t<true, DEC_MONO, false, true>(P, R, A, T, err, blocks, st, smem)
-                           : launch_async_t<false, DEC_MONO, false, true>(P, R, A, T, err, blocks, st, smem);
+    if (A.dec == DEC_MONO)
+        return P.kind == 1 ? launch_async_mono<true>(P, R, A, T, err, blocks, st, smem)
+                           : launch_async_mono<false>(P, R, A, T, err, blocks, st, smem);
     if (P.kind == 1) {
         if (A.dec == DEC_STREAM) return launch_async_t<true, DEC_STREAM>(P, R, A, T, err, blocks, st, smem);
         if (A.dec == DEC_LOOKUP) return launch_async_t<true, DEC_LOOKUP>(P, R, A, T, err, blocks, st, smem);
-        return A.dec == DEC_SPLIT ? launch_async_t<true, DEC_SPLIT>(P, R, A, T, err, blocks, st, smem)
-                                  : launch_async_t<true, DEC_MONO>(P, R, A, T, err, blocks, st, smem);
+        return launch_async_t<true, DEC_SPLIT>(P, R, A, T, err, blocks, st, smem);
     }
     if (A.dec == DEC_STREAM) return launch_async_t<false, DEC_STREAM>(P, R, A, T, err, blocks, st, smem);
     if (A.dec == DEC_LOOKUP) return launch_async_t<false, DEC_LOOKUP>(P, R, A, T, err, blocks, st, smem);
-    return A.dec == DEC_SPLIT ? launch_async_t<false, DEC_SPLIT>(P, R, A, T, err, blocks, st, smem)
-                              : launch_async_t<false, DEC_MONO>(P, R, A, T, err, blocks, st, smem);
+    return launch_async_t<false, DEC_SPLIT>(P, R, A, T, err, blocks, st, smem);
 }
 
 cudaError_t launch_presample(const DevProblem& P, const RunParams& R, const AsyncArgs& A, int blocks, cudaStream_t st)
@@ -935,8 +961,10 @@ cudaError_t launch_async_batched(const DevProblem& P0, const RunParams& R, const
     const size_t smem = stash_bytes(A.stash_slots);
     const Tallies T{};
     count_launches(1);
-    return A.dec == DEC_SPLIT ? launch_async_t<false, DEC_SPLIT, true>(P0, R, A, T, err, blocks, st, smem)
-                              : launch_async_t<false, DEC_MONO, true>(P0, R, A, T, err, blocks, st, smem);
+    if (A.dec == DEC_SPLIT) return launch_async_t<false, DEC_SPLIT, true>(P0, R, A, T, err, blocks, st, smem);
+    if (R.remap_every < TR_DEFER_MIN)
+        return launch_async_t<false, DEC_MONO, true, false, true>(P0, R, A, T, err, blocks, st, smem);
+    return launch_async_t<false, DEC_MONO, true>(P0, R, A, T, err, blocks, st, smem);
 }
 
 }  // namespace tr
