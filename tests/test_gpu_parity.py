@@ -108,6 +108,46 @@ def test_power_iteration_parity(scheme, decomp):
     prob.close()
 
 
+# ----------------------------------- the monolithic loop with deferred collisions
+# (4 or more events between remaps: pending collisions batched in the warp,
+# sources refilled in the loop, the batch tail consolidated; the benchmark
+# runs 512, the CE benchmark 64)
+
+@pytest.mark.parametrize("remap", [4, 64, 512])
+@pytest.mark.parametrize("name,n", [("cube", 100_003), ("lattice", 20_011), ("ce", 3_001)])
+def test_deferred_collision_loop_parity(name, n, remap):
+    g = _gpu_fixed(name, n, tb.SCHEME_ASYNC, tb.DECOMP_MONO, remap_every=remap)
+    _compare_fixed(g, _oracle_fixed(name, n), n)
+
+
+def test_deferred_collision_loop_spills_and_tiny_stash():
+    """Forced spills and a small stash with 512 events between remaps: the
+    tail hands particles between warps and blocks, never changing a history."""
+    n = 20_011
+    o = _oracle_fixed("lattice", n)
+    for kw in (dict(remap_every=512, spill_threshold=-32, queue_capacity=64 * 32),
+               dict(remap_every=512, stash_slots=288, blocks_per_sm=1),
+               dict(remap_every=64, stash_slots=288, spill_threshold=-32, queue_capacity=4096)):
+        g = _gpu_fixed("lattice", n, tb.SCHEME_ASYNC, tb.DECOMP_MONO, **kw)
+        _compare_fixed(g, o, n)
+
+
+@pytest.mark.parametrize("remap", [64, 512])
+def test_deferred_collision_loop_power_iteration(remap):
+    p = _problem("lattice")
+    nper, ni, na = 3000, 2, 3
+    o = oracle.power_iteration(p, nper, ni, na, seed=3, log_batch=ni + na - 1)
+    prob = tb.Problem(p)
+    g = prob.power_iteration(nper, ni, na, tb.RunOpts(seed=3, scheme=tb.SCHEME_ASYNC, decomposition=tb.DECOMP_MONO,
+                                                      remap_every=remap, want_event_log=True))
+    assert np.array_equal(g["n_source"], o["n_source"])
+    assert np.array_equal(g["k_batch"], o["k_batch"])
+    assert_tally_close(prob.tally(tb.TALLY_MESH), o["mesh_mean"], "mesh mean")
+    nlast = int(o["n_source"][-1])
+    assert_logs_equal(prob.event_log(nlast), (o["log_n"], o["log_cell"], o["log_type"]), "last batch")
+    prob.close()
+
+
 # --------------------------------------------------------------- edge cases
 
 @pytest.mark.parametrize("n", [0, 1, 31, 33, 1000 + 7])

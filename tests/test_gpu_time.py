@@ -36,10 +36,10 @@ def _ce_timed(nbins):
     return p.replace(t_census=2e-7, n_time_bins=nbins)
 
 
-def _run(spec, n, scheme, decomp, seed=1):
+def _run(spec, n, scheme, decomp, seed=1, **kw):
     prob = tb.Problem(spec)
     st = prob.run_fixed_source(tb.RunOpts(n_histories=n, seed=seed, scheme=scheme, decomposition=decomp,
-                                          want_event_log=True))
+                                          want_event_log=True, **kw))
     out = {"stats": st, "log": prob.event_log(n), "time": prob.tally(tb.TALLY_TIME),
            "scalars": prob.tally(tb.TALLY_SCALARS), "mesh": prob.tally(tb.TALLY_MESH),
            "energy": prob.tally(tb.TALLY_ENERGY)}
@@ -73,6 +73,17 @@ def test_timed_ce_parity(nbins):
     for scheme, decomp in ((tb.SCHEME_ASYNC, tb.DECOMP_MONO), (tb.SCHEME_STACK, tb.DECOMP_SPLIT),
                            (tb.SCHEME_ASYNC, tb.DECOMP_SPLIT_LOOKUP)):
         _compare(_run(spec, n, scheme, decomp, seed=2), o)
+
+
+@pytest.mark.parametrize("remap", [64, 512])
+def test_timed_deferred_collision_loop(remap):
+    """The monolithic loop with deferred collisions on timed problems."""
+    spec = _mg_timed()
+    _compare(_run(spec, 30_011, tb.SCHEME_ASYNC, tb.DECOMP_MONO, seed=1, remap_every=remap),
+             oracle.run_fixed_source(spec, 30_011, seed=1))
+    ce = _ce_timed(8)
+    _compare(_run(ce, 5_003, tb.SCHEME_ASYNC, tb.DECOMP_MONO, seed=2, remap_every=remap),
+             oracle.run_fixed_source(ce, 5_003, seed=2))
 
 
 def test_streaming_closed_form_on_gpu():
