@@ -12,8 +12,11 @@
 // back into the slots it owns and pushes each slot onto the queue of its next
 // event type.  When no queue holds a full warp's worth, the warp calls
 // make_work: it claims source indices with one atomic add and runs their
-// source events.  Once the source is exhausted, partial queues are run as
-// they are.
+// source events (or loads the particles k_presample sampled before the
+// launch).  Once the source is exhausted, partial queues are run as they are.
+// In the monolithic scheme a warp keeps its particles in registers for up to
+// remap_every passes, refilling idle lanes with new histories and batching
+// the collisions of its lanes, before it deposits them.
 //
 // Global memory is the last resort (Sec. 3.2): a link arena of 32-particle
 // links, organised in linked lists whose (head, tail) pair is packed in one
@@ -623,14 +626,16 @@ __global__ void __launch_bounds__(256, TR_ASYNC_MIN_BLOCKS) k_async(DevProblem P
                     // place (make_work inside the loop), so the warp stays full;
                     // the live count needs no update for that (the lane's death
                     // and its new history cancel).  A step that ends in a
-                    // collision leaves the collision pending (multigroup; continuous
-                    // energy keeps the two as one event); a pass runs either
+                    // collision leaves the collision pending; a pass runs either
                     // the steps (with their surface crossings) of the lanes with
                     // nothing pending, or, once TR_COLL_MIN lanes are pending
                     // (or nothing else can step), their collisions together, so
                     // the FP64 work of the collision is issued for many lanes
-                    // at once.  The collision recomputes its lookup and reaction
-                    // draw from the counter-based keys: histories are the same.
+                    // at once.  A multigroup collision recomputes its lookup and
+                    // reaction draw from the counter-based keys; a continuous-
+                    // energy one reuses what its step kept.  Histories are the
+                    // same.  (Below TR_DEFER_MIN passes the FUSE variant runs
+                    // whole events instead.)
                     // Every lane holding a slot stays in the loop, so the
                     // ballots name em; a pending collision survives a remap in
                     // p.pend.  Once the source is exhausted (the batch tail),
