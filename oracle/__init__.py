@@ -128,6 +128,8 @@ def lib():
         L.orc_exp_event.argtypes = [C.c_uint64, C.c_uint32, C.c_uint64, C.c_uint32]
         L.orc_exp_event.restype = C.c_double
         L.orc_zig_table.argtypes = [C.POINTER(C.c_double)]
+        L.orc_ce_macro.argtypes = [C.POINTER(OrcProblem), C.c_int, C.c_double, C.POINTER(C.c_double)]
+        L.orc_ce_macro.restype = C.c_int
         L.orc_elastic.argtypes = [C.c_double, C.c_double, C.c_double, C.POINTER(C.c_double), C.POINTER(C.c_double)]
         L.orc_rotate.argtypes = [C.POINTER(C.c_double), C.c_double, C.c_double, C.c_double, C.POINTER(C.c_double)]
         L.orc_cdf_sample.argtypes = [C.POINTER(C.c_double), C.POINTER(C.c_double), C.c_int32, C.c_double]
@@ -219,6 +221,15 @@ class _Marshalled:
         if getattr(prob, "inv_velocity", None) is not None:
             s.inv_vel = f64(prob.inv_velocity)
         self.s = s
+
+
+def ce_macro(prob, m: int, E: float):
+    """Macroscopic (sigma_t, sigma_a) of material m at energy E (continuous energy)."""
+    mm = _Marshalled(prob)
+    out = (C.c_double * 2)()
+    if lib().orc_ce_macro(C.byref(mm.s), int(m), float(E), out) != 0:
+        raise ValueError("orc_ce_macro failed")
+    return out[0], out[1]
 
 
 def run_fixed_source(prob, n_hist: int, seed: int = 1, tag: int = 0, max_events: int = 0, logs: bool = True,

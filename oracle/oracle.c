@@ -409,7 +409,7 @@ typedef struct {
     double *cum_s;       /* [m][g][g'] running sum of sigma_s over g' */
     double *sig_a;       /* [m][g] = sigma_t - total scatter */
     double *cum_chi;     /* [m][g] running sum of chi */
-    double *inv_de;      /* CE: per grid row 1/(E[i+1]-E[i]) */
+    double *slope;       /* CE: per grid row and reaction (s[i+1]-s[i])/(E[i+1]-E[i]) */
     int64_t n_rows;
     int64_t mesh_vox;
     /* tallies */
@@ -464,10 +464,14 @@ static int setup(ctx *C, const orc_problem *P)
         if (P->n_nuc < 1 || P->n_nuc * 3 > 64) return ORC_ERR_INVALID;
         C->G = 1;
         C->n_rows = P->nuc_off[P->n_nuc];
-        C->inv_de = malloc(sizeof(double) * (size_t)C->n_rows);
+        C->slope = malloc(sizeof(double) * 3 * (size_t)C->n_rows);
         for (int n = 0; n < P->n_nuc; ++n)
             for (int64_t r = P->nuc_off[n]; r < P->nuc_off[n + 1]; ++r)
-                C->inv_de[r] = (r + 1 < P->nuc_off[n + 1]) ? 1.0 / (P->nuc_e[r + 1] - P->nuc_e[r]) : 0.0;
+                for (int k = 0; k < 3; ++k)
+                    C->slope[3 * r + k] = (r + 1 < P->nuc_off[n + 1])
+                                              ? (P->nuc_sig[3 * (r + 1) + k] - P->nuc_sig[3 * r + k]) /
+                                                    (P->nuc_e[r + 1] - P->nuc_e[r])
+                                              : 0.0;
     }
     C->mesh_vox = P->has_mesh ? (int64_t)P->mesh_n[0] * P->mesh_n[1] * P->mesh_n[2] : 0;
     int64_t msize = C->mesh_vox * ((P->mesh_by_group && P->xs_kind == 0) ? C->G : 1);
@@ -489,7 +493,7 @@ static int setup(ctx *C, const orc_problem *P)
 static void teardown(ctx *C)
 {
     free(C->rec);
-    free(C->inv_sigt); free(C->cum_s); free(C->sig_a); free(C->cum_chi); free(C->inv_de);
+    free(C->inv_sigt); free(C->cum_s); free(C->sig_a); free(C->cum_chi); free(C->slope);
     free(C->mesh); free(C->energy); free(C->time);
     free(C->bank_pos); free(C->bank_g); free(C->bank_cell); free(C->bank_E);
 }
@@ -598,8 +602,10 @@ static void xs_lookup(const ctx *C, int m, const particle *p, xsval *X)
         return;
     }
     /* CE: per nuclide present, interpolate each reaction on the nuclide's own
-     * grid at the largest point <= E; macroscopic terms N*sigma accumulated in
-     * (nuclide, elastic/capture/fission) order; sigma_t is the running total. */
+     * grid at the largest point E_i <= E: sigma = fma(E - E_i, slope_i, s_i)
+     * with slope_i = (s_i+1 - s_i)/(E_i+1 - E_i); macroscopic terms N*sigma
+     * accumulated in (nuclide, elastic/capture/fission) order; sigma_t is the
+     * running total. */
     double cum = 0.0, sa = 0.0;
     int t = 0;
     for (int n = 0; n < P->n_nuc; ++n) {
@@ -608,10 +614,9 @@ static void xs_lookup(const ctx *C, int m, const particle *p, xsval *X)
         int64_t off = P->nuc_off[n], cnt = P->nuc_off[n + 1] - off;
         int64_t i = orc_nuclide_index(P->nuc_e + off, cnt, p->E);
         int64_t r0 = off + i;
-        double f = (p->E - P->nuc_e[r0]) * C->inv_de[r0];
+        double dE = p->E - P->nuc_e[r0];
         for (int r = 0; r < 3; ++r) {
-            double s0 = P->nuc_sig[r0 * 3 + r], s1 = P->nuc_sig[(r0 + 1) * 3 + r];
-            double sig = s0 + f * (s1 - s0);
+            double sig = fma(dE, C->slope[r0 * 3 + r], P->nuc_sig[r0 * 3 + r]);
             double mac = N * sig;
             cum = cum + mac;
             if (r > 0) sa = sa + mac;
@@ -628,6 +633,27 @@ static void xs_lookup(const ctx *C, int m, const particle *p, xsval *X)
     X->sa = sa;
     X->nsf = 0.0;
 }
+
+/* Macroscopic sigma_t and sigma_a of material m at energy E (continuous
+ * energy; pin tests).  Returns ORC_OK or an error. */
+int orc_ce_macro(const orc_problem *P, int m, double E, double out[2])
+{
+    if (P->xs_kind != 1 || m < 0 || m >= P->n_mat) return ORC_ERR_INVALID;
+    ctx C;
+    int s = setup(&C, P);
+    if (s == ORC_OK) {
+        particle p;
+        memset(&p, 0, sizeof(p));
+        p.E = E;
+        xsval X;
+        xs_lookup(&C, m, &p, &X);
+        out[0] = X.st;
+        out[1] = X.sa;
+    }
+    teardown(&C);
+    return s;
+}
+
 
 /* ------------------------------------------------------------------------ */
 /* Tallies for one straight segment (p0, d, len).                            */

@@ -129,6 +129,7 @@ double orc_uniform(uint32_t lo, uint32_t hi);
 double orc_log(double x);
 void orc_iso_dir(uint64_t seed, uint32_t tag, uint64_t id, uint32_t n, double dir[3]);
 double orc_exp_event(uint64_t seed, uint32_t tag, uint64_t id, uint32_t n);
+int orc_ce_macro(const orc_problem *P, int m, double E, double out[2]);
 void orc_zig_table(double out[1024]);
 void orc_elastic(double A, double E, double mu_cm, double *E_out, double *mu_lab);
 void orc_rotate(const double dir[3], double mu, double cphi, double sphi, double out[3]);

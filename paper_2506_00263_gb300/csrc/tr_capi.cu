@@ -336,12 +336,16 @@ extern "C" tr_status tr_problem_create(const tr_geometry_desc* G, const tr_xs_de
         P.G = 1;
         P.n_nuc = Nn;
         const long long rows = X->nuc_offset[Nn];
-        std::vector<double> invde(rows, 0.0);
+        // per grid row and reaction the slope (s[i+1] - s[i]) / (E[i+1] - E[i])
+        std::vector<double> slope(3 * (size_t)rows, 0.0);
         for (int n = 0; n < Nn; ++n) {
             const long long a = X->nuc_offset[n], b = X->nuc_offset[n + 1];
             if (b - a < 2 || !ascending(X->nuc_energy + a, (int)(b - a - 1)))
                 return fail_out(TR_ERR_INVALID, "each nuclide grid needs >= 2 ascending points");
-            for (long long r = a; r + 1 < b; ++r) invde[r] = 1.0 / (X->nuc_energy[r + 1] - X->nuc_energy[r]);
+            for (long long r = a; r + 1 < b; ++r)
+                for (int k = 0; k < 3; ++k)
+                    slope[3 * r + k] = (X->nuc_sigma[3 * (r + 1) + k] - X->nuc_sigma[3 * r + k]) /
+                                       (X->nuc_energy[r + 1] - X->nuc_energy[r]);
         }
         // union grid: all nuclide energies, sorted and unique; per union point
         // and nuclide the largest nuclide row with E_row <= E_union (clamped
@@ -377,7 +381,7 @@ extern "C" tr_status tr_problem_create(const tr_geometry_desc* G, const tr_xs_de
         }
         P.nuc_e = upload(pr, X->nuc_energy, rows, &ok);
         P.nuc_sig = upload(pr, X->nuc_sigma, rows * 3, &ok);
-        P.nuc_inv_de = upload(pr, invde.data(), rows, &ok);
+        P.nuc_slope = upload(pr, slope.data(), 3 * (size_t)rows, &ok);
         P.dens = upload(pr, X->density, (size_t)M * Nn, &ok);
         P.awr = upload(pr, X->nuc_awr, Nn, &ok);
         P.inv_ap1sq = upload(pr, iap.data(), Nn, &ok);

@@ -86,7 +86,7 @@ struct DevProblem {
     int kind, n_mat, G;
     const double *sigt, *inv_sigt, *sig_a, *nusigf, *cum_s, *cum_chi, *chi, *sigs;
     int n_nuc;
-    const double *nuc_e, *nuc_sig, *nuc_inv_de;   // CE rows
+    const double *nuc_e, *nuc_sig, *nuc_slope;    // CE rows: energy, 3 cross sections, 3 slopes to the next row
     const double *dens;                // [m][n]
     const double *awr, *inv_ap1sq;     // per nuclide
     double e_cut;
@@ -551,8 +551,9 @@ __device__ __forceinline__ int union_index(const DevProblem& P, double E)
 
 // CE macroscopic totals at the particle energy: per present nuclide (density
 // > 0, index order) and reaction (elastic, capture, fission) the term
-// N * (s0 + f (s1 - s0)), f = (E - E_i) / (E_i+1 - E_i) via the stored
-// reciprocal; sigma_t is the running sum, sigma_a the capture + fission part.
+// N * fma(E - E_i, slope_i, s_i), E_i the largest grid point <= E and
+// slope_i = (s_i+1 - s_i) / (E_i+1 - E_i) stored per row; sigma_t is the
+// running sum, sigma_a the capture + fission part.
 __device__ __forceinline__ void xs_ce(const DevProblem& P, int m, double E, XS& X)
 {
     const int u = union_index(P, E);
@@ -562,12 +563,11 @@ __device__ __forceinline__ void xs_ce(const DevProblem& P, int m, double E, XS& 
         const double N = __ldg(P.dens + m * P.n_nuc + n);
         if (!(N > 0.0)) continue;
         const int r0 = __ldg(P.uptr + (long long)u * P.n_nuc + n);
-        const double f = (E - __ldg(P.nuc_e + r0)) * __ldg(P.nuc_inv_de + r0);
+        const double dE = E - __ldg(P.nuc_e + r0);
 #pragma unroll
         for (int r = 0; r < 3; ++r) {
             const double s0 = __ldg(P.nuc_sig + 3 * (long long)r0 + r);
-            const double s1 = __ldg(P.nuc_sig + 3 * (long long)(r0 + 1) + r);
-            const double mac = N * (s0 + f * (s1 - s0));
+            const double mac = N * __fma_rn(dE, __ldg(P.nuc_slope + 3 * (long long)r0 + r), s0);
             if (X.keep && kept < CE_KEEP_NUC) X.keep->mac[3 * kept + r] = mac;
             cum = cum + mac;
             if (r > 0) sa = sa + mac;

@@ -455,11 +455,10 @@ __device__ __forceinline__ int collide_event(const DevProblem& P, const RunParam
             const double N = __ldg(P.dens + m * P.n_nuc + n);
             const bool use = N > 0.0;
             const int r0 = __ldg(P.uptr + (long long)u * P.n_nuc + n);
-            const double f = (p.E - __ldg(P.nuc_e + r0)) * __ldg(P.nuc_inv_de + r0);
+            const double dE = p.E - __ldg(P.nuc_e + r0);
             for (int r = 0; r < 3; ++r) {
                 const double s0 = __ldg(P.nuc_sig + 3 * (long long)r0 + r);
-                const double s1 = __ldg(P.nuc_sig + 3 * (long long)(r0 + 1) + r);
-                const double mac = N * (s0 + f * (s1 - s0));
+                const double mac = N * __fma_rn(dE, __ldg(P.nuc_slope + 3 * (long long)r0 + r), s0);
                 const double c2 = use ? cum + mac : cum;
                 const bool pos = use && mac > 0.0;
                 last_n = pos ? n : last_n;

@@ -303,3 +303,29 @@ def test_homogenised_lattice_is_infinite_medium():
     ev = r["events_by_type"]
     assert ev[oracle.ORC_SURF_INTERNAL] > 5 * N and ev[oracle.ORC_SURF_REFLECT] > 0
     assert abs(r["mesh"].sum() - r["scalars"][0]) <= 1e-10 * r["scalars"][0]
+
+
+def test_ce_macroscopic_cross_sections_interpolate_linearly():
+    """The continuous-energy lookup is linear interpolation in energy on each
+    nuclide's own grid, weighted by the material's densities: against
+    numpy's interp at random energies (inside every grid) and exactly at grid
+    points, for sigma_t and sigma_a (capture + fission)."""
+    p = inputs.ce_pin_cell(n_points=2000, n_res=20, n_ebins=10)
+    lo = max(e[0] for e in p.nuc_energy)
+    hi = min(e[-1] for e in p.nuc_energy)
+    rng = np.random.default_rng(5)
+    energies = list(np.exp(rng.uniform(math.log(lo), math.log(hi), 300)))
+    energies += [float(p.nuc_energy[0][k]) for k in (1, 500, 1999)]
+    for m in range(p.n_materials):
+        for E in energies:
+            ref_t = ref_a = 0.0
+            for n, (e, s) in enumerate(zip(p.nuc_energy, p.nuc_sigma)):
+                N = p.mat_density[m, n]
+                if N <= 0.0:
+                    continue
+                sig = [np.interp(E, e, s[:, r]) for r in range(3)]
+                ref_t += N * sum(sig)
+                ref_a += N * (sig[1] + sig[2])
+            st, sa = oracle.ce_macro(p, m, E)
+            assert abs(st - ref_t) <= 1e-12 * ref_t, (m, E, st, ref_t)
+            assert abs(sa - ref_a) <= 1e-12 * ref_a + 1e-300, (m, E, sa, ref_a)
