@@ -120,8 +120,8 @@ typedef struct {
 /* Tallies: an optional track-length flux mesh over [lo, hi] with n cells per
  * axis (per group when by_group != 0, multigroup only), and an optional
  * continuous-energy flux tally per material over n_energy_bins bins with
- * ascending edges.  The flux, absorption-rate and production-rate totals are
- * always scored.
+ * ascending, non-negative edges (eV; TR_ERR_INVALID otherwise).  The flux,
+ * absorption-rate and production-rate totals are always scored.
  * Time (the paper's temporal tally resolution, Sec. 4; the formulas are our
  * reading): t_census > 0 makes the problem timed.  Histories start at t = 0
  * and move at speed 1/inv_velocity[g] (multigroup) or c sqrt(2E / m_n c^2)

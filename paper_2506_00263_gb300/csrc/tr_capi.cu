@@ -469,8 +469,8 @@ extern "C" tr_status tr_problem_create(const tr_geometry_desc* G, const tr_xs_de
         P.cell2vox = upload(pr, c2v.data(), c2v.size(), &ok);
     }
     if (n_tallies == 1 && Tl->n_energy_bins > 0) {
-        if (!Tl->energy_edges || !ascending(Tl->energy_edges, Tl->n_energy_bins))
-            return fail_out(TR_ERR_INVALID, "energy edges must be ascending");
+        if (!Tl->energy_edges || !ascending(Tl->energy_edges, Tl->n_energy_bins) || !(Tl->energy_edges[0] >= 0.0))
+            return fail_out(TR_ERR_INVALID, "energy edges must be ascending and non-negative");
         P.n_ebins = Tl->n_energy_bins;
         P.e_edges = upload(pr, Tl->energy_edges, Tl->n_energy_bins + 1, &ok);
         P.energy_size = M * Tl->n_energy_bins;

@@ -420,13 +420,14 @@ __device__ __forceinline__ void iso_dir(const Stream& S, uint32_t n, Particle& p
 __device__ __forceinline__ void rotate(Particle& p, double mu, double cphi, double sphi)
 {
     double t = __fma_rn(-mu, mu, 1.0);
-    if (t < 0.0) t = 0.0;
+    if (lt0(t)) t = 0.0;
     const double st = sqrt(t);
     const double u = p.u, v = p.v, w = p.w;
-    if (fabs(w) > 0.9999999999) {
+    // |w| > 0.9999999999 and w > 0 on the bit patterns (integer instructions)
+    if ((dbits(w) & 0x7FFFFFFFFFFFFFFFll) > dbits(0.9999999999)) {
         p.u = st * cphi;
         p.v = st * sphi;
-        p.w = (w > 0.0) ? mu : -mu;
+        p.w = gt0(w) ? mu : -mu;
     } else {
         const double sq = sqrt(__fma_rn(-w, w, 1.0));
         const double a1 = st / sq;
@@ -561,7 +562,7 @@ __device__ __forceinline__ void xs_ce(const DevProblem& P, int m, double E, XS& 
     int kept = 0;
     for (int n = 0; n < P.n_nuc; ++n) {
         const double N = __ldg(P.dens + m * P.n_nuc + n);
-        if (!(N > 0.0)) continue;
+        if (!gt0(N)) continue;
         const int r0 = __ldg(P.uptr + (long long)u * P.n_nuc + n);
         const double dE = E - __ldg(P.nuc_e + r0);
 #pragma unroll

@@ -146,11 +146,14 @@ __device__ __forceinline__ void mesh_tally(const DevProblem& P, Op& op, const Pa
 __device__ __forceinline__ void energy_tally(const DevProblem& P, double* __restrict__ etal, int m, double E, double L)
 {
     const int nb = P.n_ebins;
-    if (!(E >= __ldg(P.e_edges)) || !(E < __ldg(P.e_edges + nb))) return;
+    // E > 0 and the edges are non-negative (checked at problem creation):
+    // compared on their bit patterns (integer instructions)
+    const long long eb = dbits(E);
+    if (eb < dbits(__ldg(P.e_edges)) || eb >= dbits(__ldg(P.e_edges + nb))) return;
     int lo = 0, hi = nb;
     while (hi - lo > 1) {
         const int mid = (lo + hi) >> 1;
-        if (__ldg(P.e_edges + mid) <= E) lo = mid; else hi = mid;
+        if (dbits(__ldg(P.e_edges + mid)) <= eb) lo = mid; else hi = mid;
     }
     atomicAdd(etal + m * nb + lo, L);
 }
@@ -436,8 +439,8 @@ __device__ __forceinline__ int collide_event(const DevProblem& P, const RunParam
         for (int k = 0; k < 3 * X.keep->n; ++k) {
             const double mac = X.keep->mac[k];
             const double c2 = cum + mac;
-            last = mac > 0.0 ? k : last;
-            sel = (sel < 0 && t < c2) ? k : sel;
+            last = gt0(mac) ? k : last;                  // non-negative values: integer compares
+            sel = (sel < 0 && lt_nn(t, c2)) ? k : sel;
             cum = c2;
         }
         if (sel >= 0) {
@@ -453,17 +456,17 @@ __device__ __forceinline__ int collide_event(const DevProblem& P, const RunParam
         if (cm) __syncwarp(cm);
         for (int n = 0; n < P.n_nuc; ++n) {
             const double N = __ldg(P.dens + m * P.n_nuc + n);
-            const bool use = N > 0.0;
+            const bool use = gt0(N);
             const int r0 = __ldg(P.uptr + (long long)u * P.n_nuc + n);
             const double dE = p.E - __ldg(P.nuc_e + r0);
             for (int r = 0; r < 3; ++r) {
                 const double s0 = __ldg(P.nuc_sig + 3 * (long long)r0 + r);
                 const double mac = N * __fma_rn(dE, __ldg(P.nuc_slope + 3 * (long long)r0 + r), s0);
                 const double c2 = use ? cum + mac : cum;
-                const bool pos = use && mac > 0.0;
+                const bool pos = use && gt0(mac);
                 last_n = pos ? n : last_n;
                 last_r = pos ? r : last_r;
-                const bool take = use && sel_n < 0 && t < c2;
+                const bool take = use && sel_n < 0 && lt_nn(t, c2);
                 sel_n = take ? n : sel_n;
                 sel_r = take ? r : sel_r;
                 cum = c2;
@@ -486,7 +489,7 @@ __device__ __forceinline__ int collide_event(const DevProblem& P, const RunParam
     azimuth(S, p.n, cphi, sphi, sm);
     rotate(p, mu, cphi, sphi);
     p.E = E1;
-    if (p.E < P.e_cut) return EV_CUTOFF;
+    if (lt_nn(p.E, P.e_cut)) return EV_CUTOFF;
     return EV_SCATTER;
 }
 
