@@ -254,6 +254,17 @@ __device__ __forceinline__ bool lt_nn(double a, double b) { return dbits(a) < db
 __device__ __forceinline__ bool gt0(double x) { return dbits(x) > 0; }                       // x > 0
 __device__ __forceinline__ bool lt0(double x) { return dbits(x) < 0 && (dbits(x) << 1) != 0; }  // x < 0
 __device__ __forceinline__ bool ge0(double x) { return !lt0(x); }                            // x >= 0
+// floor(x) for x >= 0 from the bits (integer instructions only); 2^31 - 1
+// from 2^31 on, as the saturating conversion gives
+__device__ __forceinline__ int floor_nn(double x)
+{
+    const long long b = dbits(x);
+    const int e = (int)((b >> 52) & 0x7FF) - 1023;
+    if (e < 0) return 0;
+    if (e > 30) return 0x7FFFFFFF;
+    const long long m = (b & 0x000FFFFFFFFFFFFFll) | 0x0010000000000000ll;
+    return (int)(m >> (52 - e));
+}
 // max(d, +0) with -0 and negatives mapped to +0 (no NaN reaches here)
 __device__ __forceinline__ double clamp0(double d) { return dbits(d) <= 0 ? 0.0 : d; }
 
@@ -599,8 +610,8 @@ __device__ __forceinline__ int sample_chi(const DevProblem& P, int m, double xi)
     const double t = xi * __ldg(cc + P.G - 1);
     int sel = -1, last = P.G - 1;
     for (int g = 0; g < P.G; ++g) {
-        sel = (sel < 0 && t < __ldg(cc + g)) ? g : sel;
-        last = __ldg(P.chi + m * P.G + g) > 0.0 ? g : last;
+        sel = (sel < 0 && lt_nn(t, __ldg(cc + g))) ? g : sel;   // non-negative: integer compares
+        last = gt0(__ldg(P.chi + m * P.G + g)) ? g : last;
     }
     return sel >= 0 ? sel : last;
 }

@@ -377,7 +377,7 @@ __device__ __forceinline__ void bank_sites(const DevProblem& P, const RunParams&
 {
     const double xf = S.first(p.n, BLK_FISSION);
     const double t = ((X.nsf * X.inv_st) * R.inv_k) + xf;
-    const int nf = (int)floor(t);
+    const int nf = floor_nn(t);   // t >= 0
     for (int c = 0; c < nf; ++c) {
         const double xs = S.first(p.n, BLK_SITE + (uint32_t)c);
         const int gs = sample_chi(P, m, xs);
@@ -509,7 +509,7 @@ __device__ __forceinline__ int surface_event(const DevProblem& P, Particle& p)
     int i = cell_i(p.cell), j = cell_j(p.cell), k = cell_k(p.cell), in = cell_in(p.cell);
     bool leak = false, refl = false, moved_xy = false, moved_z = false;
     if (f & PEND_X) {
-        const bool hi = p.u > 0.0;
+        const bool hi = gt0(p.u);
         if (hi ? (i == P.nx - 1) : (i == 0)) {
             if (P.bc[hi ? 1 : 0] == 1) {
                 p.u = -p.u;
@@ -522,7 +522,7 @@ __device__ __forceinline__ int surface_event(const DevProblem& P, Particle& p)
         }
     }
     if (f & PEND_Y) {
-        const bool hi = p.v > 0.0;
+        const bool hi = gt0(p.v);
         if (hi ? (j == P.ny - 1) : (j == 0)) {
             if (P.bc[hi ? 3 : 2] == 1) {
                 p.v = -p.v;
@@ -535,7 +535,7 @@ __device__ __forceinline__ int surface_event(const DevProblem& P, Particle& p)
         }
     }
     if (f & PEND_Z) {
-        const bool hi = p.w > 0.0;
+        const bool hi = gt0(p.w);
         if (hi ? (k == P.nz - 1) : (k == 0)) {
             if (P.bc[hi ? 5 : 4] == 1) {
                 p.w = -p.w;
