@@ -265,6 +265,11 @@ __device__ __forceinline__ int floor_nn(double x)
     const long long m = (b & 0x000FFFFFFFFFFFFFll) | 0x0010000000000000ll;
     return (int)(m >> (52 - e));
 }
+// -x by flipping the sign bit (an integer instruction; the same value)
+__device__ __forceinline__ double flip_sign(double x)
+{
+    return __longlong_as_double(dbits(x) ^ (long long)0x8000000000000000ull);
+}
 // max(d, +0) with -0 and negatives mapped to +0 (no NaN reaches here)
 __device__ __forceinline__ double clamp0(double d) { return dbits(d) <= 0 ? 0.0 : d; }
 

@@ -512,8 +512,8 @@ __device__ __forceinline__ int surface_event(const DevProblem& P, Particle& p)
         const bool hi = gt0(p.u);
         if (hi ? (i == P.nx - 1) : (i == 0)) {
             if (P.bc[hi ? 1 : 0] == 1) {
-                p.u = -p.u;
-                p.iu = -p.iu;
+                p.u = flip_sign(p.u);
+                p.iu = flip_sign(p.iu);
                 refl = true;
             } else leak = true;
         } else {
@@ -525,8 +525,8 @@ __device__ __forceinline__ int surface_event(const DevProblem& P, Particle& p)
         const bool hi = gt0(p.v);
         if (hi ? (j == P.ny - 1) : (j == 0)) {
             if (P.bc[hi ? 3 : 2] == 1) {
-                p.v = -p.v;
-                p.iv = -p.iv;
+                p.v = flip_sign(p.v);
+                p.iv = flip_sign(p.iv);
                 refl = true;
             } else leak = true;
         } else {
@@ -538,8 +538,8 @@ __device__ __forceinline__ int surface_event(const DevProblem& P, Particle& p)
         const bool hi = gt0(p.w);
         if (hi ? (k == P.nz - 1) : (k == 0)) {
             if (P.bc[hi ? 5 : 4] == 1) {
-                p.w = -p.w;
-                p.iw = -p.iw;
+                p.w = flip_sign(p.w);
+                p.iw = flip_sign(p.iw);
                 refl = true;
             } else leak = true;
         } else {
