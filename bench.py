@@ -466,6 +466,16 @@ def _hbm_roof(ev, seconds):
             "what": f"{B_EVENT} algorithmic bytes/event, {peak_kind} peak"}
 
 
+def _alu_roof(ops_per_event, ev, seconds, what):
+    """FP64-pipe roofline of a whole run: executed FP64 operations per event
+    (measured by ncu) times events, over the run's device time."""
+    _, fmax, _ = _peaks()
+    peak = N_SM * FP64_OPS_PER_CLK_PER_SM * fmax * 1e6 / 1e12
+    ach = ops_per_event * ev / seconds / 1e12
+    return {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak, "traffic": None,
+            "what": what, "peak_source": f"derived: {N_SM} SMs x {FP64_OPS_PER_CLK_PER_SM:g} FP64/clk x {fmax:.0f} MHz"}
+
+
 def run_batched_workload(args):
     import torch
     ws, rank, tb, inputs = _setup(torch)
@@ -555,9 +565,14 @@ def run_ce_workload(args):
         from paper_2506_00263_gb300 import parallel
         t, ev_all, _ = parallel.reduce_timing(t, ev_all, 0.0, device="cuda")
     if rank == 0:
-        line = _side_line(args, ws, CE_WORKLOAD, m, t, ev_all, float(args.n_hist) * args.steps * ws, sampler,
-                          _hbm_roof(ev, t), {"scheme": args.scheme, "energy_bins": args.ebins,
-                                             "histories": args.n_hist, "remap_every": opts.remap_every})
+        if (args.scheme, args.decomp, args.ebins) == ("async", "mono", 100):
+            roof = _alu_roof(FP64_OPS_CE, ev, t, f"FP64 pipe (add/mul/fma) of the run, {FP64_OPS_CE:.0f} FP64 "
+                                                 "ops/event (asynchronous monolithic, 100 bins)")
+        else:
+            roof = _hbm_roof(ev, t)
+        line = _side_line(args, ws, CE_WORKLOAD, m, t, ev_all, float(args.n_hist) * args.steps * ws, sampler, roof,
+                          {"scheme": args.scheme, "energy_bins": args.ebins,
+                           "histories": args.n_hist, "remap_every": opts.remap_every})
         print(json.dumps(line), flush=True)
     prob.close()
     if ws > 1:
@@ -753,6 +768,9 @@ def run_lattice_sweep(args):
 # The arithmetic per event is the same in every scheme (the decomposed one
 # only repeats table loads).
 FP64_OPS_LATTICE = 55.0
+# The same for the continuous-energy pin cell (1e6 histories, 100 energy bins,
+# asynchronous monolithic scheme): source pre-sampling and transport kernels.
+FP64_OPS_CE = 121.9
 # DRAM bytes (read + write) of one batch's transport (source pre-sampling and
 # transport kernels; one 1e6-history lattice batch sourced from the fission
 # bank, asynchronous monolithic scheme, 512 events between remaps), from one
