@@ -715,9 +715,12 @@ def run_baseline_table(args):
     adj = measure_adjoint(torch, tb, inputs, 3, 2, tb.DECOMP_MONO)
     rows.append({"config": "C5 gradient / forward time", "gradient_over_forward": adj["gradient_over_forward"],
                  "forward_ms": adj["forward_ms"], "backward_ms": adj["backward_ms"]})
+    # FP64 fraction where the operation count was measured for the configuration
+    ops = {"C2 7-group lattice, async": FP64_OPS_LATTICE, "C2 7-group lattice, stack": FP64_OPS_LATTICE,
+           "C3 CE pin cell": FP64_OPS_CE}
     for r in rows:
-        if "gpu_events_per_s" in r:
-            r["fp64_issue_fraction"] = r["gpu_events_per_s"] * FP64_OPS_LATTICE / fp64_peak
+        if r["config"] in ops:
+            r["fp64_issue_fraction"] = r["gpu_events_per_s"] * ops[r["config"]] / fp64_peak
             r["hbm_fraction"] = r["gpu_events_per_s"] * B_EVENT / (hbm * 1e9)
         print(json.dumps(r), flush=True)
     pool.close()
