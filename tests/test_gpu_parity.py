@@ -262,6 +262,18 @@ def test_invalid_options_rejected():
     prob.close()
 
 
+def test_invalid_energy_edges_rejected():
+    """The energy tally's bin search compares bit patterns, so its edges must
+    be ascending and non-negative; problem creation refuses others."""
+    spec = inputs.ce_pin_cell(n_points=2000, n_res=10, n_ebins=4)
+    for edges in (np.array([-1.0, 1.0, 10.0, 100.0, 1e3]), np.array([1.0, 10.0, 5.0, 100.0, 1e3])):
+        with pytest.raises(tb.TransportError) as e:
+            tb.Problem(spec.replace(energy_edges=edges))
+        assert e.value.status == tb.TR_ERR_INVALID
+    ok = tb.Problem(spec.replace(energy_edges=np.array([0.0, 1.0, 10.0, 100.0, 2e7])))
+    ok.close()
+
+
 def test_virtual_ranks_sum_equals_single_run():
     """Three contiguous shards (first_history) run separately and combined in
     rank order reproduce the single run: the multi-GPU replica/shard path
