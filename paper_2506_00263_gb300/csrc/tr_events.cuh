@@ -223,6 +223,38 @@ __device__ __forceinline__ bool source_particle(const DevProblem& P, const RunPa
 // Step event: lookup, distance to collision vs. surface, move, tally.
 // Leaves the outcome in p.pend.  Returns the lookup for the collision.
 // ---------------------------------------------------------------------------
+// Timed problems only, out of line so that untimed steps carry only a branch
+// and a call: the track length spent in each uniform bin of [t0, t1]
+// (t0 < t1), and a particle's 1/v and distance to census.
+static __device__ __noinline__ void time_bins(double* tally, int n_tbins, double tb_w, double t0, double t1,
+                                              double inv_v)
+{
+    int b = (int)floor(t0 / tb_w);
+    if (b < 0) b = 0;
+    for (; b < n_tbins; ++b) {
+        double lo = (double)b * tb_w, hi = (double)(b + 1) * tb_w;
+        if (lo >= t1) break;
+        lo = fmax(lo, t0);
+        hi = fmin(hi, t1);
+        if (hi > lo) atomicAdd(tally + b, (hi - lo) / inv_v);
+    }
+}
+
+struct CensusStep {
+    double dcen, inv_v;
+};
+
+template <bool CE>
+static __device__ __noinline__ CensusStep census_step(double v_c, const double* inv_vel, double t_cen, double E, int g,
+                                                      double t)
+{
+    CensusStep r;
+    r.inv_v = CE ? 1.0 / (v_c * sqrt(E)) : __ldg(inv_vel + g);
+    const double left = t_cen - t;
+    r.dcen = left > 0.0 ? left / r.inv_v : 0.0;
+    return r;
+}
+
 // Forward tally sink: track-length scores into the tallies and the per-lane
 // scalar accumulators.
 struct FwdSink {
@@ -246,15 +278,7 @@ struct FwdSink {
     __device__ __forceinline__ void time_segment(const DevProblem& P, double t0, double t1, double inv_v)
     {
         if (P.n_tbins <= 0 || !(t1 > t0)) return;
-        int b = (int)floor(t0 / P.tb_w);
-        if (b < 0) b = 0;
-        for (; b < P.n_tbins; ++b) {
-            double lo = (double)b * P.tb_w, hi = (double)(b + 1) * P.tb_w;
-            if (lo >= t1) break;
-            lo = fmax(lo, t0);
-            hi = fmin(hi, t1);
-            if (hi > lo) atomicAdd(T.time + b, (hi - lo) / inv_v);
-        }
+        time_bins(T.time, P.n_tbins, P.tb_w, t0, t1, inv_v);
     }
 };
 
@@ -343,12 +367,11 @@ __device__ __forceinline__ void step_event(const DevProblem& P, const RunParams&
     bool census = false;
     double inv_v = 0.0;
     if (P.timed) {
-        inv_v = CE ? 1.0 / (P.v_c * sqrt(p.E)) : __ldg(P.inv_vel + p.g);
-        const double left = P.t_cen - p.t;
-        const double dcen = left > 0.0 ? left / inv_v : 0.0;
-        if (dcen < dist) {
+        const CensusStep c = census_step<CE>(P.v_c, P.inv_vel, P.t_cen, p.E, p.g, p.t);
+        inv_v = c.inv_v;
+        if (c.dcen < dist) {
             census = true;
-            dist = dcen;
+            dist = c.dcen;
         }
     }
     const bool escape = !census && !collided && dbits(ds) == dbits(INF);   // no surface ahead: escape
