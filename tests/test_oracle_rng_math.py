@@ -217,3 +217,16 @@ def test_ziggurat_samples_are_exponential():
         assert abs((x > t).mean() - p) < 5 * math.sqrt(p * (1 - p) / n) + 1e-6, t
     scipy_stats = pytest.importorskip("scipy.stats")
     assert scipy_stats.kstest(x, "expon").pvalue > 1e-4
+
+
+def test_isotropic_components_are_uniform():
+    """For a direction uniform on the sphere each Cartesian component is
+    uniform on [-1, 1] (Archimedes): Kolmogorov-Smirnov on all three
+    components of 40k directions, and the azimuth of (v, w) uniform."""
+    scipy_stats = pytest.importorskip("scipy.stats")
+    n = 40000
+    d = np.array([oracle.iso_dir(2, 0, i, 5) for i in range(n)])
+    for k in range(3):
+        assert scipy_stats.kstest(d[:, k], "uniform", args=(-1.0, 2.0)).pvalue > 1e-4, k
+    phi = np.arctan2(d[:, 2], d[:, 1])
+    assert scipy_stats.kstest(phi, "uniform", args=(-math.pi, 2 * math.pi)).pvalue > 1e-4
