@@ -56,3 +56,28 @@ def test_noalloc_matches_allocating_run_on_two_calls():
                                       mesh.data_ptr(), 0, scal.data_ptr())
     assert e.value.status == tb.TR_ERR_INVALID
     prob.close()
+
+
+@pytest.mark.parametrize("remap", [2, 512])
+def test_noalloc_monolithic_samples_sources_in_the_loop(remap):
+    """The allocation-free run has no pre-sampling buffer, so its monolithic
+    kernel samples sources inside the loop (with deferred collisions at 512
+    events per remap, whole events at 2): same results as the allocating run,
+    which pre-samples them."""
+    import torch
+    from paper_2506_00263_gb300 import build
+    build.build()
+    prob = tb.Problem(inputs.c5g7_lattice())
+    n = 50_021
+    kw = dict(n_histories=n, seed=5, scheme=tb.SCHEME_ASYNC, decomposition=tb.DECOMP_MONO, remap_every=remap)
+    ref = prob.run_fixed_source(tb.RunOpts(**kw))
+    ref_mesh = prob.tally(tb.TALLY_MESH)
+    ref_scal = prob.tally(tb.TALLY_SCALARS)
+    mesh = torch.empty(ref_mesh.size, dtype=torch.float64, device="cuda")
+    scal = torch.empty(3, dtype=torch.float64, device="cuda")
+    st = prob.run_fixed_source_noalloc(tb.RunOpts(**kw), mesh.data_ptr(), 0, scal.data_ptr())
+    assert np.array_equal(st["final_by_type"], ref["final_by_type"])
+    assert np.array_equal(st["events_by_type"], ref["events_by_type"])
+    assert_tally_close(mesh.cpu().numpy(), ref_mesh, "mesh")
+    assert_tally_close(scal.cpu().numpy(), ref_scal, "scalars")
+    prob.close()
