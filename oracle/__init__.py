@@ -132,6 +132,9 @@ def lib():
         L.orc_ce_macro.restype = C.c_int
         L.orc_elastic.argtypes = [C.c_double, C.c_double, C.c_double, C.POINTER(C.c_double), C.POINTER(C.c_double)]
         L.orc_rotate.argtypes = [C.POINTER(C.c_double), C.c_double, C.c_double, C.c_double, C.POINTER(C.c_double)]
+        L.orc_azimuth.argtypes = [C.c_uint64, C.c_uint32, C.c_uint64, C.c_uint32, C.POINTER(C.c_double)]
+        L.orc_elastic_scatter.argtypes = [C.c_uint64, C.c_uint32, C.c_uint64, C.c_uint32, C.c_double, C.c_double,
+                                          C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_double)]
         L.orc_cdf_sample.argtypes = [C.POINTER(C.c_double), C.POINTER(C.c_double), C.c_int32, C.c_double]
         L.orc_cdf_sample.restype = C.c_double
         L.orc_mesh_segment.argtypes = [C.POINTER(OrcProblem), C.POINTER(C.c_double), C.POINTER(C.c_double),
@@ -363,6 +366,23 @@ def elastic(A, E, mu_cm):
     e, mu = C.c_double(), C.c_double()
     lib().orc_elastic(A, E, mu_cm, C.byref(e), C.byref(mu))
     return e.value, mu.value
+
+
+def azimuth(seed, tag, hid, n):
+    """(cos phi, sin phi) of event n of history hid (the CE scatter azimuth)."""
+    o = (C.c_double * 2)()
+    lib().orc_azimuth(seed, tag, hid, n, o)
+    return o[0], o[1]
+
+
+def elastic_scatter(seed, tag, hid, n, A, E, d):
+    """The continuous-energy elastic scatter of event n of history hid off a
+    target of mass ratio A: (outgoing direction, outgoing energy)."""
+    a = (C.c_double * 3)(*d)
+    o = (C.c_double * 3)()
+    e = C.c_double()
+    lib().orc_elastic_scatter(seed, tag, hid, n, float(A), float(E), a, o, C.byref(e))
+    return np.array(o[:]), e.value
 
 
 def rotate(d, mu, cphi, sphi):

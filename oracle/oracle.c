@@ -319,6 +319,12 @@ static void azimuth(uint64_t seed, uint32_t tag, uint64_t id, uint32_t n, double
     *sphi = (2.0 * (a * b)) * inv_s;
 }
 
+/* The azimuth of event n of history id: out = (cos phi, sin phi). */
+void orc_azimuth(uint64_t seed, uint32_t tag, uint64_t id, uint32_t n, double out[2])
+{
+    azimuth(seed, tag, id, n, &out[0], &out[1]);
+}
+
 void orc_iso_dir(uint64_t seed, uint32_t tag, uint64_t id, uint32_t n, double dir[3])
 {
     double a, b, a2, b2, s;
@@ -360,6 +366,23 @@ void orc_elastic(double A, double E, double mu_cm, double *E_out, double *mu_lab
     double inv_ap1sq = 1.0 / ((A + 1.0) * (A + 1.0));
     *E_out = (E * q) * inv_ap1sq;
     *mu_lab = (1.0 + A * mu_cm) / sqrt(q);
+}
+
+/* The elastic scatter of event n of history id off a target of mass ratio A:
+ * the CM cosine from block BLK_ANGLE, the lab energy and cosine, the azimuth,
+ * and the incoming direction d rotated into d_out.  The continuous-energy
+ * collision runs exactly this. */
+void orc_elastic_scatter(uint64_t seed, uint32_t tag, uint64_t id, uint32_t n, double A, double E, const double d[3],
+                         double d_out[3], double *E_out)
+{
+    double xa[2];
+    rng_block(seed, tag, id, n, BLK_ANGLE, xa);
+    double mu_cm = 2.0 * xa[0] - 1.0;
+    double mu;
+    orc_elastic(A, E, mu_cm, E_out, &mu);
+    double cphi, sphi;
+    azimuth(seed, tag, id, n, &cphi, &sphi);
+    orc_rotate(d, mu, cphi, sphi, d_out);
 }
 
 /* Inverse-CDF sample from a tabulated CDF (e[k], p[k]), k < n: the largest k
@@ -948,14 +971,8 @@ static void collide(ctx *C, particle *p, int m, const xsval *X, double xi_react)
         return;
     }
     double A = P->nuc_awr[X->term_nuc[sel]];
-    double xa[2];
-    rng_block(C->seed, C->tag, p->id, p->n, BLK_ANGLE, xa);
-    double mu_cm = 2.0 * xa[0] - 1.0;
-    double E1, mu;
-    orc_elastic(A, p->E, mu_cm, &E1, &mu);
-    double cphi, sphi, nd[3];
-    azimuth(C->seed, C->tag, p->id, p->n, &cphi, &sphi);
-    orc_rotate(p->d, mu, cphi, sphi, nd);
+    double E1, nd[3];
+    orc_elastic_scatter(C->seed, C->tag, p->id, p->n, A, p->E, p->d, nd, &E1);
     p->d[0] = nd[0]; p->d[1] = nd[1]; p->d[2] = nd[2];
     p->E = E1;
     C->events_by_type[ORC_SCATTER]++;

@@ -133,6 +133,9 @@ int orc_ce_macro(const orc_problem *P, int m, double E, double out[2]);
 void orc_zig_table(double out[1024]);
 void orc_elastic(double A, double E, double mu_cm, double *E_out, double *mu_lab);
 void orc_rotate(const double dir[3], double mu, double cphi, double sphi, double out[3]);
+void orc_azimuth(uint64_t seed, uint32_t tag, uint64_t id, uint32_t n, double out[2]);
+void orc_elastic_scatter(uint64_t seed, uint32_t tag, uint64_t id, uint32_t n, double A, double E, const double d[3],
+                         double d_out[3], double *E_out);
 double orc_cdf_sample(const double *e, const double *p, int32_t n, double xi);
 double orc_mesh_segment(const orc_problem *P, const double p0[3], const double dir[3], double len, double *mesh);
 int64_t orc_nuclide_index(const double *e, int64_t n, double E);

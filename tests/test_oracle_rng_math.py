@@ -230,3 +230,85 @@ def test_isotropic_components_are_uniform():
         assert scipy_stats.kstest(d[:, k], "uniform", args=(-1.0, 2.0)).pvalue > 1e-4, k
     phi = np.arctan2(d[:, 2], d[:, 1])
     assert scipy_stats.kstest(phi, "uniform", args=(-math.pi, 2 * math.pi)).pvalue > 1e-4
+
+
+# ------------------------------------------ the continuous-energy scatter direction
+# (the collision's elastic scatter, driven through the oracle's own helper:
+# the CM cosine, the azimuth from the disk point and the lab rotation)
+
+def test_scatter_azimuth_is_a_unit_pair_and_uniform():
+    """cos^2 phi + sin^2 phi = 1 to rounding, and phi uniform on (-pi, pi]
+    (Kolmogorov-Smirnov): a dropped factor 2 in sin phi = 2ab/s, or a^2 + b^2
+    in place of a^2 - b^2, breaks the first; a one-sided disk point the second."""
+    from scipy import stats
+    n = 20000
+    cs = np.array([oracle.azimuth(5, 0, i, 7) for i in range(n)])
+    assert np.all(np.abs(cs[:, 0] ** 2 + cs[:, 1] ** 2 - 1.0) < 4e-16 * 4)
+    phi = np.arctan2(cs[:, 1], cs[:, 0])
+    assert stats.kstest((phi + math.pi) / (2 * math.pi), "uniform").pvalue > 1e-4
+    # quadrants equally likely (sign errors in a or b skew them)
+    q = (cs[:, 0] > 0).astype(int) * 2 + (cs[:, 1] > 0)
+    counts = np.bincount(q, minlength=4)
+    assert np.all(np.abs(counts - n / 4) < 5 * math.sqrt(n * 3 / 16))
+    # phi is twice the polar angle of the accepted disk point (a, b) of the
+    # event's rejection tries (blocks 3 + t): the double-angle identity, checked
+    # with atan2 on the point itself
+    for i in range(0, n, 7):
+        for t in range(64):
+            w = _block_words(5, 0, i, 7, 3 + t)
+            a = 2.0 * oracle.uniform(w[0], w[1]) - 1.0
+            b = 2.0 * oracle.uniform(w[2], w[3]) - 1.0
+            if 0.0 < a * a + b * b <= 1.0:
+                break
+        two_theta = 2.0 * math.atan2(b, a)
+        got = math.atan2(cs[i, 1], cs[i, 0])
+        assert abs(math.remainder(got - two_theta, 2 * math.pi)) < 1e-12, (i, got, two_theta)
+
+
+@pytest.mark.parametrize("A", [1.0, 16.0, 238.0])
+def test_elastic_scatter_direction(A):
+    """Through the collision's scatter: outgoing directions are unit vectors;
+    the cosine between incoming and outgoing direction equals the lab cosine of
+    the kinematics (to rounding, per scatter); its mean is 2/(3A); the outgoing
+    direction's azimuth about the incoming one is uniform; for a fixed incoming
+    direction the mean outgoing direction is <mu> times it."""
+    from scipy import stats
+    rng = np.random.default_rng(int(A) + 11)
+    n = 20000
+    mus, phis, outs = [], [], []
+    d_fixed = np.array([0.36, -0.48, 0.8])
+    for i in range(n):
+        if i % 2:
+            d = d_fixed
+        else:
+            d = rng.normal(size=3)
+            d /= np.linalg.norm(d)
+        o, E1 = oracle.elastic_scatter(9, 0, i, 3, A, 1e5, d)
+        # the rotation's rounding leaves the norm within a few dozen ulp of 1
+        assert abs(np.linalg.norm(o) - 1.0) < 1e-12
+        mu = float(np.dot(o, d))
+        # the lab cosine of the same CM draw, from the kinematics alone
+        e_k, mu_k = oracle.elastic(A, 1e5, 2.0 * oracle.uniform(*_block_words(9, 0, i, 3, 1)[:2]) - 1.0)
+        assert abs(mu - mu_k) < 1e-12 and E1 == e_k
+        mus.append(mu)
+        if i % 2:
+            outs.append(o)
+            # azimuth of o about d_fixed in a fixed frame (e1, e2) orthogonal to it
+            e1 = np.cross(d_fixed, [0.0, 0.0, 1.0])
+            e1 /= np.linalg.norm(e1)
+            e2 = np.cross(d_fixed, e1)
+            phis.append(math.atan2(float(np.dot(o, e2)), float(np.dot(o, e1))))
+    mus = np.array(mus)
+    sd = math.sqrt(max(1.0 / 3.0 - (2.0 / (3.0 * A)) ** 2, 1e-3))
+    assert abs(mus.mean() - 2.0 / (3.0 * A)) < 5 * sd / math.sqrt(n)
+    phis = np.array(phis)
+    assert stats.kstest((phis + math.pi) / (2 * math.pi), "uniform").pvalue > 1e-4
+    mean_out = np.array(outs).mean(axis=0)
+    mu_fixed = mus[1::2].mean()
+    assert np.all(np.abs(mean_out - mu_fixed * d_fixed) < 5 / math.sqrt(n / 2))
+
+
+def _block_words(seed, tag, hid, n, j):
+    """The four words of random block j of event n of history hid (the
+    contract's key and counter layout)."""
+    return oracle.philox((n, j, hid & 0xFFFFFFFF, hid >> 32), (seed & 0xFFFFFFFF, (seed >> 32) ^ tag))
