@@ -59,6 +59,9 @@ struct tr_problem {
     tr_run_opts last_fixed{};
     // batched launches led by this problem: the captured CUDA graph and its key
     std::vector<unsigned char> ckpt;          // state of a power iteration stopped early (tr_eig_checkpoint)
+    uint64_t fingerprint = 0;                 // hash of the geometry, cross sections, source and tally descriptions
+    std::vector<double> hplanes[3];           // host copies of the planes (checkpoint validation)
+    std::vector<int> hpin;                    // host copy: 1 where the cell holds a pin
     cudaGraphExec_t batch_graph = nullptr;
     std::vector<unsigned long long> batch_key;
     unsigned long long batch_graph_launches = 0;
@@ -212,6 +215,18 @@ static long long dbl_bits(double d)
     return b;
 }
 
+// FNV-1a, 64 bits, over a byte range (the problem fingerprint a checkpoint
+// must match).
+static uint64_t fnv1a(uint64_t h, const void* p, size_t n)
+{
+    const unsigned char* b = static_cast<const unsigned char*>(p);
+    for (size_t i = 0; i < n; ++i) {
+        h ^= b[i];
+        h *= 0x100000001B3ull;
+    }
+    return h;
+}
+
 extern "C" tr_status tr_problem_create(const tr_geometry_desc* G, const tr_xs_desc* X, const tr_source_desc* S,
                                        const tr_tally_desc* Tl, int32_t n_tallies, const tr_device_ctx* ctx,
                                        tr_problem** out)
@@ -290,6 +305,28 @@ extern "C" tr_status tr_problem_create(const tr_geometry_desc* G, const tr_xs_de
     P.cellinfo = upload(pr, info.data(), ncell, &ok);
     for (int f = 0; f < 6; ++f) P.bc[f] = G->bc[f];
     P.r2 = G->pin_radius * G->pin_radius;
+    pr->hplanes[0].assign(G->x_planes, G->x_planes + G->nx + 1);
+    pr->hplanes[1].assign(G->y_planes, G->y_planes + G->ny + 1);
+    pr->hplanes[2].assign(G->z_planes, G->z_planes + G->nz + 1);
+    pr->hpin.resize(ncell);
+    for (size_t c = 0; c < ncell; ++c) pr->hpin[c] = (G->pin_material && G->pin_material[c] >= 0) ? 1 : 0;
+    uint64_t fp = 0xCBF29CE484222325ull;
+    for (int a = 0; a < 3; ++a) fp = fnv1a(fp, pr->hplanes[a].data(), pr->hplanes[a].size() * 8);
+    fp = fnv1a(fp, info.data(), ncell * 4);
+    fp = fnv1a(fp, G->bc, sizeof(G->bc));
+    fp = fnv1a(fp, &G->pin_radius, 8);
+    if (X->kind == TR_XS_MG && X->sigma_t && X->sigma_s && X->nu_sigma_f && X->chi && X->n_groups > 0) {
+        const size_t MGn = (size_t)M * X->n_groups;
+        fp = fnv1a(fp, X->sigma_t, MGn * 8);
+        fp = fnv1a(fp, X->sigma_s, MGn * X->n_groups * 8);
+        fp = fnv1a(fp, X->nu_sigma_f, MGn * 8);
+        fp = fnv1a(fp, X->chi, MGn * 8);
+    }
+    fp = fnv1a(fp, &S->kind, sizeof(S->kind));
+    fp = fnv1a(fp, S->lo, sizeof(S->lo));
+    fp = fnv1a(fp, S->hi, sizeof(S->hi));
+    if (S->source_material) fp = fnv1a(fp, S->source_material, (size_t)M);
+    pr->fingerprint = fp;
 
     // cross sections
     P.kind = X->kind;
@@ -893,9 +930,10 @@ struct EigCkpt {
     int32_t scheme, decomposition, mesh_size, energy_size, n_mat, G, nall, pad;
     double k0, bank_factor, k, ksum, ksq, kernel_ms;
     uint64_t tlaunch;
+    uint64_t fingerprint;              // the problem's (geometry, cross sections, source, tallies)
     unsigned long long counts[16];
 };
-static const char EIG_MAGIC[8] = {'T', 'R', 'E', 'I', 'G', 'C', 'K', '1'};
+static const char EIG_MAGIC[8] = {'T', 'R', 'E', 'I', 'G', 'C', 'K', '2'};
 
 static size_t eig_ckpt_bytes(uint32_t b_next, int nall, unsigned long long N)
 {
@@ -975,10 +1013,36 @@ extern "C" tr_status tr_run_power_iteration(tr_problem* pr, const tr_eig_opts* e
             h.seed != o->seed || h.problem_tag != o->problem_tag || h.scheme != o->scheme ||
             h.decomposition != o->decomposition || h.k0 != k0 || h.bank_factor != factor ||
             h.mesh_size != P.mesh_size || h.energy_size != P.energy_size || h.n_mat != P.n_mat || h.G != P.G ||
-            h.nall != nall || h.b_next < 1 || h.b_next >= nb)
+            h.nall != nall || h.b_next < 1 || h.b_next >= nb || h.fingerprint != pr->fingerprint)
             return set_err(TR_ERR_STATE, "checkpoint does not match this problem and these options");
         if (h.N > cap || eo->resume_bytes != eig_ckpt_bytes(h.b_next, nall, h.N))
             return set_err(TR_ERR_INVALID, "checkpoint size mismatch");
+        // every restored site must lie in the problem: group in range, the
+        // packed cell inside the grid (with the pin bit only where a pin
+        // is), the position finite and within that cell's planes; the
+        // transport kernels index their tables with these values
+        {
+            const unsigned char* bq = q + sizeof(h) + 24 * (size_t)h.b_next + 16 * (size_t)(nall + 1);
+            const size_t n8 = (size_t)h.N * 8, n4 = (size_t)h.N * 4;
+            for (unsigned long long i = 0; i < h.N; ++i) {
+                double x[3];
+                int32_t g;
+                uint32_t c;
+                for (int a = 0; a < 3; ++a) std::memcpy(&x[a], bq + a * n8 + 8 * i, 8);
+                std::memcpy(&g, bq + 3 * n8 + 4 * i, 4);
+                std::memcpy(&c, bq + 3 * n8 + n4 + 4 * i, 4);
+                const int ci[3] = {(int)(c & 1023u), (int)((c >> 10) & 1023u), (int)((c >> 20) & 1023u)};
+                const int nn[3] = {P.nx, P.ny, P.nz};
+                bool bad = g < 0 || g >= P.G || (c >> 31) != 0;
+                for (int a = 0; a < 3 && !bad; ++a)
+                    bad = ci[a] >= nn[a] || !std::isfinite(x[a]) || x[a] < pr->hplanes[a][ci[a]] ||
+                          x[a] > pr->hplanes[a][ci[a] + 1];
+                if (!bad && (c >> 30))
+                    bad = !pr->hpin[((size_t)ci[2] * P.ny + ci[1]) * P.nx + ci[0]];
+                if (bad) return set_err(TR_ERR_INVALID, "checkpoint source site " + std::to_string(i) +
+                                                        " lies outside the problem");
+            }
+        }
         q += sizeof(h);
         kh.assign((const double*)q, (const double*)q + h.b_next);
         q += 8 * (size_t)h.b_next;
@@ -1106,6 +1170,7 @@ extern "C" tr_status tr_run_power_iteration(tr_problem* pr, const tr_eig_opts* e
             h.ksq = ksq;
             h.kernel_ms = kernel_ms;
             h.tlaunch = tlaunch;
+            h.fingerprint = pr->fingerprint;
             TR_CUDA(cudaMemcpyAsync(h.counts, pr->counts, sizeof(h.counts), cudaMemcpyDeviceToHost, st));
             std::vector<unsigned char> buf(eig_ckpt_bytes(h.b_next, nall, N));
             unsigned char* q = buf.data() + sizeof(h);

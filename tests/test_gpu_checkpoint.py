@@ -90,3 +90,68 @@ def test_chained_stops_and_refusals():
             p.power_iteration(NPB, NI, NA, bad_opts, resume=bad_state)
         assert e.value.status == status
     p.close()
+
+
+def _bank_view(state):
+    """(N, offset of the source bank) of a serialised state: the bank (x, y,
+    z doubles, group int32, packed cell uint32, N each) ends the buffer; N is
+    the header's third 64-bit word."""
+    n = int(np.frombuffer(state, np.uint64, 1, 24)[0])
+    return n, len(state) - 32 * n
+
+
+def test_tampered_or_foreign_checkpoints_are_refused():
+    """Every restored source site is checked on the host before anything is
+    uploaded (group in range, cell inside the grid, pin bit only where a pin
+    is, position finite and inside its cell), and the state carries a
+    fingerprint of the problem it came from."""
+    spec = inputs.c5g7_lattice()
+    nz, ny, nx = spec.shape
+    p = tb.Problem(spec)
+    p.power_iteration(NPB, NI, NA, _opts(), stop_after=2)
+    s = bytes(p.eig_checkpoint())
+    n, off = _bank_view(s)
+    assert n > 0 and off > 0
+    X, Y, Z, G, CELL = 0, 8 * n, 16 * n, 24 * n, 28 * n
+    dt = {X: np.float64, Y: np.float64, Z: np.float64, G: np.int32, CELL: np.uint32}
+
+    def patched(i, **fields):
+        b = bytearray(s)
+        for name, value in fields.items():
+            f = {"x": X, "y": Y, "z": Z, "g": G, "cell": CELL}[name]
+            a = np.frombuffer(b, dt[f], n, off + f)
+            a.setflags(write=True)
+            a[i] = value
+        return bytes(b)
+
+    cells = np.frombuffer(s, np.uint32, n, off + CELL)
+    k0 = (int(cells[0]) >> 20) & 1023
+    # site 0 moved into the radial reflector cell (no pin), position inside it
+    refl = (nx - 1) | ((ny - 1) << 10) | (k0 << 20)
+    xr, yr = 0.5 * (spec.x_planes[-2] + spec.x_planes[-1]), 0.5 * (spec.y_planes[-2] + spec.y_planes[-1])
+    bad_states = [
+        patched(0, g=7),                                       # group G
+        patched(n - 1, g=-1),                                  # negative group
+        patched(3, cell=int(cells[3]) | 1023),                 # cell index beyond the grid
+        patched(5, cell=int(cells[5]) | (1 << 31)),            # stray high bit
+        patched(1, x=np.nan),                                  # non-finite position
+        patched(2, y=1e6),                                     # position outside its cell
+        patched(0, x=xr, y=yr, cell=refl | (1 << 30)),         # pin bit where the cell has no pin
+    ]
+    for bad in bad_states:
+        with pytest.raises(tb.TransportError) as e:
+            p.power_iteration(NPB, NI, NA, _opts(), resume=bad)
+        assert e.value.status == tb.TR_ERR_INVALID
+    # the same move without the pin bit is a valid site: the run resumes
+    r = p.power_iteration(NPB, NI, NA, _opts(), resume=patched(0, x=xr, y=yr, cell=refl))
+    assert r["batches_done"] == NI + NA
+    # the same shapes but other cross sections: a foreign state
+    q = tb.Problem(inputs.c5g7_lattice(xs_seed=2026))
+    with pytest.raises(tb.TransportError) as e:
+        q.power_iteration(NPB, NI, NA, _opts(), resume=s)
+    assert e.value.status == tb.TR_ERR_STATE
+    q.close()
+    # the untouched state still resumes
+    r = p.power_iteration(NPB, NI, NA, _opts(), resume=s)
+    assert r["batches_done"] == NI + NA
+    p.close()

@@ -195,8 +195,10 @@ def test_scheduler_invariance_tuning():
 
 
 def test_full_size_sampled_histories():
-    """Lattice at 1e6 histories in the benchmark's launch configuration:
-    3000 sampled histories recomputed one by one by the oracle."""
+    """Lattice at 1e6 histories with the decomposed asynchronous scheme and
+    the monolithic stack scheme: 3000 sampled histories recomputed one by one
+    by the oracle, plus conservation and tally-sum checks.  (The benchmark's
+    own configuration is compared in full in test_gpu_fullsize.py.)"""
     n = 1_000_000
     p = _problem("lattice")
     rng = np.random.default_rng(0)
