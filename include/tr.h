@@ -322,10 +322,12 @@ tr_status tr_event_log(const tr_problem *problem, uint32_t *n_events, int32_t *f
                        size_t n);
 
 /* Size of the static scratch of tr_run_fixed_source_noalloc (bytes held on
- * every GPU that loads the library) and the largest queue_capacity (particles
- * of spill space) it accepts. */
-#define TR_NOALLOC_SCRATCH_BYTES (512u * 1024u)
+ * every GPU that loads the library), the largest queue_capacity (particles
+ * of spill space) it accepts, and the most tally bins (mesh + energy + the 3
+ * scalars) a problem run through it may have. */
+#define TR_NOALLOC_SCRATCH_BYTES (1024u * 1024u)
 #define TR_NOALLOC_MAX_QUEUE_CAPACITY 4096u
+#define TR_NOALLOC_MAX_TALLY_BINS 28672u
 
 /* Fixed-source run that allocates nothing (the paper has no counterpart; it
  * exists for callers of this library that cannot allocate device memory
@@ -335,13 +337,19 @@ tr_status tr_event_log(const tr_problem *problem, uint32_t *n_events, int32_t *f
  * asynchronous scheme (opts->scheme must be TR_SCHEME_ASYNC, either
  * decomposition) and gives the same results as tr_run_fixed_source.
  *  - Scratch (error word, counters, scheduler control block, a link arena of
- *    TR_NOALLOC_MAX_QUEUE_CAPACITY particles for spills) is a file-scope
+ *    TR_NOALLOC_MAX_QUEUE_CAPACITY particles for spills, and the tally
+ *    accumulators of up to TR_NOALLOC_MAX_TALLY_BINS bins) is a file-scope
  *    __device__ array of TR_NOALLOC_SCRATCH_BYTES that each GPU loading the
  *    library holds until exit.  No cudaMalloc, cudaFree, event or stream
  *    creation happens in this call.
  *  - The first call on each device looks the array's device address up
  *    (cudaGetSymbolAddress, with that device current); make that first call
- *    before any stream capture.
+ *    before any stream capture.  With CUDA's lazy module loading, the first
+ *    call that runs a given kernel variant (scheme, decomposition, remap
+ *    frequency) also loads that kernel, which the driver may back with
+ *    device memory: make one call with the options you will use at set-up,
+ *    before the memory is reserved elsewhere; later calls with those options
+ *    take no device memory.
  *  - Every call on a device shares the array; each call clears what must
  *    start at zero.  Calls whose work overlaps on the GPU (other streams or
  *    threads) race on the array and must not be issued concurrently.
@@ -354,7 +362,8 @@ tr_status tr_event_log(const tr_problem *problem, uint32_t *n_events, int32_t *f
  *    has no timing (seconds are 0).  The problem's own tallies are left
  *    untouched.  Synchronises the problem's stream before returning.
  *  - Errors: TR_ERR_INVALID for a non-async scheme, an event log request, a
- *    queue_capacity above the maximum or NULL outputs; TR_ERR_CUDA,
+ *    queue_capacity above the maximum, more tally bins than the maximum or
+ *    NULL outputs; TR_ERR_CUDA,
  *    TR_ERR_TIMEOUT, TR_ERR_CAPACITY as for tr_run_fixed_source. */
 tr_status tr_run_fixed_source_noalloc(tr_problem *problem, const tr_run_opts *opts, double *mesh_out,
                                       double *energy_out, double *scalars_out, tr_run_stats *stats);

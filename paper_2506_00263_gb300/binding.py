@@ -382,6 +382,10 @@ class Problem:
         _check(lib().tr_eig_checkpoint(self._h, buf, n.value, C.byref(n)))
         return buf.raw[:n.value]
 
+    def tally_size(self, tally_id: int) -> int:
+        """tr_tally_size: bins of one tally (0 if absent)."""
+        return int(lib().tr_tally_size(self._h, tally_id))
+
     def tally(self, tally_id: int, stddev: bool = False) -> np.ndarray:
         n = lib().tr_tally_size(self._h, tally_id)
         out = np.zeros(n)

@@ -321,9 +321,9 @@ __device__ __forceinline__ int find_problem(const unsigned long long* off, int n
 // particles come from one problem and flushes when the problem changes.
 __device__ __forceinline__ void flush_lane(Acc& acc, const Tallies& T)
 {
-    if (acc.flux != 0.0) atomicAdd(T.scal + 0, acc.flux);
-    if (acc.absn != 0.0) atomicAdd(T.scal + 1, acc.absn);
-    if (acc.prod != 0.0) atomicAdd(T.scal + 2, acc.prod);
+    if (acc.flux) fix_add_sum(T.scal + 0, acc.flux);
+    if (acc.absn) fix_add_sum(T.scal + 1, acc.absn);
+    if (acc.prod) fix_add_sum(T.scal + 2, acc.prod);
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
         if (acc.ev[i]) atomicAdd(T.ev_type + i, (unsigned long long)acc.ev[i]);

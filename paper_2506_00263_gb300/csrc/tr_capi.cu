@@ -43,7 +43,7 @@ struct tr_problem {
     std::vector<void*> owned;                 // problem data, freed at destroy
     std::map<std::string, Buf> ws;            // run workspaces, grown on demand
     // tallies: raw accumulators, results, eigenvalue statistics
-    double *raw_mesh = nullptr, *raw_energy = nullptr, *raw_scal = nullptr, *raw_time = nullptr;
+    FixBin *raw_mesh = nullptr, *raw_energy = nullptr, *raw_scal = nullptr, *raw_time = nullptr;   // fixed-point sums
     double *res_mesh = nullptr, *res_energy = nullptr, *res_scal = nullptr, *res_time = nullptr;
     double *sd_mesh = nullptr, *sd_energy = nullptr, *sd_scal = nullptr;
     double *sum_all = nullptr, *sq_all = nullptr;   // mesh | energy | scalars concatenated
@@ -535,16 +535,16 @@ extern "C" tr_status tr_problem_create(const tr_geometry_desc* G, const tr_xs_de
         P.tb_w = P.n_tbins > 0 ? P.t_cen / (double)P.n_tbins : 0.0;
     }
     const size_t ms = std::max(P.mesh_size, 1), es = std::max(P.energy_size, 1);
-    pr->raw_mesh = (double*)own(pr, ms * 8);
-    pr->raw_energy = (double*)own(pr, es * 8);
-    pr->raw_scal = (double*)own(pr, 4 * 8);
+    pr->raw_mesh = (FixBin*)own(pr, ms * sizeof(FixBin));
+    pr->raw_energy = (FixBin*)own(pr, es * sizeof(FixBin));
+    pr->raw_scal = (FixBin*)own(pr, 4 * sizeof(FixBin));
     pr->res_mesh = (double*)own(pr, ms * 8);
     pr->res_energy = (double*)own(pr, es * 8);
     pr->res_scal = (double*)own(pr, 4 * 8);
     pr->sd_mesh = (double*)own(pr, ms * 8);
     pr->sd_energy = (double*)own(pr, es * 8);
     pr->sd_scal = (double*)own(pr, 4 * 8);
-    pr->raw_time = (double*)own(pr, std::max(P.n_tbins, 1) * 8);
+    pr->raw_time = (FixBin*)own(pr, std::max(P.n_tbins, 1) * sizeof(FixBin));
     pr->res_time = (double*)own(pr, std::max(P.n_tbins, 1) * 8);
     pr->sum_all = (double*)own(pr, (ms + es + 4) * 8);
     pr->sq_all = (double*)own(pr, (ms + es + 4) * 8);
@@ -562,6 +562,7 @@ extern "C" tr_status tr_problem_create(const tr_geometry_desc* G, const tr_xs_de
 extern "C" void tr_problem_destroy(tr_problem* pr)
 {
     if (!pr) return;
+    DeviceGuard dg(pr->ctx.device);
     cudaStreamSynchronize(pr->stream);
     if (pr->batch_graph) cudaGraphExecDestroy(pr->batch_graph);
     for (auto& kv : pr->ws) dev_free(pr, kv.second.p);
@@ -631,6 +632,8 @@ static tr_status check_err(tr_problem* pr)
     TR_CUDA(cudaMemcpyAsync(&h, pr->err, sizeof(h), cudaMemcpyDeviceToHost, pr->stream));
     TR_CUDA(cudaStreamSynchronize(pr->stream));
     if (h.code == ERR_CAPACITY) return set_err(TR_ERR_CAPACITY, "a queue, link arena or fission bank overflowed");
+    if (h.code == ERR_RANGE)
+        return set_err(TR_ERR_CAPACITY, "a tally contribution exceeded the fixed-point range (|score| >= 2^39)");
     if (h.code == ERR_TIMEOUT)
         return set_err(TR_ERR_TIMEOUT, "a device spin-wait exceeded max_spin or max_wait_ms (site " + std::to_string(h.where) + ")");
     if (h.code != 0) return set_err(TR_ERR_INVALID, "device reported invalid state (code " + std::to_string(h.code) + ")");
@@ -681,16 +684,17 @@ static Tallies make_tallies(tr_problem* pr, bool log)
     T.log_n = log ? pr->log_n : nullptr;
     T.log_cell = log ? pr->log_cell : nullptr;
     T.log_type = log ? pr->log_type : nullptr;
+    T.err = pr->err;
     return T;
 }
 
 static tr_status zero_raw(tr_problem* pr)
 {
     const DevProblem& P = pr->dp;
-    TR_CUDA(cudaMemsetAsync(pr->raw_mesh, 0, std::max(P.mesh_size, 1) * 8, pr->stream));
-    TR_CUDA(cudaMemsetAsync(pr->raw_energy, 0, std::max(P.energy_size, 1) * 8, pr->stream));
-    TR_CUDA(cudaMemsetAsync(pr->raw_scal, 0, 4 * 8, pr->stream));
-    TR_CUDA(cudaMemsetAsync(pr->raw_time, 0, std::max(P.n_tbins, 1) * 8, pr->stream));
+    TR_CUDA(cudaMemsetAsync(pr->raw_mesh, 0, std::max(P.mesh_size, 1) * sizeof(FixBin), pr->stream));
+    TR_CUDA(cudaMemsetAsync(pr->raw_energy, 0, std::max(P.energy_size, 1) * sizeof(FixBin), pr->stream));
+    TR_CUDA(cudaMemsetAsync(pr->raw_scal, 0, 4 * sizeof(FixBin), pr->stream));
+    TR_CUDA(cudaMemsetAsync(pr->raw_time, 0, std::max(P.n_tbins, 1) * sizeof(FixBin), pr->stream));
     return TR_OK;
 }
 
@@ -854,6 +858,7 @@ static RunParams base_params(const tr_run_opts* o, unsigned long long n)
 extern "C" tr_status tr_run_fixed_source(tr_problem* pr, const tr_run_opts* o, tr_run_stats* stats)
 {
     if (!pr) return set_err(TR_ERR_INVALID, "problem is NULL");
+    DeviceGuard dg(pr->ctx.device);
     tr_status s = validate_opts(o);
     if (s != TR_OK) return s;
     const DevProblem& P = pr->dp;
@@ -885,10 +890,10 @@ extern "C" tr_status tr_run_fixed_source(tr_problem* pr, const tr_run_opts* o, t
         return s;
     }
     const double inv = o->n_histories ? 1.0 / (double)o->n_histories : 0.0;
-    TR_CUDA(launch_scale(pr->raw_mesh, P.mesh_size, inv, pr->res_mesh, st));
-    TR_CUDA(launch_scale(pr->raw_energy, P.energy_size, inv, pr->res_energy, st));
-    TR_CUDA(launch_scale(pr->raw_scal, 3, inv, pr->res_scal, st));
-    TR_CUDA(launch_scale(pr->raw_time, P.n_tbins, inv, pr->res_time, st));
+    TR_CUDA(launch_fix_scale(pr->raw_mesh, P.mesh_size, inv, pr->res_mesh, st));
+    TR_CUDA(launch_fix_scale(pr->raw_energy, P.energy_size, inv, pr->res_energy, st));
+    TR_CUDA(launch_fix_scale(pr->raw_scal, 3, inv, pr->res_scal, st));
+    TR_CUDA(launch_fix_scale(pr->raw_time, P.n_tbins, inv, pr->res_time, st));
     unsigned long long cnt[16];
     TR_CUDA(cudaMemcpyAsync(cnt, pr->counts, sizeof(cnt), cudaMemcpyDeviceToHost, st));
     TR_CUDA(cudaStreamSynchronize(st));
@@ -954,6 +959,7 @@ extern "C" tr_status tr_eig_checkpoint(const tr_problem* pr, void* buf, size_t c
 extern "C" tr_status tr_run_power_iteration(tr_problem* pr, const tr_eig_opts* eo, tr_eig_result* res)
 {
     if (!pr || !eo || !res) return set_err(TR_ERR_INVALID, "NULL argument");
+    DeviceGuard dg(pr->ctx.device);
     if (pr->dp.kind != TR_XS_MG) return set_err(TR_ERR_INVALID, "power iteration needs multigroup data");
     if (pr->dp.timed) return set_err(TR_ERR_INVALID, "timed problems run fixed source only");
     tr_status s = validate_opts(&eo->run);
@@ -993,7 +999,7 @@ extern "C" tr_status tr_run_power_iteration(tr_problem* pr, const tr_eig_opts* e
     double k = eo->k0 > 0.0 ? eo->k0 : 1.0;
     unsigned long long N = eo->n_per_batch;
     double ksum = 0.0, ksq = 0.0;
-    std::vector<double> scal(3);
+    std::vector<FixBin> scal(3);
     bool have_src = false;
     double kernel_ms = 0.0;
     unsigned long long tlaunch = 0;
@@ -1099,15 +1105,16 @@ extern "C" tr_status tr_run_power_iteration(tr_problem* pr, const tr_eig_opts* e
         // gather them into one contiguous view for the statistics
         unsigned long long M = 0;
         TR_CUDA(cudaMemcpyAsync(&M, bank.count, 8, cudaMemcpyDeviceToHost, st));
-        TR_CUDA(cudaMemcpyAsync(scal.data(), pr->raw_scal, 3 * 8, cudaMemcpyDeviceToHost, st));
+        TR_CUDA(cudaMemcpyAsync(scal.data(), pr->raw_scal, 3 * sizeof(FixBin), cudaMemcpyDeviceToHost, st));
         TR_CUDA(cudaStreamSynchronize(st));
         if (M > cap) return set_err(TR_ERR_CAPACITY, "fission bank overflow");
         const double kb = k * ((double)M / (double)N);
         if (res->k_batch) res->k_batch[b] = kb;
-        if (res->ktl_batch) res->ktl_batch[b] = scal[2] / (double)N;
+        const double prod = fix_value(scal[2]);
+        if (res->ktl_batch) res->ktl_batch[b] = prod / (double)N;
         if (res->n_source) res->n_source[b] = N;
         kh.push_back(kb);
-        ktlh.push_back(scal[2] / (double)N);
+        ktlh.push_back(prod / (double)N);
         nsh.push_back(N);
         if (b >= eo->n_inactive) {
             const double inv = 1.0 / (double)N;
@@ -1255,6 +1262,7 @@ extern "C" tr_status tr_sensitivities(tr_problem* pr, const tr_run_opts* o, cons
                                       const double* d_grad_scalars, double* d_sigt, double* d_sigs, double* d_nusigf)
 {
     if (!pr || !o || !d_sigt || !d_sigs || !d_nusigf) return set_err(TR_ERR_INVALID, "NULL argument");
+    DeviceGuard dg(pr->ctx.device);
     if (pr->dp.kind != TR_XS_MG) return set_err(TR_ERR_INVALID, "sensitivities need multigroup data");
     if (pr->dp.timed) return set_err(TR_ERR_INVALID, "sensitivities are offered for untimed problems");
     tr_status s = validate_opts(o);
@@ -1347,10 +1355,10 @@ static tr_status enqueue_batched(tr_problem* lead, tr_problem* const* probs, int
     const cudaStream_t st = lead->stream;
     for (int32_t i = 0; i < n; ++i) {
         tr_problem* p = probs[i];
-        TR_CUDA(cudaMemsetAsync(p->raw_mesh, 0, std::max(p->dp.mesh_size, 1) * 8, st));
-        TR_CUDA(cudaMemsetAsync(p->raw_energy, 0, std::max(p->dp.energy_size, 1) * 8, st));
-        TR_CUDA(cudaMemsetAsync(p->raw_scal, 0, 4 * 8, st));
-        TR_CUDA(cudaMemsetAsync(p->raw_time, 0, std::max(p->dp.n_tbins, 1) * 8, st));
+        TR_CUDA(cudaMemsetAsync(p->raw_mesh, 0, std::max(p->dp.mesh_size, 1) * sizeof(FixBin), st));
+        TR_CUDA(cudaMemsetAsync(p->raw_energy, 0, std::max(p->dp.energy_size, 1) * sizeof(FixBin), st));
+        TR_CUDA(cudaMemsetAsync(p->raw_scal, 0, 4 * sizeof(FixBin), st));
+        TR_CUDA(cudaMemsetAsync(p->raw_time, 0, std::max(p->dp.n_tbins, 1) * sizeof(FixBin), st));
         TR_CUDA(cudaMemsetAsync(p->counts, 0, 16 * 8, st));
     }
     TR_CUDA(cudaMemsetAsync(lead->err, 0, sizeof(ErrorWord), st));
@@ -1382,6 +1390,8 @@ extern "C" tr_status tr_run_batched(tr_problem* const* probs, int32_t n, const u
         return set_err(TR_ERR_INVALID, "batched runs use the monolithic or decomposed scheme");
     if (opts->first_history != 0) return set_err(TR_ERR_INVALID, "first_history applies to single runs only");
     tr_problem* lead = probs[0];
+    if (!lead) return set_err(TR_ERR_INVALID, "NULL problem in the batch");
+    DeviceGuard dg(lead->ctx.device);
     unsigned long long total = 0;
     for (int32_t i = 0; i < n; ++i) {
         if (!probs[i]) return set_err(TR_ERR_INVALID, "NULL problem in the batch");
@@ -1436,6 +1446,7 @@ extern "C" tr_status tr_run_batched(tr_problem* const* probs, int32_t n, const u
     for (int32_t i = 0; i < n; ++i) {
         hp[i] = probs[i]->dp;
         ht[i] = make_tallies(probs[i], opts->want_event_log != 0);
+        ht[i].err = lead->err;   // the batch's one error word
         hoff[i + 1] = hoff[i] + n_histories[i];
         const double inv = n_histories[i] ? 1.0 / (double)n_histories[i] : 0.0;
         if (probs[i]->dp.mesh_size) hj.push_back({probs[i]->raw_mesh, probs[i]->res_mesh, probs[i]->dp.mesh_size, inv});
@@ -1628,6 +1639,7 @@ extern "C" size_t tr_tally_size(const tr_problem* pr, int32_t id)
 static tr_status copy_tally(const tr_problem* pr, int32_t id, double* out, size_t n, int32_t on_dev, bool sd)
 {
     if (!pr || !out) return set_err(TR_ERR_INVALID, "NULL argument");
+    DeviceGuard dg(pr->ctx.device);
     if (!pr->have_run) return set_err(TR_ERR_STATE, "no completed run");
     if (sd && !pr->have_std) return set_err(TR_ERR_STATE, "standard deviations come from power iteration only");
     const size_t want = tr_tally_size(pr, id);
@@ -1657,6 +1669,7 @@ extern "C" tr_status tr_event_log(const tr_problem* pr, uint32_t* n_events, int3
 {
     if (!pr) return set_err(TR_ERR_INVALID, "problem is NULL");
     if (!pr->have_run || pr->log_count == 0) return set_err(TR_ERR_STATE, "no event log (set want_event_log)");
+    DeviceGuard dg(pr->ctx.device);
     if (n != pr->log_count) return set_err(TR_ERR_INVALID, "n must equal the histories of the logged run");
     if (n_events) TR_CUDA(cudaMemcpyAsync(n_events, pr->log_n, n * 4, cudaMemcpyDeviceToHost, pr->stream));
     if (final_cell) TR_CUDA(cudaMemcpyAsync(final_cell, pr->log_cell, n * 4, cudaMemcpyDeviceToHost, pr->stream));

@@ -21,11 +21,18 @@
 #include <stdint.h>
 #include <cuda_runtime.h>
 
+#include "tr_fixed.cuh"
+
 namespace tr {
 
 constexpr int EV_SOURCE = 0, EV_SCATTER = 1, EV_ABSORB = 2, EV_SURF_INTERNAL = 3, EV_SURF_REFLECT = 4,
               EV_LEAK = 5, EV_CUTOFF = 6, EV_MAXEV = 7;
-constexpr int ERR_NONE = 0, ERR_CAPACITY = 3, ERR_TIMEOUT = 4, ERR_INVALID = 1;
+// Outcome of a collision whose scatter leaves the energy below the cutoff:
+// the event counts as a scatter and the history ends with final type CUTOFF
+// (as an event that reaches the event cap counts as its own type and ends
+// with MAXEV).  Never stored: finish_event maps it.
+constexpr int EV_SCATTER_CUTOFF = 8;
+constexpr int ERR_NONE = 0, ERR_CAPACITY = 3, ERR_TIMEOUT = 4, ERR_INVALID = 1, ERR_RANGE = 5;
 
 // Optional lane-occupancy counters (diagnostic builds with -DTR_PROFILE_LANES
 // only): per site, the number of warp arrivals and the active lanes summed.
@@ -171,18 +178,32 @@ struct Particle {
     unsigned prob;                     // problem index within a batched launch (0 otherwise)
 };
 
-// Tally accumulators written by kernels (raw sums, normalised later).
+struct ErrorWord {
+    int code;
+    int where;
+};
+
+// Tally accumulators written by kernels: raw fixed-point sums (tr_fixed.cuh),
+// converted and normalised after the run.
 struct Tallies {
-    double *mesh;                      // mesh_size
-    double *energy;                    // energy_size
-    double *scal;                      // 3: flux, absorption, production
-    double *time;                      // n_tbins (timed problems)
+    FixBin *mesh;                      // mesh_size
+    FixBin *energy;                    // energy_size
+    FixBin *scal;                      // 3: flux, absorption, production
+    FixBin *time;                      // n_tbins (timed problems)
     unsigned long long *ev_type;       // 8 event counts
     unsigned long long *fin_type;      // 8 final-type counts
     uint32_t *log_n;
     int32_t *log_cell;
     uint8_t *log_type;
+    ErrorWord *err;                    // a contribution beyond the fixed-point range sets ERR_RANGE
 };
+
+// Record a contribution beyond the fixed-point range (never expected: it
+// needs a single track-length score of 2^39).
+__device__ __forceinline__ void tally_range_error(const Tallies& T)
+{
+    if (T.err) atomicCAS(&T.err->code, 0, ERR_RANGE);
+}
 
 // Fission bank (unordered during a batch; ordered by (parent, site) later).
 struct Bank {
@@ -193,11 +214,6 @@ struct Bank {
     unsigned long long *count;
     unsigned long long capacity;
     unsigned *site_count;              // per parent: sites banked (written at death)
-};
-
-struct ErrorWord {
-    int code;
-    int where;
 };
 
 // ---------------------------------------------------------------------------

@@ -15,18 +15,35 @@ namespace tr {
 constexpr unsigned PEND_X = 1u, PEND_Y = 2u, PEND_Z = 4u, PEND_CYL = 8u, PEND_ESCAPE = 16u, PEND_COLLIDE = 32u,
                    PEND_CENSUS = 64u;
 
-// Per-thread accumulators for the always-on scalar tallies and event counts.
+// Per-thread accumulators for the always-on scalar tallies (sums of rounded
+// fixed-point contributions, tr_fixed.cuh) and event counts.
 struct Acc {
-    double flux, absn, prod;
+    long long flux, absn, prod;
     unsigned ev[8];
     unsigned fin[8];
     __device__ __forceinline__ void zero()
     {
-        flux = absn = prod = 0.0;
+        flux = absn = prod = 0;
 #pragma unroll
         for (int i = 0; i < 8; ++i) ev[i] = fin[i] = 0u;
     }
 };
+
+// Add contribution c to a per-thread scalar sum a (bin: its tally bin, where
+// the sum is spilled before it could overflow, and where a contribution too
+// large for the per-thread sum goes directly).
+__device__ __forceinline__ void acc_add(long long& a, FixBin* bin, double c, const Tallies& T)
+{
+    if (fix_small(c)) {
+        a += fix_round(c);
+        if (fix_sum_full(a)) {
+            fix_add_sum(bin, a);
+            a = 0;
+        }
+    } else if (!fix_add(bin, c)) {
+        tally_range_error(T);
+    }
+}
 
 __device__ __forceinline__ Stream make_stream(const RunParams& R, unsigned id)
 {
@@ -48,8 +65,11 @@ __device__ __forceinline__ Stream make_stream(const RunParams& R, unsigned id)
 // Mesh-tally operations: add the piece to the tally, or weight it by an
 // upstream gradient (adjoint).
 struct MeshAtomic {
-    double* mesh;
-    __device__ __forceinline__ void operator()(int i, double l) const { atomicAdd(mesh + i, l); }
+    const Tallies& T;
+    __device__ __forceinline__ void operator()(int i, double l) const
+    {
+        if (!fix_add(T.mesh + i, l)) tally_range_error(T);
+    }
 };
 struct MeshWeighted {
     const double* g;
@@ -143,7 +163,7 @@ __device__ __forceinline__ void mesh_tally(const DevProblem& P, Op& op, const Pa
 }
 
 // Energy-bin flux tally per material: bin = largest b with e[b] <= E < e[b+1].
-__device__ __forceinline__ void energy_tally(const DevProblem& P, double* __restrict__ etal, int m, double E, double L)
+__device__ __forceinline__ void energy_tally(const DevProblem& P, const Tallies& T, int m, double E, double L)
 {
     const int nb = P.n_ebins;
     // E > 0 and the edges are non-negative (checked at problem creation):
@@ -155,7 +175,7 @@ __device__ __forceinline__ void energy_tally(const DevProblem& P, double* __rest
         const int mid = (lo + hi) >> 1;
         if (dbits(__ldg(P.e_edges + mid)) <= eb) lo = mid; else hi = mid;
     }
-    atomicAdd(etal + m * nb + lo, L);
+    if (!fix_add(T.energy + m * nb + lo, L)) tally_range_error(T);
 }
 
 // ---------------------------------------------------------------------------
@@ -226,8 +246,8 @@ __device__ __forceinline__ bool source_particle(const DevProblem& P, const RunPa
 // Timed problems only, out of line so that untimed steps carry only a branch
 // and a call: the track length spent in each uniform bin of [t0, t1]
 // (t0 < t1), and a particle's 1/v and distance to census.
-static __device__ __noinline__ void time_bins(double* tally, int n_tbins, double tb_w, double t0, double t1,
-                                              double inv_v)
+static __device__ __noinline__ void time_bins(FixBin* tally, ErrorWord* err, int n_tbins, double tb_w, double t0,
+                                              double t1, double inv_v)
 {
     int b = (int)floor(t0 / tb_w);
     if (b < 0) b = 0;
@@ -236,7 +256,7 @@ static __device__ __noinline__ void time_bins(double* tally, int n_tbins, double
         if (lo >= t1) break;
         lo = fmax(lo, t0);
         hi = fmin(hi, t1);
-        if (hi > lo) atomicAdd(tally + b, (hi - lo) / inv_v);
+        if (hi > lo && !fix_add(tally + b, (hi - lo) / inv_v) && err) atomicCAS(&err->code, 0, ERR_RANGE);
     }
 }
 
@@ -264,21 +284,21 @@ struct FwdSink {
     __device__ __forceinline__ void segment(const DevProblem& P, const Particle& p, double x0, double y0, double z0,
                                             double dist, int m, const XS& X)
     {
-        acc.flux += dist;
-        acc.absn = __fma_rn(dist, X.sa, acc.absn);   // tallies: compared within tolerance, fused freely
-        acc.prod = __fma_rn(dist, X.nsf, acc.prod);
+        acc_add(acc.flux, T.scal + 0, dist, T);
+        acc_add(acc.absn, T.scal + 1, dist * X.sa, T);
+        if (!CE) acc_add(acc.prod, T.scal + 2, dist * X.nsf, T);   // continuous energy: nu Sigma_f = 0
         if (P.has_mesh && gt0(dist)) {
             const int goff = (!CE && P.by_group) ? p.g * P.mesh_vox : 0;
-            MeshAtomic op{T.mesh};
+            MeshAtomic op{T};
             mesh_tally(P, op, p, x0, y0, z0, dist, goff);
         }
-        if (CE && P.n_ebins > 0 && gt0(dist)) energy_tally(P, T.energy, m, p.E, dist);
+        if (CE && P.n_ebins > 0 && gt0(dist)) energy_tally(P, T, m, p.E, dist);
     }
     // time bins: the track length spent in each bin of [t0, t1]
     __device__ __forceinline__ void time_segment(const DevProblem& P, double t0, double t1, double inv_v)
     {
         if (P.n_tbins <= 0 || !(t1 > t0)) return;
-        time_bins(T.time, P.n_tbins, P.tb_w, t0, t1, inv_v);
+        time_bins(T.time, T.err, P.n_tbins, P.tb_w, t0, t1, inv_v);
     }
 };
 
@@ -512,7 +532,7 @@ __device__ __forceinline__ int collide_event(const DevProblem& P, const RunParam
     azimuth(S, p.n, cphi, sphi, sm);
     rotate(p, mu, cphi, sphi);
     p.E = E1;
-    if (lt_nn(p.E, P.e_cut)) return EV_CUTOFF;
+    if (lt_nn(p.E, P.e_cut)) return EV_SCATTER_CUTOFF;
     return EV_SCATTER;
 }
 
@@ -597,7 +617,9 @@ __device__ __forceinline__ bool finish_event(const DevProblem& P, const RunParam
                                              const Tallies& T, Acc& acc, const Bank& B)
 {
     TR_LANES(22);
-    acc.ev[type] += 1u;
+    const bool sc = type == EV_SCATTER_CUTOFF;
+    acc.ev[sc ? EV_SCATTER : type] += 1u;
+    if (sc) type = EV_CUTOFF;
     p.n += 1u;
     bool alive = (type == EV_SCATTER || type == EV_SURF_INTERNAL || type == EV_SURF_REFLECT);
     if (alive && p.n >= R.max_events) {
@@ -767,15 +789,21 @@ __device__ __forceinline__ int next_queue_after_step(const Particle& p)
     return p.pend == PEND_COLLIDE ? Q_COLLIDE : Q_SURFACE;
 }
 
-// Warp-reduce the per-lane accumulators and add them to the global tallies.
+// Warp-reduce the per-lane accumulators and add them to the global tallies
+// (integer sums: the result does not depend on the order).
 __device__ __forceinline__ void flush_acc(const Acc& acc, const Tallies& T)
 {
-    double f = acc.flux, a = acc.absn, pr = acc.prod;
+    unsigned long long sl[3], sh[3];
+    fix_split_sum(acc.flux, sl[0], sh[0]);
+    fix_split_sum(acc.absn, sl[1], sh[1]);
+    fix_split_sum(acc.prod, sl[2], sh[2]);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
-        f += __shfl_xor_sync(0xFFFFFFFFu, f, o);
-        a += __shfl_xor_sync(0xFFFFFFFFu, a, o);
-        pr += __shfl_xor_sync(0xFFFFFFFFu, pr, o);
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            sl[k] += __shfl_xor_sync(0xFFFFFFFFu, sl[k], o);
+            sh[k] += __shfl_xor_sync(0xFFFFFFFFu, sh[k], o);
+        }
     }
     unsigned ev[8], fin[8];
 #pragma unroll
@@ -784,9 +812,11 @@ __device__ __forceinline__ void flush_acc(const Acc& acc, const Tallies& T)
         fin[i] = __reduce_add_sync(0xFFFFFFFFu, acc.fin[i]);
     }
     if ((threadIdx.x & 31) == 0) {
-        if (f != 0.0) atomicAdd(T.scal + 0, f);
-        if (a != 0.0) atomicAdd(T.scal + 1, a);
-        if (pr != 0.0) atomicAdd(T.scal + 2, pr);
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            if (sl[k]) atomicAdd(&T.scal[k].lo, sl[k]);
+            if (sh[k]) atomicAdd(&T.scal[k].hi, sh[k]);
+        }
 #pragma unroll
         for (int i = 0; i < 8; ++i) {
             if (ev[i]) atomicAdd(T.ev_type + i, (unsigned long long)ev[i]);

@@ -4,6 +4,23 @@
 
 namespace tr {
 
+// Makes a device current for the duration of an entry point and restores the
+// caller's current device on every return path.
+struct DeviceGuard {
+    int prev = -1;
+    bool changed = false;
+    explicit DeviceGuard(int dev)
+    {
+        if (cudaGetDevice(&prev) == cudaSuccess && prev != dev) changed = cudaSetDevice(dev) == cudaSuccess;
+    }
+    ~DeviceGuard()
+    {
+        if (changed) cudaSetDevice(prev);
+    }
+    DeviceGuard(const DeviceGuard&) = delete;
+    DeviceGuard& operator=(const DeviceGuard&) = delete;
+};
+
 // Number of kernels launched through the launchers below (process-wide).
 unsigned long long launch_count();
 void count_launches(unsigned long long n);
@@ -62,7 +79,7 @@ cudaError_t launch_async_batched(const DevProblem& P0, const RunParams& R, const
                                  int blocks, cudaStream_t st);
 int async_batched_max_blocks_per_sm(int dec, int stash_slots);
 struct ScaleJob {
-    const double* in;
+    const FixBin* in;
     double* out;
     int n;
     double s;
@@ -80,8 +97,10 @@ cudaError_t launch_pop_copies(unsigned long long m, uint32_t key0, uint32_t key1
                               double fr, unsigned* copies, cudaStream_t st);
 cudaError_t launch_pop_write(const Bank& in, unsigned long long m, const unsigned* copies,
                              const unsigned long long* offset, const Bank& out, cudaStream_t st);
-cudaError_t launch_eig_accumulate(const double* raw, int n, double inv_n, double* sum, double* sq, cudaStream_t st);
+cudaError_t launch_eig_accumulate(const FixBin* raw, int n, double inv_n, double* sum, double* sq, cudaStream_t st);
 cudaError_t launch_scale(const double* in, int n, double s, double* out, cudaStream_t st);
+// out[i] = (value of fixed-point bin in[i]) * s
+cudaError_t launch_fix_scale(const FixBin* in, int n, double s, double* out, cudaStream_t st);
 cudaError_t launch_eig_finish(const double* sum, const double* sq, int n, double na, double* mean, double* sd,
                               cudaStream_t st);
 

@@ -6,8 +6,9 @@
 // start-up and forbids further allocations, or a latency-sensitive loop that
 // cannot accept the implicit device synchronisation of cudaMalloc/cudaFree.
 // This entry point serves them.  Its scratch -- the error word, the event
-// counters, the scheduler's control block and a small global link arena for
-// spilled particles -- lives in the file-scope array below, which every GPU
+// counters, the scheduler's control block, a small global link arena for
+// spilled particles and the tally accumulators (fixed-point sums, converted
+// into the caller's arrays at the end) -- lives in the file-scope array below, which every GPU
 // that loads the library holds until the process exits.  The caller passes
 // the inputs (a problem created earlier) and the outputs (device arrays for
 // the tallies).  Nothing here calls cudaMalloc, cudaFree, an event or stream
@@ -38,7 +39,8 @@ constexpr size_t OFF_NEXT = align256(OFF_CTL + sizeof(AsyncCtl));
 constexpr size_t OFF_TYPE = align256(OFF_NEXT + NOALLOC_LINKS * 4);
 constexpr size_t OFF_FILL = align256(OFF_TYPE + NOALLOC_LINKS * 4);
 constexpr size_t OFF_LINKS = align256(OFF_FILL + NOALLOC_LINKS * 4);
-constexpr size_t SCRATCH_USED = OFF_LINKS + LINK_SOA_BYTES;
+constexpr size_t OFF_TALLY = align256(OFF_LINKS + LINK_SOA_BYTES);
+constexpr size_t SCRATCH_USED = OFF_TALLY + (size_t)TR_NOALLOC_MAX_TALLY_BINS * sizeof(FixBin);
 static_assert(SCRATCH_USED <= TR_NOALLOC_SCRATCH_BYTES, "static scratch too small for its layout");
 
 }  // namespace
@@ -128,9 +130,13 @@ extern "C" tr_status tr_run_fixed_source_noalloc(tr_problem* problem, const tr_r
     cudaStream_t st = nullptr;
     const DevProblem* Pp = problem_device_data(problem, &dev, &st, &sms);
     const DevProblem& P = *Pp;
+    DeviceGuard dg(dev);   // the problem's device, current until return
     if ((P.mesh_size > 0 && !mesh_out) || (P.energy_size > 0 && !energy_out) || !scalars_out)
         return fail(TR_ERR_INVALID, "an output array for a present tally is NULL");
     if (P.timed) return fail(TR_ERR_INVALID, "timed problems have no output here: use tr_run_fixed_source");
+    const size_t n_bins = (size_t)P.mesh_size + (size_t)P.energy_size + 3;
+    if (n_bins > TR_NOALLOC_MAX_TALLY_BINS)
+        return fail(TR_ERR_INVALID, "mesh + energy tally bins + 3 exceed TR_NOALLOC_MAX_TALLY_BINS");
     int S = o->stash_slots > 0 ? o->stash_slots : 512;
     S = (S + 31) & ~31;
     if (S < 32 * 9 || S > 16384) return fail(TR_ERR_INVALID, "stash_slots must be in 288..16384");
@@ -171,16 +177,16 @@ extern "C" tr_status tr_run_fixed_source_noalloc(tr_problem* problem, const tr_r
     NA_CUDA(cudaMemsetAsync(A.ctl, 0, sizeof(AsyncCtl), st));
     NA_CUDA(cudaMemsetAsync(A.ctl->free_q, 0xFF, sizeof(A.ctl->free_q), st));
     NA_CUDA(cudaMemsetAsync(A.ctl->full_q, 0xFF, sizeof(A.ctl->full_q), st));
-    if (P.mesh_size > 0) NA_CUDA(cudaMemsetAsync(mesh_out, 0, (size_t)P.mesh_size * 8, st));
-    if (P.energy_size > 0) NA_CUDA(cudaMemsetAsync(energy_out, 0, (size_t)P.energy_size * 8, st));
-    NA_CUDA(cudaMemsetAsync(scalars_out, 0, 3 * 8, st));
+    FixBin* bins = reinterpret_cast<FixBin*>(base + OFF_TALLY);
+    NA_CUDA(cudaMemsetAsync(bins, 0, n_bins * sizeof(FixBin), st));
 
     Tallies T{};
-    T.mesh = mesh_out;
-    T.energy = energy_out;
-    T.scal = scalars_out;
+    T.scal = bins;
+    T.mesh = bins + 3;
+    T.energy = bins + 3 + P.mesh_size;
     T.ev_type = counts;
     T.fin_type = counts + 8;
+    T.err = err;
     if (o->n_histories > 0) {
         const int maxb = async_max_blocks_per_sm(P, A.dec, S);
         if (maxb < 1) return fail(TR_ERR_INVALID, "stash does not fit in shared memory");
@@ -197,13 +203,14 @@ extern "C" tr_status tr_run_fixed_source_noalloc(tr_problem* problem, const tr_r
     NA_CUDA(cudaStreamSynchronize(st));
     if (he.code == ERR_TIMEOUT) return fail(TR_ERR_TIMEOUT, "a device spin-wait exceeded max_spin or max_wait_ms");
     if (he.code == ERR_CAPACITY) return fail(TR_ERR_CAPACITY, "the static link arena overflowed");
+    if (he.code == ERR_RANGE) return fail(TR_ERR_CAPACITY, "a tally contribution exceeded the fixed-point range");
     if (he.code != 0) return fail(TR_ERR_INVALID, "device reported invalid state");
     if (hc.live != 0) return fail(TR_ERR_STATE, "run ended with live particles");
-    // tallies become means per source particle, in place
+    // tallies: means per source particle, into the caller's arrays
     const double inv = o->n_histories ? 1.0 / (double)o->n_histories : 0.0;
-    NA_CUDA(launch_scale(mesh_out, P.mesh_size, inv, mesh_out, st));
-    NA_CUDA(launch_scale(energy_out, P.energy_size, inv, energy_out, st));
-    NA_CUDA(launch_scale(scalars_out, 3, inv, scalars_out, st));
+    NA_CUDA(launch_fix_scale(T.mesh, P.mesh_size, inv, mesh_out, st));
+    NA_CUDA(launch_fix_scale(T.energy, P.energy_size, inv, energy_out, st));
+    NA_CUDA(launch_fix_scale(T.scal, 3, inv, scalars_out, st));
     NA_CUDA(cudaStreamSynchronize(st));
     if (stats) {
         std::memset(stats, 0, sizeof(*stats));

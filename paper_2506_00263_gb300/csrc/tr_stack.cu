@@ -320,12 +320,12 @@ __global__ void k_pop_write(Bank in, unsigned long long m, const unsigned* __res
     }
 }
 
-// Active-batch statistics: sum and sum of squares of raw / n per bin.
-__global__ void k_eig_accumulate(const double* __restrict__ raw, int n, double inv_n, double* __restrict__ sum,
+// Active-batch statistics: sum and sum of squares of (bin value) / n per bin.
+__global__ void k_eig_accumulate(const FixBin* __restrict__ raw, int n, double inv_n, double* __restrict__ sum,
                                  double* __restrict__ sq)
 {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        const double v = raw[i] * inv_n;
+        const double v = fix_value(raw[i]) * inv_n;
         sum[i] += v;
         sq[i] += v * v;
     }
@@ -336,13 +336,20 @@ __global__ void k_scale(const double* __restrict__ in, int n, double s, double* 
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) out[i] = in[i] * s;
 }
 
-// Many scalings in one launch: job j multiplies in[0..n) by s into out.
+// Bin values (fixed-point sums) times s.
+__global__ void k_fix_scale(const FixBin* __restrict__ in, int n, double s, double* __restrict__ out)
+{
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        out[i] = fix_value(in[i]) * s;
+}
+
+// Many conversions in one launch: job j writes the values of in[0..n) times s to out.
 __global__ void k_scale_jobs(const ScaleJob* __restrict__ jobs, int n_jobs)
 {
     for (int j = blockIdx.y; j < n_jobs; j += gridDim.y) {
         const ScaleJob J = jobs[j];
         for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < J.n; i += gridDim.x * blockDim.x)
-            J.out[i] = J.in[i] * J.s;
+            J.out[i] = fix_value(J.in[i]) * J.s;
     }
 }
 
@@ -439,7 +446,7 @@ cudaError_t launch_pop_write(const Bank& in, unsigned long long m, const unsigne
     return cudaGetLastError();
 }
 
-cudaError_t launch_eig_accumulate(const double* raw, int n, double inv_n, double* sum, double* sq, cudaStream_t st)
+cudaError_t launch_eig_accumulate(const FixBin* raw, int n, double inv_n, double* sum, double* sq, cudaStream_t st)
 {
     if (n <= 0) return cudaSuccess;
     count_launches(1);
@@ -452,6 +459,14 @@ cudaError_t launch_scale(const double* in, int n, double s, double* out, cudaStr
     if (n <= 0) return cudaSuccess;
     count_launches(1);
     k_scale<<<grid_for(n, 256, 1024), 256, 0, st>>>(in, n, s, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fix_scale(const FixBin* in, int n, double s, double* out, cudaStream_t st)
+{
+    if (n <= 0) return cudaSuccess;
+    count_launches(1);
+    k_fix_scale<<<grid_for(n, 256, 1024), 256, 0, st>>>(in, n, s, out);
     return cudaGetLastError();
 }
 
