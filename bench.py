@@ -34,11 +34,32 @@ N_INACTIVE, N_ACTIVE = 20, 50
 WORKLOAD = "c5g7-shaped 7-group lattice k-eigenvalue, 1e6 histories/batch, 20 inactive + 50 active batches"
 
 # Algorithmic bytes per event of an event-based implementation: the particle
-# record read and written once (position, direction, cached reciprocals of
-# the direction, group, cell, history index, event count, site count, pending
-# flags: 10 x 8 + 6 x 4 = 104 bytes each way).  Cross sections (3.5 KB) and
-# the 20.8 KB tally stay on chip.
-B_EVENT = 2 * 104
+# record read and written once per event.  Multigroup: 64 B (position and
+# direction 6 x 8 B; history index, event count, packed group and cell,
+# problem index 4 x 4 B), so 2 x 64 = 128 B; the cross sections (3.5 KB) and
+# the 20.8 KB tally stay on chip.  Continuous energy: a 72 B record (the
+# energy added) both ways, plus the lookup's grid pair (16 B) and 16 B per
+# (nuclide, reaction) term of the material (9 in the fuel): 304 B.
+B_EVENT = {"lattice": 2 * 64, "ce": 2 * 72 + 16 + 16 * 9}
+
+# The transport kernels' sources: the FP64-operation and DRAM-traffic figures
+# below were measured on the sources with the digest stored beside them, and
+# are reported as stale once the built sources differ.
+TRANSPORT_SOURCES = ("tr_device.cuh", "tr_events.cuh", "tr_fixed.cuh", "tr_kernels.h", "tr_async.cu", "tr_stack.cu")
+
+
+def kernel_digest(csrc=None):
+    """SHA-256 (16 hex digits) over the transport kernels' source files."""
+    import hashlib
+    csrc = csrc or os.path.join(ROOT, "paper_2506_00263_gb300", "csrc")
+    h = hashlib.sha256()
+    for name in TRANSPORT_SOURCES:
+        path = os.path.join(csrc, name)
+        if os.path.exists(path):
+            h.update(name.encode())
+            with open(path, "rb") as f:
+                h.update(f.read())
+    return h.hexdigest()[:16]
 
 
 def _peaks():
@@ -122,10 +143,29 @@ def _cpu_baseline(seconds_budget: float = 15.0):
     r = oracle.power_iteration(p, nper, ni, na, seed=1)
     dt = time.perf_counter() - t0
     ev = int(r["events_by_type"][1:].sum())
-    return {"value": ev / dt, "unit": "events/s", "cores": 1, "kind": "oracle",
-            "sample": f"lattice power iteration, {nper} histories/batch x {ni + na} batches "
-                      f"({ev} events, {dt:.1f} s, one host core)",
-            "histories_per_s": nper * (ni + na) / dt}
+    out = {"value": ev / dt, "unit": "events/s", "cores": 1, "kind": "oracle",
+           "sample": f"lattice power iteration, {nper} histories/batch x {ni + na} batches "
+                     f"({ev} events, {dt:.1f} s, one host core)",
+           "histories_per_s": nper * (ni + na) / dt}
+    out["all_cores"] = _cpu_baseline_all_cores()
+    return out
+
+
+def _cpu_baseline_all_cores(n_total=1_600_000):
+    """The same oracle on every host core: one batch's worth of lattice
+    histories split into contiguous id ranges, one spawned process per core
+    (the histories of a batch are independent); events/s over the slowest
+    worker's time."""
+    import multiprocessing as mp
+    nproc = os.cpu_count() or 1
+    per = max(n_total // nproc, 1)
+    with mp.get_context("spawn").Pool(nproc) as pool:
+        res = pool.map(_oracle_fixed_shard, [("lattice", per, i * per) for i in range(nproc)])
+    ev = sum(e for e, _ in res)
+    t = max(dt for _, dt in res)
+    return {"value": ev / t, "unit": "events/s", "cores": nproc, "kind": "oracle",
+            "sample": f"{per * nproc} lattice histories (fixed source, fission sites not iterated) over "
+                      f"{nproc} contiguous id ranges, one spawned process per core ({ev} events, {t:.1f} s)"}
 
 
 def run_reference(args):
@@ -229,23 +269,16 @@ def run_ours(args):
     hbm, fmax, peak_kind = _peaks()
     avg_launch = kern_s / max(kern_launches, 1)
     ev_per_launch = ev_tot / max(kern_launches, 1)
-    fp64_ops_per_event = FP64_OPS_PER_EVENT.get((args.scheme, args.decomp), FP64_OPS_LATTICE)
-    fp64_peak = N_SM * FP64_OPS_PER_CLK_PER_SM * fmax * 1e6 / 1e12     # TFLOP/s
-    if fp64_ops_per_event:
-        ach = fp64_ops_per_event * ev_per_launch / avg_launch / 1e12
-        traffic = TRAFFIC_PER_LAUNCH.get((args.scheme, args.decomp, opts.remap_every, args.n_per_batch))
-        roof = {"bound": "alu", "achieved": ach, "peak": fp64_peak, "unit": "TFLOP/s", "frac": ach / fp64_peak,
-                "traffic": traffic, "what": "FP64 pipe (add/mul/fma) of one batch's transport (source pre-sampling + transport loop), "
-                                         f"{fp64_ops_per_event:.0f} FP64 ops/event",
-                "peak_source": f"derived: {N_SM} SMs x {FP64_OPS_PER_CLK_PER_SM:g} FP64/clk x {fmax:.0f} MHz"}
-    else:
-        roof = None
-    hbm_ach = B_EVENT * ev_per_launch / avg_launch / 1e9
-    hbm_roof = {"bound": "hbm", "achieved": hbm_ach, "peak": hbm, "unit": "GB/s", "frac": hbm_ach / hbm,
-                "traffic": TRAFFIC_PER_LAUNCH.get((args.scheme, args.decomp, opts.remap_every, args.n_per_batch)),
-                "what": f"{B_EVENT} algorithmic bytes/event, {peak_kind} peak"}
-    if roof is None:
-        roof = hbm_roof
+    bench_cfg = (args.scheme, args.decomp, opts.remap_every, args.n_per_batch) == ("async", "mono", 512, N_PER_BATCH)
+    traffic, traffic_fresh = measured_figure(TRAFFIC, "lattice")
+    traffic = traffic if (traffic_fresh and bench_cfg) else None
+    hbm_roof = _hbm_roof(ev_per_launch, avg_launch, "lattice", traffic)
+    alu_roof = _alu_roof("lattice", ev_per_launch, avg_launch,
+                         "FP64 pipe (add/mul/fma) of one batch's transport (source pre-sampling + transport loop)",
+                         traffic)
+    # the binding roof is the FP64 pipe; its per-event operation count is an
+    # ncu measurement and counts only while it describes the built kernels
+    roof = alu_roof if (alu_roof and not alu_roof.get("stale")) else hbm_roof
 
     # ---- end to end through the C ABI with host buffers ----
     e2e = None
@@ -274,7 +307,11 @@ def run_ours(args):
     if rank == 0 and not args.no_extras:
         adj = measure_adjoint(torch, tb, inputs, 3, 2, decomp)
         bat = measure_batched(torch, tb, inputs, 2, 2, decomp)
+        paper = measure_paper_setting(torch, tb, spec)
+        ce = measure_ce_line(torch, tb, inputs)
         extras = {
+            "paper_setting": paper,
+            "ce_pin_cell": ce,
             "gradient": {"workload": ADJ_WORKLOAD, "forward_ms": adj["forward_ms"], "backward_ms": adj["backward_ms"],
                          "gradient_over_forward": adj["gradient_over_forward"]},
             "batched": {"workload": BATCH_WORKLOAD, "events_per_s": bat["events_per_s"],
@@ -295,7 +332,7 @@ def run_ours(args):
                    "n_per_batch": args.n_per_batch, "batches": args.inactive + args.active,
                    "l2": "flushed between steps (512 MB write)"},
         "histories_per_s": hist_all / t,
-        "roofline": roof, "hbm_roofline": hbm_roof,
+        "roofline": roof, "hbm_roofline": hbm_roof, "alu_roofline": alu_roof,
         "e2e": e2e, "cpu_baseline": cpu, "gpu_launches": launches,
         "clocks": sampler.summary(),
         "transport": {"kernel_seconds": kern_s, "launches": kern_launches, "avg_launch_ms": 1e3 * avg_launch},
@@ -306,6 +343,49 @@ def run_ours(args):
     if ws > 1:
         torch.distributed.destroy_process_group()
     return 0
+
+
+PAPER_BATCHES = (2, 6)   # inactive, active batches of the paper-setting comparison (1e6 histories each)
+
+
+def measure_paper_setting(torch, tb, spec, n_per_batch=N_PER_BATCH):
+    """The lattice power iteration at the paper's setting, one event per remap
+    (whole events per pass), with asynchronous and stack-based remapping, and
+    with the default 512 events per remap, on the same batches: events/s of
+    each (CUDA events around the whole power iteration)."""
+    stream = torch.cuda.current_stream()
+    prob = tb.Problem(spec)
+    out = {"workload": f"the benchmark lattice, {n_per_batch} histories/batch, {PAPER_BATCHES[0]} inactive + "
+                       f"{PAPER_BATCHES[1]} active batches"}
+    for label, scheme, remap in (("async_1_event_per_remap", tb.SCHEME_ASYNC, 1),
+                                 ("stack_1_event_per_remap", tb.SCHEME_STACK, 1),
+                                 ("async_512_events_per_remap", tb.SCHEME_ASYNC, 512)):
+        opts = tb.RunOpts(seed=1, scheme=scheme, decomposition=tb.DECOMP_MONO, remap_every=remap)
+        prob.power_iteration(n_per_batch, 1, 2, opts)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        r = prob.power_iteration(n_per_batch, PAPER_BATCHES[0], PAPER_BATCHES[1], opts)
+        e1.record(stream)
+        e1.synchronize()
+        out[label] = int(r["events"]) / (e0.elapsed_time(e1) * 1e-3)
+    prob.close()
+    out["async_over_stack_at_1_event_per_remap"] = out["async_1_event_per_remap"] / out["stack_1_event_per_remap"]
+    return out
+
+
+def measure_ce_line(torch, tb, inputs, n=1_000_000, steps=3):
+    """The continuous-energy pin cell (1e6 histories, 100 energy bins,
+    asynchronous monolithic, 64 events per remap): events/s and rooflines."""
+    prob = tb.Problem(inputs.ce_pin_cell(n_ebins=100))
+    opts = tb.RunOpts(n_histories=n, seed=1, scheme=tb.SCHEME_ASYNC, decomposition=tb.DECOMP_MONO, remap_every=64)
+    t, ev = _time_fixed(torch, tb, prob, opts, steps, 2)
+    prob.close()
+    return {"workload": CE_WORKLOAD + f", {n} histories, 100 bins, 64 events per remap",
+            "events_per_s": ev / t, "histories_per_s": n * steps / t,
+            "hbm_roofline": _hbm_roof(ev, t, "ce"),
+            "alu_roofline": _alu_roof("ce", ev, t, "FP64 pipe (add/mul/fma) of the run")}
 
 
 BATCH_WORKLOAD = ("256 independent multigroup voxel boxes (groups from {1,2,7,20,70}, 1-8 materials, "
@@ -459,21 +539,34 @@ def _side_line(args, ws, workload, m, t, ev_all, hist_all, sampler, roof, extra)
             "cpu_baseline": None, "gpu_launches": m["launches"], "clocks": sampler.summary()}
 
 
-def _hbm_roof(ev, seconds):
+def _hbm_roof(ev, seconds, workload="lattice", traffic=None):
+    """HBM roofline: algorithmic bytes per event (B_EVENT) times events over
+    the device time, against the measured copy bandwidth."""
     hbm, _, peak_kind = _peaks()
-    ach = B_EVENT * ev / seconds / 1e9
-    return {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm, "traffic": None,
-            "what": f"{B_EVENT} algorithmic bytes/event, {peak_kind} peak"}
+    b = B_EVENT[workload]
+    ach = b * ev / seconds / 1e9
+    return {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm, "traffic": traffic,
+            "target_frac": 0.5,
+            "what": f"{b} algorithmic bytes/event (particle record read and written once), {peak_kind} peak"}
 
 
-def _alu_roof(ops_per_event, ev, seconds, what):
-    """FP64-pipe roofline of a whole run: executed FP64 operations per event
-    (measured by ncu) times events, over the run's device time."""
+def _alu_roof(workload, ev, seconds, what, traffic=None):
+    """FP64-pipe roofline: executed FP64 operations per event (an ncu
+    measurement of the kernels with the recorded source digest) times events
+    over the device time, against 152 SMs x 2 FP64 operations per clock at the
+    maximum SM clock.  Marked stale when the kernels changed since."""
+    ops, fresh = measured_figure(FP64_OPS, workload)
+    if ops is None:
+        return None
     _, fmax, _ = _peaks()
     peak = N_SM * FP64_OPS_PER_CLK_PER_SM * fmax * 1e6 / 1e12
-    ach = ops_per_event * ev / seconds / 1e12
-    return {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak, "traffic": None,
-            "what": what, "peak_source": f"derived: {N_SM} SMs x {FP64_OPS_PER_CLK_PER_SM:g} FP64/clk x {fmax:.0f} MHz"}
+    ach = ops * ev / seconds / 1e12
+    r = {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak, "traffic": traffic,
+         "what": f"{what}, {ops:g} FP64 ops/event (ncu, kernels {FP64_OPS[workload][1]})",
+         "peak_source": f"derived: {N_SM} SMs x {FP64_OPS_PER_CLK_PER_SM:g} FP64/clk x {fmax:.0f} MHz"}
+    if not fresh:
+        r["stale"] = f"measured on kernels {FP64_OPS[workload][1]}, built kernels are {kernel_digest()}"
+    return r
 
 
 def run_batched_workload(args):
@@ -490,7 +583,7 @@ def run_batched_workload(args):
         t, ev_all, hist_all = parallel.reduce_timing(t, ev_all, hist_all, device="cuda")
     if rank == 0:
         line = _side_line(args, ws, BATCH_WORKLOAD, m, t, ev_all, hist_all, sampler,
-                          _hbm_roof(m["events"], m["kernel_seconds"]),
+                          _hbm_roof(m["events"], m["kernel_seconds"], "lattice"),
                           {"problems": m["problems"], "tuning_used": m["tuning_used"]})
         line.update({"first_call_s": m["first_call_s"], "sequential_single_runs": m["sequential_single_runs"],
                      "transport": {"kernel_seconds": m["kernel_seconds"], "launches": args.steps}})
@@ -513,7 +606,7 @@ def run_adjoint_workload(args):
         t, ev_all, _ = parallel.reduce_timing(t, ev_all, 0.0, device="cuda")
     if rank == 0:
         line = _side_line(args, ws, ADJ_WORKLOAD, m, t, ev_all, None, sampler,
-                          _hbm_roof(m["events"], m["forward_ms"] * 1e-3 * args.steps), {})
+                          _hbm_roof(m["events"], m["forward_ms"] * 1e-3 * args.steps, "lattice"), {})
         line.update({k: m[k] for k in ("forward_ms", "backward_ms", "gradient_over_forward")})
         print(json.dumps(line), flush=True)
     if ws > 1:
@@ -565,11 +658,10 @@ def run_ce_workload(args):
         from paper_2506_00263_gb300 import parallel
         t, ev_all, _ = parallel.reduce_timing(t, ev_all, 0.0, device="cuda")
     if rank == 0:
-        if (args.scheme, args.decomp, args.ebins) == ("async", "mono", 100):
-            roof = _alu_roof(FP64_OPS_CE, ev, t, f"FP64 pipe (add/mul/fma) of the run, {FP64_OPS_CE:.0f} FP64 "
-                                                 "ops/event (asynchronous monolithic, 100 bins)")
-        else:
-            roof = _hbm_roof(ev, t)
+        roof = _hbm_roof(ev, t, "ce")
+        if (args.scheme, args.decomp, args.ebins, opts.remap_every) == ("async", "mono", 100, 64):
+            alu = _alu_roof("ce", ev, t, "FP64 pipe (add/mul/fma) of the run (asynchronous monolithic, 100 bins)")
+            roof = alu if (alu and not alu.get("stale")) else roof
         line = _side_line(args, ws, CE_WORKLOAD, m, t, ev_all, float(args.n_hist) * args.steps * ws, sampler, roof,
                           {"scheme": args.scheme, "energy_bins": args.ebins,
                            "histories": args.n_hist, "remap_every": opts.remap_every})
@@ -716,12 +808,17 @@ def run_baseline_table(args):
     rows.append({"config": "C5 gradient / forward time", "gradient_over_forward": adj["gradient_over_forward"],
                  "forward_ms": adj["forward_ms"], "backward_ms": adj["backward_ms"]})
     # FP64 fraction where the operation count was measured for the configuration
-    ops = {"C2 7-group lattice, async": FP64_OPS_LATTICE, "C2 7-group lattice, stack": FP64_OPS_LATTICE,
-           "C3 CE pin cell": FP64_OPS_CE}
+    kinds = {"C2 7-group lattice, async": "lattice", "C2 7-group lattice, stack": "lattice", "C3 CE pin cell": "ce",
+             "C1 one-group cube": "lattice"}
     for r in rows:
-        if r["config"] in ops:
-            r["fp64_issue_fraction"] = r["gpu_events_per_s"] * ops[r["config"]] / fp64_peak
-            r["hbm_fraction"] = r["gpu_events_per_s"] * B_EVENT / (hbm * 1e9)
+        kind = kinds.get(r["config"])
+        if kind:
+            r["hbm_fraction"] = r["gpu_events_per_s"] * B_EVENT[kind] / (hbm * 1e9)
+            ops, fresh = measured_figure(FP64_OPS, kind)
+            if ops and r["config"] != "C1 one-group cube":
+                r["fp64_issue_fraction"] = r["gpu_events_per_s"] * ops / fp64_peak
+                if not fresh:
+                    r["fp64_issue_fraction_stale"] = True
         print(json.dumps(r), flush=True)
     pool.close()
     return 0
@@ -764,22 +861,26 @@ def run_lattice_sweep(args):
 
 
 # FP64 thread-operations (dadd + dmul + dfma, divisions and square roots
-# included as executed) per transport event on the lattice workload, from an
-# ncu capture of one power-iteration step of three batches: the source
-# pre-sampling and transport kernels together
-# (sm__sass_thread_inst_executed_ops_dadd_dmul_dfma_pred_on.sum / events).
-# The arithmetic per event is the same in every scheme (the decomposed one
-# only repeats table loads).
-FP64_OPS_LATTICE = 55.0
-# The same for the continuous-energy pin cell (1e6 histories, 100 energy bins,
-# asynchronous monolithic scheme): source pre-sampling and transport kernels.
-FP64_OPS_CE = 121.9
-# DRAM bytes (read + write) of one batch's transport (source pre-sampling and
-# transport kernels; one 1e6-history lattice batch sourced from the fission
-# bank, asynchronous monolithic scheme, 512 events between remaps), from one
-# ncu capture of the current kernels: dram__bytes_read.sum + dram__bytes_write.sum.
-TRAFFIC_PER_LAUNCH = {("async", "mono", 512, 1_000_000): 219.9e6}
-FP64_OPS_PER_EVENT = {(s, d): FP64_OPS_LATTICE for s in ("async", "stack") for d in ("mono", "split")}
+# included as executed) per transport event, from an ncu capture
+# (sm__sass_thread_inst_executed_ops_dadd_dmul_dfma_pred_on.sum / events) of
+# the source pre-sampling and transport kernels: the lattice power iteration
+# (asynchronous monolithic, 512 events between remaps) and the CE pin cell
+# (1e6 histories, 100 bins, 64 events between remaps).  Each figure carries
+# the kernel_digest() of the sources it was measured on.
+FP64_OPS = {"lattice": (55.0, "be1a0aa713203f72"), "ce": (121.9, "be1a0aa713203f72")}
+# DRAM bytes (read + write) of one 1e6-history lattice batch's transport
+# (source pre-sampling and transport kernels, asynchronous monolithic, 512
+# events between remaps), dram__bytes_read.sum + dram__bytes_write.sum.
+TRAFFIC = {"lattice": (219.9e6, "be1a0aa713203f72")}
+
+
+def measured_figure(table, key):
+    """(value, fresh) of a measured per-kernel figure: fresh when it was
+    measured on the sources built now."""
+    if key not in table:
+        return None, False
+    value, digest = table[key]
+    return value, digest == kernel_digest()
 
 
 def _pinned_copy(spec, torch):

@@ -327,7 +327,7 @@ tr_status tr_event_log(const tr_problem *problem, uint32_t *n_events, int32_t *f
  * scalars) a problem run through it may have. */
 #define TR_NOALLOC_SCRATCH_BYTES (1024u * 1024u)
 #define TR_NOALLOC_MAX_QUEUE_CAPACITY 4096u
-#define TR_NOALLOC_MAX_TALLY_BINS 28672u
+#define TR_NOALLOC_MAX_TALLY_BINS 24576u
 
 /* Fixed-source run that allocates nothing (the paper has no counterpart; it
  * exists for callers of this library that cannot allocate device memory
@@ -367,6 +367,29 @@ tr_status tr_event_log(const tr_problem *problem, uint32_t *n_events, int32_t *f
  *    TR_ERR_TIMEOUT, TR_ERR_CAPACITY as for tr_run_fixed_source. */
 tr_status tr_run_fixed_source_noalloc(tr_problem *problem, const tr_run_opts *opts, double *mesh_out,
                                       double *energy_out, double *scalars_out, tr_run_stats *stats);
+
+/* Device-side check of the random numbers, for the test suite (Philox-4x32-10,
+ * Salmon et al., SC'11; the generator is our reading of the paper's
+ * hash-based generator, Sec. 3): for i < n, the library's device Philox on
+ * counter ctr[4i..4i+3] and key key[2i..2i+1], and a call of CUDA's own
+ * curand_Philox4x32_10 on the same words.  All arrays are host memory: ctr
+ * 4n and key 2n words in, ours and curand_out 4n words out each.  Uses the
+ * current device and device scratch it allocates; synchronous.  Errors:
+ * TR_ERR_INVALID for NULL arrays or n > 2^26, TR_ERR_CUDA. */
+tr_status tr_selftest_philox(const uint32_t *ctr, const uint32_t *key, size_t n, uint32_t *ours,
+                             uint32_t *curand_out);
+
+/* Device-side check of the logarithm the transport kernels evaluate (Tang's
+ * table-driven method with the problem's table): out[i] = log(x[i]) for the
+ * n host values x (positive, finite, normal; others give TR_ERR_INVALID),
+ * computed on the problem's device, written to the host array out.  Device
+ * scratch is allocated; synchronous on the problem's stream.  n <= 2^26. */
+tr_status tr_selftest_log(const tr_problem *problem, const double *x, size_t n, double *out);
+
+/* The exponential ziggurat table the transport kernels of this problem read
+ * (built on the device at problem creation): 1024 doubles to the host array
+ * out, {W_i, C_i} for the 256 layers, then {f_i, f_i+1 - f_i}.  Synchronous. */
+tr_status tr_selftest_zig_table(const tr_problem *problem, double *out);
 
 /* Diagnostics: number of kernels this library has launched in this process
  * (all kernels, all problems).  Read it before and after a call to count the

@@ -137,8 +137,29 @@ def lib():
     L.tr_eig_checkpoint.argtypes = [C.c_void_p, C.c_void_p, C.c_size_t, C.POINTER(C.c_size_t)]
     L.tr_eig_checkpoint.restype = C.c_int
     L.tr_version.restype = C.c_char_p
+    L.tr_selftest_philox.argtypes = [C.POINTER(C.c_uint32), C.POINTER(C.c_uint32), C.c_size_t,
+                                     C.POINTER(C.c_uint32), C.POINTER(C.c_uint32)]
+    L.tr_selftest_philox.restype = C.c_int
+    L.tr_selftest_log.argtypes = [C.c_void_p, _dp, C.c_size_t, _dp]
+    L.tr_selftest_log.restype = C.c_int
+    L.tr_selftest_zig_table.argtypes = [C.c_void_p, _dp]
+    L.tr_selftest_zig_table.restype = C.c_int
     _lib = L
     return L
+
+
+def selftest_philox(ctr, key):
+    """tr_selftest_philox: (library Philox, curand Philox) on n counters (n x 4
+    uint32) and keys (n x 2 uint32), each n x 4 uint32."""
+    ctr = np.ascontiguousarray(ctr, np.uint32)
+    key = np.ascontiguousarray(key, np.uint32)
+    n = ctr.shape[0]
+    ours = np.zeros((n, 4), np.uint32)
+    lib_out = np.zeros((n, 4), np.uint32)
+    u32 = C.POINTER(C.c_uint32)
+    _check(lib().tr_selftest_philox(ctr.ctypes.data_as(u32), key.ctypes.data_as(u32), n,
+                                    ours.ctypes.data_as(u32), lib_out.ctypes.data_as(u32)))
+    return ours, lib_out
 
 
 class TransportError(RuntimeError):
@@ -381,6 +402,19 @@ class Problem:
         buf = C.create_string_buffer(n.value)
         _check(lib().tr_eig_checkpoint(self._h, buf, n.value, C.byref(n)))
         return buf.raw[:n.value]
+
+    def selftest_log(self, x) -> np.ndarray:
+        """tr_selftest_log: the device logarithm of the transport kernels."""
+        x = np.ascontiguousarray(x, np.float64)
+        out = np.empty_like(x)
+        _check(lib().tr_selftest_log(self._h, x.ctypes.data_as(_dp), x.size, out.ctypes.data_as(_dp)))
+        return out
+
+    def zig_table(self) -> np.ndarray:
+        """tr_selftest_zig_table: the ziggurat table the transport kernels read."""
+        out = np.empty(1024, np.float64)
+        _check(lib().tr_selftest_zig_table(self._h, out.ctypes.data_as(_dp)))
+        return out
 
     def tally_size(self, tally_id: int) -> int:
         """tr_tally_size: bins of one tally (0 if absent)."""

@@ -18,7 +18,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libtr.so")
-SOURCES = ["tr_capi.cu", "tr_stack.cu", "tr_async.cu", "tr_noalloc.cu", "tr_adjoint.cu"]
+SOURCES = ["tr_capi.cu", "tr_stack.cu", "tr_async.cu", "tr_noalloc.cu", "tr_adjoint.cu", "tr_selftest.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-fmad=false", "-prec-div=true", "-prec-sqrt=true",
          "-Xcompiler", "-fPIC,-ffp-contract=off,-fno-fast-math", "-Xptxas", "-warn-spills"]

@@ -38,6 +38,7 @@ constexpr int N_GQ = 32;
 
 struct Stash {
     double *x, *y, *z, *u, *v, *w, *iu, *iv, *iw, *ia, *E, *t;
+    double *hf, *ha, *hp;              // the histories' running scalar scores
     double *xst, *xist, *xsa, *xnsf;   // lookup-event decomposition only (else NULL)
     int* g;
     unsigned *cell, *id, *n, *nsites, *pend, *prob;
@@ -51,8 +52,16 @@ constexpr int CNT_FREE = N_QUEUES, CNT_LOCK = N_QUEUES + 1, CNT_RUN = N_QUEUES +
 
 __host__ __device__ __forceinline__ size_t stash_bytes(int S, bool xs = false)
 {
-    return (size_t)S * ((xs ? 16 : 12) * sizeof(double) + sizeof(int) + 6 * sizeof(unsigned)) +
+    return (size_t)S * ((xs ? 19 : 15) * sizeof(double) + sizeof(int) + 6 * sizeof(unsigned)) +
            (size_t)S * (N_QUEUES + 1) * sizeof(unsigned short) + 16 * sizeof(int);
+}
+
+// Dynamic shared memory of one block: the stash, then (8-byte aligned) the
+// threads' fixed-point sums of ended histories' scalar scores.
+__host__ __device__ __forceinline__ size_t fx_offset(int S, bool xs) { return (stash_bytes(S, xs) + 15) & ~size_t(15); }
+__host__ __device__ __forceinline__ size_t async_smem_bytes(int S, bool xs)
+{
+    return fx_offset(S, xs) + 256 * ACC_FX_WORDS * sizeof(long long);
 }
 
 __device__ __forceinline__ Stash carve(unsigned char* base, int S, bool xs)
@@ -64,6 +73,7 @@ __device__ __forceinline__ Stash carve(unsigned char* base, int S, bool xs)
     s.iu = d; d += S; s.iv = d; d += S; s.iw = d; d += S; s.ia = d; d += S;
     s.E = d; d += S;
     s.t = d; d += S;
+    s.hf = d; d += S; s.ha = d; d += S; s.hp = d; d += S;
     s.xst = s.xist = s.xsa = s.xnsf = nullptr;
     if (xs) {
         s.xst = d; d += S; s.xist = d; d += S; s.xsa = d; d += S; s.xnsf = d; d += S;
@@ -90,6 +100,7 @@ template <bool XS>
 __device__ __forceinline__ void slot_load(const Stash& s, int i, Particle& p, bool tm)
 {
     if (tm) p.t = s.t[i];
+    p.hf = s.hf[i]; p.ha = s.ha[i]; p.hp = s.hp[i];
     if (XS) {
         p.xst = s.xst[i]; p.xist = s.xist[i]; p.xsa = s.xsa[i]; p.xnsf = s.xnsf[i];
     }
@@ -105,6 +116,7 @@ template <bool XS>
 __device__ __forceinline__ void slot_store(const Stash& s, int i, const Particle& p, bool tm)
 {
     if (tm) s.t[i] = p.t;
+    s.hf[i] = p.hf; s.ha[i] = p.ha; s.hp[i] = p.hp;
     if (XS) {
         s.xst[i] = p.xst; s.xist[i] = p.xist; s.xsa[i] = p.xsa; s.xnsf[i] = p.xnsf;
     }
@@ -129,6 +141,7 @@ __device__ __forceinline__ void load_particle_l2(const SoA& s, unsigned long lon
     p.u = __ldcg(s.u + i); p.v = __ldcg(s.v + i); p.w = __ldcg(s.w + i);
     p.iu = __ldcg(s.iu + i); p.iv = __ldcg(s.iv + i); p.iw = __ldcg(s.iw + i); p.ia = __ldcg(s.ia + i);
     p.E = __ldcg(s.E + i); p.g = __ldcg(s.g + i); p.t = __ldcg(s.t + i);
+    p.hf = __ldcg(s.hf + i); p.ha = __ldcg(s.ha + i); p.hp = __ldcg(s.hp + i);
     p.cell = __ldcg(s.cell + i); p.id = __ldcg(s.id + i); p.n = __ldcg(s.n + i);
     p.nsites = __ldcg(s.nsites + i); p.pend = __ldcg(s.pend + i); p.prob = __ldcg(s.prob + i);
 }
@@ -316,14 +329,12 @@ __device__ __forceinline__ int find_problem(const unsigned long long* off, int n
     return lo;
 }
 
-// Batched launches: add a lane's event counts and scalar scores to the
-// tallies of the problem they belong to.  A lane accumulates while its
-// particles come from one problem and flushes when the problem changes.
+// Batched launches: add a lane's event counts to the tallies of the problem
+// they belong to (a lane counts while its particles come from one problem and
+// flushes when the problem changes; ended histories add their scalar scores
+// to their own problem's bins directly).
 __device__ __forceinline__ void flush_lane(Acc& acc, const Tallies& T)
 {
-    if (acc.flux) fix_add_sum(T.scal + 0, acc.flux);
-    if (acc.absn) fix_add_sum(T.scal + 1, acc.absn);
-    if (acc.prod) fix_add_sum(T.scal + 2, acc.prod);
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
         if (acc.ev[i]) atomicAdd(T.ev_type + i, (unsigned long long)acc.ev[i]);
@@ -361,6 +372,7 @@ __global__ void __launch_bounds__(256, TR_ASYNC_MIN_BLOCKS) k_async(DevProblem P
 
     Acc acc;
     acc.zero();
+    if (!BATCHED) acc_attach(acc, reinterpret_cast<long long*>(smem + fx_offset(S, XS)));
     unsigned long long idle_spins = 0;
     uint64_t idle_t0 = 0;    // when this warp last started waiting for work
     bool idle = false;
@@ -888,7 +900,7 @@ static int occupancy_async(size_t smem)
 
 int async_max_blocks_per_sm(const DevProblem& P, int dec, int stash_slots, bool pre)
 {
-    const size_t smem = stash_bytes(stash_slots, dec == DEC_LOOKUP);
+    const size_t smem = async_smem_bytes(stash_slots, dec == DEC_LOOKUP);
     if (pre && dec == DEC_MONO)
         return P.kind == 1 ? occupancy_async<true, DEC_MONO, false, true>(smem)
                            : occupancy_async<false, DEC_MONO, false, true>(smem);
@@ -929,7 +941,7 @@ static cudaError_t launch_async_mono(const DevProblem& P, const RunParams& R, co
 cudaError_t launch_async(const DevProblem& P, const RunParams& R, const AsyncArgs& A, const Tallies& T, ErrorWord* err,
                          int blocks, cudaStream_t st, int* smem_bytes_out)
 {
-    const size_t smem = stash_bytes(A.stash_slots, A.dec == DEC_LOOKUP);
+    const size_t smem = async_smem_bytes(A.stash_slots, A.dec == DEC_LOOKUP);
     if (smem_bytes_out) *smem_bytes_out = (int)smem;
     count_launches(1);
     if (A.dec == DEC_MONO)
@@ -956,14 +968,14 @@ cudaError_t launch_presample(const DevProblem& P, const RunParams& R, const Asyn
 // Batched launches (multigroup; monolithic or decomposed).
 int async_batched_max_blocks_per_sm(int dec, int stash_slots)
 {
-    const size_t smem = stash_bytes(stash_slots);
+    const size_t smem = async_smem_bytes(stash_slots, false);
     return dec == DEC_SPLIT ? occupancy_async<false, DEC_SPLIT, true>(smem) : occupancy_async<false, DEC_MONO, true>(smem);
 }
 
 cudaError_t launch_async_batched(const DevProblem& P0, const RunParams& R, const AsyncArgs& A, ErrorWord* err,
                                  int blocks, cudaStream_t st)
 {
-    const size_t smem = stash_bytes(A.stash_slots);
+    const size_t smem = async_smem_bytes(A.stash_slots, false);
     const Tallies T{};
     count_launches(1);
     if (A.dec == DEC_SPLIT) return launch_async_t<false, DEC_SPLIT, true>(P0, R, A, T, err, blocks, st, smem);

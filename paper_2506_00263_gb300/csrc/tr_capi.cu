@@ -586,7 +586,7 @@ constexpr unsigned long long PRESAMPLE_MAX_HIST = 1ull << 24;
 static bool carve_soa(tr_problem* pr, const char* name, unsigned long long cap, SoA& s)
 {
     const size_t n = (size_t)cap;
-    const size_t bytes = n * (16 * 8 + 7 * 4) + 23 * 256;
+    const size_t bytes = n * (19 * 8 + 7 * 4) + 26 * 256;
     unsigned char* b = (unsigned char*)workspace(pr, name, bytes);
     if (!b) return false;
     auto take = [&](size_t sz) {
@@ -599,6 +599,7 @@ static bool carve_soa(tr_problem* pr, const char* name, unsigned long long cap, 
     s.iu = (double*)take(8); s.iv = (double*)take(8); s.iw = (double*)take(8); s.ia = (double*)take(8);
     s.E = (double*)take(8);
     s.t = (double*)take(8);
+    s.hf = (double*)take(8); s.ha = (double*)take(8); s.hp = (double*)take(8);
     s.xst = (double*)take(8); s.xist = (double*)take(8); s.xsa = (double*)take(8); s.xnsf = (double*)take(8);
     s.g = (int*)take(4);
     s.cell = (unsigned*)take(4); s.id = (unsigned*)take(4); s.n = (unsigned*)take(4);

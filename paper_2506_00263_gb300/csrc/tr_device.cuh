@@ -157,10 +157,12 @@ __device__ __forceinline__ uint64_t now_ns()
 // that a surface event does not repeat four divisions), energy (CE) or
 // group (MG), packed cell, history index, event count, banked-site count, the
 // pending surface flags of the decomposed scheme and the problem index of a
-// batched launch; with the lookup event, the cached cross sections (Sigma_t,
-// 1/Sigma_t, Sigma_a, nu Sigma_f).
+// batched launch; the history's running scalar scores (track length,
+// absorption and production, summed in event order); with the lookup event,
+// the cached cross sections (Sigma_t, 1/Sigma_t, Sigma_a, nu Sigma_f).
 struct SoA {
     double *x, *y, *z, *u, *v, *w, *iu, *iv, *iw, *ia, *E, *t;
+    double *hf, *ha, *hp;
     double *xst, *xist, *xsa, *xnsf;
     int *g;
     unsigned *cell, *id, *n, *nsites, *pend, *prob;
@@ -171,6 +173,10 @@ struct Particle {
     double iu, iv, iw, ia;
     double E;
     double t;                          // time since the source (timed problems)
+    // the history's scalar scores so far (track length, absorption,
+    // production), summed in event order: the same value whatever the
+    // schedule; converted to fixed point once, when the history ends
+    double hf, ha, hp;
     double xst, xist, xsa, xnsf;       // lookup-event decomposition: cross sections of (material, E or g)
     int g;
     unsigned cell;                     // i | j << 10 | k << 20 | inside << 30

@@ -15,33 +15,53 @@ namespace tr {
 constexpr unsigned PEND_X = 1u, PEND_Y = 2u, PEND_Z = 4u, PEND_CYL = 8u, PEND_ESCAPE = 16u, PEND_COLLIDE = 32u,
                    PEND_CENSUS = 64u;
 
-// Per-thread accumulators for the always-on scalar tallies (sums of rounded
-// fixed-point contributions, tr_fixed.cuh) and event counts.
+// Per-thread accumulators: event counts, and the fixed-point sums
+// (tr_fixed.cuh) of the scalar scores of the histories this thread ended.
+// Those sums live in shared memory (fx: three per thread), or fx is null and
+// each ended history goes to its tally bins directly.
 struct Acc {
-    long long flux, absn, prod;
+    long long* fx;
     unsigned ev[8];
     unsigned fin[8];
     __device__ __forceinline__ void zero()
     {
-        flux = absn = prod = 0;
+        fx = nullptr;
 #pragma unroll
         for (int i = 0; i < 8; ++i) ev[i] = fin[i] = 0u;
     }
 };
 
-// Add contribution c to a per-thread scalar sum a (bin: its tally bin, where
-// the sum is spilled before it could overflow, and where a contribution too
-// large for the per-thread sum goes directly).
-__device__ __forceinline__ void acc_add(long long& a, FixBin* bin, double c, const Tallies& T)
+// Shared-memory words per thread for Acc::fx.
+constexpr int ACC_FX_WORDS = 3;
+
+// Points acc at this thread's three fixed-point sums in `base` (block-wide
+// array of blockDim.x * 3 words) and clears them.
+__device__ __forceinline__ void acc_attach(Acc& acc, long long* base)
 {
-    if (fix_small(c)) {
-        a += fix_round(c);
-        if (fix_sum_full(a)) {
-            fix_add_sum(bin, a);
-            a = 0;
+    acc.fx = base + 3 * threadIdx.x;
+    acc.fx[0] = acc.fx[1] = acc.fx[2] = 0;
+}
+
+// A history's scalar scores at its end: each rounded once to fixed point and
+// added to this thread's sums (spilled to the bin before they could
+// overflow), or straight to the bin.
+__device__ __forceinline__ void acc_history(const Acc& acc, const Tallies& T, const Particle& p)
+{
+    if (!T.scal) return;
+    const double h[3] = {p.hf, p.ha, p.hp};
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const double c = h[k];
+        if (acc.fx && fix_small(c)) {
+            long long s = acc.fx[k] + fix_round(c);
+            if (fix_sum_full(s)) {
+                fix_add_sum(T.scal + k, s);
+                s = 0;
+            }
+            acc.fx[k] = s;
+        } else if (dbits(c) << 1) {
+            if (!fix_add(T.scal + k, c)) tally_range_error(T);
         }
-    } else if (!fix_add(bin, c)) {
-        tally_range_error(T);
     }
 }
 
@@ -197,6 +217,7 @@ __device__ __forceinline__ bool source_particle(const DevProblem& P, const RunPa
     p.g = 0;
     p.E = 0.0;
     p.t = 0.0;
+    p.hf = p.ha = p.hp = 0.0;
     if (site != nullptr || P.src_kind != 0 || P.src_iso) {
         iso_dir(S, 0u, p);
     } else {
@@ -281,12 +302,12 @@ struct FwdSink {
     const Tallies& T;
     Acc& acc;
     template <bool CE>
-    __device__ __forceinline__ void segment(const DevProblem& P, const Particle& p, double x0, double y0, double z0,
+    __device__ __forceinline__ void segment(const DevProblem& P, Particle& p, double x0, double y0, double z0,
                                             double dist, int m, const XS& X)
     {
-        acc_add(acc.flux, T.scal + 0, dist, T);
-        acc_add(acc.absn, T.scal + 1, dist * X.sa, T);
-        if (!CE) acc_add(acc.prod, T.scal + 2, dist * X.nsf, T);   // continuous energy: nu Sigma_f = 0
+        p.hf += dist;
+        p.ha = __fma_rn(dist, X.sa, p.ha);   // tallies: compared within tolerance, fused freely
+        if (!CE) p.hp = __fma_rn(dist, X.nsf, p.hp);   // continuous energy: nu Sigma_f = 0
         if (P.has_mesh && gt0(dist)) {
             const int goff = (!CE && P.by_group) ? p.g * P.mesh_vox : 0;
             MeshAtomic op{T};
@@ -627,6 +648,7 @@ __device__ __forceinline__ bool finish_event(const DevProblem& P, const RunParam
         type = EV_MAXEV;
     }
     if (!alive) {
+        acc_history(acc, T, p);
         acc.fin[type] += 1u;
         if (R.want_log) {
             T.log_n[p.id] = p.n;
@@ -736,6 +758,7 @@ __device__ __forceinline__ int split_surface_next(const DevProblem& P, const Run
 __device__ __forceinline__ void load_particle(const SoA& s, unsigned long long i, Particle& p, bool ce, bool xs = false)
 {
     p.t = s.t[i];
+    p.hf = s.hf[i]; p.ha = s.ha[i]; p.hp = s.hp[i];
     if (xs) {
         p.xst = s.xst[i]; p.xist = s.xist[i]; p.xsa = s.xsa[i]; p.xnsf = s.xnsf[i];
     }
@@ -751,6 +774,7 @@ __device__ __forceinline__ void store_particle(const SoA& s, unsigned long long 
                                                bool xs = false)
 {
     s.t[i] = p.t;
+    s.hf[i] = p.hf; s.ha[i] = p.ha; s.hp[i] = p.hp;
     if (xs) {
         s.xst[i] = p.xst; s.xist[i] = p.xist; s.xsa[i] = p.xsa; s.xnsf[i] = p.xnsf;
     }
@@ -779,6 +803,7 @@ __device__ __forceinline__ bool load_presampled(const SoA& s, unsigned long long
     p.pend = 0u;
     p.prob = 0u;
     p.t = 0.0;
+    p.hf = p.ha = p.hp = 0.0;
     return s.id[i] == (unsigned)i;
 }
 
@@ -793,10 +818,11 @@ __device__ __forceinline__ int next_queue_after_step(const Particle& p)
 // (integer sums: the result does not depend on the order).
 __device__ __forceinline__ void flush_acc(const Acc& acc, const Tallies& T)
 {
-    unsigned long long sl[3], sh[3];
-    fix_split_sum(acc.flux, sl[0], sh[0]);
-    fix_split_sum(acc.absn, sl[1], sh[1]);
-    fix_split_sum(acc.prod, sl[2], sh[2]);
+    unsigned long long sl[3] = {0ull, 0ull, 0ull}, sh[3] = {0ull, 0ull, 0ull};
+    if (acc.fx) {
+#pragma unroll
+        for (int k = 0; k < 3; ++k) fix_split_sum(acc.fx[k], sl[k], sh[k]);
+    }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
 #pragma unroll
@@ -812,10 +838,12 @@ __device__ __forceinline__ void flush_acc(const Acc& acc, const Tallies& T)
         fin[i] = __reduce_add_sync(0xFFFFFFFFu, acc.fin[i]);
     }
     if ((threadIdx.x & 31) == 0) {
+        if (T.scal) {
 #pragma unroll
-        for (int k = 0; k < 3; ++k) {
-            if (sl[k]) atomicAdd(&T.scal[k].lo, sl[k]);
-            if (sh[k]) atomicAdd(&T.scal[k].hi, sh[k]);
+            for (int k = 0; k < 3; ++k) {
+                if (sl[k]) atomicAdd(&T.scal[k].lo, sl[k]);
+                if (sh[k]) atomicAdd(&T.scal[k].hi, sh[k]);
+            }
         }
 #pragma unroll
         for (int i = 0; i < 8; ++i) {

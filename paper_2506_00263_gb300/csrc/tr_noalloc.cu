@@ -30,8 +30,8 @@ namespace {
 
 constexpr unsigned long long NOALLOC_LINKS = TR_NOALLOC_MAX_QUEUE_CAPACITY / 32;
 constexpr size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
-// per particle slot of the link arena: 12 doubles + 7 32-bit words (as carve_links below)
-constexpr size_t LINK_SOA_BYTES = 19 * 256 + NOALLOC_LINKS * 32 * (12 * 8 + 7 * 4);
+// per particle slot of the link arena: 15 doubles + 7 32-bit words (as carve_links below)
+constexpr size_t LINK_SOA_BYTES = 22 * 256 + NOALLOC_LINKS * 32 * (15 * 8 + 7 * 4);
 constexpr size_t OFF_ERR = 0;
 constexpr size_t OFF_COUNTS = align256(OFF_ERR + sizeof(ErrorWord));
 constexpr size_t OFF_CTL = align256(OFF_COUNTS + 16 * sizeof(unsigned long long));
@@ -92,6 +92,7 @@ void carve_links(unsigned char* b, unsigned long long n, SoA& s)
     s.iu = (double*)take(8); s.iv = (double*)take(8); s.iw = (double*)take(8); s.ia = (double*)take(8);
     s.E = (double*)take(8);
     s.t = (double*)take(8);
+    s.hf = (double*)take(8); s.ha = (double*)take(8); s.hp = (double*)take(8);
     s.xst = s.xist = s.xsa = s.xnsf = nullptr;   // the lookup-event decomposition is not offered here
     s.g = (int*)take(4);
     s.cell = (unsigned*)take(4); s.id = (unsigned*)take(4); s.n = (unsigned*)take(4);

@@ -57,8 +57,10 @@ __global__ void __launch_bounds__(256) k_stack_mono(DevProblem P, RunParams R, S
     StackCtl* ctl = A.ctl;
     const unsigned long long in_count = ctl->in_count[Q_STEP];
     const unsigned long long cap = ctl->capacity;
+    __shared__ long long fx[256 * ACC_FX_WORDS];
     Acc acc;
     acc.zero();
+    acc_attach(acc, fx);
     for (;;) {
         unsigned long long base = 0;
         if (lane == 0) base = atomicAdd(&ctl->pop, 32ull);
@@ -122,8 +124,10 @@ __global__ void __launch_bounds__(256) k_stack_split(DevProblem P, RunParams R, 
         start[q + 1] = start[q] + ((cnt[q] + 31ull) & ~31ull);
     }
     const unsigned long long cap = ctl->capacity;
+    __shared__ long long fx[256 * ACC_FX_WORDS];
     Acc acc;
     acc.zero();
+    acc_attach(acc, fx);
     for (;;) {
         unsigned long long base = 0;
         if (lane == 0) base = atomicAdd(&ctl->pop, 32ull);

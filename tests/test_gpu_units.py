@@ -1,0 +1,84 @@
+"""Device-side pins of the arithmetic building blocks, beyond what histories
+happen to exercise: the device Philox against a call of CUDA's own curand
+Philox4x32-10 and against the oracle; the device logarithm bit for bit
+against the oracle's on a million inputs (powers of two, 1 +- ulp, the
+table's breakpoints, the uniforms the transport draws, the range
+extremes), within 4 ulp of the C library; the ziggurat table the transport
+kernels read bit for bit against the oracle's."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2506_00263_gb300 import binding as tb
+from paper_2506_00263_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_2506_00263_gb300 import build
+    build.build()
+
+
+def test_device_philox_equals_curand_and_oracle():
+    rng = np.random.default_rng(17)
+    n = 200_000
+    ctr = rng.integers(0, 2 ** 32, size=(n, 4), dtype=np.uint64).astype(np.uint32)
+    key = rng.integers(0, 2 ** 32, size=(n, 2), dtype=np.uint64).astype(np.uint32)
+    # edge words: zeros, all ones, and the layouts the transport uses
+    ctr[:4] = [[0, 0, 0, 0], [0xFFFFFFFF] * 4, [1, 0, 5, 0], [7, 3000, 123456, 1]]
+    key[:4] = [[0, 0], [0xFFFFFFFF, 0xFFFFFFFF], [1, 0], [1, 0x80000000]]
+    ours, cur = tb.selftest_philox(ctr, key)
+    assert np.array_equal(ours, cur), int(np.argmax(np.any(ours != cur, axis=1)))
+    for i in list(range(8)) + list(rng.integers(0, n, 200)):
+        assert tuple(int(v) for v in ours[i]) == oracle.philox(ctr[i], key[i]), i
+
+
+def _log_inputs():
+    rng = np.random.default_rng(23)
+    xs = [2.0 ** np.arange(-1022, 1024, dtype=np.float64)]
+    one = np.float64(1.0)
+    xs.append(np.array([np.nextafter(one, 0.0), one, np.nextafter(one, 2.0), np.finfo(np.float64).tiny,
+                        np.finfo(np.float64).max, math.sqrt(2.0), math.sqrt(0.5)]))
+    # around sqrt(2) (where m is halved) and every table breakpoint 1 + (k + 1/2)/128
+    for c in [math.sqrt(2.0)] + [1.0 + (k + 0.5) / 128.0 for k in range(-64, 55)]:
+        b = np.array([c], np.float64).view(np.int64)[0]
+        xs.append((b + np.arange(-3, 4, dtype=np.int64)).view(np.float64))
+    # the uniforms the transport draws, ((w >> 12) + 1/2) 2^-52
+    w = rng.integers(0, 2 ** 52, size=500_000, dtype=np.uint64)
+    xs.append((w.astype(np.float64) + 0.5) * 2.0 ** -52)
+    xs.append(np.array([2.0 ** -53, 1.0 - 2.0 ** -53]))
+    # log-uniform over the normal range, and values near 1
+    xs.append(np.exp(rng.uniform(-700.0, 700.0, 400_000)))
+    xs.append(1.0 + rng.uniform(-1e-3, 1e-3, 200_000))
+    x = np.concatenate(xs)
+    return x[(x > 0) & np.isfinite(x) & (x >= np.finfo(np.float64).tiny)]
+
+
+def test_device_log_equals_oracle_bitwise():
+    x = _log_inputs()
+    assert x.size > 1_000_000
+    prob = tb.Problem(inputs.cube_one_group())
+    got = prob.selftest_log(x)
+    prob.close()
+    orc = np.array([oracle.log(v) for v in x])
+    diff = got.view(np.int64) != orc.view(np.int64)
+    assert not diff.any(), (int(diff.sum()), x[diff][:4], got[diff][:4], orc[diff][:4])
+    ref = np.log(x)
+    ulp = np.spacing(np.abs(ref))
+    nz = ref != 0.0
+    assert np.max(np.abs(got[nz] - ref[nz]) / ulp[nz]) <= 4.0
+    assert np.all(got[~nz] == 0.0)
+
+
+def test_device_ziggurat_table_equals_oracle_bitwise():
+    prob = tb.Problem(inputs.c5g7_lattice())
+    t = prob.zig_table()
+    prob.close()
+    W, Cw, f, df = oracle.zig_table()
+    dev = {"W": t[0:512:2], "C": t[1:512:2], "f": t[512::2], "df": t[513::2]}
+    for name, a, b in (("W", dev["W"], W), ("C", dev["C"], Cw), ("f", dev["f"], f), ("df", dev["df"], df)):
+        assert np.array_equal(a.view(np.int64), np.asarray(b).view(np.int64)), name

@@ -15,7 +15,7 @@ from tests._util import assert_tally_close
 pytestmark = pytest.mark.gpu
 
 MAX_QUEUE = 4096          # TR_NOALLOC_MAX_QUEUE_CAPACITY in include/tr.h
-MAX_BINS = 28672          # TR_NOALLOC_MAX_TALLY_BINS in include/tr.h
+MAX_BINS = 24576          # TR_NOALLOC_MAX_TALLY_BINS in include/tr.h
 
 
 def _same_bits(a, b, what):
