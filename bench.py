@@ -475,34 +475,40 @@ def measure_batched(torch, tb, inputs, steps, warmup, decomp, seed=1, tuning=(0,
 
 
 def measure_adjoint(torch, tb, inputs, steps, warmup, decomp, seed=1, sampler=None, barrier=None):
-    """One step = forward fixed-source run + tr_sensitivities (derivatives of
-    g . mesh + absorption rate) on the fission-off lattice, 1e6 histories."""
+    """One step = one forward and one backward pass through TransportFn
+    (torch.autograd) on the fission-off lattice, 1e6 histories: the forward
+    pass writes the cross sections (CUDA tensors) into a kept problem on the
+    device and runs the fixed-source transport; the backward pass of
+    L = g . mesh + absorption rate runs the derivative kernels.  Forward and
+    backward are timed separately with CUDA events on the stream."""
     import contextlib
     import numpy as np
+    from paper_2506_00263_gb300.autograd import transport
     spec = inputs.c5g7_lattice(fission=False)
     opts = tb.RunOpts(n_histories=1_000_000, seed=seed, scheme=tb.SCHEME_ASYNC, decomposition=decomp,
                       remap_every=512 if decomp == tb.DECOMP_MONO else 1)
     prob = tb.Problem(spec)
-    M, G = spec.n_materials, spec.n_groups
+    xs0 = [torch.tensor(a, dtype=torch.float64, device="cuda") for a in (spec.sigma_t, spec.sigma_s,
+                                                                           spec.nu_sigma_f)]
     g_mesh = torch.tensor(np.random.default_rng(3).uniform(-1, 1, spec.mesh_size), dtype=torch.float64,
                           device="cuda")
-    g_scal = torch.tensor([0.0, 1.0, 0.0], dtype=torch.float64, device="cuda")
-    d_st = torch.empty((M, G), dtype=torch.float64, device="cuda")
-    d_ss = torch.empty((M, G, G), dtype=torch.float64, device="cuda")
-    d_nf = torch.empty((M, G), dtype=torch.float64, device="cuda")
     stream = torch.cuda.current_stream()
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float64, device="cuda")
 
-    def fwd():
-        return prob.run_fixed_source(opts)
-
-    def bwd():
-        prob.sensitivities(opts, g_mesh.data_ptr(), g_scal.data_ptr(), d_st.data_ptr(), d_ss.data_ptr(),
-                           d_nf.data_ptr())
+    def one_step(events=None):
+        xs = [x.clone().requires_grad_(True) for x in xs0]
+        if events:
+            events[0].record(stream)
+        mesh, scal = transport(xs[0], xs[1], xs[2], prob, opts)
+        if events:
+            events[1].record(stream)
+        ((mesh * g_mesh).sum() + scal[1]).backward()
+        if events:
+            events[2].record(stream)
+        return xs
 
     for _ in range(warmup):
-        fwd()
-        bwd()
+        one_step()
     torch.cuda.synchronize()
     if barrier:
         barrier()
@@ -513,20 +519,16 @@ def measure_adjoint(torch, tb, inputs, steps, warmup, decomp, seed=1, sampler=No
         for k in range(steps):
             flush.fill_(float(k))
             e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
-            e[0].record(stream)
-            r = fwd()
-            e[1].record(stream)
-            bwd()
-            e[2].record(stream)
+            one_step(e)
             e[2].synchronize()
             t_f += e[0].elapsed_time(e[1]) * 1e-3
             t_b += e[1].elapsed_time(e[2]) * 1e-3
-            ev += int(r["events"])
+            ev += int(prob.last_stats["events"])
     launches = tb.kernel_launch_count() - launches0
     prob.close()
     return {"seconds": t_f + t_b, "events": ev, "launches": launches, "forward_ms": 1e3 * t_f / steps,
             "backward_ms": 1e3 * t_b / steps, "gradient_over_forward": t_b / t_f,
-            "forward_events_per_s": ev / t_f}
+            "forward_events_per_s": ev / t_f, "through": "torch.autograd (TransportFn forward + backward)"}
 
 
 def _side_line(args, ws, workload, m, t, ev_all, hist_all, sampler, roof, extra):

@@ -197,6 +197,24 @@ tr_status tr_problem_create(const tr_geometry_desc *geometry, const tr_xs_desc *
                             const tr_source_desc *source, const tr_tally_desc *tallies, int32_t n_tallies,
                             const tr_device_ctx *ctx, tr_problem **out);
 
+/* Replace the multigroup cross sections of a problem in place (the paper has
+ * no counterpart: it serves the derivative workflow, where the cross
+ * sections are the parameters being optimised).  sigma_t [m][g],
+ * sigma_s [m][g][g'] and nu_sigma_f [m][g], n_materials x n_groups as at
+ * creation, row-major doubles; device memory of the problem's device when
+ * on_device != 0 (no host copy), else host memory.  The derived tables
+ * (1/sigma_t, the cumulative scattering rows, sigma_a) are rebuilt on the
+ * device with the operations problem creation uses, so runs equal those of
+ * a problem created with these values.  chi is unchanged.  Results and a
+ * kept power-iteration state of earlier runs are dropped (TR_ERR_STATE until
+ * the next run), and checkpoints taken before no longer match.  Synchronises
+ * the problem's stream.  Errors: TR_ERR_INVALID for NULL arrays, a
+ * continuous-energy problem, a sigma_t that is not positive and finite or a
+ * sigma_s that is negative or not finite (the problem keeps its previous
+ * values); TR_ERR_NOMEM; TR_ERR_CUDA. */
+tr_status tr_problem_set_xs(tr_problem *problem, const double *sigma_t, const double *sigma_s,
+                            const double *nu_sigma_f, int32_t on_device);
+
 /* Destroy a problem (NULL-safe); frees through the context's callbacks on its stream. */
 void tr_problem_destroy(tr_problem *problem);
 

@@ -104,7 +104,7 @@ class OrcSens(C.Structure):
         ("n_hist", C.c_uint64), ("seed", C.c_uint64), ("tag", C.c_uint32), ("max_events", C.c_uint32),
         ("g_mesh", C.POINTER(C.c_double)), ("g_scal", C.POINTER(C.c_double)),
         ("d_sigt", C.POINTER(C.c_double)), ("d_sigs", C.POINTER(C.c_double)), ("d_nusigf", C.POINTER(C.c_double)),
-        ("value", C.c_double),
+        ("value", C.c_double), ("id_offset", C.c_uint64),
     ]
 
 
@@ -268,13 +268,13 @@ def run_fixed_source(prob, n_hist: int, seed: int = 1, tag: int = 0, max_events:
 
 
 def sensitivities(prob, n_hist: int, g_mesh=None, g_scal=None, seed: int = 1, tag: int = 0,
-                  max_events: int = 0) -> dict:
+                  max_events: int = 0, id_offset: int = 0) -> dict:
     """Score-function + pathwise derivatives of L = g . tallies with respect to
     sigma_t [m][g], sigma_s [m][g][g'] and nu_sigma_f [m][g]."""
     L = lib()
     m = _Marshalled(prob)
     o = OrcSens()
-    o.n_hist, o.seed, o.tag, o.max_events = n_hist, seed, tag, max_events
+    o.n_hist, o.seed, o.tag, o.max_events, o.id_offset = n_hist, seed, tag, max_events, id_offset
     keep = []
     if g_mesh is not None:
         gm = np.ascontiguousarray(g_mesh, np.float64)

@@ -1216,7 +1216,8 @@ int orc_sensitivities(const orc_problem *P, orc_sens *o)
     nsum *dst = calloc((size_t)M * G, sizeof(nsum)), *dss = calloc((size_t)M * G * G, sizeof(nsum));
     nsum *dnf = calloc((size_t)M * G, sizeof(nsum)), val;
     memset(&val, 0, sizeof(val));
-    for (uint64_t id = 0; id < o->n_hist && st == ORC_OK; ++id) {
+    for (uint64_t k = 0; k < o->n_hist && st == ORC_OK; ++k) {
+        const uint64_t id = o->id_offset + k;
         particle p;
         C.rec_n = 0;
         st = source_particle(&C, &p, id, NULL, 0, 0, 0.0);

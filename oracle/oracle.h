@@ -117,6 +117,7 @@ typedef struct {
     double *d_sigs;                      /* out [m][g][g'] */
     double *d_nusigf;                    /* out [m][g] */
     double value;                        /* out: L itself (mean per source particle) */
+    uint64_t id_offset;                  /* first history index (histories id_offset .. id_offset + n_hist - 1) */
 } orc_sens;
 
 int orc_fixed_source(const orc_problem *P, orc_fixed *o);

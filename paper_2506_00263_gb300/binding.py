@@ -136,6 +136,8 @@ def lib():
     L.tr_run_batched.restype = C.c_int
     L.tr_eig_checkpoint.argtypes = [C.c_void_p, C.c_void_p, C.c_size_t, C.POINTER(C.c_size_t)]
     L.tr_eig_checkpoint.restype = C.c_int
+    L.tr_problem_set_xs.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32]
+    L.tr_problem_set_xs.restype = C.c_int
     L.tr_version.restype = C.c_char_p
     L.tr_selftest_philox.argtypes = [C.POINTER(C.c_uint32), C.POINTER(C.c_uint32), C.c_size_t,
                                      C.POINTER(C.c_uint32), C.POINTER(C.c_uint32)]
@@ -234,6 +236,7 @@ class Problem:
     def __init__(self, prob: "_inp.Problem", device=None, use_torch_allocator: bool = True):
         L = lib()
         self.spec = prob
+        self.xs_generation = 0            # tr_problem_set_xs calls so far
         keep = []
 
         def f64(a):
@@ -323,11 +326,16 @@ class Problem:
                                    C.byref(h)))
         self._h = h
         self.last_stats = None
+        Problem.live += 1
+
+    # problems created and not yet closed in this process
+    live = 0
 
     def close(self):
         if getattr(self, "_h", None):
             lib().tr_problem_destroy(self._h)
             self._h = None
+            Problem.live -= 1
 
     def __del__(self):
         try:
@@ -343,8 +351,8 @@ class Problem:
         st = RunStats()
         c = opts.to_c()
         _check(lib().tr_run_fixed_source(self._h, C.byref(c), C.byref(st)))
-        self.last_stats = st
-        return stats_dict(st)
+        self.last_stats = stats_dict(st)
+        return self.last_stats
 
     def run_fixed_source_noalloc(self, opts: RunOpts, mesh_ptr: int, energy_ptr: int, scalars_ptr: int) -> dict:
         """tr_run_fixed_source_noalloc: the asynchronous fixed-source run with
@@ -415,6 +423,25 @@ class Problem:
         out = np.empty(1024, np.float64)
         _check(lib().tr_selftest_zig_table(self._h, out.ctypes.data_as(_dp)))
         return out
+
+    def set_xs(self, sigma_t, sigma_s, nu_sigma_f):
+        """tr_problem_set_xs: new multigroup cross sections, either numpy
+        arrays (host) or contiguous float64 CUDA tensors on the problem's
+        device (passed by pointer, no host copy).  Shapes as at creation."""
+        arrs = (sigma_t, sigma_s, nu_sigma_f)
+        on_dev = all(hasattr(a, "data_ptr") and getattr(a, "is_cuda", False) for a in arrs)
+        if on_dev:
+            for a in arrs:
+                if str(a.dtype) != "torch.float64" or not a.is_contiguous():
+                    raise ValueError("device cross sections must be contiguous float64 tensors")
+            ptrs = [a.data_ptr() for a in arrs]
+            keep = arrs
+        else:
+            keep = [np.ascontiguousarray(a, np.float64) for a in arrs]
+            ptrs = [k.ctypes.data for k in keep]
+        _check(lib().tr_problem_set_xs(self._h, ptrs[0], ptrs[1], ptrs[2], 1 if on_dev else 0))
+        del keep
+        self.xs_generation += 1
 
     def tally_size(self, tally_id: int) -> int:
         """tr_tally_size: bins of one tally (0 if absent)."""

@@ -60,9 +60,11 @@ struct tr_problem {
     // batched launches led by this problem: the captured CUDA graph and its key
     std::vector<unsigned char> ckpt;          // state of a power iteration stopped early (tr_eig_checkpoint)
     uint64_t fingerprint = 0;                 // hash of the geometry, cross sections, source and tally descriptions
+    uint64_t xs_generation = 0;               // cross-section updates (tr_problem_set_xs) so far
     std::vector<double> hplanes[3];           // host copies of the planes (checkpoint validation)
     std::vector<int> hpin;                    // host copy: 1 where the cell holds a pin
     cudaGraphExec_t batch_graph = nullptr;
+    std::map<std::vector<unsigned long long>, cudaGraphExec_t> stack_graphs;   // stack-scheme loops by buffers
     std::vector<unsigned long long> batch_key;
     unsigned long long batch_graph_launches = 0;
 };
@@ -195,6 +197,29 @@ __global__ void k_zig_table(DevProblem P, double* out)
         out[2 * ZIG_N + 2 * i + 1] = Fn - F;
         X = Xn;
         F = Fn;
+    }
+}
+
+// Derived multigroup tables from sigma_t and sigma_s, one thread per (m, g),
+// with the operations and order problem creation uses on the host: 1/sigma_t,
+// the running sum of sigma_s[m][g][h] over h, sigma_a = sigma_t - sum.  A
+// non-positive or non-finite sigma_t, or a negative or non-finite sigma_s,
+// sets *bad.
+__global__ void k_mg_derived(int MG, int G, const double* __restrict__ st, const double* __restrict__ ss,
+                             double* inv, double* sa, double* cum, int* bad)
+{
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < MG; i += gridDim.x * blockDim.x) {
+        const double t = st[i];
+        if (!(t > 0.0) || !isfinite(t)) atomicExch(bad, 1);
+        inv[i] = 1.0 / t;
+        double c = 0.0;
+        for (int h = 0; h < G; ++h) {
+            const double v = ss[(size_t)i * G + h];
+            if (!(v >= 0.0) || !isfinite(v)) atomicExch(bad, 1);
+            c = c + v;
+            cum[(size_t)i * G + h] = c;
+        }
+        sa[i] = t - c;
     }
 }
 
@@ -559,12 +584,57 @@ extern "C" tr_status tr_problem_create(const tr_geometry_desc* G, const tr_xs_de
     return TR_OK;
 }
 
+extern "C" tr_status tr_problem_set_xs(tr_problem* pr, const double* sigma_t, const double* sigma_s,
+                                       const double* nu_sigma_f, int32_t on_device)
+{
+    if (!pr || !sigma_t || !sigma_s || !nu_sigma_f) return set_err(TR_ERR_INVALID, "NULL argument");
+    if (pr->dp.kind != TR_XS_MG) return set_err(TR_ERR_INVALID, "tr_problem_set_xs needs multigroup data");
+    DeviceGuard dg(pr->ctx.device);
+    DevProblem& P = pr->dp;
+    const cudaStream_t st = pr->stream;
+    const size_t MG = (size_t)P.n_mat * P.G;
+    const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    int* bad = (int*)workspace(pr, "set_xs_flag", sizeof(int));
+    if (!bad) return set_err(TR_ERR_NOMEM, "workspace allocation failed");
+    // new values land in scratch first: a refused update leaves the problem as it was
+    double* nst = (double*)workspace(pr, "set_xs_st", MG * 8);
+    double* nss = (double*)workspace(pr, "set_xs_ss", MG * P.G * 8);
+    double* ninv = (double*)workspace(pr, "set_xs_inv", MG * 8);
+    double* nsa = (double*)workspace(pr, "set_xs_sa", MG * 8);
+    double* ncum = (double*)workspace(pr, "set_xs_cum", MG * P.G * 8);
+    if (!nst || !nss || !ninv || !nsa || !ncum) return set_err(TR_ERR_NOMEM, "workspace allocation failed");
+    TR_CUDA(cudaMemcpyAsync(nst, sigma_t, MG * 8, kind, st));
+    TR_CUDA(cudaMemcpyAsync(nss, sigma_s, MG * P.G * 8, kind, st));
+    TR_CUDA(cudaMemsetAsync(bad, 0, sizeof(int), st));
+    count_launches(1);
+    k_mg_derived<<<(unsigned)std::min<size_t>((MG + 127) / 128, 1024), 128, 0, st>>>((int)MG, P.G, nst, nss, ninv, nsa,
+                                                                                    ncum, bad);
+    TR_CUDA(cudaGetLastError());
+    int hbad = 0;
+    TR_CUDA(cudaMemcpyAsync(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost, st));
+    TR_CUDA(cudaStreamSynchronize(st));
+    if (hbad) return set_err(TR_ERR_INVALID, "sigma_t must be positive and finite, sigma_s non-negative and finite");
+    TR_CUDA(cudaMemcpyAsync(const_cast<double*>(P.sigt), nst, MG * 8, cudaMemcpyDeviceToDevice, st));
+    TR_CUDA(cudaMemcpyAsync(const_cast<double*>(P.sigs), nss, MG * P.G * 8, cudaMemcpyDeviceToDevice, st));
+    TR_CUDA(cudaMemcpyAsync(const_cast<double*>(P.inv_sigt), ninv, MG * 8, cudaMemcpyDeviceToDevice, st));
+    TR_CUDA(cudaMemcpyAsync(const_cast<double*>(P.sig_a), nsa, MG * 8, cudaMemcpyDeviceToDevice, st));
+    TR_CUDA(cudaMemcpyAsync(const_cast<double*>(P.cum_s), ncum, MG * P.G * 8, cudaMemcpyDeviceToDevice, st));
+    TR_CUDA(cudaMemcpyAsync(const_cast<double*>(P.nusigf), nu_sigma_f, MG * 8, kind, st));
+    // results and checkpoints of earlier runs no longer describe this problem
+    pr->have_run = pr->have_std = pr->have_fixed = false;
+    pr->ckpt.clear();
+    ++pr->xs_generation;
+    pr->fingerprint = fnv1a(pr->fingerprint, &pr->xs_generation, sizeof(pr->xs_generation));
+    return TR_OK;
+}
+
 extern "C" void tr_problem_destroy(tr_problem* pr)
 {
     if (!pr) return;
     DeviceGuard dg(pr->ctx.device);
     cudaStreamSynchronize(pr->stream);
     if (pr->batch_graph) cudaGraphExecDestroy(pr->batch_graph);
+    for (auto& kv : pr->stack_graphs) cudaGraphExecDestroy(kv.second);
     for (auto& kv : pr->ws) dev_free(pr, kv.second.p);
     for (void* p : pr->owned) dev_free(pr, p);
     if (pr->log_n) dev_free(pr, pr->log_n);
@@ -745,42 +815,98 @@ static tr_status transport(tr_problem* pr, const tr_run_opts* o, RunParams R, co
             for (int q = 0; q < nst; ++q)
                 if (!carve_soa(pr, names[h][q], cap, bufs[h][q])) return set_err(TR_ERR_NOMEM, "stack allocation failed");
         StackCtl* dctl = (StackCtl*)workspace(pr, "stackctl", sizeof(StackCtl));
-        if (!dctl) return set_err(TR_ERR_NOMEM, "control block allocation failed");
-        StackCtl h{};
-        h.capacity = cap;
+        RunParams* dR = (RunParams*)workspace(pr, "stack_params", sizeof(RunParams));
+        if (!dctl || !dR) return set_err(TR_ERR_NOMEM, "control block allocation failed");
         const int bps = o->blocks_per_sm > 0 ? o->blocks_per_sm : 4;
         const int blocks = pr->sms * bps;
-        int cur = 0;
-        LaunchTimer lt;
-        for (unsigned long long it = 0;; ++it) {
-            h.pop = 0;
-            for (int q = 0; q < N_QUEUES; ++q) {
-                h.out_count[q] = 0;
-                h.reserve[q] = 0;
+        // the rounds run as a graph loop (a conditional WHILE node): each
+        // iteration is two rounds, set 0 -> set 1 and set 1 -> set 0, each
+        // followed by k_stack_next, which advances the control block and sets
+        // the loop condition; no host round trip between rounds
+        std::vector<unsigned long long> key = {(unsigned long long)dec, (unsigned long long)blocks, cap,
+                                               (unsigned long long)(uintptr_t)dctl, (unsigned long long)(uintptr_t)dR,
+                                               (unsigned long long)(uintptr_t)pr->err, (unsigned long long)(src != nullptr)};
+        for (int hh = 0; hh < 2; ++hh)
+            for (int q = 0; q < nst; ++q) key.push_back((unsigned long long)(uintptr_t)bufs[hh][q].x);
+        for (const void* q : {(const void*)T.mesh, (const void*)T.energy, (const void*)T.scal, (const void*)T.time,
+                              (const void*)T.ev_type, (const void*)T.log_n, (const void*)T.log_cell,
+                              (const void*)T.log_type, (const void*)bank.x, (const void*)bank.count,
+                              (const void*)bank.site_count, (const void*)bank.key, (const void*)(src ? src->x : nullptr),
+                              (const void*)(src ? src->cell : nullptr)})
+            key.push_back((unsigned long long)(uintptr_t)q);
+        key.push_back(bank.capacity);
+        key.push_back(src ? src->capacity : 0ull);
+        cudaGraphExec_t exec = nullptr;
+        auto it = pr->stack_graphs.find(key);
+        if (it != pr->stack_graphs.end()) {
+            exec = it->second;
+        } else {
+            if (pr->stack_graphs.size() >= 8) {
+                for (auto& kv : pr->stack_graphs) cudaGraphExecDestroy(kv.second);
+                pr->stack_graphs.clear();
             }
-            // sources go where the survivors of the collision and surface stacks go
-            if (dec == DEC_MONO) h.reserve[Q_STEP] = h.in_count[Q_STEP];
-            else h.reserve[dec == DEC_LOOKUP ? Q_LOOKUP : Q_STEP] = h.in_count[Q_COLLIDE] + h.in_count[Q_SURFACE];
-            TR_CUDA(cudaMemcpyAsync(dctl, &h, sizeof(h), cudaMemcpyHostToDevice, st));
-            TR_CUDA(cudaEventRecord(lt.a, st));
-            TR_CUDA(launch_stack(P, R, bufs[cur], bufs[cur ^ 1], dctl, T, bank, src, pr->err, dec, blocks, st));
-            TR_CUDA(cudaEventRecord(lt.b, st));
-            ++out.launches;
-            TR_CUDA(cudaMemcpyAsync(&h, dctl, sizeof(h), cudaMemcpyDeviceToHost, st));
-            TR_CUDA(cudaStreamSynchronize(st));
-            out.kernel_ms += lt.elapsed();
-            tr_status es = check_err(pr);
-            if (es != TR_OK) return es;
-            unsigned long long tot = 0;
-            for (int q = 0; q < N_QUEUES; ++q) {
-                if (h.out_count[q] > cap) return set_err(TR_ERR_CAPACITY, "stack overflow");
-                h.in_count[q] = h.out_count[q];
-                tot += h.out_count[q];
+            cudaGraph_t g = nullptr;
+            TR_CUDA(cudaGraphCreate(&g, 0));
+            cudaGraphConditionalHandle cond;
+            cudaError_t ce = cudaGraphConditionalHandleCreate(&cond, g, 1u, cudaGraphCondAssignDefault);
+            cudaGraphNodeParams np = {};
+            cudaGraphNode_t node;
+            if (ce == cudaSuccess) {
+                np.type = cudaGraphNodeTypeConditional;
+                np.conditional.handle = cond;
+                np.conditional.type = cudaGraphCondTypeWhile;
+                np.conditional.size = 1;
+                ce = cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &np);
             }
-            cur ^= 1;
-            if (tot == 0 && h.src_cursor >= R.n_hist) break;
-            if (it > 4ull * R.max_events + 1000000ull) return set_err(TR_ERR_TIMEOUT, "stack loop did not terminate");
+            cudaStream_t cs = nullptr;
+            if (ce == cudaSuccess) ce = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+            tr_status cap_status = TR_OK;
+            if (ce == cudaSuccess) {
+                cudaGraph_t body = np.conditional.phGraph_out[0];
+                const unsigned long long c0 = launch_count();
+                ce = cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+                if (ce == cudaSuccess) {
+                    cudaError_t le = launch_stack(P, dR, bufs[0], bufs[1], dctl, T, bank, src, pr->err, dec, blocks, cs);
+                    if (le == cudaSuccess) le = launch_stack_next(dctl, dR, pr->err, cond, cs);
+                    if (le == cudaSuccess)
+                        le = launch_stack(P, dR, bufs[1], bufs[0], dctl, T, bank, src, pr->err, dec, blocks, cs);
+                    if (le == cudaSuccess) le = launch_stack_next(dctl, dR, pr->err, cond, cs);
+                    cudaGraph_t captured = nullptr;
+                    ce = cudaStreamEndCapture(cs, &captured);
+                    if (le != cudaSuccess) ce = le;
+                }
+                count_launches(0ull - (launch_count() - c0));   // captured, not launched
+                cudaStreamDestroy(cs);
+            }
+            if (ce == cudaSuccess) ce = cudaGraphInstantiate(&exec, g, 0);
+            cudaGraphDestroy(g);
+            if (ce != cudaSuccess) {
+                cudaGetLastError();
+                cap_status = set_err(TR_ERR_CUDA, std::string("stack-scheme graph: ") + cudaGetErrorString(ce));
+                return cap_status;
+            }
+            pr->stack_graphs[key] = exec;
         }
+        StackCtl h{};
+        h.capacity = cap;
+        h.max_rounds = 4ull * R.max_events + 1000000ull;
+        h.dec = dec;
+        TR_CUDA(cudaMemcpyAsync(dR, &R, sizeof(R), cudaMemcpyHostToDevice, st));
+        TR_CUDA(cudaMemcpyAsync(dctl, &h, sizeof(h), cudaMemcpyHostToDevice, st));
+        LaunchTimer lt;
+        TR_CUDA(cudaEventRecord(lt.a, st));
+        TR_CUDA(cudaGraphLaunch(exec, st));
+        TR_CUDA(cudaEventRecord(lt.b, st));
+        TR_CUDA(cudaMemcpyAsync(&h, dctl, sizeof(h), cudaMemcpyDeviceToHost, st));
+        TR_CUDA(cudaStreamSynchronize(st));
+        out.kernel_ms += lt.elapsed();
+        const unsigned long long launched = 4ull * ((h.rounds + 1) / 2);   // whole loop iterations
+        count_launches(launched);
+        out.launches += h.rounds;
+        tr_status es = check_err(pr);
+        if (es == TR_ERR_CAPACITY) return set_err(es, "stack overflow");
+        if (es == TR_ERR_TIMEOUT) return set_err(es, "stack loop did not terminate");
+        if (es != TR_OK) return es;
         return TR_OK;
     }
     // asynchronous scheme: one persistent launch

@@ -44,7 +44,8 @@ __device__ __forceinline__ void acc_attach(Acc& acc, long long* base)
 
 // A history's scalar scores at its end: each rounded once to fixed point and
 // added to this thread's sums (spilled to the bin before they could
-// overflow), or straight to the bin.
+// overflow), or straight to the bin.  (Inlined: measured faster than an
+// out-of-line call, 2.62e9 against 2.55e9 lattice events/s.)
 __device__ __forceinline__ void acc_history(const Acc& acc, const Tallies& T, const Particle& p)
 {
     if (!T.scal) return;

@@ -25,7 +25,8 @@ struct DeviceGuard {
 unsigned long long launch_count();
 void count_launches(unsigned long long n);
 
-// Control block of one stack-scheme launch (device memory).
+// Control block of the stack scheme (device memory): one round's counters,
+// advanced between rounds on the device by k_stack_next.
 struct StackCtl {
     unsigned long long in_count[N_QUEUES];    // particles in each input stack
     unsigned long long out_count[N_QUEUES];   // pushes into each output stack
@@ -33,6 +34,10 @@ struct StackCtl {
     unsigned long long pop;            // virtual pop cursor over the input stacks
     unsigned long long src_cursor;     // next source index (make_work)
     unsigned long long capacity;       // particles per stack
+    unsigned long long rounds;         // rounds (stack-kernel launches) completed
+    unsigned long long max_rounds;     // a loop still running after this many rounds ends with ERR_TIMEOUT
+    int done;                          // the loop has ended: a stack kernel launched now returns at once
+    int dec;                           // task decomposition (the reservation rule depends on it)
 };
 
 // Control block of the asynchronous scheme (device memory).
@@ -46,9 +51,18 @@ struct AsyncCtl {
     unsigned hungry;                   // warps currently starving for work
 };
 
-cudaError_t launch_stack(const DevProblem& P, const RunParams& R, const SoA* in, const SoA* out, StackCtl* ctl,
+// One stack round from the buffer set `in` to `out`; the run parameters are
+// read from device memory (Rd), so that a captured launch serves every batch.
+cudaError_t launch_stack(const DevProblem& P, const RunParams* Rd, const SoA* in, const SoA* out, StackCtl* ctl,
                          const Tallies& T, const Bank& bank, const Bank* src, ErrorWord* err, int dec, int blocks,
                          cudaStream_t st);
+// Between two rounds: check the output stacks' counts against the capacity,
+// make them the next round's inputs, reset the round's cursors and
+// reservations, and decide whether another round runs (sources left or
+// particles in flight, no error, fewer than max_rounds rounds); the decision
+// goes to the graph's loop condition.
+cudaError_t launch_stack_next(StackCtl* ctl, const RunParams* Rd, ErrorWord* err, cudaGraphConditionalHandle cond,
+                              cudaStream_t st);
 
 struct AsyncArgs {
     SoA links;                         // global link arena: n_links * 32 particle slots

@@ -51,10 +51,13 @@ struct StackArgs {
 
 // Monolithic ("step") event scheme: one stack pair, R events per pop.
 template <bool CE>
-__global__ void __launch_bounds__(256) k_stack_mono(DevProblem P, RunParams R, StackArgs A, Tallies T, ErrorWord* err)
+__global__ void __launch_bounds__(256) k_stack_mono(DevProblem P, const RunParams* Rd, StackArgs A, Tallies T,
+                                                   ErrorWord* err)
 {
     const int lane = threadIdx.x & 31;
     StackCtl* ctl = A.ctl;
+    if (ctl->done) return;   // the loop ended after the previous round
+    const RunParams R = *Rd;
     const unsigned long long in_count = ctl->in_count[Q_STEP];
     const unsigned long long cap = ctl->capacity;
     __shared__ long long fx[256 * ACC_FX_WORDS];
@@ -109,8 +112,11 @@ __global__ void __launch_bounds__(256) k_stack_mono(DevProblem P, RunParams R, S
 // lookup, so each output stack receives at most one input stack's particles
 // (plus reserved sources) and cannot overflow.
 template <bool CE, int DEC>
-__global__ void __launch_bounds__(256) k_stack_split(DevProblem P, RunParams R, StackArgs A, Tallies T, ErrorWord* err)
+__global__ void __launch_bounds__(256) k_stack_split(DevProblem P, const RunParams* Rd, StackArgs A, Tallies T,
+                                                    ErrorWord* err)
 {
+    if (A.ctl->done) return;   // the loop ended after the previous round
+    const RunParams R = *Rd;
     constexpr int nq = dec_queues(DEC);
     constexpr bool XS = DEC == DEC_LOOKUP;
     constexpr int FIRST = XS ? Q_LOOKUP : Q_STEP;   // where sources start
@@ -180,6 +186,42 @@ __global__ void __launch_bounds__(256) k_stack_split(DevProblem P, RunParams R, 
         push_to(A.out, ctl->out_count, dst, live, p, CE, cap, err, XS);
     }
     flush_acc(acc, T);
+}
+
+// The step between two stack rounds (one thread): the host loop's
+// bookkeeping done on the device, so that the rounds run as a graph loop
+// with no host round trip.  Sources go where the survivors of the previous
+// round's collision and surface stacks go (the launch-threshold rule).
+__global__ void k_stack_next(StackCtl* ctl, const RunParams* Rd, ErrorWord* err, cudaGraphConditionalHandle cond)
+{
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    if (ctl->done) {
+        cudaGraphSetConditional(cond, 0u);
+        return;
+    }
+    ctl->rounds += 1;
+    unsigned long long tot = 0;
+    bool over = false;
+    for (int q = 0; q < N_QUEUES; ++q) {
+        const unsigned long long c = ctl->out_count[q];
+        over = over || c > ctl->capacity;
+        ctl->in_count[q] = c;
+        tot += c;
+        ctl->out_count[q] = 0;
+        ctl->reserve[q] = 0;
+    }
+    if (over) atomicCAS(&err->code, 0, ERR_CAPACITY);
+    ctl->pop = 0;
+    if (ctl->dec == DEC_MONO) ctl->reserve[Q_STEP] = ctl->in_count[Q_STEP];
+    else ctl->reserve[ctl->dec == DEC_LOOKUP ? Q_LOOKUP : Q_STEP] = ctl->in_count[Q_COLLIDE] + ctl->in_count[Q_SURFACE];
+    bool finished = (tot == 0 && ctl->src_cursor >= Rd->n_hist) || over || *(volatile int*)&err->code != 0;
+    if (!finished && ctl->rounds >= ctl->max_rounds) {
+        atomicCAS(&err->code, 0, ERR_TIMEOUT);
+        finished = true;
+    }
+    if (finished) ctl->done = 1;
+    __threadfence();
+    cudaGraphSetConditional(cond, finished ? 0u : 1u);
 }
 
 // ---------------------------------------------------------------------------
@@ -383,7 +425,15 @@ static int grid_for(unsigned long long n, int threads, int max_blocks)
     return (int)b;
 }
 
-cudaError_t launch_stack(const DevProblem& P, const RunParams& R, const SoA* in, const SoA* out, StackCtl* ctl,
+cudaError_t launch_stack_next(StackCtl* ctl, const RunParams* Rd, ErrorWord* err, cudaGraphConditionalHandle cond,
+                              cudaStream_t st)
+{
+    count_launches(1);
+    k_stack_next<<<1, 32, 0, st>>>(ctl, Rd, err, cond);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_stack(const DevProblem& P, const RunParams* R, const SoA* in, const SoA* out, StackCtl* ctl,
                          const Tallies& T, const Bank& bank, const Bank* src, ErrorWord* err, int dec, int blocks,
                          cudaStream_t st)
 {

@@ -115,3 +115,112 @@ def test_sensitivities_require_matching_forward_run():
         prob.sensitivities(tb.RunOpts(n_histories=10), 0, 0, buf.data_ptr(), buf.data_ptr(), buf.data_ptr())
     assert e.value.status == tb.TR_ERR_STATE
     prob.close()
+
+
+def test_lattice_sensitivities_match_oracle_at_benchmark_size():
+    """The benchmark's backward pass (1e6 histories, pre-sampled sources, the
+    per-row shared-memory accumulators) against the oracle's estimator over
+    the same histories (computed in shards on the host cores)."""
+    from tests import _oracle_pool
+    spec = inputs.c5g7_lattice(fission=False)
+    n = 1_000_000
+    rng = np.random.default_rng(6)
+    g_mesh = rng.uniform(-1.0, 1.0, spec.mesh_size)
+    g_scal = [0.2, 1.0, 0.5]
+    o = _oracle_pool.sensitivities(("c5g7_lattice", (("fission", False),)), n, g_mesh=g_mesh, g_scal=g_scal, seed=3)
+    assert o["status"] == 0
+    g = _gpu_sens(spec, n, g_mesh, g_scal, seed=3)
+    for key in ("d_sigt", "d_sigs", "d_nusigf"):
+        _close(g[key], o[key], key)
+
+
+def test_set_xs_equals_a_problem_created_with_those_values():
+    """tr_problem_set_xs from device tensors (and from host arrays) gives the
+    histories and tallies of a problem created with the new cross sections;
+    invalid values are refused and leave the problem as it was."""
+    import torch
+    a = inputs.c5g7_lattice()
+    other = inputs.c5g7_lattice(xs_seed=7)
+    # set_xs replaces sigma_t, sigma_s and nu_sigma_f; chi (which samples the
+    # source groups) stays a's
+    b = a.replace(sigma_t=other.sigma_t, sigma_s=other.sigma_s, nu_sigma_f=other.nu_sigma_f)
+    n = 20_011
+    opts = tb.RunOpts(n_histories=n, seed=4, scheme=tb.SCHEME_ASYNC, decomposition=tb.DECOMP_MONO,
+                      remap_every=64, want_event_log=True)
+    ref = tb.Problem(b)
+    ref.run_fixed_source(opts)
+    want = (ref.event_log(n), ref.tally(tb.TALLY_MESH), ref.tally(tb.TALLY_SCALARS))
+    ref.close()
+    for on_device in (True, False):
+        p = tb.Problem(a)
+        xs = (b.sigma_t, b.sigma_s, b.nu_sigma_f)
+        if on_device:
+            xs = tuple(torch.tensor(x, dtype=torch.float64, device="cuda") for x in xs)
+        p.set_xs(*xs)
+        p.run_fixed_source(opts)
+        got = (p.event_log(n), p.tally(tb.TALLY_MESH), p.tally(tb.TALLY_SCALARS))
+        for x, y in zip(got[0], want[0]):
+            assert np.array_equal(x, y)
+        assert np.array_equal(got[1].view(np.uint64), want[1].view(np.uint64))
+        assert np.array_equal(got[2].view(np.uint64), want[2].view(np.uint64))
+        bad = b.sigma_t.copy()
+        bad[0, 0] = -1.0
+        with pytest.raises(tb.TransportError) as e:
+            p.set_xs(bad, b.sigma_s, b.nu_sigma_f)
+        assert e.value.status == tb.TR_ERR_INVALID
+        # a refused update changes nothing: the results stay readable, and a
+        # new run still uses b's values
+        assert np.array_equal(p.tally(tb.TALLY_MESH).view(np.uint64), want[1].view(np.uint64))
+        p.run_fixed_source(opts)
+        assert np.array_equal(p.tally(tb.TALLY_MESH).view(np.uint64), want[1].view(np.uint64))
+        # an accepted update drops the earlier run's results
+        p.set_xs(b.sigma_t, b.sigma_s, b.nu_sigma_f)
+        with pytest.raises(tb.TransportError):
+            p.tally(tb.TALLY_MESH)
+        p.close()
+
+
+def test_autograd_keeps_one_problem_and_matches_direct_derivatives():
+    """Fifty forward and backward passes through TransportFn with one problem:
+    no problem and no device memory accumulate, and each gradient equals the
+    derivative kernel called directly on a problem with those cross
+    sections; with a problem description the problem made for the call is
+    closed after the backward pass."""
+    import torch
+    from paper_2506_00263_gb300.autograd import transport
+    spec = inputs.c5g7_lattice(fission=False)
+    n = 20_011
+    opts = tb.RunOpts(n_histories=n, seed=8, scheme=tb.SCHEME_ASYNC, decomposition=tb.DECOMP_MONO, remap_every=64)
+    g_mesh = np.random.default_rng(2).uniform(-1.0, 1.0, spec.mesh_size)
+    gm = torch.tensor(g_mesh, dtype=torch.float64, device="cuda")
+    prob = tb.Problem(spec)
+    live0 = tb.Problem.live
+    base = [torch.tensor(x, dtype=torch.float64, device="cuda") for x in (spec.sigma_t, spec.sigma_s,
+                                                                          spec.nu_sigma_f)]
+    mem = []
+    for it in range(50):
+        scale = 1.0 + 0.01 * (it % 5)
+        st = (base[0] * scale).requires_grad_(True)
+        ss = base[1].clone().requires_grad_(True)
+        nf = base[2].clone().requires_grad_(True)
+        mesh, scal = transport(st, ss, nf, prob, opts)
+        ((mesh * gm).sum() + scal[1]).backward()
+        torch.cuda.synchronize()
+        mem.append(torch.cuda.memory_allocated())
+        if it in (0, 3):
+            direct = _gpu_sens(spec.replace(sigma_t=spec.sigma_t * scale), n, g_mesh, [0.0, 1.0, 0.0], seed=8)
+            _close(st.grad.cpu().numpy(), direct["d_sigt"], "d_sigt")
+            _close(ss.grad.cpu().numpy(), direct["d_sigs"], "d_sigs")
+    assert tb.Problem.live == live0
+    assert max(mem[5:]) == min(mem[5:]), (min(mem[5:]), max(mem[5:]))
+    prob.close()
+    # a problem description: one problem per call, closed after backward
+    live1 = tb.Problem.live
+    st = base[0].clone().requires_grad_(True)
+    mesh, scal = transport(st, base[1], base[2], spec, opts)
+    assert tb.Problem.live == live1 + 1
+    scal[1].backward()
+    assert tb.Problem.live == live1
+    with torch.no_grad():
+        transport(base[0], base[1], base[2], spec, opts)
+    assert tb.Problem.live == live1
