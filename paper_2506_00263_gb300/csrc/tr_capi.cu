@@ -61,6 +61,7 @@ struct tr_problem {
     std::vector<unsigned char> ckpt;          // state of a power iteration stopped early (tr_eig_checkpoint)
     uint64_t fingerprint = 0;                 // hash of the geometry, cross sections, source and tally descriptions
     uint64_t xs_generation = 0;               // cross-section updates (tr_problem_set_xs) so far
+    unsigned long long hist_cap = 0;          // stride of the per-history score arrays (histories)
     std::vector<double> hplanes[3];           // host copies of the planes (checkpoint validation)
     std::vector<int> hpin;                    // host copy: 1 where the cell holds a pin
     cudaGraphExec_t batch_graph = nullptr;
@@ -652,6 +653,9 @@ extern "C" void tr_problem_destroy(tr_problem* pr)
 // monolithic launch (16.8M: 2.6 GB of particle records); larger runs sample
 // inside the launch, with the same results.
 constexpr unsigned long long PRESAMPLE_MAX_HIST = 1ull << 24;
+// Largest history count whose scalar scores are stored per history and
+// reduced in a fixed order after the launch (1.6 GB of scores at 2^26).
+constexpr unsigned long long HIST_MAX = 1ull << 26;
 
 static bool carve_soa(tr_problem* pr, const char* name, unsigned long long cap, SoA& s)
 {
@@ -756,6 +760,7 @@ static Tallies make_tallies(tr_problem* pr, bool log)
     T.log_cell = log ? pr->log_cell : nullptr;
     T.log_type = log ? pr->log_type : nullptr;
     T.err = pr->err;
+    T.hist_f = T.hist_a = T.hist_p = nullptr;
     return T;
 }
 
@@ -803,8 +808,24 @@ static tr_status transport(tr_problem* pr, const tr_run_opts* o, RunParams R, co
     const DevProblem& P = pr->dp;
     const cudaStream_t st = pr->stream;
     const int dec = o->decomposition;   // DEC_MONO, DEC_SPLIT, DEC_LOOKUP (same values as TR_DECOMP_*)
-    const Tallies T = make_tallies(pr, R.want_log != 0);
+    Tallies T = make_tallies(pr, R.want_log != 0);
     if (R.n_hist == 0) return TR_OK;
+    // scalar scores: each ended history stores its sums (by history index),
+    // reduced in a fixed order after the launch (runs above HIST_MAX
+    // histories round them into per-thread fixed-point sums instead)
+    double* hist_partial = nullptr;
+    if (R.n_hist <= HIST_MAX) {
+        // the arrays' stride only grows (in steps of 2^16 histories), so
+        // their addresses, which a captured stack-scheme loop bakes in, stay
+        // put from batch to batch
+        pr->hist_cap = std::max(pr->hist_cap, (R.n_hist + 65535) & ~65535ull);
+        double* h = (double*)workspace(pr, "hist_sums", 3 * pr->hist_cap * sizeof(double));
+        hist_partial = (double*)workspace(pr, "hist_partial", hist_partials(pr->hist_cap) * sizeof(double));
+        if (!h || !hist_partial) return set_err(TR_ERR_NOMEM, "history score buffer allocation failed");
+        T.hist_f = h;
+        T.hist_a = h + pr->hist_cap;
+        T.hist_p = h + 2 * pr->hist_cap;
+    }
     if (o->scheme == TR_SCHEME_STACK) {
         unsigned long long cap = o->queue_capacity ? o->queue_capacity : std::min<unsigned long long>(R.n_hist, 1ull << 22);
         cap = std::max<unsigned long long>((cap + 31) & ~31ull, 64);
@@ -829,6 +850,7 @@ static tr_status transport(tr_problem* pr, const tr_run_opts* o, RunParams R, co
         for (int hh = 0; hh < 2; ++hh)
             for (int q = 0; q < nst; ++q) key.push_back((unsigned long long)(uintptr_t)bufs[hh][q].x);
         for (const void* q : {(const void*)T.mesh, (const void*)T.energy, (const void*)T.scal, (const void*)T.time,
+                              (const void*)T.hist_f, (const void*)T.hist_a,
                               (const void*)T.ev_type, (const void*)T.log_n, (const void*)T.log_cell,
                               (const void*)T.log_type, (const void*)bank.x, (const void*)bank.count,
                               (const void*)bank.site_count, (const void*)bank.key, (const void*)(src ? src->x : nullptr),
@@ -907,7 +929,8 @@ static tr_status transport(tr_problem* pr, const tr_run_opts* o, RunParams R, co
         if (es == TR_ERR_CAPACITY) return set_err(es, "stack overflow");
         if (es == TR_ERR_TIMEOUT) return set_err(es, "stack loop did not terminate");
         if (es != TR_OK) return es;
-        return TR_OK;
+        TR_CUDA(launch_hist_reduce(T, R.n_hist, hist_partial, st));
+        return hist_partial ? check_err(pr) : TR_OK;   // the reduction reports an out-of-range total
     }
     // asynchronous scheme: one persistent launch
     int S = o->stash_slots > 0 ? o->stash_slots : 512;
@@ -960,7 +983,8 @@ static tr_status transport(tr_problem* pr, const tr_run_opts* o, RunParams R, co
     out.spills += hc.spills;
     out.refills += hc.refills;
     if (hc.live != 0) return set_err(TR_ERR_STATE, "asynchronous run ended with live particles");
-    return TR_OK;
+    TR_CUDA(launch_hist_reduce(T, R.n_hist, hist_partial, st));
+    return hist_partial ? check_err(pr) : TR_OK;   // the reduction reports an out-of-range total
 }
 
 static RunParams base_params(const tr_run_opts* o, unsigned long long n)
@@ -1477,7 +1501,7 @@ std::vector<unsigned long long> batch_signature(tr_problem* const* probs, int32_
 static tr_status enqueue_batched(tr_problem* lead, tr_problem* const* probs, int32_t n, const uint64_t* nh,
                                  const tr_run_opts* o, const BatchTuning& tune, DevProblem* d_probs, Tallies* d_tal,
                                  unsigned long long* d_off, ScaleJob* d_jobs, int n_jobs, const AsyncArgs& A0,
-                                 unsigned long long total)
+                                 unsigned long long total, int maxch, double* hist_partial)
 {
     const cudaStream_t st = lead->stream;
     for (int32_t i = 0; i < n; ++i) {
@@ -1502,6 +1526,7 @@ static tr_status enqueue_batched(tr_problem* lead, tr_problem* const* probs, int
     R.remap_every = tune.remap_every;
     R.want_log = o->want_event_log ? 1 : 0;
     if (total > 0) TR_CUDA(launch_async_batched(lead->dp, R, A, lead->err, lead->sms * tune.blocks_per_sm, st));
+    if (hist_partial) TR_CUDA(launch_hist_reduce_batched(d_tal, d_off, n, maxch, hist_partial, lead->err, st));
     TR_CUDA(launch_scale_jobs(d_jobs, n_jobs, st));
     return TR_OK;
 }
@@ -1570,11 +1595,30 @@ extern "C" tr_status tr_run_batched(tr_problem* const* probs, int32_t n, const u
     std::vector<Tallies> ht(n);
     std::vector<unsigned long long> hoff(n + 1, 0);
     std::vector<ScaleJob> hj;
+    for (int32_t i = 0; i < n; ++i) hoff[i + 1] = hoff[i] + n_histories[i];
+    // scalar scores stored per history (each member in its own range) and
+    // reduced per member in a fixed order after the launch, as single runs do
+    double* hist = nullptr;
+    double* hist_partial = nullptr;
+    int maxch = 0;
+    unsigned long long hstride = 0;
+    if (total <= HIST_MAX) {
+        hstride = (total + 65535) & ~65535ull;
+        for (int32_t i = 0; i < n; ++i) maxch = std::max(maxch, hist_chunks(n_histories[i]));
+        hist = (double*)workspace(lead, "batch_hist", 3 * std::max(hstride, 1ull) * sizeof(double));
+        hist_partial = (double*)workspace(lead, "batch_hist_partial",
+                                          3 * (size_t)n * (size_t)std::max(maxch, 1) * sizeof(double));
+        if (!hist || !hist_partial) return set_err(TR_ERR_NOMEM, "history score buffer allocation failed");
+    }
     for (int32_t i = 0; i < n; ++i) {
         hp[i] = probs[i]->dp;
         ht[i] = make_tallies(probs[i], opts->want_event_log != 0);
         ht[i].err = lead->err;   // the batch's one error word
-        hoff[i + 1] = hoff[i] + n_histories[i];
+        if (hist) {
+            ht[i].hist_f = hist + hoff[i];
+            ht[i].hist_a = hist + hstride + hoff[i];
+            ht[i].hist_p = hist + 2 * hstride + hoff[i];
+        }
         const double inv = n_histories[i] ? 1.0 / (double)n_histories[i] : 0.0;
         if (probs[i]->dp.mesh_size) hj.push_back({probs[i]->raw_mesh, probs[i]->res_mesh, probs[i]->dp.mesh_size, inv});
         if (probs[i]->dp.energy_size)
@@ -1624,7 +1668,8 @@ extern "C" tr_status tr_run_batched(tr_problem* const* probs, int32_t n, const u
         BatchTuning pick = cands[0];
         for (const BatchTuning& t : cands) {
             TR_CUDA(cudaEventRecord(e0, st));
-            s = enqueue_batched(lead, probs, n, sample.data(), opts, t, d_probs, d_tal, d_soff, d_jobs, 0, A, stotal);
+            s = enqueue_batched(lead, probs, n, sample.data(), opts, t, d_probs, d_tal, d_soff, d_jobs, 0, A, stotal,
+                                maxch, hist_partial);
             if (s != TR_OK) return s;
             TR_CUDA(cudaEventRecord(e1, st));
             TR_CUDA(cudaEventSynchronize(e1));
@@ -1654,8 +1699,10 @@ extern "C" tr_status tr_run_batched(tr_problem* const* probs, int32_t n, const u
     gkey.push_back((unsigned long long)tune.remap_every);
     for (const void* q : {(const void*)d_probs, (const void*)d_tal, (const void*)d_off, (const void*)d_jobs,
                           (const void*)A.links.x, (const void*)A.link_next, (const void*)A.link_type,
-                          (const void*)A.link_fill, (const void*)A.ctl, (const void*)lead->err})
+                          (const void*)A.link_fill, (const void*)A.ctl, (const void*)lead->err, (const void*)hist,
+                          (const void*)hist_partial})
         gkey.push_back((unsigned long long)(uintptr_t)q);
+    gkey.push_back((unsigned long long)maxch);
     for (int32_t i = 0; i < n; ++i)
         for (const void* q : {(const void*)probs[i]->raw_mesh, (const void*)probs[i]->raw_energy,
                               (const void*)probs[i]->raw_scal, (const void*)probs[i]->raw_time,
@@ -1676,7 +1723,7 @@ extern "C" tr_status tr_run_batched(tr_problem* const* probs, int32_t n, const u
         cudaStream_t saved = lead->stream;
         lead->stream = cap;
         s = enqueue_batched(lead, probs, n, n_histories, opts, tune, d_probs, d_tal, d_off, d_jobs, (int)hj.size(), A,
-                            total);
+                            total, maxch, hist_partial);
         lead->stream = saved;
         const cudaError_t ce = cudaStreamEndCapture(cap, &g);
         cudaStreamDestroy(cap);

@@ -42,26 +42,27 @@ __device__ __forceinline__ void acc_attach(Acc& acc, long long* base)
     acc.fx[0] = acc.fx[1] = acc.fx[2] = 0;
 }
 
-// A history's scalar scores at its end: each rounded once to fixed point and
-// added to this thread's sums (spilled to the bin before they could
-// overflow), or straight to the bin.  (Inlined: measured faster than an
-// out-of-line call, 2.62e9 against 2.55e9 lattice events/s.)
-__device__ __forceinline__ void acc_history(const Acc& acc, const Tallies& T, const Particle& p)
+// A history's scalar scores at its end, when no per-history buffer is given
+// (the allocation-free entry, batched launches, runs above 2^26 histories):
+// each rounded once to fixed point and added to this thread's sums (spilled
+// to the bin before they could overflow), or straight to the bin.  Out of
+// line, so that the kernels' hot loops carry only the call.
+static __device__ __noinline__ void acc_history_sums(long long* fx, FixBin* scal, ErrorWord* err, double hf,
+                                                     double ha, double hp)
 {
-    if (!T.scal) return;
-    const double h[3] = {p.hf, p.ha, p.hp};
+    const double h[3] = {hf, ha, hp};
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
         const double c = h[k];
-        if (acc.fx && fix_small(c)) {
-            long long s = acc.fx[k] + fix_round(c);
+        if (fx && fix_small(c)) {
+            long long s = fx[k] + fix_round(c);
             if (fix_sum_full(s)) {
-                fix_add_sum(T.scal + k, s);
+                fix_add_sum(scal + k, s);
                 s = 0;
             }
-            acc.fx[k] = s;
+            fx[k] = s;
         } else if (dbits(c) << 1) {
-            if (!fix_add(T.scal + k, c)) tally_range_error(T);
+            if (!fix_add(scal + k, c) && err) atomicCAS(&err->code, 0, ERR_RANGE);
         }
     }
 }
@@ -89,7 +90,7 @@ struct MeshAtomic {
     const Tallies& T;
     __device__ __forceinline__ void operator()(int i, double l) const
     {
-        if (!fix_add(T.mesh + i, l)) tally_range_error(T);
+        if (!fix_add_nn(T.mesh + i, l)) tally_range_error(T);   // l > 0
     }
 };
 struct MeshWeighted {
@@ -196,7 +197,7 @@ __device__ __forceinline__ void energy_tally(const DevProblem& P, const Tallies&
         const int mid = (lo + hi) >> 1;
         if (dbits(__ldg(P.e_edges + mid)) <= eb) lo = mid; else hi = mid;
     }
-    if (!fix_add(T.energy + m * nb + lo, L)) tally_range_error(T);
+    if (!fix_add_nn(T.energy + m * nb + lo, L)) tally_range_error(T);   // L > 0
 }
 
 // ---------------------------------------------------------------------------
@@ -278,7 +279,7 @@ static __device__ __noinline__ void time_bins(FixBin* tally, ErrorWord* err, int
         if (lo >= t1) break;
         lo = fmax(lo, t0);
         hi = fmin(hi, t1);
-        if (hi > lo && !fix_add(tally + b, (hi - lo) / inv_v) && err) atomicCAS(&err->code, 0, ERR_RANGE);
+        if (hi > lo && !fix_add_nn(tally + b, (hi - lo) / inv_v) && err) atomicCAS(&err->code, 0, ERR_RANGE);
     }
 }
 
@@ -649,7 +650,13 @@ __device__ __forceinline__ bool finish_event(const DevProblem& P, const RunParam
         type = EV_MAXEV;
     }
     if (!alive) {
-        acc_history(acc, T, p);
+        if (T.hist_f) {
+            T.hist_f[p.id] = p.hf;
+            T.hist_a[p.id] = p.ha;
+            T.hist_p[p.id] = p.hp;
+        } else if (T.scal) {
+            acc_history_sums(acc.fx, T.scal, T.err, p.hf, p.ha, p.hp);
+        }
         acc.fin[type] += 1u;
         if (R.want_log) {
             T.log_n[p.id] = p.n;

@@ -144,6 +144,19 @@ __device__ __forceinline__ bool fix_add(FixBin* bin, double c)
     return ok;
 }
 
+// The same for a non-negative contribution (a track length): below 2^14 the
+// rounded value X fits one 64-bit word and splits with two integer
+// operations; larger values take the general path.
+__device__ __forceinline__ bool fix_add_nn(FixBin* bin, double c)
+{
+    const unsigned long long b = fix_bits(c);
+    if ((b >> 52) >= (unsigned long long)(1023 + 14)) return fix_add(bin, c);
+    const unsigned long long x = fix_mag_small(b);
+    atomicAdd(&bin->lo, x & FIX_LO_MASK);
+    atomicAdd(&bin->hi, x >> FIX_LO);
+    return true;
+}
+
 __device__ __forceinline__ void fix_add_sum(FixBin* bin, long long x)
 {
     unsigned long long lo, hi;

@@ -113,6 +113,16 @@ cudaError_t launch_pop_write(const Bank& in, unsigned long long m, const unsigne
                              const unsigned long long* offset, const Bank& out, cudaStream_t st);
 cudaError_t launch_eig_accumulate(const FixBin* raw, int n, double inv_n, double* sum, double* sq, cudaStream_t st);
 cudaError_t launch_scale(const double* in, int n, double s, double* out, cudaStream_t st);
+// The per-history scalar scores of histories [0, n) (T.hist_*) summed in a
+// fixed order and added to T.scal; partial: 3 ceil(n / 4096) doubles of scratch.
+cudaError_t launch_hist_reduce(const Tallies& T, unsigned long long n, double* partial, cudaStream_t st);
+inline unsigned long long hist_partials(unsigned long long n) { return 3 * ((n + 4095) / 4096) + 3; }
+// Batched launches: problem p's histories [0, off[p+1] - off[p]) reduced from
+// tal[p].hist_* into tal[p].scal; maxch = the most 4096-history chunks of
+// any problem; partial: 3 n_probs maxch doubles of scratch.
+cudaError_t launch_hist_reduce_batched(const Tallies* tal, const unsigned long long* off, int n_probs, int maxch,
+                                      double* partial, ErrorWord* err, cudaStream_t st);
+inline int hist_chunks(unsigned long long n) { return (int)((n + 4095) / 4096); }
 // out[i] = (value of fixed-point bin in[i]) * s
 cudaError_t launch_fix_scale(const FixBin* in, int n, double s, double* out, cudaStream_t st);
 cudaError_t launch_eig_finish(const double* sum, const double* sq, int n, double na, double* mean, double* sd,

@@ -366,6 +366,105 @@ __global__ void k_pop_write(Bank in, unsigned long long m, const unsigned* __res
     }
 }
 
+// Fixed-order reduction of the per-history scalar scores: block b sums the
+// HIST_CHUNK histories [b HIST_CHUNK, (b + 1) HIST_CHUNK) -- thread t the
+// elements t, t + 256, ... in turn, then a fixed tree over the threads --
+// into partial[3 b + k]; one block then sums the partials the same way and
+// writes each total, rounded once to fixed point, to its scalar bin.  The
+// order depends on n alone, so the sums are the same for any schedule.
+constexpr int HIST_CHUNK = 4096;
+
+__device__ __forceinline__ double block_sum_fixed(double v, double* sh)
+{
+    sh[threadIdx.x] = v;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) sh[threadIdx.x] = sh[threadIdx.x] + sh[threadIdx.x + w];
+        __syncthreads();
+    }
+    const double r = sh[0];
+    __syncthreads();
+    return r;
+}
+
+__global__ void __launch_bounds__(256) k_hist_partial(const double* __restrict__ hf, const double* __restrict__ ha,
+                                                      const double* __restrict__ hp, unsigned long long n,
+                                                      double* __restrict__ partial)
+{
+    __shared__ double sh[256];
+    const unsigned long long b0 = (unsigned long long)blockIdx.x * HIST_CHUNK;
+    const double* src[3] = {hf, ha, hp};
+    for (int k = 0; k < 3; ++k) {
+        double s = 0.0;
+        for (unsigned long long i = b0 + threadIdx.x; i < b0 + HIST_CHUNK && i < n; i += blockDim.x) s = s + src[k][i];
+        const double t = block_sum_fixed(s, sh);
+        if (threadIdx.x == 0) partial[3 * (unsigned long long)blockIdx.x + k] = t;
+    }
+}
+
+__global__ void __launch_bounds__(256) k_hist_final(const double* __restrict__ partial, unsigned long long nb,
+                                                    FixBin* scal, ErrorWord* err)
+{
+    __shared__ double sh[256];
+    for (int k = 0; k < 3; ++k) {
+        double s = 0.0;
+        for (unsigned long long b = threadIdx.x; b < nb; b += blockDim.x) s = s + partial[3 * b + k];
+        const double t = block_sum_fixed(s, sh);
+        if (threadIdx.x == 0) {
+            unsigned long long lo, hi;
+            if (!fix_split(t, lo, hi)) atomicCAS(&err->code, 0, ERR_RANGE);
+            scal[k].lo += lo;
+            scal[k].hi += hi;
+        }
+    }
+}
+
+// The same for a batched launch: problem p = blockIdx.y reduces its
+// histories [0, off[p+1] - off[p]) from its own per-history arrays, chunk
+// blockIdx.x of at most `maxch`, into partial[(p maxch + chunk) 3 + k]; then
+// one block per problem sums its chunks in order into its scalar bins.
+__global__ void __launch_bounds__(256) k_hist_partial_batched(const Tallies* __restrict__ tal,
+                                                              const unsigned long long* __restrict__ off, int maxch,
+                                                              double* __restrict__ partial)
+{
+    __shared__ double sh[256];
+    const int p = blockIdx.y;
+    const unsigned long long n = off[p + 1] - off[p];
+    const unsigned long long b0 = (unsigned long long)blockIdx.x * HIST_CHUNK;
+    if (b0 >= n && blockIdx.x > 0) return;   // the whole block leaves together
+    const Tallies T = tal[p];
+    const double* src[3] = {T.hist_f, T.hist_a, T.hist_p};
+    for (int k = 0; k < 3; ++k) {
+        double s = 0.0;
+        for (unsigned long long i = b0 + threadIdx.x; i < b0 + HIST_CHUNK && i < n; i += blockDim.x) s = s + src[k][i];
+        const double t = block_sum_fixed(s, sh);
+        if (threadIdx.x == 0) partial[((unsigned long long)p * maxch + blockIdx.x) * 3 + k] = t;
+    }
+}
+
+__global__ void __launch_bounds__(256) k_hist_final_batched(const Tallies* __restrict__ tal,
+                                                            const unsigned long long* __restrict__ off, int maxch,
+                                                            const double* __restrict__ partial, ErrorWord* err)
+{
+    __shared__ double sh[256];
+    const int p = blockIdx.x;
+    const unsigned long long n = off[p + 1] - off[p];
+    const unsigned long long nb = n ? (n + HIST_CHUNK - 1) / HIST_CHUNK : 0;
+    FixBin* scal = tal[p].scal;
+    for (int k = 0; k < 3; ++k) {
+        double s = 0.0;
+        for (unsigned long long b = threadIdx.x; b < nb; b += blockDim.x)
+            s = s + partial[((unsigned long long)p * maxch + b) * 3 + k];
+        const double t = block_sum_fixed(s, sh);
+        if (threadIdx.x == 0 && nb) {
+            unsigned long long lo, hi;
+            if (!fix_split(t, lo, hi)) atomicCAS(&err->code, 0, ERR_RANGE);
+            scal[k].lo += lo;
+            scal[k].hi += hi;
+        }
+    }
+}
+
 // Active-batch statistics: sum and sum of squares of (bin value) / n per bin.
 __global__ void k_eig_accumulate(const FixBin* __restrict__ raw, int n, double inv_n, double* __restrict__ sum,
                                  double* __restrict__ sq)
@@ -513,6 +612,26 @@ cudaError_t launch_scale(const double* in, int n, double s, double* out, cudaStr
     if (n <= 0) return cudaSuccess;
     count_launches(1);
     k_scale<<<grid_for(n, 256, 1024), 256, 0, st>>>(in, n, s, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_hist_reduce(const Tallies& T, unsigned long long n, double* partial, cudaStream_t st)
+{
+    if (n == 0 || !T.hist_f) return cudaSuccess;
+    const unsigned long long nb = (n + HIST_CHUNK - 1) / HIST_CHUNK;
+    count_launches(2);
+    k_hist_partial<<<(unsigned)nb, 256, 0, st>>>(T.hist_f, T.hist_a, T.hist_p, n, partial);
+    k_hist_final<<<1, 256, 0, st>>>(partial, nb, T.scal, T.err);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_hist_reduce_batched(const Tallies* tal, const unsigned long long* off, int n_probs, int maxch,
+                                      double* partial, ErrorWord* err, cudaStream_t st)
+{
+    if (n_probs <= 0 || maxch <= 0) return cudaSuccess;
+    count_launches(2);
+    k_hist_partial_batched<<<dim3((unsigned)maxch, (unsigned)n_probs), 256, 0, st>>>(tal, off, maxch, partial);
+    k_hist_final_batched<<<(unsigned)n_probs, 256, 0, st>>>(tal, off, maxch, partial, err);
     return cudaGetLastError();
 }
 
