@@ -65,6 +65,8 @@ class OrcProblem(C.Structure):
         ("mesh_lo", C.c_double * 3), ("mesh_hi", C.c_double * 3),
         ("e_edges", C.POINTER(C.c_double)),
         ("inv_vel", C.POINTER(C.c_double)), ("n_tbins", C.c_int32), ("t_cen", C.c_double),
+        ("ww_lo", C.POINTER(C.c_double)), ("ww_upper", C.c_double), ("ww_survival", C.c_double),
+        ("ww_max_split", C.c_int32),
     ]
 
 
@@ -223,6 +225,10 @@ class _Marshalled:
         s.n_tbins = int(getattr(prob, "n_time_bins", 0) or 0)
         if getattr(prob, "inv_velocity", None) is not None:
             s.inv_vel = f64(prob.inv_velocity)
+        if getattr(prob, "ww_lower", None) is not None:
+            s.ww_lo = f64(prob.ww_lower)
+            s.ww_upper, s.ww_survival = float(prob.ww_upper), float(prob.ww_survival)
+            s.ww_max_split = int(prob.ww_max_split)
         self.s = s
 
 

@@ -98,6 +98,9 @@ static void rng_block(uint64_t seed, uint32_t tag, uint64_t id, uint32_t n, uint
 #define BLK_ANGLE 1u     /* (CM cosine of an elastic scatter, unused) */
 #define BLK_FISSION 2u   /* (number of fission sites, unused) */
 #define BLK_AZIMUTH 3u   /* 3 + t: azimuth rejection try t, t < 64 */
+#define BLK_CLOSE 4000u  /* (closeout roulette, unused) */
+#define BLK_SPLIT 4001u  /* 4001 + c: stream tag of split copy c (word 0), c < 64 */
+#define MAX_SPLIT 64
 #define N_AZIMUTH_TRIES 64u
 #define BLK_SITE 100u    /* 100 + c: fission site c (chi sample, unused) */
 #define BLK_POS 200u     /* 200 + 2t, 201 + 2t: source position trial t */
@@ -452,6 +455,9 @@ typedef struct {
     struct orc_rec { int m, g, collided, react, h; double len, f; } *rec;
     int rec_n, rec_cap, recording;
     const double *gw_mesh, *gw_scal;
+    /* weight windows: the current family's split copies waiting to run */
+    struct particle_s *split;
+    int split_n, split_cap;
 } ctx;
 
 static int setup(ctx *C, const orc_problem *P)
@@ -516,6 +522,7 @@ static int setup(ctx *C, const orc_problem *P)
 static void teardown(ctx *C)
 {
     free(C->rec);
+    free(C->split);
     free(C->inv_sigt); free(C->cum_s); free(C->sig_a); free(C->cum_chi); free(C->slope);
     free(C->mesh); free(C->energy); free(C->time);
     free(C->bank_pos); free(C->bank_g); free(C->bank_cell); free(C->bank_E);
@@ -535,15 +542,16 @@ static void clear_tallies(ctx *C)
 /* ------------------------------------------------------------------------ */
 /* Particle state                                                            */
 /* ------------------------------------------------------------------------ */
-typedef struct {
+typedef struct particle_s {
     double x[3], d[3], E;
     double t;                            /* time since the source (timed problems) */
     int32_t g, ci[3], in;
     uint32_t n;
-    uint64_t id;
+    uint64_t id;                         /* random-stream id: batch << 32 | index, a split copy's tag xored into the high word */
     int alive, final_type;
     double track;
     uint32_t coll;
+    double w;                            /* statistical weight (1 at birth; the closeout changes it) */
 } particle;
 
 static int64_t cell_lin(const orc_problem *P, const particle *p)
@@ -716,7 +724,9 @@ static void mesh_range(const orc_problem *P, int a, double x0, double x1, int *i
     *i1 = (int)f1;
 }
 
-static void score_mesh(ctx *C, const double p0[3], const double d[3], double len, int g, double *out)
+/* Track length of the segment in each mesh cell it crosses, times the
+ * weight w, added to the mesh tally (or to out). */
+static void score_mesh(ctx *C, const double p0[3], const double d[3], double len, int g, double *out, double w)
 {
     const orc_problem *P = C->P;
     if (!P->has_mesh || !(len > 0.0)) return;
@@ -736,7 +746,7 @@ static void score_mesh(ctx *C, const double p0[3], const double d[3], double len
                 if (l > 0.0) {
                     int64_t v = ((int64_t)idx[2] * P->mesh_n[1] + idx[1]) * P->mesh_n[0] + idx[0];
                     if (out) out[goff + v] += l;
-                    else nadd(&C->mesh[goff + v], l);
+                    else nadd(&C->mesh[goff + v], w * l);
                 }
             }
 }
@@ -748,17 +758,20 @@ double orc_mesh_segment(const orc_problem *P, const double p0[3], const double d
     C.P = P;
     C.G = P->n_grp;
     C.mesh_vox = (int64_t)P->mesh_n[0] * P->mesh_n[1] * P->mesh_n[2];
-    score_mesh(&C, p0, dir, len, 0, mesh);
+    score_mesh(&C, p0, dir, len, 0, mesh, 1.0);
     return len;
 }
 
+/* The segment's scores: its track length times the particle's weight (1 in
+ * analog runs, so the weighted scores are the plain track lengths). */
 static void score_segment(ctx *C, const particle *p, const double p0[3], double len, int m, const xsval *X)
 {
     const orc_problem *P = C->P;
-    score_mesh(C, p0, p->d, len, p->g, NULL);
-    nadd(&C->scal[0], len);
-    nadd(&C->scal[1], len * X->sa);
-    nadd(&C->scal[2], len * X->nsf);
+    const double wl = p->w * len;
+    score_mesh(C, p0, p->d, len, p->g, NULL, p->w);
+    nadd(&C->scal[0], wl);
+    nadd(&C->scal[1], wl * X->sa);
+    nadd(&C->scal[2], wl * X->nsf);
     if (P->n_ebins > 0 && P->xs_kind == 1) {
         const double *e = P->e_edges;
         int nb = P->n_ebins;
@@ -768,7 +781,7 @@ static void score_segment(ctx *C, const particle *p, const double p0[3], double 
                 int mid = lo + (hi - lo) / 2;
                 if (e[mid] <= p->E) lo = mid; else hi = mid;
             }
-            nadd(&C->energy[(int64_t)m * nb + lo], len);
+            nadd(&C->energy[(int64_t)m * nb + lo], wl);
         }
     }
 }
@@ -888,6 +901,7 @@ static int source_particle(ctx *C, particle *p, uint64_t id, const double *site_
         }
     }
     p->n = 1;
+    p->w = 1.0;
     C->events_by_type[ORC_SOURCE]++;
     return ORC_OK;
 }
@@ -983,7 +997,7 @@ static void collide(ctx *C, particle *p, int m, const xsval *X, double xi_react)
  * the segment occupies [t0, t1] in time; each uniform bin b of width
  * w = t_cen / n_tbins gets the track length spent in it, (hi - lo) / inv_v
  * with [lo, hi] = [t0, t1] clipped to [b w, (b + 1) w]. */
-static void score_time(ctx *C, double t0, double t1, double inv_v)
+static void score_time(ctx *C, double t0, double t1, double inv_v, double wt)
 {
     const orc_problem *P = C->P;
     if (P->n_tbins <= 0 || !(t1 > t0)) return;
@@ -996,7 +1010,76 @@ static void score_time(ctx *C, double t0, double t1, double inv_v)
         if (lo >= t1) break;
         if (t0 > lo) lo = t0;
         if (t1 < hi) hi = t1;
-        if (hi > lo) nadd(&C->time[b], (hi - lo) / inv_v);
+        if (hi > lo) nadd(&C->time[b], wt * ((hi - lo) / inv_v));
+    }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Closeout (Sec. 4: weights and weight windows for the particle's next loop */
+/* iteration).  Our reading: the window of the particle's tally-mesh voxel   */
+/* (i_a = floor((x_a - lo_a) (1 / ((hi_a - lo_a) / n_a))), outside the mesh: */
+/* none) and group has lower bound L (0: none), upper bound ww_upper L and   */
+/* survival weight S = ww_survival L.  Below L: Russian roulette, survive    */
+/* with probability w / S (xi S < w, xi the first uniform of block BLK_CLOSE */
+/* at the particle's event count n) at weight S, else the history ends as    */
+/* CUTOFF.  Above the upper bound: k = min(ceil(w / U), ww_max_split) copies */
+/* of weight w / k; the particle continues as copy 0 and copy c = 1..k-1     */
+/* takes the stream tag t_c = word 0 of block BLK_SPLIT + c, with bit 31 set,*/
+/* xored into the high word of its stream id.  Copies are pushed on the     */
+/* family's stack and run after the particle.                                */
+/* ------------------------------------------------------------------------ */
+static int ww_voxel(const orc_problem *P, const particle *p)
+{
+    if (!P->has_mesh) return -1;
+    int idx[3];
+    for (int a = 0; a < 3; ++a) {
+        const double w = (P->mesh_hi[a] - P->mesh_lo[a]) / (double)P->mesh_n[a];
+        const double t = floor((p->x[a] - P->mesh_lo[a]) * (1.0 / w));
+        if (!(t >= 0.0) || !(t < (double)P->mesh_n[a])) return -1;
+        idx[a] = (int)t;
+    }
+    return (idx[2] * P->mesh_n[1] + idx[1]) * P->mesh_n[0] + idx[0];
+}
+
+static void closeout(ctx *C, particle *p)
+{
+    const orc_problem *P = C->P;
+    const int v = ww_voxel(P, p);
+    if (v < 0) return;
+    const int g = P->xs_kind == 0 ? p->g : 0;
+    const int G = P->xs_kind == 0 ? C->G : 1;
+    const double L = P->ww_lo[(int64_t)v * G + g];
+    if (!(L > 0.0)) return;
+    if (p->w < L) {
+        const double S = P->ww_survival * L;
+        double xi[2];
+        rng_block(C->seed, C->tag, p->id, p->n, BLK_CLOSE, xi);
+        if (xi[0] * S < p->w) {
+            p->w = S;
+        } else {
+            kill(p, ORC_CUTOFF);
+        }
+        return;
+    }
+    const double U = P->ww_upper * L;
+    if (!(p->w > U)) return;
+    int k = (int)ceil(p->w / U);
+    if (k > P->ww_max_split) k = P->ww_max_split;
+    if (k < 2) return;
+    p->w = p->w / (double)k;
+    for (int c = 1; c < k; ++c) {
+        uint32_t r[4];
+        rng_words(C->seed, C->tag, p->id, p->n, BLK_SPLIT + (uint32_t)c, r);
+        const uint64_t tag = (uint64_t)(r[0] | 0x80000000u);
+        if (C->split_n == C->split_cap) {
+            C->split_cap = C->split_cap ? 2 * C->split_cap : 64;
+            C->split = realloc(C->split, sizeof(particle) * (size_t)C->split_cap);
+        }
+        particle q = *p;
+        q.id = p->id ^ (tag << 32);
+        q.track = 0.0;
+        q.coll = 0;
+        C->split[C->split_n++] = q;
     }
 }
 
@@ -1086,7 +1169,7 @@ static void event(ctx *C, particle *p)
     if (P->t_cen > 0.0) {
         double t0 = p->t;
         p->t = census ? P->t_cen : fma(dist, inv_v, p->t);
-        score_time(C, t0, p->t, inv_v);
+        score_time(C, t0, p->t, inv_v, p->w);
     }
     p->track += dist;
     if (C->recording) record_event(C, p, m, collided, dist, weighted_segment(C, p, p0, dist, &X));
@@ -1134,6 +1217,7 @@ static void event(ctx *C, particle *p)
     }
     p->n++;
     if (p->alive && p->n >= C->max_events) kill(p, ORC_MAXEV);
+    if (p->alive && P->ww_lo) closeout(C, p);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -1171,6 +1255,7 @@ int orc_fixed_source(const orc_problem *P, orc_fixed *o)
         particle p;
         st = source_particle(&C, &p, id, NULL, 0, 0, 0.0);
         if (st) break;
+        C.split_n = 0;
         while (p.alive) event(&C, &p);
         o->final_by_type[p.final_type]++;
         if (o->log_n) o->log_n[i] = p.n;
@@ -1178,6 +1263,12 @@ int orc_fixed_source(const orc_problem *P, orc_fixed *o)
         if (o->log_type) o->log_type[i] = (uint8_t)p.final_type;
         if (o->hist_track) o->hist_track[i] = p.track;
         if (o->hist_coll) o->hist_coll[i] = p.coll;
+        /* split copies of this history (weight windows), depth first */
+        while (C.split_n > 0) {
+            particle q = C.split[--C.split_n];
+            while (q.alive) event(&C, &q);
+            o->final_by_type[q.final_type]++;
+        }
     }
     finish_tallies(&C, (double)o->n_hist, o->mesh, o->energy, o->scalars);
     finish_time(&C, (double)o->n_hist, o->time_tally);
@@ -1202,7 +1293,7 @@ int orc_fixed_source(const orc_problem *P, orc_fixed *o)
 /* ------------------------------------------------------------------------ */
 int orc_sensitivities(const orc_problem *P, orc_sens *o)
 {
-    if (P->xs_kind != 0 || P->t_cen > 0.0) return ORC_ERR_INVALID;   /* untimed multigroup only */
+    if (P->xs_kind != 0 || P->t_cen > 0.0 || P->ww_lo) return ORC_ERR_INVALID;   /* untimed analog multigroup only */
     ctx C;
     int st = setup(&C, P);
     if (st) { teardown(&C); return st; }
@@ -1280,7 +1371,7 @@ int orc_sensitivities(const orc_problem *P, orc_sens *o)
 /* ------------------------------------------------------------------------ */
 int orc_power_iteration(const orc_problem *P, orc_eig *o)
 {
-    if (P->xs_kind != 0 || P->t_cen > 0.0) return ORC_ERR_INVALID;   /* untimed multigroup only */
+    if (P->xs_kind != 0 || P->t_cen > 0.0 || P->ww_lo) return ORC_ERR_INVALID;   /* untimed analog multigroup only */
     ctx C;
     int st = setup(&C, P);
     if (st) { teardown(&C); return st; }

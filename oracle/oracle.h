@@ -60,6 +60,13 @@ typedef struct {
     const double *inv_vel;
     int32_t n_tbins;
     double t_cen;
+    /* weight windows (NULL = none; fixed source only): the lower bound per
+     * tally-mesh voxel and group, [voxel][g] (0: no window there); upper bound
+     * ww_upper x lower, roulette survival weight ww_survival x lower, at most
+     * ww_max_split copies per split */
+    const double *ww_lo;
+    double ww_upper, ww_survival;
+    int32_t ww_max_split;
 } orc_problem;
 
 typedef struct {

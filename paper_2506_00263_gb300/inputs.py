@@ -96,6 +96,13 @@ class Problem:
     inv_velocity: Optional[np.ndarray] = None
     n_time_bins: int = 0
     t_census: float = 0.0
+    # weight windows (fixed source; None = analog): lower bound per tally-mesh
+    # voxel and group, (mesh voxels, G) with 0 = no window; upper bound and
+    # roulette survival weight as multiples of it; most copies per split
+    ww_lower: Optional[np.ndarray] = None
+    ww_upper: float = 5.0
+    ww_survival: float = 3.0
+    ww_max_split: int = 16
 
     @property
     def shape(self):
