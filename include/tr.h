@@ -163,7 +163,7 @@ typedef struct {
     uint64_t queue_capacity;            /* stack: particles per event stack; async: global links */
     int32_t blocks_per_sm;              /* resident blocks per SM */
     int32_t remap_every;                /* events a particle advances between remaps (>= 1) */
-    int32_t stash_slots;                /* async: particle slots per block stash */
+    int32_t stash_slots;                /* async: particle slots per block stash (0: 288 monolithic, 512 otherwise) */
     int64_t max_spin;                   /* async: iterations before a spin-wait gives up */
     uint32_t max_events;                /* per-history event cap (default 1e7) */
     int32_t want_event_log;             /* keep per-history (events, cell, type) for tr_event_log */

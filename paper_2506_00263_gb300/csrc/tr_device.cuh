@@ -352,40 +352,31 @@ __device__ __forceinline__ double tr_log(const double* __restrict__ tab, double 
 // curve), else try t+1 takes words 0-1 of that block.  The table
 // ({W_i, C_i}, {f_i, df_i = f_i+1 - f_i}) is built at problem creation.
 // ---------------------------------------------------------------------------
-// The rejection part of the ziggurat (about 1 % of draws), out of line so
-// that the hot loops carry only the accepted first try: from the first try's
-// layer i, uniform U and candidate x, the tries of blocks BLK_ZIG + k.
-static __device__ __noinline__ double exp_sample_slow(const double* zig_tab, const double* log_tab, Stream S,
-                                                      uint32_t n, int i, double U, double x)
+__device__ __forceinline__ double exp_sample(const DevProblem& P, const Stream& S, uint32_t n, uint32_t lo, uint32_t hi)
 {
-    const double2* wc = reinterpret_cast<const double2*>(zig_tab);
+    // (the rejection part stays inline: with ~25 lanes per warp a warp takes
+    // it in about a fifth of its steps, and out of line it measured slower)
+    const double2* wc = reinterpret_cast<const double2*>(P.zig_tab);
     const double2* fd = wc + ZIG_N;
+    int i = (int)(lo & 0xFFu);
+    double U = u01(lo, hi);
     double2 t = __ldg(wc + i);
+    double x = U * t.x;
+    if (lt_nn(x, t.y)) return x;
     for (uint32_t k = 0; k < N_ZIG; ++k) {
         const uint4 w = S.block(n, BLK_ZIG + k);
         const double U2 = u01(w.z, w.w);
-        if (i == 0) return t.y - tr_log(log_tab, U2);
+        if (i == 0) return t.y - tr_log(P.log_tab, U2);
         const double2 f = __ldg(fd + i);
         const double y = __fma_rn(U2, f.y, f.x);
-        if (lt_nn(x, -tr_log(log_tab, y))) return x;
+        if (lt_nn(x, -tr_log(P.log_tab, y))) return x;
         i = (int)(w.x & 0xFFu);
         U = u01(w.x, w.y);
         t = __ldg(wc + i);
         x = U * t.x;
         if (lt_nn(x, t.y)) return x;
     }
-    return -tr_log(log_tab, U);   // after N_ZIG rejected tries (probability below 1e-100)
-}
-
-__device__ __forceinline__ double exp_sample(const DevProblem& P, const Stream& S, uint32_t n, uint32_t lo, uint32_t hi)
-{
-    const double2* wc = reinterpret_cast<const double2*>(P.zig_tab);
-    const int i = (int)(lo & 0xFFu);
-    const double U = u01(lo, hi);
-    const double2 t = __ldg(wc + i);
-    const double x = U * t.x;
-    if (lt_nn(x, t.y)) return x;
-    return exp_sample_slow(P.zig_tab, P.log_tab, S, n, i, U, x);
+    return -tr_log(P.log_tab, U);   // after N_ZIG rejected tries (probability below 1e-100)
 }
 
 // ---------------------------------------------------------------------------
@@ -406,23 +397,6 @@ __device__ __forceinline__ bool azimuth_try(const Stream& S, uint32_t n, uint32_
     return dbits(s) <= dbits(1.0) && gt0(s);   // 0 < s <= 1 (s >= +0)
 }
 
-// Tries 2 .. N_AZIMUTH - 1 of the disk point (both first tries rejected, about
-// 5 % of calls), out of line so that the hot loops carry only the first two;
-// after N_AZIMUTH rejected tries (probability 1e-43) the point (1, 0).
-struct DiskPoint {
-    double a, b, a2, b2, s;
-};
-static __device__ __noinline__ DiskPoint disk_point_retry(Stream S, uint32_t n)
-{
-    DiskPoint d;
-    for (uint32_t t = 2; t < N_AZIMUTH; ++t) {
-        TR_LANES(6);
-        if (azimuth_try(S, n, t, d.a, d.b, d.a2, d.b2, d.s)) return d;
-    }
-    d.a = 1.0; d.b = 0.0; d.a2 = 1.0; d.b2 = 0.0; d.s = 1.0;
-    return d;
-}
-
 // The first accepted rejection try: (a, b) uniform in the unit disk, s =
 // a^2 + b^2.  sm: the lanes of this warp that call it together (a mask every
 // one of them passes, computed by a ballot), regrouped after the rejection
@@ -440,9 +414,14 @@ __device__ __forceinline__ void disk_point(const Stream& S, uint32_t n, double& 
         a = a1; b = b1; a2 = a21; b2 = b21; s = s1;
         ok = true;
     }
+    // (the retries stay inline: with ~16 scattering lanes a warp needs them
+    // in about half of its collision passes)
+    for (uint32_t t = 2; !ok && t < N_AZIMUTH; ++t) {
+        TR_LANES(6);
+        ok = azimuth_try(S, n, t, a, b, a2, b2, s);
+    }
     if (!ok) {
-        const DiskPoint d = disk_point_retry(S, n);
-        a = d.a; b = d.b; a2 = d.a2; b2 = d.b2; s = d.s;
+        a = 1.0; b = 0.0; a2 = 1.0; b2 = 0.0; s = 1.0;
     }
     if (sm) __syncwarp(sm);
     TR_LANES(19);
