@@ -904,6 +904,30 @@ def _pinned_copy(spec, torch):
     return spec.replace(**kw), nbytes
 
 
+ISSUE_OPS = ["dadd", "dmul", "dfma", "ddiv", "dsqrt", "ffma", "imad"]
+
+
+def run_issue_rate(args):
+    """The arithmetic pipes' issue rates (the roofline's ALU denominators):
+    one JSON line per operation, then the FP64 fma issued by 1..32 lanes of a
+    warp (warp instructions per second), with the SM clock sampled during it."""
+    import torch
+    _, _, tb, _ = _setup(torch)
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    reps = max(args.steps, 3)          # best of `reps` timed launches per operation
+    with ClockSampler(0) as sampler:
+        rows = [{"op": name, "per_s": max(tb.issue_rate(op) for _ in range(reps))}
+                for op, name in enumerate(ISSUE_OPS)]
+        lanes = [{"lanes": k, "warp_instr_per_s": max(tb.issue_rate(7, k) for _ in range(reps))}
+                 for k in (1, 2, 4, 8, 16, 32)]
+    clocks = sampler.summary()
+    mhz = clocks.get("sm_mhz") or clocks.get("sm_max_mhz")
+    for r in rows:
+        r["per_clk_per_sm"] = r["per_s"] / (sms * mhz * 1e6) if mhz else None
+        print(json.dumps(dict({"workload": "issue-rate"}, **r)))
+    print(json.dumps({"workload": "issue-rate", "partial_warp_dfma": lanes, "sms": sms, "clocks": clocks}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -924,7 +948,7 @@ def main():
                     help="monolithic / streaming: events between remaps (0: 512 for the lattice, 64 for the CE pin cell)")
     ap.add_argument("--queue", type=int, default=0, help="stack: particles per stack; async: spill links x 32")
     ap.add_argument("--workload", choices=["lattice", "batched", "adjoint", "ce", "ce-sweep", "ce-time-sweep",
-                                           "lattice-sweep", "baseline-table"],
+                                           "lattice-sweep", "baseline-table", "issue-rate"],
                     default="lattice",
                     help="lattice: the k-eigenvalue lattice; batched: 256 box problems in one launch; "
                          "adjoint: forward + derivative kernels on the fixed-source lattice; ce: the continuous-"
@@ -952,6 +976,8 @@ def main():
         return run_lattice_sweep(args)
     if args.workload == "baseline-table":
         return run_baseline_table(args)
+    if args.workload == "issue-rate":
+        return run_issue_rate(args)
     return run_ours(args)
 
 

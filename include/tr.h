@@ -128,7 +128,22 @@ typedef struct {
  * (continuous energy); a history whose time would pass t_census first ends
  * there with the event TR_EV_CUTOFF.  n_time_bins > 0 (at most 4096) adds a
  * flux tally over that many uniform bins of [0, t_census).  Timed problems
- * run fixed source only. */
+ * run fixed source only.
+ * Weight windows (the closeout event of the paper's decomposed scheme,
+ * Sec. 4, "weights and weight windows for the particle's next loop
+ * iteration"; the rules are our reading): ww_lower != NULL gives a lower
+ * bound L per mesh voxel and group ([voxel][g], G = 1 for continuous energy;
+ * 0 = no window).  Particles carry a weight (1 at birth) and every score is
+ * weight x track length.  After each event a particle survives, in the voxel
+ * holding its position: below L, Russian roulette to weight ww_survival x L
+ * (the history otherwise ends as TR_EV_CUTOFF); above ww_upper x L, a split
+ * into k = min(ceil(w / (ww_upper L)), ww_max_split) copies of weight w / k,
+ * each copy with its own random stream.  Needs the mesh; requires
+ * ww_upper > 1, 0 < ww_survival <= ww_upper, 2 <= ww_max_split <= 64.
+ * Offered for fixed-source runs with the monolithic scheme (both
+ * schedulers); copies go to the block's stash (asynchronous scheme: a full
+ * stash gives TR_ERR_CAPACITY; raise stash_slots) or to the output stack
+ * (stack scheme: TR_ERR_CAPACITY beyond queue_capacity). */
 typedef struct {
     int32_t has_mesh;
     int32_t mesh_n[3];
@@ -138,6 +153,9 @@ typedef struct {
     const double *energy_edges;         /* n_energy_bins + 1 */
     int32_t n_time_bins;                /* 0 .. 4096 (needs t_census > 0) */
     double t_census;                    /* s; 0 = untimed */
+    const double *ww_lower;             /* [mesh voxel][g] weight-window lower bounds, or NULL */
+    double ww_upper, ww_survival;       /* upper bound and survival weight, as multiples of the lower bound */
+    int32_t ww_max_split;               /* most copies per split */
 } tr_tally_desc;
 
 /* Device context.  alloc/free (optional) receive the byte size or pointer,
@@ -408,6 +426,17 @@ tr_status tr_selftest_log(const tr_problem *problem, const double *x, size_t n, 
  * (built on the device at problem creation): 1024 doubles to the host array
  * out, {W_i, C_i} for the 256 layers, then {f_i, f_i+1 - f_i}.  Synchronous. */
 tr_status tr_selftest_zig_table(const tr_problem *problem, double *out);
+
+/* Issue-rate probe of the arithmetic pipes (the roofline's denominators; the
+ * paper has no counterpart): eight independent dependency chains per thread,
+ * eight blocks of 256 threads per SM on the current device.  op 0..4: FP64
+ * add, multiply, fma, division and square root (correctly rounded); 5: FP32
+ * fma; 6: INT32 multiply-add (thread-operations per second to *per_second);
+ * 7: FP64 fma executed by only the first `lanes` (1..32) lanes of each warp
+ * (FP64 warp instructions per second: constant in `lanes` when a warp
+ * instruction costs the same pipe time however few lanes are active).
+ * Allocates device scratch; synchronous.  TR_ERR_INVALID for a bad op. */
+tr_status tr_selftest_issue_rate(int32_t op, int32_t lanes, double *per_second);
 
 /* Diagnostics: number of kernels this library has launched in this process
  * (all kernels, all problems).  Read it before and after a call to count the

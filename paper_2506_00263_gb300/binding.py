@@ -56,7 +56,9 @@ class SourceDesc(C.Structure):
 class TallyDesc(C.Structure):
     _fields_ = [("has_mesh", C.c_int32), ("mesh_n", C.c_int32 * 3), ("by_group", C.c_int32),
                 ("n_energy_bins", C.c_int32), ("mesh_lo", C.c_double * 3), ("mesh_hi", C.c_double * 3),
-                ("energy_edges", _dp), ("n_time_bins", C.c_int32), ("t_census", C.c_double)]
+                ("energy_edges", _dp), ("n_time_bins", C.c_int32), ("t_census", C.c_double),
+                ("ww_lower", _dp), ("ww_upper", C.c_double), ("ww_survival", C.c_double),
+                ("ww_max_split", C.c_int32)]
 
 
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
@@ -146,8 +148,17 @@ def lib():
     L.tr_selftest_log.restype = C.c_int
     L.tr_selftest_zig_table.argtypes = [C.c_void_p, _dp]
     L.tr_selftest_zig_table.restype = C.c_int
+    L.tr_selftest_issue_rate.argtypes = [C.c_int32, C.c_int32, _dp]
+    L.tr_selftest_issue_rate.restype = C.c_int
     _lib = L
     return L
+
+
+def issue_rate(op: int, lanes: int = 32) -> float:
+    """tr_selftest_issue_rate: operations (op 7: FP64 warp instructions) per second."""
+    v = C.c_double()
+    _check(lib().tr_selftest_issue_rate(op, lanes, C.byref(v)))
+    return v.value
 
 
 def selftest_philox(ctr, key):
@@ -312,6 +323,11 @@ class Problem:
             n_t = 1
             t.t_census = float(prob.t_census)
             t.n_time_bins = int(prob.n_time_bins)
+        if getattr(prob, "ww_lower", None) is not None:
+            n_t = 1
+            t.ww_lower = f64(prob.ww_lower)
+            t.ww_upper, t.ww_survival = float(prob.ww_upper), float(prob.ww_survival)
+            t.ww_max_split = int(prob.ww_max_split)
 
         if use_torch_allocator:
             self._ctx, self._keep_ctx = _torch_ctx(device)

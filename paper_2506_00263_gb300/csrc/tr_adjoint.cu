@@ -31,6 +31,7 @@ namespace tr {
 // Adjoint tally sink: the upstream-gradient-weighted contribution of the
 // segment, plus what the flight score needs.
 struct AdjSink {
+    static constexpr bool kWW = false;   // derivatives are offered for analog runs
     const double* g_mesh;
     const double* g_scal;
     double f, len;

@@ -39,6 +39,8 @@ constexpr int N_GQ = 32;
 struct Stash {
     double *x, *y, *z, *u, *v, *w, *iu, *iv, *iw, *ia, *E, *t;
     double *hf, *ha, *hp;              // the histories' running scalar scores
+    double* wt;                        // weight-window problems: weights (else NULL)
+    unsigned* sid;                     // weight-window problems: split copies' stream tags (else NULL)
     double *xst, *xist, *xsa, *xnsf;   // lookup-event decomposition only (else NULL)
     int* g;
     unsigned *cell, *id, *n, *nsites, *pend, *prob;
@@ -50,21 +52,25 @@ struct Stash {
 // control words after the queue counts
 constexpr int CNT_FREE = N_QUEUES, CNT_LOCK = N_QUEUES + 1, CNT_RUN = N_QUEUES + 2;
 
-__host__ __device__ __forceinline__ size_t stash_bytes(int S, bool xs = false)
+__host__ __device__ __forceinline__ size_t stash_bytes(int S, bool xs = false, bool ww = false)
 {
     return (size_t)S * ((xs ? 19 : 15) * sizeof(double) + sizeof(int) + 6 * sizeof(unsigned)) +
+           (ww ? (size_t)S * (sizeof(double) + sizeof(unsigned)) : 0) +
            (size_t)S * (N_QUEUES + 1) * sizeof(unsigned short) + 16 * sizeof(int);
 }
 
 // Dynamic shared memory of one block: the stash, then (8-byte aligned) the
 // threads' fixed-point sums of ended histories' scalar scores.
-__host__ __device__ __forceinline__ size_t fx_offset(int S, bool xs) { return (stash_bytes(S, xs) + 15) & ~size_t(15); }
-__host__ __device__ __forceinline__ size_t async_smem_bytes(int S, bool xs)
+__host__ __device__ __forceinline__ size_t fx_offset(int S, bool xs, bool ww = false)
 {
-    return fx_offset(S, xs) + 256 * ACC_FX_WORDS * sizeof(long long);
+    return (stash_bytes(S, xs, ww) + 15) & ~size_t(15);
+}
+__host__ __device__ __forceinline__ size_t async_smem_bytes(int S, bool xs, bool ww = false)
+{
+    return fx_offset(S, xs, ww) + 256 * ACC_FX_WORDS * sizeof(long long);
 }
 
-__device__ __forceinline__ Stash carve(unsigned char* base, int S, bool xs)
+__device__ __forceinline__ Stash carve(unsigned char* base, int S, bool xs, bool ww = false)
 {
     Stash s;
     double* d = reinterpret_cast<double*>(base);
@@ -78,10 +84,20 @@ __device__ __forceinline__ Stash carve(unsigned char* base, int S, bool xs)
     if (xs) {
         s.xst = d; d += S; s.xist = d; d += S; s.xsa = d; d += S; s.xnsf = d; d += S;
     }
+    s.wt = nullptr;
+    s.sid = nullptr;
+    if (ww) {
+        s.wt = d;
+        d += S;
+    }
     unsigned* u = reinterpret_cast<unsigned*>(d);
     s.g = reinterpret_cast<int*>(u); u += S;
     s.cell = u; u += S; s.id = u; u += S; s.n = u; u += S; s.nsites = u; u += S; s.pend = u; u += S;
     s.prob = u; u += S;
+    if (ww) {
+        s.sid = u;
+        u += S;
+    }
     unsigned short* h = reinterpret_cast<unsigned short*>(u);
     for (int q = 0; q < N_QUEUES; ++q) {
         s.q[q] = h;
@@ -95,10 +111,16 @@ __device__ __forceinline__ Stash carve(unsigned char* base, int S, bool xs)
     return s;
 }
 
-// tm: the problem is timed (or the launch is batched): the particle's time travels too
-template <bool XS>
+// tm: the problem is timed (or the launch is batched): the particle's time
+// travels too; WW: the weight and stream tag (weight-window problems)
+template <bool XS, bool WW = false>
 __device__ __forceinline__ void slot_load(const Stash& s, int i, Particle& p, bool tm)
 {
+    p.nsplit = 0u;
+    if (WW) {
+        p.wt = s.wt[i];
+        p.sid = s.sid[i];
+    }
     if (tm) p.t = s.t[i];
     p.hf = s.hf[i]; p.ha = s.ha[i]; p.hp = s.hp[i];
     if (XS) {
@@ -112,9 +134,13 @@ __device__ __forceinline__ void slot_load(const Stash& s, int i, Particle& p, bo
     p.prob = s.prob[i];
 }
 
-template <bool XS>
+template <bool XS, bool WW = false>
 __device__ __forceinline__ void slot_store(const Stash& s, int i, const Particle& p, bool tm)
 {
+    if (WW) {
+        s.wt[i] = p.wt;
+        s.sid[i] = p.sid;
+    }
     if (tm) s.t[i] = p.t;
     s.hf[i] = p.hf; s.ha[i] = p.ha; s.hp[i] = p.hp;
     if (XS) {
@@ -131,9 +157,14 @@ __device__ __forceinline__ void slot_store(const Stash& s, int i, const Particle
 // Particle state of a global link, read through L2 (ld.global.cg): the link
 // was written by another SM, and this SM's L1 may still hold lines from an
 // earlier use of the same link.
-template <bool XS>
+template <bool XS, bool WW = false>
 __device__ __forceinline__ void load_particle_l2(const SoA& s, unsigned long long i, Particle& p)
 {
+    p.nsplit = 0u;
+    if (WW) {
+        p.wt = __ldcg(s.wt + i);
+        p.sid = __ldcg(s.sid + i);
+    }
     if (XS) {
         p.xst = __ldcg(s.xst + i); p.xist = __ldcg(s.xist + i); p.xsa = __ldcg(s.xsa + i); p.xnsf = __ldcg(s.xnsf + i);
     }
@@ -261,6 +292,53 @@ __device__ __forceinline__ unsigned new_link(const AsyncArgs& A, int start, cons
     return NIL;
 }
 
+// Weight-window split copies of this warp's particles (p.nsplit each) into
+// free slots of the block's stash, queued for steps (warp-collective).  The
+// copies are counted live while the stash is still locked, so no warp can
+// take one and end it before it is counted.  A stash without room for them
+// is a capacity error.
+template <bool XS>
+__device__ bool deposit_copies(const Stash& st, const RunParams& R, Particle& p, bool live, AsyncCtl* ctl,
+                               ErrorWord* err, bool tm)
+{
+    const int lane = threadIdx.x & 31;
+    const unsigned k = live ? p.nsplit : 0u;
+    unsigned incl = k;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned y = __shfl_up_sync(FULLM, incl, o);
+        if (lane >= o) incl += y;
+    }
+    const unsigned total = __shfl_sync(FULLM, incl, 31);
+    if (total == 0u) return true;
+    const unsigned base = incl - k;
+    if (!lock_stash(st, R, err)) return false;
+    const int nf = *(volatile int*)(st.cnt + CNT_FREE);
+    const int c = *(volatile int*)(st.cnt + Q_STEP);
+    const bool ok = nf >= (int)total;
+    if (ok) {
+        for (unsigned j = 0; j < k; ++j) {
+            const Particle q = split_copy(R, p, j + 1u);
+            const int sl = st.fr[nf - 1 - (int)(base + j)];
+            slot_store<XS, true>(st, sl, q, tm);
+            st.q[Q_STEP][c + (int)(base + j)] = (unsigned short)sl;
+        }
+    }
+    __syncwarp();
+    if (lane == 0 && ok) {
+        atomicAdd(&ctl->live, (unsigned long long)total);
+        st.cnt[CNT_FREE] = nf - (int)total;
+        st.cnt[Q_STEP] = c + (int)total;
+    }
+    unlock_stash(st);
+    if (!ok) {
+        if (lane == 0) fail(err, ERR_CAPACITY, 11);
+        return false;
+    }
+    p.nsplit = 0u;
+    return true;
+}
+
 // ---------------------------------------------------------------------------
 // The persistent kernel
 // ---------------------------------------------------------------------------
@@ -349,14 +427,17 @@ __device__ __forceinline__ void flush_lane(Acc& acc, const Tallies& T)
 // than TR_DEFER_MIN events between remaps): each pass runs whole events, as
 // the paper's monolithic scheme does; a deferred collision would wait for the
 // next take.
-template <bool CE, int DEC, bool BATCHED = false, bool PRE = false, bool FUSE = false>
+// WW (monolithic only): weight-window problems -- weighted scores, the
+// closeout after every event, split copies deposited into the stash.
+template <bool CE, int DEC, bool BATCHED = false, bool PRE = false, bool FUSE = false, bool WW = false>
 __global__ void __launch_bounds__(256, TR_ASYNC_MIN_BLOCKS) k_async(DevProblem P, RunParams R, AsyncArgs A, Tallies T, ErrorWord* err)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     constexpr bool SPLIT = DEC != DEC_MONO;
     constexpr bool XS = DEC == DEC_LOOKUP;   // cross sections travel with the particle
+    static_assert(!WW || (DEC == DEC_MONO && !BATCHED), "weight windows run with the monolithic scheme");
     const int S = A.stash_slots;
-    const Stash st = carve(smem, S, XS);
+    const Stash st = carve(smem, S, XS, WW);
     const int lane = threadIdx.x & 31;
     constexpr int nq = dec_queues(DEC);
     const bool tm = BATCHED || P.timed != 0;   // particle times travel through the stash
@@ -368,11 +449,16 @@ __global__ void __launch_bounds__(256, TR_ASYNC_MIN_BLOCKS) k_async(DevProblem P
         st.cnt[CNT_FREE] = S;
     }
     for (int i = threadIdx.x; i < S; i += blockDim.x) st.fr[i] = (unsigned short)(S - 1 - i);
+    if (CE && P.hash_smem_off) {
+        // the union-grid hash buckets, read by every lookup's first step
+        int* h = reinterpret_cast<int*>(smem + P.hash_smem_off);
+        for (int i = threadIdx.x; i <= P.n_hash; i += blockDim.x) h[i] = __ldg(P.hash + i);
+    }
     __syncthreads();
 
     Acc acc;
     acc.zero();
-    if (!BATCHED) acc_attach(acc, reinterpret_cast<long long*>(smem + fx_offset(S, XS)));
+    if (!BATCHED) acc_attach(acc, reinterpret_cast<long long*>(smem + fx_offset(S, XS, WW)));
     unsigned long long idle_spins = 0;
     uint64_t idle_t0 = 0;    // when this warp last started waiting for work
     bool idle = false;
@@ -484,13 +570,13 @@ __global__ void __launch_bounds__(256, TR_ASYNC_MIN_BLOCKS) k_async(DevProblem P
                 bool bad = false;
                 if (lane < fill) {
                     Particle p;
-                    load_particle_l2<XS>(A.links, (unsigned long long)link * 32 + lane, p);
+                    load_particle_l2<XS, WW>(A.links, (unsigned long long)link * 32 + lane, p);
                     bad = BATCHED && p.prob >= (unsigned)A.n_probs;
                     const DevProblem& PP = (BATCHED && !bad) ? A.probs[p.prob] : P;
                     bad = bad || p.id >= R.n_hist || cell_i(p.cell) >= PP.nx || cell_j(p.cell) >= PP.ny ||
                           cell_k(p.cell) >= PP.nz || sl < 0 || sl >= S || (!CE && (p.g < 0 || p.g >= PP.G));
                     if (!bad && cell_in(p.cell)) bad = info_pin(cell_info(PP, p.cell)) < 0;
-                    if (!bad) slot_store<XS>(st, sl, p, tm);
+                    if (!bad) slot_store<XS, WW>(st, sl, p, tm);
                 }
                 if (__any_sync(FULLM, bad)) {
                     if (lane == 0) fail(err, ERR_INVALID, 7);
@@ -548,8 +634,8 @@ __global__ void __launch_bounds__(256, TR_ASYNC_MIN_BLOCKS) k_async(DevProblem P
                 continue;
             }
             Particle p;
-            slot_load<XS>(st, slot, p, tm);
-            store_particle(A.links, (unsigned long long)link * 32 + lane, p, CE, XS);
+            slot_load<XS, WW>(st, slot, p, tm);
+            store_particle(A.links, (unsigned long long)link * 32 + lane, p, CE, XS, WW);
             __threadfence();
             __syncwarp();
             if (lane == 0) {
@@ -614,7 +700,7 @@ __global__ void __launch_bounds__(256, TR_ASYNC_MIN_BLOCKS) k_async(DevProblem P
             if (lane == 0 && made) atomicAdd(&ctl->live, (unsigned long long)made);
         } else {
             // mode 0 (warp-uniform): lanes beyond a partial link hold no slot and stay idle
-            if (slot >= 0) slot_load<XS>(st, slot, p, tm);
+            if (slot >= 0) slot_load<XS, WW>(st, slot, p, tm);
             __syncwarp();   // reconverge: the event below must run once for all lanes, not per lane group
             const unsigned em = __ballot_sync(FULLM, slot >= 0);   // the lanes that hold a particle
             if (slot >= 0) {
@@ -665,6 +751,9 @@ __global__ void __launch_bounds__(256, TR_ASYNC_MIN_BLOCKS) k_async(DevProblem P
                     CEKeep ck;
                     bool ck_ok = false;
                     for (int r = 0; r < R.remap_every; ++r) {
+                        // weight windows: a pass that left split copies ends
+                        // the take, so that the whole warp deposits them
+                        if (WW && __any_sync(em, live && p.nsplit != 0u)) break;
                         if (MERGE && r > 0 && !src_more && em == FULLM) {
                             const unsigned dead = __ballot_sync(FULLM, !live);
                             const int nd = __popc(dead);
@@ -701,7 +790,7 @@ __global__ void __launch_bounds__(256, TR_ASYNC_MIN_BLOCKS) k_async(DevProblem P
                                     if (lane == 0 && k > 0) atomicAdd(&ctl->live, 0ull - (unsigned long long)k);
                                     if (adopt) {
                                         slot = ns;
-                                        slot_load<XS>(st, slot, p, tm);
+                                        slot_load<XS, WW>(st, slot, p, tm);
                                         live = true;
                                         pend_coll = p.pend == PEND_COLLIDE;
                                         ck_ok = false;
@@ -743,7 +832,7 @@ __global__ void __launch_bounds__(256, TR_ASYNC_MIN_BLOCKS) k_async(DevProblem P
                         if (live) TR_LANES(13);
                         if (live && !src_more) TR_LANES(31);
                         if constexpr (FUSE) {
-                            if (live) live = mono_event<CE>(PP, RR, p, TT, acc, A.bank, err, lm);
+                            if (live) live = mono_event<CE, WW>(PP, RR, p, TT, acc, A.bank, err, lm);
                             continue;
                         }
                         if constexpr (CE) {
@@ -751,9 +840,10 @@ __global__ void __launch_bounds__(256, TR_ASYNC_MIN_BLOCKS) k_async(DevProblem P
                             if (pm == lm || __popc(pm) >= TR_COLL_MIN_CE) {
                                 const bool kc = live && pend_coll && ck_ok;
                                 const unsigned pk = __ballot_sync(em, kc);
-                                if (kc) live = kept_collide<CE>(PP, RR, p, TT, acc, A.bank, err, pk, ck);
+                                if (kc) live = kept_collide<CE, WW>(PP, RR, p, TT, acc, A.bank, err, pk, ck);
                                 const unsigned pr = pm & ~pk;
-                                if ((pr >> lane) & 1u) live = split_collide<CE>(PP, RR, p, TT, acc, A.bank, err, pr);
+                                if ((pr >> lane) & 1u)
+                                    live = split_collide<CE, false, WW>(PP, RR, p, TT, acc, A.bank, err, pr);
                                 if ((pm >> lane) & 1u) {
                                     pend_coll = false;
                                     p.pend = 0u;
@@ -762,7 +852,7 @@ __global__ void __launch_bounds__(256, TR_ASYNC_MIN_BLOCKS) k_async(DevProblem P
                                 tr::XS X;
                                 X.keep = &ck;
                                 double xr;
-                                FwdSink sink{TT, acc};
+                                FwdSinkT<WW> sink{TT, acc};
                                 step_event<CE>(PP, RR, p, sink, X, xr);
                                 if (p.pend == PEND_COLLIDE) {
                                     pend_coll = true;
@@ -770,7 +860,7 @@ __global__ void __launch_bounds__(256, TR_ASYNC_MIN_BLOCKS) k_async(DevProblem P
                                     ck.st = X.st;
                                     ck.xi = xr;
                                 } else {
-                                    live = finish_event(PP, RR, p, surface_event(PP, p), TT, acc, A.bank);
+                                    live = finish_event<WW>(PP, RR, p, surface_event(PP, p), TT, acc, A.bank);
                                     p.pend = 0u;
                                 }
                             }
@@ -780,7 +870,7 @@ __global__ void __launch_bounds__(256, TR_ASYNC_MIN_BLOCKS) k_async(DevProblem P
                         if (pm == lm || __popc(pm) >= TR_COLL_MIN) {
                             if (live && pend_coll) {
                                 TR_LANES(15);
-                                live = split_collide<CE>(PP, RR, p, TT, acc, A.bank, err, pm);
+                                live = split_collide<CE, false, WW>(PP, RR, p, TT, acc, A.bank, err, pm);
                                 pend_coll = false;
                                 p.pend = 0u;
                             }
@@ -788,12 +878,12 @@ __global__ void __launch_bounds__(256, TR_ASYNC_MIN_BLOCKS) k_async(DevProblem P
                             TR_LANES(14);
                             tr::XS X;
                             double xr;
-                            FwdSink sink{TT, acc};
+                            FwdSinkT<WW> sink{TT, acc};
                             step_event<CE>(PP, RR, p, sink, X, xr);
                             if (p.pend == PEND_COLLIDE) {
                                 pend_coll = true;
                             } else {
-                                live = finish_event(PP, RR, p, surface_event(PP, p), TT, acc, A.bank);
+                                live = finish_event<WW>(PP, RR, p, surface_event(PP, p), TT, acc, A.bank);
                                 p.pend = 0u;
                             }
                         }
@@ -848,9 +938,12 @@ __global__ void __launch_bounds__(256, TR_ASYNC_MIN_BLOCKS) k_async(DevProblem P
             const unsigned died = __popc(__ballot_sync(FULLM, slot >= 0 && !live));
             if (lane == 0 && died) atomicAdd(&ctl->live, 0ull - (unsigned long long)died);
         }
-        if (live) slot_store<XS>(st, slot, p, tm);
+        if (live) slot_store<XS, WW>(st, slot, p, tm);
         // ---------------- deposit (under the stash lock) ----------------
         __syncwarp();
+        if constexpr (WW) {
+            if (!deposit_copies<XS>(st, R, p, live, ctl, err, tm)) break;   // split copies first
+        }
         if (!lock_stash(st, R, err)) break;
         const bool has = slot >= 0;
         if (MERGE && lane == 0) st.cnt[CNT_RUN] -= 1;
@@ -880,27 +973,53 @@ __global__ void __launch_bounds__(256, TR_ASYNC_MIN_BLOCKS) k_async(DevProblem P
 
 namespace tr {
 
-template <bool CE, int DEC, bool BATCHED = false, bool PRE = false, bool FUSE = false>
+template <bool CE, int DEC, bool BATCHED = false, bool PRE = false, bool FUSE = false, bool WW = false>
 static cudaError_t prepare_async(size_t smem)
 {
-    return cudaFuncSetAttribute(k_async<CE, DEC, BATCHED, PRE, FUSE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)smem);
+    return cudaFuncSetAttribute(k_async<CE, DEC, BATCHED, PRE, FUSE, WW>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
 }
 
-template <bool CE, int DEC, bool BATCHED = false, bool PRE = false, bool FUSE = false>
+template <bool CE, int DEC, bool BATCHED = false, bool PRE = false, bool FUSE = false, bool WW = false>
 static int occupancy_async(size_t smem)
 {
     int nb = 0;
-    if (prepare_async<CE, DEC, BATCHED, PRE, FUSE>(smem) != cudaSuccess) return 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_async<CE, DEC, BATCHED, PRE, FUSE>, 256, smem) !=
+    if (prepare_async<CE, DEC, BATCHED, PRE, FUSE, WW>(smem) != cudaSuccess) return 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_async<CE, DEC, BATCHED, PRE, FUSE, WW>, 256, smem) !=
         cudaSuccess)
         return 0;
     return nb;
 }
 
+// Continuous energy: the union-grid hash buckets (n_hash + 1 ints) are staged
+// in each block's shared memory, after the stash and the score sums, when
+// they fit there at TR_ASYNC_MIN_BLOCKS blocks per SM (228 KB per SM, 1 KB of
+// it reserved per block) and take at most TR_HASH_SMEM_MAX bytes.  Returns
+// the byte offset (0: not staged); *total becomes the block's dynamic shared
+// memory.
+#ifndef TR_HASH_SMEM_MAX
+#define TR_HASH_SMEM_MAX (64 * 1024)
+#endif
+static size_t hash_stage(const DevProblem& P, size_t smem, size_t* total)
+{
+    *total = smem;
+    if (P.kind != 1 || !P.hash || P.n_hash < 1) return 0;
+    const size_t off = (smem + 15) & ~size_t(15);
+    const size_t bytes = (size_t)(P.n_hash + 1) * sizeof(int);
+    if (bytes > TR_HASH_SMEM_MAX || (off + bytes + 1024) * TR_ASYNC_MIN_BLOCKS > 228 * 1024) return 0;
+    *total = off + bytes;
+    return off;
+}
+
 int async_max_blocks_per_sm(const DevProblem& P, int dec, int stash_slots, bool pre)
 {
-    const size_t smem = async_smem_bytes(stash_slots, dec == DEC_LOOKUP);
+    size_t smem;
+    if (P.ww_lo) {
+        hash_stage(P, async_smem_bytes(stash_slots, false, true), &smem);
+        return P.kind == 1 ? occupancy_async<true, DEC_MONO, false, false, false, true>(smem)
+                           : occupancy_async<false, DEC_MONO, false, false, false, true>(smem);
+    }
+    hash_stage(P, async_smem_bytes(stash_slots, dec == DEC_LOOKUP), &smem);
     if (pre && dec == DEC_MONO)
         return P.kind == 1 ? occupancy_async<true, DEC_MONO, false, true>(smem)
                            : occupancy_async<false, DEC_MONO, false, true>(smem);
@@ -914,13 +1033,13 @@ int async_max_blocks_per_sm(const DevProblem& P, int dec, int stash_slots, bool 
     return dec == DEC_SPLIT ? occupancy_async<false, DEC_SPLIT>(smem) : occupancy_async<false, DEC_MONO>(smem);
 }
 
-template <bool CE, int DEC, bool BATCHED = false, bool PRE = false, bool FUSE = false>
+template <bool CE, int DEC, bool BATCHED = false, bool PRE = false, bool FUSE = false, bool WW = false>
 static cudaError_t launch_async_t(const DevProblem& P, const RunParams& R, const AsyncArgs& A, const Tallies& T,
                                   ErrorWord* err, int blocks, cudaStream_t st, size_t smem)
 {
-    const cudaError_t e = prepare_async<CE, DEC, BATCHED, PRE, FUSE>(smem);
+    const cudaError_t e = prepare_async<CE, DEC, BATCHED, PRE, FUSE, WW>(smem);
     if (e != cudaSuccess) return e;
-    k_async<CE, DEC, BATCHED, PRE, FUSE><<<blocks, 256, smem, st>>>(P, R, A, T, err);
+    k_async<CE, DEC, BATCHED, PRE, FUSE, WW><<<blocks, 256, smem, st>>>(P, R, A, T, err);
     return cudaGetLastError();
 }
 
@@ -931,6 +1050,9 @@ static cudaError_t launch_async_mono(const DevProblem& P, const RunParams& R, co
                                      ErrorWord* err, int blocks, cudaStream_t st, size_t smem)
 {
     const bool fuse = R.remap_every < TR_DEFER_MIN;
+    if (P.ww_lo)   // weight windows: sources sampled in the loop
+        return fuse ? launch_async_t<CE, DEC_MONO, false, false, true, true>(P, R, A, T, err, blocks, st, smem)
+                    : launch_async_t<CE, DEC_MONO, false, false, false, true>(P, R, A, T, err, blocks, st, smem);
     if (A.use_pre)
         return fuse ? launch_async_t<CE, DEC_MONO, false, true, true>(P, R, A, T, err, blocks, st, smem)
                     : launch_async_t<CE, DEC_MONO, false, true>(P, R, A, T, err, blocks, st, smem);
@@ -938,10 +1060,13 @@ static cudaError_t launch_async_mono(const DevProblem& P, const RunParams& R, co
                 : launch_async_t<CE, DEC_MONO>(P, R, A, T, err, blocks, st, smem);
 }
 
-cudaError_t launch_async(const DevProblem& P, const RunParams& R, const AsyncArgs& A, const Tallies& T, ErrorWord* err,
-                         int blocks, cudaStream_t st, int* smem_bytes_out)
+cudaError_t launch_async(const DevProblem& Pin, const RunParams& R, const AsyncArgs& A, const Tallies& T,
+                         ErrorWord* err, int blocks, cudaStream_t st, int* smem_bytes_out)
 {
-    const size_t smem = async_smem_bytes(A.stash_slots, A.dec == DEC_LOOKUP);
+    DevProblem P = Pin;
+    size_t smem;
+    P.hash_smem_off = (int)hash_stage(P, async_smem_bytes(A.stash_slots, A.dec == DEC_LOOKUP, P.ww_lo != nullptr),
+                                      &smem);
     if (smem_bytes_out) *smem_bytes_out = (int)smem;
     count_launches(1);
     if (A.dec == DEC_MONO)

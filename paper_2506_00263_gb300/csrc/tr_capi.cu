@@ -13,6 +13,10 @@
 #include "../../include/tr.h"
 #include "tr_kernels.h"
 
+#ifndef TR_HASH_MANT
+#define TR_HASH_MANT 8   // union-grid hash: leading mantissa bits of E per bucket
+#endif
+
 using namespace tr;
 
 static thread_local std::string g_err;
@@ -427,8 +431,9 @@ extern "C" tr_status tr_problem_create(const tr_geometry_desc* G, const tr_xs_de
                 uptr[(size_t)u * Nn + n] = (int)r;
             }
         }
-        // hash on the bit pattern of E: exponent plus 8 leading mantissa bits
-        const int shift = 44;
+        // hash on the bit pattern of E: exponent plus TR_HASH_MANT leading
+        // mantissa bits (2^TR_HASH_MANT buckets per octave)
+        const int shift = 52 - TR_HASH_MANT;
         const long long base = dbl_bits(ue[0]) >> shift, top = dbl_bits(ue[U - 1]) >> shift;
         const int nh = (int)(top - base + 1);
         std::vector<int> hash(nh + 1);
@@ -560,6 +565,23 @@ extern "C" tr_status tr_problem_create(const tr_geometry_desc* G, const tr_xs_de
         P.n_tbins = Tl->n_time_bins;
         P.tb_w = P.n_tbins > 0 ? P.t_cen / (double)P.n_tbins : 0.0;
     }
+    // weight windows on the tally mesh (the closeout event)
+    P.ww_lo = nullptr;
+    if (n_tallies == 1 && Tl->ww_lower) {
+        if (!P.has_mesh) return fail_out(TR_ERR_INVALID, "weight windows need the tally mesh");
+        if (!(Tl->ww_upper > 1.0) || !(Tl->ww_survival > 0.0) || !(Tl->ww_survival <= Tl->ww_upper) ||
+            !std::isfinite(Tl->ww_upper) || Tl->ww_max_split < 2 || Tl->ww_max_split > WW_MAX_SPLIT)
+            return fail_out(TR_ERR_INVALID,
+                            "weight windows need ww_upper > 1, 0 < ww_survival <= ww_upper, 2 <= ww_max_split <= 64");
+        const size_t nw = (size_t)P.mesh_vox * P.G;
+        for (size_t i = 0; i < nw; ++i)
+            if (!(Tl->ww_lower[i] >= 0.0) || !std::isfinite(Tl->ww_lower[i]))
+                return fail_out(TR_ERR_INVALID, "weight-window lower bounds must be finite and non-negative");
+        P.ww_lo = upload(pr, Tl->ww_lower, nw, &ok);
+        P.ww_up = Tl->ww_upper;
+        P.ww_surv = Tl->ww_survival;
+        P.ww_max_split = Tl->ww_max_split;
+    }
     const size_t ms = std::max(P.mesh_size, 1), es = std::max(P.energy_size, 1);
     pr->raw_mesh = (FixBin*)own(pr, ms * sizeof(FixBin));
     pr->raw_energy = (FixBin*)own(pr, es * sizeof(FixBin));
@@ -660,7 +682,7 @@ constexpr unsigned long long HIST_MAX = 1ull << 26;
 static bool carve_soa(tr_problem* pr, const char* name, unsigned long long cap, SoA& s)
 {
     const size_t n = (size_t)cap;
-    const size_t bytes = n * (19 * 8 + 7 * 4) + 26 * 256;
+    const size_t bytes = n * (20 * 8 + 8 * 4) + 28 * 256;
     unsigned char* b = (unsigned char*)workspace(pr, name, bytes);
     if (!b) return false;
     auto take = [&](size_t sz) {
@@ -675,7 +697,9 @@ static bool carve_soa(tr_problem* pr, const char* name, unsigned long long cap, 
     s.t = (double*)take(8);
     s.hf = (double*)take(8); s.ha = (double*)take(8); s.hp = (double*)take(8);
     s.xst = (double*)take(8); s.xist = (double*)take(8); s.xsa = (double*)take(8); s.xnsf = (double*)take(8);
+    s.wt = (double*)take(8);
     s.g = (int*)take(4);
+    s.sid = (unsigned*)take(4);
     s.cell = (unsigned*)take(4); s.id = (unsigned*)take(4); s.n = (unsigned*)take(4);
     s.nsites = (unsigned*)take(4); s.pend = (unsigned*)take(4); s.prob = (unsigned*)take(4);
     return true;
@@ -827,7 +851,10 @@ static tr_status transport(tr_problem* pr, const tr_run_opts* o, RunParams R, co
         T.hist_p = h + 2 * pr->hist_cap;
     }
     if (o->scheme == TR_SCHEME_STACK) {
-        unsigned long long cap = o->queue_capacity ? o->queue_capacity : std::min<unsigned long long>(R.n_hist, 1ull << 22);
+        // default: the histories (split copies of weight-window problems: room for 8 per history)
+        unsigned long long cap = o->queue_capacity ? o->queue_capacity
+                                                   : std::min<unsigned long long>(P.ww_lo ? 8 * R.n_hist + 4096 : R.n_hist,
+                                                                                  1ull << 22);
         cap = std::max<unsigned long long>((cap + 31) & ~31ull, 64);
         const int nst = dec_queues(dec);
         SoA bufs[2][N_QUEUES] = {};
@@ -936,7 +963,7 @@ static tr_status transport(tr_problem* pr, const tr_run_opts* o, RunParams R, co
     // default stash: 288 slots for the monolithic scheme (its particles stay in
     // registers; a smaller stash leaves more of the shared L1 array as cache:
     // lattice 2.78e9 events/s at 288 slots, 2.74e9 at 512), 512 otherwise
-    int S = o->stash_slots > 0 ? o->stash_slots : (o->decomposition == TR_DECOMP_MONO ? 288 : 512);
+    int S = o->stash_slots > 0 ? o->stash_slots : (o->decomposition == TR_DECOMP_MONO && !P.ww_lo ? 288 : 512);
     S = (S + 31) & ~31;
     if (S < 32 * 9 || S > 16384) return set_err(TR_ERR_INVALID, "stash_slots must be in 288..16384");
     const unsigned long long n_links = o->queue_capacity ? (o->queue_capacity + 31) / 32 : 8192;
@@ -954,7 +981,7 @@ static tr_status transport(tr_problem* pr, const tr_run_opts* o, RunParams R, co
     A.dec = dec;
     A.stash_slots = S;
     // monolithic scheme: sample the sources ahead of the launch (make_work loads them)
-    if (dec == DEC_MONO && R.n_hist <= PRESAMPLE_MAX_HIST) {
+    if (dec == DEC_MONO && R.n_hist <= PRESAMPLE_MAX_HIST && !P.ww_lo) {
         if (!carve_soa(pr, "presample", R.n_hist, A.pre)) return set_err(TR_ERR_NOMEM, "source buffer allocation failed");
         A.use_pre = 1;
     }
@@ -1017,6 +1044,8 @@ extern "C" tr_status tr_run_fixed_source(tr_problem* pr, const tr_run_opts* o, t
     if (s != TR_OK) return s;
     const DevProblem& P = pr->dp;
     const cudaStream_t st = pr->stream;
+    if (P.ww_lo && o->decomposition != TR_DECOMP_MONO)
+        return set_err(TR_ERR_INVALID, "weight windows run with the monolithic scheme");
     RunParams R = base_params(o, o->n_histories);
     if (R.want_log) {
         s = ensure_log(pr, std::max<unsigned long long>(o->n_histories, 1));
@@ -1115,6 +1144,7 @@ extern "C" tr_status tr_run_power_iteration(tr_problem* pr, const tr_eig_opts* e
     if (!pr || !eo || !res) return set_err(TR_ERR_INVALID, "NULL argument");
     DeviceGuard dg(pr->ctx.device);
     if (pr->dp.kind != TR_XS_MG) return set_err(TR_ERR_INVALID, "power iteration needs multigroup data");
+    if (pr->dp.ww_lo) return set_err(TR_ERR_INVALID, "weight windows are offered for fixed-source runs");
     if (pr->dp.timed) return set_err(TR_ERR_INVALID, "timed problems run fixed source only");
     tr_status s = validate_opts(&eo->run);
     if (s != TR_OK) return s;
@@ -1418,6 +1448,7 @@ extern "C" tr_status tr_sensitivities(tr_problem* pr, const tr_run_opts* o, cons
     if (!pr || !o || !d_sigt || !d_sigs || !d_nusigf) return set_err(TR_ERR_INVALID, "NULL argument");
     DeviceGuard dg(pr->ctx.device);
     if (pr->dp.kind != TR_XS_MG) return set_err(TR_ERR_INVALID, "sensitivities need multigroup data");
+    if (pr->dp.ww_lo) return set_err(TR_ERR_INVALID, "sensitivities are offered for analog runs");
     if (pr->dp.timed) return set_err(TR_ERR_INVALID, "sensitivities are offered for untimed problems");
     tr_status s = validate_opts(o);
     if (s != TR_OK) return s;
@@ -1551,6 +1582,7 @@ extern "C" tr_status tr_run_batched(tr_problem* const* probs, int32_t n, const u
     for (int32_t i = 0; i < n; ++i) {
         if (!probs[i]) return set_err(TR_ERR_INVALID, "NULL problem in the batch");
         if (probs[i]->dp.kind != TR_XS_MG) return set_err(TR_ERR_INVALID, "batched runs need multigroup problems");
+        if (probs[i]->dp.ww_lo) return set_err(TR_ERR_INVALID, "batched runs are analog (no weight windows)");
         if (probs[i]->ctx.device != lead->ctx.device) return set_err(TR_ERR_INVALID, "all problems on one device");
         if (n_histories[i] >= (1ull << 32)) return set_err(TR_ERR_INVALID, "n_histories must be < 2^32 per problem");
         for (int32_t j = 0; j < i; ++j)

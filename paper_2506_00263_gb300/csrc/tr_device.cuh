@@ -65,6 +65,9 @@ constexpr uint32_t N_POS = 1024u;
 constexpr uint32_t BLK_ZIG = 3000u;    // 3000 + t: exponential ziggurat, try t's wedge or tail
                                        // uniform (words 2-3) and try t+1's layer and uniform (words 0-1)
 constexpr uint32_t N_ZIG = 64u;
+constexpr uint32_t BLK_CLOSE = 4000u;  // (closeout roulette, -)
+constexpr uint32_t BLK_SPLIT = 4001u;  // 4001 + c: stream tag of split copy c (word 0), c < 64
+constexpr int WW_MAX_SPLIT = 64;
 constexpr int ZIG_N = 256;             // ziggurat layers
 constexpr uint32_t TAG_POP = 0x80000000u;
 
@@ -104,6 +107,8 @@ struct DevProblem {
     int hash_shift;
     long long hash_base;
     const int *hash;                   // n_hash + 1: first union index whose bucket >= b
+    int hash_smem_off;                 // > 0: this launch's blocks hold hash[] at this byte offset of
+                                       // their dynamic shared memory (0: read it from global memory)
     // source
     int src_kind, src_iso, src_group, n_cdf;
     double src_pt[3], src_dir[3], src_lo[3], src_hi[3], src_energy;
@@ -125,6 +130,10 @@ struct DevProblem {
     const double* log_tab;
     // exponential ziggurat: {W_i, C_i} pairs, then {f_i, df_i} pairs (see exp_sample)
     const double* zig_tab;
+    // weight windows (closeout): lower bound per mesh voxel and group, or null
+    const double* ww_lo;
+    double ww_up, ww_surv;
+    int ww_max_split;
 };
 
 // Per-run parameters.
@@ -163,6 +172,8 @@ __device__ __forceinline__ uint64_t now_ns()
 struct SoA {
     double *x, *y, *z, *u, *v, *w, *iu, *iv, *iw, *ia, *E, *t;
     double *hf, *ha, *hp;
+    double *wt;                        // weight (weight-window problems)
+    unsigned *sid;                     // stream tag of a split copy (weight-window problems)
     double *xst, *xist, *xsa, *xnsf;
     int *g;
     unsigned *cell, *id, *n, *nsites, *pend, *prob;
@@ -178,6 +189,11 @@ struct Particle {
     // schedule; converted to fixed point once, when the history ends
     double hf, ha, hp;
     double xst, xist, xsa, xnsf;       // lookup-event decomposition: cross sections of (material, E or g)
+    // weight-window problems: the weight (1 at birth); the stream tag of a
+    // split copy (0 for a source history; xored into the stream's high word);
+    // copies the closeout asked for after the last event
+    double wt;
+    unsigned sid, nsplit;
     int g;
     unsigned cell;                     // i | j << 10 | k << 20 | inside << 30
     unsigned id, n, nsites, pend;
@@ -577,13 +593,23 @@ __device__ __forceinline__ void xs_mg(const DevProblem& P, int m, int g, XS& X)
 // buckets the double bit pattern of E (exponent + leading mantissa bits, a
 // piecewise-linear log2), giving a short range for a binary search that
 // compares bit patterns (all energies are positive).
+extern __shared__ __align__(16) unsigned char tr_dyn_smem[];
+
 __device__ __forceinline__ int union_index(const DevProblem& P, double E)
 {
     const long long eb = dbits(E);
     long long bkt = (eb >> P.hash_shift) - P.hash_base;
     if (bkt < 0) bkt = 0;
     if (bkt > P.n_hash - 1) bkt = P.n_hash - 1;
-    int lo = __ldg(P.hash + bkt) - 1, hi = __ldg(P.hash + bkt + 1);
+    int lo, hi;
+    if (P.hash_smem_off) {
+        const int* h = reinterpret_cast<const int*>(tr_dyn_smem + P.hash_smem_off);
+        lo = h[bkt] - 1;
+        hi = h[bkt + 1];
+    } else {
+        lo = __ldg(P.hash + bkt) - 1;
+        hi = __ldg(P.hash + bkt + 1);
+    }
     if (lo < 0) lo = 0;
     if (hi > P.n_union - 1) hi = P.n_union - 1;
     // invariant: ue[lo] <= E < ue[hi] (or boundaries)

@@ -77,6 +77,16 @@ __device__ __forceinline__ Stream make_stream(const RunParams& R, unsigned id)
     return S;
 }
 
+// The particle's random stream: its history's, with a split copy's stream
+// tag xored into the high word (weight-window problems).
+template <bool WW>
+__device__ __forceinline__ Stream particle_stream(const RunParams& R, const Particle& p)
+{
+    Stream S = make_stream(R, p.id);
+    if (WW) S.id_hi ^= p.sid;
+    return S;
+}
+
 // ---------------------------------------------------------------------------
 // Track-length mesh tally.  A segment never leaves its geometry cell; when
 // that cell lies inside one mesh cell on every axis (precomputed per axis)
@@ -91,6 +101,15 @@ struct MeshAtomic {
     __device__ __forceinline__ void operator()(int i, double l) const
     {
         if (!fix_add_nn(T.mesh + i, l)) tally_range_error(T);   // l > 0
+    }
+};
+// The same for weighted particles: each piece times the weight.
+struct MeshAtomicW {
+    const Tallies& T;
+    double wt;
+    __device__ __forceinline__ void operator()(int i, double l) const
+    {
+        if (!fix_add_nn(T.mesh + i, wt * l)) tally_range_error(T);
     }
 };
 struct MeshWeighted {
@@ -185,7 +204,7 @@ __device__ __forceinline__ void mesh_tally(const DevProblem& P, Op& op, const Pa
 }
 
 // Energy-bin flux tally per material: bin = largest b with e[b] <= E < e[b+1].
-__device__ __forceinline__ void energy_tally(const DevProblem& P, const Tallies& T, int m, double E, double L)
+__device__ __forceinline__ void energy_tally(const DevProblem& P, const Tallies& T, int m, double E, double L)   // L: weighted
 {
     const int nb = P.n_ebins;
     // E > 0 and the edges are non-negative (checked at problem creation):
@@ -220,6 +239,8 @@ __device__ __forceinline__ bool source_particle(const DevProblem& P, const RunPa
     p.E = 0.0;
     p.t = 0.0;
     p.hf = p.ha = p.hp = 0.0;
+    p.wt = 1.0;
+    p.sid = p.nsplit = 0u;
     if (site != nullptr || P.src_kind != 0 || P.src_iso) {
         iso_dir(S, 0u, p);
     } else {
@@ -270,7 +291,7 @@ __device__ __forceinline__ bool source_particle(const DevProblem& P, const RunPa
 // and a call: the track length spent in each uniform bin of [t0, t1]
 // (t0 < t1), and a particle's 1/v and distance to census.
 static __device__ __noinline__ void time_bins(FixBin* tally, ErrorWord* err, int n_tbins, double tb_w, double t0,
-                                              double t1, double inv_v)
+                                              double t1, double inv_v, double wt)
 {
     int b = (int)floor(t0 / tb_w);
     if (b < 0) b = 0;
@@ -279,7 +300,7 @@ static __device__ __noinline__ void time_bins(FixBin* tally, ErrorWord* err, int
         if (lo >= t1) break;
         lo = fmax(lo, t0);
         hi = fmin(hi, t1);
-        if (hi > lo && !fix_add_nn(tally + b, (hi - lo) / inv_v) && err) atomicCAS(&err->code, 0, ERR_RANGE);
+        if (hi > lo && !fix_add_nn(tally + b, wt * ((hi - lo) / inv_v)) && err) atomicCAS(&err->code, 0, ERR_RANGE);
     }
 }
 
@@ -298,32 +319,44 @@ static __device__ __noinline__ CensusStep census_step(double v_c, const double* 
     return r;
 }
 
-// Forward tally sink: track-length scores into the tallies and the per-lane
-// scalar accumulators.
-struct FwdSink {
+// Forward tally sink: track-length scores into the tallies and the
+// particle's running scalar scores.  WW: weighted particles (weight-window
+// problems), every score times the particle's weight.
+template <bool WW>
+struct FwdSinkT {
+    static constexpr bool kWW = WW;
     const Tallies& T;
     Acc& acc;
+    double wt = 1.0;                   // WW: the particle's weight (set by segment for time_segment)
     template <bool CE>
     __device__ __forceinline__ void segment(const DevProblem& P, Particle& p, double x0, double y0, double z0,
                                             double dist, int m, const XS& X)
     {
-        p.hf += dist;
-        p.ha = __fma_rn(dist, X.sa, p.ha);   // tallies: compared within tolerance, fused freely
-        if (!CE) p.hp = __fma_rn(dist, X.nsf, p.hp);   // continuous energy: nu Sigma_f = 0
+        const double dl = WW ? p.wt * dist : dist;
+        if (WW) wt = p.wt;
+        p.hf += dl;
+        p.ha = __fma_rn(dl, X.sa, p.ha);   // tallies: compared within tolerance, fused freely
+        if (!CE) p.hp = __fma_rn(dl, X.nsf, p.hp);   // continuous energy: nu Sigma_f = 0
         if (P.has_mesh && gt0(dist)) {
             const int goff = (!CE && P.by_group) ? p.g * P.mesh_vox : 0;
-            MeshAtomic op{T};
-            mesh_tally(P, op, p, x0, y0, z0, dist, goff);
+            if (WW) {
+                MeshAtomicW op{T, p.wt};
+                mesh_tally(P, op, p, x0, y0, z0, dist, goff);
+            } else {
+                MeshAtomic op{T};
+                mesh_tally(P, op, p, x0, y0, z0, dist, goff);
+            }
         }
-        if (CE && P.n_ebins > 0 && gt0(dist)) energy_tally(P, T, m, p.E, dist);
+        if (CE && P.n_ebins > 0 && gt0(dist)) energy_tally(P, T, m, p.E, dl);
     }
-    // time bins: the track length spent in each bin of [t0, t1]
+    // time bins: the (weighted) track length spent in each bin of [t0, t1]
     __device__ __forceinline__ void time_segment(const DevProblem& P, double t0, double t1, double inv_v)
     {
         if (P.n_tbins <= 0 || !(t1 > t0)) return;
-        time_bins(T.time, T.err, P.n_tbins, P.tb_w, t0, t1, inv_v);
+        time_bins(T.time, T.err, P.n_tbins, P.tb_w, t0, t1, inv_v, wt);
     }
 };
+using FwdSink = FwdSinkT<false>;
 
 // CACHED: the cross sections come from the particle (left there by the
 // lookup event) instead of a lookup here; the values are the same.
@@ -345,7 +378,7 @@ __device__ __forceinline__ void step_event(const DevProblem& P, const RunParams&
     } else {
         xs_lookup<CE>(P, p, m, X);
     }
-    const Stream S = make_stream(R, p.id);
+    const Stream S = particle_stream<Sink::kWW>(R, p);
     const uint4 b0 = S.block(p.n, BLK_MAIN);
     xi_react = u01(b0.z, b0.w);
     const double dcol = exp_sample(P, S, p.n, b0.x, b0.y) * X.inv_st;
@@ -469,12 +502,12 @@ __device__ __forceinline__ void bank_sites(const DevProblem& P, const RunParams&
 // and the scattering lanes after the azimuth loop, so that the FP64 work of
 // the direction sampling is issued once for all of them: the FP64 pipe
 // charges a warp instruction the same however few lanes are active.
-template <bool CE>
+template <bool CE, bool WW = false>
 __device__ __forceinline__ int collide_event(const DevProblem& P, const RunParams& R, Particle& p, const XS& X,
                                              double xi_react, const Bank& B, ErrorWord* err, unsigned cm = 0u)
 {
     TR_LANES(16);
-    const Stream S = make_stream(R, p.id);
+    const Stream S = particle_stream<WW>(R, p);
     const int m = material(P, p.cell);
     if (!CE) {
         if (R.eig && gt0(X.nsf)) bank_sites(P, R, S, p, m, X, B, err);
@@ -634,8 +667,72 @@ __device__ __forceinline__ int surface_event(const DevProblem& P, Particle& p)
     return refl ? EV_SURF_REFLECT : EV_SURF_INTERNAL;
 }
 
-// Close an event: count it, advance n, apply the event cap.  Returns whether
-// the history continues; on death records the final state.
+// Closeout (the closeout event of the paper's decomposed scheme, Sec. 4:
+// weights and weight windows for the particle's next loop iteration; the
+// rules are our reading, the same as the oracle's).  The window of the
+// tally-mesh voxel holding the particle (i_a = floor((x_a - lo_a) (1 / w_a)),
+// outside the mesh: none) and its group has lower bound L (0: none), upper
+// bound ww_up L and survival weight ww_surv L.  Below L: Russian roulette,
+// survival when xi (the first uniform of block BLK_CLOSE at the particle's
+// event count) times the survival weight is below the weight, at the
+// survival weight; otherwise the history ends as CUTOFF.  Above the upper
+// bound: k = min(ceil(w / U), ww_max_split) copies of weight w / k; the
+// particle continues as copy 0 and leaves k - 1 in p.nsplit for the
+// scheduler to create (tag of copy c: word 0 of block BLK_SPLIT + c, bit 31
+// set).  Returns whether the particle lives on.
+__device__ __forceinline__ bool closeout(const DevProblem& P, const RunParams& R, Particle& p, int& type)
+{
+    const double xs[3] = {p.x, p.y, p.z};
+    int idx[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const double t = floor((xs[a] - P.mesh_lo[a]) * P.mesh_iw[a]);
+        if (!(t >= 0.0) || !(t < (double)P.mesh_n[a])) return true;
+        idx[a] = (int)t;
+    }
+    const int v = (idx[2] * P.mesh_n[1] + idx[1]) * P.mesh_n[0] + idx[0];
+    // continuous energy: one window per voxel (G = 1); p.g carries no group
+    // there (stacks and spill links do not store it)
+    const double L = __ldg(P.ww_lo + (long long)v * P.G + (P.kind == 1 ? 0 : p.g));
+    if (!(L > 0.0)) return true;
+    const Stream S = particle_stream<true>(R, p);
+    if (p.wt < L) {
+        const double Sw = P.ww_surv * L;
+        if (S.first(p.n, BLK_CLOSE) * Sw < p.wt) {
+            p.wt = Sw;
+            return true;
+        }
+        type = EV_CUTOFF;
+        return false;
+    }
+    const double U = P.ww_up * L;
+    if (!(p.wt > U)) return true;
+    int k = (int)ceil(p.wt / U);
+    if (k > P.ww_max_split) k = P.ww_max_split;
+    if (k < 2) return true;
+    p.wt = p.wt / (double)k;
+    p.nsplit = (unsigned)(k - 1);
+    return true;
+}
+
+// Split copy c (1 .. p.nsplit) of particle p: its state with its own stream
+// tag, no pending outcome, its scores starting at 0.
+__device__ __forceinline__ Particle split_copy(const RunParams& R, const Particle& p, unsigned c)
+{
+    Particle q = p;
+    const Stream S = particle_stream<true>(R, p);
+    q.sid = p.sid ^ (S.block(p.n, BLK_SPLIT + c).x | 0x80000000u);
+    q.hf = q.ha = q.hp = 0.0;
+    q.nsplit = 0u;
+    q.pend = 0u;
+    return q;
+}
+
+// Close an event: count it, advance n, apply the event cap (and, WW, the
+// weight-window closeout).  Returns whether the history continues; on death
+// records the final state.  A split copy (p.sid != 0) ends without a log
+// entry, its scores going to the per-thread fixed-point sums.
+template <bool WW = false>
 __device__ __forceinline__ bool finish_event(const DevProblem& P, const RunParams& R, Particle& p, int type,
                                              const Tallies& T, Acc& acc, const Bank& B)
 {
@@ -649,8 +746,10 @@ __device__ __forceinline__ bool finish_event(const DevProblem& P, const RunParam
         alive = false;
         type = EV_MAXEV;
     }
+    if (WW && alive) alive = closeout(P, R, p, type);
     if (!alive) {
-        if (T.hist_f) {
+        const bool primary = !WW || p.sid == 0u;
+        if (T.hist_f && primary) {
             T.hist_f[p.id] = p.hf;
             T.hist_a[p.id] = p.ha;
             T.hist_p[p.id] = p.hp;
@@ -658,7 +757,7 @@ __device__ __forceinline__ bool finish_event(const DevProblem& P, const RunParam
             acc_history_sums(acc.fx, T.scal, T.err, p.hf, p.ha, p.hp);
         }
         acc.fin[type] += 1u;
-        if (R.want_log) {
+        if (R.want_log && primary) {
             T.log_n[p.id] = p.n;
             T.log_cell[p.id] = cell_id(P, p.cell);
             T.log_type[p.id] = (uint8_t)type;
@@ -670,7 +769,7 @@ __device__ __forceinline__ bool finish_event(const DevProblem& P, const RunParam
 
 // One monolithic event (step followed by collision or surface crossing).
 // em: the lanes of this warp that run this event together (from a ballot), or 0.
-template <bool CE>
+template <bool CE, bool WW = false>
 __device__ __forceinline__ bool mono_event(const DevProblem& P, const RunParams& R, Particle& p, const Tallies& T,
                                            Acc& acc, const Bank& B, ErrorWord* err, unsigned em = 0u)
 {
@@ -679,14 +778,14 @@ __device__ __forceinline__ bool mono_event(const DevProblem& P, const RunParams&
     CEKeep keep;
     if (CE) X.keep = &keep;   // the collision below reuses the lookup's terms
     double xi_react;
-    FwdSink sink{T, acc};
+    FwdSinkT<WW> sink{T, acc};
     step_event<CE>(P, R, p, sink, X, xi_react);
     const bool coll = p.pend == PEND_COLLIDE;
     const unsigned cm = em ? __ballot_sync(em, coll) : 0u;
     int type;
-    if (coll) type = collide_event<CE>(P, R, p, X, xi_react, B, err, cm);
+    if (coll) type = collide_event<CE, WW>(P, R, p, X, xi_react, B, err, cm);
     else type = surface_event(P, p);
-    return finish_event(P, R, p, type, T, acc, B);
+    return finish_event<WW>(P, R, p, type, T, acc, B);
 }
 
 // Lookup event (decomposition with the lookup as an event of its own): the
@@ -706,7 +805,7 @@ __device__ __forceinline__ void lookup_event(const DevProblem& P, Particle& p)
 
 // Decomposed collision event: repeats the lookup (or, CACHED, takes the
 // particle's) and the reaction draw.
-template <bool CE, bool CACHED = false>
+template <bool CE, bool CACHED = false, bool WW = false>
 __device__ __forceinline__ bool split_collide(const DevProblem& P, const RunParams& R, Particle& p, const Tallies& T,
                                              Acc& acc, const Bank& B, ErrorWord* err, unsigned em = 0u)
 {
@@ -719,15 +818,15 @@ __device__ __forceinline__ bool split_collide(const DevProblem& P, const RunPara
     } else {
         xs_lookup<CE>(P, p, material(P, p.cell), X);
     }
-    const Stream S = make_stream(R, p.id);
+    const Stream S = particle_stream<WW>(R, p);
     const uint4 b0 = S.block(p.n, BLK_MAIN);
-    const int type = collide_event<CE>(P, R, p, X, u01(b0.z, b0.w), B, err, em);
-    return finish_event(P, R, p, type, T, acc, B);
+    const int type = collide_event<CE, WW>(P, R, p, X, u01(b0.z, b0.w), B, err, em);
+    return finish_event<WW>(P, R, p, type, T, acc, B);
 }
 
 // A continuous-energy collision deferred within the lane that made its step:
 // the step's lookup terms, sigma_t and reaction draw come from k.
-template <bool CE>
+template <bool CE, bool WW = false>
 __device__ __forceinline__ bool kept_collide(const DevProblem& P, const RunParams& R, Particle& p, const Tallies& T,
                                             Acc& acc, const Bank& B, ErrorWord* err, unsigned em, CEKeep& k)
 {
@@ -737,15 +836,16 @@ __device__ __forceinline__ bool kept_collide(const DevProblem& P, const RunParam
     X.sa = 0.0;
     X.nsf = 0.0;
     X.keep = &k;
-    const int type = collide_event<CE>(P, R, p, X, k.xi, B, err, em);
-    return finish_event(P, R, p, type, T, acc, B);
+    const int type = collide_event<CE, WW>(P, R, p, X, k.xi, B, err, em);
+    return finish_event<WW>(P, R, p, type, T, acc, B);
 }
 
+template <bool WW = false>
 __device__ __forceinline__ bool split_surface(const DevProblem& P, const RunParams& R, Particle& p, const Tallies& T,
                                              Acc& acc, const Bank& B)
 {
     const int type = surface_event(P, p);
-    return finish_event(P, R, p, type, T, acc, B);
+    return finish_event<WW>(P, R, p, type, T, acc, B);
 }
 
 // Surface event of the lookup-event decomposition: the next event is a lookup
@@ -763,8 +863,14 @@ __device__ __forceinline__ int split_surface_next(const DevProblem& P, const Run
 // ---------------------------------------------------------------------------
 // SoA load / store
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ void load_particle(const SoA& s, unsigned long long i, Particle& p, bool ce, bool xs = false)
+__device__ __forceinline__ void load_particle(const SoA& s, unsigned long long i, Particle& p, bool ce, bool xs = false,
+                                              bool ww = false)
 {
+    p.nsplit = 0u;
+    if (ww) {
+        p.wt = s.wt[i];
+        p.sid = s.sid[i];
+    }
     p.t = s.t[i];
     p.hf = s.hf[i]; p.ha = s.ha[i]; p.hp = s.hp[i];
     if (xs) {
@@ -773,14 +879,23 @@ __device__ __forceinline__ void load_particle(const SoA& s, unsigned long long i
     p.x = s.x[i]; p.y = s.y[i]; p.z = s.z[i];
     p.u = s.u[i]; p.v = s.v[i]; p.w = s.w[i];
     p.iu = s.iu[i]; p.iv = s.iv[i]; p.iw = s.iw[i]; p.ia = s.ia[i];
-    if (ce) p.E = s.E[i]; else p.g = s.g[i];
+    if (ce) {
+        p.E = s.E[i];
+        p.g = 0;
+    } else {
+        p.g = s.g[i];
+    }
     p.cell = s.cell[i]; p.id = s.id[i]; p.n = s.n[i]; p.nsites = s.nsites[i]; p.pend = s.pend[i];
     p.prob = s.prob[i];
 }
 
 __device__ __forceinline__ void store_particle(const SoA& s, unsigned long long i, const Particle& p, bool ce,
-                                               bool xs = false)
+                                               bool xs = false, bool ww = false)
 {
+    if (ww) {
+        s.wt[i] = p.wt;
+        s.sid[i] = p.sid;
+    }
     s.t[i] = p.t;
     s.hf[i] = p.hf; s.ha[i] = p.ha; s.hp[i] = p.hp;
     if (xs) {
@@ -812,6 +927,8 @@ __device__ __forceinline__ bool load_presampled(const SoA& s, unsigned long long
     p.prob = 0u;
     p.t = 0.0;
     p.hf = p.ha = p.hp = 0.0;
+    p.wt = 1.0;
+    p.sid = p.nsplit = 0u;
     return s.id[i] == (unsigned)i;
 }
 

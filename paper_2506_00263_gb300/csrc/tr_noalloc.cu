@@ -94,6 +94,8 @@ void carve_links(unsigned char* b, unsigned long long n, SoA& s)
     s.t = (double*)take(8);
     s.hf = (double*)take(8); s.ha = (double*)take(8); s.hp = (double*)take(8);
     s.xst = s.xist = s.xsa = s.xnsf = nullptr;   // the lookup-event decomposition is not offered here
+    s.wt = nullptr;                              // nor are weight windows
+    s.sid = nullptr;
     s.g = (int*)take(4);
     s.cell = (unsigned*)take(4); s.id = (unsigned*)take(4); s.n = (unsigned*)take(4);
     s.nsites = (unsigned*)take(4); s.pend = (unsigned*)take(4); s.prob = (unsigned*)take(4);
@@ -135,6 +137,7 @@ extern "C" tr_status tr_run_fixed_source_noalloc(tr_problem* problem, const tr_r
     if ((P.mesh_size > 0 && !mesh_out) || (P.energy_size > 0 && !energy_out) || !scalars_out)
         return fail(TR_ERR_INVALID, "an output array for a present tally is NULL");
     if (P.timed) return fail(TR_ERR_INVALID, "timed problems have no output here: use tr_run_fixed_source");
+    if (P.ww_lo) return fail(TR_ERR_INVALID, "weight windows need tr_run_fixed_source");
     const size_t n_bins = (size_t)P.mesh_size + (size_t)P.energy_size + 3;
     if (n_bins > TR_NOALLOC_MAX_TALLY_BINS)
         return fail(TR_ERR_INVALID, "mesh + energy tally bins + 3 exceed TR_NOALLOC_MAX_TALLY_BINS");

@@ -2,8 +2,9 @@
 // the test suite: the library's Philox-4x32-10 (Salmon et al., SC'11) beside a
 // call of CUDA's own curand Philox4x32-10 on the same counters and keys; the
 // table-driven logarithm as the transport kernels evaluate it; and the
-// exponential ziggurat table the transport kernels read.  The transport
-// itself never calls these.
+// exponential ziggurat table the transport kernels read; and an issue-rate
+// probe of the arithmetic pipes for the roofline's ALU denominator.  The
+// transport itself never calls these.
 #include <curand_kernel.h>
 
 #include <cstring>
@@ -36,6 +37,46 @@ __global__ void k_log(const double* __restrict__ tab, const double* __restrict__
 {
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
         out[i] = tr_log(tab, x[i]);
+}
+
+// Issue-rate probe of the arithmetic pipes, the roofline's denominators: eight
+// independent dependency chains per thread.  OP 0..4: FP64 add, mul, fma,
+// division, square root (IEEE, correctly rounded); 5: FP32 fma; 6: INT32
+// multiply-add; 7: FP64 fma in only the first `lanes` lanes of each warp.
+constexpr int PROBE_ITERS = 4096;
+
+template <int OP>
+__global__ void __launch_bounds__(256) k_issue(double* out, double a0, double b, int lanes)
+{
+    double x[8];
+    float f[8];
+    unsigned u[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        x[j] = a0 + 1e-3 * j + 1e-9 * threadIdx.x;
+        f[j] = (float)x[j];
+        u[j] = 2654435761u * (threadIdx.x + j);
+    }
+    const bool on = OP != 7 || (int)(threadIdx.x & 31) < lanes;
+    if (on) {
+#pragma unroll 4
+        for (int i = 0; i < PROBE_ITERS; ++i) {
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                if (OP == 0) x[j] = __dadd_rn(x[j], b);
+                if (OP == 1) x[j] = __dmul_rn(x[j], b);
+                if (OP == 2 || OP == 7) x[j] = __fma_rn(x[j], b, b);
+                if (OP == 3) x[j] = __ddiv_rn(b, x[j]);
+                if (OP == 4) x[j] = __dsqrt_rn(__dadd_rn(x[j], b));
+                if (OP == 5) f[j] = __fmaf_rn(f[j], (float)b, (float)b);
+                if (OP == 6) u[j] = u[j] * 2654435761u + 12345u;
+            }
+        }
+    }
+    double s = 0.0;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) s += x[j] + (double)f[j] + (double)u[j];
+    out[blockIdx.x * blockDim.x + threadIdx.x] = s;
 }
 
 tr_status fail(tr_status s, const std::string& m)
@@ -123,5 +164,47 @@ extern "C" tr_status tr_selftest_zig_table(const tr_problem* problem, double* ou
     DeviceGuard dg(dev);
     ST_CUDA(cudaMemcpyAsync(out, P->zig_tab, 4 * ZIG_N * sizeof(double), cudaMemcpyDeviceToHost, st));
     ST_CUDA(cudaStreamSynchronize(st));
+    return TR_OK;
+}
+
+extern "C" tr_status tr_selftest_issue_rate(int32_t op, int32_t lanes, double* per_second)
+{
+    if (!per_second || op < 0 || op > 7 || (op == 7 && (lanes < 1 || lanes > 32)))
+        return fail(TR_ERR_INVALID, "op must be 0..7 (lanes 1..32 for op 7)");
+    int dev = 0, sms = 0;
+    ST_CUDA(cudaGetDevice(&dev));
+    ST_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    const int threads = 256, blocks = sms * 8;
+    Scratch s;
+    ST_CUDA(cudaMalloc(&s.p, (size_t)threads * blocks * sizeof(double)));
+    double* d = static_cast<double*>(s.p);
+    cudaEvent_t e0, e1;
+    ST_CUDA(cudaEventCreate(&e0));
+    ST_CUDA(cudaEventCreate(&e1));
+    const double b = op == 0 ? 1e-9 : op == 1 ? 1.0000001 : op == 3 ? 1.5 : op == 4 ? 0.25 : 0.5;
+    float ms = 0.f;
+    for (int rep = 0; rep < 2; ++rep) {   // the second launch is timed
+        cudaEventRecord(e0);
+        count_launches(1);
+        switch (op) {
+        case 0: k_issue<0><<<blocks, threads>>>(d, 1.0, b, 32); break;
+        case 1: k_issue<1><<<blocks, threads>>>(d, 1.0, b, 32); break;
+        case 2: k_issue<2><<<blocks, threads>>>(d, 1.0, b, 32); break;
+        case 3: k_issue<3><<<blocks, threads>>>(d, 1.0, b, 32); break;
+        case 4: k_issue<4><<<blocks, threads>>>(d, 1.0, b, 32); break;
+        case 5: k_issue<5><<<blocks, threads>>>(d, 1.0, b, 32); break;
+        case 6: k_issue<6><<<blocks, threads>>>(d, 1.0, b, 32); break;
+        default: k_issue<7><<<blocks, threads>>>(d, 1.0, b, lanes); break;
+        }
+        cudaEventRecord(e1);
+        cudaEventSynchronize(e1);
+        cudaEventElapsedTime(&ms, e0, e1);
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    ST_CUDA(cudaGetLastError());
+    const double chains = (double)threads * blocks * 8.0 * PROBE_ITERS;
+    // op 7: FP64 warp instructions per second (one per warp per chain step)
+    *per_second = (op == 7 ? chains / 32.0 : chains) / (ms * 1e-3);
     return TR_OK;
 }

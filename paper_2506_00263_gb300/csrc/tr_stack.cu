@@ -23,7 +23,7 @@ constexpr unsigned FULL = 0xFFFFFFFFu;
 // written and raises a capacity error
 __device__ __forceinline__ void push_to(const SoA* outs, unsigned long long* out_count, int dst, bool live,
                                         const Particle& p, bool ce, unsigned long long cap, ErrorWord* err,
-                                        bool xs = false)
+                                        bool xs = false, bool ww = false)
 {
     const int lane = threadIdx.x & 31;
     const unsigned act = __ballot_sync(FULL, live);
@@ -36,7 +36,7 @@ __device__ __forceinline__ void push_to(const SoA* outs, unsigned long long* out
     base = __shfl_sync(FULL, base, leader);
     if (live) {
         const unsigned long long pos = base + __popc(grp & ((1u << lane) - 1u));
-        if (pos < cap) store_particle(outs[dst], pos, p, ce, xs);
+        if (pos < cap) store_particle(outs[dst], pos, p, ce, xs, ww);
         else atomicCAS(&err->code, 0, ERR_CAPACITY);
     }
 }
@@ -49,8 +49,26 @@ struct StackArgs {
     int use_src;
 };
 
-// Monolithic ("step") event scheme: one stack pair, R events per pop.
-template <bool CE>
+// Weight-window split copies (p.nsplit each) pushed onto the output step
+// stack (warp-collective).
+__device__ __forceinline__ void push_copies(const SoA* outs, unsigned long long* out_count, bool live, Particle& p,
+                                            const RunParams& R, bool ce, unsigned long long cap, ErrorWord* err)
+{
+    const unsigned k = live ? p.nsplit : 0u;
+    const unsigned kmax = __reduce_max_sync(FULL, k);
+    for (unsigned c = 1; c <= kmax; ++c) {
+        const bool has = c <= k;
+        Particle q;
+        if (has) q = split_copy(R, p, c);
+        push_to(outs, out_count, Q_STEP, has, q, ce, cap, err, false, true);
+    }
+    p.nsplit = 0u;
+}
+
+// Monolithic ("step") event scheme: one stack pair, R events per pop.  WW:
+// weight-window problems (weighted scores, closeout, split copies pushed
+// onto the output stack).
+template <bool CE, bool WW = false>
 __global__ void __launch_bounds__(256) k_stack_mono(DevProblem P, const RunParams* Rd, StackArgs A, Tallies T,
                                                    ErrorWord* err)
 {
@@ -73,14 +91,16 @@ __global__ void __launch_bounds__(256) k_stack_mono(DevProblem P, const RunParam
         if (base < in_count) {
             const unsigned long long i = base + lane;
             if (i < in_count) {
-                load_particle(A.in[Q_STEP], i, p, CE);
+                load_particle(A.in[Q_STEP], i, p, CE, false, WW);
                 live = true;
             }
             __syncwarp();
             for (int r = 0; r < R.remap_every; ++r) {
                 const unsigned em = __ballot_sync(FULL, live);   // every lane of the warp is here
                 if (!em) break;
-                if (live) live = mono_event<CE>(P, R, p, T, acc, A.bank, err, em);
+                if (live) live = mono_event<CE, WW>(P, R, p, T, acc, A.bank, err, em);
+                __syncwarp();
+                if (WW) push_copies(A.out, ctl->out_count, live, p, R, CE, cap, err);
             }
         } else {
             // make_work: the input stack is fully claimed; create sources
@@ -100,7 +120,7 @@ __global__ void __launch_bounds__(256) k_stack_mono(DevProblem P, const RunParam
                 acc.ev[EV_SOURCE] += 1u;
             }
         }
-        push_to(A.out, ctl->out_count, Q_STEP, live, p, CE, cap, err);
+        push_to(A.out, ctl->out_count, Q_STEP, live, p, CE, cap, err, false, WW);
     }
     flush_acc(acc, T);
 }
@@ -553,6 +573,9 @@ cudaError_t launch_stack(const DevProblem& P, const RunParams* R, const SoA* in,
     } else if (dec == DEC_SPLIT) {
         if (P.kind == 1) k_stack_split<true, DEC_SPLIT><<<blocks, 256, 0, st>>>(P, R, A, T, err);
         else k_stack_split<false, DEC_SPLIT><<<blocks, 256, 0, st>>>(P, R, A, T, err);
+    } else if (P.ww_lo) {
+        if (P.kind == 1) k_stack_mono<true, true><<<blocks, 256, 0, st>>>(P, R, A, T, err);
+        else k_stack_mono<false, true><<<blocks, 256, 0, st>>>(P, R, A, T, err);
     } else {
         if (P.kind == 1) k_stack_mono<true><<<blocks, 256, 0, st>>>(P, R, A, T, err);
         else k_stack_mono<false><<<blocks, 256, 0, st>>>(P, R, A, T, err);

@@ -4,7 +4,8 @@ Philox4x32-10 and against the oracle; the device logarithm bit for bit
 against the oracle's on a million inputs (powers of two, 1 +- ulp, the
 table's breakpoints, the uniforms the transport draws, the range
 extremes), within 4 ulp of the C library; the ziggurat table the transport
-kernels read bit for bit against the oracle's."""
+kernels read bit for bit against the oracle's; and the issue-rate probe
+behind the roofline's ALU denominator."""
 import math
 
 import numpy as np
@@ -82,3 +83,20 @@ def test_device_ziggurat_table_equals_oracle_bitwise():
     dev = {"W": t[0:512:2], "C": t[1:512:2], "f": t[512::2], "df": t[513::2]}
     for name, a, b in (("W", dev["W"], W), ("C", dev["C"], Cw), ("f", dev["f"], f), ("df", dev["df"], df)):
         assert np.array_equal(a.view(np.int64), np.asarray(b).view(np.int64)), name
+
+
+def test_issue_rate_probe():
+    """The FP64 pipe retires at most 2 thread-operations per SM per clock and
+    a warp instruction costs the same however few lanes run it."""
+    import torch
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    dfma = max(tb.issue_rate(2) for _ in range(3))
+    ffma = max(tb.issue_rate(5) for _ in range(3))
+    assert 0.5 * sms * 2 * 1.0e9 < dfma < sms * 2 * 2.2e9, dfma
+    assert ffma > 16 * dfma
+    one, full = (max(tb.issue_rate(7, k) for _ in range(3)) for k in (1, 32))
+    assert abs(one / full - 1.0) < 0.15, (one, full)
+    for bad in ((8, 32), (-1, 32), (7, 0), (7, 33)):
+        with pytest.raises(tb.TransportError) as e:
+            tb.issue_rate(*bad)
+        assert e.value.status == tb.TR_ERR_INVALID
