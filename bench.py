@@ -904,7 +904,9 @@ def _pinned_copy(spec, torch):
     return spec.replace(**kw), nbytes
 
 
-ISSUE_OPS = ["dadd", "dmul", "dfma", "ddiv", "dsqrt", "ffma", "imad"]
+ISSUE_OPS = {0: "dadd", 1: "dmul", 2: "dfma", 3: "ddiv", 4: "dsqrt", 5: "ffma", 6: "imad",
+             8: "drcp (IEEE sequence)", 9: "drcp (sf_rcp, integer pipe)", 10: "dsqrt (IEEE sequence)",
+             11: "dsqrt (sf_sqrt, integer pipe)"}
 
 
 def run_issue_rate(args):
@@ -917,7 +919,7 @@ def run_issue_rate(args):
     reps = max(args.steps, 3)          # best of `reps` timed launches per operation
     with ClockSampler(0) as sampler:
         rows = [{"op": name, "per_s": max(tb.issue_rate(op) for _ in range(reps))}
-                for op, name in enumerate(ISSUE_OPS)]
+                for op, name in ISSUE_OPS.items()]
         lanes = [{"lanes": k, "warp_instr_per_s": max(tb.issue_rate(7, k) for _ in range(reps))}
                  for k in (1, 2, 4, 8, 16, 32)]
     clocks = sampler.summary()

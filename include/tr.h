@@ -434,9 +434,19 @@ tr_status tr_selftest_zig_table(const tr_problem *problem, double *out);
  * fma; 6: INT32 multiply-add (thread-operations per second to *per_second);
  * 7: FP64 fma executed by only the first `lanes` (1..32) lanes of each warp
  * (FP64 warp instructions per second: constant in `lanes` when a warp
- * instruction costs the same pipe time however few lanes are active).
+ * instruction costs the same pipe time however few lanes are active);
+ * 8 / 9: reciprocal by the IEEE sequence / by tr_selftest_softfp's integer
+ * method; 10 / 11: square root, the same pair.
  * Allocates device scratch; synchronous.  TR_ERR_INVALID for a bad op. */
 tr_status tr_selftest_issue_rate(int32_t op, int32_t lanes, double *per_second);
+
+/* The transport kernels' correctly rounded reciprocal and square root
+ * computed on the integer and FP32 pipes (paper has no counterpart: a GB300
+ * economy of the FP64 pipe), beside the IEEE hardware sequences, for n host
+ * doubles x[] into out[]: op 0: sf_rcp(x), 1: 1.0 / x, 2: sf_sqrt(x),
+ * 3: sqrt(x).  Ops 0 and 1 (2 and 3) must agree bit for bit on every input.
+ * Allocates device scratch; synchronous.  n <= 2^26. */
+tr_status tr_selftest_softfp(int32_t op, const double *x, size_t n, double *out);
 
 /* Diagnostics: number of kernels this library has launched in this process
  * (all kernels, all problems).  Read it before and after a call to count the

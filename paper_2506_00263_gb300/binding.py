@@ -150,8 +150,18 @@ def lib():
     L.tr_selftest_zig_table.restype = C.c_int
     L.tr_selftest_issue_rate.argtypes = [C.c_int32, C.c_int32, _dp]
     L.tr_selftest_issue_rate.restype = C.c_int
+    L.tr_selftest_softfp.argtypes = [C.c_int32, _dp, C.c_size_t, _dp]
+    L.tr_selftest_softfp.restype = C.c_int
     _lib = L
     return L
+
+
+def softfp(op: int, x) -> np.ndarray:
+    """tr_selftest_softfp: 0 sf_rcp, 1 1/x, 2 sf_sqrt, 3 sqrt, elementwise on the device."""
+    x = np.ascontiguousarray(x, np.float64)
+    out = np.empty_like(x)
+    _check(lib().tr_selftest_softfp(op, x.ctypes.data_as(_dp), x.size, out.ctypes.data_as(_dp)))
+    return out
 
 
 def issue_rate(op: int, lanes: int = 32) -> float:

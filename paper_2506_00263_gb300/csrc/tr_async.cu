@@ -836,19 +836,42 @@ __global__ void __launch_bounds__(256, TR_ASYNC_MIN_BLOCKS) k_async(DevProblem P
                             continue;
                         }
                         if constexpr (CE) {
+                            // A pass is either the collision pass (warp-uniform
+                            // choice) or the step pass; either way each lane ends
+                            // at most one event.  Continuous energy closes it with
+                            // one finish_event below (one inlined copy of the
+                            // closing code and of the collision, whether the lane
+                            // kept its step's lookup terms or computes them again:
+                            // measured faster); multigroup keeps a closing copy per
+                            // path (measured faster there).
                             const unsigned pm = __ballot_sync(em, live && pend_coll);
-                            if (pm == lm || __popc(pm) >= TR_COLL_MIN_CE) {
-                                const bool kc = live && pend_coll && ck_ok;
-                                const unsigned pk = __ballot_sync(em, kc);
-                                if (kc) live = kept_collide<CE, WW>(PP, RR, p, TT, acc, A.bank, err, pk, ck);
-                                const unsigned pr = pm & ~pk;
-                                if ((pr >> lane) & 1u)
-                                    live = split_collide<CE, false, WW>(PP, RR, p, TT, acc, A.bank, err, pr);
-                                if ((pm >> lane) & 1u) {
+                            const bool cpass = pm == lm || __popc(pm) >= TR_COLL_MIN_CE;
+                            int type = -1;
+                            if (cpass) {
+                                if (live && pend_coll) {
+                                    TR_LANES(15);
+                                    tr::XS X;
+                                    double xr;
+                                    X.keep = &ck;
+                                    if (ck_ok) {
+                                        // the step's lookup terms, sigma_t and reaction draw
+                                        X.st = ck.st;
+                                        X.inv_st = X.sa = X.nsf = 0.0;
+                                        xr = ck.xi;
+                                    } else {
+                                        // arrived pending from the stash: the lookup
+                                        // and the draw again, the same values
+                                        xs_lookup<CE>(PP, p, material(PP, p.cell), X);
+                                        const Stream S = particle_stream<WW>(RR, p);
+                                        const uint4 b0 = S.block(p.n, BLK_MAIN);
+                                        xr = u01(b0.z, b0.w);
+                                    }
+                                    type = collide_event<CE, WW>(PP, RR, p, X, xr, A.bank, err, pm);
                                     pend_coll = false;
                                     p.pend = 0u;
                                 }
                             } else if (live && !pend_coll) {
+                                TR_LANES(14);
                                 tr::XS X;
                                 X.keep = &ck;
                                 double xr;
@@ -860,10 +883,11 @@ __global__ void __launch_bounds__(256, TR_ASYNC_MIN_BLOCKS) k_async(DevProblem P
                                     ck.st = X.st;
                                     ck.xi = xr;
                                 } else {
-                                    live = finish_event<WW>(PP, RR, p, surface_event(PP, p), TT, acc, A.bank);
+                                    type = surface_event(PP, p);
                                     p.pend = 0u;
                                 }
                             }
+                            if (type >= 0) live = finish_event<WW>(PP, RR, p, type, TT, acc, A.bank);
                             continue;
                         }
                         const unsigned pm = __ballot_sync(em, live && pend_coll);

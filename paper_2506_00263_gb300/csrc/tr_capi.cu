@@ -14,7 +14,7 @@
 #include "tr_kernels.h"
 
 #ifndef TR_HASH_MANT
-#define TR_HASH_MANT 8   // union-grid hash: leading mantissa bits of E per bucket
+#define TR_HASH_MANT 10  // union-grid hash: leading mantissa bits of E per bucket
 #endif
 
 using namespace tr;

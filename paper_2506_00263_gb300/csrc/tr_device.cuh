@@ -22,8 +22,22 @@
 #include <cuda_runtime.h>
 
 #include "tr_fixed.cuh"
+#include "tr_softfp.cuh"
 
 namespace tr {
+
+// The transport's correctly rounded reciprocal and square root: the same
+// bits as 1.0 / x and sqrt(x).  TR_SOFTFP bit 0 (reciprocal) and bit 1
+// (square root) select the integer-pipe versions of tr_softfp.cuh instead
+// of the IEEE sequences on the FP64 pipe.  Alone they run 2.1x (reciprocal)
+// and 3.0x (square root) the IEEE rate, but inside the transport kernels
+// they measured slower (lattice 2.77e9 -> 2.61e9 events/s with both: the
+// kernels are not bound by FP64 issue alone), so the default is 0.
+#ifndef TR_SOFTFP
+#define TR_SOFTFP 0
+#endif
+__device__ __forceinline__ double tr_rcp(double x) { return (TR_SOFTFP & 1) ? sf_rcp(x) : __drcp_rn(x); }
+__device__ __forceinline__ double tr_sqrt(double x) { return (TR_SOFTFP & 2) ? sf_sqrt(x) : __dsqrt_rn(x); }
 
 constexpr int EV_SOURCE = 0, EV_SCATTER = 1, EV_ABSORB = 2, EV_SURF_INTERNAL = 3, EV_SURF_REFLECT = 4,
               EV_LEAK = 5, EV_CUTOFF = 6, EV_MAXEV = 7;
@@ -448,7 +462,7 @@ __device__ __forceinline__ void azimuth(const Stream& S, uint32_t n, double& cph
 {
     double a, b, a2, b2, s;
     disk_point(S, n, a, b, a2, b2, s, sm);
-    const double inv_s = __drcp_rn(s);
+    const double inv_s = tr_rcp(s);
     cphi = (a2 - b2) * inv_s;
     sphi = (2.0 * (a * b)) * inv_s;
 }
@@ -457,12 +471,12 @@ __device__ __forceinline__ void set_reciprocals(Particle& p)
 {
     TR_LANES(20);
     // (bits << 1) != 0 is x != +-0
-    // __drcp_rn is the correctly rounded reciprocal: the same value as 1.0 / x
-    p.iu = (dbits(p.u) << 1) ? __drcp_rn(p.u) : 0.0;
-    p.iv = (dbits(p.v) << 1) ? __drcp_rn(p.v) : 0.0;
-    p.iw = (dbits(p.w) << 1) ? __drcp_rn(p.w) : 0.0;
+    // tr_rcp is the correctly rounded reciprocal: the same value as 1.0 / x
+    p.iu = (dbits(p.u) << 1) ? tr_rcp(p.u) : 0.0;
+    p.iv = (dbits(p.v) << 1) ? tr_rcp(p.v) : 0.0;
+    p.iw = (dbits(p.w) << 1) ? tr_rcp(p.w) : 0.0;
     const double a = __fma_rn(p.u, p.u, p.v * p.v);
-    p.ia = gt0(a) ? __drcp_rn(a) : 0.0;
+    p.ia = gt0(a) ? tr_rcp(a) : 0.0;
 }
 
 // Isotropic direction (Marsaglia, Ann. Math. Stat. 43 (1972) 645): with the
@@ -472,7 +486,7 @@ __device__ __forceinline__ void iso_dir(const Stream& S, uint32_t n, Particle& p
 {
     double a, b, a2, b2, s;
     disk_point(S, n, a, b, a2, b2, s, sm);
-    const double t = 2.0 * sqrt(1.0 - s);
+    const double t = 2.0 * tr_sqrt(1.0 - s);
     p.u = __fma_rn(-2.0, s, 1.0);   // 2 s is exact: the same value as 1.0 - 2.0 * s
     p.v = a * t;
     p.w = b * t;
@@ -483,7 +497,7 @@ __device__ __forceinline__ void rotate(Particle& p, double mu, double cphi, doub
 {
     double t = __fma_rn(-mu, mu, 1.0);
     if (lt0(t)) t = 0.0;
-    const double st = sqrt(t);
+    const double st = tr_sqrt(t);
     const double u = p.u, v = p.v, w = p.w;
     // |w| > 0.9999999999 and w > 0 on the bit patterns (integer instructions)
     if ((dbits(w) & 0x7FFFFFFFFFFFFFFFll) > dbits(0.9999999999)) {
@@ -491,7 +505,7 @@ __device__ __forceinline__ void rotate(Particle& p, double mu, double cphi, doub
         p.v = st * sphi;
         p.w = gt0(w) ? mu : -mu;
     } else {
-        const double sq = sqrt(__fma_rn(-w, w, 1.0));
+        const double sq = tr_sqrt(__fma_rn(-w, w, 1.0));
         const double a1 = st / sq;
         p.u = mu * u + a1 * ((u * w) * cphi - v * sphi);
         p.v = mu * v + a1 * ((v * w) * cphi + u * sphi);
@@ -650,7 +664,7 @@ __device__ __forceinline__ void xs_ce(const DevProblem& P, int m, double E, XS& 
     }
     if (X.keep) X.keep->n = kept <= CE_KEEP_NUC ? kept : -1;
     X.st = cum;
-    X.inv_st = 1.0 / cum;
+    X.inv_st = tr_rcp(cum);
     X.sa = sa;
     X.nsf = 0.0;
 }

@@ -405,7 +405,7 @@ __device__ __forceinline__ void step_event(const DevProblem& P, const RunParams&
         pin_terms(P, p, cc, kk);
         const double a = __fma_rn(p.u, p.u, p.v * p.v);
         const double disc = __fma_rn(kk, kk, -(a * cc));
-        const double sq = sqrt(lt0(disc) ? 0.0 : disc);
+        const double sq = tr_sqrt(lt0(disc) ? 0.0 : disc);
         const double d_in = (sq - kk) * p.ia;
         const double d_out = ((-kk) - sq) * p.ia;
         const bool hit = gt0(a) && (in || (lt0(kk) && ge0(disc)));
@@ -583,7 +583,7 @@ __device__ __forceinline__ int collide_event(const DevProblem& P, const RunParam
     const double mu_cm = __fma_rn(2.0, S.first(p.n, BLK_ANGLE), -1.0);   // 2 xi exact: same as 2 xi - 1
     const double q = (A * A + (2.0 * A) * mu_cm) + 1.0;
     const double E1 = (p.E * q) * __ldg(P.inv_ap1sq + sel_n);
-    const double mu = (1.0 + A * mu_cm) / sqrt(q);
+    const double mu = (1.0 + A * mu_cm) / tr_sqrt(q);
     double cphi, sphi;
     azimuth(S, p.n, cphi, sphi, sm);
     rotate(p, mu, cphi, sphi);
@@ -821,22 +821,6 @@ __device__ __forceinline__ bool split_collide(const DevProblem& P, const RunPara
     const Stream S = particle_stream<WW>(R, p);
     const uint4 b0 = S.block(p.n, BLK_MAIN);
     const int type = collide_event<CE, WW>(P, R, p, X, u01(b0.z, b0.w), B, err, em);
-    return finish_event<WW>(P, R, p, type, T, acc, B);
-}
-
-// A continuous-energy collision deferred within the lane that made its step:
-// the step's lookup terms, sigma_t and reaction draw come from k.
-template <bool CE, bool WW = false>
-__device__ __forceinline__ bool kept_collide(const DevProblem& P, const RunParams& R, Particle& p, const Tallies& T,
-                                            Acc& acc, const Bank& B, ErrorWord* err, unsigned em, CEKeep& k)
-{
-    XS X;
-    X.st = k.st;
-    X.inv_st = 0.0;
-    X.sa = 0.0;
-    X.nsf = 0.0;
-    X.keep = &k;
-    const int type = collide_event<CE, WW>(P, R, p, X, k.xi, B, err, em);
     return finish_event<WW>(P, R, p, type, T, acc, B);
 }
 

@@ -2,8 +2,10 @@
 // the test suite: the library's Philox-4x32-10 (Salmon et al., SC'11) beside a
 // call of CUDA's own curand Philox4x32-10 on the same counters and keys; the
 // table-driven logarithm as the transport kernels evaluate it; and the
-// exponential ziggurat table the transport kernels read; and an issue-rate
-// probe of the arithmetic pipes for the roofline's ALU denominator.  The
+// exponential ziggurat table the transport kernels read; the integer-pipe
+// reciprocal and square root beside the IEEE hardware sequences; and an
+// issue-rate probe of the arithmetic pipes for the roofline's ALU
+// denominator.  The
 // transport itself never calls these.
 #include <curand_kernel.h>
 
@@ -12,6 +14,7 @@
 
 #include "../../include/tr.h"
 #include "tr_kernels.h"
+#include "tr_softfp.cuh"
 
 using namespace tr;
 
@@ -39,10 +42,20 @@ __global__ void k_log(const double* __restrict__ tab, const double* __restrict__
         out[i] = tr_log(tab, x[i]);
 }
 
+__global__ void k_softfp(int op, const double* __restrict__ x, size_t n, double* out)
+{
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        const double v = x[i];
+        out[i] = op == 0 ? sf_rcp(v) : op == 1 ? __drcp_rn(v) : op == 2 ? sf_sqrt(v) : __dsqrt_rn(v);
+    }
+}
+
 // Issue-rate probe of the arithmetic pipes, the roofline's denominators: eight
 // independent dependency chains per thread.  OP 0..4: FP64 add, mul, fma,
 // division, square root (IEEE, correctly rounded); 5: FP32 fma; 6: INT32
-// multiply-add; 7: FP64 fma in only the first `lanes` lanes of each warp.
+// multiply-add; 7: FP64 fma in only the first `lanes` lanes of each warp;
+// 8 / 9: reciprocal, IEEE sequence / integer-pipe sf_rcp; 10 / 11: square
+// root, IEEE sequence / sf_sqrt.
 constexpr int PROBE_ITERS = 4096;
 
 template <int OP>
@@ -69,7 +82,11 @@ __global__ void __launch_bounds__(256) k_issue(double* out, double a0, double b,
                 if (OP == 3) x[j] = __ddiv_rn(b, x[j]);
                 if (OP == 4) x[j] = __dsqrt_rn(__dadd_rn(x[j], b));
                 if (OP == 5) f[j] = __fmaf_rn(f[j], (float)b, (float)b);
-                if (OP == 6) u[j] = u[j] * 2654435761u + 12345u;
+                if (OP == 6) u[j] = u[j] * u[j] + 12345u;   // not affine: the chain cannot be folded
+                if (OP == 8) x[j] = __drcp_rn(x[j]);
+                if (OP == 9) x[j] = sf_rcp(x[j]);
+                if (OP == 10) x[j] = __dsqrt_rn(__dadd_rn(x[j], b));
+                if (OP == 11) x[j] = sf_sqrt(__dadd_rn(x[j], b));
             }
         }
     }
@@ -169,8 +186,8 @@ extern "C" tr_status tr_selftest_zig_table(const tr_problem* problem, double* ou
 
 extern "C" tr_status tr_selftest_issue_rate(int32_t op, int32_t lanes, double* per_second)
 {
-    if (!per_second || op < 0 || op > 7 || (op == 7 && (lanes < 1 || lanes > 32)))
-        return fail(TR_ERR_INVALID, "op must be 0..7 (lanes 1..32 for op 7)");
+    if (!per_second || op < 0 || op > 11 || (op == 7 && (lanes < 1 || lanes > 32)))
+        return fail(TR_ERR_INVALID, "op must be 0..11 (lanes 1..32 for op 7)");
     int dev = 0, sms = 0;
     ST_CUDA(cudaGetDevice(&dev));
     ST_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
@@ -181,7 +198,7 @@ extern "C" tr_status tr_selftest_issue_rate(int32_t op, int32_t lanes, double* p
     cudaEvent_t e0, e1;
     ST_CUDA(cudaEventCreate(&e0));
     ST_CUDA(cudaEventCreate(&e1));
-    const double b = op == 0 ? 1e-9 : op == 1 ? 1.0000001 : op == 3 ? 1.5 : op == 4 ? 0.25 : 0.5;
+    const double b = op == 0 ? 1e-9 : op == 1 ? 1.0000001 : op == 3 ? 1.5 : (op == 4 || op >= 10) ? 0.25 : 0.5;
     float ms = 0.f;
     for (int rep = 0; rep < 2; ++rep) {   // the second launch is timed
         cudaEventRecord(e0);
@@ -194,7 +211,11 @@ extern "C" tr_status tr_selftest_issue_rate(int32_t op, int32_t lanes, double* p
         case 4: k_issue<4><<<blocks, threads>>>(d, 1.0, b, 32); break;
         case 5: k_issue<5><<<blocks, threads>>>(d, 1.0, b, 32); break;
         case 6: k_issue<6><<<blocks, threads>>>(d, 1.0, b, 32); break;
-        default: k_issue<7><<<blocks, threads>>>(d, 1.0, b, lanes); break;
+        case 7: k_issue<7><<<blocks, threads>>>(d, 1.0, b, lanes); break;
+        case 8: k_issue<8><<<blocks, threads>>>(d, 1.0, b, 32); break;
+        case 9: k_issue<9><<<blocks, threads>>>(d, 1.0, b, 32); break;
+        case 10: k_issue<10><<<blocks, threads>>>(d, 1.0, b, 32); break;
+        default: k_issue<11><<<blocks, threads>>>(d, 1.0, b, 32); break;
         }
         cudaEventRecord(e1);
         cudaEventSynchronize(e1);
@@ -206,5 +227,22 @@ extern "C" tr_status tr_selftest_issue_rate(int32_t op, int32_t lanes, double* p
     const double chains = (double)threads * blocks * 8.0 * PROBE_ITERS;
     // op 7: FP64 warp instructions per second (one per warp per chain step)
     *per_second = (op == 7 ? chains / 32.0 : chains) / (ms * 1e-3);
+    return TR_OK;
+}
+
+extern "C" tr_status tr_selftest_softfp(int32_t op, const double* x, size_t n, double* out)
+{
+    if (!x || !out || op < 0 || op > 3) return fail(TR_ERR_INVALID, "op must be 0..3 and x, out non-NULL");
+    if (n == 0) return TR_OK;
+    if (n > (1u << 26)) return fail(TR_ERR_INVALID, "n must be at most 2^26");
+    Scratch s;
+    ST_CUDA(cudaMalloc(&s.p, 2 * n * sizeof(double)));
+    double* d_x = static_cast<double*>(s.p);
+    double* d_out = d_x + n;
+    ST_CUDA(cudaMemcpy(d_x, x, n * 8, cudaMemcpyHostToDevice));
+    count_launches(1);
+    k_softfp<<<(unsigned)((n + 255) / 256 < 4096 ? (n + 255) / 256 : 4096), 256>>>(op, d_x, n, d_out);
+    ST_CUDA(cudaGetLastError());
+    ST_CUDA(cudaMemcpy(out, d_out, n * 8, cudaMemcpyDeviceToHost));
     return TR_OK;
 }

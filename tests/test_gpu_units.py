@@ -5,7 +5,8 @@ against the oracle's on a million inputs (powers of two, 1 +- ulp, the
 table's breakpoints, the uniforms the transport draws, the range
 extremes), within 4 ulp of the C library; the ziggurat table the transport
 kernels read bit for bit against the oracle's; and the issue-rate probe
-behind the roofline's ALU denominator."""
+behind the roofline's ALU denominator; the integer-pipe reciprocal and square
+root bit for bit against the IEEE operations."""
 import math
 
 import numpy as np
@@ -96,7 +97,41 @@ def test_issue_rate_probe():
     assert ffma > 16 * dfma
     one, full = (max(tb.issue_rate(7, k) for _ in range(3)) for k in (1, 32))
     assert abs(one / full - 1.0) < 0.15, (one, full)
-    for bad in ((8, 32), (-1, 32), (7, 0), (7, 33)):
+    for bad in ((12, 32), (-1, 32), (7, 0), (7, 33)):
         with pytest.raises(tb.TransportError) as e:
             tb.issue_rate(*bad)
         assert e.value.status == tb.TR_ERR_INVALID
+
+
+def _softfp_inputs():
+    rng = np.random.default_rng(23)
+    xs = [rng.integers(0, 2 ** 64, size=2_000_000, dtype=np.uint64).view(np.float64),
+          rng.uniform(-1.0, 1.0, 2_000_000),
+          1.0 + np.arange(-20000, 20000) * 2.0 ** -52,
+          np.ldexp(1.0, np.arange(-1074, 1024)).astype(np.float64)]
+    edge = []
+    for e in (0, 1, 2, 1021, 1022, 1023, 1024, 2043, 2044, 2045, 2046, 2047):
+        for frac in (0, 1, 2, (1 << 52) - 1, (1 << 52) - 2, 1 << 51, (1 << 51) + 1, 0x5555555555555):
+            for sign in (0, 1):
+                edge.append((sign << 63) | (e << 52) | frac)
+    xs.append(np.array(edge, np.uint64).view(np.float64))
+    return np.concatenate(xs)
+
+
+def test_integer_pipe_reciprocal_and_sqrt_are_correctly_rounded():
+    """sf_rcp and sf_sqrt (the transport kernels' reciprocal and square root
+    on the integer and FP32 pipes) return the bits of the IEEE operations on
+    4 million inputs: random bit patterns over the whole range, direction
+    cosines, 1 +- k ulp, every power of two, the exponent and mantissa edges,
+    zeros, subnormals, infinities and NaNs; numpy (IEEE) agrees."""
+    x = _softfp_inputs()
+    with np.errstate(all="ignore"):
+        host_rcp = 1.0 / x
+        host_sqrt = np.sqrt(x)
+    for soft, hw, host in ((0, 1, host_rcp), (2, 3, host_sqrt)):
+        a = tb.softfp(soft, x)
+        b = tb.softfp(hw, x)
+        bad = (a.view(np.uint64) != b.view(np.uint64)) & ~(np.isnan(a) & np.isnan(b))
+        assert not bad.any(), (soft, int(bad.sum()), x[bad][:4], a[bad][:4], b[bad][:4])
+        badh = (a.view(np.uint64) != host.view(np.uint64)) & ~(np.isnan(a) & np.isnan(host))
+        assert not badh.any(), (soft, int(badh.sum()), x[badh][:4], a[badh][:4], host[badh][:4])
