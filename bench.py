@@ -45,7 +45,8 @@ B_EVENT = {"lattice": 2 * 64, "ce": 2 * 72 + 16 + 16 * 9}
 # The transport kernels' sources: the FP64-operation and DRAM-traffic figures
 # below were measured on the sources with the digest stored beside them, and
 # are reported as stale once the built sources differ.
-TRANSPORT_SOURCES = ("tr_device.cuh", "tr_events.cuh", "tr_fixed.cuh", "tr_kernels.h", "tr_async.cu", "tr_stack.cu")
+TRANSPORT_SOURCES = ("tr_device.cuh", "tr_events.cuh", "tr_fixed.cuh", "tr_softfp.cuh", "tr_kernels.h", "tr_async.cu",
+                     "tr_stack.cu")
 
 
 def kernel_digest(csrc=None):
@@ -380,12 +381,14 @@ def measure_ce_line(torch, tb, inputs, n=1_000_000, steps=3):
     asynchronous monolithic, 64 events per remap): events/s and rooflines."""
     prob = tb.Problem(inputs.ce_pin_cell(n_ebins=100))
     opts = tb.RunOpts(n_histories=n, seed=1, scheme=tb.SCHEME_ASYNC, decomposition=tb.DECOMP_MONO, remap_every=64)
-    t, ev = _time_fixed(torch, tb, prob, opts, steps, 2)
+    with ClockSampler(torch.cuda.current_device()) as sampler:
+        t, ev = _time_fixed(torch, tb, prob, opts, steps, 2)
     prob.close()
     return {"workload": CE_WORKLOAD + f", {n} histories, 100 bins, 64 events per remap",
-            "events_per_s": ev / t, "histories_per_s": n * steps / t,
-            "hbm_roofline": _hbm_roof(ev, t, "ce"),
-            "alu_roofline": _alu_roof("ce", ev, t, "FP64 pipe (add/mul/fma) of the run")}
+            "events_per_s": ev / t, "histories_per_s": n * steps / t, "clocks": sampler.summary(),
+            "hbm_roofline": _hbm_roof(ev / steps, t / steps, "ce", _fresh_traffic("ce")),
+            "alu_roofline": _alu_roof("ce", ev / steps, t / steps, "FP64 pipe (add/mul/fma) of the run",
+                                      _fresh_traffic("ce"))}
 
 
 BATCH_WORKLOAD = ("256 independent multigroup voxel boxes (groups from {1,2,7,20,70}, 1-8 materials, "
@@ -660,9 +663,13 @@ def run_ce_workload(args):
         from paper_2506_00263_gb300 import parallel
         t, ev_all, _ = parallel.reduce_timing(t, ev_all, 0.0, device="cuda")
     if rank == 0:
-        roof = _hbm_roof(ev, t, "ce")
-        if (args.scheme, args.decomp, args.ebins, opts.remap_every) == ("async", "mono", 100, 64):
-            alu = _alu_roof("ce", ev, t, "FP64 pipe (add/mul/fma) of the run (asynchronous monolithic, 100 bins)")
+        measured_cfg = (args.scheme, args.decomp, args.ebins, opts.remap_every, args.n_hist) == \
+            ("async", "mono", 100, 64, 1_000_000)
+        traffic = _fresh_traffic("ce") if measured_cfg else None
+        roof = _hbm_roof(ev / args.steps, t / args.steps, "ce", traffic)
+        if measured_cfg:
+            alu = _alu_roof("ce", ev / args.steps, t / args.steps,
+                            "FP64 pipe (add/mul/fma) of the run (asynchronous monolithic, 100 bins)", traffic)
             roof = alu if (alu and not alu.get("stale")) else roof
         line = _side_line(args, ws, CE_WORKLOAD, m, t, ev_all, float(args.n_hist) * args.steps * ws, sampler, roof,
                           {"scheme": args.scheme, "energy_bins": args.ebins,
@@ -869,11 +876,19 @@ def run_lattice_sweep(args):
 # (asynchronous monolithic, 512 events between remaps) and the CE pin cell
 # (1e6 histories, 100 bins, 64 events between remaps).  Each figure carries
 # the kernel_digest() of the sources it was measured on.
-FP64_OPS = {"lattice": (55.0, "be1a0aa713203f72"), "ce": (121.9, "be1a0aa713203f72")}
-# DRAM bytes (read + write) of one 1e6-history lattice batch's transport
-# (source pre-sampling and transport kernels, asynchronous monolithic, 512
-# events between remaps), dram__bytes_read.sum + dram__bytes_write.sum.
-TRAFFIC = {"lattice": (219.9e6, "be1a0aa713203f72")}
+FP64_OPS = {"lattice": (54.8, "d468b692fee8b80e"), "ce": (120.5, "d468b692fee8b80e")}
+# DRAM bytes (read + write), dram__bytes_read.sum + dram__bytes_write.sum, of
+# one 1e6-history lattice batch's transport (source pre-sampling and transport
+# kernels, asynchronous monolithic, 512 events between remaps; the mean of the
+# timed step's three batches) and of one 1e6-history CE pin-cell run (the same
+# two kernels, 64 events between remaps, 100 energy bins).
+TRAFFIC = {"lattice": (229.5e6, "d468b692fee8b80e"), "ce": (224.0e6, "d468b692fee8b80e")}
+
+
+def _fresh_traffic(key):
+    """The measured DRAM bytes per launch of `key`, or None once the kernels changed."""
+    v, fresh = measured_figure(TRAFFIC, key)
+    return v if fresh else None
 
 
 def measured_figure(table, key):
