@@ -725,11 +725,8 @@ static bool carve_bank(tr_problem* pr, const char* name, unsigned long long cap,
     return true;
 }
 
-static tr_status check_err(tr_problem* pr)
+static tr_status decode_err(const ErrorWord& h)
 {
-    ErrorWord h{};
-    TR_CUDA(cudaMemcpyAsync(&h, pr->err, sizeof(h), cudaMemcpyDeviceToHost, pr->stream));
-    TR_CUDA(cudaStreamSynchronize(pr->stream));
     if (h.code == ERR_CAPACITY) return set_err(TR_ERR_CAPACITY, "a queue, link arena or fission bank overflowed");
     if (h.code == ERR_RANGE)
         return set_err(TR_ERR_CAPACITY, "a tally contribution exceeded the fixed-point range (|score| >= 2^39)");
@@ -738,6 +735,23 @@ static tr_status check_err(tr_problem* pr)
     if (h.code != 0) return set_err(TR_ERR_INVALID, "device reported invalid state (code " + std::to_string(h.code) + ")");
     return TR_OK;
 }
+
+static tr_status check_err(tr_problem* pr)
+{
+    ErrorWord h{};
+    TR_CUDA(cudaMemcpyAsync(&h, pr->err, sizeof(h), cudaMemcpyDeviceToHost, pr->stream));
+    TR_CUDA(cudaStreamSynchronize(pr->stream));
+    return decode_err(h);
+}
+
+// Status words read back after a launch, gathered on the device into one
+// buffer so that the host reads them with a single copy.
+struct Readback {
+    AsyncCtl hc;
+    ErrorWord err;
+    unsigned long long count[2];
+    FixBin scal[3];
+};
 
 static tr_status ensure_log(tr_problem* pr, size_t n)
 {
@@ -801,6 +815,13 @@ static tr_status zero_raw(tr_problem* pr)
 struct TransportOut {
     unsigned long long launches = 0, spills = 0, refills = 0;
     double kernel_ms = 0.0;
+    // in: a device counter to read with the launch's status (the fission
+    // bank's size), or null; out (when `have_readback`): its value and the
+    // scalar tallies' raw bins
+    const unsigned long long* want_count = nullptr;
+    bool have_readback = false;
+    unsigned long long count = 0;
+    FixBin scal[3] = {};
 };
 
 // Device time of one kernel launch: events recorded around it on the stream.
@@ -1000,10 +1021,37 @@ static tr_status transport(tr_problem* pr, const tr_run_opts* o, RunParams R, co
     TR_CUDA(launch_async(P, R, A, T, pr->err, pr->sms * bps, st, &smem));
     TR_CUDA(cudaEventRecord(lt.b, st));
     out.launches += 1;
-    TR_CUDA(cudaMemcpyAsync(&hc, A.ctl, sizeof(hc), cudaMemcpyDeviceToHost, st));
+    // the fixed-order reduction of the per-history scores follows the launch
+    // in the stream (after a failed launch its sums are discarded)
+    TR_CUDA(launch_hist_reduce(T, R.n_hist, hist_partial, st));
+    // one host round trip: control block, error word, the caller's counter
+    // and the scalar bins, gathered on the device
+    Readback* drb = (Readback*)workspace(pr, "readback", sizeof(Readback));
+    if (!drb) return set_err(TR_ERR_NOMEM, "readback buffer allocation failed");
+    Gather g{};
+    g.src[0] = A.ctl;
+    g.dst[0] = &drb->hc;
+    g.bytes[0] = sizeof(AsyncCtl);
+    g.src[1] = pr->err;
+    g.dst[1] = &drb->err;
+    g.bytes[1] = sizeof(ErrorWord);
+    g.src[2] = pr->raw_scal;
+    g.dst[2] = drb->scal;
+    g.bytes[2] = 3 * sizeof(FixBin);
+    g.n = 3;
+    if (out.want_count) {
+        g.src[3] = out.want_count;
+        g.dst[3] = &drb->count[0];
+        g.bytes[3] = sizeof(unsigned long long);
+        g.n = 4;
+    }
+    TR_CUDA(launch_gather(g, st));
+    Readback rb;
+    TR_CUDA(cudaMemcpyAsync(&rb, drb, sizeof(rb), cudaMemcpyDeviceToHost, st));
     TR_CUDA(cudaStreamSynchronize(st));
+    hc = rb.hc;
     out.kernel_ms += lt.elapsed();
-    tr_status es = check_err(pr);
+    tr_status es = decode_err(rb.err);
     if (es == TR_ERR_TIMEOUT)
         return set_err(es, g_err + "; live " + std::to_string(hc.live) + ", source cursor " +
                                std::to_string(hc.src_cursor) + " of " + std::to_string(R.n_hist) + ", spills " +
@@ -1013,8 +1061,10 @@ static tr_status transport(tr_problem* pr, const tr_run_opts* o, RunParams R, co
     out.spills += hc.spills;
     out.refills += hc.refills;
     if (hc.live != 0) return set_err(TR_ERR_STATE, "asynchronous run ended with live particles");
-    TR_CUDA(launch_hist_reduce(T, R.n_hist, hist_partial, st));
-    return hist_partial ? check_err(pr) : TR_OK;   // the reduction reports an out-of-range total
+    out.have_readback = true;
+    out.count = rb.count[0];
+    std::memcpy(out.scal, rb.scal, sizeof(out.scal));
+    return TR_OK;
 }
 
 static RunParams base_params(const tr_run_opts* o, unsigned long long n)
@@ -1281,16 +1331,22 @@ extern "C" tr_status tr_run_power_iteration(tr_problem* pr, const tr_eig_opts* e
         R.inv_k = 1.0 / k;
         R.n_hist = N;
         TransportOut to;
+        to.want_count = bank.count;
         s = transport(pr, o, R, bank, have_src ? &source : nullptr, to);
         if (s != TR_OK) return s;
         kernel_ms += to.kernel_ms;
         tlaunch += to.launches;
-        // the raw accumulators hold separate copies for mesh, energy, scalars;
-        // gather them into one contiguous view for the statistics
+        // the bank's size and the scalar bins (read with the launch's status
+        // by the asynchronous scheme; the stack scheme reads them here)
         unsigned long long M = 0;
-        TR_CUDA(cudaMemcpyAsync(&M, bank.count, 8, cudaMemcpyDeviceToHost, st));
-        TR_CUDA(cudaMemcpyAsync(scal.data(), pr->raw_scal, 3 * sizeof(FixBin), cudaMemcpyDeviceToHost, st));
-        TR_CUDA(cudaStreamSynchronize(st));
+        if (to.have_readback) {
+            M = to.count;
+            std::memcpy(scal.data(), to.scal, 3 * sizeof(FixBin));
+        } else {
+            TR_CUDA(cudaMemcpyAsync(&M, bank.count, 8, cudaMemcpyDeviceToHost, st));
+            TR_CUDA(cudaMemcpyAsync(scal.data(), pr->raw_scal, 3 * sizeof(FixBin), cudaMemcpyDeviceToHost, st));
+            TR_CUDA(cudaStreamSynchronize(st));
+        }
         if (M > cap) return set_err(TR_ERR_CAPACITY, "fission bank overflow");
         const double kb = k * ((double)M / (double)N);
         if (res->k_batch) res->k_batch[b] = kb;
@@ -1314,25 +1370,42 @@ extern "C" tr_status tr_run_power_iteration(tr_problem* pr, const tr_eig_opts* e
             pr->log_count = R.want_log ? N : 0;
             break;
         }
-        // order the bank by (parent, site sequence)
+        // order the bank by (parent, site sequence); splitting roulette back
+        // to n_per_batch.  The host reads the two scan totals and the error
+        // word once, after the population is written (the kernels bound
+        // every index by its buffer and report overflows in the error word).
+        Readback* drb = (Readback*)workspace(pr, "readback", sizeof(Readback));
+        if (!drb) return set_err(TR_ERR_NOMEM, "readback buffer allocation failed");
         TR_CUDA(launch_scan(site_count, N, tiles, offs, total, st));
-        unsigned long long tot = 0;
-        TR_CUDA(cudaMemcpyAsync(&tot, total, 8, cudaMemcpyDeviceToHost, st));
-        TR_CUDA(cudaStreamSynchronize(st));
-        if (tot != M) return set_err(TR_ERR_STATE, "bank site counts disagree with the bank size");
+        Gather g1{};
+        g1.src[0] = total;
+        g1.dst[0] = &drb->count[0];
+        g1.bytes[0] = sizeof(unsigned long long);
+        g1.n = 1;
+        TR_CUDA(launch_gather(g1, st));
         TR_CUDA(launch_bank_order(bank, M, offs, ordered, pr->err, st));
-        // splitting roulette back to n_per_batch
         const double r = (double)eo->n_per_batch / (double)M;
         const double fl = std::floor(r), fr = r - fl;
         TR_CUDA(launch_pop_copies(M, R.key0, (uint32_t)(o->seed >> 32) ^ TAG_POP, b, (unsigned)fl, fr, copies, st));
         TR_CUDA(launch_scan(copies, M, tiles, offs, total, st));
-        unsigned long long nn = 0;
-        TR_CUDA(cudaMemcpyAsync(&nn, total, 8, cudaMemcpyDeviceToHost, st));
+        TR_CUDA(launch_pop_write(ordered, M, copies, offs, source, cap, pr->err, st));
+        Gather g2{};
+        g2.src[0] = total;
+        g2.dst[0] = &drb->count[1];
+        g2.bytes[0] = sizeof(unsigned long long);
+        g2.src[1] = pr->err;
+        g2.dst[1] = &drb->err;
+        g2.bytes[1] = sizeof(ErrorWord);
+        g2.n = 2;
+        TR_CUDA(launch_gather(g2, st));
+        Readback rb;
+        TR_CUDA(cudaMemcpyAsync(&rb, drb, sizeof(rb), cudaMemcpyDeviceToHost, st));
         TR_CUDA(cudaStreamSynchronize(st));
+        const unsigned long long tot = rb.count[0], nn = rb.count[1];
+        if (tot != M) return set_err(TR_ERR_STATE, "bank site counts disagree with the bank size");
         if (nn > cap) return set_err(TR_ERR_CAPACITY, "source bank overflow after population control");
         if (nn >= (1ull << 32)) return set_err(TR_ERR_CAPACITY, "batch too large");
-        TR_CUDA(launch_pop_write(ordered, M, copies, offs, source, st));
-        s = check_err(pr);
+        s = decode_err(rb.err);
         if (s != TR_OK) return s;
         N = nn;
         have_src = true;

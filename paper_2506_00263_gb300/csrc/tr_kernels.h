@@ -110,7 +110,18 @@ cudaError_t launch_bank_order(const Bank& in, unsigned long long m, const unsign
 cudaError_t launch_pop_copies(unsigned long long m, uint32_t key0, uint32_t key1, uint32_t batch, unsigned fl,
                               double fr, unsigned* copies, cudaStream_t st);
 cudaError_t launch_pop_write(const Bank& in, unsigned long long m, const unsigned* copies,
-                             const unsigned long long* offset, const Bank& out, cudaStream_t st);
+                             const unsigned long long* offset, const Bank& out, unsigned long long cap, ErrorWord* err,
+                             cudaStream_t st);
+// Up to 8 small device-to-device copies in one single-block launch, so that
+// the host reads a batch's status words (gathered in one buffer) with one
+// copy: one host round trip instead of one per word.
+struct Gather {
+    const void* src[8];
+    void* dst[8];
+    unsigned bytes[8];
+    int n;
+};
+cudaError_t launch_gather(const Gather& g, cudaStream_t st);
 cudaError_t launch_eig_accumulate(const FixBin* raw, int n, double inv_n, double* sum, double* sq, cudaStream_t st);
 cudaError_t launch_scale(const double* in, int n, double s, double* out, cudaStream_t st);
 // The per-history scalar scores of histories [0, n) (T.hist_*) summed in a

@@ -369,13 +369,20 @@ __global__ void k_pop_copies(unsigned long long m, uint32_t key0, uint32_t key1,
     }
 }
 
+// (copies beyond the output's capacity are not written: they raise a
+// capacity error, which the host reads with the batch's other status words)
 __global__ void k_pop_write(Bank in, unsigned long long m, const unsigned* __restrict__ copies,
-                            const unsigned long long* __restrict__ offset, Bank out)
+                            const unsigned long long* __restrict__ offset, Bank out, unsigned long long cap,
+                            ErrorWord* err)
 {
     for (unsigned long long s = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; s < m;
          s += (unsigned long long)gridDim.x * blockDim.x) {
         const unsigned long long o = offset[s];
-        const unsigned c = copies[s];
+        unsigned c = copies[s];
+        if (o + c > cap) {
+            atomicCAS(&err->code, 0, ERR_CAPACITY);
+            c = o < cap ? (unsigned)(cap - o) : 0u;
+        }
         for (unsigned k = 0; k < c; ++k) {
             out.x[o + k] = in.x[s];
             out.y[o + k] = in.y[s];
@@ -614,11 +621,29 @@ cudaError_t launch_pop_copies(unsigned long long m, uint32_t key0, uint32_t key1
 }
 
 cudaError_t launch_pop_write(const Bank& in, unsigned long long m, const unsigned* copies,
-                             const unsigned long long* offset, const Bank& out, cudaStream_t st)
+                             const unsigned long long* offset, const Bank& out, unsigned long long cap, ErrorWord* err,
+                             cudaStream_t st)
 {
     if (m == 0) return cudaSuccess;
     count_launches(1);
-    k_pop_write<<<grid_for(m, 256, 4096), 256, 0, st>>>(in, m, copies, offset, out);
+    k_pop_write<<<grid_for(m, 256, 4096), 256, 0, st>>>(in, m, copies, offset, out, cap, err);
+    return cudaGetLastError();
+}
+
+__global__ void k_gather(Gather g)
+{
+    for (int k = 0; k < g.n; ++k) {
+        const unsigned char* src = static_cast<const unsigned char*>(g.src[k]);
+        unsigned char* dst = static_cast<unsigned char*>(g.dst[k]);
+        for (unsigned i = threadIdx.x; i < g.bytes[k]; i += blockDim.x) dst[i] = src[i];
+    }
+}
+
+cudaError_t launch_gather(const Gather& g, cudaStream_t st)
+{
+    if (g.n <= 0) return cudaSuccess;
+    count_launches(1);
+    k_gather<<<1, 256, 0, st>>>(g);
     return cudaGetLastError();
 }
 
