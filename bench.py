@@ -42,11 +42,11 @@ WORKLOAD = "c5g7-shaped 7-group lattice k-eigenvalue, 1e6 histories/batch, 20 in
 # (nuclide, reaction) term of the material (9 in the fuel): 304 B.
 B_EVENT = {"lattice": 2 * 64, "ce": 2 * 72 + 16 + 16 * 9}
 
-# The transport kernels' sources: the FP64-operation and DRAM-traffic figures
-# below were measured on the sources with the digest stored beside them, and
-# are reported as stale once the built sources differ.
-TRANSPORT_SOURCES = ("tr_device.cuh", "tr_events.cuh", "tr_fixed.cuh", "tr_softfp.cuh", "tr_kernels.h", "tr_async.cu",
-                     "tr_stack.cu")
+# The sources the measured kernels (k_presample and k_async, tr_async.cu and
+# the headers it includes) are compiled from: the FP64-operation and
+# DRAM-traffic figures below were measured on the sources with the digest
+# stored beside them, and are reported as stale once the built sources differ.
+TRANSPORT_SOURCES = ("tr_device.cuh", "tr_events.cuh", "tr_fixed.cuh", "tr_softfp.cuh", "tr_kernels.h", "tr_async.cu")
 
 
 def kernel_digest(csrc=None):

@@ -495,6 +495,24 @@ __device__ __forceinline__ void bank_sites(const DevProblem& P, const RunParams&
     }
 }
 
+// Multigroup collision up to its direction: fission banking and the
+// reaction, the first g' with xi * Sigma_t below the cumulative Sigma_s.
+// Returns g', or -1 for absorption.
+template <bool WW>
+__device__ __forceinline__ int collide_mg_react(const DevProblem& P, const RunParams& R, Particle& p, const XS& X,
+                                                double xi_react, const Bank& B, ErrorWord* err, unsigned cm)
+{
+    const Stream S = particle_stream<WW>(R, p);
+    const int m = material(P, p.cell);
+    if (R.eig && gt0(X.nsf)) bank_sites(P, R, S, p, m, X, B, err);
+    if (cm) __syncwarp(cm);
+    const double t = xi_react * X.st;
+    const double* cs = P.cum_s + (m * P.G + p.g) * P.G;
+    int gp = -1;
+    for (int h = 0; h < P.G; ++h) gp = (gp < 0 && lt_nn(t, __ldg(cs + h))) ? h : gp;
+    return gp;
+}
+
 // cm: the lanes of this warp that run the collision together (a mask every
 // one of them passes, from a ballot), or 0.  With a mask the colliding lanes
 // are regrouped after the fission banking and the reaction selection (which
@@ -508,15 +526,8 @@ __device__ __forceinline__ int collide_event(const DevProblem& P, const RunParam
 {
     TR_LANES(16);
     const Stream S = particle_stream<WW>(R, p);
-    const int m = material(P, p.cell);
     if (!CE) {
-        if (R.eig && gt0(X.nsf)) bank_sites(P, R, S, p, m, X, B, err);
-        if (cm) __syncwarp(cm);
-        // the first g' with xi * Sigma_t below the cumulative Sigma_s; none: absorption
-        const double t = xi_react * X.st;
-        const double* cs = P.cum_s + (m * P.G + p.g) * P.G;
-        int gp = -1;
-        for (int h = 0; h < P.G; ++h) gp = (gp < 0 && lt_nn(t, __ldg(cs + h))) ? h : gp;
+        const int gp = collide_mg_react<WW>(P, R, p, X, xi_react, B, err, cm);
         const unsigned sm = cm ? __ballot_sync(cm, gp >= 0) : 0u;
         if (gp < 0) return EV_ABSORB;
         TR_LANES(17);
@@ -524,6 +535,7 @@ __device__ __forceinline__ int collide_event(const DevProblem& P, const RunParam
         iso_dir(S, p.n, p, sm);
         return EV_SCATTER;
     }
+    const int m = material(P, p.cell);
     // continuous energy: the lookup terms in order, and the first (nuclide,
     // reaction) with xi * sigma_t below the running sum; if none (rounding),
     // the last term with a positive value.  Nuclides absent from the material
