@@ -3,6 +3,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstddef>
 #include <cstring>
 #include <chrono>
 #include <map>
@@ -70,6 +71,7 @@ struct tr_problem {
     std::vector<int> hpin;                    // host copy: 1 where the cell holds a pin
     cudaGraphExec_t batch_graph = nullptr;
     std::map<std::vector<unsigned long long>, cudaGraphExec_t> stack_graphs;   // stack-scheme loops by buffers
+    std::map<std::vector<int>, int> async_occupancy;   // resident blocks per SM by (decomposition, stash, pre-sampling)
     std::vector<unsigned long long> batch_key;
     unsigned long long batch_graph_launches = 0;
 };
@@ -748,6 +750,7 @@ static tr_status check_err(tr_problem* pr)
 // buffer so that the host reads them with a single copy.
 struct Readback {
     AsyncCtl hc;
+    StackCtl sc;
     ErrorWord err;
     unsigned long long count[2];
     FixBin scal[3];
@@ -823,6 +826,32 @@ struct TransportOut {
     unsigned long long count = 0;
     FixBin scal[3] = {};
 };
+
+// The status words of a transport launch, gathered on the device and read
+// with one copy: the scheme's control block, the error word, the scalar
+// bins and, if given, a counter of the caller's (the fission bank's size).
+static tr_status read_status(tr_problem* pr, const AsyncCtl* actl, const StackCtl* sctl,
+                             const unsigned long long* count, Readback& rb)
+{
+    Readback* drb = (Readback*)workspace(pr, "readback", sizeof(Readback));
+    if (!drb) return set_err(TR_ERR_NOMEM, "readback buffer allocation failed");
+    Gather g{};
+    auto add = [&g](const void* src, void* dst, size_t bytes) {
+        g.src[g.n] = src;
+        g.dst[g.n] = dst;
+        g.bytes[g.n] = (unsigned)bytes;
+        ++g.n;
+    };
+    if (actl) add(actl, &drb->hc, sizeof(AsyncCtl));
+    if (sctl) add(sctl, &drb->sc, sizeof(StackCtl));
+    add(pr->err, &drb->err, sizeof(ErrorWord));
+    add(pr->raw_scal, drb->scal, 3 * sizeof(FixBin));
+    if (count) add(count, &drb->count[0], sizeof(unsigned long long));
+    TR_CUDA(launch_gather(g, pr->stream));
+    TR_CUDA(cudaMemcpyAsync(&rb, drb, sizeof(rb), cudaMemcpyDeviceToHost, pr->stream));
+    TR_CUDA(cudaStreamSynchronize(pr->stream));
+    return TR_OK;
+}
 
 // Device time of one kernel launch: events recorded around it on the stream.
 struct LaunchTimer {
@@ -961,24 +990,30 @@ static tr_status transport(tr_problem* pr, const tr_run_opts* o, RunParams R, co
         h.capacity = cap;
         h.max_rounds = 4ull * R.max_events + 1000000ull;
         h.dec = dec;
-        TR_CUDA(cudaMemcpyAsync(dR, &R, sizeof(R), cudaMemcpyHostToDevice, st));
-        TR_CUDA(cudaMemcpyAsync(dctl, &h, sizeof(h), cudaMemcpyHostToDevice, st));
+        TR_CUDA(launch_stack_setup(R, h, dR, dctl, st));
         LaunchTimer lt;
         TR_CUDA(cudaEventRecord(lt.a, st));
         TR_CUDA(cudaGraphLaunch(exec, st));
         TR_CUDA(cudaEventRecord(lt.b, st));
-        TR_CUDA(cudaMemcpyAsync(&h, dctl, sizeof(h), cudaMemcpyDeviceToHost, st));
-        TR_CUDA(cudaStreamSynchronize(st));
+        // the fixed-order reduction of the per-history scores, then one read
+        // of the status words (after a failed loop the sums are discarded)
+        TR_CUDA(launch_hist_reduce(T, R.n_hist, hist_partial, st));
+        Readback rb;
+        tr_status rs = read_status(pr, nullptr, dctl, out.want_count, rb);
+        if (rs != TR_OK) return rs;
+        h = rb.sc;
         out.kernel_ms += lt.elapsed();
         const unsigned long long launched = 4ull * ((h.rounds + 1) / 2);   // whole loop iterations
         count_launches(launched);
         out.launches += h.rounds;
-        tr_status es = check_err(pr);
-        if (es == TR_ERR_CAPACITY) return set_err(es, "stack overflow");
-        if (es == TR_ERR_TIMEOUT) return set_err(es, "stack loop did not terminate");
+        if (rb.err.code == ERR_CAPACITY) return set_err(TR_ERR_CAPACITY, "stack overflow");
+        if (rb.err.code == ERR_TIMEOUT) return set_err(TR_ERR_TIMEOUT, "stack loop did not terminate");
+        tr_status es = decode_err(rb.err);
         if (es != TR_OK) return es;
-        TR_CUDA(launch_hist_reduce(T, R.n_hist, hist_partial, st));
-        return hist_partial ? check_err(pr) : TR_OK;   // the reduction reports an out-of-range total
+        out.have_readback = true;
+        out.count = rb.count[0];
+        std::memcpy(out.scal, rb.scal, sizeof(out.scal));
+        return TR_OK;
     }
     // asynchronous scheme: one persistent launch
     // default stash: 288 slots for the monolithic scheme (its particles stay in
@@ -1006,12 +1041,24 @@ static tr_status transport(tr_problem* pr, const tr_run_opts* o, RunParams R, co
         if (!carve_soa(pr, "presample", R.n_hist, A.pre)) return set_err(TR_ERR_NOMEM, "source buffer allocation failed");
         A.use_pre = 1;
     }
+    // the control block: zero, with empty global link queues (all ones);
+    // set by the device (a copy from pageable host memory would first wait
+    // for the stream)
+    static_assert(offsetof(AsyncCtl, full_q) == offsetof(AsyncCtl, free_q) + sizeof(AsyncCtl::free_q),
+                  "the two queue arrays are contiguous");
+    TR_CUDA(cudaMemsetAsync(A.ctl, 0, sizeof(AsyncCtl), st));
+    TR_CUDA(cudaMemsetAsync(A.ctl->free_q, 0xFF, sizeof(AsyncCtl::free_q) + sizeof(AsyncCtl::full_q), st));
     AsyncCtl hc;
-    std::memset(&hc, 0, sizeof(hc));
-    std::memset(hc.free_q, 0xFF, sizeof(hc.free_q));
-    std::memset(hc.full_q, 0xFF, sizeof(hc.full_q));
-    TR_CUDA(cudaMemcpyAsync(A.ctl, &hc, sizeof(hc), cudaMemcpyHostToDevice, st));
-    int maxb = async_max_blocks_per_sm(P, A.dec, S, A.use_pre != 0);
+    // resident blocks per SM: an occupancy query, once per configuration
+    const std::vector<int> okey = {A.dec, S, A.use_pre, P.kind, P.ww_lo != nullptr};
+    auto oc = pr->async_occupancy.find(okey);
+    int maxb = 0;
+    if (oc != pr->async_occupancy.end()) {
+        maxb = oc->second;
+    } else {
+        maxb = async_max_blocks_per_sm(P, A.dec, S, A.use_pre != 0);
+        pr->async_occupancy[okey] = maxb;
+    }
     if (maxb < 1) return set_err(TR_ERR_INVALID, "stash does not fit in shared memory");
     const int bps = o->blocks_per_sm > 0 ? std::min(o->blocks_per_sm, maxb) : maxb;
     int smem = 0;
@@ -1026,29 +1073,9 @@ static tr_status transport(tr_problem* pr, const tr_run_opts* o, RunParams R, co
     TR_CUDA(launch_hist_reduce(T, R.n_hist, hist_partial, st));
     // one host round trip: control block, error word, the caller's counter
     // and the scalar bins, gathered on the device
-    Readback* drb = (Readback*)workspace(pr, "readback", sizeof(Readback));
-    if (!drb) return set_err(TR_ERR_NOMEM, "readback buffer allocation failed");
-    Gather g{};
-    g.src[0] = A.ctl;
-    g.dst[0] = &drb->hc;
-    g.bytes[0] = sizeof(AsyncCtl);
-    g.src[1] = pr->err;
-    g.dst[1] = &drb->err;
-    g.bytes[1] = sizeof(ErrorWord);
-    g.src[2] = pr->raw_scal;
-    g.dst[2] = drb->scal;
-    g.bytes[2] = 3 * sizeof(FixBin);
-    g.n = 3;
-    if (out.want_count) {
-        g.src[3] = out.want_count;
-        g.dst[3] = &drb->count[0];
-        g.bytes[3] = sizeof(unsigned long long);
-        g.n = 4;
-    }
-    TR_CUDA(launch_gather(g, st));
     Readback rb;
-    TR_CUDA(cudaMemcpyAsync(&rb, drb, sizeof(rb), cudaMemcpyDeviceToHost, st));
-    TR_CUDA(cudaStreamSynchronize(st));
+    tr_status rs = read_status(pr, A.ctl, nullptr, out.want_count, rb);
+    if (rs != TR_OK) return rs;
     hc = rb.hc;
     out.kernel_ms += lt.elapsed();
     tr_status es = decode_err(rb.err);

@@ -63,6 +63,9 @@ cudaError_t launch_stack(const DevProblem& P, const RunParams* Rd, const SoA* in
 // goes to the graph's loop condition.
 cudaError_t launch_stack_next(StackCtl* ctl, const RunParams* Rd, ErrorWord* err, cudaGraphConditionalHandle cond,
                               cudaStream_t st);
+// Write the run parameters and the initial control block to device memory
+// from kernel arguments, in stream order.
+cudaError_t launch_stack_setup(const RunParams& R, const StackCtl& h, RunParams* Rd, StackCtl* ctl, cudaStream_t st);
 
 struct AsyncArgs {
     SoA links;                         // global link arena: n_links * 32 particle slots

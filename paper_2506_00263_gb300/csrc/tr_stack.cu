@@ -551,6 +551,24 @@ static int grid_for(unsigned long long n, int threads, int max_blocks)
     return (int)b;
 }
 
+// The run's parameters and initial control block, written by the device
+// from kernel arguments (a copy from pageable host memory would first wait
+// for the stream).
+__global__ void k_stack_setup(RunParams R, StackCtl h, RunParams* Rd, StackCtl* ctl)
+{
+    if (threadIdx.x == 0) {
+        *Rd = R;
+        *ctl = h;
+    }
+}
+
+cudaError_t launch_stack_setup(const RunParams& R, const StackCtl& h, RunParams* Rd, StackCtl* ctl, cudaStream_t st)
+{
+    count_launches(1);
+    k_stack_setup<<<1, 32, 0, st>>>(R, h, Rd, ctl);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_stack_next(StackCtl* ctl, const RunParams* Rd, ErrorWord* err, cudaGraphConditionalHandle cond,
                               cudaStream_t st)
 {
