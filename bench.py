@@ -304,6 +304,9 @@ def run_ours(args):
         e2e = {"value": ev_e / t_e, "unit": "events/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
 
     # ---- the other reported quantities (not part of the timed value) ----
+    # (the benchmark problem is released first: with it alive, the CE pin
+    # cell's transport measured 16 % slower)
+    prob.close()
     extras = None
     if rank == 0 and not args.no_extras:
         ce = measure_ce_line(torch, tb, inputs)
@@ -340,7 +343,6 @@ def run_ours(args):
         "extras": extras,
     }
     print(json.dumps(line), flush=True)
-    prob.close()
     if ws > 1:
         torch.distributed.destroy_process_group()
     return 0
@@ -675,7 +677,6 @@ def run_ce_workload(args):
                           {"scheme": args.scheme, "energy_bins": args.ebins,
                            "histories": args.n_hist, "remap_every": opts.remap_every})
         print(json.dumps(line), flush=True)
-    prob.close()
     if ws > 1:
         torch.distributed.destroy_process_group()
     return 0
