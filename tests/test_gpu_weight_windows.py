@@ -103,6 +103,25 @@ def test_continuous_energy_with_windows():
         _compare(_gpu(spec, n, scheme, remap, seed=2, stash_slots=1024), o)
 
 
+def test_windows_with_forced_spills_through_the_global_links():
+    """Split copies and window-weighted particles that travel through the
+    global spill links (their records leave and re-enter the block stashes):
+    the same histories and tallies as the oracle, multigroup and continuous
+    energy (a continuous-energy record carries no group index)."""
+    base = inputs.ce_pin_cell(n_points=20000, n_res=60, n_ebins=100)
+    base = base.replace(mesh_lo=(-0.63, -0.63, -50.0), mesh_hi=(0.63, 0.63, 50.0), mesh_n=(4, 4, 1))
+    ww = np.array([0.05, 0.4, 0.05, 0.4, 0.4, 0.05, 0.4, 0.05, 0.05, 0.4, 0.05, 0.4, 0.4, 0.05, 0.4, 0.05])
+    ce = base.replace(ww_lower=ww.reshape(-1, 1), ww_upper=4.0, ww_survival=2.0, ww_max_split=4)
+    for spec, n, seed in ((_checkerboard_box(), 10_007, 3), (ce, 3_001, 2)):
+        o = oracle.run_fixed_source(spec, n, seed=seed)
+        assert o["status"] == 0
+        for remap in (64, 512):
+            g = _gpu(spec, n, tb.SCHEME_ASYNC, remap, seed=seed, stash_slots=512, spill_threshold=-32,
+                     queue_capacity=8192 * 32)
+            assert g["stats"]["spills"] > 0, g["stats"]
+            _compare(g, o)
+
+
 def test_inactive_windows_equal_the_analog_run():
     spec = _checkerboard_box()
     analog = inputs.box_mg("ww_box", (0.0, 0.0, 0.0), (10.0, 10.0, 10.0), sigma_t=[1.0], sigma_s=[[0.5]],
