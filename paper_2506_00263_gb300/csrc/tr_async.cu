@@ -182,7 +182,10 @@ __device__ __forceinline__ void fail(ErrorWord* err, int code, int where)
     if (atomicCAS(&err->code, 0, code) == 0) err->where = where;
 }
 
-// Shared-memory lock, taken by lane 0 for the whole warp.  Bounded.
+// Shared-memory lock, taken by lane 0 for the whole warp.  Bounded: the
+// spin count and the wall clock are checked every 64 failed tries (a clock
+// read per try slowed the contended case); the first tries spin without a
+// pause.
 __device__ __forceinline__ bool lock_stash(const Stash& s, const RunParams& R, ErrorWord* err)
 {
     bool ok = true;
@@ -191,12 +194,13 @@ __device__ __forceinline__ bool lock_stash(const Stash& s, const RunParams& R, E
         uint64_t t0 = 0;
         while (atomicCAS(s.cnt + CNT_LOCK, 0, 1) != 0) {
             if (spins == 0) t0 = now_ns();
-            if (++spins > R.max_spin || now_ns() - t0 > R.max_wait_ns) {
+            ++spins;
+            if ((spins & 63ull) == 0ull && (spins > R.max_spin || now_ns() - t0 > R.max_wait_ns)) {
                 fail(err, ERR_TIMEOUT, 1);
                 ok = false;
                 break;
             }
-            __nanosleep(32);
+            if (spins > 4ull) __nanosleep(32);
         }
         __threadfence_block();
     }
@@ -485,9 +489,9 @@ __global__ void __launch_bounds__(256, TR_ASYNC_MIN_BLOCKS) k_async(DevProblem P
         g_hungry = __shfl_sync(FULLM, g_hungry, 0);
         // ---------------- take work (under the stash lock) ----------------
         if (!lock_stash(st, R, err)) break;
-        int cnts[N_QUEUES];
+        int cnts[N_QUEUES] = {};
 #pragma unroll
-        for (int q = 0; q < N_QUEUES; ++q) cnts[q] = *(volatile int*)(st.cnt + q);
+        for (int q = 0; q < nq; ++q) cnts[q] = *(volatile int*)(st.cnt + q);
         const int nfree = *(volatile int*)(st.cnt + CNT_FREE);
         const int n_run = *(volatile int*)(st.cnt + CNT_RUN);
         int q = 0;
@@ -608,7 +612,7 @@ __global__ void __launch_bounds__(256, TR_ASYNC_MIN_BLOCKS) k_async(DevProblem P
                 if (lane == 0) fail(err, ERR_TIMEOUT, 4);
                 break;
             }
-            __nanosleep(200);
+            __nanosleep(50);
             continue;
         }
         if (idle) {
@@ -972,6 +976,7 @@ __global__ void __launch_bounds__(256, TR_ASYNC_MIN_BLOCKS) k_async(DevProblem P
         const bool has = slot >= 0;
         if (MERGE && lane == 0) st.cnt[CNT_RUN] -= 1;
         for (int qq = 0; qq <= N_QUEUES; ++qq) {
+            if (qq < N_QUEUES && qq >= nq) continue;   // queues this decomposition never fills
             const bool mine = has && (qq == N_QUEUES ? next == Q_DEAD : next == qq);
             const unsigned mask = __ballot_sync(FULLM, mine);
             if (!mask) continue;
