@@ -471,11 +471,11 @@ __global__ void __launch_bounds__(256, TR_ASYNC_MIN_BLOCKS) k_async(DevProblem P
     int tail_wait = 0;      // polls passed over a partial queue while other warps run
     const int qstart = (int)(blockIdx.x * 7 + (threadIdx.x >> 5)) & (N_GQ - 1);
 
-    for (;;) {
-        // warp-uniform reads of the global state (lane 0, broadcast)
-        int g_err = 0;
-        unsigned long long g_src = 0, g_live = 0;
-        unsigned g_hungry = 0;
+    // warp-uniform reads of the global state (lane 0, broadcast)
+    int g_err = 0;
+    unsigned long long g_src = 0, g_live = 0;
+    unsigned g_hungry = 0;
+    auto read_global = [&]() {
         if (lane == 0) {
             g_err = *(volatile int*)&err->code;
             g_src = *(volatile unsigned long long*)&ctl->src_cursor;
@@ -483,12 +483,23 @@ __global__ void __launch_bounds__(256, TR_ASYNC_MIN_BLOCKS) k_async(DevProblem P
             g_hungry = *(volatile unsigned*)&ctl->hungry;
         }
         g_err = __shfl_sync(FULLM, g_err, 0);
-        if (g_err != 0) break;
         g_src = __shfl_sync(FULLM, g_src, 0);
         g_live = __shfl_sync(FULLM, g_live, 0);
         g_hungry = __shfl_sync(FULLM, g_hungry, 0);
+    };
+    // a deposit keeps the stash lock for the take that follows it (one lock
+    // round per event instead of two); the global state is then read before
+    // the deposit
+    bool held = false;
+    for (;;) {
+        if (!held) read_global();
+        if (g_err != 0) {
+            if (held) unlock_stash(st);
+            break;
+        }
         // ---------------- take work (under the stash lock) ----------------
-        if (!lock_stash(st, R, err)) break;
+        if (!held && !lock_stash(st, R, err)) break;
+        held = false;
         int cnts[N_QUEUES] = {};
 #pragma unroll
         for (int q = 0; q < nq; ++q) cnts[q] = *(volatile int*)(st.cnt + q);
@@ -972,6 +983,7 @@ __global__ void __launch_bounds__(256, TR_ASYNC_MIN_BLOCKS) k_async(DevProblem P
         if constexpr (WW) {
             if (!deposit_copies<XS>(st, R, p, live, ctl, err, tm)) break;   // split copies first
         }
+        read_global();
         if (!lock_stash(st, R, err)) break;
         const bool has = slot >= 0;
         if (MERGE && lane == 0) st.cnt[CNT_RUN] -= 1;
@@ -991,7 +1003,10 @@ __global__ void __launch_bounds__(256, TR_ASYNC_MIN_BLOCKS) k_async(DevProblem P
             if (lane == 0) *cp = c + __popc(mask);
             __syncwarp();
         }
-        unlock_stash(st);
+        // (not with forced spills, a diagnostic setting: they need queues
+        // that build up between other warps' deposits and takes)
+        held = R.spill_threshold >= 0;
+        if (!held) unlock_stash(st);
     }
     if (idle && lane == 0) atomicSub(&ctl->hungry, 1u);
     if (BATCHED) flush_lane(acc, A.tallies[acc_prob]);
