@@ -664,7 +664,7 @@ __device__ __forceinline__ void xs_ce(const DevProblem& P, int m, double E, XS& 
     }
     if (X.keep) X.keep->n = kept <= CE_KEEP_NUC ? kept : -1;
     X.st = cum;
-    X.inv_st = tr_rcp(cum);
+    X.inv_st = sf_rcp(cum);   // on the integer pipe: the FP64 pipe is the CE kernels' bound (the same bits as 1.0 / cum)
     X.sa = sa;
     X.nsf = 0.0;
 }
