@@ -462,21 +462,24 @@ __device__ __forceinline__ void azimuth(const Stream& S, uint32_t n, double& cph
 {
     double a, b, a2, b2, s;
     disk_point(S, n, a, b, a2, b2, s, sm);
-    const double inv_s = tr_rcp(s);
+    const double inv_s = sf_rcp(s);   // continuous energy only: on the integer pipe (the same bits)
     cphi = (a2 - b2) * inv_s;
     sphi = (2.0 * (a * b)) * inv_s;
 }
 
+// SOFT: the reciprocals on the integer pipe (sf_rcp, the same bits), for
+// the continuous-energy scatter, whose kernels are the most FP64-bound.
+template <bool SOFT = false>
 __device__ __forceinline__ void set_reciprocals(Particle& p)
 {
     TR_LANES(20);
     // (bits << 1) != 0 is x != +-0
     // tr_rcp is the correctly rounded reciprocal: the same value as 1.0 / x
-    p.iu = (dbits(p.u) << 1) ? tr_rcp(p.u) : 0.0;
-    p.iv = (dbits(p.v) << 1) ? tr_rcp(p.v) : 0.0;
-    p.iw = (dbits(p.w) << 1) ? tr_rcp(p.w) : 0.0;
+    p.iu = (dbits(p.u) << 1) ? (SOFT ? sf_rcp(p.u) : tr_rcp(p.u)) : 0.0;
+    p.iv = (dbits(p.v) << 1) ? (SOFT ? sf_rcp(p.v) : tr_rcp(p.v)) : 0.0;
+    p.iw = (dbits(p.w) << 1) ? (SOFT ? sf_rcp(p.w) : tr_rcp(p.w)) : 0.0;
     const double a = __fma_rn(p.u, p.u, p.v * p.v);
-    p.ia = gt0(a) ? tr_rcp(a) : 0.0;
+    p.ia = gt0(a) ? (SOFT ? sf_rcp(a) : tr_rcp(a)) : 0.0;
 }
 
 // Isotropic direction (Marsaglia, Ann. Math. Stat. 43 (1972) 645): with the
@@ -497,7 +500,7 @@ __device__ __forceinline__ void rotate(Particle& p, double mu, double cphi, doub
 {
     double t = __fma_rn(-mu, mu, 1.0);
     if (lt0(t)) t = 0.0;
-    const double st = tr_sqrt(t);
+    const double st = sf_sqrt(t);   // the rotation (continuous energy only): square roots on the integer pipe
     const double u = p.u, v = p.v, w = p.w;
     // |w| > 0.9999999999 and w > 0 on the bit patterns (integer instructions)
     if ((dbits(w) & 0x7FFFFFFFFFFFFFFFll) > dbits(0.9999999999)) {
@@ -505,13 +508,13 @@ __device__ __forceinline__ void rotate(Particle& p, double mu, double cphi, doub
         p.v = st * sphi;
         p.w = gt0(w) ? mu : -mu;
     } else {
-        const double sq = tr_sqrt(__fma_rn(-w, w, 1.0));
+        const double sq = sf_sqrt(__fma_rn(-w, w, 1.0));
         const double a1 = st / sq;
         p.u = mu * u + a1 * ((u * w) * cphi - v * sphi);
         p.v = mu * v + a1 * ((v * w) * cphi + u * sphi);
         p.w = mu * w - (st * sq) * cphi;
     }
-    set_reciprocals(p);
+    set_reciprocals<true>(p);
 }
 
 // ---------------------------------------------------------------------------

@@ -595,7 +595,7 @@ __device__ __forceinline__ int collide_event(const DevProblem& P, const RunParam
     const double mu_cm = __fma_rn(2.0, S.first(p.n, BLK_ANGLE), -1.0);   // 2 xi exact: same as 2 xi - 1
     const double q = (A * A + (2.0 * A) * mu_cm) + 1.0;
     const double E1 = (p.E * q) * __ldg(P.inv_ap1sq + sel_n);
-    const double mu = (1.0 + A * mu_cm) / tr_sqrt(q);
+    const double mu = (1.0 + A * mu_cm) / sf_sqrt(q);   // integer-pipe square root (the same bits)
     double cphi, sphi;
     azimuth(S, p.n, cphi, sphi, sm);
     rotate(p, mu, cphi, sphi);

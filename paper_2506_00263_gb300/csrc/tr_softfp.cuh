@@ -10,10 +10,10 @@
 // for every input (zero, subnormal, infinite and NaN inputs, and reciprocals
 // that leave the normal range, take the hardware operation), so the
 // arithmetic contract is unchanged.  Alone they run at 2.1x (reciprocal) and
-// 3.0x (square root) the IEEE rate.  The continuous-energy lookup takes its
-// 1/sigma_t with sf_rcp (measured 2 % faster); elsewhere the transport
-// kernels select them with TR_SOFTFP (off by default: there they measured
-// slower, tr_device.cuh).
+// 3.0x (square root) the IEEE rate.  The continuous-energy kernels use them
+// for the lookup's 1/sigma_t and the scatter's reciprocals and square roots
+// (measured 3.5 % faster there); the multigroup kernels select them with
+// TR_SOFTFP (off by default: there they measured slower, tr_device.cuh).
 //
 // Reciprocal of x = +-m 2^(e - 1075), m in [2^52, 2^53), e in [1, 2044]:
 // 1/x = 2^(1022 - e) (2^53 / m), whose mantissa is M = RN(2^105 / m).  With
