@@ -390,7 +390,9 @@ __global__ void __launch_bounds__(256) k_presample(DevProblem P, RunParams R, Ba
     const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
     for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < R.n_hist; i += stride) {
         Particle p;
-        const bool ok = source_particle<CE>(P, R, (unsigned)i, p, use_src ? &src : nullptr, i);
+        // (directions with the integer-pipe square root and reciprocals: the
+        // same bits, and this kernel is FP64-bound)
+        const bool ok = source_particle<CE, true>(P, R, (unsigned)i, p, use_src ? &src : nullptr, i);
         out.x[i] = p.x; out.y[i] = p.y; out.z[i] = p.z;
         out.u[i] = p.u; out.v[i] = p.v; out.w[i] = p.w;
         out.iu[i] = p.iu; out.iv[i] = p.iv; out.iw[i] = p.iw; out.ia[i] = p.ia;

@@ -485,15 +485,18 @@ __device__ __forceinline__ void set_reciprocals(Particle& p)
 // Isotropic direction (Marsaglia, Ann. Math. Stat. 43 (1972) 645): with the
 // disk point (a, b), s = a^2 + b^2, (1 - 2s, 2a sqrt(1 - s), 2b sqrt(1 - s))
 // is uniform on the unit sphere; no division and one square root.
+// SOFT: the square root and the reciprocals on the integer pipe (the same
+// bits; the source pre-sampling kernel, where it measured faster).
+template <bool SOFT = false>
 __device__ __forceinline__ void iso_dir(const Stream& S, uint32_t n, Particle& p, unsigned sm = 0u)
 {
     double a, b, a2, b2, s;
     disk_point(S, n, a, b, a2, b2, s, sm);
-    const double t = 2.0 * tr_sqrt(1.0 - s);
+    const double t = 2.0 * (SOFT ? sf_sqrt(1.0 - s) : tr_sqrt(1.0 - s));
     p.u = __fma_rn(-2.0, s, 1.0);   // 2 s is exact: the same value as 1.0 - 2.0 * s
     p.v = a * t;
     p.w = b * t;
-    set_reciprocals(p);
+    set_reciprocals<SOFT>(p);
 }
 
 __device__ __forceinline__ void rotate(Particle& p, double mu, double cphi, double sphi)

@@ -222,7 +222,7 @@ __device__ __forceinline__ void energy_tally(const DevProblem& P, const Tallies&
 // ---------------------------------------------------------------------------
 // Source event (make_work): event count 0 draws; leaves n = 1.
 // ---------------------------------------------------------------------------
-template <bool CE>
+template <bool CE, bool SOFT = false>
 __device__ __forceinline__ bool source_particle(const DevProblem& P, const RunParams& R, unsigned id, Particle& p,
                                                 const Bank* site, unsigned long long site_idx)
 {
@@ -242,12 +242,12 @@ __device__ __forceinline__ bool source_particle(const DevProblem& P, const RunPa
     p.wt = 1.0;
     p.sid = p.nsplit = 0u;
     if (site != nullptr || P.src_kind != 0 || P.src_iso) {
-        iso_dir(S, 0u, p);
+        iso_dir<SOFT>(S, 0u, p);
     } else {
         p.u = P.src_dir[0];
         p.v = P.src_dir[1];
         p.w = P.src_dir[2];
-        set_reciprocals(p);
+        set_reciprocals<SOFT>(p);
     }
     if (site != nullptr) {
         p.x = site->x[site_idx];
