@@ -444,8 +444,10 @@ tr_status tr_selftest_issue_rate(int32_t op, int32_t lanes, double *per_second);
  * computed on the integer and FP32 pipes (paper has no counterpart: a GB300
  * economy of the FP64 pipe), beside the IEEE hardware sequences, for n host
  * doubles x[] into out[]: op 0: sf_rcp(x), 1: 1.0 / x, 2: sf_sqrt(x),
- * 3: sqrt(x).  Ops 0 and 1 (2 and 3) must agree bit for bit on every input.
- * Allocates device scratch; synchronous.  n <= 2^26. */
+ * 3: sqrt(x); op 4: sf_div(x[2i], x[2i+1]), 5: x[2i] / x[2i+1] into
+ * out[i] for i < n/2 (n even).  Ops 0 and 1 (2 and 3, 4 and 5) must agree
+ * bit for bit on every input.  Allocates device scratch; synchronous.
+ * n <= 2^26. */
 tr_status tr_selftest_softfp(int32_t op, const double *x, size_t n, double *out);
 
 /* Diagnostics: number of kernels this library has launched in this process

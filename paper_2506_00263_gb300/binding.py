@@ -157,9 +157,10 @@ def lib():
 
 
 def softfp(op: int, x) -> np.ndarray:
-    """tr_selftest_softfp: 0 sf_rcp, 1 1/x, 2 sf_sqrt, 3 sqrt, elementwise on the device."""
+    """tr_selftest_softfp: 0 sf_rcp, 1 1/x, 2 sf_sqrt, 3 sqrt, elementwise on
+    the device; 4 sf_div, 5 division, of the pairs (x[2i], x[2i+1])."""
     x = np.ascontiguousarray(x, np.float64)
-    out = np.empty_like(x)
+    out = np.empty(x.size // 2 if op >= 4 else x.size)
     _check(lib().tr_selftest_softfp(op, x.ctypes.data_as(_dp), x.size, out.ctypes.data_as(_dp)))
     return out
 

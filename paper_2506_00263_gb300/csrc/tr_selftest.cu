@@ -3,10 +3,9 @@
 // call of CUDA's own curand Philox4x32-10 on the same counters and keys; the
 // table-driven logarithm as the transport kernels evaluate it; and the
 // exponential ziggurat table the transport kernels read; the integer-pipe
-// reciprocal and square root beside the IEEE hardware sequences; and an
-// issue-rate probe of the arithmetic pipes for the roofline's ALU
-// denominator.  The
-// transport itself never calls these.
+// reciprocal, square root and division beside the IEEE hardware sequences;
+// and an issue-rate probe of the arithmetic pipes for the roofline's ALU
+// denominator.  The transport itself never calls these.
 #include <curand_kernel.h>
 
 #include <cstring>
@@ -42,8 +41,77 @@ __global__ void k_log(const double* __restrict__ tab, const double* __restrict__
         out[i] = tr_log(tab, x[i]);
 }
 
+// y1 ~ 2^115 / m for a mantissa m in [2^52, 2^53), within a few units: the
+// FP32 seed and second-order fixed-point Newton step of sf_rcp
+// (tr_softfp.cuh), which is exact (2^63) for m = 2^52.
+__device__ __forceinline__ unsigned long long recip115(unsigned long long m)
+{
+    const float rf = __frcp_rn(__uint2float_rn((unsigned)(m >> 21)));
+    const unsigned long long y0 = __float2uint_rz(rf * 0x1p61f);          // ~ 2^82 / m, <= 2^30
+    const long long d = (long long)(0ull - m * y0);                        // 2^82 - m y0
+    const long long c1 = __mul64hi(d, (long long)(y0 << 15));             // y0 2^33 t
+    const long long c2 = __mul64hi(c1, d) >> 18;                           // y0 2^33 t^2
+    return (y0 << 33) + (unsigned long long)(c1 + c2);
+}
+
+// Quotient a / b on the integer and FP32 pipes, correctly rounded (ties to
+// even), for finite nonzero normal a and b with a normal result; anything
+// else takes the hardware division.  Measured in the continuous-energy
+// scatter's two divisions, it returned the same bits and ran 0.3 % slower
+// than the IEEE division there, so the transport kernels do not use it; it
+// stays here with its bitwise check.  With the mantissas ma, mb and k = 54 (ma >= mb) or 55, the
+// quotient's 55 leading bits are Q = floor(ma 2^k / mb) in [2^54, 2^55): an
+// estimate from the reciprocal 2^115 / mb is corrected to the exact Q by the
+// remainder ma 2^k - Q mb (a signed 64-bit word), and Q's two low bits with
+// the remainder's sign decide the rounding of the 53-bit mantissa Q / 4.
+__device__ __forceinline__ double sf_div(double a, double b)
+{
+    const unsigned long long ba = (unsigned long long)__double_as_longlong(a);
+    const unsigned long long bb = (unsigned long long)__double_as_longlong(b);
+    const unsigned ea = (unsigned)(ba >> 52) & 0x7FFu, eb = (unsigned)(bb >> 52) & 0x7FFu;
+    if (ea - 1u > 2045u || eb - 1u > 2045u) return __ddiv_rn(a, b);
+    const unsigned long long ma = (ba & 0x000FFFFFFFFFFFFFull) | 0x0010000000000000ull;
+    const unsigned long long mb = (bb & 0x000FFFFFFFFFFFFFull) | 0x0010000000000000ull;
+    const unsigned lt = ma < mb ? 1u : 0u;
+    const int E = (int)ea - (int)eb + 1023 - (int)lt;
+    if (E < 1 || E > 2045) return __ddiv_rn(a, b);   // (2046 is reached only by rounding: kept out)
+    const unsigned long long hi = __umul64hi(ma << 11, recip115(mb));   // (exactly 2^63 for mb = 2^52)
+    unsigned long long q = hi >> (8u - lt);
+    long long r = (long long)((ma << (54u + lt)) - q * mb);   // ma 2^k - q mb, small
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+        if (r < 0) {
+            q -= 1ull;
+            r += (long long)mb;
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+        if (r >= (long long)mb) {
+            q += 1ull;
+            r -= (long long)mb;
+        }
+    }
+    unsigned long long mant = q >> 2;
+    const unsigned long long guard = (q >> 1) & 1ull;
+    const bool sticky = (q & 1ull) || r != 0;
+    mant += (guard && (sticky || (mant & 1ull))) ? 1ull : 0ull;
+    unsigned long long eo = (unsigned long long)E;
+    if (mant == 0x0020000000000000ull) {   // rounded up to 2^53
+        mant = 0x0010000000000000ull;
+        eo += 1ull;
+    }
+    return __longlong_as_double((long long)(((ba ^ bb) & 0x8000000000000000ull) | (eo << 52) |
+                                            (mant - 0x0010000000000000ull)));
+}
+
 __global__ void k_softfp(int op, const double* __restrict__ x, size_t n, double* out)
 {
+    if (op >= 4) {   // quotients of the pairs (x[2i], x[2i + 1])
+        for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n / 2; i += (size_t)gridDim.x * blockDim.x)
+            out[i] = op == 4 ? sf_div(x[2 * i], x[2 * i + 1]) : __ddiv_rn(x[2 * i], x[2 * i + 1]);
+        return;
+    }
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
         const double v = x[i];
         out[i] = op == 0 ? sf_rcp(v) : op == 1 ? __drcp_rn(v) : op == 2 ? sf_sqrt(v) : __dsqrt_rn(v);
@@ -232,7 +300,8 @@ extern "C" tr_status tr_selftest_issue_rate(int32_t op, int32_t lanes, double* p
 
 extern "C" tr_status tr_selftest_softfp(int32_t op, const double* x, size_t n, double* out)
 {
-    if (!x || !out || op < 0 || op > 3) return fail(TR_ERR_INVALID, "op must be 0..3 and x, out non-NULL");
+    if (!x || !out || op < 0 || op > 5) return fail(TR_ERR_INVALID, "op must be 0..5 and x, out non-NULL");
+    if (op >= 4 && (n & 1)) return fail(TR_ERR_INVALID, "ops 4 and 5 take pairs: n must be even");
     if (n == 0) return TR_OK;
     if (n > (1u << 26)) return fail(TR_ERR_INVALID, "n must be at most 2^26");
     Scratch s;
@@ -243,6 +312,6 @@ extern "C" tr_status tr_selftest_softfp(int32_t op, const double* x, size_t n, d
     count_launches(1);
     k_softfp<<<(unsigned)((n + 255) / 256 < 4096 ? (n + 255) / 256 : 4096), 256>>>(op, d_x, n, d_out);
     ST_CUDA(cudaGetLastError());
-    ST_CUDA(cudaMemcpy(out, d_out, n * 8, cudaMemcpyDeviceToHost));
+    ST_CUDA(cudaMemcpy(out, d_out, (op >= 4 ? n / 2 : n) * 8, cudaMemcpyDeviceToHost));
     return TR_OK;
 }

@@ -135,3 +135,53 @@ def test_integer_pipe_reciprocal_and_sqrt_are_correctly_rounded():
         assert not bad.any(), (soft, int(bad.sum()), x[bad][:4], a[bad][:4], b[bad][:4])
         badh = (a.view(np.uint64) != host.view(np.uint64)) & ~(np.isnan(a) & np.isnan(host))
         assert not badh.any(), (soft, int(badh.sum()), x[badh][:4], a[badh][:4], host[badh][:4])
+
+
+def _division_pairs():
+    """Pairs (a, b): random bit patterns, values of the transport's range,
+    equal and adjacent mantissas, quotients near the overflow and underflow
+    thresholds, exact quotients and near-ties (a = b q +- a few ulps for a
+    q with a half-ulp tail), and the edge patterns of the reciprocal test."""
+    rng = np.random.default_rng(29)
+    n = 1_000_000
+    rb = lambda k: rng.integers(0, 2 ** 64, size=k, dtype=np.uint64).view(np.float64)
+    pairs = [(rb(n), rb(n)),
+             (rng.uniform(-1.0, 1.0, n), rng.uniform(0.5, 3.0, n)),
+             (rng.uniform(1.0, 2.0, n), rng.uniform(1.0, 2.0, n))]
+    m = rng.uniform(1.0, 2.0, 200_000)
+    for k in (-2, -1, 0, 1, 2):
+        pairs.append((m, m + k * np.spacing(m)))
+    # exact and near-tie quotients: q has 54 significant bits (a half-ulp tail), b has few bits
+    q = (rng.integers(2 ** 53, 2 ** 54, 200_000, dtype=np.int64) | 1).astype(np.float64)   # rounds when cast
+    b = rng.integers(1, 64, 200_000).astype(np.float64) * 2.0 ** -3
+    a = q * b
+    for k in (-2, -1, 0, 1, 2):
+        pairs.append((a + k * np.spacing(a), b))
+    # quotients around the top and bottom of the normal range
+    e = rng.integers(-6, 7, 100_000)
+    pairs.append((np.ldexp(rng.uniform(1.0, 2.0, 100_000), 1023 + np.minimum(e, 0)),
+                  np.ldexp(rng.uniform(1.0, 2.0, 100_000), np.minimum(e, 0) - 1)))
+    pairs.append((np.ldexp(rng.uniform(1.0, 2.0, 100_000), -1022 + np.maximum(e, 0)),
+                  np.ldexp(rng.uniform(1.0, 2.0, 100_000), np.maximum(e, 0) + 1)))
+    edge = _softfp_inputs()[-(12 * 8 * 2):]
+    pairs.append((np.repeat(edge, edge.size), np.tile(edge, edge.size)))
+    a = np.concatenate([p[0] for p in pairs])
+    b = np.concatenate([p[1] for p in pairs])
+    return a, b
+
+
+def test_integer_pipe_division_is_correctly_rounded():
+    """sf_div (the quotient on the integer and FP32 pipes) returns the bits of
+    the IEEE division, and of numpy's, on about 5 million pairs."""
+    a, b = _division_pairs()
+    x = np.empty(2 * a.size)
+    x[0::2], x[1::2] = a, b
+    with np.errstate(all="ignore"):
+        host = a / b
+    s = tb.softfp(4, x)
+    h = tb.softfp(5, x)
+    for other, name in ((h, "device"), (host, "numpy")):
+        bad = (s.view(np.uint64) != other.view(np.uint64)) & ~(np.isnan(s) & np.isnan(other))
+        assert not bad.any(), (name, int(bad.sum()), a[bad][:4], b[bad][:4], s[bad][:4], other[bad][:4])
+    with pytest.raises(tb.TransportError):
+        tb.softfp(4, np.ones(3))
