@@ -448,7 +448,15 @@ __global__ void __launch_bounds__(256, TR_ASYNC_MIN_BLOCKS) k_async(DevProblem P
     constexpr int nq = dec_queues(DEC);
     const bool tm = BATCHED || P.timed != 0;   // particle times travel through the stash
     constexpr bool MERGE = !SPLIT && !BATCHED;   // batch-tail consolidation of the monolithic loop
+    constexpr bool WALK = !SPLIT && !BATCHED;    // mesh walks deferred to the warp's queue (WalkQ)
     AsyncCtl* ctl = A.ctl;
+    WalkQ* wq = nullptr;
+    if (WALK && P.has_mesh && P.mesh_walk) {
+        if (A.walkq) wq = A.walkq + (size_t)blockIdx.x * 8 + (threadIdx.x >> 5);
+        else if (P.walk_smem_off)
+            wq = reinterpret_cast<WalkQ*>(smem + P.walk_smem_off + (threadIdx.x >> 5) * walkq_bytes());
+    }
+    if (wq && lane == 0) wq->n = 0;
 
     if (threadIdx.x == 0) {
         for (int q = 0; q <= CNT_RUN; ++q) st.cnt[q] = 0;
@@ -844,12 +852,27 @@ __global__ void __launch_bounds__(256, TR_ASYNC_MIN_BLOCKS) k_async(DevProblem P
                         }
                         const unsigned lm = __ballot_sync(em, live);
                         if (!lm) break;
+                        if constexpr (WALK) {
+                            // drain 32 deferred mesh walks once 32 are queued, before a
+                            // pass that may queue 32 more
+                            if (wq) {
+                                __syncwarp(em);
+                                int nq_w = *(volatile int*)&wq->n;
+                                nq_w = nq_w < WALKQ_CAP ? nq_w : WALKQ_CAP;
+                                if (nq_w >= 32) {
+                                    walk_run<WW>(PP, TT, wq, nq_w - 32, nq_w, em);
+                                    __syncwarp(em);
+                                    if (lane == leader) wq->n = nq_w - 32;
+                                    __syncwarp(em);
+                                }
+                            }
+                        }
                         TR_LANES(12);
                         if (!src_more) TR_LANES(25);
                         if (live) TR_LANES(13);
                         if (live && !src_more) TR_LANES(31);
                         if constexpr (FUSE) {
-                            if (live) live = mono_event<CE, WW>(PP, RR, p, TT, acc, A.bank, err, lm);
+                            if (live) live = mono_event<CE, WW, WALK>(PP, RR, p, TT, acc, A.bank, err, lm, wq);
                             continue;
                         }
                         if constexpr (CE) {
@@ -892,7 +915,7 @@ __global__ void __launch_bounds__(256, TR_ASYNC_MIN_BLOCKS) k_async(DevProblem P
                                 tr::XS X;
                                 X.keep = &ck;
                                 double xr;
-                                FwdSinkT<WW> sink{TT, acc};
+                                FwdSinkT<WW, WALK> sink{TT, acc, 1.0, wq};
                                 step_event<CE>(PP, RR, p, sink, X, xr);
                                 if (p.pend == PEND_COLLIDE) {
                                     pend_coll = true;
@@ -919,7 +942,7 @@ __global__ void __launch_bounds__(256, TR_ASYNC_MIN_BLOCKS) k_async(DevProblem P
                             TR_LANES(14);
                             tr::XS X;
                             double xr;
-                            FwdSinkT<WW> sink{TT, acc};
+                            FwdSinkT<WW, WALK> sink{TT, acc, 1.0, wq};
                             step_event<CE>(PP, RR, p, sink, X, xr);
                             if (p.pend == PEND_COLLIDE) {
                                 pend_coll = true;
@@ -1011,6 +1034,13 @@ __global__ void __launch_bounds__(256, TR_ASYNC_MIN_BLOCKS) k_async(DevProblem P
         if (!held) unlock_stash(st);
     }
     if (idle && lane == 0) atomicSub(&ctl->hungry, 1u);
+    if constexpr (WALK) {
+        if (wq) {   // the warp's remaining deferred mesh walks
+            __syncwarp();
+            const int nq_w = *(volatile int*)&wq->n;
+            walk_run<WW>(P, T, wq, 0, nq_w < WALKQ_CAP ? nq_w : WALKQ_CAP, FULLM);
+        }
+    }
     if (BATCHED) flush_lane(acc, A.tallies[acc_prob]);
     else flush_acc(acc, T);
 }
@@ -1057,15 +1087,34 @@ static size_t hash_stage(const DevProblem& P, size_t smem, size_t* total)
     return off;
 }
 
-int async_max_blocks_per_sm(const DevProblem& P, int dec, int stash_slots, bool pre)
+// Dynamic shared memory of a non-batched launch: the stash and the score
+// sums; with walk_smem, the monolithic kernel's mesh-walk queues (one WalkQ
+// per warp) when the problem has cells that lie in no single mesh voxel; the
+// union-grid hash when it fits.  Sets the offsets in P; returns the bytes.
+static size_t async_layout(DevProblem& P, int dec, int stash_slots, bool walk_smem)
 {
-    size_t smem;
+    size_t smem = async_smem_bytes(stash_slots, dec == DEC_LOOKUP, P.ww_lo != nullptr);
+    P.walk_smem_off = 0;
+    if (walk_smem && dec == DEC_MONO && P.has_mesh && P.mesh_walk) {
+        const size_t off = (smem + 15) & ~size_t(15);
+        P.walk_smem_off = (int)off;
+        smem = off + 8 * walkq_bytes();   // 256 threads: 8 warps
+    }
+    size_t total;
+    P.hash_smem_off = (int)hash_stage(P, smem, &total);
+    return total;
+}
+
+size_t walk_queue_bytes(int blocks) { return (size_t)blocks * 8 * sizeof(WalkQ); }
+
+int async_max_blocks_per_sm(const DevProblem& Pin, int dec, int stash_slots, bool pre, bool walk_smem)
+{
+    DevProblem P = Pin;
+    const size_t smem = async_layout(P, dec, stash_slots, walk_smem);
     if (P.ww_lo) {
-        hash_stage(P, async_smem_bytes(stash_slots, false, true), &smem);
         return P.kind == 1 ? occupancy_async<true, DEC_MONO, false, false, false, true>(smem)
                            : occupancy_async<false, DEC_MONO, false, false, false, true>(smem);
     }
-    hash_stage(P, async_smem_bytes(stash_slots, dec == DEC_LOOKUP), &smem);
     if (pre && dec == DEC_MONO)
         return P.kind == 1 ? occupancy_async<true, DEC_MONO, false, true>(smem)
                            : occupancy_async<false, DEC_MONO, false, true>(smem);
@@ -1110,9 +1159,7 @@ cudaError_t launch_async(const DevProblem& Pin, const RunParams& R, const AsyncA
                          ErrorWord* err, int blocks, cudaStream_t st, int* smem_bytes_out)
 {
     DevProblem P = Pin;
-    size_t smem;
-    P.hash_smem_off = (int)hash_stage(P, async_smem_bytes(A.stash_slots, A.dec == DEC_LOOKUP, P.ww_lo != nullptr),
-                                      &smem);
+    const size_t smem = async_layout(P, A.dec, A.stash_slots, A.walkq == nullptr);
     if (smem_bytes_out) *smem_bytes_out = (int)smem;
     count_launches(1);
     if (A.dec == DEC_MONO)

@@ -536,6 +536,8 @@ extern "C" tr_status tr_problem_create(const tr_geometry_desc* G, const tr_xs_de
                 off += ng[a];
             }
         }
+        P.mesh_walk = (P.has_mesh && std::find(c2v.begin(), c2v.end(), -1) != c2v.end()) ? 1 : 0;
+        P.walk_smem_off = 0;
         P.cell2vox = upload(pr, c2v.data(), c2v.size(), &ok);
     }
     if (n_tallies == 1 && Tl->n_energy_bins > 0) {
@@ -1061,6 +1063,12 @@ static tr_status transport(tr_problem* pr, const tr_run_opts* o, RunParams R, co
     }
     if (maxb < 1) return set_err(TR_ERR_INVALID, "stash does not fit in shared memory");
     const int bps = o->blocks_per_sm > 0 ? std::min(o->blocks_per_sm, maxb) : maxb;
+    // monolithic scheme: the warps' deferred mesh walks queue in global memory
+    // (L2-resident; in shared memory they would halve the L1 cache)
+    if (dec == DEC_MONO && P.has_mesh && P.mesh_walk) {
+        A.walkq = (WalkQ*)workspace(pr, "walkq", walk_queue_bytes(pr->sms * bps));
+        if (!A.walkq) return set_err(TR_ERR_NOMEM, "mesh-walk queue allocation failed");
+    }
     int smem = 0;
     LaunchTimer lt;
     TR_CUDA(cudaEventRecord(lt.a, st));

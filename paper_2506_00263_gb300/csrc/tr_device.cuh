@@ -132,6 +132,9 @@ struct DevProblem {
     int has_mesh, mesh_n[3], by_group, n_ebins, mesh_vox;
     double mesh_lo[3], mesh_hi[3], mesh_w[3], mesh_iw[3];
     const int *cell2vox;               // [nx | ny | nz]: mesh voxel holding geometry cell i on that axis, or -1
+    int mesh_walk;                     // some cell lies in no single mesh voxel: its segments take the mesh walk
+    int walk_smem_off;                 // > 0: this launch's warps queue those segments (WalkQ) at this byte
+                                       // offset of their dynamic shared memory (the monolithic asynchronous kernel)
     const double *e_edges;
     int mesh_size, energy_size;
     // time: histories start at t = 0 and end at the census time t_cen (timed

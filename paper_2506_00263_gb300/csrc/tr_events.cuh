@@ -189,18 +189,82 @@ __device__ __forceinline__ void mesh_tally_dda(const DevProblem& P, Op& op, cons
     }
 }
 
+// The one-voxel fast path: a segment in a geometry cell that lies inside one
+// mesh voxel puts its whole length there.  Returns false when the cell spans
+// several voxels (or none) on some axis, and the segment needs the walk.
 template <class Op>
-__device__ __forceinline__ void mesh_tally(const DevProblem& P, Op& op, const Particle& p, double x0, double y0,
-                                           double z0, double L, int goff)
+__device__ __forceinline__ bool mesh_tally_cell(const DevProblem& P, Op& op, const Particle& p, double L, int goff)
 {
     const int vx = __ldg(P.cell2vox + cell_i(p.cell));
     const int vy = __ldg(P.cell2vox + P.nx + cell_j(p.cell));
     const int vz = __ldg(P.cell2vox + P.nx + P.ny + cell_k(p.cell));
-    if ((vx | vy | vz) >= 0) {
-        op(goff + (vz * P.mesh_n[1] + vy) * P.mesh_n[0] + vx, L);
+    if ((vx | vy | vz) < 0) return false;
+    op(goff + (vz * P.mesh_n[1] + vy) * P.mesh_n[0] + vx, L);
+    return true;
+}
+
+template <class Op>
+__device__ __forceinline__ void mesh_tally(const DevProblem& P, Op& op, const Particle& p, double x0, double y0,
+                                           double z0, double L, int goff)
+{
+    if (!mesh_tally_cell(P, op, p, L, goff)) mesh_tally_dda(P, op, p, x0, y0, z0, L, goff);
+}
+
+// Deferred mesh walks.  The segments that need the walk come from the few
+// lanes of a warp whose particles are in such cells, so inline each FP64 warp
+// instruction of the walk serves one or two lanes (the FP64 pipe charges a
+// warp instruction the same however few lanes are active).  The monolithic
+// asynchronous kernel queues them per warp in shared memory instead and walks
+// them 32 at a time.  The mesh tally sums fixed-point pieces, so their order
+// does not change it, and each piece comes from the same inputs as inline:
+// the tallies are the same bits either way.
+constexpr int WALKQ_CAP = 64;          // a warp drains 32 entries before each pass: at most 31 + 32 queued
+struct WalkQ {
+    double x0[WALKQ_CAP], y0[WALKQ_CAP], z0[WALKQ_CAP];
+    double u[WALKQ_CAP], v[WALKQ_CAP], w[WALKQ_CAP];
+    double iu[WALKQ_CAP], iv[WALKQ_CAP], iw[WALKQ_CAP];
+    double len[WALKQ_CAP], wt[WALKQ_CAP];
+    int goff[WALKQ_CAP];
+    int n;
+};
+__host__ __device__ constexpr size_t walkq_bytes() { return (sizeof(WalkQ) + 15) & ~size_t(15); }
+
+__device__ __forceinline__ void walk_push(WalkQ* q, const Particle& p, double x0, double y0, double z0, double L,
+                                          int goff, double wt, ErrorWord* err)
+{
+    const int i = q ? atomicAdd(&q->n, 1) : WALKQ_CAP;
+    if (i >= WALKQ_CAP) {   // (the drain before every pass rules this out; no queue: a launch error)
+        if (err) atomicCAS(&err->code, 0, ERR_CAPACITY);
         return;
     }
-    mesh_tally_dda(P, op, p, x0, y0, z0, L, goff);
+    q->x0[i] = x0; q->y0[i] = y0; q->z0[i] = z0;
+    q->u[i] = p.u; q->v[i] = p.v; q->w[i] = p.w;
+    q->iu[i] = p.iu; q->iv[i] = p.iv; q->iw[i] = p.iw;
+    q->len[i] = L;
+    q->wt[i] = wt;
+    q->goff[i] = goff;
+}
+
+// Walks entries [first, n) of a warp's queue with the lanes of m (every lane
+// of m calls it).
+template <bool WW>
+static __device__ __forceinline__ void walk_run(const DevProblem& P, const Tallies& T, const WalkQ* q, int first, int n,
+                                             unsigned m)
+{
+    const int lane = (int)(threadIdx.x & 31);
+    const int nl = __popc(m), rank = __popc(m & ((1u << lane) - 1u));
+    for (int i = first + rank; i < n; i += nl) {
+        Particle d;
+        d.u = q->u[i]; d.v = q->v[i]; d.w = q->w[i];
+        d.iu = q->iu[i]; d.iv = q->iv[i]; d.iw = q->iw[i];
+        if (WW) {
+            MeshAtomicW op{T, q->wt[i]};
+            mesh_tally_dda(P, op, d, q->x0[i], q->y0[i], q->z0[i], q->len[i], q->goff[i]);
+        } else {
+            MeshAtomic op{T};
+            mesh_tally_dda(P, op, d, q->x0[i], q->y0[i], q->z0[i], q->len[i], q->goff[i]);
+        }
+    }
 }
 
 // Energy-bin flux tally per material: bin = largest b with e[b] <= E < e[b+1].
@@ -322,12 +386,13 @@ static __device__ __noinline__ CensusStep census_step(double v_c, const double* 
 // Forward tally sink: track-length scores into the tallies and the
 // particle's running scalar scores.  WW: weighted particles (weight-window
 // problems), every score times the particle's weight.
-template <bool WW>
+template <bool WW, bool WQ = false>
 struct FwdSinkT {
     static constexpr bool kWW = WW;
     const Tallies& T;
     Acc& acc;
     double wt = 1.0;                   // WW: the particle's weight (set by segment for time_segment)
+    WalkQ* wq = nullptr;               // WQ: the warp's queue of deferred mesh walks
     template <bool CE>
     __device__ __forceinline__ void segment(const DevProblem& P, Particle& p, double x0, double y0, double z0,
                                             double dist, int m, const XS& X)
@@ -339,7 +404,17 @@ struct FwdSinkT {
         if (!CE) p.hp = __fma_rn(dl, X.nsf, p.hp);   // continuous energy: nu Sigma_f = 0
         if (P.has_mesh && gt0(dist)) {
             const int goff = (!CE && P.by_group) ? p.g * P.mesh_vox : 0;
-            if (WW) {
+            if (WQ) {
+                bool one;
+                if (WW) {
+                    MeshAtomicW op{T, p.wt};
+                    one = mesh_tally_cell(P, op, p, dist, goff);
+                } else {
+                    MeshAtomic op{T};
+                    one = mesh_tally_cell(P, op, p, dist, goff);
+                }
+                if (!one) walk_push(wq, p, x0, y0, z0, dist, goff, WW ? p.wt : 1.0, T.err);
+            } else if (WW) {
                 MeshAtomicW op{T, p.wt};
                 mesh_tally(P, op, p, x0, y0, z0, dist, goff);
             } else {
@@ -781,16 +856,18 @@ __device__ __forceinline__ bool finish_event(const DevProblem& P, const RunParam
 
 // One monolithic event (step followed by collision or surface crossing).
 // em: the lanes of this warp that run this event together (from a ballot), or 0.
-template <bool CE, bool WW = false>
+// WQ: mesh walks go to the warp's queue wq.
+template <bool CE, bool WW = false, bool WQ = false>
 __device__ __forceinline__ bool mono_event(const DevProblem& P, const RunParams& R, Particle& p, const Tallies& T,
-                                           Acc& acc, const Bank& B, ErrorWord* err, unsigned em = 0u)
+                                           Acc& acc, const Bank& B, ErrorWord* err, unsigned em = 0u,
+                                           WalkQ* wq = nullptr)
 {
     TR_LANES(10);
     XS X;
     CEKeep keep;
     if (CE) X.keep = &keep;   // the collision below reuses the lookup's terms
     double xi_react;
-    FwdSinkT<WW> sink{T, acc};
+    FwdSinkT<WW, WQ> sink{T, acc, 1.0, wq};
     step_event<CE>(P, R, p, sink, X, xi_react);
     const bool coll = p.pend == PEND_COLLIDE;
     const unsigned cm = em ? __ballot_sync(em, coll) : 0u;

@@ -67,6 +67,8 @@ cudaError_t launch_stack_next(StackCtl* ctl, const RunParams* Rd, ErrorWord* err
 // from kernel arguments, in stream order.
 cudaError_t launch_stack_setup(const RunParams& R, const StackCtl& h, RunParams* Rd, StackCtl* ctl, cudaStream_t st);
 
+struct WalkQ;   // a warp's deferred mesh walks (tr_events.cuh)
+
 struct AsyncArgs {
     SoA links;                         // global link arena: n_links * 32 particle slots
     unsigned* link_next;               // per link: next link in its list
@@ -85,11 +87,16 @@ struct AsyncArgs {
     const Tallies* tallies;
     const unsigned long long* hist_off;   // n_probs + 1 cumulative history counts
     int n_probs;
+    // monolithic scheme, problems whose mesh tally needs walks: one queue per
+    // warp of the grid in global memory (walk_queue_bytes), or NULL: the
+    // queues take shared memory (async_max_blocks_per_sm with walk_smem)
+    WalkQ* walkq;
 };
 
 cudaError_t launch_async(const DevProblem& P, const RunParams& R, const AsyncArgs& A, const Tallies& T, ErrorWord* err,
                          int blocks, cudaStream_t st, int* smem_bytes_out);
-int async_max_blocks_per_sm(const DevProblem& P, int dec, int stash_slots, bool pre = false);
+int async_max_blocks_per_sm(const DevProblem& P, int dec, int stash_slots, bool pre = false, bool walk_smem = false);
+size_t walk_queue_bytes(int blocks);   // AsyncArgs::walkq of a launch of this many blocks
 // Samples the source particles of histories [0, R.n_hist) into A.pre.
 cudaError_t launch_presample(const DevProblem& P, const RunParams& R, const AsyncArgs& A, int blocks, cudaStream_t st);
 cudaError_t launch_async_batched(const DevProblem& P0, const RunParams& R, const AsyncArgs& A, ErrorWord* err,

@@ -195,7 +195,8 @@ extern "C" tr_status tr_run_fixed_source_noalloc(tr_problem* problem, const tr_r
     T.fin_type = counts + 8;
     T.err = err;
     if (o->n_histories > 0) {
-        const int maxb = async_max_blocks_per_sm(P, A.dec, S);
+        // (mesh-walk queues, if the problem needs them, in shared memory: nothing to allocate)
+        const int maxb = async_max_blocks_per_sm(P, A.dec, S, false, true);
         if (maxb < 1) return fail(TR_ERR_INVALID, "stash does not fit in shared memory");
         const int bps = o->blocks_per_sm > 0 ? (o->blocks_per_sm < maxb ? o->blocks_per_sm : maxb) : maxb;
         int smem = 0;
