@@ -481,10 +481,11 @@ __device__ __forceinline__ void step_event(const DevProblem& P, const RunParams&
         const double a = __fma_rn(p.u, p.u, p.v * p.v);
         const double disc = __fma_rn(kk, kk, -(a * cc));
         const double sq = tr_sqrt(lt0(disc) ? 0.0 : disc);
-        const double d_in = (sq - kk) * p.ia;
-        const double d_out = ((-kk) - sq) * p.ia;
+        // inside (sq - k) ia, outside ((-k) - sq) ia = ((-sq) - k) ia (IEEE
+        // addition commutes): one subtraction and one product for both
+        const double d = ((in ? sq : flip_sign(sq)) - kk) * p.ia;
         const bool hit = gt0(a) && (in || (lt0(kk) && ge0(disc)));
-        dcyl = hit ? clamp0(in ? d_in : d_out) : INF;
+        dcyl = hit ? clamp0(d) : INF;
     }
     TR_LANES(3);
     unsigned flags = 0u;
