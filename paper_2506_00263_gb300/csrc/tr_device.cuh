@@ -655,6 +655,7 @@ __device__ __forceinline__ void xs_ce(const DevProblem& P, int m, double E, XS& 
     const int u = union_index(P, E);
     double cum = 0.0, sa = 0.0;
     int kept = 0;
+#pragma unroll 4   // (measured slightly faster: the nuclides' loads issue together)
     for (int n = 0; n < P.n_nuc; ++n) {
         const double N = __ldg(P.dens + m * P.n_nuc + n);
         if (!gt0(N)) continue;
