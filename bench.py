@@ -877,13 +877,13 @@ def run_lattice_sweep(args):
 # (asynchronous monolithic, 512 events between remaps) and the CE pin cell
 # (1e6 histories, 100 bins, 64 events between remaps).  Each figure carries
 # the kernel_digest() of the sources it was measured on.
-FP64_OPS = {"lattice": (51.7, "fed5a6b948d70ec3"), "ce": (93.9, "fed5a6b948d70ec3")}
+FP64_OPS = {"lattice": (52.1, "1e6989d1c99dfc06"), "ce": (94.1, "1e6989d1c99dfc06")}
 # DRAM bytes (read + write), dram__bytes_read.sum + dram__bytes_write.sum, of
 # one 1e6-history lattice batch's transport (source pre-sampling and transport
 # kernels, asynchronous monolithic, 512 events between remaps; the mean of the
 # timed step's three batches) and of one 1e6-history CE pin-cell run (the same
 # two kernels, 64 events between remaps, 100 energy bins).
-TRAFFIC = {"lattice": (229.7e6, "fed5a6b948d70ec3"), "ce": (224.0e6, "fed5a6b948d70ec3")}
+TRAFFIC = {"lattice": (248.5e6, "1e6989d1c99dfc06"), "ce": (223.1e6, "1e6989d1c99dfc06")}
 
 
 def _fresh_traffic(key):
