@@ -214,8 +214,8 @@ __device__ __forceinline__ void mesh_tally(const DevProblem& P, Op& op, const Pa
 // lanes of a warp whose particles are in such cells, so inline each FP64 warp
 // instruction of the walk serves one or two lanes (the FP64 pipe charges a
 // warp instruction the same however few lanes are active).  The monolithic
-// asynchronous kernel queues them per warp in shared memory instead and walks
-// them 32 at a time.  The mesh tally sums fixed-point pieces, so their order
+// asynchronous kernel instead queues them per warp (in global memory, or in
+// shared memory for the allocation-free entry) and walks them 32 at a time.  The mesh tally sums fixed-point pieces, so their order
 // does not change it, and each piece comes from the same inputs as inline:
 // the tallies are the same bits either way.
 constexpr int WALKQ_CAP = 64;          // a warp drains 32 entries before each pass: at most 31 + 32 queued
@@ -248,8 +248,8 @@ __device__ __forceinline__ void walk_push(WalkQ* q, const Particle& p, double x0
 // Walks entries [first, n) of a warp's queue with the lanes of m (every lane
 // of m calls it).
 template <bool WW>
-static __device__ __forceinline__ void walk_run(const DevProblem& P, const Tallies& T, const WalkQ* q, int first, int n,
-                                             unsigned m)
+static __device__ __forceinline__ void walk_run(const DevProblem& P, const Tallies& T, const WalkQ* q, int first,
+                                                int n, unsigned m)
 {
     const int lane = (int)(threadIdx.x & 31);
     const int nl = __popc(m), rank = __popc(m & ((1u << lane) - 1u));
