@@ -877,13 +877,13 @@ def run_lattice_sweep(args):
 # (asynchronous monolithic, 512 events between remaps) and the CE pin cell
 # (1e6 histories, 100 bins, 64 events between remaps).  Each figure carries
 # the kernel_digest() of the sources it was measured on.
-FP64_OPS = {"lattice": (52.1, "1e6989d1c99dfc06"), "ce": (94.1, "1e6989d1c99dfc06")}
+FP64_OPS = {"lattice": (52.1, "2b3524419633bdfe"), "ce": (94.1, "2b3524419633bdfe")}
 # DRAM bytes (read + write), dram__bytes_read.sum + dram__bytes_write.sum, of
 # one 1e6-history lattice batch's transport (source pre-sampling and transport
 # kernels, asynchronous monolithic, 512 events between remaps; the mean of the
 # timed step's three batches) and of one 1e6-history CE pin-cell run (the same
 # two kernels, 64 events between remaps, 100 energy bins).
-TRAFFIC = {"lattice": (248.5e6, "1e6989d1c99dfc06"), "ce": (223.1e6, "1e6989d1c99dfc06")}
+TRAFFIC = {"lattice": (248.5e6, "2b3524419633bdfe"), "ce": (223.2e6, "2b3524419633bdfe")}
 
 
 def _fresh_traffic(key):
