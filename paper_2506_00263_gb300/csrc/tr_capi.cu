@@ -1640,8 +1640,8 @@ std::vector<unsigned long long> batch_signature(tr_problem* const* probs, int32_
 
 // Enqueue one batched run (everything from zeroing to normalisation) on the
 // leader's stream; used directly and under stream capture.
-static tr_status enqueue_batched(tr_problem* lead, tr_problem* const* probs, int32_t n, const uint64_t* nh,
-                                 const tr_run_opts* o, const BatchTuning& tune, DevProblem* d_probs, Tallies* d_tal,
+static tr_status enqueue_batched(tr_problem* lead, tr_problem* const* probs, int32_t n, const tr_run_opts* o,
+                                 const BatchTuning& tune, DevProblem* d_probs, Tallies* d_tal,
                                  unsigned long long* d_off, ScaleJob* d_jobs, int n_jobs, const AsyncArgs& A0,
                                  unsigned long long total, int maxch, double* hist_partial)
 {
@@ -1811,8 +1811,8 @@ extern "C" tr_status tr_run_batched(tr_problem* const* probs, int32_t n, const u
         BatchTuning pick = cands[0];
         for (const BatchTuning& t : cands) {
             TR_CUDA(cudaEventRecord(e0, st));
-            s = enqueue_batched(lead, probs, n, sample.data(), opts, t, d_probs, d_tal, d_soff, d_jobs, 0, A, stotal,
-                                maxch, hist_partial);
+            s = enqueue_batched(lead, probs, n, opts, t, d_probs, d_tal, d_soff, d_jobs, 0, A, stotal, maxch,
+                                hist_partial);
             if (s != TR_OK) return s;
             TR_CUDA(cudaEventRecord(e1, st));
             TR_CUDA(cudaEventSynchronize(e1));
@@ -1865,8 +1865,8 @@ extern "C" tr_status tr_run_batched(tr_problem* const* probs, int32_t n, const u
         // capture on a private stream: the leader's stream is swapped for the capture
         cudaStream_t saved = lead->stream;
         lead->stream = cap;
-        s = enqueue_batched(lead, probs, n, n_histories, opts, tune, d_probs, d_tal, d_off, d_jobs, (int)hj.size(), A,
-                            total, maxch, hist_partial);
+        s = enqueue_batched(lead, probs, n, opts, tune, d_probs, d_tal, d_off, d_jobs, (int)hj.size(), A, total, maxch,
+                            hist_partial);
         lead->stream = saved;
         const cudaError_t ce = cudaStreamEndCapture(cap, &g);
         cudaStreamDestroy(cap);
